@@ -1,0 +1,32 @@
+"""Thermal observables from one batch of samples (Sec. II Eq. 11, Sec. III.A Eq. 13).
+
+TEST INFRASTRUCTURE (oracle): see oracle/__init__.py.
+
+After a total imaginary time t = sum of the SR steps tau, the PEPS approximates
+e^{-t calH}|I> = |rho_beta> with beta = 2t (Eq. 3), and Eq. 11 gives the internal energy
+of the thermal state at inverse temperature 2 beta = 4t, which is beta_obs here.  That
+state is (rho rho^T + rho^T rho) / (2 Tr rho rho^T); with w_i the sample weights:
+  <H>   = 1/2 sum_i w_i (E_sys,i + E_anc,i)                (Eq. 11)
+  <H^2> = 1/2 sum_i w_i (E_sys,i^2 + E_anc,i^2)             (||H rho||^2 = sum |rho|^2 E_sys^2)
+  C/N   = beta_obs^2 (<H^2> - <H>^2) / N
+  <Mz^2>= 1/2 sum_i w_i (M(s_i)^2 + M(s'_i)^2),  chi = beta_obs <Mz^2> / N, <Mz>^2 := 0 (Eq. 13)
+"""
+import numpy as np
+
+from .lattice import spin_anc, spin_sys, sz_of
+
+
+def observables(lat, t, w, e_sys, e_anc, S_batch):
+    beta_obs = 4.0 * t
+    w = np.asarray(w, dtype=np.float64)
+    es, ea = np.asarray(e_sys), np.asarray(e_anc)
+    H1 = 0.5 * float(w @ (es + ea))
+    H2 = 0.5 * float(w @ (es * es + ea * ea))
+    S_batch = np.asarray(S_batch)
+    Ms = np.sum(sz_of(spin_sys(S_batch)), axis=1)
+    Ma = np.sum(sz_of(spin_anc(S_batch)), axis=1)
+    M2 = 0.5 * float(w @ (Ms * Ms + Ma * Ma))
+    N = lat.N
+    diag = np.all(spin_sys(S_batch) == spin_anc(S_batch), axis=1)
+    return dict(t=t, beta_obs=beta_obs, E_site=H1 / N, C_site=beta_obs ** 2 * (H2 - H1 * H1) / N,
+                chi=beta_obs * M2 / N, Mz2=M2, diag_frac=float(np.mean(diag)))
