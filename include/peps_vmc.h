@@ -1,0 +1,157 @@
+/*
+ * peps_vmc.h -- C ABI of the GB300 (sm_103a) finite-temperature PEPS-VMC library.
+ *
+ * Method: Zhang, Zhang, Wang, He, "Scalable tensor network algorithm for thermal quantum
+ * many-body systems in two dimension", arXiv:2409.05285.  The vectorised density matrix
+ * |rho> = sum_S rho_theta(S)|S> (Sec. II Eqs. 2-4) is a PEPS with physical index
+ * S = 2 s + s' (system spin s, ancilla spin s'; 0 = up).  Starting from |I> (beta = 0,
+ * App. A perturbation of the zero entries) each stochastic-reconfiguration step
+ * theta' = theta - tau (G + eps)^-1 g (Eqs. 5-7, 10) approximates exp(-tau calH)|rho>,
+ * calH = H x I + I x H^T (Eq. 3), H the J1-J2 Heisenberg model (Eq. 12) on an open
+ * L1 x L2 square lattice.  After total imaginary time t the sampled observables are those
+ * of the thermal state at inverse temperature beta_obs = 4 t (Eq. 11).
+ *
+ * Layouts (all row-major):
+ *   site i = r * L2 + c.  Leg dimensions: left/right/up/down = D, or 1 on the open edge.
+ *   theta      float64 [N_p]: per site the block [4][dl][dr][du][dd]; N_p = 4 sum_i sz_i.
+ *   configs    uint8 [n][L1*L2], entries 0..3.
+ *   O rows     [n][N_o] (N_o = sum_i sz_i): per site the derivative of log rho with
+ *              respect to the slice T_i^{S_i} (Eq. 8), float64 for PEPS_FP64, float32
+ *              otherwise.
+ *
+ * Ownership: the context owns every device buffer it allocates; the caller owns every
+ * pointer it passes.  All work is enqueued on the stream given at peps_init (a
+ * cudaStream_t passed as void*; NULL = legacy default stream).  Calls that return host
+ * results synchronise that stream before returning.  One context must not be used from
+ * two host threads at once.
+ *
+ * Errors: every int-returning call returns PEPS_OK (0) on success, a negative PEPS_E*
+ * code on failure (the context keeps a message, see peps_last_error), or a positive
+ * warning code.
+ */
+#ifndef PEPS_VMC_H
+#define PEPS_VMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PEPS_OK 0
+#define PEPS_WARN_CG_MAXIT 1 /* CG stopped at max_cg; the update was still applied */
+#define PEPS_EINVAL (-1)     /* invalid argument (sizes, null pointers, limits) */
+#define PEPS_ENOMEM (-2)     /* device allocation failed or exceeds the context budget */
+#define PEPS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define PEPS_ESTATE (-4)     /* call out of order (e.g. sr_step before an evaluation) */
+#define PEPS_ENOTFINITE (-5) /* non-finite amplitude, energy or CG scalar */
+
+/* Arithmetic of the per-sample contraction (environment, amplitude, E_loc, O).  The
+ * log-amplitude accumulation, the SR reductions and CG, and the observables are float64
+ * in every mode. */
+#define PEPS_FP64 0 /* float64 throughout */
+#define PEPS_FP32 1 /* float32 contraction and truncation, float32 O storage */
+
+#define PEPS_MODEL_J1J2 0 /* Eq. 12: J1 sum_<ij> S_i.S_j + J2 sum_<<ij>> S_i.S_j */
+
+typedef struct peps_ctx peps_ctx;
+
+/* Problem statement (Sec. II/III): lattice, couplings, bond D, boundary bond chi (D_c),
+ * number of Markov chains (= samples per SR step), arithmetic, initial perturbation. */
+typedef struct {
+  int L1, L2;        /* rows, columns; 2 <= L1, L2 <= 16 */
+  int model;         /* PEPS_MODEL_J1J2 */
+  double J1, J2;     /* couplings of Eq. 12 */
+  int D;             /* PEPS bond dimension, 1 <= D <= 8 */
+  int chi;           /* boundary-MPS bond dimension, 1 <= chi <= 64 */
+  int n_chains;      /* chains advanced per sweep and samples per SR step, >= 1 */
+  int precision;     /* PEPS_FP64 | PEPS_FP32 */
+  double init_noise; /* amplitude a of the U[-a, a] perturbation of the zero entries */
+  uint64_t seed;     /* Philox key for the perturbation, the chain starts and Metropolis */
+  int n_blocks;      /* persistent blocks of the sample kernels; 0 = automatic */
+} peps_params;
+
+/* Results of one step (observables of Eq. 11, C_v, Eq. 13 at beta_obs = 4 t). */
+typedef struct {
+  double t;         /* imaginary time sum(tau) at which the samples were taken */
+  double beta_obs;  /* 4 t */
+  double E_site;    /* <H>/N */
+  double E_err;     /* standard error of E_site (p = 2: plain; p = 1: weighted) */
+  double C_site;    /* beta_obs^2 (<H^2> - <H>^2) / N */
+  double chi_sus;   /* beta_obs <Mz^2> / N */
+  double accept;    /* Metropolis acceptance ratio of the last peps_mc_sweep */
+  double diag_frac; /* fraction of samples with s = s' on every site */
+  int cg_iters;     /* CG iterations of the last peps_sr_step */
+  double cg_resid;  /* |r| / |g| at exit */
+  int p;            /* sampling exponent of the samples (2 or 1) */
+} peps_stats;
+
+/* Creates a context: allocates device buffers, sets theta to the perturbed beta = 0
+ * state (App. A), and the chains to diagonal configurations (s = s') drawn from Philox.
+ * stream: cudaStream_t as void* (may be NULL).  Returns PEPS_EINVAL for sizes outside
+ * the limits, PEPS_ENOMEM when allocation fails. */
+int peps_init(const peps_params* params, void* stream, peps_ctx** out);
+
+/* Advances every chain by n_sweeps Metropolis sweeps sampling |rho|^p, p = 2 (Sec. II)
+ * or p = 1 (reweighted sampling, App. A Eq. A1).  Move set per sweep: both-flips,
+ * system-only and ancilla-only exchanges on horizontal and vertical bonds. */
+int peps_mc_sweep(peps_ctx* ctx, int n_sweeps, int p);
+
+/* Evaluates nb configurations: log|rho|, sign, E_sys, E_anc (E_loc of Eq. 9 is their
+ * sum) and, when O is non-null, the O rows (Eq. 8).  S == NULL evaluates the context's
+ * own chains (nb must equal n_chains) and keeps the results for peps_sr_step /
+ * peps_observables.  on_device != 0: S and every output pointer are device pointers;
+ * otherwise host pointers (copies are made on the context stream).  Null output
+ * pointers are skipped.  O has the element type of the precision (double for
+ * PEPS_FP64, float otherwise). */
+int peps_eval_batch(peps_ctx* ctx, const uint8_t* S, int nb, int on_device, double* log_abs,
+                    int8_t* sign, double* e_sys, double* e_anc, void* O);
+
+/* One SR update from the last evaluation of the chains (sampled with exponent p):
+ * weights (1/n for p = 2, |rho|/sum|rho| for p = 1), g = <O (E_loc - <E_loc>)>, CG solve
+ * of (G + eps I) x = g from x = 0 with the relative-residual test tol before each
+ * iteration and at most max_cg iterations, theta -= tau x, t += tau.  stats (may be
+ * NULL) receives the observables of those samples and the CG result.  Returns
+ * PEPS_WARN_CG_MAXIT when CG stopped at max_cg. */
+int peps_sr_step(peps_ctx* ctx, double tau, double eps, int max_cg, double cg_tol, int p,
+                 peps_stats* stats);
+
+/* Observables of the last evaluation of the chains (sampled with exponent p). */
+int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
+
+/* One whole cooling step: n_sweeps sweeps, evaluation of the chains, SR update. */
+int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
+              double cg_tol, peps_stats* stats);
+
+/* Parameter vector and chain configurations (host buffers).  n must equal N_p, or
+ * n_chains * L1 * L2 for the configurations. */
+int peps_get_theta(peps_ctx* ctx, double* host, size_t n);
+int peps_set_theta(peps_ctx* ctx, const double* host, size_t n);
+int peps_get_configs(peps_ctx* ctx, uint8_t* host, size_t n);
+int peps_set_configs(peps_ctx* ctx, const uint8_t* host, size_t n);
+
+/* Sizes: N_p, N_o, and the number of sweeps done so far (the Philox sweep counter). */
+size_t peps_num_params(const peps_ctx* ctx);
+size_t peps_o_row_len(const peps_ctx* ctx);
+int64_t peps_sweeps_done(const peps_ctx* ctx);
+int peps_set_sweeps_done(peps_ctx* ctx, int64_t sweeps);
+
+/* Device counters of the last peps_eval_batch / peps_mc_sweep launch: algorithmic
+ * flops (contractions, Householder, Jacobi), Jacobi sweeps. */
+int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
+
+/* Releases every device buffer of the context (NULL is ignored). */
+void peps_free(peps_ctx* ctx);
+
+/* Message of the last error on this context ("" when none). */
+const char* peps_last_error(const peps_ctx* ctx);
+
+/* Library version string. */
+const char* peps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PEPS_VMC_H */

@@ -1,0 +1,224 @@
+"""ctypes binding of libpeps_vmc.so (declarations: include/peps_vmc.h).
+
+Argument marshalling only: every step of the cooling path runs in the CUDA library.
+Importing works without a GPU; creating a context needs the built library and a GPU and
+raises if either is missing (there is no CPU fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from .build import LIB
+
+PEPS_OK = 0
+PEPS_WARN_CG_MAXIT = 1
+PEPS_EINVAL = -1
+PEPS_ENOMEM = -2
+PEPS_ECUDA = -3
+PEPS_ESTATE = -4
+PEPS_ENOTFINITE = -5
+PEPS_FP64 = 0
+PEPS_FP32 = 1
+PEPS_MODEL_J1J2 = 0
+
+EXPORTS = [
+    "peps_init", "peps_mc_sweep", "peps_eval_batch", "peps_sr_step", "peps_observables",
+    "peps_step", "peps_get_theta", "peps_set_theta", "peps_get_configs", "peps_set_configs",
+    "peps_num_params", "peps_o_row_len", "peps_sweeps_done", "peps_set_sweeps_done",
+    "peps_last_counters", "peps_free", "peps_last_error", "peps_version",
+]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L1", ctypes.c_int), ("L2", ctypes.c_int), ("model", ctypes.c_int),
+                ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("D", ctypes.c_int),
+                ("chi", ctypes.c_int), ("n_chains", ctypes.c_int), ("precision", ctypes.c_int),
+                ("init_noise", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("n_blocks", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("beta_obs", ctypes.c_double), ("E_site", ctypes.c_double),
+                ("E_err", ctypes.c_double), ("C_site", ctypes.c_double), ("chi_sus", ctypes.c_double),
+                ("accept", ctypes.c_double), ("diag_frac", ctypes.c_double), ("cg_iters", ctypes.c_int),
+                ("cg_resid", ctypes.c_double), ("p", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=None):
+    """Loads the library (once).  Raises OSError when it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        raise OSError(f"libpeps_vmc.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.peps_init.argtypes = [ctypes.POINTER(Params), vp, ctypes.POINTER(vp)]
+    lib.peps_mc_sweep.argtypes = [vp, ip, ip]
+    lib.peps_eval_batch.argtypes = [vp, vp, ip, ip, vp, vp, vp, vp, vp]
+    lib.peps_sr_step.argtypes = [vp, dp, dp, ip, dp, ip, ctypes.POINTER(Stats)]
+    lib.peps_observables.argtypes = [vp, ip, ctypes.POINTER(Stats)]
+    lib.peps_step.argtypes = [vp, ip, ip, dp, dp, ip, dp, ctypes.POINTER(Stats)]
+    lib.peps_get_theta.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.peps_set_theta.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.peps_get_configs.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.peps_set_configs.argtypes = [vp, vp, ctypes.c_size_t]
+    lib.peps_num_params.argtypes = [vp]
+    lib.peps_num_params.restype = ctypes.c_size_t
+    lib.peps_o_row_len.argtypes = [vp]
+    lib.peps_o_row_len.restype = ctypes.c_size_t
+    lib.peps_sweeps_done.argtypes = [vp]
+    lib.peps_sweeps_done.restype = ctypes.c_int64
+    lib.peps_set_sweeps_done.argtypes = [vp, ctypes.c_int64]
+    lib.peps_last_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_int64)]
+    lib.peps_free.argtypes = [vp]
+    lib.peps_free.restype = None
+    lib.peps_last_error.argtypes = [vp]
+    lib.peps_last_error.restype = ctypes.c_char_p
+    lib.peps_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+class PepsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"peps error {code}: {msg}")
+        self.code = code
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """One cooling run: PEPS parameters, Markov chains and work buffers on the GPU."""
+
+    def __init__(self, L1, L2, D, chi, n_chains, J1=1.0, J2=0.0, precision=PEPS_FP64,
+                 init_noise=1e-3, seed=0, n_blocks=0, stream=None):
+        self.lib = load()
+        self.params = Params(L1=L1, L2=L2, model=PEPS_MODEL_J1J2, J1=J1, J2=J2, D=D, chi=chi,
+                             n_chains=n_chains, precision=precision, init_noise=init_noise,
+                             seed=seed, n_blocks=n_blocks)
+        self.ctx = ctypes.c_void_p()
+        rc = self.lib.peps_init(ctypes.byref(self.params), stream, ctypes.byref(self.ctx))
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_init failed")
+        self.L1, self.L2, self.N = L1, L2, L1 * L2
+        self.n_chains = n_chains
+        self.precision = precision
+        self.Np = int(self.lib.peps_num_params(self.ctx))
+        self.No = int(self.lib.peps_o_row_len(self.ctx))
+        self.o_dtype = np.float64 if precision == PEPS_FP64 else np.float32
+
+    def _check(self, rc, allow=(PEPS_OK,)):
+        if rc not in allow:
+            raise PepsError(rc, self.lib.peps_last_error(self.ctx).decode())
+        return rc
+
+    def close(self):
+        if self.ctx:
+            self.lib.peps_free(self.ctx)
+            self.ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- state
+    def get_theta(self):
+        out = np.empty(self.Np, np.float64)
+        self._check(self.lib.peps_get_theta(self.ctx, _ptr(out), self.Np))
+        return out
+
+    def set_theta(self, theta):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        self._check(self.lib.peps_set_theta(self.ctx, _ptr(th), th.size))
+
+    def get_configs(self):
+        out = np.empty((self.n_chains, self.N), np.uint8)
+        self._check(self.lib.peps_get_configs(self.ctx, _ptr(out), out.size))
+        return out
+
+    def set_configs(self, S):
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        self._check(self.lib.peps_set_configs(self.ctx, _ptr(S), S.size))
+
+    @property
+    def sweeps_done(self):
+        return int(self.lib.peps_sweeps_done(self.ctx))
+
+    @sweeps_done.setter
+    def sweeps_done(self, v):
+        self._check(self.lib.peps_set_sweeps_done(self.ctx, int(v)))
+
+    # -- the cooling path
+    def mc_sweep(self, n_sweeps=1, p=2):
+        self._check(self.lib.peps_mc_sweep(self.ctx, n_sweeps, p))
+
+    def eval_batch(self, S=None, with_O=True):
+        """Evaluates host configurations S (uint8 [nb][N]); S=None evaluates the chains.
+        Returns numpy arrays (log_abs, sign, e_sys, e_anc, O or None)."""
+        nb = self.n_chains if S is None else int(S.shape[0])
+        la = np.empty(nb, np.float64)
+        sg = np.empty(nb, np.int8)
+        es = np.empty(nb, np.float64)
+        ea = np.empty(nb, np.float64)
+        O = np.empty((nb, self.No), self.o_dtype) if with_O else None
+        Sp = None if S is None else _ptr(np.ascontiguousarray(S, dtype=np.uint8))
+        self._check(self.lib.peps_eval_batch(self.ctx, Sp, nb, 0, _ptr(la), _ptr(sg), _ptr(es),
+                                             _ptr(ea), _ptr(O)))
+        return la, sg, es, ea, O
+
+    def eval_batch_device(self, S, log_abs, sign, e_sys, e_anc, O=None):
+        """Device-pointer variant (torch CUDA tensors)."""
+        self._check(self.lib.peps_eval_batch(self.ctx, _ptr(S), int(S.shape[0]), 1, _ptr(log_abs),
+                                             _ptr(sign), _ptr(e_sys), _ptr(e_anc), _ptr(O)))
+
+    def eval_chains(self):
+        """Evaluates the chains and keeps the results on the device for sr_step."""
+        self._check(self.lib.peps_eval_batch(self.ctx, None, self.n_chains, 1, None, None, None,
+                                             None, None))
+
+    def sr_step(self, tau, eps=1e-4, max_cg=100, cg_tol=1e-10, p=2):
+        st = Stats()
+        rc = self._check(self.lib.peps_sr_step(self.ctx, tau, eps, max_cg, cg_tol, p,
+                                               ctypes.byref(st)),
+                         allow=(PEPS_OK, PEPS_WARN_CG_MAXIT))
+        d = st.as_dict()
+        d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
+        return d
+
+    def observables(self, p=2):
+        st = Stats()
+        self._check(self.lib.peps_observables(self.ctx, p, ctypes.byref(st)))
+        return st.as_dict()
+
+    def step(self, n_sweeps=1, p=2, tau=0.02, eps=1e-4, max_cg=100, cg_tol=1e-10):
+        st = Stats()
+        rc = self._check(self.lib.peps_step(self.ctx, n_sweeps, p, tau, eps, max_cg, cg_tol,
+                                            ctypes.byref(st)),
+                         allow=(PEPS_OK, PEPS_WARN_CG_MAXIT))
+        d = st.as_dict()
+        d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
+        return d
+
+    def counters(self):
+        f = ctypes.c_double()
+        j = ctypes.c_int64()
+        self._check(self.lib.peps_last_counters(self.ctx, ctypes.byref(f), ctypes.byref(j)))
+        return f.value, j.value

@@ -1,0 +1,668 @@
+// C ABI of the PEPS-VMC cooling step (declarations and contracts: include/peps_vmc.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/peps_vmc.h"
+#include "pv_philox.cuh"
+#include "pv_sample.cuh"
+#include "pv_sr.cuh"
+
+using namespace pv;
+
+namespace {
+
+constexpr int SAMPLE_THREADS = 256;
+constexpr double JTOL_F64 = 1e-15;
+constexpr float JTOL_F32 = 2e-7f;
+constexpr int JAC_MAX_SWEEPS = 60;
+
+// ------------------------------------------------------------------ sample kernels
+
+// Initial parameters: the beta = 0 state with its zero entries perturbed (App. A):
+// entry t = noise (2u - 1), u = Philox(seed; t lo, t hi, 0, TAG_INIT); the [0,0,0,0]
+// entries of the S = 0 and S = 3 slices of every site are 1.
+__global__ void k_init_theta(long long Np, int N, const long long* __restrict__ toff,
+                             double noise, uint64_t seed, double* __restrict__ theta,
+                             float* __restrict__ theta_f) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    double u = philox_uniform(seed, (uint32_t)t, (uint32_t)(t >> 32), 0u, TAG_INIT);
+    double v = noise * (2.0 * u - 1.0);
+    int lo = 0, hi = N;   // site of t: toff[j] <= t < toff[j+1]
+    while (hi - lo > 1) {
+      int mid = (lo + hi) >> 1;
+      if (toff[mid] <= t) lo = mid; else hi = mid;
+    }
+    long long sz = (toff[lo + 1] - toff[lo]) / 4;
+    long long rel = t - toff[lo];
+    if (rel == 0 || rel == 3 * sz) v = 1.0;
+    theta[t] = v;
+    if (theta_f) theta_f[t] = (float)v;
+  }
+}
+
+// Initial chains: diagonal configurations, s_i = low bit of Philox(seed; chain, site, 0, TAG_CFG).
+__global__ void k_init_configs(int n, int N, uint64_t seed, uint8_t* __restrict__ S) {
+  long long tot = (long long)n * N;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    int ch = (int)(t / N), j = (int)(t % N);
+    uint32_t b = philox_bits(seed, (uint32_t)ch, (uint32_t)j, 0u, TAG_CFG) & 1u;
+    S[t] = (uint8_t)(3u * b);
+  }
+}
+
+template <typename T>
+__device__ void init_shared(Shared<T>& sh) {
+  if (threadIdx.x == 0) {
+    sh.flops = 0;
+    sh.jac_sweeps = 0;
+    sh.flag = 0;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void flush_counters(Shared<T>& sh, double* flops, unsigned long long* jsw) {
+  if (threadIdx.x == 0) {
+    atomicAdd(flops, sh.flops);
+    atomicAdd(jsw, (unsigned long long)sh.jac_sweeps);
+  }
+}
+
+// Persistent evaluation kernel: block b handles samples b, b + grid, ...
+template <typename T, typename OT>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_eval(Geom g, const T* __restrict__ theta, const uint8_t* __restrict__ S, int n,
+           T* scratch, int* iscratch, long long sreal, long long sint,
+           double* __restrict__ log_abs, int8_t* __restrict__ sign, double* __restrict__ es,
+           double* __restrict__ ea, OT* __restrict__ O, long long No, T jtol, int max_sweeps,
+           double* flops, unsigned long long* jsw) {
+  __shared__ Shared<T> sh;
+  Scratch<T> sc;
+  sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
+          g.L1, g.L2, g.D, g.chi);
+  init_shared(sh);
+  const int N = g.N();
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) sh.S[j] = S[(long long)s * N + j];
+    __syncthreads();
+    SampleOut r = eval_sample<T, T, OT>(g, sc, sh, theta, O ? O + (long long)s * No : nullptr,
+                                        jtol, max_sweeps);
+    if (threadIdx.x == 0) {
+      if (log_abs) log_abs[s] = r.log_abs;
+      if (sign) sign[s] = (int8_t)r.sign;
+      if (es) es[s] = r.e_sys;
+      if (ea) ea[s] = r.e_anc;
+    }
+    __syncthreads();
+  }
+  flush_counters(sh, flops, jsw);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(SAMPLE_THREADS)
+    k_mc(Geom g, const T* __restrict__ theta, uint8_t* __restrict__ S, int n, T* scratch,
+         int* iscratch, long long sreal, long long sint, int p, uint64_t seed, long long sweep0,
+         int n_sweeps, int* __restrict__ acc, int* __restrict__ prop, T jtol, int max_sweeps,
+         double* flops, unsigned long long* jsw) {
+  __shared__ Shared<T> sh;
+  Scratch<T> sc;
+  sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
+          g.L1, g.L2, g.D, g.chi);
+  init_shared(sh);
+  const int N = g.N();
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    for (int j = threadIdx.x; j < N; j += blockDim.x) sh.S[j] = S[(long long)s * N + j];
+    __syncthreads();
+    int a_tot = 0, p_tot = 0;
+    for (int k = 0; k < n_sweeps; ++k) {
+      int a = 0, pr = 0;
+      mc_sweep<T, T>(g, sc, sh, theta, p, seed, (uint32_t)s, (uint32_t)(sweep0 + k), jtol,
+                     max_sweeps, &a, &pr);
+      a_tot += a;
+      p_tot += pr;
+    }
+    for (int j = threadIdx.x; j < N; j += blockDim.x) S[(long long)s * N + j] = sh.S[j];
+    if (threadIdx.x == 0) {
+      acc[s] = a_tot;
+      prop[s] = p_tot;
+    }
+    __syncthreads();
+  }
+  flush_counters(sh, flops, jsw);
+}
+
+template <typename T>
+__global__ void k_to_real(long long n, const double* __restrict__ a, T* __restrict__ b) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    b[t] = (T)a[t];
+}
+
+int grid_for(long long n, int threads, int cap = 152 * 16) {
+  long long b = (n + threads - 1) / threads;
+  if (b < 1) b = 1;
+  return (int)std::min<long long>(b, cap);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ context
+
+struct peps_ctx {
+  peps_params P{};
+  cudaStream_t stream = nullptr;
+  int N = 0;
+  long long Np = 0, No = 0;
+  std::vector<long long> toff, ooff;
+  long long* d_toff = nullptr;
+  long long* d_ooff = nullptr;
+  int* d_o2site = nullptr;
+  double* d_theta = nullptr;
+  float* d_theta_f = nullptr;
+  uint8_t* d_S = nullptr;   // chains
+  // evaluation of the chains
+  double *d_log_abs = nullptr, *d_es = nullptr, *d_ea = nullptr;
+  int8_t* d_sign = nullptr;
+  void* d_O = nullptr;
+  bool have_eval = false;
+  // external batches
+  uint8_t* d_xS = nullptr;
+  double *d_xla = nullptr, *d_xes = nullptr, *d_xea = nullptr;
+  int8_t* d_xsg = nullptr;
+  void* d_xO = nullptr;
+  int x_cap = 0;
+  // sample scratch
+  void* d_scr = nullptr;
+  int* d_iscr = nullptr;
+  int nblk = 0;
+  long long sreal = 0, sint = 0;
+  double* d_flops = nullptr;
+  unsigned long long* d_jsw = nullptr;
+  int *d_acc = nullptr, *d_prop = nullptr;
+  // SR
+  double *d_w = nullptr, *d_E = nullptr, *d_obar = nullptr, *d_g = nullptr, *d_x = nullptr;
+  double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_y = nullptr, *d_part = nullptr;
+  double *d_part2 = nullptr, *d_bp1 = nullptr, *d_bp2 = nullptr, *d_ypart = nullptr;
+  float* d_pf = nullptr;
+  SRScalars* d_sc = nullptr;
+  int nch = 0, nvb = 0, nyb = 0;
+  double t = 0;
+  int64_t sweeps = 0;
+  double last_accept = 0;
+  std::string err;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+int fail(peps_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+#define PV_CUDA(ctx, call)                                                               \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, PEPS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename P>
+int dalloc(peps_ctx* c, P** ptr, size_t bytes) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, PEPS_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+  }
+  c->allocs.push_back(p);
+  *ptr = (P*)p;
+  return PEPS_OK;
+}
+
+#define PV_TRY(x)                \
+  do {                           \
+    int rc_ = (x);               \
+    if (rc_ != PEPS_OK) return rc_; \
+  } while (0)
+
+Geom make_geom(const peps_ctx* c) {
+  Geom g;
+  g.L1 = c->P.L1;
+  g.L2 = c->P.L2;
+  g.D = c->P.D;
+  g.chi = c->P.chi;
+  g.J1 = c->P.J1;
+  g.J2 = c->P.J2;
+  g.theta_off = c->d_toff;
+  g.o_off = c->d_ooff;
+  return g;
+}
+
+bool fp64(const peps_ctx* c) { return c->P.precision == PEPS_FP64; }
+
+int ensure_batch(peps_ctx* c, int nb) {
+  if (nb <= c->x_cap) return PEPS_OK;
+  size_t osz = fp64(c) ? sizeof(double) : sizeof(float);
+  PV_TRY(dalloc(c, &c->d_xS, (size_t)nb * c->N));
+  PV_TRY(dalloc(c, &c->d_xla, (size_t)nb * sizeof(double)));
+  PV_TRY(dalloc(c, &c->d_xes, (size_t)nb * sizeof(double)));
+  PV_TRY(dalloc(c, &c->d_xea, (size_t)nb * sizeof(double)));
+  PV_TRY(dalloc(c, &c->d_xsg, (size_t)nb));
+  PV_TRY(dalloc(c, &c->d_xO, (size_t)nb * c->No * osz));
+  c->x_cap = nb;
+  return PEPS_OK;
+}
+
+// Launches the evaluation kernel on device buffers.
+int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, double* es,
+                double* ea, void* O) {
+  Geom g = make_geom(c);
+  PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
+  PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
+  int grid = std::min(c->nblk, nb);
+  if (fp64(c)) {
+    k_eval<double, double><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+        g, c->d_theta, dS, nb, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
+        (double*)O, c->No, JTOL_F64, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw);
+  } else {
+    k_eval<float, float><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+        g, c->d_theta_f, dS, nb, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
+        (float*)O, c->No, JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw);
+  }
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* peps_version(void) { return "peps_vmc 0.1 (sm_103a)"; }
+
+const char* peps_last_error(const peps_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+void peps_free(peps_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  delete ctx;
+}
+
+int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
+  if (!P || !out) return PEPS_EINVAL;
+  *out = nullptr;
+  if (P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
+      P->chi < 1 || P->chi > 64 || P->n_chains < 1 || P->model != PEPS_MODEL_J1J2 ||
+      (P->precision != PEPS_FP64 && P->precision != PEPS_FP32) || P->n_blocks < 0 ||
+      !(P->init_noise >= 0))
+    return PEPS_EINVAL;
+  peps_ctx* c = new peps_ctx();
+  c->P = *P;
+  c->stream = (cudaStream_t)stream;
+  c->N = P->L1 * P->L2;
+  const int L2 = P->L2;
+  c->toff.assign(c->N + 1, 0);
+  c->ooff.assign(c->N + 1, 0);
+  for (int i = 0; i < c->N; ++i) {
+    int r = i / L2, cc = i % L2;
+    long long sz = (long long)(cc == 0 ? 1 : P->D) * (cc == L2 - 1 ? 1 : P->D) *
+                   (r == 0 ? 1 : P->D) * (r == P->L1 - 1 ? 1 : P->D);
+    c->toff[i + 1] = c->toff[i] + 4 * sz;
+    c->ooff[i + 1] = c->ooff[i] + sz;
+  }
+  c->Np = c->toff[c->N];
+  c->No = c->ooff[c->N];
+  std::vector<int> o2site(c->No);
+  for (int i = 0; i < c->N; ++i)
+    for (long long o = c->ooff[i]; o < c->ooff[i + 1]; ++o) o2site[o] = i;
+  int rc = PEPS_OK;
+  auto bail = [&](int code) {
+    std::string m = c->err;
+    peps_free(c);
+    (void)m;
+    return code;
+  };
+  const int n = P->n_chains;
+  size_t real = fp64(c) ? sizeof(double) : sizeof(float);
+  if ((rc = dalloc(c, &c->d_toff, (c->N + 1) * sizeof(long long)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_ooff, (c->N + 1) * sizeof(long long)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_o2site, c->No * sizeof(int)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_theta, c->Np * sizeof(double)))) return bail(rc);
+  if (!fp64(c) && (rc = dalloc(c, &c->d_theta_f, c->Np * sizeof(float)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_S, (size_t)n * c->N))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_log_abs, n * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_es, n * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_ea, n * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_sign, n))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_O, (size_t)n * c->No * real))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_acc, n * sizeof(int)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_prop, n * sizeof(int)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_flops, sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_jsw, sizeof(unsigned long long)))) return bail(rc);
+  // persistent sample blocks and their scratch
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ScratchDims sd = scratch_dims(P->L1, P->L2, P->D, P->chi);
+  c->sreal = (sd.n_real + 31) & ~31LL;
+  c->sint = (sd.n_int + 31) & ~31LL;
+  int want = P->n_blocks > 0 ? P->n_blocks : sms * 4;
+  c->nblk = std::max(1, std::min(want, n));
+  if ((rc = dalloc(c, &c->d_scr, (size_t)c->nblk * c->sreal * real))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_iscr, (size_t)c->nblk * c->sint * sizeof(int)))) return bail(rc);
+  // SR buffers
+  c->nch = (n + OTV_CHUNK - 1) / OTV_CHUNK;
+  c->nvb = grid_for(c->Np, SR_THREADS, 1024);
+  c->nyb = (n + (SR_THREADS / 32) - 1) / (SR_THREADS / 32);
+  if ((rc = dalloc(c, &c->d_w, n * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_E, n * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_y, n * sizeof(double)))) return bail(rc);
+  for (double** v : {&c->d_obar, &c->d_g, &c->d_x, &c->d_r, &c->d_p, &c->d_q})
+    if ((rc = dalloc(c, v, c->Np * sizeof(double)))) return bail(rc);
+  if (!fp64(c) && (rc = dalloc(c, &c->d_pf, c->Np * sizeof(float)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_part, (size_t)c->nch * c->Np * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_part2, (size_t)c->nch * c->Np * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_bp1, c->nvb * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_bp2, c->nvb * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_ypart, c->nyb * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_sc, sizeof(SRScalars)))) return bail(rc);
+  cudaError_t e;
+  e = cudaMemcpyAsync(c->d_toff, c->toff.data(), (c->N + 1) * sizeof(long long),
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_ooff, c->ooff.data(), (c->N + 1) * sizeof(long long),
+                        cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_o2site, o2site.data(), c->No * sizeof(int), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e != cudaSuccess) return bail(fail(c, PEPS_ECUDA, cudaGetErrorString(e)));
+  k_init_theta<<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->N, c->d_toff,
+                                                             P->init_noise, P->seed, c->d_theta,
+                                                             c->d_theta_f);
+  k_init_configs<<<grid_for((long long)n * c->N, 256), 256, 0, c->stream>>>(n, c->N, P->seed,
+                                                                            c->d_S);
+  e = cudaStreamSynchronize(c->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return bail(fail(c, PEPS_ECUDA, cudaGetErrorString(e)));
+  *out = c;
+  return PEPS_OK;
+}
+
+size_t peps_num_params(const peps_ctx* c) { return c ? (size_t)c->Np : 0; }
+size_t peps_o_row_len(const peps_ctx* c) { return c ? (size_t)c->No : 0; }
+int64_t peps_sweeps_done(const peps_ctx* c) { return c ? c->sweeps : 0; }
+int peps_set_sweeps_done(peps_ctx* c, int64_t s) {
+  if (!c || s < 0) return PEPS_EINVAL;
+  c->sweeps = s;
+  return PEPS_OK;
+}
+
+int peps_get_theta(peps_ctx* c, double* host, size_t n) {
+  if (!c || !host || n != (size_t)c->Np) return fail(c, PEPS_EINVAL, "get_theta: size");
+  PV_CUDA(c, cudaMemcpyAsync(host, c->d_theta, n * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PEPS_OK;
+}
+
+int peps_set_theta(peps_ctx* c, const double* host, size_t n) {
+  if (!c || !host || n != (size_t)c->Np) return fail(c, PEPS_EINVAL, "set_theta: size");
+  PV_CUDA(c, cudaMemcpyAsync(c->d_theta, host, n * sizeof(double), cudaMemcpyHostToDevice,
+                             c->stream));
+  if (c->d_theta_f)
+    k_to_real<float><<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->d_theta,
+                                                                   c->d_theta_f);
+  PV_CUDA(c, cudaGetLastError());
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_eval = false;
+  return PEPS_OK;
+}
+
+int peps_get_configs(peps_ctx* c, uint8_t* host, size_t n) {
+  if (!c || !host || n != (size_t)c->P.n_chains * c->N) return fail(c, PEPS_EINVAL, "get_configs: size");
+  PV_CUDA(c, cudaMemcpyAsync(host, c->d_S, n, cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PEPS_OK;
+}
+
+int peps_set_configs(peps_ctx* c, const uint8_t* host, size_t n) {
+  if (!c || !host || n != (size_t)c->P.n_chains * c->N) return fail(c, PEPS_EINVAL, "set_configs: size");
+  for (size_t i = 0; i < n; ++i)
+    if (host[i] > 3) return fail(c, PEPS_EINVAL, "set_configs: entry > 3");
+  PV_CUDA(c, cudaMemcpyAsync(c->d_S, host, n, cudaMemcpyHostToDevice, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->have_eval = false;
+  return PEPS_OK;
+}
+
+int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
+  if (!c || n_sweeps < 0 || (p != 1 && p != 2)) return fail(c, PEPS_EINVAL, "mc_sweep: args");
+  if (n_sweeps == 0) return PEPS_OK;
+  Geom g = make_geom(c);
+  const int n = c->P.n_chains;
+  PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
+  PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
+  int grid = std::min(c->nblk, n);
+  if (fp64(c)) {
+    k_mc<double><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+        g, c->d_theta, c->d_S, n, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
+        c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F64, JAC_MAX_SWEEPS,
+        c->d_flops, c->d_jsw);
+  } else {
+    k_mc<float><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+        g, c->d_theta_f, c->d_S, n, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
+        c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F32, JAC_MAX_SWEEPS,
+        c->d_flops, c->d_jsw);
+  }
+  PV_CUDA(c, cudaGetLastError());
+  c->sweeps += n_sweeps;
+  c->have_eval = false;
+  std::vector<int> a(n), b(n);
+  PV_CUDA(c, cudaMemcpyAsync(a.data(), c->d_acc, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaMemcpyAsync(b.data(), c->d_prop, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  long long sa = 0, sb = 0;
+  for (int i = 0; i < n; ++i) {
+    sa += a[i];
+    sb += b[i];
+  }
+  c->last_accept = sb > 0 ? (double)sa / (double)sb : 0.0;
+  return PEPS_OK;
+}
+
+int peps_eval_batch(peps_ctx* c, const uint8_t* S, int nb, int on_device, double* log_abs,
+                    int8_t* sign, double* e_sys, double* e_anc, void* O) {
+  if (!c || nb < 0) return fail(c, PEPS_EINVAL, "eval_batch: args");
+  size_t osz = fp64(c) ? sizeof(double) : sizeof(float);
+  if (S == nullptr) {
+    if (nb != c->P.n_chains) return fail(c, PEPS_EINVAL, "eval_batch: nb != n_chains");
+    PV_TRY(launch_eval(c, c->d_S, nb, c->d_log_abs, c->d_sign, c->d_es, c->d_ea, c->d_O));
+    c->have_eval = true;
+    if (on_device) {
+      if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, c->d_log_abs, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, c->d_sign, nb, cudaMemcpyDeviceToDevice, c->stream));
+      if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, c->d_es, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, c->d_ea, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (O) PV_CUDA(c, cudaMemcpyAsync(O, c->d_O, (size_t)nb * c->No * osz, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, c->d_log_abs, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, c->d_sign, nb, cudaMemcpyDeviceToHost, c->stream));
+      if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, c->d_es, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, c->d_ea, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      if (O) PV_CUDA(c, cudaMemcpyAsync(O, c->d_O, (size_t)nb * c->No * osz, cudaMemcpyDeviceToHost, c->stream));
+    }
+    PV_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PEPS_OK;
+  }
+  if (nb == 0) return PEPS_OK;
+  if (on_device) {
+    PV_TRY(launch_eval(c, S, nb, log_abs, sign, e_sys, e_anc, O));
+    PV_CUDA(c, cudaStreamSynchronize(c->stream));
+    return PEPS_OK;
+  }
+  PV_TRY(ensure_batch(c, nb));
+  PV_CUDA(c, cudaMemcpyAsync(c->d_xS, S, (size_t)nb * c->N, cudaMemcpyHostToDevice, c->stream));
+  PV_TRY(launch_eval(c, c->d_xS, nb, c->d_xla, c->d_xsg, c->d_xes, c->d_xea, O ? c->d_xO : nullptr));
+  if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, c->d_xla, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, c->d_xsg, nb, cudaMemcpyDeviceToHost, c->stream));
+  if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, c->d_xes, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, c->d_xea, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (O) PV_CUDA(c, cudaMemcpyAsync(O, c->d_xO, (size_t)nb * c->No * osz, cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  return PEPS_OK;
+}
+
+int peps_last_counters(peps_ctx* c, double* flops, int64_t* jsw) {
+  if (!c) return PEPS_EINVAL;
+  double f = 0;
+  unsigned long long j = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&f, c->d_flops, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaMemcpyAsync(&j, c->d_jsw, sizeof(j), cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (flops) *flops = f;
+  if (jsw) *jsw = (int64_t)j;
+  return PEPS_OK;
+}
+
+static int fill_stats(peps_ctx* c, int p, peps_stats* st, bool with_cg) {
+  SRScalars h;
+  PV_CUDA(c, cudaMemcpyAsync(&h, c->d_sc, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (!st) return PEPS_OK;
+  const double N = (double)c->N;
+  st->t = c->t;
+  st->beta_obs = 4.0 * c->t;
+  st->E_site = h.H1 / N;
+  st->E_err = h.Eerr / N;
+  st->C_site = st->beta_obs * st->beta_obs * (h.H2 - h.H1 * h.H1) / N;
+  st->chi_sus = st->beta_obs * h.M2 / N;
+  st->accept = c->last_accept;
+  st->diag_frac = h.diag;
+  st->p = p;
+  if (with_cg) {
+    st->cg_iters = h.iters;
+    st->cg_resid = h.gnorm > 0 ? std::sqrt(h.rr) / h.gnorm : 0.0;
+  } else {
+    st->cg_iters = 0;
+    st->cg_resid = 0;
+  }
+  return PEPS_OK;
+}
+
+static int launch_weights(peps_ctx* c, int p) {
+  k_sr_weights<<<1, SR_WEIGHT_THREADS, 0, c->stream>>>(c->P.n_chains, c->N, p, c->d_log_abs,
+                                                       c->d_es, c->d_ea, c->d_S, c->d_w, c->d_E,
+                                                       c->d_sc);
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+int peps_observables(peps_ctx* c, int p, peps_stats* st) {
+  if (!c || (p != 1 && p != 2)) return fail(c, PEPS_EINVAL, "observables: args");
+  if (!c->have_eval) return fail(c, PEPS_ESTATE, "observables: no evaluation of the chains");
+  PV_TRY(launch_weights(c, p));
+  return fill_stats(c, p, st, false);
+}
+
+int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol, int p,
+                 peps_stats* st) {
+  if (!c || (p != 1 && p != 2) || max_cg < 0 || !(eps >= 0) || !(cg_tol >= 0) ||
+      !std::isfinite(tau))
+    return fail(c, PEPS_EINVAL, "sr_step: args");
+  if (!c->have_eval) return fail(c, PEPS_ESTATE, "sr_step: no evaluation of the chains");
+  const int n = c->P.n_chains;
+  const long long Np = c->Np, No = c->No;
+  cudaStream_t s = c->stream;
+  PV_TRY(launch_weights(c, p));
+  // mean and gradient (one pass over O)
+  dim3 cgrid((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
+  if (fp64(c))
+    k_colsum1<double, true><<<cgrid, SR_THREADS, 0, s>>>(
+        n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr);
+  else
+    k_colsum1_f32<true><<<cgrid, SR_THREADS, 0, s>>>(
+        n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr);
+  k_colsum2_grad<<<grid_for(Np, SR_THREADS, 1 << 20), SR_THREADS, 0, s>>>(
+      Np, c->nch, c->d_part, c->d_part2, c->d_obar, c->d_g);
+  PV_CUDA(c, cudaGetLastError());
+  // CG
+  const int nvb = c->nvb;
+  k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_g, c->d_bp1, nullptr);
+  k_cg_init<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_x, c->d_r, c->d_p, c->d_pf, nvb,
+                                       c->d_bp1, c->d_sc, max_cg, cg_tol, eps);
+  k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_obar, c->d_p, c->d_bp2, nullptr);   // obar.p
+  PV_CUDA(c, cudaGetLastError());
+  const int ov_blocks = c->nyb;
+  for (int it = 0; it < max_cg; ++it) {
+    if (fp64(c))
+      k_ov<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const double*)c->d_O, c->d_S,
+                                                    c->d_toff, c->d_ooff, c->d_p, c->d_pf,
+                                                    c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2,
+                                                    c->d_sc);
+    else
+      k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
+                                                   c->d_toff, c->d_ooff, c->d_p, c->d_pf, c->d_w,
+                                                   c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc);
+    if (fp64(c))
+      k_colsum1<double, false><<<cgrid, SR_THREADS, 0, s>>>(
+          n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done);
+    else
+      k_colsum1_f32<false><<<cgrid, SR_THREADS, 0, s>>>(
+          n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done);
+    k_otv2<<<nvb, SR_THREADS, 0, s>>>(Np, c->nch, c->d_part, c->d_obar, c->d_p, c->d_q,
+                                      ov_blocks, c->d_ypart, c->d_bp1, c->d_sc);
+    k_cg_a<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_x, c->d_r, c->d_p, c->d_q, nvb, c->d_bp1,
+                                      c->d_bp2, c->d_sc);
+    k_cg_b<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_r, c->d_p, c->d_pf, c->d_obar, nvb, c->d_bp2,
+                                      c->d_bp1, c->d_sc);
+    k_cg_scalars<<<1, 1, 0, s>>>(nvb, c->d_bp2, c->d_sc);
+    // obar.p partials for the next k_ov are in d_bp1; swap roles
+    std::swap(c->d_bp1, c->d_bp2);
+    PV_CUDA(c, cudaGetLastError());
+    if ((it & 7) == 7) {
+      int done = 0;
+      PV_CUDA(c, cudaMemcpyAsync(&done, &c->d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PV_CUDA(c, cudaStreamSynchronize(s));
+      if (done) break;
+    }
+  }
+  k_update<<<grid_for(Np, 256), 256, 0, s>>>(Np, tau, c->d_x, c->d_theta, c->d_theta_f);
+  PV_CUDA(c, cudaGetLastError());
+  int rc = fill_stats(c, p, st, true);
+  if (rc != PEPS_OK) return rc;
+  SRScalars h;
+  PV_CUDA(c, cudaMemcpy(&h, c->d_sc, sizeof(h), cudaMemcpyDeviceToHost));
+  c->t += tau;
+  c->have_eval = false;
+  if (!std::isfinite(h.rr) || !std::isfinite(h.H1))
+    return fail(c, PEPS_ENOTFINITE, "sr_step: non-finite energy or residual");
+  return (h.iters >= max_cg && max_cg > 0 && h.gnorm > 0 &&
+          std::sqrt(h.rr) > cg_tol * h.gnorm)
+             ? PEPS_WARN_CG_MAXIT
+             : PEPS_OK;
+}
+
+int peps_step(peps_ctx* c, int n_sweeps, int p, double tau, double eps, int max_cg,
+              double cg_tol, peps_stats* st) {
+  PV_TRY(peps_mc_sweep(c, n_sweeps, p));
+  if (!c) return PEPS_EINVAL;
+  PV_TRY(peps_eval_batch(c, nullptr, c->P.n_chains, 1, nullptr, nullptr, nullptr, nullptr,
+                         nullptr));
+  return peps_sr_step(c, tau, eps, max_cg, cg_tol, p, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,374 @@
+// Stochastic-reconfiguration kernels (Sec. II, Eqs. 5-7 and 10): sample weights and
+// observables, the log-derivative mean and gradient, and the CG solve of
+// (G + eps I) x = g with G applied as two passes over the O rows.
+//
+// O rows are compressed: row i holds, per site j, the slice S_ij of the derivative, so
+// the full-space index of column o (site j, offset k) is theta_off[j] + S_ij sz_j + k.
+// Every reduction has a fixed order (deterministic results for a fixed launch shape).
+#pragma once
+
+#include <cstdint>
+
+namespace pv {
+
+struct SRScalars {
+  // sample statistics
+  double Ebar;       // sum_i w_i E_i (E = E_sys + E_anc)
+  double H1, H2;     // <H>, <H^2> of Eq. 11 (symmetrised over the two layers)
+  double M2;         // <Mz^2>
+  double diag;       // fraction of diagonal samples
+  double Eerr;       // standard error of <H>
+  // CG state
+  double rr, gnorm, pq, obp, sumy;
+  int iters, done, maxit, pad;
+  double tol, eps;
+};
+
+constexpr int SR_THREADS = 256;
+constexpr int SR_WEIGHT_THREADS = 1024;
+constexpr int OTV_CHUNK = 128;   // samples per partial sum of the O^T y pass
+
+template <typename T>
+__device__ __forceinline__ T blk_sum(T v, T* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = 0;
+  int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// Weights and sample statistics (one block).  p = 2: w = 1/n; p = 1: w = |rho|/sum|rho|
+// (Eq. A1).  Observables: <H> = 1/2 sum w (Es + Ea), <H^2> = 1/2 sum w (Es^2 + Ea^2),
+// <Mz^2> = 1/2 sum w (M(s)^2 + M(s')^2).
+__global__ void k_sr_weights(int n, int N, int p, const double* __restrict__ log_abs,
+                             const double* __restrict__ es, const double* __restrict__ ea,
+                             const uint8_t* __restrict__ S, double* __restrict__ w,
+                             double* __restrict__ E, SRScalars* sc) {
+  __shared__ double red[32];
+  double mx = -INFINITY;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, log_abs[i]);
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ double redm[32];
+  if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = redm[0];
+  for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmax(mx, redm[i]);
+  double zs = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    zs += (p == 2) ? 1.0 : exp(log_abs[i] - mx);
+  double Z = blk_sum(zs, red);
+  double e1 = 0, h1 = 0, h2 = 0, m2 = 0, dg = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double wi = ((p == 2) ? 1.0 : exp(log_abs[i] - mx)) / Z;
+    w[i] = wi;
+    double a = es[i], b = ea[i];
+    E[i] = a + b;
+    e1 += wi * (a + b);
+    h1 += wi * 0.5 * (a + b);
+    h2 += wi * 0.5 * (a * a + b * b);
+    int ms = 0, ma = 0, dd = 1;
+    for (int j = 0; j < N; ++j) {
+      int s = S[(long long)i * N + j];
+      ms += (s >> 1) ? -1 : 1;
+      ma += (s & 1) ? -1 : 1;
+      dd &= ((s >> 1) == (s & 1));
+    }
+    m2 += wi * 0.5 * (0.25 * ms * ms + 0.25 * ma * ma);
+    dg += dd;
+  }
+  e1 = blk_sum(e1, red);
+  h1 = blk_sum(h1, red);
+  h2 = blk_sum(h2, red);
+  m2 = blk_sum(m2, red);
+  dg = blk_sum(dg, red);
+  double ve = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double d = 0.5 * (es[i] + ea[i]) - h1;
+    ve += w[i] * w[i] * d * d;
+  }
+  ve = blk_sum(ve, red);
+  if (threadIdx.x == 0) {
+    sc->Ebar = e1;
+    sc->H1 = h1;
+    sc->H2 = h2;
+    sc->M2 = m2;
+    sc->diag = dg / n;
+    sc->Eerr = sqrt(ve);
+  }
+}
+
+// Stage 1 of a segmented column sum over samples: for each column o of the O rows and
+// each chunk of OTV_CHUNK samples, acc[S_ij] += c_i O[i][o] for the four values of S_ij,
+// written to part[chunk][theta index].  Two coefficient vectors at once (c1 = y or w,
+// c2 = w (E - Ebar) or unused).
+template <typename OT, bool TWO>
+__global__ void k_colsum1(int n, int N, long long No, const OT* __restrict__ O,
+                          const uint8_t* __restrict__ S, const int* __restrict__ o2site,
+                          const long long* __restrict__ toff, const long long* __restrict__ ooff,
+                          const double* __restrict__ c1, const double* __restrict__ c2,
+                          const double* __restrict__ shift, double* __restrict__ part1,
+                          double* __restrict__ part2, long long Np, const int* done) {
+  if (done && *done) return;
+  const double Ebar_shift = TWO ? *shift : 0.0;
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= No) return;
+  int ch = blockIdx.y;
+  int i0 = ch * OTV_CHUNK, i1 = min(n, i0 + OTV_CHUNK);
+  int j = o2site[o];
+  long long k = o - ooff[j];
+  long long sz = (ooff[j + 1] - ooff[j]);
+  double a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+  for (int i = i0; i < i1; ++i) {
+    double v = (double)O[(long long)i * No + o];
+    int s = S[(long long)i * N + j];
+    double x = c1[i] * v;
+    double y = TWO ? c1[i] * (c2[i] - Ebar_shift) * v : 0.0;
+    if (s == 0) { a0 += x; if (TWO) b0 += y; }
+    else if (s == 1) { a1 += x; if (TWO) b1 += y; }
+    else if (s == 2) { a2 += x; if (TWO) b2 += y; }
+    else { a3 += x; if (TWO) b3 += y; }
+  }
+  long long t = toff[j] + k;
+  double* p1 = part1 + (long long)ch * Np;
+  p1[t] = a0;
+  p1[t + sz] = a1;
+  p1[t + 2 * sz] = a2;
+  p1[t + 3 * sz] = a3;
+  if (TWO) {
+    double* p2 = part2 + (long long)ch * Np;
+    p2[t] = b0;
+    p2[t + sz] = b1;
+    p2[t + 2 * sz] = b2;
+    p2[t + 3 * sz] = b3;
+  }
+}
+
+// Float rows: products and the per-chunk sums in float32, chunk totals in float64.
+template <bool TWO>
+__global__ void k_colsum1_f32(int n, int N, long long No, const float* __restrict__ O,
+                              const uint8_t* __restrict__ S, const int* __restrict__ o2site,
+                              const long long* __restrict__ toff,
+                              const long long* __restrict__ ooff, const double* __restrict__ c1,
+                              const double* __restrict__ c2, const double* __restrict__ shift,
+                              double* __restrict__ part1, double* __restrict__ part2,
+                              long long Np, const int* done) {
+  if (done && *done) return;
+  const double Ebar_shift = TWO ? *shift : 0.0;
+  long long o = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (o >= No) return;
+  int ch = blockIdx.y;
+  int i0 = ch * OTV_CHUNK, i1 = min(n, i0 + OTV_CHUNK);
+  int j = o2site[o];
+  long long k = o - ooff[j];
+  long long sz = (ooff[j + 1] - ooff[j]);
+  float a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+  for (int i = i0; i < i1; ++i) {
+    float v = O[(long long)i * No + o];
+    int s = S[(long long)i * N + j];
+    float x = (float)c1[i] * v;
+    float y = TWO ? (float)(c1[i] * (c2[i] - Ebar_shift)) * v : 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (s == q) {
+        a[q] += x;
+        if (TWO) b[q] += y;
+      }
+    }
+  }
+  long long t = toff[j] + k;
+  double* p1 = part1 + (long long)ch * Np;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) p1[t + q * sz] = (double)a[q];
+  if (TWO) {
+    double* p2 = part2 + (long long)ch * Np;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) p2[t + q * sz] = (double)b[q];
+  }
+}
+
+// Stage 2 for the mean and gradient: obar = sum_ch part1, g = sum_ch part2.
+__global__ void k_colsum2_grad(long long Np, int nch, const double* __restrict__ part1,
+                               const double* __restrict__ part2, double* __restrict__ obar,
+                               double* __restrict__ g) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= Np) return;
+  double a = 0, b = 0;
+  for (int c = 0; c < nch; ++c) {
+    a += part1[(long long)c * Np + t];
+    b += part2[(long long)c * Np + t];
+  }
+  obar[t] = a;
+  g[t] = b;
+}
+
+// Block-partial dot products of length-Np vectors: part[block] = sum over the block.
+__global__ void k_dot_part(long long Np, const double* __restrict__ a,
+                           const double* __restrict__ b, double* __restrict__ part,
+                           const SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc && sc->done) return;
+  double s = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x)
+    s += a[t] * b[t];
+  s = blk_sum(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__device__ __forceinline__ double sum_parts(const double* part, int n) {
+  double s = 0;
+  for (int i = 0; i < n; ++i) s += part[i];
+  return s;
+}
+
+// CG set-up: x = 0, r = p = g, rr = g.g, gnorm, done flag.
+__global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __restrict__ x,
+                          double* __restrict__ r, double* __restrict__ p, float* __restrict__ pf,
+                          int ndp, const double* __restrict__ dpart, SRScalars* sc, int maxit,
+                          double tol, double eps) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] = 0;
+    r[t] = g[t];
+    p[t] = g[t];
+    if (pf) pf[t] = (float)g[t];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double rr = sum_parts(dpart, ndp);
+    sc->rr = rr;
+    sc->gnorm = sqrt(rr);
+    sc->iters = 0;
+    sc->maxit = maxit;
+    sc->tol = tol;
+    sc->eps = eps;
+    sc->done = (maxit <= 0 || !(sqrt(rr) > tol * sqrt(rr))) ? 1 : 0;
+  }
+}
+
+// y_i = w_i [ (O_i . p) - obar . p ], one warp per sample; per-block partials of sum y.
+template <typename OT>
+__global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
+                     const uint8_t* __restrict__ S, const long long* __restrict__ toff,
+                     const long long* __restrict__ ooff, const double* __restrict__ p,
+                     const float* __restrict__ pf, const double* __restrict__ w,
+                     double* __restrict__ y, double* __restrict__ ypart, int ndp,
+                     const double* __restrict__ dpart, const SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double obp = sum_parts(dpart, ndp);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  double yi = 0;
+  if (i < n) {
+    const OT* row = O + (long long)i * No;
+    double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      int s = S[(long long)i * N + j];
+      long long o0 = ooff[j], sz = ooff[j + 1] - o0;
+      long long t0 = toff[j] + (long long)s * sz;
+      if (sizeof(OT) == 4) {
+        float a = 0;
+        for (long long k = lane; k < sz; k += 32) a += (float)row[o0 + k] * pf[t0 + k];
+        acc += (double)a;
+      } else {
+        for (long long k = lane; k < sz; k += 32) acc += (double)row[o0 + k] * p[t0 + k];
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    yi = w[i] * (acc - obp);
+    if (lane == 0) y[i] = yi;
+  }
+  double contrib = (lane == 0) ? yi : 0.0;
+  double s = blk_sum(contrib, red);
+  if (threadIdx.x == 0) ypart[blockIdx.x] = s;
+}
+
+// q = sum_ch part - (sum y) obar + eps p ; block partials of p.q.
+__global__ void k_otv2(long long Np, int nch, const double* __restrict__ part,
+                       const double* __restrict__ obar, const double* __restrict__ p,
+                       double* __restrict__ q, int nyp, const double* __restrict__ ypart,
+                       double* __restrict__ pqpart, SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double sumy = sum_parts(ypart, nyp);
+  double eps = sc->eps;
+  double s = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    double a = 0;
+    for (int c = 0; c < nch; ++c) a += part[(long long)c * Np + t];
+    double qt = a - sumy * obar[t] + eps * p[t];
+    q[t] = qt;
+    s += p[t] * qt;
+  }
+  s = blk_sum(s, red);
+  if (threadIdx.x == 0) pqpart[blockIdx.x] = s;
+}
+
+// alpha = rr / p.q ; x += alpha p ; r -= alpha q ; block partials of r.r
+__global__ void k_cg_a(long long Np, double* __restrict__ x, double* __restrict__ r,
+                       const double* __restrict__ p, const double* __restrict__ q, int npq,
+                       const double* __restrict__ pqpart, double* __restrict__ rrpart,
+                       SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double alpha = sc->rr / sum_parts(pqpart, npq);
+  double s = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    x[t] += alpha * p[t];
+    double rt = r[t] - alpha * q[t];
+    r[t] = rt;
+    s += rt * rt;
+  }
+  s = blk_sum(s, red);
+  if (threadIdx.x == 0) rrpart[blockIdx.x] = s;
+}
+
+// beta = rr_new / rr ; p = r + beta p ; block partials of obar.p for the next pass.
+// The last block to finish updates the scalars (iteration count, convergence flag).
+__global__ void k_cg_b(long long Np, const double* __restrict__ r, double* __restrict__ p,
+                       float* __restrict__ pf, const double* __restrict__ obar, int nrr,
+                       const double* __restrict__ rrpart, double* __restrict__ obpart,
+                       SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double rr_new = sum_parts(rrpart, nrr);
+  double beta = rr_new / sc->rr;
+  double s = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    double pt = r[t] + beta * p[t];
+    p[t] = pt;
+    if (pf) pf[t] = (float)pt;
+    s += obar[t] * pt;
+  }
+  s = blk_sum(s, red);
+  if (threadIdx.x == 0) obpart[blockIdx.x] = s;
+}
+
+// Scalars after an iteration (one thread): rr <- rr_new, iteration count, stop test.
+__global__ void k_cg_scalars(int nrr, const double* __restrict__ rrpart, SRScalars* sc) {
+  if (sc->done) return;
+  double rr_new = sum_parts(rrpart, nrr);
+  sc->rr = rr_new;
+  sc->iters += 1;
+  if (sc->iters >= sc->maxit || !(sqrt(rr_new) > sc->tol * sc->gnorm)) sc->done = 1;
+}
+
+// theta -= tau x (and the float32 copy).
+__global__ void k_update(long long Np, double tau, const double* __restrict__ x,
+                         double* __restrict__ theta, float* __restrict__ theta_f) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    double v = theta[t] - tau * x[t];
+    theta[t] = v;
+    if (theta_f) theta_f[t] = (float)v;
+  }
+}
+
+}  // namespace pv

@@ -1,0 +1,50 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU, and exports every function
+that include/peps_vmc.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+from paper_2409_05285_gb300 import binding
+from paper_2409_05285_gb300.build import LIB, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names += re.findall(r"\b(peps_[a-z0-9_]+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol():
+    build()
+    assert os.path.exists(LIB)
+    lib = ctypes.CDLL(LIB)
+    names = declared_functions()
+    assert "peps_init" in names and "peps_sr_step" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(binding.EXPORTS) <= set(names)
+
+
+def test_binding_loads_and_reports_version():
+    lib = binding.load()
+    assert lib.peps_version().startswith(b"peps_vmc")
+    assert lib.peps_last_error(None) == b""
+
+
+def test_invalid_params_rejected_without_gpu_work():
+    lib = binding.load()
+    p = binding.Params(L1=1, L2=4, model=0, J1=1.0, J2=0.0, D=2, chi=4, n_chains=4,
+                       precision=0, init_noise=1e-3, seed=0, n_blocks=0)
+    ctx = ctypes.c_void_p()
+    assert lib.peps_init(ctypes.byref(p), None, ctypes.byref(ctx)) == binding.PEPS_EINVAL
+    p.L1, p.chi = 4, 65
+    assert lib.peps_init(ctypes.byref(p), None, ctypes.byref(ctx)) == binding.PEPS_EINVAL
+    p.chi, p.precision = 4, 7
+    assert lib.peps_init(ctypes.byref(p), None, ctypes.byref(ctx)) == binding.PEPS_EINVAL
+    assert not ctx.value

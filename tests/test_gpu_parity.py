@@ -1,0 +1,196 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on the same seeded
+inputs.  Tolerances: FP64 path, amplitudes 1e-10 relative (|d log rho| <= 1e-10), local
+energies and O entries 1e-9 relative to their scale; FP32 path, 2e-4 relative."""
+import numpy as np
+import pytest
+
+from oracle import peps, sampler, sr, observables as obs_mod
+from oracle.lattice import Lattice
+from paper_2409_05285_gb300 import binding
+from paper_2409_05285_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2409_05285_gb300.build import build
+    build()
+
+
+def _ctx(L1, L2, D, chi, n, J2=0.0, prec=binding.PEPS_FP64, seed=0, noise=1e-3, n_blocks=0):
+    return binding.Context(L1, L2, D, chi, n, J1=1.0, J2=J2, precision=prec, init_noise=noise,
+                           seed=seed, n_blocks=n_blocks)
+
+
+def _compare_eval(lat, th, S, chi, got, tol_la, tol_e, tol_o):
+    la, sg, es, ea, O = got
+    for k in range(S.shape[0]):
+        r = peps.eval_sample(lat, th, S[k], chi)
+        assert sg[k] == r['sign'], k
+        assert abs(la[k] - r['log_abs']) <= tol_la, (k, la[k], r['log_abs'])
+        scale = max(1.0, abs(r['e_sys']), abs(r['e_anc']))
+        assert abs(es[k] - r['e_sys']) <= tol_e * scale, (k, es[k], r['e_sys'])
+        assert abs(ea[k] - r['e_anc']) <= tol_e * scale, (k, ea[k], r['e_anc'])
+        oscale = max(1.0, np.max(np.abs(r['O'])))
+        assert np.max(np.abs(O[k].astype(np.float64) - r['O'])) <= tol_o * oscale, k
+
+
+CASES = [  # (L1, L2, D, chi, J2, n): exact chi, truncated chi, ragged tails, NNN bonds
+    (2, 2, 2, 4, 0.0, 6),
+    (4, 4, 2, 4, 0.0, 12),
+    (3, 5, 2, 3, 0.5, 7),
+    (4, 4, 3, 4, 0.5, 5),
+    (5, 3, 3, 5, 0.2, 5),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_eval_fp64_matches_oracle(case):
+    L1, L2, D, chi, J2, n = case
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=L1 * 10 + L2, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=D)
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2, n_blocks=3)
+    ctx.set_theta(th)
+    _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-9)
+
+
+def test_eval_fp64_heis8_shape():
+    # 8x8, D=4, chi=16: the bench workload's contraction sizes (truncating chi), sampled rows.
+    L, D, chi = 8, 4, 16
+    lat = Lattice(L, L, D)
+    th = wl.random_theta(L, L, D, seed=81, scale=0.2, diag_bias=1.0)
+    S = wl.random_configs(L, L, 3, seed=82)
+    ctx = _ctx(L, L, D, chi, 3)
+    ctx.set_theta(th)
+    _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-8)
+
+
+def test_eval_fp32_matches_oracle():
+    L1, L2, D, chi, J2 = 4, 4, 3, 4, 0.5
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=5, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, 6, seed=6)
+    ctx = _ctx(L1, L2, D, chi, 6, J2=J2, prec=binding.PEPS_FP32)
+    ctx.set_theta(th)
+    _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 2e-4, 2e-4, 2e-3)
+
+
+def test_init_matches_oracle_bit_exact():
+    L1, L2, D, n, seed = 4, 5, 3, 9, 1234
+    lat = Lattice(L1, L2, D)
+    ctx = _ctx(L1, L2, D, 9, n, seed=seed, noise=1e-3)
+    assert np.array_equal(ctx.get_theta(), peps.init_theta(lat, seed, 1e-3))
+    assert np.array_equal(ctx.get_configs(), peps.init_configs(lat, seed, n))
+    assert ctx.Np == lat.Np and ctx.No == lat.No
+
+
+@pytest.mark.parametrize("p", [2, 1])
+def test_mc_sweep_matches_oracle(p):
+    L1, L2, D, chi, J2, n = 4, 4, 2, 4, 0.3, 16
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=7, scale=0.4, diag_bias=1.0)
+    S0 = wl.random_configs(L1, L2, n, seed=8, diagonal_fraction=0.7)
+    seed = 99
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2, seed=seed, n_blocks=5)
+    ctx.set_theta(th)
+    ctx.set_configs(S0)
+    ctx.sweeps_done = 3
+    ctx.mc_sweep(2, p)
+    got = ctx.get_configs()
+    mismatch = 0
+    for k in range(n):
+        Sk = S0[k]
+        for sw in (3, 4):
+            Sk, _, _ = sampler.mc_sweep(lat, th, Sk, chi, p, seed, k, sw)
+        mismatch += int(not np.array_equal(Sk, got[k]))
+    assert mismatch == 0
+    assert ctx.sweeps_done == 5
+
+
+def test_mc_sweep_truncated_chi_matches_oracle():
+    L1, L2, D, chi, n = 4, 4, 3, 4, 6
+    lat = Lattice(L1, L2, D)
+    th = wl.random_theta(L1, L2, D, seed=17, scale=0.4, diag_bias=1.0)
+    S0 = wl.random_configs(L1, L2, n, seed=18)
+    ctx = _ctx(L1, L2, D, chi, n, seed=5)
+    ctx.set_theta(th)
+    ctx.set_configs(S0)
+    ctx.mc_sweep(1, 2)
+    got = ctx.get_configs()
+    for k in range(n):
+        Sk, _, _ = sampler.mc_sweep(lat, th, S0[k], chi, 2, 5, k, 0)
+        assert np.array_equal(Sk, got[k]), k
+
+
+@pytest.mark.parametrize("p", [2, 1])
+def test_sr_step_matches_oracle(p):
+    L1, L2, D, chi, J2, n = 3, 3, 2, 4, 0.5, 40
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=21, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=22)
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2)
+    ctx.set_theta(th)
+    ctx.set_configs(S)
+    ctx.eval_chains()
+    tau, eps, tol = 0.05, 1e-3, 1e-12
+    st = ctx.sr_step(tau, eps=eps, max_cg=500, cg_tol=tol, p=p)
+    th_gpu = ctx.get_theta()
+    res = [peps.eval_sample(lat, th, S[k], chi) for k in range(n)]
+    la = np.array([r['log_abs'] for r in res])
+    es = np.array([r['e_sys'] for r in res])
+    ea = np.array([r['e_anc'] for r in res])
+    O = np.array([r['O'] for r in res])
+    th_or, x, g, it, resid = sr.sr_step(lat, th, S, la, es, ea, O, p, tau, eps, tol, 500)
+    w = sr.weights(la, p)
+    Of = sr.expand_O(lat, S, O)
+    obar, _, _ = sr.sr_quantities(Of, w, es + ea)
+    xd = np.linalg.solve(sr.dense_G(Of, w, obar, eps), g)
+    x_gpu = (th - th_gpu) / tau
+    assert np.max(np.abs(x_gpu - xd)) <= 1e-8 * np.max(np.abs(xd))
+    assert np.max(np.abs(x_gpu - x)) <= 1e-8 * np.max(np.abs(xd))
+    assert st['cg_resid'] <= tol and not st['cg_maxit']
+    assert abs(st['cg_iters'] - it) <= 2
+    o = obs_mod.observables(lat, 0.0, w, es, ea, S)
+    assert st['E_site'] == pytest.approx(o['E_site'], rel=1e-10, abs=1e-12)
+    assert st['diag_frac'] == pytest.approx(o['diag_frac'])
+
+
+def test_sr_step_cg_maxit_warning_and_observables():
+    L1, L2, D, chi, n = 3, 3, 2, 4, 24
+    lat = Lattice(L1, L2, D)
+    th = wl.random_theta(L1, L2, D, seed=31, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=32)
+    ctx = _ctx(L1, L2, D, chi, n)
+    ctx.set_theta(th)
+    ctx.set_configs(S)
+    ctx.eval_chains()
+    ob = ctx.observables(p=2)
+    res = [peps.eval_sample(lat, th, S[k], chi, with_O=False) for k in range(n)]
+    es = np.array([r['e_sys'] for r in res])
+    ea = np.array([r['e_anc'] for r in res])
+    o = obs_mod.observables(lat, 0.0, np.full(n, 1.0 / n), es, ea, S)
+    assert ob['E_site'] == pytest.approx(o['E_site'], rel=1e-10, abs=1e-12)
+    st = ctx.sr_step(0.01, eps=1e-4, max_cg=2, cg_tol=1e-14, p=2)
+    assert st['cg_maxit'] and st['cg_iters'] == 2
+
+
+def test_errors_and_edge_cases():
+    ctx = _ctx(3, 3, 2, 4, 4)
+    with pytest.raises(binding.PepsError) as e:
+        ctx.sr_step(0.01)
+    assert e.value.code == binding.PEPS_ESTATE
+    bad = np.full((4, 9), 5, np.uint8)
+    with pytest.raises(binding.PepsError) as e:
+        ctx.set_configs(bad)
+    assert e.value.code == binding.PEPS_EINVAL
+    with pytest.raises(binding.PepsError):
+        ctx.mc_sweep(1, p=3)
+    la, sg, es, ea, O = ctx.eval_batch(np.zeros((0, 9), np.uint8))
+    assert la.size == 0
+    # beta = 0 state with no noise: rho = 1 on diagonal configurations, 0 elsewhere
+    ctx0 = _ctx(3, 3, 2, 4, 4, noise=0.0)
+    S = np.array([[0] * 9, [3] * 9, [0, 3, 0, 3, 3, 0, 0, 0, 3], [1] + [0] * 8], np.uint8)
+    la, sg, es, ea, _ = ctx0.eval_batch(S, with_O=False)
+    assert np.allclose(la[:3], 0.0, atol=1e-14) and list(sg) == [1, 1, 1, 0]
