@@ -1,0 +1,358 @@
+"""Benchmark of one finite-temperature PEPS-VMC cooling step on GB300.
+
+A step is the whole hot path of one stochastic-reconfiguration step (arXiv:2409.05285,
+Sec. II): one Metropolis sweep of every chain, the evaluation of every chain (boundary-MPS
+environments, amplitude, E_loc, O rows), and the SR update (weights, gradient, CG solve
+with two passes over the O rows per iteration, theta update).
+
+Workload (default): 8x8 open Heisenberg J=1, d^2 = 4, D = 4, chi = 16, 8192 chains, the
+state after a short cooling run from the perturbed beta = 0 state; tau = 0.02, eps = 1e-4,
+CG tolerance 1e-10 relative, at most 100 CG iterations.  The O rows (8192 x 10816 values,
+709 MB in float64) are larger than L2, so no L2 flush is needed between steps.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
+sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PEPS samples/s per SR cooling step (mixed vs FP64 at <=1e-3 E/site); p50/p99 step latency"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# Per-SM issue rates of GB300 (sm_103): 128 FP32 FMA/clk, 2 FP64 FMA/clk; 152 SMs; 2070 MHz.
+SMS, MAX_MHZ = 152, 2070.0
+PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
+PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"bench_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cooled_state(ctx, steps, tau, p_switch_t):
+    """Cools the fresh context for `steps` SR steps (p = 1 while beta_obs < 0.3)."""
+    t = 0.0
+    for _ in range(steps):
+        p = 1 if 4 * t < p_switch_t else 2
+        ctx.step(n_sweeps=1, p=p, tau=tau, eps=1e-4, max_cg=100, cg_tol=1e-10)
+        t += tau
+    return t
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_2409_05285_gb300 import binding
+    from paper_2409_05285_gb300.build import build
+    from paper_2409_05285_gb300.workloads import WORKLOADS
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if ws > 1:
+        torch.distributed.barrier()
+    wl = WORKLOADS[args.workload]
+    prec = binding.PEPS_FP32 if args.precision == "fp32" else binding.PEPS_FP64
+    stream = torch.cuda.Stream()
+    n = args.chains or wl.n_samples
+    ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
+                          init_noise=wl.init_noise, seed=wl.seed + rank,
+                          stream=ctypes_stream(stream))
+    ctx.mc_sweep(args.burn, p=1)
+    t0 = cooled_state(ctx, args.precool, wl.tau, 0.3)
+    tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
+    p = 2
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        ctx.step(n_sweeps=1, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+    clocks = Clocks(local)
+    step_ms, mc_ms, eval_ms, sr_ms, eval_flops, mc_flops, cg_its, stats = [], [], [], [], [], [], [], []
+    jac = []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e_start, e_end = ev(), ev()
+    e_start.record(stream)
+    for _ in range(args.steps):
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        ctx.mc_sweep(1, p)
+        e1.record(stream)
+        mc_flops.append(ctx.counters()[0])
+        ctx.eval_chains()
+        e2.record(stream)
+        f_ev, j_ev = ctx.counters()
+        eval_flops.append(f_ev)
+        jac.append(j_ev / n)
+        st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=p)
+        e3.record(stream)
+        stats.append(st)
+        cg_its.append(st["cg_iters"])
+        e3.synchronize()
+        mc_ms.append(e0.elapsed_time(e1))
+        eval_ms.append(e1.elapsed_time(e2))
+        sr_ms.append(e2.elapsed_time(e3))
+        step_ms.append(e0.elapsed_time(e3))
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = e_start.elapsed_time(e_end)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    samples_per_s = ws * n / (ms_per_step / 1e3)
+
+    # end to end through the public API with host buffers: upload theta and the chain
+    # configurations from pinned host memory, run the step, read theta' and S' back.
+    th_h = torch.from_numpy(ctx.get_theta()).pin_memory()
+    S_h = torch.from_numpy(ctx.get_configs()).pin_memory()
+    th_np, S_np = th_h.numpy(), S_h.numpy()
+    e2e_ms = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.set_theta(th_np)
+        ctx.set_configs(S_np)
+        ctx.step(n_sweeps=1, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+        th_np[:] = ctx.get_theta()
+        S_np[:] = ctx.get_configs()
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+    e2e_step = statistics.median(e2e_ms)
+
+    peaks = measured_peaks()
+    dom_flops = statistics.mean(eval_flops)
+    dom_ms = statistics.mean(eval_ms)
+    achieved = dom_flops / (dom_ms / 1e3) / 1e12
+    peak = PEAK_FP64_TFLOPS if prec == binding.PEPS_FP64 else PEAK_FP32_TFLOPS
+    step_sorted = sorted(step_ms)
+    out = {
+        "metric": METRIC,
+        "value": samples_per_s,
+        "unit": "samples/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64" if prec == binding.PEPS_FP64 else "f32",
+        "data": "synthetic (seeded beta=0 PEPS cooled in-run; no dataset)",
+        "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg J1={wl.J1} J2={wl.J2}, d2=4, "
+                               f"D={wl.D}, chi={wl.chi}, chains={n} per GPU",
+                   "global_batch": ws * n, "tau": tau, "eps": eps, "max_cg": max_cg,
+                   "cg_tol": tol, "t_start": t0, "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (O rows %.0f MB)" % (n * ctx.No * (8 if prec == 0 else 4) / 1e6)},
+        "sr_steps_per_s": ws / (ms_per_step / 1e3),
+        "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
+                       "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+        "phase_ms": {"mc_sweep": statistics.mean(mc_ms), "eval": statistics.mean(eval_ms),
+                     "sr_step": statistics.mean(sr_ms)},
+        "cg_iters": statistics.mean(cg_its),
+        "eval_gflop_per_sample": statistics.mean(eval_flops) / n / 1e9,
+        "jacobi_sweeps_per_sample": statistics.mean(jac),
+        "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"],
+        "roofline": {"kernel": "k_eval (per-sample contraction)", "bound": "alu",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "derived: %s FMA/clk/SM x 152 SMs x 2070 MHz" % ("2 FP64" if prec == 0 else "128 FP32")},
+        "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(ctx.Np * 8 + n * ctx.N),
+                "d2h_bytes_per_step": int(ctx.Np * 8 + n * ctx.N)},
+        "gpu_launches": None,
+        "clocks": clk,
+    }
+    # kernel launches per step: 1 k_mc + 1 k_eval + SR (weights, colsum x2, dot, init, dot,
+    # 6 per CG iteration, update) -- the CUDA kernels of this library
+    out["gpu_launches"] = int(args.steps * (2 + 6 + 6 * statistics.mean(cg_its) + 1))
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, n, args.cpu_samples)
+    ctx.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def ctypes_stream(stream):
+    import ctypes
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _oracle_chain(args):
+    """One chain of the oracle: a Metropolis sweep then the evaluation (runs in a worker)."""
+    L, D, chi, J1, J2, seed, chain, theta = args
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import peps, sampler
+    from oracle.lattice import Lattice
+    lat = Lattice(L, L, D, J1=J1, J2=J2)
+    S = peps.init_configs(lat, seed, chain + 1)[chain]
+    S, _, _ = sampler.mc_sweep(lat, theta, S, chi, 2, seed, chain, 0)
+    r = peps.eval_sample(lat, theta, S, chi)
+    return S, r["log_abs"], r["e_sys"], r["e_anc"], r["O"]
+
+
+def oracle_step(wl, n_samples, pool):
+    """The oracle's cooling step on n_samples chains (sweep + evaluation per chain in the
+    pool, then the SR update).  Returns seconds."""
+    import numpy as np
+    from oracle import peps, sr
+    from oracle.lattice import Lattice
+    lat = Lattice(wl.L, wl.L, wl.D, J1=wl.J1, J2=wl.J2)
+    theta = peps.init_theta(lat, wl.seed, wl.init_noise)
+    t0 = time.perf_counter()
+    res = pool.map(_oracle_chain, [(wl.L, wl.D, wl.chi, wl.J1, wl.J2, wl.seed, c, theta)
+                                   for c in range(n_samples)])
+    S = np.array([r[0] for r in res])
+    la = np.array([r[1] for r in res])
+    es = np.array([r[2] for r in res])
+    ea = np.array([r[3] for r in res])
+    O = np.array([r[4] for r in res])
+    sr.sr_step(lat, theta, S, la, es, ea, O, 2, wl.tau, wl.eps, wl.cg_tol, wl.max_cg)
+    return time.perf_counter() - t0
+
+
+def _one_thread_workers():
+    # one BLAS thread per worker process: the pool already spans the host cores
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+
+
+def cpu_baseline(wl, n, n_samples):
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    _one_thread_workers()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        secs = oracle_step(wl, n_samples, pool)
+    return {"value": n_samples / secs, "unit": "samples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n_samples} chains of the {wl.L}x{wl.L} D={wl.D} chi={wl.chi} workload: one "
+                      f"Metropolis sweep + evaluation each (spawn pool over {cores} host cores), "
+                      f"then one SR step on those samples; value = samples / wall time"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import multiprocessing as mp
+    from paper_2409_05285_gb300.workloads import WORKLOADS
+    wl = WORKLOADS[args.workload]
+    cores = os.cpu_count() or 1
+    _one_thread_workers()
+    ctx = mp.get_context("spawn")
+    n_s = args.cpu_samples
+    with ctx.Pool(cores) as pool:
+        for _ in range(args.warmup):
+            oracle_step(wl, min(n_s, cores), pool)
+        times = [oracle_step(wl, n_s, pool) for _ in range(args.steps)]
+    ms = 1e3 * statistics.mean(times)
+    v = n_s / (ms / 1e3)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg D={wl.D} "
+                                                       f"chi={wl.chi}, {n_s} chains per step (bounded sample)"},
+           "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                            "sample": f"{n_s} chains per step: sweep + evaluation + SR step"},
+           "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heis8")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--chains", type=int, default=0)
+    ap.add_argument("--burn", type=int, default=2)
+    ap.add_argument("--precool", type=int, default=2)
+    ap.add_argument("--cpu-samples", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -46,6 +46,8 @@ extern "C" {
 #define PEPS_ECUDA (-3)      /* a CUDA runtime call failed */
 #define PEPS_ESTATE (-4)     /* call out of order (e.g. sr_step before an evaluation) */
 #define PEPS_ENOTFINITE (-5) /* non-finite amplitude, energy or CG scalar */
+#define PEPS_ECORRUPT (-6)   /* checkpoint unreadable, of another problem, or failing its checksum */
+#define PEPS_EIO (-7)        /* checkpoint file could not be written */
 
 /* Arithmetic of the per-sample contraction (environment, amplitude, E_loc, O).  The
  * log-amplitude accumulation, the SR reductions and CG, and the observables are float64
@@ -136,6 +138,18 @@ size_t peps_num_params(const peps_ctx* ctx);
 size_t peps_o_row_len(const peps_ctx* ctx);
 int64_t peps_sweeps_done(const peps_ctx* ctx);
 int peps_set_sweeps_done(peps_ctx* ctx, int64_t sweeps);
+
+/* Checkpoint of the cooling state: parameters, theta (float64), chain configurations,
+ * imaginary time t and the Philox sweep counter, with an FNV-1a checksum.  Restoring it
+ * into a context created with the same lattice, couplings, D, chi and chain count
+ * resumes the run bit for bit (same kernels, same random numbers).  peps_restore returns
+ * PEPS_ECORRUPT for a truncated or altered file or a different problem, and leaves the
+ * context unchanged in that case. */
+int peps_checkpoint(peps_ctx* ctx, const char* path);
+int peps_restore(peps_ctx* ctx, const char* path);
+
+/* Imaginary time t = sum of the tau of the SR steps applied so far. */
+double peps_time(const peps_ctx* ctx);
 
 /* Device counters of the last peps_eval_batch / peps_mc_sweep launch: algorithmic
  * flops (contractions, Householder, Jacobi), Jacobi sweeps. */

@@ -18,6 +18,8 @@ PEPS_ENOMEM = -2
 PEPS_ECUDA = -3
 PEPS_ESTATE = -4
 PEPS_ENOTFINITE = -5
+PEPS_ECORRUPT = -6
+PEPS_EIO = -7
 PEPS_FP64 = 0
 PEPS_FP32 = 1
 PEPS_MODEL_J1J2 = 0
@@ -26,7 +28,8 @@ EXPORTS = [
     "peps_init", "peps_mc_sweep", "peps_eval_batch", "peps_sr_step", "peps_observables",
     "peps_step", "peps_get_theta", "peps_set_theta", "peps_get_configs", "peps_set_configs",
     "peps_num_params", "peps_o_row_len", "peps_sweeps_done", "peps_set_sweeps_done",
-    "peps_last_counters", "peps_free", "peps_last_error", "peps_version",
+    "peps_last_counters", "peps_free", "peps_last_error", "peps_version", "peps_checkpoint",
+    "peps_restore", "peps_time",
 ]
 
 
@@ -80,6 +83,10 @@ def load(path=None):
     lib.peps_set_sweeps_done.argtypes = [vp, ctypes.c_int64]
     lib.peps_last_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64)]
+    lib.peps_checkpoint.argtypes = [vp, ctypes.c_char_p]
+    lib.peps_restore.argtypes = [vp, ctypes.c_char_p]
+    lib.peps_time.argtypes = [vp]
+    lib.peps_time.restype = ctypes.c_double
     lib.peps_free.argtypes = [vp]
     lib.peps_free.restype = None
     lib.peps_last_error.argtypes = [vp]
@@ -157,6 +164,16 @@ class Context:
     def set_configs(self, S):
         S = np.ascontiguousarray(S, dtype=np.uint8)
         self._check(self.lib.peps_set_configs(self.ctx, _ptr(S), S.size))
+
+    @property
+    def t(self):
+        return float(self.lib.peps_time(self.ctx))
+
+    def checkpoint(self, path):
+        self._check(self.lib.peps_checkpoint(self.ctx, str(path).encode()))
+
+    def restore(self, path):
+        self._check(self.lib.peps_restore(self.ctx, str(path).encode()))
 
     @property
     def sweeps_done(self):

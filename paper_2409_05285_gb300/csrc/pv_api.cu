@@ -78,16 +78,19 @@ __device__ void flush_counters(Shared<T>& sh, double* flops, unsigned long long*
 
 // Persistent evaluation kernel: block b handles samples b, b + grid, ...
 template <typename T, typename OT>
-__global__ void __launch_bounds__(SAMPLE_THREADS)
+__global__ void __launch_bounds__(SAMPLE_THREADS, 4)
     k_eval(Geom g, const T* __restrict__ theta, const uint8_t* __restrict__ S, int n,
            T* scratch, int* iscratch, long long sreal, long long sint,
            double* __restrict__ log_abs, int8_t* __restrict__ sign, double* __restrict__ es,
            double* __restrict__ ea, OT* __restrict__ O, long long No, T jtol, int max_sweeps,
-           double* flops, unsigned long long* jsw) {
+           double* flops, unsigned long long* jsw, int smem_bytes) {
   __shared__ Shared<T> sh;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   Scratch<T> sc;
   sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
           g.L1, g.L2, g.D, g.chi);
+  sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
+  sc.smem_cap = smem_bytes / (int)sizeof(T);
   init_shared(sh);
   const int N = g.N();
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -107,15 +110,18 @@ __global__ void __launch_bounds__(SAMPLE_THREADS)
 }
 
 template <typename T>
-__global__ void __launch_bounds__(SAMPLE_THREADS)
+__global__ void __launch_bounds__(SAMPLE_THREADS, 4)
     k_mc(Geom g, const T* __restrict__ theta, uint8_t* __restrict__ S, int n, T* scratch,
          int* iscratch, long long sreal, long long sint, int p, uint64_t seed, long long sweep0,
          int n_sweeps, int* __restrict__ acc, int* __restrict__ prop, T jtol, int max_sweeps,
-         double* flops, unsigned long long* jsw) {
+         double* flops, unsigned long long* jsw, int smem_bytes) {
   __shared__ Shared<T> sh;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
   Scratch<T> sc;
   sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
           g.L1, g.L2, g.D, g.chi);
+  sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
+  sc.smem_cap = smem_bytes / (int)sizeof(T);
   init_shared(sh);
   const int N = g.N();
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -184,6 +190,7 @@ struct peps_ctx {
   int* d_iscr = nullptr;
   int nblk = 0;
   long long sreal = 0, sint = 0;
+  int smem_bytes = 0;   // dynamic shared memory of the sample kernels (Jacobi work matrices)
   double* d_flops = nullptr;
   unsigned long long* d_jsw = nullptr;
   int *d_acc = nullptr, *d_prop = nullptr;
@@ -271,13 +278,13 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
   int grid = std::min(c->nblk, nb);
   if (fp64(c)) {
-    k_eval<double, double><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+    k_eval<double, double><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
         g, c->d_theta, dS, nb, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
-        (double*)O, c->No, JTOL_F64, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw);
+        (double*)O, c->No, JTOL_F64, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes);
   } else {
-    k_eval<float, float><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+    k_eval<float, float><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
         g, c->d_theta_f, dS, nb, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
-        (float*)O, c->No, JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw);
+        (float*)O, c->No, JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes);
   }
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
@@ -356,6 +363,26 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   ScratchDims sd = scratch_dims(P->L1, P->L2, P->D, P->chi);
   c->sreal = (sd.n_real + 31) & ~31LL;
   c->sint = (sd.n_int + 31) & ~31LL;
+  {
+    // Jacobi work matrices in shared memory when both fit in 96 KB
+    long long cD = (long long)P->chi * P->D;
+    long long need = cD * (cD + 1) * 2 * (long long)real;
+    c->smem_bytes = need <= 96 * 1024 ? (int)need : 0;
+    if (c->smem_bytes > 48 * 1024) {
+      cudaError_t ea;
+      if (fp64(c)) {
+        ea = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+      } else {
+        ea = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+      }
+      if (ea != cudaSuccess) {
+        cudaGetLastError();
+        c->smem_bytes = 0;
+      }
+    }
+  }
   int want = P->n_blocks > 0 ? P->n_blocks : sms * 4;
   c->nblk = std::max(1, std::min(want, n));
   if ((rc = dalloc(c, &c->d_scr, (size_t)c->nblk * c->sreal * real))) return bail(rc);
@@ -454,15 +481,15 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
   int grid = std::min(c->nblk, n);
   if (fp64(c)) {
-    k_mc<double><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+    k_mc<double><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
         g, c->d_theta, c->d_S, n, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
         c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F64, JAC_MAX_SWEEPS,
-        c->d_flops, c->d_jsw);
+        c->d_flops, c->d_jsw, c->smem_bytes);
   } else {
-    k_mc<float><<<grid, SAMPLE_THREADS, 0, c->stream>>>(
+    k_mc<float><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
         g, c->d_theta_f, c->d_S, n, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
         c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F32, JAC_MAX_SWEEPS,
-        c->d_flops, c->d_jsw);
+        c->d_flops, c->d_jsw, c->smem_bytes);
   }
   PV_CUDA(c, cudaGetLastError());
   c->sweeps += n_sweeps;
@@ -654,6 +681,103 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
           std::sqrt(h.rr) > cg_tol * h.gnorm)
              ? PEPS_WARN_CG_MAXIT
              : PEPS_OK;
+}
+
+double peps_time(const peps_ctx* c) { return c ? c->t : 0.0; }
+
+namespace {
+struct CkptHeader {
+  char magic[8];
+  uint32_t version, pad;
+  int L1, L2, model, D, chi, n_chains, precision, pad2;
+  double J1, J2, t;
+  int64_t sweeps, Np, nS;
+};
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+  const unsigned char* b = (const unsigned char*)p;
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ULL;
+  }
+  return h;
+}
+}  // namespace
+
+int peps_checkpoint(peps_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, PEPS_EINVAL, "checkpoint: args");
+  std::vector<double> th(c->Np);
+  std::vector<uint8_t> S((size_t)c->P.n_chains * c->N);
+  PV_TRY(peps_get_theta(c, th.data(), th.size()));
+  PV_TRY(peps_get_configs(c, S.data(), S.size()));
+  CkptHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "PEPSCKP1", 8);
+  h.version = 1;
+  h.L1 = c->P.L1;
+  h.L2 = c->P.L2;
+  h.model = c->P.model;
+  h.D = c->P.D;
+  h.chi = c->P.chi;
+  h.n_chains = c->P.n_chains;
+  h.precision = c->P.precision;
+  h.J1 = c->P.J1;
+  h.J2 = c->P.J2;
+  h.t = c->t;
+  h.sweeps = c->sweeps;
+  h.Np = c->Np;
+  h.nS = (int64_t)S.size();
+  uint64_t sum = 1469598103934665603ULL;
+  sum = fnv1a(&h, sizeof(h), sum);
+  sum = fnv1a(th.data(), th.size() * sizeof(double), sum);
+  sum = fnv1a(S.data(), S.size(), sum);
+  FILE* f = fopen(path, "wb");
+  if (!f) return fail(c, PEPS_EIO, std::string("checkpoint: cannot open ") + path);
+  bool ok = fwrite(&h, sizeof(h), 1, f) == 1 &&
+            fwrite(th.data(), sizeof(double), th.size(), f) == th.size() &&
+            fwrite(S.data(), 1, S.size(), f) == S.size() && fwrite(&sum, sizeof(sum), 1, f) == 1;
+  ok = (fclose(f) == 0) && ok;
+  return ok ? PEPS_OK : fail(c, PEPS_EIO, "checkpoint: write failed");
+}
+
+int peps_restore(peps_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, PEPS_EINVAL, "restore: args");
+  FILE* f = fopen(path, "rb");
+  if (!f) return fail(c, PEPS_ECORRUPT, std::string("restore: cannot open ") + path);
+  CkptHeader h;
+  bool ok = fread(&h, sizeof(h), 1, f) == 1 && memcmp(h.magic, "PEPSCKP1", 8) == 0 &&
+            h.version == 1 && h.L1 == c->P.L1 && h.L2 == c->P.L2 && h.model == c->P.model &&
+            h.D == c->P.D && h.chi == c->P.chi && h.n_chains == c->P.n_chains &&
+            h.J1 == c->P.J1 && h.J2 == c->P.J2 && h.Np == c->Np &&
+            h.nS == (int64_t)c->P.n_chains * c->N && h.sweeps >= 0;
+  std::vector<double> th;
+  std::vector<uint8_t> S;
+  uint64_t sum = 0;
+  if (ok) {
+    th.resize(c->Np);
+    S.resize((size_t)h.nS);
+    ok = fread(th.data(), sizeof(double), th.size(), f) == th.size() &&
+         fread(S.data(), 1, S.size(), f) == S.size() && fread(&sum, sizeof(sum), 1, f) == 1;
+  }
+  if (ok) {
+    char extra;
+    ok = fread(&extra, 1, 1, f) == 0;   // no trailing bytes
+  }
+  fclose(f);
+  if (ok) {
+    uint64_t chk = 1469598103934665603ULL;
+    chk = fnv1a(&h, sizeof(h), chk);
+    chk = fnv1a(th.data(), th.size() * sizeof(double), chk);
+    chk = fnv1a(S.data(), S.size(), chk);
+    ok = chk == sum;
+    for (size_t i = 0; ok && i < S.size(); ++i) ok = S[i] <= 3;
+  }
+  if (!ok) return fail(c, PEPS_ECORRUPT, std::string("restore: corrupt or mismatched checkpoint ") + path);
+  PV_TRY(peps_set_theta(c, th.data(), th.size()));
+  PV_TRY(peps_set_configs(c, S.data(), S.size()));
+  c->t = h.t;
+  c->sweeps = h.sweeps;
+  return PEPS_OK;
 }
 
 int peps_step(peps_ctx* c, int n_sweeps, int p, double tau, double eps, int max_cg,

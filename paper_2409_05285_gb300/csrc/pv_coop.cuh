@@ -166,25 +166,71 @@ PV_HD Spec make_spec(const char* out, const char* a, const char* b, const Dims& 
 }
 
 // Executes the contraction with the whole block (grid-stride over output elements).
+// Adjacent output (and contraction) dimensions whose strides chain in both operands are
+// merged first; the index arithmetic is 32-bit and the contraction loop keeps four
+// independent accumulators.
 template <typename T, typename TA, typename TB>
 PV_HDN void contract(T* out, const TA* A, const TB* B, const Spec& s) {
-  for (long long idx = PV_TID; idx < s.total; idx += PV_NTHR) {
-    long long rem = idx, oa = 0, ob = 0;
-    for (int dd = s.no - 1; dd >= 0; --dd) {
-      long long i = rem % s.os[dd];
-      rem /= s.os[dd];
-      oa += i * s.ao[dd];
-      ob += i * s.bo[dd];
+  int no = 0, os[6], ao[6], bo[6];
+  for (int d = 0; d < s.no; ++d) {
+    int n = s.os[d], a = (int)s.ao[d], b = (int)s.bo[d];
+    if (n == 1) continue;
+    if (no > 0 && ao[no - 1] == a * n && bo[no - 1] == b * n) {
+      os[no - 1] *= n;
+      ao[no - 1] = a;
+      bo[no - 1] = b;
+    } else {
+      os[no] = n;
+      ao[no] = a;
+      bo[no] = b;
+      ++no;
     }
-    T acc = 0;
-    for (int k0 = 0; k0 < s.ks[0]; ++k0)
-      for (int k1 = 0; k1 < s.ks[1]; ++k1)
-        for (int k2 = 0; k2 < s.ks[2]; ++k2) {
-          long long ia = oa + k0 * s.ak[0] + k1 * s.ak[1] + k2 * s.ak[2];
-          long long ib = ob + k0 * s.bk[0] + k1 * s.bk[1] + k2 * s.bk[2];
-          acc += (T)A[ia] * (T)B[ib];
+  }
+  int nk = 0, ks[3], ak[3], bk[3];
+  for (int d = 0; d < s.nk; ++d) {
+    int n = s.ks[d], a = (int)s.ak[d], b = (int)s.bk[d];
+    if (n == 1) continue;
+    if (nk > 0 && ak[nk - 1] == a * n && bk[nk - 1] == b * n) {
+      ks[nk - 1] *= n;
+      ak[nk - 1] = a;
+      bk[nk - 1] = b;
+    } else {
+      ks[nk] = n;
+      ak[nk] = a;
+      bk[nk] = b;
+      ++nk;
+    }
+  }
+  for (int d = nk; d < 3; ++d) {
+    ks[d] = 1;
+    ak[d] = bk[d] = 0;
+  }
+  const int total = (int)s.total;
+  const int K0 = ks[0], a0 = ak[0], b0 = bk[0];
+  for (int idx = PV_TID; idx < total; idx += PV_NTHR) {
+    int rem = idx, oa = 0, ob = 0;
+    for (int d = no - 1; d >= 0; --d) {
+      int q = rem / os[d];
+      int i = rem - q * os[d];
+      rem = q;
+      oa += i * ao[d];
+      ob += i * bo[d];
+    }
+    T acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+    for (int k2 = 0; k2 < ks[2]; ++k2)
+      for (int k1 = 0; k1 < ks[1]; ++k1) {
+        const TA* pa = A + oa + k1 * ak[1] + k2 * ak[2];
+        const TB* pb = B + ob + k1 * bk[1] + k2 * bk[2];
+        int k0 = 0;
+        for (; k0 + 4 <= K0; k0 += 4) {
+          acc0 += (T)pa[k0 * a0] * (T)pb[k0 * b0];
+          acc1 += (T)pa[(k0 + 1) * a0] * (T)pb[(k0 + 1) * b0];
+          acc2 += (T)pa[(k0 + 2) * a0] * (T)pb[(k0 + 2) * b0];
+          acc3 += (T)pa[(k0 + 3) * a0] * (T)pb[(k0 + 3) * b0];
         }
-    out[idx] = acc;
+        for (; k0 < K0; ++k0) acc0 += (T)pa[k0 * a0] * (T)pb[k0 * b0];
+      }
+    out[idx] = (acc0 + acc1) + (acc2 + acc3);
   }
   PV_SYNC();
 }
@@ -288,14 +334,25 @@ PV_HDN double lq_factor(T* Lout, T* W, int m, int n, T* red, T* sh) {
 }
 
 // ---------------------------------------------------------------------------------------
-// One-sided (Hestenes) Jacobi: rotates the `nc` columns of Y (column-major, column j at
-// Y + j*len) until they are mutually orthogonal; when V is given the same rotations are
-// applied to its nc columns of length vlen.  Columns are paired in parallel round-robin
-// order, one warp per pair.  Returns the flop count; *sweeps_out receives the number of
-// sweeps.  `flag` is one shared int.
+// One-sided (Hestenes) Jacobi: rotates the `nc` columns of Y (column j at Y + j*ldy, length
+// len) until they are mutually orthogonal; when V is given the same rotations are applied
+// to its nc columns (column j at V + j*ldv, length vlen).  Columns are paired in parallel
+// round-robin order; each pair is handled by a group of G lanes (G a power of two, as many
+// lanes as the block allows).  Returns the flop count; *sweeps_out receives the number of
+// sweeps.  `flag` is one shared int, `red` PV_NWARP shared entries.
 template <typename T>
-PV_HDN double jacobi(T* Y, int nc, int len, T* V, int vlen, T tol, int max_sweeps, int* flag,
-                    int* sweeps_out) {
+PV_HD T group_sum(T v, int G) {
+#if defined(__CUDA_ARCH__)
+  for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+#else
+  (void)G;
+#endif
+  return v;
+}
+
+template <typename T>
+PV_HDN double jacobi(T* Y, int ldy, int nc, int len, T* V, int ldv, int vlen, T tol,
+                     int max_sweeps, int* flag, int* sweeps_out, T* red) {
   int np = nc + (nc & 1);   // even number of positions; position nc is empty when nc is odd
   double flops = 0;
   int sweep = 0;
@@ -303,60 +360,83 @@ PV_HDN double jacobi(T* Y, int nc, int len, T* V, int vlen, T tol, int max_sweep
     if (sweeps_out) *sweeps_out = 0;
     return 0;
   }
+  // Stopping test |x_p.x_q| <= tol |x_p||x_q| with tol no finer than the rounding of a
+  // length-len dot product; columns below eps*len of the matrix norm are treated as zero
+  // (their directions carry no weight and rounding keeps them from converging).
+  const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+  const T tol_eff = tol > (T)4 * len * eps ? tol : (T)4 * len * eps;
+  T nf2 = 0;
+  for (int j = 0; j < nc; ++j)
+    for (int i = PV_TID; i < len; i += PV_NTHR) nf2 += Y[(long long)j * ldy + i] * Y[(long long)j * ldy + i];
+  nf2 = cta_sum(nf2, red);
+  const T tiny = (eps * len) * (eps * len) * nf2;
+  const int npair = np / 2;
+  int G = 1;
+#if defined(__CUDA_ARCH__)
+  while (G < 32 && G * 2 * npair <= PV_NTHR) G *= 2;
+#endif
+  const int ngroups = PV_NTHR / G;
+  const int grp = PV_TID / G, gl = PV_TID % G;
+  const int iters = (npair + ngroups - 1) / ngroups;
   for (; sweep < max_sweeps; ++sweep) {
     if (PV_TID == 0) *flag = 0;
     PV_SYNC();
     for (int rnd = 0; rnd < np - 1; ++rnd) {
-      for (int pr = PV_WARP; pr < np / 2; pr += PV_NWARP) {
-        int p, q;
-        if (pr == 0) {
-          p = np - 1;
-          q = rnd;
-        } else {
-          p = (rnd + pr) % (np - 1);
-          q = (rnd - pr + (np - 1)) % (np - 1);
+      for (int it = 0; it < iters; ++it) {
+        int pr = grp + it * ngroups;
+        int p = 0, q = 0;
+        bool act = pr < npair;
+        if (act) {
+          if (pr == 0) {
+            p = np - 1;
+            q = rnd;
+          } else {
+            p = (rnd + pr) % (np - 1);
+            q = (rnd - pr + (np - 1)) % (np - 1);
+          }
+          if (p > q) {
+            int t = p;
+            p = q;
+            q = t;
+          }
+          act = q < nc;
         }
-        if (p >= nc || q >= nc) continue;
-        if (p > q) {
-          int t = p;
-          p = q;
-          q = t;
-        }
-        T* xp = Y + (long long)p * len;
-        T* xq = Y + (long long)q * len;
+        T* xp = Y + (long long)p * ldy;
+        T* xq = Y + (long long)q * ldy;
         T a = 0, b = 0, g = 0;
-        for (int i = PV_LANE; i < len; i += PV_WSIZE) {
-          T u = xp[i], w = xq[i];
-          a += u * u;
-          b += w * w;
-          g += u * w;
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
+        if (act)
+          for (int i = gl; i < len; i += G) {
+            T u = xp[i], w = xq[i];
+            a += u * u;
+            b += w * w;
+            g += u * w;
+          }
+        a = group_sum(a, G);
+        b = group_sum(b, G);
+        g = group_sum(g, G);
         T ag = g < 0 ? -g : g;
-        if (ag > tol * sqrt(a) * sqrt(b) && ag > (T)0) {
+        if (act && ag > tol_eff * sqrt(a) * sqrt(b) && a > tiny && b > tiny) {
           T zeta = (b - a) / ((T)2 * g);
           T az = zeta < 0 ? -zeta : zeta;
           T t = (T)1 / (az + sqrt((T)1 + az * az));
           if (zeta < 0) t = -t;
           T c = (T)1 / sqrt((T)1 + t * t);
-          T s = c * t;
-          for (int i = PV_LANE; i < len; i += PV_WSIZE) {
+          T sn = c * t;
+          for (int i = gl; i < len; i += G) {
             T u = xp[i], w = xq[i];
-            xp[i] = c * u - s * w;
-            xq[i] = s * u + c * w;
+            xp[i] = c * u - sn * w;
+            xq[i] = sn * u + c * w;
           }
           if (V) {
-            T* vp = V + (long long)p * vlen;
-            T* vq = V + (long long)q * vlen;
-            for (int i = PV_LANE; i < vlen; i += PV_WSIZE) {
+            T* vp = V + (long long)p * ldv;
+            T* vq = V + (long long)q * ldv;
+            for (int i = gl; i < vlen; i += G) {
               T u = vp[i], w = vq[i];
-              vp[i] = c * u - s * w;
-              vq[i] = s * u + c * w;
+              vp[i] = c * u - sn * w;
+              vq[i] = sn * u + c * w;
             }
           }
-          if (PV_LANE == 0) {
+          if (gl == 0) {
 #if defined(__CUDA_ARCH__)
             atomicAdd(flag, 1);
 #else
@@ -364,9 +444,6 @@ PV_HDN double jacobi(T* Y, int nc, int len, T* V, int vlen, T tol, int max_sweep
 #endif
           }
         }
-#if defined(__CUDA_ARCH__)
-        __syncwarp();
-#endif
       }
       PV_SYNC();
     }

@@ -81,6 +81,8 @@ struct Scratch {
   T *envD, *envU[2], *C, *Lf, *W, *Am, *Y, *V, *Uk, *carry, *sig;
   T *p1L, *p1R, *p2L, *p2R, *t0, *t1, *t2, *m0, *m1;
   int *bondD, *bondU[2], *bondC, *kf, *order;
+  T* smem = nullptr;        // optional fast buffer for the Jacobi matrices
+  long long smem_cap = 0;   // its capacity in elements
 
   PV_HD void bind(T* base, int* ibase, int L1, int L2, int D, int chi) {
     d = scratch_dims(L1, L2, D, chi);
@@ -230,17 +232,33 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
       fl += einsum(sc.Y, "qk", sc.Am, "qb", Lc, "bk", dq);
       nc = m;
       len = k;
-      for (long long i = PV_TID; i < (long long)m * m; i += PV_NTHR)
-        sc.V[i] = (i / m == i % m) ? (T)1 : (T)0;
-      PV_SYNC();
     }
+    // work copy: shared memory (columns padded to an odd stride) when it fits
+    T* Yw = sc.Y;
+    T* Vw = sc.V;
+    int ldy = len, ldv = m;
+    long long need = (long long)nc * (len + 1) + (tall ? 0 : (long long)m * (m + 1));
+    if (sc.smem && need <= sc.smem_cap) {
+      ldy = len | 1;
+      ldv = m | 1;
+      Yw = sc.smem;
+      Vw = sc.smem + (long long)nc * ldy;
+      for (long long i = PV_TID; i < (long long)nc * len; i += PV_NTHR)
+        Yw[(i / len) * ldy + i % len] = sc.Y[i];
+    }
+    if (!tall) {
+      for (long long i = PV_TID; i < (long long)m * m; i += PV_NTHR)
+        Vw[(i / m) * ldv + i % m] = (i / m == i % m) ? (T)1 : (T)0;
+    }
+    PV_SYNC();
     int sweeps = 0;
-    fl += jacobi(sc.Y, nc, len, tall ? (T*)nullptr : sc.V, m, jtol, max_sweeps, &sh.flag, &sweeps);
+    fl += jacobi(Yw, ldy, nc, len, tall ? (T*)nullptr : Vw, ldv, m, jtol, max_sweeps, &sh.flag,
+                 &sweeps, sh.red);
     if (PV_TID == 0) sh.jac_sweeps += sweeps;
     // singular values (column norms) and their descending order (ties by index)
     for (int j = PV_WARP; j < nc; j += PV_NWARP) {
       T s2 = 0;
-      const T* y = sc.Y + (long long)j * len;
+      const T* y = Yw + (long long)j * ldy;
       for (int i = PV_LANE; i < len; i += PV_WSIZE) s2 += y[i] * y[i];
       s2 = warp_sum(s2);
       if (PV_LANE == 0) sc.sig[j] = sqrt(s2);
@@ -265,9 +283,9 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
       T v;
       if (tall) {
         T s = sc.sig[j];
-        v = s > (T)0 ? sc.Y[(long long)j * len + q] / s : (T)0;
+        v = s > (T)0 ? Yw[(long long)j * ldy + q] / s : (T)0;
       } else {
-        v = sc.V[(long long)j * m + q];
+        v = Vw[(long long)j * ldv + q];
       }
       sc.Uk[idx] = v;
     }

@@ -194,3 +194,35 @@ def test_errors_and_edge_cases():
     S = np.array([[0] * 9, [3] * 9, [0, 3, 0, 3, 3, 0, 0, 0, 3], [1] + [0] * 8], np.uint8)
     la, sg, es, ea, _ = ctx0.eval_batch(S, with_O=False)
     assert np.allclose(la[:3], 0.0, atol=1e-14) and list(sg) == [1, 1, 1, 0]
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    L1, L2, D, chi, n = 3, 3, 2, 4, 16
+    a = _ctx(L1, L2, D, chi, n, J2=0.5, seed=11, noise=1e-2)
+    a.mc_sweep(2, p=1)
+    a.step(n_sweeps=1, p=1, tau=0.02)
+    ck = tmp_path / "state.ckpt"
+    a.checkpoint(ck)
+    for _ in range(2):
+        a.step(n_sweeps=1, p=2, tau=0.02)
+    b = _ctx(L1, L2, D, chi, n, J2=0.5, seed=11, noise=1e-2)
+    b.restore(ck)
+    assert b.t == pytest.approx(0.02) and b.sweeps_done == 3
+    for _ in range(2):
+        b.step(n_sweeps=1, p=2, tau=0.02)
+    assert np.array_equal(a.get_theta(), b.get_theta())
+    assert np.array_equal(a.get_configs(), b.get_configs())
+    # a corrupted or foreign checkpoint is rejected and leaves the context as it was
+    raw = bytearray(ck.read_bytes())
+    raw[200] ^= 0x40
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(bytes(raw))
+    th = b.get_theta()
+    with pytest.raises(binding.PepsError) as e:
+        b.restore(bad)
+    assert e.value.code == binding.PEPS_ECORRUPT
+    assert np.array_equal(th, b.get_theta())
+    other = _ctx(L1, L2, D, chi + 1, n, J2=0.5)
+    with pytest.raises(binding.PepsError) as e:
+        other.restore(ck)
+    assert e.value.code == binding.PEPS_ECORRUPT
