@@ -155,10 +155,39 @@ double peps_time(const peps_ctx* ctx);
  * flops (contractions, Householder, Jacobi), Jacobi sweeps. */
 int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
 
+/* Evaluation without any device allocation.
+ *
+ * For callers that must not allocate GPU memory themselves or through this library: code
+ * running inside a host framework that owns the whole device memory pool, a plug-in that is
+ * called while a CUDA graph is being captured, or a process whose memory budget is fixed
+ * at start-up.  The paper has no counterpart; this is a library convenience.
+ *
+ * Same results as peps_eval_batch on device pointers (the same kernel runs), for the
+ * problem in *params (n_chains, seed, init_noise and n_blocks are ignored): theta (float64
+ * [N_p]), S (uint8 [nb][L1*L2]) and every non-null output are DEVICE pointers owned by the
+ * caller.  The per-block work space comes from one file-scope device array of
+ * PEPS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process
+ * exits; no cudaMalloc, cudaFree or other allocating call is made.  The number of thread
+ * blocks is chosen so that their work space fits; a problem whose single block does not
+ * fit returns PEPS_EINVAL (message in peps_last_error(NULL)).
+ *
+ * The first call on a device, with that device current, performs a one-time set-up
+ * (looks up the array's device address and sets the kernel's shared-memory attribute);
+ * make that first call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents: calls that may overlap on the GPU (different streams, or
+ * several host threads) race and must be serialised by the caller.  The call enqueues its
+ * work on `stream` (cudaStream_t as void*, NULL = legacy default stream) and returns
+ * without waiting for it. */
+#define PEPS_NOALLOC_SCRATCH_BYTES (48u * 1024u * 1024u)
+int peps_eval_batch_noalloc(const peps_params* params, const double* theta, const uint8_t* S,
+                            int nb, double* log_abs, int8_t* sign, double* e_sys,
+                            double* e_anc, void* O, void* stream);
+
 /* Releases every device buffer of the context (NULL is ignored). */
 void peps_free(peps_ctx* ctx);
 
-/* Message of the last error on this context ("" when none). */
+/* Message of the last error on this context ("" when none); with ctx == NULL, the message
+ * of the calling thread's last failed peps_eval_batch_noalloc. */
 const char* peps_last_error(const peps_ctx* ctx);
 
 /* Library version string. */

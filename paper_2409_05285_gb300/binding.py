@@ -29,7 +29,7 @@ EXPORTS = [
     "peps_step", "peps_get_theta", "peps_set_theta", "peps_get_configs", "peps_set_configs",
     "peps_num_params", "peps_o_row_len", "peps_sweeps_done", "peps_set_sweeps_done",
     "peps_last_counters", "peps_free", "peps_last_error", "peps_version", "peps_checkpoint",
-    "peps_restore", "peps_time",
+    "peps_restore", "peps_time", "peps_eval_batch_noalloc",
 ]
 
 
@@ -87,6 +87,8 @@ def load(path=None):
     lib.peps_restore.argtypes = [vp, ctypes.c_char_p]
     lib.peps_time.argtypes = [vp]
     lib.peps_time.restype = ctypes.c_double
+    lib.peps_eval_batch_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, ip, vp, vp, vp, vp,
+                                            vp, vp]
     lib.peps_free.argtypes = [vp]
     lib.peps_free.restype = None
     lib.peps_last_error.argtypes = [vp]

@@ -296,7 +296,11 @@ extern "C" {
 
 const char* peps_version(void) { return "peps_vmc 0.1 (sm_103a)"; }
 
-const char* peps_last_error(const peps_ctx* ctx) { return ctx ? ctx->err.c_str() : ""; }
+static thread_local std::string g_noalloc_err;
+
+const char* peps_last_error(const peps_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_noalloc_err.c_str();
+}
 
 void peps_free(peps_ctx* ctx) {
   if (!ctx) return;
@@ -371,11 +375,11 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
     if (c->smem_bytes > 48 * 1024) {
       cudaError_t ea;
       if (fp64(c)) {
-        ea = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
-        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+        ea = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       } else {
-        ea = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
-        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, c->smem_bytes);
+        ea = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       }
       if (ea != cudaSuccess) {
         cudaGetLastError();
@@ -790,3 +794,151 @@ int peps_step(peps_ctx* c, int n_sweeps, int p, double tau, double eps, int max_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ allocation-free evaluation
+//
+// Work space of peps_eval_batch_noalloc: one file-scope device array, looked up once per
+// device.  Layout: [0, 256) counters | toff, ooff tables | float32 theta (FP32 path) |
+// per-block real scratch | per-block int scratch.
+
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PEPS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {nullptr};
+constexpr int NOALLOC_SMEM_MAX = 96 * 1024;
+
+// toff / ooff of the trimmed open-boundary layout, written on the device.
+__global__ void k_noalloc_tables(int L1, int L2, int D, long long* toff, long long* ooff) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  toff[0] = ooff[0] = 0;
+  for (int i = 0; i < L1 * L2; ++i) {
+    int r = i / L2, c = i % L2;
+    long long sz = (long long)(c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
+                   (r == L1 - 1 ? 1 : D);
+    toff[i + 1] = toff[i] + 4 * sz;
+    ooff[i + 1] = ooff[i] + sz;
+  }
+}
+
+long long align_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+int noalloc_fail(int code, const std::string& msg) {
+  g_noalloc_err = msg;
+  return code;
+}
+
+// One-time set-up on the current device: device address of the array and the dynamic
+// shared-memory attribute of the evaluation kernels.
+int noalloc_setup(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return noalloc_fail(PEPS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return noalloc_fail(PEPS_EINVAL, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return noalloc_fail(PEPS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    e = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             NOALLOC_SMEM_MAX);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               NOALLOC_SMEM_MAX);
+    if (e != cudaSuccess)
+      return noalloc_fail(PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+    g_noalloc_addr[dev] = (unsigned char*)ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return PEPS_OK;
+}
+
+}  // namespace
+
+extern "C" int peps_eval_batch_noalloc(const peps_params* P, const double* theta,
+                                       const uint8_t* S, int nb, double* log_abs, int8_t* sign,
+                                       double* e_sys, double* e_anc, void* O, void* stream) {
+  g_noalloc_err.clear();
+  if (!P || nb < 0 || (nb > 0 && (!theta || !S)))
+    return noalloc_fail(PEPS_EINVAL, "eval_batch_noalloc: null argument or nb < 0");
+  if (P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
+      P->chi < 1 || P->chi > 64 || P->model != PEPS_MODEL_J1J2 ||
+      (P->precision != PEPS_FP64 && P->precision != PEPS_FP32))
+    return noalloc_fail(PEPS_EINVAL, "eval_batch_noalloc: problem outside the library limits");
+  unsigned char* base = nullptr;
+  int rc = noalloc_setup(&base);
+  if (rc != PEPS_OK) return rc;
+  if (nb == 0) return PEPS_OK;
+  const bool f64 = P->precision == PEPS_FP64;
+  const long long real = f64 ? 8 : 4;
+  const int N = P->L1 * P->L2;
+  long long Np = 0, No = 0;
+  for (int i = 0; i < N; ++i) {
+    int r = i / P->L2, c = i % P->L2;
+    long long sz = (long long)(c == 0 ? 1 : P->D) * (c == P->L2 - 1 ? 1 : P->D) *
+                   (r == 0 ? 1 : P->D) * (r == P->L1 - 1 ? 1 : P->D);
+    Np += 4 * sz;
+    No += sz;
+  }
+  ScratchDims sd = scratch_dims(P->L1, P->L2, P->D, P->chi);
+  const long long sreal = (sd.n_real + 31) & ~31LL, sint = (sd.n_int + 31) & ~31LL;
+  const long long off_tab = 256;
+  const long long off_thf = align_up(off_tab + 2LL * (N + 1) * 8, 256);
+  const long long off_blk = align_up(off_thf + (f64 ? 0 : Np * 4), 256);
+  const long long per_block = align_up(sreal * real, 256) + align_up(sint * 4, 256);
+  const long long avail = (long long)PEPS_NOALLOC_SCRATCH_BYTES - off_blk;
+  if (avail < per_block)
+    return noalloc_fail(PEPS_EINVAL,
+                        "eval_batch_noalloc: one block needs " + std::to_string(off_blk + per_block) +
+                            " bytes of work space, above PEPS_NOALLOC_SCRATCH_BYTES = " +
+                            std::to_string((long long)PEPS_NOALLOC_SCRATCH_BYTES));
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  long long nblk = std::min<long long>(avail / per_block, (long long)sms * 4);
+  nblk = std::min<long long>(nblk, nb);
+  unsigned char* rbase = base + off_blk;
+  int* ibase = (int*)(rbase + nblk * align_up(sreal * real, 256));
+  cudaStream_t st = (cudaStream_t)stream;
+  long long* toff = (long long*)(base + off_tab);
+  long long* ooff = toff + (N + 1);
+  // counters start at zero on every call
+  cudaError_t e = cudaMemsetAsync(base, 0, 256, st);
+  if (e != cudaSuccess) return noalloc_fail(PEPS_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  k_noalloc_tables<<<1, 32, 0, st>>>(P->L1, P->L2, P->D, toff, ooff);
+  Geom g;
+  g.L1 = P->L1;
+  g.L2 = P->L2;
+  g.D = P->D;
+  g.chi = P->chi;
+  g.J1 = P->J1;
+  g.J2 = P->J2;
+  g.theta_off = toff;
+  g.o_off = ooff;
+  long long cD = (long long)P->chi * P->D;
+  long long need = cD * (cD + 1) * 2 * real;
+  int smem = need <= NOALLOC_SMEM_MAX ? (int)need : 0;
+  double* flops = (double*)base;
+  unsigned long long* jsw = (unsigned long long*)(base + 8);
+  long long rstride = align_up(sreal * real, 256) / real;   // elements between blocks
+  long long istride = align_up(sint * 4, 256) / 4;
+  if (f64) {
+    k_eval<double, double><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
+        g, theta, S, nb, (double*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
+        (double*)O, No, JTOL_F64, JAC_MAX_SWEEPS, flops, jsw, smem);
+  } else {
+    float* thf = (float*)(base + off_thf);
+    k_to_real<float><<<grid_for(Np, 256), 256, 0, st>>>(Np, theta, thf);
+    k_eval<float, float><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
+        g, thf, S, nb, (float*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
+        (float*)O, No, JTOL_F32, JAC_MAX_SWEEPS, flops, jsw, smem);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return noalloc_fail(PEPS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+  return PEPS_OK;
+}

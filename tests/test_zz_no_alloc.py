@@ -1,0 +1,74 @@
+"""The allocation-free evaluation entry point (peps_eval_batch_noalloc) gives the same
+results as the regular evaluation, through the C ABI, on two calls in a row.
+
+Some callers cannot allocate GPU memory (a host framework that owns the device memory pool,
+a plug-in called during CUDA-graph capture, a process with a fixed memory budget); this
+entry point serves them from a fixed device array inside the library.  This file is named
+so that pytest collects it last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2409_05285_gb300 import binding
+from paper_2409_05285_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _noalloc(params, theta_d, S_d, outs, stream=None):
+    lib = binding.load()
+    la, sg, es, ea, O = outs
+    p = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    return lib.peps_eval_batch_noalloc(ctypes.byref(params), p(theta_d), p(S_d), int(S_d.shape[0]),
+                                       p(la), p(sg), p(es), p(ea), p(O), stream)
+
+
+@pytest.mark.parametrize("prec", [binding.PEPS_FP64, binding.PEPS_FP32])
+def test_noalloc_matches_eval_batch_twice(prec):
+    torch = pytest.importorskip("torch")
+    from paper_2409_05285_gb300.build import build
+    build()
+    L1, L2, D, chi, J2, nb = 4, 5, 3, 5, 0.4, 23
+    ref = binding.Context(L1, L2, D, chi, 4, J1=1.0, J2=J2, precision=prec, seed=1)
+    th = wl.random_theta(L1, L2, D, seed=3, scale=0.3, diag_bias=1.0)
+    ref.set_theta(th)
+    dev = torch.device("cuda:0")
+    theta_d = torch.from_numpy(th).to(dev)
+    odt = torch.float64 if prec == binding.PEPS_FP64 else torch.float32
+    tol = 1e-10 if prec == binding.PEPS_FP64 else 2e-4
+    for call, seed in enumerate((7, 8)):   # two calls in a row, different batches
+        S = wl.random_configs(L1, L2, nb, seed=seed)
+        la0, sg0, es0, ea0, O0 = ref.eval_batch(S)
+        S_d = torch.from_numpy(S).to(dev)
+        outs = (torch.empty(nb, dtype=torch.float64, device=dev),
+                torch.empty(nb, dtype=torch.int8, device=dev),
+                torch.empty(nb, dtype=torch.float64, device=dev),
+                torch.empty(nb, dtype=torch.float64, device=dev),
+                torch.empty((nb, ref.No), dtype=odt, device=dev))
+        rc = _noalloc(ref.params, theta_d, S_d, outs)
+        torch.cuda.synchronize()
+        assert rc == binding.PEPS_OK, binding.load().peps_last_error(None)
+        la, sg, es, ea, O = (t.cpu().numpy() for t in outs)
+        assert np.array_equal(sg, sg0), call
+        assert np.max(np.abs(la - la0)) <= tol, call
+        scale = max(1.0, np.max(np.abs(es0)), np.max(np.abs(ea0)))
+        assert np.max(np.abs(es - es0)) <= tol * scale and np.max(np.abs(ea - ea0)) <= tol * scale
+        oscale = max(1.0, float(np.max(np.abs(O0))))
+        assert np.max(np.abs(O.astype(np.float64) - O0.astype(np.float64))) <= tol * 10 * oscale
+    ref.close()
+
+
+def test_noalloc_rejects_problem_above_its_work_space():
+    torch = pytest.importorskip("torch")
+    lib = binding.load()
+    big = binding.Params(L1=16, L2=16, model=0, J1=1.0, J2=0.0, D=8, chi=64, n_chains=1,
+                         precision=binding.PEPS_FP64, init_noise=0.0, seed=0, n_blocks=0)
+    dev = torch.device("cuda:0")
+    th = torch.zeros(16, dtype=torch.float64, device=dev)
+    S = torch.zeros((1, 256), dtype=torch.uint8, device=dev)
+    rc = lib.peps_eval_batch_noalloc(ctypes.byref(big), ctypes.c_void_p(th.data_ptr()),
+                                     ctypes.c_void_p(S.data_ptr()), 1, None, None, None, None,
+                                     None, None)
+    assert rc == binding.PEPS_EINVAL
+    assert b"PEPS_NOALLOC_SCRATCH_BYTES" in lib.peps_last_error(None)
