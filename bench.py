@@ -125,7 +125,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     n = args.chains or wl.n_samples
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
-                          init_noise=wl.init_noise, seed=wl.seed + rank,
+                          init_noise=wl.init_noise, seed=wl.seed + rank, n_blocks=args.blocks,
                           stream=ctypes_stream(stream))
     ctx.mc_sweep(args.burn, p=1)
     t0 = cooled_state(ctx, args.precool, wl.tau, 0.3)
@@ -192,6 +192,9 @@ def run_ours(args):
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
     e2e_step = statistics.median(e2e_ms)
 
+    fp64_check = None
+    if prec == binding.PEPS_FP32 and not args.no_fp64_check:
+        fp64_check = compare_fp64(ctx, wl, binding, min(n, args.fp64_chains), stream, torch)
     peaks = measured_peaks()
     dom_flops = statistics.mean(eval_flops)
     dom_ms = statistics.mean(eval_ms)
@@ -234,6 +237,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(ctx.Np * 8 + n * ctx.N)},
         "gpu_launches": None,
         "clocks": clk,
+        "fp64_check": fp64_check,
     }
     # kernel launches per step: 1 k_mc + 1 k_eval + SR (weights, colsum x2, dot, init, dot,
     # 6 per CG iteration, update) -- the CUDA kernels of this library
@@ -245,6 +249,38 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def compare_fp64(ctx, wl, binding, m, stream, torch):
+    """The FP32 path against the FP64 path on the same parameters and the same m chain
+    configurations: amplitude and local-energy differences, and the evaluation throughput
+    of both paths on those configurations."""
+    import numpy as np
+    th = ctx.get_theta()
+    S = np.ascontiguousarray(ctx.get_configs()[:m])
+    ref = binding.Context(wl.L, wl.L, wl.D, wl.chi, m, J1=wl.J1, J2=wl.J2,
+                          precision=binding.PEPS_FP64, seed=wl.seed,
+                          stream=ctypes_stream(stream))
+    ref.set_theta(th)
+    out = {}
+    for name, c in (("fp32", ctx), ("fp64", ref)):
+        c.eval_batch(S[: min(m, 8)], with_O=False)   # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        la, sg, es, ea, _ = c.eval_batch(S, with_O=True)
+        torch.cuda.synchronize()
+        out[name] = (la, sg, es + ea, m / (time.perf_counter() - t0))
+    ref.close()
+    la32, sg32, e32, r32 = out["fp32"]
+    la64, sg64, e64, r64 = out["fp64"]
+    N = wl.L * wl.L
+    return {"chains": m, "max_abs_dlog_amp": float(np.max(np.abs(la32 - la64))),
+            "sign_mismatch": int(np.sum(sg32 != sg64)),
+            "E_site_fp32": float(np.mean(e32) / (2 * N)), "E_site_fp64": float(np.mean(e64) / (2 * N)),
+            "dE_site": float(abs(np.mean(e32) - np.mean(e64)) / (2 * N)),
+            "max_dEloc_site": float(np.max(np.abs(e32 - e64)) / (2 * N)),
+            "eval_samples_per_s_fp32": r32, "eval_samples_per_s_fp64": r64,
+            "speedup_fp32_over_fp64": r32 / r64}
 
 
 def ctypes_stream(stream):
@@ -342,10 +378,13 @@ def main():
     ap.add_argument("--workload", default="heis8")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--chains", type=int, default=0)
+    ap.add_argument("--blocks", type=int, default=0, help="persistent blocks of the sample kernels (0 = auto)")
     ap.add_argument("--burn", type=int, default=2)
     ap.add_argument("--precool", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--fp64-chains", type=int, default=608)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

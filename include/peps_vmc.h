@@ -72,7 +72,17 @@ typedef struct {
   double init_noise; /* amplitude a of the U[-a, a] perturbation of the zero entries */
   uint64_t seed;     /* Philox key for the perturbation, the chain starts and Metropolis */
   int n_blocks;      /* persistent blocks of the sample kernels; 0 = automatic */
+  int block_mode;    /* PEPS_BLOCKS_AUTO | PEPS_BLOCKS_NARROW | PEPS_BLOCKS_WIDE */
 } peps_params;
+
+/* Thread-block layout of the per-sample kernels.  Narrow: 256 threads, four blocks per SM,
+ * work buffers in global memory (Jacobi matrices in shared memory).  Wide: 1024 threads,
+ * one block per SM, every short-lived buffer in shared memory (PEPS_EINVAL when they do
+ * not fit in 220 KB).  Automatic picks narrow blocks (faster on GB300 for the workloads
+ * measured).  Results are identical in both layouts. */
+#define PEPS_BLOCKS_AUTO 0
+#define PEPS_BLOCKS_NARROW 1
+#define PEPS_BLOCKS_WIDE 2
 
 /* Results of one step (observables of Eq. 11, C_v, Eq. 13 at beta_obs = 4 t). */
 typedef struct {
@@ -163,7 +173,8 @@ int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
  * at start-up.  The paper has no counterpart; this is a library convenience.
  *
  * Same results as peps_eval_batch on device pointers (the same kernel runs), for the
- * problem in *params (n_chains, seed, init_noise and n_blocks are ignored): theta (float64
+ * problem in *params (n_chains, seed, init_noise, n_blocks and block_mode are ignored; the
+ * narrow block layout is used): theta (float64
  * [N_p]), S (uint8 [nb][L1*L2]) and every non-null output are DEVICE pointers owned by the
  * caller.  The per-block work space comes from one file-scope device array of
  * PEPS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until the process

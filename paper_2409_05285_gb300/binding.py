@@ -23,6 +23,9 @@ PEPS_EIO = -7
 PEPS_FP64 = 0
 PEPS_FP32 = 1
 PEPS_MODEL_J1J2 = 0
+PEPS_BLOCKS_AUTO = 0
+PEPS_BLOCKS_NARROW = 1
+PEPS_BLOCKS_WIDE = 2
 
 EXPORTS = [
     "peps_init", "peps_mc_sweep", "peps_eval_batch", "peps_sr_step", "peps_observables",
@@ -38,7 +41,7 @@ class Params(ctypes.Structure):
                 ("J1", ctypes.c_double), ("J2", ctypes.c_double), ("D", ctypes.c_int),
                 ("chi", ctypes.c_int), ("n_chains", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init_noise", ctypes.c_double), ("seed", ctypes.c_uint64),
-                ("n_blocks", ctypes.c_int)]
+                ("n_blocks", ctypes.c_int), ("block_mode", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -116,11 +119,11 @@ class Context:
     """One cooling run: PEPS parameters, Markov chains and work buffers on the GPU."""
 
     def __init__(self, L1, L2, D, chi, n_chains, J1=1.0, J2=0.0, precision=PEPS_FP64,
-                 init_noise=1e-3, seed=0, n_blocks=0, stream=None):
+                 init_noise=1e-3, seed=0, n_blocks=0, stream=None, block_mode=PEPS_BLOCKS_AUTO):
         self.lib = load()
         self.params = Params(L1=L1, L2=L2, model=PEPS_MODEL_J1J2, J1=J1, J2=J2, D=D, chi=chi,
                              n_chains=n_chains, precision=precision, init_noise=init_noise,
-                             seed=seed, n_blocks=n_blocks)
+                             seed=seed, n_blocks=n_blocks, block_mode=block_mode)
         self.ctx = ctypes.c_void_p()
         rc = self.lib.peps_init(ctypes.byref(self.params), stream, ctypes.byref(self.ctx))
         if rc != PEPS_OK:

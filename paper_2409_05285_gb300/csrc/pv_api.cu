@@ -17,7 +17,9 @@ using namespace pv;
 
 namespace {
 
-constexpr int SAMPLE_THREADS = 256;
+constexpr int SAMPLE_THREADS = 256;   // narrow blocks
+constexpr int WIDE_THREADS = 1024;    // wide blocks (temporaries in shared memory)
+constexpr int WIDE_SMEM_MAX = 220 * 1024;
 constexpr double JTOL_F64 = 1e-15;
 constexpr float JTOL_F32 = 2e-7f;
 constexpr int JAC_MAX_SWEEPS = 60;
@@ -76,9 +78,11 @@ __device__ void flush_counters(Shared<T>& sh, double* flops, unsigned long long*
   }
 }
 
-// Persistent evaluation kernel: block b handles samples b, b + grid, ...
-template <typename T, typename OT>
-__global__ void __launch_bounds__(SAMPLE_THREADS, 4)
+// Persistent evaluation kernel: block b handles samples b, b + grid, ...  WIDE blocks
+// (1024 threads, one per SM) keep every short-lived buffer in shared memory; narrow
+// blocks (256 threads, four per SM) keep only the Jacobi matrices there.
+template <typename T, typename OT, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_eval(Geom g, const T* __restrict__ theta, const uint8_t* __restrict__ S, int n,
            T* scratch, int* iscratch, long long sreal, long long sint,
            double* __restrict__ log_abs, int8_t* __restrict__ sign, double* __restrict__ es,
@@ -89,8 +93,12 @@ __global__ void __launch_bounds__(SAMPLE_THREADS, 4)
   Scratch<T> sc;
   sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
           g.L1, g.L2, g.D, g.chi);
-  sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
-  sc.smem_cap = smem_bytes / (int)sizeof(T);
+  if (THREADS == WIDE_THREADS) {
+    sc.bind_shared((T*)dyn_smem, g.D, g.chi);
+  } else {
+    sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
+    sc.smem_cap = smem_bytes / (int)sizeof(T);
+  }
   init_shared(sh);
   const int N = g.N();
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -109,8 +117,8 @@ __global__ void __launch_bounds__(SAMPLE_THREADS, 4)
   flush_counters(sh, flops, jsw);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(SAMPLE_THREADS, 4)
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_mc(Geom g, const T* __restrict__ theta, uint8_t* __restrict__ S, int n, T* scratch,
          int* iscratch, long long sreal, long long sint, int p, uint64_t seed, long long sweep0,
          int n_sweeps, int* __restrict__ acc, int* __restrict__ prop, T jtol, int max_sweeps,
@@ -120,8 +128,12 @@ __global__ void __launch_bounds__(SAMPLE_THREADS, 4)
   Scratch<T> sc;
   sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
           g.L1, g.L2, g.D, g.chi);
-  sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
-  sc.smem_cap = smem_bytes / (int)sizeof(T);
+  if (THREADS == WIDE_THREADS) {
+    sc.bind_shared((T*)dyn_smem, g.D, g.chi);
+  } else {
+    sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
+    sc.smem_cap = smem_bytes / (int)sizeof(T);
+  }
   init_shared(sh);
   const int N = g.N();
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -190,7 +202,8 @@ struct peps_ctx {
   int* d_iscr = nullptr;
   int nblk = 0;
   long long sreal = 0, sint = 0;
-  int smem_bytes = 0;   // dynamic shared memory of the sample kernels (Jacobi work matrices)
+  int smem_bytes = 0;   // dynamic shared memory of the sample kernels
+  bool wide = false;    // 1024-thread blocks with every short-lived buffer in shared memory
   double* d_flops = nullptr;
   unsigned long long* d_jsw = nullptr;
   int *d_acc = nullptr, *d_prop = nullptr;
@@ -277,15 +290,19 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
   PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
   int grid = std::min(c->nblk, nb);
+#define PV_EVAL_LAUNCH(T, TH, THETA)                                                         \
+  k_eval<T, T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                  \
+      g, THETA, dS, nb, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea, (T*)O, \
+      c->No, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw,   \
+      c->smem_bytes)
   if (fp64(c)) {
-    k_eval<double, double><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
-        g, c->d_theta, dS, nb, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
-        (double*)O, c->No, JTOL_F64, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes);
+    if (c->wide) PV_EVAL_LAUNCH(double, WIDE_THREADS, c->d_theta);
+    else PV_EVAL_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
   } else {
-    k_eval<float, float><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
-        g, c->d_theta_f, dS, nb, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea,
-        (float*)O, c->No, JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes);
+    if (c->wide) PV_EVAL_LAUNCH(float, WIDE_THREADS, c->d_theta_f);
+    else PV_EVAL_LAUNCH(float, SAMPLE_THREADS, c->d_theta_f);
   }
+#undef PV_EVAL_LAUNCH
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
 }
@@ -315,7 +332,7 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   if (P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
       P->chi < 1 || P->chi > 64 || P->n_chains < 1 || P->model != PEPS_MODEL_J1J2 ||
       (P->precision != PEPS_FP64 && P->precision != PEPS_FP32) || P->n_blocks < 0 ||
-      !(P->init_noise >= 0))
+      !(P->init_noise >= 0) || P->block_mode < PEPS_BLOCKS_AUTO || P->block_mode > PEPS_BLOCKS_WIDE)
     return PEPS_EINVAL;
   peps_ctx* c = new peps_ctx();
   c->P = *P;
@@ -368,26 +385,36 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   c->sreal = (sd.n_real + 31) & ~31LL;
   c->sint = (sd.n_int + 31) & ~31LL;
   {
-    // Jacobi work matrices in shared memory when both fit in 96 KB
     long long cD = (long long)P->chi * P->D;
-    long long need = cD * (cD + 1) * 2 * (long long)real;
-    c->smem_bytes = need <= 96 * 1024 ? (int)need : 0;
+    long long wide_bytes = Scratch<double>::shared_elems(P->D, P->chi) * (long long)real;
+    long long jac_bytes = cD * (cD + 1) * 2 * (long long)real;
+    ScratchDims sd0 = scratch_dims(1, 1, P->D, P->chi);
+    bool fits = wide_bytes <= WIDE_SMEM_MAX;
+    if (P->block_mode == PEPS_BLOCKS_WIDE && !fits) return bail(fail(c, PEPS_EINVAL, "wide blocks: buffers exceed shared memory"));
+    // Measured on GB300 (8x8, D=4, chi=16, float32): four narrow blocks per SM keep four
+    // samples in flight and beat one wide block by 2x, so automatic picks narrow blocks.
+    (void)sd0;
+    c->wide = P->block_mode == PEPS_BLOCKS_WIDE;
+    c->smem_bytes = c->wide ? (int)wide_bytes : (jac_bytes <= 96 * 1024 ? (int)jac_bytes : 0);
+    cudaError_t ea = cudaSuccess;
     if (c->smem_bytes > 48 * 1024) {
-      cudaError_t ea;
-      if (fp64(c)) {
-        ea = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+      if (c->wide) {
+        ea = fp64(c) ? cudaFuncSetAttribute(k_eval<double, double, WIDE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, WIDE_SMEM_MAX)
+                     : cudaFuncSetAttribute(k_eval<float, float, WIDE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, WIDE_SMEM_MAX);
+        if (ea == cudaSuccess)
+          ea = fp64(c) ? cudaFuncSetAttribute(k_mc<double, WIDE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, WIDE_SMEM_MAX)
+                       : cudaFuncSetAttribute(k_mc<float, WIDE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, WIDE_SMEM_MAX);
       } else {
-        ea = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-        if (ea == cudaSuccess) ea = cudaFuncSetAttribute(k_mc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-      }
-      if (ea != cudaSuccess) {
-        cudaGetLastError();
-        c->smem_bytes = 0;
+        ea = fp64(c) ? cudaFuncSetAttribute(k_eval<double, double, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)
+                     : cudaFuncSetAttribute(k_eval<float, float, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+        if (ea == cudaSuccess)
+          ea = fp64(c) ? cudaFuncSetAttribute(k_mc<double, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)
+                       : cudaFuncSetAttribute(k_mc<float, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
       }
     }
+    if (ea != cudaSuccess) return bail(fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea)));
   }
-  int want = P->n_blocks > 0 ? P->n_blocks : sms * 4;
+  int want = P->n_blocks > 0 ? P->n_blocks : (c->wide ? sms : sms * 4);
   c->nblk = std::max(1, std::min(want, n));
   if ((rc = dalloc(c, &c->d_scr, (size_t)c->nblk * c->sreal * real))) return bail(rc);
   if ((rc = dalloc(c, &c->d_iscr, (size_t)c->nblk * c->sint * sizeof(int)))) return bail(rc);
@@ -484,17 +511,19 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
   int grid = std::min(c->nblk, n);
+#define PV_MC_LAUNCH(T, TH, THETA)                                                            \
+  k_mc<T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                        \
+      g, THETA, c->d_S, n, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, p, c->P.seed,          \
+      c->sweeps, n_sweeps, c->d_acc, c->d_prop, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32,          \
+      JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes)
   if (fp64(c)) {
-    k_mc<double><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
-        g, c->d_theta, c->d_S, n, (double*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
-        c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F64, JAC_MAX_SWEEPS,
-        c->d_flops, c->d_jsw, c->smem_bytes);
+    if (c->wide) PV_MC_LAUNCH(double, WIDE_THREADS, c->d_theta);
+    else PV_MC_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
   } else {
-    k_mc<float><<<grid, SAMPLE_THREADS, c->smem_bytes, c->stream>>>(
-        g, c->d_theta_f, c->d_S, n, (float*)c->d_scr, c->d_iscr, c->sreal, c->sint, p,
-        c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop, JTOL_F32, JAC_MAX_SWEEPS,
-        c->d_flops, c->d_jsw, c->smem_bytes);
+    if (c->wide) PV_MC_LAUNCH(float, WIDE_THREADS, c->d_theta_f);
+    else PV_MC_LAUNCH(float, SAMPLE_THREADS, c->d_theta_f);
   }
+#undef PV_MC_LAUNCH
   PV_CUDA(c, cudaGetLastError());
   c->sweeps += n_sweeps;
   c->have_eval = false;
@@ -845,10 +874,10 @@ int noalloc_setup(unsigned char** out) {
     e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
     if (e != cudaSuccess)
       return noalloc_fail(PEPS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    e = cudaFuncSetAttribute(k_eval<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_eval<double, double, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              NOALLOC_SMEM_MAX);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_eval<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_eval<float, float, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                NOALLOC_SMEM_MAX);
     if (e != cudaSuccess)
       return noalloc_fail(PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -928,13 +957,13 @@ extern "C" int peps_eval_batch_noalloc(const peps_params* P, const double* theta
   long long rstride = align_up(sreal * real, 256) / real;   // elements between blocks
   long long istride = align_up(sint * 4, 256) / 4;
   if (f64) {
-    k_eval<double, double><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
+    k_eval<double, double, SAMPLE_THREADS><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
         g, theta, S, nb, (double*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
         (double*)O, No, JTOL_F64, JAC_MAX_SWEEPS, flops, jsw, smem);
   } else {
     float* thf = (float*)(base + off_thf);
     k_to_real<float><<<grid_for(Np, 256), 256, 0, st>>>(Np, theta, thf);
-    k_eval<float, float><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
+    k_eval<float, float, SAMPLE_THREADS><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
         g, thf, S, nb, (float*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
         (float*)O, No, JTOL_F32, JAC_MAX_SWEEPS, flops, jsw, smem);
   }

@@ -207,6 +207,65 @@ PV_HDN void contract(T* out, const TA* A, const TB* B, const Spec& s) {
   }
   const int total = (int)s.total;
   const int K0 = ks[0], a0 = ak[0], b0 = bk[0];
+  // Register blocking: when the last (merged) output dimension is a multiple of 4, each
+  // thread computes 4 consecutive outputs along it, sharing the index arithmetic and the
+  // operand loads that do not depend on that dimension.
+  const int nlast = no > 0 ? os[no - 1] : 1;
+  if (no > 0 && (nlast & 3) == 0 && total >= 4 * PV_NTHR / 2) {
+    const int la = ao[no - 1], lb = bo[no - 1];
+    const int quads = total >> 2;
+    for (int qd = PV_TID; qd < quads; qd += PV_NTHR) {
+      int idx = qd << 2;
+      int rem = idx, oa = 0, ob = 0;
+      for (int d = no - 1; d >= 0; --d) {
+        int q = rem / os[d];
+        int i = rem - q * os[d];
+        rem = q;
+        oa += i * ao[d];
+        ob += i * bo[d];
+      }
+      T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+      for (int k2 = 0; k2 < ks[2]; ++k2)
+        for (int k1 = 0; k1 < ks[1]; ++k1) {
+          const TA* pa = A + oa + k1 * ak[1] + k2 * ak[2];
+          const TB* pb = B + ob + k1 * bk[1] + k2 * bk[2];
+          if (la == 0) {
+            for (int k0 = 0; k0 < K0; ++k0) {
+              T av = (T)pa[k0 * a0];
+              const TB* q = pb + k0 * b0;
+              c0 += av * (T)q[0];
+              c1 += av * (T)q[lb];
+              c2 += av * (T)q[2 * lb];
+              c3 += av * (T)q[3 * lb];
+            }
+          } else if (lb == 0) {
+            for (int k0 = 0; k0 < K0; ++k0) {
+              T bv = (T)pb[k0 * b0];
+              const TA* q = pa + k0 * a0;
+              c0 += (T)q[0] * bv;
+              c1 += (T)q[la] * bv;
+              c2 += (T)q[2 * la] * bv;
+              c3 += (T)q[3 * la] * bv;
+            }
+          } else {
+            for (int k0 = 0; k0 < K0; ++k0) {
+              const TA* qa = pa + k0 * a0;
+              const TB* qb = pb + k0 * b0;
+              c0 += (T)qa[0] * (T)qb[0];
+              c1 += (T)qa[la] * (T)qb[lb];
+              c2 += (T)qa[2 * la] * (T)qb[2 * lb];
+              c3 += (T)qa[3 * la] * (T)qb[3 * lb];
+            }
+          }
+        }
+      out[idx] = c0;
+      out[idx + 1] = c1;
+      out[idx + 2] = c2;
+      out[idx + 3] = c3;
+    }
+    PV_SYNC();
+    return;
+  }
   for (int idx = PV_TID; idx < total; idx += PV_NTHR) {
     int rem = idx, oa = 0, ob = 0;
     for (int d = no - 1; d >= 0; --d) {

@@ -59,7 +59,7 @@ PV_HD ScratchDims scratch_dims(int L1, int L2, int D, int chi) {
   s.TMP = (long long)chi * chi * D * D * D;
   s.n_real = (long long)(L1 + 1) * L2 * s.ENV   // down envs
              + 2LL * L2 * s.ENV                 // up envs (ping-pong)
-             + (long long)L2 * s.CB             // product MPS
+             + s.CB                             // one site of the product MPS
              + (long long)(L2 + 1) * s.LB       // right factors
              + s.CB                             // Householder work
              + s.CB                             // carry * C_c
@@ -69,8 +69,9 @@ PV_HD ScratchDims scratch_dims(int L1, int L2, int D, int chi) {
              + cD                               // singular values
              + 2LL * (L2 + 1) * s.P1            // one-row partials
              + 2LL * (L2 + 1) * s.P2            // two-row partials
-             + 3 * s.TMP                        // temporaries
-             + 2 * s.P2;                        // modified partials
+             + 2 * s.TMP                        // temporaries (ping-pong)
+             + 4 * s.P2                         // modified / cached partials
+             + (long long)D * D * D * D;        // site environment
   s.n_int = (long long)(L1 + 1) * (L2 + 1) + 2LL * (L2 + 1) + (L2 + 1) + (L2 + 1) + cD;
   return s;
 }
@@ -78,11 +79,49 @@ PV_HD ScratchDims scratch_dims(int L1, int L2, int D, int chi) {
 template <typename T>
 struct Scratch {
   ScratchDims d;
-  T *envD, *envU[2], *C, *Lf, *W, *Am, *Y, *V, *Uk, *carry, *sig;
-  T *p1L, *p1R, *p2L, *p2R, *t0, *t1, *t2, *m0, *m1;
+  T *envD, *envU[2], *Cs, *Lf, *W, *Am, *Y, *V, *Uk, *carry, *sig;
+  T *p1L, *p1R, *p2L, *p2R, *t0, *t1, *m0, *m1, *m2, *m3, *envo;
   int *bondD, *bondU[2], *bondC, *kf, *order;
   T* smem = nullptr;        // optional fast buffer for the Jacobi matrices
   long long smem_cap = 0;   // its capacity in elements
+
+  // Elements of shared memory that hold every short-lived buffer (bind_shared).
+  PV_HD static long long shared_elems(int D, int chi) {
+    ScratchDims q = scratch_dims(1, 1, D, chi);
+    long long cD = (long long)chi * D;
+    long long jac = 2 * cD * (cD + 1);
+    return 2 * q.TMP + 4 * q.P2 + (long long)D * D * D * D + (jac <= q.TMP ? 0 : jac);
+  }
+
+  // Places the temporaries, the partial buffers, the one-site product MPS, the
+  // Householder work matrix, carry, kept vectors and the Jacobi matrices in shared
+  // memory.  Buffers that are never live at the same time share space: W and the Jacobi
+  // matrices (step (i) vs step (ii) of the truncation), Cs and t1, Am and m0/m1, carry/Uk
+  // and m2/m3.
+  PV_HD void bind_shared(T* sm, int D, int chi) {
+    long long cD = (long long)chi * D;
+    T* q = sm;
+    t0 = q; q += d.TMP;
+    t1 = q; q += d.TMP;
+    m0 = q; q += d.P2;
+    m1 = q; q += d.P2;
+    m2 = q; q += d.P2;
+    m3 = q; q += d.P2;
+    envo = q; q += (long long)D * D * D * D;
+    W = t0;
+    Cs = t1;
+    Am = m0;      // Am: chi*D*cD <= 2 * P2
+    carry = m2;   // chi*cD <= P2
+    Uk = m3;
+    long long jac = 2 * cD * (cD + 1);
+    if (jac <= d.TMP) {
+      smem = t0;
+      smem_cap = d.TMP;
+    } else {
+      smem = q;
+      smem_cap = jac;
+    }
+  }
 
   PV_HD void bind(T* base, int* ibase, int L1, int L2, int D, int chi) {
     d = scratch_dims(L1, L2, D, chi);
@@ -91,7 +130,7 @@ struct Scratch {
     envD = p; p += (long long)(L1 + 1) * L2 * d.ENV;
     envU[0] = p; p += (long long)L2 * d.ENV;
     envU[1] = p; p += (long long)L2 * d.ENV;
-    C = p; p += (long long)L2 * d.CB;
+    Cs = p; p += d.CB;
     Lf = p; p += (long long)(L2 + 1) * d.LB;
     W = p; p += d.CB;
     Am = p; p += d.CB;
@@ -106,9 +145,11 @@ struct Scratch {
     p2R = p; p += (long long)(L2 + 1) * d.P2;
     t0 = p; p += d.TMP;
     t1 = p; p += d.TMP;
-    t2 = p; p += d.TMP;
     m0 = p; p += d.P2;
     m1 = p; p += d.P2;
+    m2 = p; p += d.P2;
+    m3 = p; p += d.P2;
+    envo = p; p += (long long)D * D * D * D;
     int* q = ibase;
     bondD = q; q += (L1 + 1) * (L2 + 1);
     bondU[0] = q; q += L2 + 1;
@@ -141,38 +182,55 @@ PV_HD const TT* site_tensor(const Geom& g, const TT* theta, int r, int c, int S)
 
 // ---------------------------------------------------------------- environments
 
-// Row r absorbed into an environment.  down: env below row r (phys = dd(r)); the result
-// has phys du(r).  up: env above row r (phys = du(r)); result phys dd(r).
+// Site c of row r absorbed into an environment, into Cout.  down: env below row r
+// (phys = dd(r)); the result has phys du(r).  up: env above row r (phys = du(r)); result
+// phys dd(r).  Bond (a, l) of the product is fused as a*dl + l.
 template <typename T, typename TT>
-PV_HDN double absorb_row(const Geom& g, Scratch<T>& sc, const T* env, const int* bond, bool down,
-                        int r, const TT* theta, const unsigned char* S) {
-  double fl = 0;
-  for (int c = 0; c < g.L2; ++c) {
-    const TT* A = site_tensor(g, theta, r, c, S[r * g.L2 + c]);
-    Dims dm;
-    dm.set('a', bond[c]).set('b', bond[c + 1]).set('l', g.dl(c)).set('r', g.dr(c));
-    dm.set('u', g.du(r)).set('d', g.dd(r));
-    const T* E = env + (long long)c * sc.d.ENV;
-    T* Cc = sc.C + (long long)c * sc.d.CB;
-    if (down)
-      fl += einsum(Cc, "alubr", E, "adb", A, "lrud", dm);
-    else
-      fl += einsum(Cc, "aldbr", E, "aub", A, "lrud", dm);
-    if (PV_TID == 0) sc.bondC[c] = bond[c] * g.dl(c);
-  }
-  if (PV_TID == 0) sc.bondC[g.L2] = 1;
-  PV_SYNC();
-  return fl;
+PV_HDN double absorb_site(const Geom& g, Scratch<T>& sc, const T* env, const int* bond, bool down,
+                          int r, int c, const TT* theta, const unsigned char* S, T* Cout) {
+  const TT* A = site_tensor(g, theta, r, c, S[r * g.L2 + c]);
+  Dims dm;
+  dm.set('a', bond[c]).set('b', bond[c + 1]).set('l', g.dl(c)).set('r', g.dr(c));
+  dm.set('u', g.du(r)).set('d', g.dd(r));
+  const T* E = env + (long long)c * sc.d.ENV;
+  if (down) return einsum(Cout, "alubr", E, "adb", A, "lrud", dm);
+  return einsum(Cout, "aldbr", E, "aub", A, "lrud", dm);
 }
 
-// Compresses the product MPS in sc.C (bonds sc.bondC, phys p) into `out` (bonds
-// out_bond), normalising and accumulating the log-scale into *ls (thread 0 writes).
+// Bonds of the product MPS of `bond` and row r (bond c fused with the row's left leg).
 template <typename T>
-PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* out,
-                      int* out_bond, double* ls, T jtol, int max_sweeps) {
+PV_HD void product_bonds(const Geom& g, Scratch<T>& sc, const int* bond) {
+  if (PV_TID == 0) {
+    for (int c = 0; c < g.L2; ++c) sc.bondC[c] = bond[c] * g.dl(c);
+    sc.bondC[g.L2] = 1;
+  }
+  PV_SYNC();
+}
+
+// Product MPS producer: the environment and row whose product is compressed.
+template <typename T, typename TT>
+struct Product {
+  const T* env;
+  const int* bond;
+  bool down;
+  int r;
+  const TT* theta;
+  const unsigned char* S;
+};
+
+// Compresses the product MPS of pr (bonds sc.bondC, phys p) into `out` (bonds out_bond),
+// normalising and accumulating the log-scale into *ls (thread 0 writes).  The product is
+// formed one site at a time (into sc.Cs) when a site is needed.
+template <typename T, typename TT>
+PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, const Product<T, TT>& pr,
+                       T* out, int* out_bond, double* ls, T jtol, int max_sweeps) {
   const int n = g.L2;
   const int chi = g.chi;
   double fl = 0;
+  product_bonds(g, sc, pr.bond);
+  auto site = [&](int c) {
+    fl += absorb_site(g, sc, pr.env, pr.bond, pr.down, pr.r, c, pr.theta, pr.S, sc.Cs);
+  };
   int maxb = 0;
   for (int c = 0; c <= n; ++c) maxb = sc.bondC[c] > maxb ? sc.bondC[c] : maxb;
   double lsum = 0;
@@ -180,7 +238,7 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
     for (int c = 0; c < n; ++c) {
       long long len = (long long)sc.bondC[c] * p * sc.bondC[c + 1];
       T* o = out + (long long)c * sc.d.ENV;
-      copy(o, sc.C + (long long)c * sc.d.CB, len);
+      fl += absorb_site(g, sc, pr.env, pr.bond, pr.down, pr.r, c, pr.theta, pr.S, o);
       lsum += normalize_maxabs(o, len, sh.red);
     }
     if (PV_TID == 0) {
@@ -199,8 +257,8 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
   for (int c = n - 1; c >= 1; --c) {
     Dims dm;
     dm.set('a', sc.bondC[c]).set('p', p).set('b', sc.bondC[c + 1]).set('k', sc.kf[c + 1]);
-    fl += einsum(sc.W, "apk", sc.C + (long long)c * sc.d.CB, "apb",
-                 sc.Lf + (long long)(c + 1) * sc.d.LB, "bk", dm);
+    site(c);
+    fl += einsum(sc.W, "apk", sc.Cs, "apb", sc.Lf + (long long)(c + 1) * sc.d.LB, "bk", dm);
     int m = sc.bondC[c], nn = p * sc.kf[c + 1];
     fl += lq_factor(sc.Lf + (long long)c * sc.d.LB, sc.W, m, nn, sh.red, sh.red);
     if (PV_TID == 0) sc.kf[c] = m < nn ? m : nn;
@@ -217,7 +275,8 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
     int a = sc.bondC[c], b = sc.bondC[c + 1], k = sc.kf[c + 1];
     Dims dm;
     dm.set('x', bprev).set('a', a).set('p', p).set('b', b);
-    fl += einsum(sc.Am, "xpb", sc.carry, "xa", sc.C + (long long)c * sc.d.CB, "apb", dm);
+    site(c);
+    fl += einsum(sc.Am, "xpb", sc.carry, "xa", sc.Cs, "apb", dm);
     int m = bprev * p;
     Dims dq;
     dq.set('q', m).set('b', b).set('k', k);
@@ -276,6 +335,16 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
     PV_SYNC();
     int kmax = m < k ? m : k;
     int kk = chi < kmax ? chi : kmax;
+    // Columns below the rounding floor of the Jacobi (norm^2 <= (eps len)^2 |X|^2) were not
+    // orthogonalised; they are zero singular values and give zero vectors, never
+    // normalised noise (which would not be orthogonal to the kept directions).
+    T zero2 = 0;
+    if (tall) {
+      T nf2 = 0;
+      for (int j = 0; j < nc; ++j) nf2 += sc.sig[j] * sc.sig[j];
+      const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+      zero2 = (eps * len) * (eps * len) * nf2;
+    }
     // kept left singular vectors Uk[q][j']
     for (long long idx = PV_TID; idx < (long long)m * kk; idx += PV_NTHR) {
       int q = (int)(idx / kk), jp = (int)(idx % kk);
@@ -283,7 +352,7 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
       T v;
       if (tall) {
         T s = sc.sig[j];
-        v = s > (T)0 ? Yw[(long long)j * ldy + q] / s : (T)0;
+        v = s * s > zero2 ? Yw[(long long)j * ldy + q] / s : (T)0;
       } else {
         v = Vw[(long long)j * ldv + q];
       }
@@ -305,7 +374,8 @@ PV_HDN double compress(const Geom& g, Scratch<T>& sc, Shared<T>& sh, int p, T* o
     Dims dm;
     dm.set('x', bprev).set('a', sc.bondC[c]).set('p', p).set('b', sc.bondC[c + 1]);
     T* o = out + (long long)c * sc.d.ENV;
-    fl += einsum(o, "xpb", sc.carry, "xa", sc.C + (long long)c * sc.d.CB, "apb", dm);
+    site(c);
+    fl += einsum(o, "xpb", sc.carry, "xa", sc.Cs, "apb", dm);
     lsum += normalize_maxabs(o, (long long)bprev * p * sc.bondC[c + 1], sh.red);
     if (PV_TID == 0) {
       out_bond[n] = 1;
@@ -363,7 +433,7 @@ PV_HDN double s1_right(const Geom& g, Scratch<T>& sc, const Strip1& st, int c, T
   return fl;
 }
 
-// Env[l,r,u,d] = sum L[a,l,b] U[a,u,x] Dn[b,d,y] R[x,r,y]  (into sc.t2)
+// Env[l,r,u,d] = sum L[a,l,b] U[a,u,x] Dn[b,d,y] R[x,r,y]  (into sc.envo)
 template <typename T>
 PV_HDN double s1_env(const Geom& g, Scratch<T>& sc, const Strip1& st, int c, const T* L,
                     const T* R) {
@@ -374,7 +444,7 @@ PV_HDN double s1_env(const Geom& g, Scratch<T>& sc, const Strip1& st, int c, con
   const T* Dn = (const T*)st.Dn + (long long)c * sc.d.ENV;
   double fl = einsum(sc.t0, "lbux", L, "alb", U, "aux", dm);
   fl += einsum(sc.t1, "lbury", sc.t0, "lbux", R, "xry", dm);
-  fl += einsum(sc.t2, "lrud", sc.t1, "lbury", Dn, "bdy", dm);
+  fl += einsum(sc.envo, "lrud", sc.t1, "lbury", Dn, "bdy", dm);
   return fl;
 }
 
@@ -406,8 +476,8 @@ PV_HDN double s2_left(const Geom& g, Scratch<T>& sc, const Strip2& st, int c, T*
   const T* Dn = (const T*)st.Dn + (long long)c * sc.d.ENV;
   double fl = einsum(sc.t0, "ijbux", Lin, "aijb", U, "aux", dm);
   fl += einsum(sc.t1, "jbxrm", sc.t0, "ijbux", A1, "irum", dm);
-  fl += einsum(sc.t2, "bxrsd", sc.t1, "jbxrm", A2, "jsmd", dm);
-  fl += einsum(Lout, "xrsy", sc.t2, "bxrsd", Dn, "bdy", dm);
+  fl += einsum(sc.t0, "bxrsd", sc.t1, "jbxrm", A2, "jsmd", dm);
+  fl += einsum(Lout, "xrsy", sc.t0, "bxrsd", Dn, "bdy", dm);
   return fl;
 }
 
@@ -423,8 +493,8 @@ PV_HDN double s2_right(const Geom& g, Scratch<T>& sc, const Strip2& st, int c, T
   const T* Dn = (const T*)st.Dn + (long long)c * sc.d.ENV;
   double fl = einsum(sc.t0, "bdxrs", Dn, "bdy", Rin, "xrsy", dm);
   fl += einsum(sc.t1, "jmbxr", A2, "jsmd", sc.t0, "bdxrs", dm);
-  fl += einsum(sc.t2, "iujbx", A1, "irum", sc.t1, "jmbxr", dm);
-  fl += einsum(Rout, "aijb", U, "aux", sc.t2, "iujbx", dm);
+  fl += einsum(sc.t0, "iujbx", A1, "irum", sc.t1, "jmbxr", dm);
+  fl += einsum(Rout, "aijb", U, "aux", sc.t0, "iujbx", dm);
   return fl;
 }
 
@@ -461,10 +531,10 @@ PV_HDN double build_down(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT*
   for (int r = g.L1 - 1; r >= 1; --r) {
     T* envN = sc.envD + (long long)(r + 1) * g.L2 * sc.d.ENV;
     int* bN = sc.bondD + (r + 1) * (g.L2 + 1);
-    fl += absorb_row(g, sc, envN, bN, true, r, theta, sh.S);
     if (PV_TID == 0) sh.lsD[r] = sh.lsD[r + 1];
     PV_SYNC();
-    fl += compress(g, sc, sh, g.du(r), sc.envD + (long long)r * g.L2 * sc.d.ENV,
+    Product<T, TT> pr{envN, bN, true, r, theta, sh.S};
+    fl += compress(g, sc, sh, g.du(r), pr, sc.envD + (long long)r * g.L2 * sc.d.ENV,
                    sc.bondD + r * (g.L2 + 1), &sh.lsD[r], jtol, max_sweeps);
   }
   return fl;
@@ -522,7 +592,7 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
         long long n = g.sz(r, c);
         OT* o = O + g.o_off[r * L2 + c];
         double inv = 1.0 / (double)val;
-        for (long long k = PV_TID; k < n; k += PV_NTHR) o[k] = (OT)((double)sc.t2[k] * inv);
+        for (long long k = PV_TID; k < n; k += PV_NTHR) o[k] = (OT)((double)sc.envo[k] * inv);
         PV_SYNC();
       }
     }
@@ -647,10 +717,10 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
       }
       // absorb row r into the up environment
       int nxt = cur ^ 1;
-      fl += absorb_row(g, sc, sc.envU[cur], sc.bondU[cur], false, r, theta, S);
       if (PV_TID == 0) sh.lsU[nxt] = sh.lsU[cur];
       PV_SYNC();
-      fl += compress(g, sc, sh, g.dd(r), sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
+      Product<T, TT> pr{sc.envU[cur], sc.bondU[cur], false, r, theta, S};
+      fl += compress(g, sc, sh, g.dd(r), pr, sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
                      max_sweeps);
       cur = nxt;
     }
@@ -667,11 +737,14 @@ PV_HD bool mc_accept(double u, double ratio, int p) {
 }
 
 // One Metropolis sweep of one chain (configuration in sh.S, updated in place).
-// Move m at site i has counter (chain, sweep, 8 i + m, TAG_MC).
+// Move m at site i has counter (chain, sweep, 8 i + m, TAG_MC).  The strip value of the
+// current configuration (the ratio's denominator) and the advanced left partial are kept
+// between proposals: they are the same contractions of the same operands, so reusing them
+// changes no value.
 template <typename T, typename TT>
 PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* theta, int p,
-                    uint64_t seed, uint32_t chain, uint32_t sweep, T jtol, int max_sweeps,
-                    int* n_acc, int* n_prop) {
+                     uint64_t seed, uint32_t chain, uint32_t sweep, T jtol, int max_sweeps,
+                     int* n_acc, int* n_prop) {
   double fl = build_down(g, sc, sh, theta, jtol, max_sweeps);
   const int L2 = g.L2;
   unsigned char* S = sh.S;
@@ -680,6 +753,17 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
   if (PV_TID == 0) sh.lsU[cur] = 0;
   PV_SYNC();
   int acc = 0, prop = 0;
+  auto take = [&](bool accepted, int i, int Si2, int j, int Sj2) {
+    if (accepted) {
+      ++acc;
+      PV_SYNC();
+      if (PV_TID == 0) {
+        S[i] = (unsigned char)Si2;
+        if (j >= 0) S[j] = (unsigned char)Sj2;
+      }
+      PV_SYNC();
+    }
+  };
   for (int r = 0; r < g.L1; ++r) {
     Strip1 st{sc.envU[cur], sc.bondU[cur], down_env(g, sc, r + 1), down_bond(g, sc, r + 1), r};
     if (PV_TID == 0) {
@@ -691,27 +775,34 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
       fl += s1_right(g, sc, st, c, sc.p1R + (long long)c * sc.d.P1,
                      sc.p1R + (long long)(c + 1) * sc.d.P1,
                      site_tensor(g, theta, r, c, S[r * L2 + c]));
-    T* Lc = sc.p1L;   // running left partial (slot 0 / 1 alternate)
+    // Lc: left partial up to column c; P = Lc x column c (current S); Q = P x column c+1.
+    T* Lc = sc.p1L;
+    T* P = sc.m0;
+    T* Q = sc.m1;
+    T* X = sc.m2;
+    T* Y = sc.m3;
+    fl += s1_left(g, sc, st, 0, P, Lc, site_tensor(g, theta, r, 0, S[r * L2]));
     for (int c = 0; c < L2; ++c) {
       int i = r * L2 + c;
       const T* R1 = sc.p1R + (long long)(c + 1) * sc.d.P1;
       long long n1 = s1_len<T>(st, g, c + 1);
       // move 0: both-flip of site i
       {
-        fl += s1_left(g, sc, st, c, sc.m0, Lc, site_tensor(g, theta, r, c, S[i]));
-        T den = dot(sc.m0, R1, n1, sh.red);
-        fl += s1_left(g, sc, st, c, sc.m1, Lc, site_tensor(g, theta, r, c, 3 - S[i]));
-        T num = dot(sc.m1, R1, n1, sh.red);
+        T den = dot(P, R1, n1, sh.red);
+        fl += s1_left(g, sc, st, c, X, Lc, site_tensor(g, theta, r, c, 3 - S[i]));
+        T num = dot(X, R1, n1, sh.red);
         double u = philox_uniform(seed, chain, sweep, (uint32_t)(8 * i + 0), TAG_MC);
         ++prop;
-        if (mc_accept(u, (double)num / (double)den, p)) {
-          ++acc;
-          PV_SYNC();
-          if (PV_TID == 0) S[i] = (unsigned char)(3 - S[i]);
-          PV_SYNC();
+        bool a = mc_accept(u, (double)num / (double)den, p);
+        take(a, i, 3 - S[i], -1, 0);
+        if (a) {
+          T* t = P;
+          P = X;
+          X = t;
         }
       }
       // moves 1, 2: system / ancilla exchange with (r, c+1)
+      bool q_valid = false;   // Q == P x column c+1 at the current S
       if (c + 1 < L2) {
         const T* R2 = sc.p1R + (long long)(c + 2) * sc.d.P1;
         long long n2 = s1_len<T>(st, g, c + 2);
@@ -728,29 +819,41 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
             Si2 = 2 * si + aj;
             Sj2 = 2 * sj + ai;
           }
-          fl += s1_left(g, sc, st, c, sc.m0, Lc, site_tensor(g, theta, r, c, S[i]));
-          fl += s1_left(g, sc, st, c + 1, sc.m1, sc.m0, site_tensor(g, theta, r, c + 1, S[j]));
-          T den = dot(sc.m1, R2, n2, sh.red);
-          fl += s1_left(g, sc, st, c, sc.m0, Lc, site_tensor(g, theta, r, c, Si2));
-          fl += s1_left(g, sc, st, c + 1, sc.m1, sc.m0, site_tensor(g, theta, r, c + 1, Sj2));
-          T num = dot(sc.m1, R2, n2, sh.red);
+          if (!q_valid) {
+            fl += s1_left(g, sc, st, c + 1, Q, P, site_tensor(g, theta, r, c + 1, S[j]));
+            q_valid = true;
+          }
+          T den = dot(Q, R2, n2, sh.red);
+          fl += s1_left(g, sc, st, c, X, Lc, site_tensor(g, theta, r, c, Si2));
+          fl += s1_left(g, sc, st, c + 1, Y, X, site_tensor(g, theta, r, c + 1, Sj2));
+          T num = dot(Y, R2, n2, sh.red);
           double u = philox_uniform(seed, chain, sweep, (uint32_t)(8 * i + 1 + layer), TAG_MC);
           ++prop;
-          if (mc_accept(u, (double)num / (double)den, p)) {
-            ++acc;
-            PV_SYNC();
-            if (PV_TID == 0) {
-              S[i] = (unsigned char)Si2;
-              S[j] = (unsigned char)Sj2;
-            }
-            PV_SYNC();
+          bool a = mc_accept(u, (double)num / (double)den, p);
+          take(a, i, Si2, j, Sj2);
+          if (a) {
+            T* t = P;
+            P = X;
+            X = t;
+            t = Q;
+            Q = Y;
+            Y = t;
           }
         }
       }
-      // advance the left partial past column c (final S)
+      // advance: the left partial past column c is P
       T* Ln = (Lc == sc.p1L) ? sc.p1L + sc.d.P1 : sc.p1L;
-      fl += s1_left(g, sc, st, c, Ln, Lc, site_tensor(g, theta, r, c, S[i]));
+      copy(Ln, P, s1_len<T>(st, g, c + 1));
       Lc = Ln;
+      if (c + 1 < L2) {
+        if (q_valid) {
+          T* t = P;
+          P = Q;
+          Q = t;
+        } else {
+          fl += s1_left(g, sc, st, c + 1, P, Lc, site_tensor(g, theta, r, c + 1, S[i + 1]));
+        }
+      }
     }
     if (r + 1 < g.L1) {
       Strip2 s2{sc.envU[cur], sc.bondU[cur], down_env(g, sc, r + 2), down_bond(g, sc, r + 2), r};
@@ -765,10 +868,16 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
                        site_tensor(g, theta, r, c, S[r * L2 + c]),
                        site_tensor(g, theta, r + 1, c, S[(r + 1) * L2 + c]));
       T* L2c = sc.p2L;
+      T* P2 = sc.m0;
+      T* X2 = sc.m1;
       for (int c = 0; c < L2; ++c) {
         int i = r * L2 + c, j = i + L2;
         const T* R = sc.p2R + (long long)(c + 1) * sc.d.P2;
         long long n = s2_len<T>(s2, g, c + 1);
+        fl += s2_left(g, sc, s2, c, P2, L2c, site_tensor(g, theta, r, c, S[i]),
+                      site_tensor(g, theta, r + 1, c, S[j]));
+        T den = 0;
+        bool den_valid = false;
         for (int layer = 0; layer < 2; ++layer) {
           int si = S[i] >> 1, sj = S[j] >> 1, ai = S[i] & 1, aj = S[j] & 1;
           int Si2, Sj2;
@@ -781,34 +890,33 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
             Si2 = 2 * si + aj;
             Sj2 = 2 * sj + ai;
           }
-          fl += s2_left(g, sc, s2, c, sc.m0, L2c, site_tensor(g, theta, r, c, S[i]),
-                        site_tensor(g, theta, r + 1, c, S[j]));
-          T den = dot(sc.m0, R, n, sh.red);
-          fl += s2_left(g, sc, s2, c, sc.m1, L2c, site_tensor(g, theta, r, c, Si2),
+          if (!den_valid) {
+            den = dot(P2, R, n, sh.red);
+            den_valid = true;
+          }
+          fl += s2_left(g, sc, s2, c, X2, L2c, site_tensor(g, theta, r, c, Si2),
                         site_tensor(g, theta, r + 1, c, Sj2));
-          T num = dot(sc.m1, R, n, sh.red);
+          T num = dot(X2, R, n, sh.red);
           double u = philox_uniform(seed, chain, sweep, (uint32_t)(8 * i + 3 + layer), TAG_MC);
           ++prop;
-          if (mc_accept(u, (double)num / (double)den, p)) {
-            ++acc;
-            PV_SYNC();
-            if (PV_TID == 0) {
-              S[i] = (unsigned char)Si2;
-              S[j] = (unsigned char)Sj2;
-            }
-            PV_SYNC();
+          bool a = mc_accept(u, (double)num / (double)den, p);
+          take(a, i, Si2, j, Sj2);
+          if (a) {
+            T* t = P2;
+            P2 = X2;
+            X2 = t;
+            den = num;
           }
         }
         T* Ln = (L2c == sc.p2L) ? sc.p2L + sc.d.P2 : sc.p2L;
-        fl += s2_left(g, sc, s2, c, Ln, L2c, site_tensor(g, theta, r, c, S[i]),
-                      site_tensor(g, theta, r + 1, c, S[j]));
+        copy(Ln, P2, s2_len<T>(s2, g, c + 1));
         L2c = Ln;
       }
       int nxt = cur ^ 1;
-      fl += absorb_row(g, sc, sc.envU[cur], sc.bondU[cur], false, r, theta, S);
       if (PV_TID == 0) sh.lsU[nxt] = sh.lsU[cur];
       PV_SYNC();
-      fl += compress(g, sc, sh, g.dd(r), sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
+      Product<T, TT> pr{sc.envU[cur], sc.bondU[cur], false, r, theta, S};
+      fl += compress(g, sc, sh, g.dd(r), pr, sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
                      max_sweeps);
       cur = nxt;
     }

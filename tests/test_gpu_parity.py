@@ -18,9 +18,10 @@ def _built():
     build()
 
 
-def _ctx(L1, L2, D, chi, n, J2=0.0, prec=binding.PEPS_FP64, seed=0, noise=1e-3, n_blocks=0):
+def _ctx(L1, L2, D, chi, n, J2=0.0, prec=binding.PEPS_FP64, seed=0, noise=1e-3, n_blocks=0,
+         mode=binding.PEPS_BLOCKS_AUTO):
     return binding.Context(L1, L2, D, chi, n, J1=1.0, J2=J2, precision=prec, init_noise=noise,
-                           seed=seed, n_blocks=n_blocks)
+                           seed=seed, n_blocks=n_blocks, block_mode=mode)
 
 
 def _compare_eval(lat, th, S, chi, got, tol_la, tol_e, tol_o):
@@ -45,13 +46,17 @@ CASES = [  # (L1, L2, D, chi, J2, n): exact chi, truncated chi, ragged tails, NN
 ]
 
 
+MODES = [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_WIDE]
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("case", CASES)
-def test_eval_fp64_matches_oracle(case):
+def test_eval_fp64_matches_oracle(case, mode):
     L1, L2, D, chi, J2, n = case
     lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
     th = wl.random_theta(L1, L2, D, seed=L1 * 10 + L2, scale=0.3, diag_bias=1.0)
     S = wl.random_configs(L1, L2, n, seed=D)
-    ctx = _ctx(L1, L2, D, chi, n, J2=J2, n_blocks=3)
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2, n_blocks=3, mode=mode)
     ctx.set_theta(th)
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-9)
 
@@ -62,19 +67,33 @@ def test_eval_fp64_heis8_shape():
     lat = Lattice(L, L, D)
     th = wl.random_theta(L, L, D, seed=81, scale=0.2, diag_bias=1.0)
     S = wl.random_configs(L, L, 3, seed=82)
-    ctx = _ctx(L, L, D, chi, 3)
+    ctx = _ctx(L, L, D, chi, 3, mode=binding.PEPS_BLOCKS_NARROW)
     ctx.set_theta(th)
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-8)
 
 
-def test_eval_fp32_matches_oracle():
+@pytest.mark.parametrize("mode", MODES)
+def test_eval_fp32_matches_oracle(mode):
     L1, L2, D, chi, J2 = 4, 4, 3, 4, 0.5
     lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
     th = wl.random_theta(L1, L2, D, seed=5, scale=0.3, diag_bias=1.0)
     S = wl.random_configs(L1, L2, 6, seed=6)
-    ctx = _ctx(L1, L2, D, chi, 6, J2=J2, prec=binding.PEPS_FP32)
+    ctx = _ctx(L1, L2, D, chi, 6, J2=J2, prec=binding.PEPS_FP32, mode=mode)
     ctx.set_theta(th)
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 2e-4, 2e-4, 2e-3)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_eval_fp32_heis8_near_product_state(mode):
+    # The bench workload's sizes in both block layouts, on a state near the beta=0 product
+    # state (most singular values of the truncation below the float32 rounding floor).
+    L, D, chi = 8, 4, 16
+    lat = Lattice(L, L, D)
+    th = wl.random_theta(L, L, D, seed=83, scale=0.05, diag_bias=1.0)
+    S = wl.random_configs(L, L, 4, seed=84)
+    ctx = _ctx(L, L, D, chi, 4, prec=binding.PEPS_FP32, mode=mode)
+    ctx.set_theta(th)
+    _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-3, 1e-3, 5e-3)
 
 
 def test_init_matches_oracle_bit_exact():
@@ -86,14 +105,15 @@ def test_init_matches_oracle_bit_exact():
     assert ctx.Np == lat.Np and ctx.No == lat.No
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("p", [2, 1])
-def test_mc_sweep_matches_oracle(p):
+def test_mc_sweep_matches_oracle(p, mode):
     L1, L2, D, chi, J2, n = 4, 4, 2, 4, 0.3, 16
     lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
     th = wl.random_theta(L1, L2, D, seed=7, scale=0.4, diag_bias=1.0)
     S0 = wl.random_configs(L1, L2, n, seed=8, diagonal_fraction=0.7)
     seed = 99
-    ctx = _ctx(L1, L2, D, chi, n, J2=J2, seed=seed, n_blocks=5)
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2, seed=seed, n_blocks=5, mode=mode)
     ctx.set_theta(th)
     ctx.set_configs(S0)
     ctx.sweeps_done = 3
