@@ -87,7 +87,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
            T* scratch, int* iscratch, long long sreal, long long sint,
            double* __restrict__ log_abs, int8_t* __restrict__ sign, double* __restrict__ es,
            double* __restrict__ ea, OT* __restrict__ O, long long No, T jtol, int max_sweeps,
-           double* flops, unsigned long long* jsw, int smem_bytes) {
+           double* flops, unsigned long long* jsw, int smem_bytes, T* ucache, int* ubond,
+           long long ustride, long long ubstride) {
   __shared__ Shared<T> sh;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Scratch<T> sc;
@@ -104,8 +105,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     for (int j = threadIdx.x; j < N; j += blockDim.x) sh.S[j] = S[(long long)s * N + j];
     __syncthreads();
+    UCache<T> uc{ucache ? ucache + (long long)s * ustride : nullptr,
+                 ucache ? ubond + (long long)s * ubstride : nullptr};
     SampleOut r = eval_sample<T, T, OT>(g, sc, sh, theta, O ? O + (long long)s * No : nullptr,
-                                        jtol, max_sweeps);
+                                        jtol, max_sweeps, uc);
     if (threadIdx.x == 0) {
       if (log_abs) log_abs[s] = r.log_abs;
       if (sign) sign[s] = (int8_t)r.sign;
@@ -122,7 +125,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_mc(Geom g, const T* __restrict__ theta, uint8_t* __restrict__ S, int n, T* scratch,
          int* iscratch, long long sreal, long long sint, int p, uint64_t seed, long long sweep0,
          int n_sweeps, int* __restrict__ acc, int* __restrict__ prop, T jtol, int max_sweeps,
-         double* flops, unsigned long long* jsw, int smem_bytes) {
+         double* flops, unsigned long long* jsw, int smem_bytes, T* ucache, int* ubond,
+         long long ustride, long long ubstride) {
   __shared__ Shared<T> sh;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   Scratch<T> sc;
@@ -142,8 +146,13 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     int a_tot = 0, p_tot = 0;
     for (int k = 0; k < n_sweeps; ++k) {
       int a = 0, pr = 0;
+      UCache<T> uc{nullptr, nullptr};
+      if (ucache && k == n_sweeps - 1) {   // keep the environments of the final configuration
+        uc.env = ucache + (long long)s * ustride;
+        uc.bond = ubond + (long long)s * ubstride;
+      }
       mc_sweep<T, T>(g, sc, sh, theta, p, seed, (uint32_t)s, (uint32_t)(sweep0 + k), jtol,
-                     max_sweeps, &a, &pr);
+                     max_sweeps, &a, &pr, uc);
       a_tot += a;
       p_tot += pr;
     }
@@ -204,6 +213,11 @@ struct peps_ctx {
   long long sreal = 0, sint = 0;
   int smem_bytes = 0;   // dynamic shared memory of the sample kernels
   bool wide = false;    // 1024-thread blocks with every short-lived buffer in shared memory
+  // up environments of the chains' final configurations, written by the sweep
+  void* d_ucache = nullptr;
+  int* d_ubond = nullptr;
+  long long ustride = 0, ubstride = 0;
+  bool ucache_valid = false;
   double* d_flops = nullptr;
   unsigned long long* d_jsw = nullptr;
   int *d_acc = nullptr, *d_prop = nullptr;
@@ -285,7 +299,8 @@ int ensure_batch(peps_ctx* c, int nb) {
 
 // Launches the evaluation kernel on device buffers.
 int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, double* es,
-                double* ea, void* O) {
+                double* ea, void* O, bool use_cache = false) {
+  void* ucache = use_cache ? c->d_ucache : nullptr;
   Geom g = make_geom(c);
   PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
@@ -294,7 +309,7 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
   k_eval<T, T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                  \
       g, THETA, dS, nb, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea, (T*)O, \
       c->No, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw,   \
-      c->smem_bytes)
+      c->smem_bytes, (T*)ucache, c->d_ubond, c->ustride, c->ubstride)
   if (fp64(c)) {
     if (c->wide) PV_EVAL_LAUNCH(double, WIDE_THREADS, c->d_theta);
     else PV_EVAL_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
@@ -418,6 +433,18 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   c->nblk = std::max(1, std::min(want, n));
   if ((rc = dalloc(c, &c->d_scr, (size_t)c->nblk * c->sreal * real))) return bail(rc);
   if ((rc = dalloc(c, &c->d_iscr, (size_t)c->nblk * c->sint * sizeof(int)))) return bail(rc);
+  {
+    // up-environment cache: used when it takes at most a quarter of the free memory
+    c->ustride = (long long)P->L1 * P->L2 * sd.ENV;
+    c->ubstride = (long long)P->L1 * (P->L2 + 1);
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    size_t need = (size_t)n * (c->ustride * real + c->ubstride * sizeof(int));
+    if (need <= fr / 4) {
+      if ((rc = dalloc(c, &c->d_ucache, (size_t)n * c->ustride * real))) return bail(rc);
+      if ((rc = dalloc(c, &c->d_ubond, (size_t)n * c->ubstride * sizeof(int)))) return bail(rc);
+    }
+  }
   // SR buffers
   c->nch = (n + OTV_CHUNK - 1) / OTV_CHUNK;
   c->nvb = grid_for(c->Np, SR_THREADS, 1024);
@@ -483,6 +510,7 @@ int peps_set_theta(peps_ctx* c, const double* host, size_t n) {
   PV_CUDA(c, cudaGetLastError());
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_eval = false;
+  c->ucache_valid = false;
   return PEPS_OK;
 }
 
@@ -500,6 +528,7 @@ int peps_set_configs(peps_ctx* c, const uint8_t* host, size_t n) {
   PV_CUDA(c, cudaMemcpyAsync(c->d_S, host, n, cudaMemcpyHostToDevice, c->stream));
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_eval = false;
+  c->ucache_valid = false;
   return PEPS_OK;
 }
 
@@ -515,7 +544,8 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   k_mc<T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                        \
       g, THETA, c->d_S, n, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, p, c->P.seed,          \
       c->sweeps, n_sweeps, c->d_acc, c->d_prop, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32,          \
-      JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes)
+      JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes, (T*)c->d_ucache, c->d_ubond,       \
+      c->ustride, c->ubstride)
   if (fp64(c)) {
     if (c->wide) PV_MC_LAUNCH(double, WIDE_THREADS, c->d_theta);
     else PV_MC_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
@@ -527,6 +557,7 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   PV_CUDA(c, cudaGetLastError());
   c->sweeps += n_sweeps;
   c->have_eval = false;
+  c->ucache_valid = c->d_ucache != nullptr;
   std::vector<int> a(n), b(n);
   PV_CUDA(c, cudaMemcpyAsync(a.data(), c->d_acc, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PV_CUDA(c, cudaMemcpyAsync(b.data(), c->d_prop, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -546,7 +577,8 @@ int peps_eval_batch(peps_ctx* c, const uint8_t* S, int nb, int on_device, double
   size_t osz = fp64(c) ? sizeof(double) : sizeof(float);
   if (S == nullptr) {
     if (nb != c->P.n_chains) return fail(c, PEPS_EINVAL, "eval_batch: nb != n_chains");
-    PV_TRY(launch_eval(c, c->d_S, nb, c->d_log_abs, c->d_sign, c->d_es, c->d_ea, c->d_O));
+    PV_TRY(launch_eval(c, c->d_S, nb, c->d_log_abs, c->d_sign, c->d_es, c->d_ea, c->d_O,
+                       c->ucache_valid));
     c->have_eval = true;
     if (on_device) {
       if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, c->d_log_abs, nb * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -708,6 +740,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   PV_CUDA(c, cudaMemcpy(&h, c->d_sc, sizeof(h), cudaMemcpyDeviceToHost));
   c->t += tau;
   c->have_eval = false;
+  c->ucache_valid = false;
   if (!std::isfinite(h.rr) || !std::isfinite(h.H1))
     return fail(c, PEPS_ENOTFINITE, "sr_step: non-finite energy or residual");
   return (h.iters >= max_cg && max_cg > 0 && h.gnorm > 0 &&
@@ -959,13 +992,13 @@ extern "C" int peps_eval_batch_noalloc(const peps_params* P, const double* theta
   if (f64) {
     k_eval<double, double, SAMPLE_THREADS><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
         g, theta, S, nb, (double*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
-        (double*)O, No, JTOL_F64, JAC_MAX_SWEEPS, flops, jsw, smem);
+        (double*)O, No, JTOL_F64, JAC_MAX_SWEEPS, flops, jsw, smem, nullptr, nullptr, 0, 0);
   } else {
     float* thf = (float*)(base + off_thf);
     k_to_real<float><<<grid_for(Np, 256), 256, 0, st>>>(Np, theta, thf);
     k_eval<float, float, SAMPLE_THREADS><<<(int)nblk, SAMPLE_THREADS, smem, st>>>(
         g, thf, S, nb, (float*)rbase, ibase, rstride, istride, log_abs, sign, e_sys, e_anc,
-        (float*)O, No, JTOL_F32, JAC_MAX_SWEEPS, flops, jsw, smem);
+        (float*)O, No, JTOL_F32, JAC_MAX_SWEEPS, flops, jsw, smem, nullptr, nullptr, 0, 0);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return noalloc_fail(PEPS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -507,6 +507,23 @@ PV_HD long long s2_len(const Strip2& st, const Geom& g, int c) {
 
 // ---------------------------------------------------------------- per-sample driver
 
+// Up environments of one chain kept between the Metropolis sweep and the evaluation:
+// row boundaries 0..L1-1, tensors [L1][L2][ENV], bonds [L1][L2+1] (null when unused).
+template <typename T>
+struct UCache {
+  T* env;
+  int* bond;
+};
+
+template <typename T>
+PV_HD void ucache_store(const Geom& g, Scratch<T>& sc, UCache<T> uc, int rb, const T* env,
+                        const int* bond) {
+  if (!uc.env) return;
+  copy(uc.env + (long long)rb * g.L2 * sc.d.ENV, env, (long long)g.L2 * sc.d.ENV);
+  for (int c = PV_TID; c <= g.L2; c += PV_NTHR) uc.bond[rb * (g.L2 + 1) + c] = bond[c];
+  PV_SYNC();
+}
+
 struct SampleOut {
   double log_abs;
   int sign;
@@ -551,9 +568,11 @@ PV_HD int* down_bond(const Geom& g, Scratch<T>& sc, int r) {
 
 // Evaluation of one configuration (already in sh.S): amplitude, E_sys, E_anc and, when
 // O is non-null, the compressed O row.
+// With uc.env set, the up environments come from the cache written by the sweep that
+// produced this configuration (same contractions of the same rows: identical values).
 template <typename T, typename TT, typename OT>
 PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* theta,
-                            OT* O, T jtol, int max_sweeps) {
+                            OT* O, T jtol, int max_sweeps, UCache<T> uc) {
   SampleOut res;
   res.e_sys = res.e_anc = 0;
   double fl = build_down(g, sc, sh, theta, jtol, max_sweeps);
@@ -564,7 +583,9 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
   if (PV_TID == 0) sh.lsU[cur] = 0;
   PV_SYNC();
   for (int r = 0; r < g.L1; ++r) {
-    Strip1 st{sc.envU[cur], sc.bondU[cur], down_env(g, sc, r + 1), down_bond(g, sc, r + 1), r};
+    const T* Uenv = uc.env ? uc.env + (long long)r * L2 * sc.d.ENV : sc.envU[cur];
+    const int* Ubond = uc.env ? uc.bond + r * (L2 + 1) : sc.bondU[cur];
+    Strip1 st{Uenv, Ubond, down_env(g, sc, r + 1), down_bond(g, sc, r + 1), r};
     // left and right partials of the one-row strip
     if (PV_TID == 0) {
       sc.p1L[0] = 1;
@@ -626,7 +647,7 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
     }
     // two-row strip: vertical and next-nearest-neighbour bonds between rows r and r+1
     if (r + 1 < g.L1) {
-      Strip2 s2{sc.envU[cur], sc.bondU[cur], down_env(g, sc, r + 2), down_bond(g, sc, r + 2), r};
+      Strip2 s2{Uenv, Ubond, down_env(g, sc, r + 2), down_bond(g, sc, r + 2), r};
       if (PV_TID == 0) {
         sc.p2L[0] = 1;
         sc.p2R[(long long)L2 * sc.d.P2] = 1;
@@ -715,14 +736,16 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
           }
         }
       }
-      // absorb row r into the up environment
-      int nxt = cur ^ 1;
-      if (PV_TID == 0) sh.lsU[nxt] = sh.lsU[cur];
-      PV_SYNC();
-      Product<T, TT> pr{sc.envU[cur], sc.bondU[cur], false, r, theta, S};
-      fl += compress(g, sc, sh, g.dd(r), pr, sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
-                     max_sweeps);
-      cur = nxt;
+      // absorb row r into the up environment (unless the cache holds it)
+      if (!uc.env) {
+        int nxt = cur ^ 1;
+        if (PV_TID == 0) sh.lsU[nxt] = sh.lsU[cur];
+        PV_SYNC();
+        Product<T, TT> pr{sc.envU[cur], sc.bondU[cur], false, r, theta, S};
+        fl += compress(g, sc, sh, g.dd(r), pr, sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
+                       max_sweeps);
+        cur = nxt;
+      }
     }
   }
   if (PV_TID == 0) sh.flops += fl;
@@ -744,7 +767,7 @@ PV_HD bool mc_accept(double u, double ratio, int p) {
 template <typename T, typename TT>
 PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* theta, int p,
                      uint64_t seed, uint32_t chain, uint32_t sweep, T jtol, int max_sweeps,
-                     int* n_acc, int* n_prop) {
+                     int* n_acc, int* n_prop, UCache<T> uc) {
   double fl = build_down(g, sc, sh, theta, jtol, max_sweeps);
   const int L2 = g.L2;
   unsigned char* S = sh.S;
@@ -752,6 +775,7 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
   trivial_env(g, sc, sc.envU[cur], sc.bondU[cur]);
   if (PV_TID == 0) sh.lsU[cur] = 0;
   PV_SYNC();
+  ucache_store(g, sc, uc, 0, sc.envU[cur], sc.bondU[cur]);
   int acc = 0, prop = 0;
   auto take = [&](bool accepted, int i, int Si2, int j, int Sj2) {
     if (accepted) {
@@ -919,6 +943,7 @@ PV_HDN void mc_sweep(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const TT* the
       fl += compress(g, sc, sh, g.dd(r), pr, sc.envU[nxt], sc.bondU[nxt], &sh.lsU[nxt], jtol,
                      max_sweeps);
       cur = nxt;
+      ucache_store(g, sc, uc, r + 1, sc.envU[cur], sc.bondU[cur]);
     }
   }
   if (PV_TID == 0) sh.flops += fl;

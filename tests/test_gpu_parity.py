@@ -246,3 +246,17 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     with pytest.raises(binding.PepsError) as e:
         other.restore(ck)
     assert e.value.code == binding.PEPS_ECORRUPT
+
+
+@pytest.mark.parametrize("prec", [binding.PEPS_FP64, binding.PEPS_FP32])
+def test_eval_with_cached_up_environments_is_identical(prec):
+    # eval_chains after a sweep reuses the sweep's up environments; the values must be the
+    # same bits as an evaluation of the same configurations from scratch.
+    L1, L2, D, chi, n = 5, 4, 3, 4, 12
+    ctx = _ctx(L1, L2, D, chi, n, J2=0.5, prec=prec, seed=3, noise=0.05)
+    ctx.mc_sweep(2, p=2)
+    S = ctx.get_configs()
+    la0, sg0, es0, ea0, O0 = ctx.eval_batch(None)
+    la1, sg1, es1, ea1, O1 = ctx.eval_batch(S)
+    assert np.array_equal(la0, la1) and np.array_equal(sg0, sg1)
+    assert np.array_equal(es0, es1) and np.array_equal(ea0, ea1) and np.array_equal(O0, O1)
