@@ -369,6 +369,54 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_serve(args):
+    """Serving loop under a seeded Poisson stream of cooling requests (bounded version of the
+    mixed-request workload: arrivals at `--rate` per s over `--window` s; L in {4, 6, 8},
+    D in {2, 4}, chi = D^2, J1 = 1, J2 ~ U[0, 0.6], t_end ~ U[0.02, 0.1], 1024 chains)."""
+    import numpy as np
+    import torch
+
+    from paper_2409_05285_gb300 import binding
+    from paper_2409_05285_gb300.build import build
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    build()
+    rng = np.random.default_rng(args.seed)
+    arrivals, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / args.rate)
+        if t > args.window:
+            break
+        L = int(rng.choice([4, 6, 8]))
+        D = int(rng.choice([2, 4]))
+        arrivals.append((t, dict(L1=L, L2=L, D=D, chi=D * D, n_chains=1024,
+                                 J2=float(rng.uniform(0, 0.6)),
+                                 t_end=0.02 * int(rng.integers(1, 6)),
+                                 seed=int(rng.integers(1 << 30)))))
+    srv = binding.Server(max_active=args.max_active)
+    t0 = time.perf_counter()
+    ids = []
+    for ta, kw in arrivals:
+        d = ta - (time.perf_counter() - t0)
+        if d > 0:
+            time.sleep(d)
+        ids.append(srv.submit(precision=binding.PEPS_FP32, **kw))
+    srv.drain()
+    wall = time.perf_counter() - t0
+    m = srv.metrics()
+    srv.close()
+    out = {"metric": "serving: per-SR-step latency p50/p99 and aggregate samples/s under a "
+                     "Poisson stream of cooling requests", "value": m["samples_per_s"],
+           "unit": "samples/s", "n_gpus": 1, "latency_ms": {"p50": m["p50_ms"], "p99": m["p99_ms"]},
+           "steps": m["steps"], "requests": len(ids), "wall_s": wall, "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"Poisson arrivals {args.rate}/s over {args.window} s, seed "
+                                  f"{args.seed}; L in {{4,6,8}}, D in {{2,4}}, chi=D^2, J2~U[0,0.6], "
+                                  "t_end in {0.02..0.1}, 1024 chains, tau=0.02",
+                      "max_active": args.max_active}}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -384,11 +432,18 @@ def main():
     ap.add_argument("--cpu-samples", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--window", type=float, default=1.0)
+    ap.add_argument("--max-active", type=int, default=4)
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-chains", type=int, default=608)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

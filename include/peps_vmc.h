@@ -143,6 +143,10 @@ int peps_set_theta(peps_ctx* ctx, const double* host, size_t n);
 int peps_get_configs(peps_ctx* ctx, uint8_t* host, size_t n);
 int peps_set_configs(peps_ctx* ctx, const uint8_t* host, size_t n);
 
+/* Device bytes a context for these parameters allocates (upper bound; 0 for invalid
+ * parameters).  Used for admission by footprint. */
+size_t peps_footprint(const peps_params* params);
+
 /* Sizes: N_p, N_o, and the number of sweeps done so far (the Philox sweep counter). */
 size_t peps_num_params(const peps_ctx* ctx);
 size_t peps_o_row_len(const peps_ctx* ctx);
@@ -164,6 +168,56 @@ double peps_time(const peps_ctx* ctx);
 /* Device counters of the last peps_eval_batch / peps_mc_sweep launch: algorithmic
  * flops (contractions, Householder, Jacobi), Jacobi sweeps. */
 int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
+
+/* ---------------------------------------------------------------- serving loop
+ *
+ * Continuous batching of cooling runs.  Requests are queued by peps_srv_submit (any host
+ * thread) and admitted in arrival order while the sum of the admitted contexts'
+ * footprints stays within the budget and fewer than max_active run.  Every admitted
+ * request gets its own context and CUDA stream and a host worker that runs its steps, so
+ * the work of concurrent requests overlaps on the device; when a request finishes its
+ * memory is released and the next queued requests are admitted.  A request's results do
+ * not depend on what else runs (its own random stream, fixed reduction orders), so a
+ * request gives the same bits alone and in a mix. */
+typedef struct peps_server peps_server;
+
+typedef struct {
+  peps_params params;  /* problem; params.n_chains = samples per SR step */
+  double tau;          /* imaginary-time step */
+  double t_end;        /* run until t >= t_end (beta_obs = 4 t_end) */
+  double eps, cg_tol;  /* SR shift and CG relative tolerance */
+  int max_cg;          /* CG iteration cap */
+  int n_sweeps;        /* Metropolis sweeps per step */
+  int n_burn;          /* burn-in sweeps before the first step */
+  double p1_until_beta; /* reweighted sampling (p = 1) while beta_obs < this */
+} peps_request;
+
+#define PEPS_REQ_QUEUED 0
+#define PEPS_REQ_RUNNING 1
+#define PEPS_REQ_DONE 2
+#define PEPS_REQ_FAILED 3
+
+/* Creates a server.  hbm_budget: device bytes available to admitted requests (0 = 80% of
+ * the free memory); max_active: concurrently running requests (>= 1); blocks_per_request:
+ * persistent sample blocks per request (0 = the device's 4 x SMs divided by max_active). */
+int peps_srv_create(size_t hbm_budget, int max_active, int blocks_per_request, peps_server** out);
+/* Queues a request; *req_id receives its id.  PEPS_EINVAL for invalid parameters or a
+ * footprint above the whole budget. */
+int peps_srv_submit(peps_server* srv, const peps_request* req, int* req_id);
+/* State of a request (PEPS_REQ_*), steps done so far, and up to cap per-step statistics
+ * (observables of each step's samples, as from peps_sr_step). */
+int peps_srv_poll(peps_server* srv, int req_id, int* state, int* n_steps, peps_stats* per_step,
+                  int cap);
+/* Final parameter vector of a finished request (host buffer of N_p doubles). */
+int peps_srv_theta(peps_server* srv, int req_id, double* host, size_t n);
+/* Blocks until every submitted request has finished. */
+int peps_srv_drain(peps_server* srv);
+/* Step latency over all finished steps (ms, p50 and p99), aggregate samples/s between the
+ * first admission and the last finished step, and the number of steps measured. */
+int peps_srv_metrics(peps_server* srv, double* p50_ms, double* p99_ms, double* samples_per_s,
+                     int64_t* n_steps);
+/* Waits for running requests, then releases the server (NULL is ignored). */
+void peps_srv_free(peps_server* srv);
 
 /* Evaluation without any device allocation.
  *

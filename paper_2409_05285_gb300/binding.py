@@ -32,7 +32,9 @@ EXPORTS = [
     "peps_step", "peps_get_theta", "peps_set_theta", "peps_get_configs", "peps_set_configs",
     "peps_num_params", "peps_o_row_len", "peps_sweeps_done", "peps_set_sweeps_done",
     "peps_last_counters", "peps_free", "peps_last_error", "peps_version", "peps_checkpoint",
-    "peps_restore", "peps_time", "peps_eval_batch_noalloc",
+    "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
+    "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
+    "peps_srv_metrics", "peps_srv_free",
 ]
 
 
@@ -53,6 +55,15 @@ class Stats(ctypes.Structure):
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
+
+class Request(ctypes.Structure):
+    _fields_ = [("params", Params), ("tau", ctypes.c_double), ("t_end", ctypes.c_double),
+                ("eps", ctypes.c_double), ("cg_tol", ctypes.c_double), ("max_cg", ctypes.c_int),
+                ("n_sweeps", ctypes.c_int), ("n_burn", ctypes.c_int),
+                ("p1_until_beta", ctypes.c_double)]
+
+
+PEPS_REQ_QUEUED, PEPS_REQ_RUNNING, PEPS_REQ_DONE, PEPS_REQ_FAILED = 0, 1, 2, 3
 
 _lib = None
 
@@ -92,6 +103,18 @@ def load(path=None):
     lib.peps_time.restype = ctypes.c_double
     lib.peps_eval_batch_noalloc.argtypes = [ctypes.POINTER(Params), vp, vp, ip, vp, vp, vp, vp,
                                             vp, vp]
+    lib.peps_footprint.argtypes = [ctypes.POINTER(Params)]
+    lib.peps_footprint.restype = ctypes.c_size_t
+    lib.peps_srv_create.argtypes = [ctypes.c_size_t, ip, ip, ctypes.POINTER(vp)]
+    lib.peps_srv_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ip)]
+    lib.peps_srv_poll.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                  ctypes.POINTER(Stats), ip]
+    lib.peps_srv_theta.argtypes = [vp, ip, vp, ctypes.c_size_t]
+    lib.peps_srv_drain.argtypes = [vp]
+    lib.peps_srv_metrics.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp),
+                                     ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_int64)]
+    lib.peps_srv_free.argtypes = [vp]
+    lib.peps_srv_free.restype = None
     lib.peps_free.argtypes = [vp]
     lib.peps_free.restype = None
     lib.peps_last_error.argtypes = [vp]
@@ -244,3 +267,70 @@ class Context:
         j = ctypes.c_int64()
         self._check(self.lib.peps_last_counters(self.ctx, ctypes.byref(f), ctypes.byref(j)))
         return f.value, j.value
+
+
+class Server:
+    """Continuous-batching serving loop of cooling runs (peps_srv_*)."""
+
+    def __init__(self, hbm_budget=0, max_active=4, blocks_per_request=0):
+        self.lib = load()
+        self.srv = ctypes.c_void_p()
+        rc = self.lib.peps_srv_create(hbm_budget, max_active, blocks_per_request,
+                                      ctypes.byref(self.srv))
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_srv_create failed")
+        self.nparams = {}
+
+    def submit(self, L1, L2, D, chi, n_chains, t_end, tau=0.02, J1=1.0, J2=0.0,
+               precision=PEPS_FP64, seed=0, init_noise=1e-3, eps=1e-4, cg_tol=1e-10, max_cg=100,
+               n_sweeps=1, n_burn=2, p1_until_beta=0.3):
+        P = Params(L1=L1, L2=L2, model=PEPS_MODEL_J1J2, J1=J1, J2=J2, D=D, chi=chi,
+                   n_chains=n_chains, precision=precision, init_noise=init_noise, seed=seed,
+                   n_blocks=0, block_mode=PEPS_BLOCKS_AUTO)
+        q = Request(params=P, tau=tau, t_end=t_end, eps=eps, cg_tol=cg_tol, max_cg=max_cg,
+                    n_sweeps=n_sweeps, n_burn=n_burn, p1_until_beta=p1_until_beta)
+        rid = ctypes.c_int()
+        rc = self.lib.peps_srv_submit(self.srv, ctypes.byref(q), ctypes.byref(rid))
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_srv_submit failed")
+        from .workloads import n_params
+        self.nparams[rid.value] = n_params(L1, L2, D)
+        return rid.value
+
+    def poll(self, rid, cap=4096):
+        st, n = ctypes.c_int(), ctypes.c_int()
+        buf = (Stats * cap)()
+        rc = self.lib.peps_srv_poll(self.srv, rid, ctypes.byref(st), ctypes.byref(n), buf, cap)
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_srv_poll failed")
+        return st.value, [buf[i].as_dict() for i in range(min(n.value, cap))]
+
+    def theta(self, rid):
+        out = np.empty(self.nparams[rid], np.float64)
+        rc = self.lib.peps_srv_theta(self.srv, rid, _ptr(out), out.size)
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_srv_theta failed")
+        return out
+
+    def drain(self):
+        rc = self.lib.peps_srv_drain(self.srv)
+        if rc != PEPS_OK:
+            raise PepsError(rc, "a request failed")
+
+    def metrics(self):
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        n = ctypes.c_int64()
+        self.lib.peps_srv_metrics(self.srv, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                  ctypes.byref(n))
+        return {"p50_ms": a.value, "p99_ms": b.value, "samples_per_s": c.value, "steps": n.value}
+
+    def close(self):
+        if self.srv:
+            self.lib.peps_srv_free(self.srv)
+            self.srv = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -483,6 +483,37 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   return PEPS_OK;
 }
 
+size_t peps_footprint(const peps_params* P) {
+  if (!P || P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
+      P->chi < 1 || P->chi > 64 || P->n_chains < 1)
+    return 0;
+  const size_t real = P->precision == PEPS_FP64 ? 8 : 4;
+  const long long N = (long long)P->L1 * P->L2, n = P->n_chains;
+  long long Np = 0, No = 0;
+  for (long long i = 0; i < N; ++i) {
+    int r = (int)(i / P->L2), c = (int)(i % P->L2);
+    long long sz = (long long)(c == 0 ? 1 : P->D) * (c == P->L2 - 1 ? 1 : P->D) *
+                   (r == 0 ? 1 : P->D) * (r == P->L1 - 1 ? 1 : P->D);
+    Np += 4 * sz;
+    No += sz;
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ScratchDims sd = scratch_dims(P->L1, P->L2, P->D, P->chi);
+  long long sreal = (sd.n_real + 31) & ~31LL, sint = (sd.n_int + 31) & ~31LL;
+  long long nblk = P->n_blocks > 0 ? P->n_blocks : (P->block_mode == PEPS_BLOCKS_WIDE ? sms : 4LL * sms);
+  nblk = std::max(1LL, std::min(nblk, n));
+  long long nch = (n + OTV_CHUNK - 1) / OTV_CHUNK;
+  size_t b = 0;
+  b += 2 * (N + 1) * 8 + No * 4 + Np * 8 + (real == 4 ? Np * 4 : 0);   // tables, theta
+  b += n * N + n * (8 * 3 + 1 + 4 * 2) + (size_t)n * No * real;       // chains, outputs, O
+  b += (size_t)nblk * (sreal * real + sint * 4);                       // sample scratch
+  b += (size_t)n * ((long long)P->L1 * P->L2 * sd.ENV * real + (long long)P->L1 * (P->L2 + 1) * 4);
+  b += n * 8 * 3 + 6 * Np * 8 + (real == 4 ? Np * 4 : 0) + 2 * (size_t)nch * Np * 8;   // SR
+  return b + (1 << 20);
+}
+
 size_t peps_num_params(const peps_ctx* c) { return c ? (size_t)c->Np : 0; }
 size_t peps_o_row_len(const peps_ctx* c) { return c ? (size_t)c->No : 0; }
 int64_t peps_sweeps_done(const peps_ctx* c) { return c ? c->sweeps : 0; }
