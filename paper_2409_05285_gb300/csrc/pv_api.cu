@@ -97,6 +97,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   if (THREADS == WIDE_THREADS) {
     sc.bind_shared((T*)dyn_smem, g.D, g.chi);
   } else {
+    sc.alias_global();
     sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
     sc.smem_cap = smem_bytes / (int)sizeof(T);
   }
@@ -135,6 +136,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   if (THREADS == WIDE_THREADS) {
     sc.bind_shared((T*)dyn_smem, g.D, g.chi);
   } else {
+    sc.alias_global();
     sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
     sc.smem_cap = smem_bytes / (int)sizeof(T);
   }

@@ -230,6 +230,7 @@ PV_HDN void contract(T* out, const TA* A, const TB* B, const Spec& s) {
           const TA* pa = A + oa + k1 * ak[1] + k2 * ak[2];
           const TB* pb = B + ob + k1 * bk[1] + k2 * bk[2];
           if (la == 0) {
+#pragma unroll 4
             for (int k0 = 0; k0 < K0; ++k0) {
               T av = (T)pa[k0 * a0];
               const TB* q = pb + k0 * b0;
@@ -239,6 +240,7 @@ PV_HDN void contract(T* out, const TA* A, const TB* B, const Spec& s) {
               c3 += av * (T)q[3 * lb];
             }
           } else if (lb == 0) {
+#pragma unroll 4
             for (int k0 = 0; k0 < K0; ++k0) {
               T bv = (T)pb[k0 * b0];
               const TA* q = pa + k0 * a0;
@@ -248,6 +250,7 @@ PV_HDN void contract(T* out, const TA* A, const TB* B, const Spec& s) {
               c3 += (T)q[3 * la] * bv;
             }
           } else {
+#pragma unroll 4
             for (int k0 = 0; k0 < K0; ++k0) {
               const TA* qa = pa + k0 * a0;
               const TB* qb = pb + k0 * b0;

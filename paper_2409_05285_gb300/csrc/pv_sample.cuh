@@ -85,6 +85,17 @@ struct Scratch {
   T* smem = nullptr;        // optional fast buffer for the Jacobi matrices
   long long smem_cap = 0;   // its capacity in elements
 
+  // Narrow layout in global memory: buffers that are never live at the same time share
+  // space, so fewer distinct cache lines are touched per block (W and Cs share the
+  // temporaries, Am / carry / Uk the partial buffers).
+  PV_HD void alias_global() {
+    W = t0;
+    Cs = t1;
+    Am = m0;
+    carry = m2;
+    Uk = m3;
+  }
+
   // Elements of shared memory that hold every short-lived buffer (bind_shared).
   PV_HD static long long shared_elems(int D, int chi) {
     ScratchDims q = scratch_dims(1, 1, D, chi);
@@ -592,33 +603,30 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
       sc.p1R[(long long)L2 * sc.d.P1] = 1;
     }
     PV_SYNC();
-    for (int c = 0; c < L2; ++c)
-      fl += s1_left(g, sc, st, c, sc.p1L + (long long)(c + 1) * sc.d.P1,
-                    sc.p1L + (long long)c * sc.d.P1, site_tensor(g, theta, r, c, S[r * L2 + c]));
     for (int c = L2 - 1; c >= 0; --c)
       fl += s1_right(g, sc, st, c, sc.p1R + (long long)c * sc.d.P1,
                      sc.p1R + (long long)(c + 1) * sc.d.P1,
                      site_tensor(g, theta, r, c, S[r * L2 + c]));
-    T val = sc.p1L[(long long)L2 * sc.d.P1];
+    // the strip value is R_0 (a 1x1x1 tensor); left partials are rolled below
+    T val = sc.p1R[0];
     if (r == 0) {
       T av = val < 0 ? -val : val;
       res.log_abs = (av > 0 ? log((double)av) : -INFINITY) + sh.lsD[1];
       res.sign = val > 0 ? 1 : (val < 0 ? -1 : 0);
     }
-    // O rows of the sites of row r
-    if (O) {
-      for (int c = 0; c < L2; ++c) {
-        fl += s1_env(g, sc, st, c, sc.p1L + (long long)c * sc.d.P1,
-                     sc.p1R + (long long)(c + 1) * sc.d.P1);
+    // O rows of the sites of row r and horizontal bonds, with a rolling left partial Lc
+    T* Lc = sc.p1L;
+    T* Lnext = sc.p1L + sc.d.P1;
+    for (int c = 0; c < L2; ++c) {
+      if (O) {
+        fl += s1_env(g, sc, st, c, Lc, sc.p1R + (long long)(c + 1) * sc.d.P1);
         long long n = g.sz(r, c);
         OT* o = O + g.o_off[r * L2 + c];
         double inv = 1.0 / (double)val;
         for (long long k = PV_TID; k < n; k += PV_NTHR) o[k] = (OT)((double)sc.envo[k] * inv);
         PV_SYNC();
       }
-    }
-    // horizontal bonds of row r
-    for (int c = 0; c + 1 < L2; ++c) {
+      if (c + 1 >= L2) break;
       int i = r * L2 + c, j = i + 1;
       int si = S[i] >> 1, sj = S[j] >> 1, ai = S[i] & 1, aj = S[j] & 1;
       res.e_sys += g.J1 * sz_of<T>(si) * sz_of<T>(sj);
@@ -634,8 +642,7 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
           Si2 = 2 * si + aj;
           Sj2 = 2 * sj + ai;
         }
-        fl += s1_left(g, sc, st, c, sc.m0, sc.p1L + (long long)c * sc.d.P1,
-                      site_tensor(g, theta, r, c, Si2));
+        fl += s1_left(g, sc, st, c, sc.m0, Lc, site_tensor(g, theta, r, c, Si2));
         fl += s1_left(g, sc, st, c + 1, sc.m1, sc.m0, site_tensor(g, theta, r, c + 1, Sj2));
         T num = dot(sc.m1, sc.p1R + (long long)(c + 2) * sc.d.P1, s1_len<T>(st, g, c + 2), sh.red);
         double ratio = (double)num / (double)val;
@@ -644,6 +651,10 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
         else
           res.e_anc += 0.5 * g.J1 * ratio;
       }
+      fl += s1_left(g, sc, st, c, Lnext, Lc, site_tensor(g, theta, r, c, S[r * L2 + c]));
+      T* tmp = Lc;
+      Lc = Lnext;
+      Lnext = tmp;
     }
     // two-row strip: vertical and next-nearest-neighbour bonds between rows r and r+1
     if (r + 1 < g.L1) {
@@ -653,16 +664,14 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
         sc.p2R[(long long)L2 * sc.d.P2] = 1;
       }
       PV_SYNC();
-      for (int c = 0; c < L2; ++c)
-        fl += s2_left(g, sc, s2, c, sc.p2L + (long long)(c + 1) * sc.d.P2,
-                      sc.p2L + (long long)c * sc.d.P2, site_tensor(g, theta, r, c, S[r * L2 + c]),
-                      site_tensor(g, theta, r + 1, c, S[(r + 1) * L2 + c]));
       for (int c = L2 - 1; c >= 0; --c)
         fl += s2_right(g, sc, s2, c, sc.p2R + (long long)c * sc.d.P2,
                        sc.p2R + (long long)(c + 1) * sc.d.P2,
                        site_tensor(g, theta, r, c, S[r * L2 + c]),
                        site_tensor(g, theta, r + 1, c, S[(r + 1) * L2 + c]));
-      T val2 = sc.p2L[(long long)L2 * sc.d.P2];
+      T val2 = sc.p2R[0];
+      T* L2c = sc.p2L;              // rolling left partial of the two-row strip
+      T* L2n = sc.p2L + sc.d.P2;
       for (int c = 0; c < L2; ++c) {
         // vertical bond (r,c)-(r+1,c)
         {
@@ -681,8 +690,8 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
               Si2 = 2 * si + aj;
               Sj2 = 2 * sj + ai;
             }
-            fl += s2_left(g, sc, s2, c, sc.m0, sc.p2L + (long long)c * sc.d.P2,
-                          site_tensor(g, theta, r, c, Si2), site_tensor(g, theta, r + 1, c, Sj2));
+            fl += s2_left(g, sc, s2, c, sc.m0, L2c, site_tensor(g, theta, r, c, Si2),
+                          site_tensor(g, theta, r + 1, c, Sj2));
             T num = dot(sc.m0, sc.p2R + (long long)(c + 1) * sc.d.P2, s2_len<T>(s2, g, c + 1),
                         sh.red);
             double ratio = (double)num / (double)val2;
@@ -721,8 +730,8 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
                 s01 = Si2;
                 s10 = Sj2;
               }
-              fl += s2_left(g, sc, s2, c, sc.m0, sc.p2L + (long long)c * sc.d.P2,
-                            site_tensor(g, theta, r, c, s00), site_tensor(g, theta, r + 1, c, s10));
+              fl += s2_left(g, sc, s2, c, sc.m0, L2c, site_tensor(g, theta, r, c, s00),
+                            site_tensor(g, theta, r + 1, c, s10));
               fl += s2_left(g, sc, s2, c + 1, sc.m1, sc.m0, site_tensor(g, theta, r, c + 1, s01),
                             site_tensor(g, theta, r + 1, c + 1, s11));
               T num = dot(sc.m1, sc.p2R + (long long)(c + 2) * sc.d.P2, s2_len<T>(s2, g, c + 2),
@@ -735,6 +744,12 @@ PV_HDN SampleOut eval_sample(const Geom& g, Scratch<T>& sc, Shared<T>& sh, const
             }
           }
         }
+        // advance the left partial past column c
+        fl += s2_left(g, sc, s2, c, L2n, L2c, site_tensor(g, theta, r, c, S[r * L2 + c]),
+                      site_tensor(g, theta, r + 1, c, S[(r + 1) * L2 + c]));
+        T* t2p = L2c;
+        L2c = L2n;
+        L2n = t2p;
       }
       // absorb row r into the up environment (unless the cache holds it)
       if (!uc.env) {
