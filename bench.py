@@ -26,6 +26,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PEPS samples/s per SR cooling step (mixed vs FP64 at <=1e-3 E/site); p50/p99 step latency"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+BLOCK_MODES = {"auto": 0, "narrow": 1, "wide": 2, "batched": 3}
 # Per-SM issue rates of GB300 (sm_103): 128 FP32 FMA/clk, 2 FP64 FMA/clk; 152 SMs; 2070 MHz.
 SMS, MAX_MHZ = 152, 2070.0
 PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
@@ -126,7 +127,7 @@ def run_ours(args):
     n = args.chains or wl.n_samples
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
                           init_noise=wl.init_noise, seed=wl.seed + rank, n_blocks=args.blocks,
-                          stream=ctypes_stream(stream))
+                          stream=ctypes_stream(stream), block_mode=BLOCK_MODES[args.block_mode])
     ctx.mc_sweep(args.burn, p=1)
     t0 = cooled_state(ctx, args.precool, wl.tau, 0.3)
     tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
@@ -427,6 +428,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0, help="persistent blocks of the sample kernels (0 = auto)")
+    ap.add_argument("--block-mode", default="auto", choices=list(BLOCK_MODES))
     ap.add_argument("--burn", type=int, default=2)
     ap.add_argument("--precool", type=int, default=2)
     ap.add_argument("--cpu-samples", type=int, default=32)

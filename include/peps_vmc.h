@@ -72,7 +72,7 @@ typedef struct {
   double init_noise; /* amplitude a of the U[-a, a] perturbation of the zero entries */
   uint64_t seed;     /* Philox key for the perturbation, the chain starts and Metropolis */
   int n_blocks;      /* persistent blocks of the sample kernels; 0 = automatic */
-  int block_mode;    /* PEPS_BLOCKS_AUTO | PEPS_BLOCKS_NARROW | PEPS_BLOCKS_WIDE */
+  int block_mode;    /* PEPS_BLOCKS_AUTO | _NARROW | _WIDE | _BATCHED */
 } peps_params;
 
 /* Thread-block layout of the per-sample kernels.  Narrow: 256 threads, four blocks per SM,
@@ -83,6 +83,11 @@ typedef struct {
 #define PEPS_BLOCKS_AUTO 0
 #define PEPS_BLOCKS_NARROW 1
 #define PEPS_BLOCKS_WIDE 2
+/* Batched: every contraction, truncation and update is one launch over a chunk of chains
+ * in lockstep (work buffers for the whole chunk in device memory, chunk size bounded by
+ * the free memory).  PEPS_EINVAL at peps_init when the Jacobi work matrices exceed the
+ * shared memory of one block. */
+#define PEPS_BLOCKS_BATCHED 3
 
 /* Results of one step (observables of Eq. 11, C_v, Eq. 13 at beta_obs = 4 t). */
 typedef struct {

@@ -26,6 +26,7 @@ PEPS_MODEL_J1J2 = 0
 PEPS_BLOCKS_AUTO = 0
 PEPS_BLOCKS_NARROW = 1
 PEPS_BLOCKS_WIDE = 2
+PEPS_BLOCKS_BATCHED = 3
 
 EXPORTS = [
     "peps_init", "peps_mc_sweep", "peps_eval_batch", "peps_sr_step", "peps_observables",

@@ -12,6 +12,9 @@
 #include "pv_philox.cuh"
 #include "pv_sample.cuh"
 #include "pv_sr.cuh"
+#include "pv_batch.cuh"
+
+#include <memory>
 
 using namespace pv;
 
@@ -183,6 +186,56 @@ int grid_for(long long n, int threads, int cap = 152 * 16) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ batched engine
+
+namespace {
+
+// Type-erased batched engine of a context (float64 or float32 arithmetic).
+struct BatchIface {
+  virtual ~BatchIface() {}
+  virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
+                    void* O, bool cached) = 0;
+  virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
+                  int* acc, int* prop) = 0;
+  double flops = 0;
+  int chunk = 0;
+};
+
+template <typename T>
+struct BatchImpl : BatchIface {
+  CudaBE<T, T> be;
+  BatchRunner<T, CudaBE<T, T>, T> run;
+  int N = 0;
+  long long No = 0;
+  double *es_tmp = nullptr, *ea_tmp = nullptr;
+  BatchImpl() : run(be) {}
+
+  void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
+            bool cached) override {
+    run.flops = 0;
+    for (int off = 0; off < nb; off += chunk) {
+      int n = std::min(chunk, nb - off);
+      run.eval(S + (long long)off * N, n, la ? la + off : nullptr, sg ? sg + off : nullptr,
+               es ? es + off : es_tmp, ea ? ea + off : ea_tmp,
+               O ? (T*)O + (long long)off * No : nullptr, No, cached && nb <= chunk);
+    }
+    flops = run.flops;
+  }
+  void mc(uint8_t* S, int n_all, int p, uint64_t seed, long long sweep0, int n_sweeps, int* acc,
+          int* prop) override {
+    run.flops = 0;
+    for (int off = 0; off < n_all; off += chunk) {
+      int n = std::min(chunk, n_all - off);
+      for (int k = 0; k < n_sweeps; ++k)
+        run.mc(S + (long long)off * N, n, p, seed, off, (uint32_t)(sweep0 + k), acc + off,
+               prop + off);
+    }
+    flops = run.flops;
+  }
+};
+
+}  // namespace
+
 // ------------------------------------------------------------------ context
 
 struct peps_ctx {
@@ -235,6 +288,7 @@ struct peps_ctx {
   double last_accept = 0;
   std::string err;
   std::vector<void*> allocs;
+  std::unique_ptr<BatchIface> batch;   // batched engine (block_mode PEPS_BLOCKS_BATCHED)
 };
 
 namespace {
@@ -306,6 +360,14 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
   Geom g = make_geom(c);
   PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
+  if (c->batch) {
+    c->batch->eval(dS, nb, la, sg, es, ea, O, use_cache);
+    double f = c->batch->flops;
+    PV_CUDA(c, cudaMemcpyAsync(c->d_flops, &f, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PV_CUDA(c, cudaStreamSynchronize(c->stream));   // f lives on this stack frame
+    PV_CUDA(c, cudaGetLastError());
+    return PEPS_OK;
+  }
   int grid = std::min(c->nblk, nb);
 #define PV_EVAL_LAUNCH(T, TH, THETA)                                                         \
   k_eval<T, T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                  \
@@ -322,6 +384,97 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
 #undef PV_EVAL_LAUNCH
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
+}
+
+}  // namespace
+
+namespace {
+
+template <typename T>
+int make_batch_t(peps_ctx* c, int sms) {
+  const peps_params* P = &c->P;
+  auto* b = new BatchImpl<T>();
+  c->batch.reset(b);
+  const int n = P->n_chains;
+  const long long cD = (long long)P->chi * P->D;
+  const long long cap = 2 * cD * (cD + 1);
+  const size_t trunc_bytes = (size_t)cap * sizeof(T) + (size_t)(cD + 4) * (sizeof(T) + 4) + 16;
+  if (trunc_bytes > 200 * 1024) return fail(c, PEPS_EINVAL, "batched blocks: Jacobi matrices exceed shared memory");
+  if (trunc_bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kb_trunc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trunc_bytes);
+    if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  std::vector<long long> sz;
+  long long n8, nd;
+  BatchBufs<T>::sizes(P->L1, P->L2, P->D, P->chi, sz, n8, nd);
+  long long per = 0;
+  for (long long x : sz) per += x;
+  size_t per_bytes = (size_t)per * sizeof(T) + (size_t)n8 + (size_t)nd * 8 + 16;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  long long chunk = std::min<long long>({(long long)n, (long long)(fr / 2 / per_bytes), 65535LL});
+  if (chunk < 1) return fail(c, PEPS_ENOMEM, "batched blocks: no room for one chain's buffers");
+  b->chunk = (int)chunk;
+  T* real = nullptr;
+  int8_t* i8 = nullptr;
+  double* dbl = nullptr;
+  int rc;
+  if ((rc = dalloc(c, &real, (size_t)per * chunk * sizeof(T)))) return rc;
+  if ((rc = dalloc(c, &i8, (size_t)n8 * chunk))) return rc;
+  if ((rc = dalloc(c, &dbl, (size_t)nd * chunk * sizeof(double)))) return rc;
+  if ((rc = dalloc(c, &b->es_tmp, (size_t)chunk * sizeof(double)))) return rc;
+  if ((rc = dalloc(c, &b->ea_tmp, (size_t)chunk * sizeof(double)))) return rc;
+  std::vector<int> bi, bj;
+  std::vector<double> bJ;
+  bond_lists(P->L1, P->L2, P->J1, P->J2, bi, bj, bJ);
+  int *dbi = nullptr, *dbj = nullptr;
+  double* dbJ = nullptr;
+  size_t nb = bi.size() ? bi.size() : 1;
+  if ((rc = dalloc(c, &dbi, nb * sizeof(int)))) return rc;
+  if ((rc = dalloc(c, &dbj, nb * sizeof(int)))) return rc;
+  if ((rc = dalloc(c, &dbJ, nb * sizeof(double)))) return rc;
+  if (!bi.empty()) {
+    cudaMemcpy(dbi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(dbj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(dbJ, bJ.data(), bJ.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  b->be.st = c->stream;
+  b->be.bi = dbi;
+  b->be.bj = dbj;
+  b->be.bJ = dbJ;
+  b->be.nb = (int)bi.size();
+  b->be.N = c->N;
+  b->be.trunc_cap = cap;
+  b->be.sms = sms;
+  {
+    int lq_max = 96 * 1024;
+    cudaError_t e = cudaFuncSetAttribute(kb_lq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq_max);
+    b->be.lq_smem_max = e == cudaSuccess ? lq_max : 48 * 1024;
+    if (e != cudaSuccess) cudaGetLastError();
+  }
+  b->N = c->N;
+  b->No = c->No;
+  auto& r = b->run;
+  r.shp.build(P->L1, P->L2, P->D, P->chi);
+  r.L1 = P->L1;
+  r.L2 = P->L2;
+  r.D = P->D;
+  r.chi = P->chi;
+  r.N = c->N;
+  r.J1 = P->J1;
+  r.J2 = P->J2;
+  r.theta = fp64(c) ? (const T*)(const void*)c->d_theta : (const T*)(const void*)c->d_theta_f;
+  r.toff = c->toff;
+  r.ooff = c->ooff;
+  r.jtol = sizeof(T) == 8 ? (T)JTOL_F64 : (T)JTOL_F32;
+  r.max_sweeps = JAC_MAX_SWEEPS;
+  r.sweeps = c->d_jsw;
+  r.b.bind(real, chunk, i8, dbl, P->L1, P->L2, P->D, P->chi);
+  return PEPS_OK;
+}
+
+int make_batch(peps_ctx* c, int sms) {
+  return fp64(c) ? make_batch_t<double>(c, sms) : make_batch_t<float>(c, sms);
 }
 
 }  // namespace
@@ -349,7 +502,7 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   if (P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
       P->chi < 1 || P->chi > 64 || P->n_chains < 1 || P->model != PEPS_MODEL_J1J2 ||
       (P->precision != PEPS_FP64 && P->precision != PEPS_FP32) || P->n_blocks < 0 ||
-      !(P->init_noise >= 0) || P->block_mode < PEPS_BLOCKS_AUTO || P->block_mode > PEPS_BLOCKS_WIDE)
+      !(P->init_noise >= 0) || P->block_mode < PEPS_BLOCKS_AUTO || P->block_mode > PEPS_BLOCKS_BATCHED)
     return PEPS_EINVAL;
   peps_ctx* c = new peps_ctx();
   c->P = *P;
@@ -432,6 +585,7 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
     if (ea != cudaSuccess) return bail(fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(ea)));
   }
   int want = P->n_blocks > 0 ? P->n_blocks : (c->wide ? sms : sms * 4);
+  if (P->block_mode == PEPS_BLOCKS_BATCHED) want = 1;   // the batched engine has its own buffers
   c->nblk = std::max(1, std::min(want, n));
   if ((rc = dalloc(c, &c->d_scr, (size_t)c->nblk * c->sreal * real))) return bail(rc);
   if ((rc = dalloc(c, &c->d_iscr, (size_t)c->nblk * c->sint * sizeof(int)))) return bail(rc);
@@ -442,7 +596,7 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     size_t need = (size_t)n * (c->ustride * real + c->ubstride * sizeof(int));
-    if (need <= fr / 4) {
+    if (P->block_mode != PEPS_BLOCKS_BATCHED && need <= fr / 4) {
       if ((rc = dalloc(c, &c->d_ucache, (size_t)n * c->ustride * real))) return bail(rc);
       if ((rc = dalloc(c, &c->d_ubond, (size_t)n * c->ubstride * sizeof(int)))) return bail(rc);
     }
@@ -463,6 +617,9 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
   if ((rc = dalloc(c, &c->d_bp2, c->nvb * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_ypart, c->nyb * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_sc, sizeof(SRScalars)))) return bail(rc);
+  if (P->block_mode == PEPS_BLOCKS_BATCHED) {
+    if ((rc = make_batch(c, sms))) return bail(rc);
+  }
   cudaError_t e;
   e = cudaMemcpyAsync(c->d_toff, c->toff.data(), (c->N + 1) * sizeof(long long),
                       cudaMemcpyHostToDevice, c->stream);
@@ -573,6 +730,14 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   PV_CUDA(c, cudaMemsetAsync(c->d_flops, 0, sizeof(double), c->stream));
   PV_CUDA(c, cudaMemsetAsync(c->d_jsw, 0, sizeof(unsigned long long), c->stream));
   int grid = std::min(c->nblk, n);
+  if (c->batch) {
+    PV_CUDA(c, cudaMemsetAsync(c->d_acc, 0, n * sizeof(int), c->stream));
+    PV_CUDA(c, cudaMemsetAsync(c->d_prop, 0, n * sizeof(int), c->stream));
+    c->batch->mc(c->d_S, n, p, c->P.seed, c->sweeps, n_sweeps, c->d_acc, c->d_prop);
+    double f = c->batch->flops;
+    PV_CUDA(c, cudaMemcpyAsync(c->d_flops, &f, sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else {
 #define PV_MC_LAUNCH(T, TH, THETA)                                                            \
   k_mc<T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                        \
       g, THETA, c->d_S, n, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, p, c->P.seed,          \
@@ -587,10 +752,11 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
     else PV_MC_LAUNCH(float, SAMPLE_THREADS, c->d_theta_f);
   }
 #undef PV_MC_LAUNCH
+  }
   PV_CUDA(c, cudaGetLastError());
   c->sweeps += n_sweeps;
   c->have_eval = false;
-  c->ucache_valid = c->d_ucache != nullptr;
+  c->ucache_valid = c->batch ? (n <= c->batch->chunk) : (c->d_ucache != nullptr);
   std::vector<int> a(n), b(n);
   PV_CUDA(c, cudaMemcpyAsync(a.data(), c->d_acc, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   PV_CUDA(c, cudaMemcpyAsync(b.data(), c->d_prop, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -632,12 +798,14 @@ int peps_eval_batch(peps_ctx* c, const uint8_t* S, int nb, int on_device, double
   if (nb == 0) return PEPS_OK;
   if (on_device) {
     PV_TRY(launch_eval(c, S, nb, log_abs, sign, e_sys, e_anc, O));
+    if (c->batch) c->ucache_valid = false;   // the batched engine's environments were reused
     PV_CUDA(c, cudaStreamSynchronize(c->stream));
     return PEPS_OK;
   }
   PV_TRY(ensure_batch(c, nb));
   PV_CUDA(c, cudaMemcpyAsync(c->d_xS, S, (size_t)nb * c->N, cudaMemcpyHostToDevice, c->stream));
   PV_TRY(launch_eval(c, c->d_xS, nb, c->d_xla, c->d_xsg, c->d_xes, c->d_xea, O ? c->d_xO : nullptr));
+  if (c->batch) c->ucache_valid = false;
   if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, c->d_xla, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, c->d_xsg, nb, cudaMemcpyDeviceToHost, c->stream));
   if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, c->d_xes, nb * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

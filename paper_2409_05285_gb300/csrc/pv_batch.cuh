@@ -1,0 +1,1348 @@
+// Batched engine: the per-sample work of the cooling step (boundary-MPS environments,
+// amplitude, E_loc, O rows, Metropolis sweep) executed in lockstep over a batch of chains.
+// Every contraction, truncation, dot product and update is one operation over the whole
+// batch (a kernel launch on the GPU), so the work streams through memory with the
+// parallelism of the batch instead of one thread block walking one chain.
+//
+// The arithmetic is that of the per-sample engine (pv_sample.cuh): the same contractions
+// in the same order, the same Householder and Jacobi routines, the same Philox draws.
+// Bond dimensions depend only on the position, so all shapes are known on the host.
+#pragma once
+
+#include <cstdint>
+#include <cmath>
+#include <vector>
+
+#include "pv_coop.cuh"
+#include "pv_philox.cuh"
+#include "pv_sample.cuh"
+
+namespace pv {
+
+// Operand of a batched contraction: a per-sample tensor (base + s * stride) or a slice of
+// the parameter vector T_i^{S} with S taken per sample from the configurations or from a
+// per-sample selection array.
+enum OpMode { OP_BATCH = 0, OP_SITE_S = 1, OP_SITE_SEL = 2 };
+
+template <typename T>
+struct Operand {
+  const T* base;
+  long long stride;      // OP_BATCH: elements between samples
+  int mode;
+  long long site_off;    // OP_SITE_*: theta offset of the site
+  long long site_sz;     //            elements of one slice
+  const uint8_t* S;      // OP_SITE_S: configurations [n][N]
+  int site;              //            site index
+  int N;
+  const int8_t* sel;     // OP_SITE_SEL: local index per sample
+
+  PV_HD const T* at(int s) const {
+    if (mode == OP_BATCH) return base + (long long)s * stride;
+    int v = mode == OP_SITE_S ? (int)S[(long long)s * N + site] : (int)sel[s];
+    return base + site_off + (long long)v * site_sz;
+  }
+};
+
+template <typename T>
+PV_HD Operand<T> batch_op(const T* base, long long stride) {
+  Operand<T> o;
+  o.base = base;
+  o.stride = stride;
+  o.mode = OP_BATCH;
+  o.site_off = o.site_sz = 0;
+  o.S = nullptr;
+  o.site = o.N = 0;
+  o.sel = nullptr;
+  return o;
+}
+
+// Merged-dimension form of a contraction (as in contract()).
+struct MSpec {
+  int no, nk;
+  int os[6], ao[6], bo[6];
+  int ks[3], ak[3], bk[3];
+  int total;
+  double flops;
+};
+
+inline MSpec merge_spec(const Spec& s) {
+  MSpec m;
+  m.no = 0;
+  for (int d = 0; d < s.no; ++d) {
+    int n = s.os[d], a = (int)s.ao[d], b = (int)s.bo[d];
+    if (n == 1) continue;
+    if (m.no > 0 && m.ao[m.no - 1] == a * n && m.bo[m.no - 1] == b * n) {
+      m.os[m.no - 1] *= n;
+      m.ao[m.no - 1] = a;
+      m.bo[m.no - 1] = b;
+    } else {
+      m.os[m.no] = n;
+      m.ao[m.no] = a;
+      m.bo[m.no] = b;
+      ++m.no;
+    }
+  }
+  m.nk = 0;
+  for (int d = 0; d < s.nk; ++d) {
+    int n = s.ks[d], a = (int)s.ak[d], b = (int)s.bk[d];
+    if (n == 1) continue;
+    if (m.nk > 0 && m.ak[m.nk - 1] == a * n && m.bk[m.nk - 1] == b * n) {
+      m.ks[m.nk - 1] *= n;
+      m.ak[m.nk - 1] = a;
+      m.bk[m.nk - 1] = b;
+    } else {
+      m.ks[m.nk] = n;
+      m.ak[m.nk] = a;
+      m.bk[m.nk] = b;
+      ++m.nk;
+    }
+  }
+  for (int d = m.nk; d < 3; ++d) {
+    m.ks[d] = 1;
+    m.ak[d] = m.bk[d] = 0;
+  }
+  m.total = (int)s.total;
+  m.flops = 2.0 * (double)s.total * (double)s.kprod;
+  return m;
+}
+
+// Four consecutive outputs (along the last merged dimension) of one sample's contraction.
+template <typename T>
+PV_HD void ein_quad(const MSpec& m, T* out, const T* A, const T* B, int idx) {
+  int rem = idx, oa = 0, ob = 0;
+  for (int d = m.no - 1; d >= 0; --d) {
+    int q = rem / m.os[d];
+    int i = rem - q * m.os[d];
+    rem = q;
+    oa += i * m.ao[d];
+    ob += i * m.bo[d];
+  }
+  const int la = m.no > 0 ? m.ao[m.no - 1] : 0, lb = m.no > 0 ? m.bo[m.no - 1] : 0;
+  const int K0 = m.ks[0], a0 = m.ak[0], b0 = m.bk[0];
+  T c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+  for (int k2 = 0; k2 < m.ks[2]; ++k2)
+    for (int k1 = 0; k1 < m.ks[1]; ++k1) {
+      const T* pa = A + oa + k1 * m.ak[1] + k2 * m.ak[2];
+      const T* pb = B + ob + k1 * m.bk[1] + k2 * m.bk[2];
+#pragma unroll 4
+      for (int k0 = 0; k0 < K0; ++k0) {
+        const T* qa = pa + k0 * a0;
+        const T* qb = pb + k0 * b0;
+        c0 += qa[0] * qb[0];
+        c1 += qa[la] * qb[lb];
+        c2 += qa[2 * la] * qb[2 * lb];
+        c3 += qa[3 * la] * qb[3 * lb];
+      }
+    }
+  out[idx] = c0;
+  out[idx + 1] = c1;
+  out[idx + 2] = c2;
+  out[idx + 3] = c3;
+}
+
+template <typename T>
+PV_HD void ein_one(const MSpec& m, T* out, const T* A, const T* B, int idx) {
+  int rem = idx, oa = 0, ob = 0;
+  for (int d = m.no - 1; d >= 0; --d) {
+    int q = rem / m.os[d];
+    int i = rem - q * m.os[d];
+    rem = q;
+    oa += i * m.ao[d];
+    ob += i * m.bo[d];
+  }
+  T acc = 0;
+  for (int k2 = 0; k2 < m.ks[2]; ++k2)
+    for (int k1 = 0; k1 < m.ks[1]; ++k1) {
+      const T* pa = A + oa + k1 * m.ak[1] + k2 * m.ak[2];
+      const T* pb = B + ob + k1 * m.bk[1] + k2 * m.bk[2];
+      for (int k0 = 0; k0 < m.ks[0]; ++k0) acc += pa[k0 * m.ak[0]] * pb[k0 * m.bk[0]];
+    }
+  out[idx] = acc;
+}
+
+PV_HD bool quad_ok(const MSpec& m) { return m.no > 0 && (m.os[m.no - 1] & 3) == 0; }
+
+// GEMM form of a contraction: every output label belongs to exactly one operand, so
+// out = C[M][N] with the M index made of A's output labels and N of B's, both with the
+// strides of the row-major output.  ok == false when some output label is in both
+// operands (not used by this engine).
+struct GSpec {
+  int nm, nn, nk;
+  int ms[4], mA[4], mC[4];
+  int ns[4], nB[4], nC[4];
+  int ks[4], kA[4], kB[4];
+  int M, N, K;
+  bool ok;
+};
+
+inline GSpec gemm_spec(const Spec& s) {
+  GSpec g;
+  g.nm = g.nn = g.nk = 0;
+  g.M = g.N = g.K = 1;
+  g.ok = true;
+  long long cstride[6];
+  long long st = 1;
+  for (int d = s.no - 1; d >= 0; --d) {
+    cstride[d] = st;
+    st *= s.os[d];
+  }
+  for (int d = 0; d < s.no; ++d) {
+    if (s.os[d] == 1) continue;
+    bool inA = s.ao[d] != 0, inB = s.bo[d] != 0;
+    if (inA == inB) {
+      g.ok = false;
+      return g;
+    }
+    if (inA) {
+      if (g.nm == 4) { g.ok = false; return g; }
+      g.ms[g.nm] = s.os[d];
+      g.mA[g.nm] = (int)s.ao[d];
+      g.mC[g.nm] = (int)cstride[d];
+      g.M *= s.os[d];
+      ++g.nm;
+    } else {
+      if (g.nn == 4) { g.ok = false; return g; }
+      g.ns[g.nn] = s.os[d];
+      g.nB[g.nn] = (int)s.bo[d];
+      g.nC[g.nn] = (int)cstride[d];
+      g.N *= s.os[d];
+      ++g.nn;
+    }
+  }
+  for (int d = 0; d < s.nk; ++d) {
+    if (s.ks[d] == 1) continue;
+    if (g.nk == 4) { g.ok = false; return g; }
+    g.ks[g.nk] = s.ks[d];
+    g.kA[g.nk] = (int)s.ak[d];
+    g.kB[g.nk] = (int)s.bk[d];
+    g.K *= s.ks[d];
+    ++g.nk;
+  }
+  return g;
+}
+
+// Offsets of a row-major multi-index over dims (sz, stride1, stride2).
+PV_HD void gemm_offsets(int idx, int n, const int* sz, const int* s1, const int* s2, int& o1,
+                        int& o2) {
+  o1 = o2 = 0;
+  for (int d = n - 1; d >= 0; --d) {
+    int q = idx / sz[d];
+    int i = idx - q * sz[d];
+    idx = q;
+    o1 += i * s1[d];
+    o2 += i * s2[d];
+  }
+}
+
+// ------------------------------------------------------------------------ shapes
+
+// Bond dimensions of every environment and of the truncation steps, from the geometry.
+struct Shapes {
+  int L1, L2, D, chi;
+  // env bonds: down[r][c] (r = 1..L1), up[r][c] (r = 0..L1-1)
+  std::vector<std::vector<int>> down, up;
+
+  int dl(int c) const { return c == 0 ? 1 : D; }
+  int dr(int c) const { return c == L2 - 1 ? 1 : D; }
+  int du(int r) const { return r == 0 ? 1 : D; }
+  int dd(int r) const { return r == L1 - 1 ? 1 : D; }
+
+  // Output bonds of compressing (env with bonds `in`) x row r.
+  std::vector<int> compress_bonds(const std::vector<int>& in, int p) const {
+    std::vector<int> bc(L2 + 1), out(L2 + 1);
+    int maxb = 0;
+    for (int c = 0; c < L2; ++c) bc[c] = in[c] * dl(c);
+    bc[L2] = 1;
+    for (int c = 0; c <= L2; ++c) maxb = bc[c] > maxb ? bc[c] : maxb;
+    if (maxb <= chi) return bc;
+    std::vector<int> kf(L2 + 1);
+    kf[L2] = 1;
+    for (int c = L2 - 1; c >= 1; --c) kf[c] = bc[c] < p * kf[c + 1] ? bc[c] : p * kf[c + 1];
+    out[0] = 1;
+    int bprev = 1;
+    for (int c = 0; c < L2 - 1; ++c) {
+      int m = bprev * p, k = kf[c + 1];
+      int kmax = m < k ? m : k;
+      int kk = chi < kmax ? chi : kmax;
+      out[c + 1] = kk;
+      bprev = kk;
+    }
+    out[L2] = 1;
+    return out;
+  }
+
+  void build(int L1_, int L2_, int D_, int chi_) {
+    L1 = L1_;
+    L2 = L2_;
+    D = D_;
+    chi = chi_;
+    down.assign(L1 + 1, std::vector<int>(L2 + 1, 1));
+    up.assign(L1, std::vector<int>(L2 + 1, 1));
+    for (int r = L1 - 1; r >= 1; --r) down[r] = compress_bonds(down[r + 1], du(r));
+    for (int r = 1; r < L1; ++r) up[r] = compress_bonds(up[r - 1], dd(r - 1));
+  }
+};
+
+}  // namespace pv
+
+namespace pv {
+
+// ------------------------------------------------------------ per-sample operations
+// Each functor does one sample's share of an operation; the GPU backend runs one thread
+// block per sample, the host backend a plain loop.
+
+template <typename T>
+struct OpLq {   // Lf[s] = triangular factor of W[s] (m x nn); W overwritten
+  T* Lf;
+  long long ls;
+  T* W;
+  long long ws;
+  int m, nn;
+  T* red;
+  PV_HD void operator()(int s, T* redbuf) const {
+    lq_factor(Lf + (long long)s * ls, W + (long long)s * ws, m, nn, redbuf, redbuf);
+  }
+};
+
+// Truncation of one bond: Jacobi on Y (nc columns of length len, or the m rows when not
+// tall), the kk leading left singular vectors into Uk and the environment tensor `out`,
+// which is max-abs normalised with the logarithm added to ls[s].
+template <typename T>
+struct OpTrunc {
+  const T* Y;
+  long long ys;
+  bool tall;
+  int nc, len, m, kk;
+  T* Uk;
+  long long uks;
+  T* out;
+  long long outs;
+  double* lsv;
+  int lstride;
+  T jtol;
+  int max_sweeps;
+  unsigned long long* sweeps;
+  PV_HD void operator()(int s, T* red, int* flag, T* smem, long long smem_cap, int* order,
+                        T* sig) const {
+    const T* Ys = Y + (long long)s * ys;
+    int ldy = len | 1, ldv = m | 1;
+    T* Yw = smem;
+    T* Vw = smem + (long long)nc * ldy;
+    for (long long i = PV_TID; i < (long long)nc * len; i += PV_NTHR)
+      Yw[(i / len) * ldy + i % len] = Ys[i];
+    if (!tall)
+      for (long long i = PV_TID; i < (long long)m * m; i += PV_NTHR)
+        Vw[(i / m) * ldv + i % m] = (i / m == i % m) ? (T)1 : (T)0;
+    PV_SYNC();
+    int sw = 0;
+    jacobi(Yw, ldy, nc, len, tall ? (T*)nullptr : Vw, ldv, m, jtol, max_sweeps, flag, &sw, red);
+    for (int j = PV_WARP; j < nc; j += PV_NWARP) {
+      T s2 = 0;
+      const T* y = Yw + (long long)j * ldy;
+      for (int i = PV_LANE; i < len; i += PV_WSIZE) s2 += y[i] * y[i];
+      s2 = warp_sum(s2);
+      if (PV_LANE == 0) sig[j] = sqrt(s2);
+    }
+    PV_SYNC();
+    for (int j = PV_TID; j < nc; j += PV_NTHR) {
+      int rank = 0;
+      T sj = sig[j];
+      for (int i = 0; i < nc; ++i) {
+        T si = sig[i];
+        rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
+      }
+      order[rank] = j;
+    }
+    PV_SYNC();
+    T zero2 = 0;
+    if (tall) {
+      T nf2 = 0;
+      for (int j = 0; j < nc; ++j) nf2 += sig[j] * sig[j];
+      const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+      zero2 = (eps * len) * (eps * len) * nf2;
+    }
+    T* U = Uk + (long long)s * uks;
+    for (long long idx = PV_TID; idx < (long long)m * kk; idx += PV_NTHR) {
+      int q = (int)(idx / kk), jp = (int)(idx % kk);
+      int j = order[jp];
+      T v;
+      if (tall) {
+        T sg = sig[j];
+        v = sg * sg > zero2 ? Yw[(long long)j * ldy + q] / sg : (T)0;
+      } else {
+        v = Vw[(long long)j * ldv + q];
+      }
+      U[idx] = v;
+    }
+    PV_SYNC();
+    T* o = out + (long long)s * outs;
+    copy(o, U, (long long)m * kk);
+    double l = normalize_maxabs(o, (long long)m * kk, red);
+    if (PV_TID == 0) {
+      lsv[(long long)s * lstride] += l;
+#if defined(__CUDA_ARCH__)
+      atomicAdd(sweeps, (unsigned long long)sw);
+#else
+      *sweeps += (unsigned long long)sw;
+#endif
+    }
+    PV_SYNC();
+    (void)smem_cap;
+  }
+};
+
+template <typename T>
+struct OpNorm {   // x[s] /= max|x[s]|, ls[s] += log max
+  T* x;
+  long long xs, len;
+  double* lsv;
+  int lstride;
+  PV_HD void operator()(int s, T* red) const {
+    double l = normalize_maxabs(x + (long long)s * xs, len, red);
+    if (PV_TID == 0) lsv[(long long)s * lstride] += l;
+    PV_SYNC();
+  }
+};
+
+template <typename T>
+struct OpDot {   // out[s] = a[s] . b[s]
+  const T* a;
+  long long as;
+  const T* b;
+  long long bs, len;
+  T* out;
+  PV_HD void operator()(int s, T* red) const {
+    T v = dot(a + (long long)s * as, b + (long long)s * bs, len, red);
+    if (PV_TID == 0) out[s] = v;
+    PV_SYNC();
+  }
+};
+
+// --------------------------------------------------------------- elementwise per sample
+
+template <typename T>
+struct ElemSet {   // x[s][off] = v
+  T* x;
+  long long xs, off;
+  T v;
+  PV_HD void operator()(int s) const { x[(long long)s * xs + off] = v; }
+};
+
+template <typename T>
+struct ElemCopyMasked {   // dst[s][:len] = src[s][:len] where mask[s] (all when mask null)
+  T* dst;
+  long long ds;
+  const T* src;
+  long long ss, len;
+  const int8_t* mask;
+};
+
+// Local indices of a proposal: flip of site i, or exchange of layer (0 system, 1 ancilla)
+// between sites i and j; valid = the move changes the configuration.
+struct ElemSel {
+  const uint8_t* S;
+  int N, i, j, kind;   // kind 0 flip, 1 system exchange, 2 ancilla exchange
+  int8_t *si, *sj, *valid;
+  PV_HD void operator()(int s) const {
+    int a = S[(long long)s * N + i];
+    if (kind == 0) {
+      si[s] = (int8_t)(3 - a);
+      valid[s] = 1;
+      return;
+    }
+    int b = S[(long long)s * N + j];
+    int sa = a >> 1, sb = b >> 1, aa = a & 1, ab = b & 1;
+    if (kind == 1) {
+      si[s] = (int8_t)(2 * sb + aa);
+      sj[s] = (int8_t)(2 * sa + ab);
+      valid[s] = sa != sb;
+    } else {
+      si[s] = (int8_t)(2 * sa + ab);
+      sj[s] = (int8_t)(2 * sb + aa);
+      valid[s] = aa != ab;
+    }
+  }
+};
+
+// E += coef * num/den where valid (local-energy ratio terms).
+template <typename T>
+struct ElemRatio {
+  const T* num;
+  const T* den;
+  long long dens;   // stride of den (0: per-sample scalar array)
+  const int8_t* valid;
+  double coef;
+  double* e;
+  PV_HD void operator()(int s) const {
+    if (valid[s]) e[s] += coef * (double)num[s] / (double)den[(long long)s * dens];
+  }
+};
+
+// Diagonal part of E_sys, E_anc: sum over bonds J S^z_i S^z_j on each layer.
+struct ElemDiag {
+  const uint8_t* S;
+  int N, nb;
+  const int* bi;
+  const int* bj;
+  const double* bJ;
+  double *es, *ea;
+  PV_HD void operator()(int s) const {
+    const uint8_t* x = S + (long long)s * N;
+    double a = 0, b = 0;
+    for (int k = 0; k < nb; ++k) {
+      int p = x[bi[k]], q = x[bj[k]];
+      double zs = ((p >> 1) ? -0.5 : 0.5) * ((q >> 1) ? -0.5 : 0.5);
+      double za = ((p & 1) ? -0.5 : 0.5) * ((q & 1) ? -0.5 : 0.5);
+      a += bJ[k] * zs;
+      b += bJ[k] * za;
+    }
+    es[s] = a;
+    ea[s] = b;
+  }
+};
+
+// Amplitude from the row-0 strip value and the down log-scale.
+template <typename T>
+struct ElemAmp {
+  const T* val;
+  long long vs;
+  const double* lsd;
+  int lstride;
+  double* log_abs;
+  int8_t* sign;
+  PV_HD void operator()(int s) const {
+    T v = val[(long long)s * vs];
+    T av = v < 0 ? -v : v;
+    if (log_abs) log_abs[s] = (av > 0 ? log((double)av) : -INFINITY) + lsd[(long long)s * lstride];
+    if (sign) sign[s] = (int8_t)(v > 0 ? 1 : (v < 0 ? -1 : 0));
+  }
+};
+
+// Metropolis test of a proposal: u = Philox(seed; chain, sweep, id, TAG_MC) < |num/den|^p.
+// On acceptance the configuration takes the proposed local indices and `den` the
+// numerator; acc/prop count the proposals made.
+template <typename T>
+struct ElemAccept {
+  uint8_t* S;
+  int N, i, j;   // j < 0: single-site move
+  const int8_t *si, *sj, *valid;
+  const T* num;
+  T* den;
+  int p;
+  uint64_t seed;
+  int chain0;
+  uint32_t sweep, id;
+  int *acc, *prop;
+  int8_t* accepted;
+  PV_HD void operator()(int s) const {
+    accepted[s] = 0;
+    if (!valid[s]) return;
+    double u = philox_uniform(seed, (uint32_t)(chain0 + s), sweep, id, TAG_MC);
+    double ratio = (double)num[s] / (double)den[s];
+    double q = p == 2 ? ratio * ratio : (ratio < 0 ? -ratio : ratio);
+    prop[s] += 1;
+    if (u < q) {
+      acc[s] += 1;
+      accepted[s] = 1;
+      S[(long long)s * N + i] = (uint8_t)si[s];
+      if (j >= 0) S[(long long)s * N + j] = (uint8_t)sj[s];
+      den[s] = num[s];
+    }
+  }
+};
+
+// O row entries of one site: O[s][o_off + k] = env[s][k] / val[s].
+template <typename T, typename OT>
+struct ElemO {
+  OT* O;
+  long long No, o_off, sz;
+  const T* env;
+  long long es;
+  const T* val;
+  long long vs;
+};
+
+}  // namespace pv
+
+namespace pv {
+
+// ------------------------------------------------------------------ the batched runner
+
+template <typename T>
+struct BatchBufs {
+  long long ENV, CB, LB, P1, P2, TMP, D4;
+  T *envD, *envU, *Cs, *W, *Lf, *Am, *Y, *carry, *Uk;
+  T *p1R, *p1L, *p2R, *p2L, *t0, *t1, *m0, *m1, *m2, *m3, *envo;
+  T *val, *num, *den, *val2;
+  double *lsD, *lsU;
+  int8_t *si, *sj, *valid, *accepted;
+  long long sD, sU, sLf, sp1R, sp1L, sp2R, sp2L;   // per-sample strides of the multi-slot buffers
+
+  // Element counts per sample of every buffer, in allocation order.
+  static void sizes(int L1, int L2, int D, int chi, std::vector<long long>& real_sz,
+                    long long& int8_per_sample, long long& dbl_per_sample) {
+    ScratchDims d = scratch_dims(L1, L2, D, chi);
+    long long cD = (long long)chi * D;
+    real_sz = {(long long)(L1 + 1) * L2 * d.ENV,   // envD
+               (long long)L1 * L2 * d.ENV,         // envU
+               d.CB, d.CB,                         // Cs, W
+               (long long)(L2 + 1) * d.LB,         // Lf
+               d.P2,                               // Am
+               d.LB,                               // Y
+               cD * chi, cD * chi,                 // carry, Uk
+               (long long)(L2 + 1) * d.P1, 2 * d.P1,
+               (long long)(L2 + 1) * d.P2, 2 * d.P2,
+               d.TMP, d.TMP,
+               d.P2, d.P2, d.P2, d.P2,
+               (long long)D * D * D * D,
+               1, 1, 1, 1};                        // val, num, den, val2
+    int8_per_sample = 4;
+    dbl_per_sample = (long long)(L1 + 1) + 1;
+  }
+
+  void bind(T* real, long long n, int8_t* i8, double* dbl, int L1, int L2, int D, int chi) {
+    ScratchDims d = scratch_dims(L1, L2, D, chi);
+    ENV = d.ENV;
+    CB = d.CB;
+    LB = d.LB;
+    P1 = d.P1;
+    P2 = d.P2;
+    TMP = d.TMP;
+    D4 = (long long)D * D * D * D;
+    std::vector<long long> sz;
+    long long n8, nd;
+    sizes(L1, L2, D, chi, sz, n8, nd);
+    T** dst[] = {&envD, &envU, &Cs, &W, &Lf, &Am, &Y, &carry, &Uk, &p1R, &p1L, &p2R, &p2L,
+                 &t0, &t1, &m0, &m1, &m2, &m3, &envo, &val, &num, &den, &val2};
+    T* p = real;
+    for (size_t k = 0; k < sz.size(); ++k) {
+      *dst[k] = p;
+      p += sz[k] * n;
+    }
+    sD = sz[0];
+    sU = sz[1];
+    sLf = sz[4];
+    sp1R = sz[9];
+    sp1L = sz[10];
+    sp2R = sz[11];
+    sp2L = sz[12];
+    si = i8;
+    sj = i8 + n;
+    valid = i8 + 2 * n;
+    accepted = i8 + 3 * n;
+    lsD = dbl;
+    lsU = dbl + (L1 + 1) * n;
+  }
+};
+
+// Buffer slot stride helper: per-sample tensors of size `sz` packed [n][sz].
+template <typename T, typename BE, typename OT>
+struct BatchRunner {
+  BE& be;
+  Shapes shp;
+  int L1, L2, D, chi, N;
+  double J1, J2;
+  const T* theta;
+  std::vector<long long> toff, ooff;
+  BatchBufs<T> b;
+  T jtol;
+  int max_sweeps;
+  double flops = 0;
+  unsigned long long* sweeps;   // Jacobi sweep counter (device or host)
+
+  BatchRunner(BE& be_) : be(be_) {}
+
+  int dl(int c) const { return c == 0 ? 1 : D; }
+  int dr(int c) const { return c == L2 - 1 ? 1 : D; }
+  int du(int r) const { return r == 0 ? 1 : D; }
+  int dd(int r) const { return r == L1 - 1 ? 1 : D; }
+  long long szs(int r, int c) const { return (long long)dl(c) * dr(c) * du(r) * dd(r); }
+
+  Operand<T> site(int r, int c, const uint8_t* S) const {
+    Operand<T> o = batch_op<T>(theta, 0);
+    o.mode = OP_SITE_S;
+    o.site_off = toff[r * L2 + c];
+    o.site_sz = szs(r, c);
+    o.S = S;
+    o.site = r * L2 + c;
+    o.N = N;
+    return o;
+  }
+  Operand<T> site_sel(int r, int c, const int8_t* sel) const {
+    Operand<T> o = site(r, c, nullptr);
+    o.mode = OP_SITE_SEL;
+    o.sel = sel;
+    return o;
+  }
+  static Operand<T> bat(const T* base, long long stride) { return batch_op<T>(base, stride); }
+
+  void ein(T* out, long long os, const char* so, Operand<T> A, const char* sa, Operand<T> B,
+           const char* sb, const Dims& d, int n) {
+    Spec raw = make_spec(so, sa, sb, d);
+    MSpec m = merge_spec(raw);
+    flops += m.flops * n;
+    be.ein(raw, m, out, os, A, B, n);
+  }
+
+  // ---------------------------------------------------------------- environments
+  // env tensor c of a multi-row environment array
+  Operand<T> envt(const T* rowbase, long long stride, int c) const {
+    return bat(rowbase + (long long)c * b.ENV, stride);
+  }
+
+  void absorb_site(const T* envrow, long long es, const std::vector<int>& bond, bool down, int r,
+                   int c, const uint8_t* S, T* out, long long os, int n) {
+    Dims dm;
+    dm.set('a', bond[c]).set('b', bond[c + 1]).set('l', dl(c)).set('r', dr(c));
+    dm.set('u', du(r)).set('d', dd(r));
+    if (down)
+      ein(out, os, "alubr", envt(envrow, es, c), "adb", site(r, c, S), "lrud", dm, n);
+    else
+      ein(out, os, "aldbr", envt(envrow, es, c), "aub", site(r, c, S), "lrud", dm, n);
+  }
+
+  // Compress (env x row r) into outrow (same stride es); log-scales ls[s*lstride] += ...
+  void compress(const T* envrow, long long es, const std::vector<int>& bond, bool down, int r,
+                const uint8_t* S, T* outrow, long long os, double* ls, int lstride, int n) {
+    const int p = down ? du(r) : dd(r);
+    std::vector<int> bc(L2 + 1);
+    int maxb = 0;
+    for (int c = 0; c < L2; ++c) bc[c] = bond[c] * dl(c);
+    bc[L2] = 1;
+    for (int c = 0; c <= L2; ++c) maxb = bc[c] > maxb ? bc[c] : maxb;
+    if (maxb <= chi) {
+      for (int c = 0; c < L2; ++c) {
+        T* o = outrow + (long long)c * b.ENV;
+        absorb_site(envrow, es, bond, down, r, c, S, o, os, n);
+        be.norm(OpNorm<T>{o, os, (long long)bc[c] * p * bc[c + 1], ls, lstride}, n);
+      }
+      return;
+    }
+    std::vector<int> kf(L2 + 1);
+    kf[L2] = 1;
+    be.set(b.Lf, b.sLf, (long long)L2 * b.LB, (T)1, n);
+    for (int c = L2 - 1; c >= 1; --c) {
+      absorb_site(envrow, es, bond, down, r, c, S, b.Cs, b.CB, n);
+      Dims dm;
+      dm.set('a', bc[c]).set('p', p).set('b', bc[c + 1]).set('k', kf[c + 1]);
+      ein(b.W, b.CB, "apk", bat(b.Cs, b.CB), "apb", bat(b.Lf + (long long)(c + 1) * b.LB, b.sLf),
+          "bk", dm, n);
+      int m = bc[c], nn = p * kf[c + 1];
+      be.lq(OpLq<T>{b.Lf + (long long)c * b.LB, b.sLf, b.W, b.CB, m, nn, nullptr}, n);
+      flops += lq_flops(m, nn) * n;
+      kf[c] = m < nn ? m : nn;
+    }
+    be.set(b.carry, (long long)chi * (chi * D), 0, (T)1, n);
+    int bprev = 1;
+    for (int c = 0; c < L2 - 1; ++c) {
+      int a = bc[c], bb = bc[c + 1], k = kf[c + 1];
+      absorb_site(envrow, es, bond, down, r, c, S, b.Cs, b.CB, n);
+      Dims dm;
+      dm.set('x', bprev).set('a', a).set('p', p).set('b', bb);
+      ein(b.Am, b.P2, "xpb", bat(b.carry, (long long)chi * chi * D), "xa", bat(b.Cs, b.CB), "apb",
+          dm, n);
+      int m = bprev * p;
+      bool tall = k <= m;
+      Dims dq;
+      dq.set('q', m).set('b', bb).set('k', k);
+      const T* Lc = b.Lf + (long long)(c + 1) * b.LB;
+      ein(b.Y, b.LB, tall ? "kq" : "qk", bat(b.Am, b.P2), "qb", bat(Lc, b.sLf), "bk", dq, n);
+      int nc = tall ? k : m, len = tall ? m : k;
+      int kmax = m < k ? m : k;
+      int kk = chi < kmax ? chi : kmax;
+      T* o = outrow + (long long)c * b.ENV;
+      be.trunc(OpTrunc<T>{b.Y, b.LB, tall, nc, len, m, kk, b.Uk, (long long)chi * chi * D, o, os,
+                          ls, lstride, jtol, max_sweeps, sweeps},
+               n);
+      Dims dc;
+      dc.set('q', m).set('j', kk).set('b', bb);
+      ein(b.carry, (long long)chi * chi * D, "jb", bat(b.Uk, (long long)chi * chi * D), "qj",
+          bat(b.Am, b.P2), "qb", dc, n);
+      bprev = kk;
+    }
+    {
+      int c = L2 - 1;
+      absorb_site(envrow, es, bond, down, r, c, S, b.Cs, b.CB, n);
+      Dims dm;
+      dm.set('x', bprev).set('a', bc[c]).set('p', p).set('b', bc[c + 1]);
+      T* o = outrow + (long long)c * b.ENV;
+      ein(o, os, "xpb", bat(b.carry, (long long)chi * chi * D), "xa", bat(b.Cs, b.CB), "apb", dm, n);
+      be.norm(OpNorm<T>{o, os, (long long)bprev * p * bc[c + 1], ls, lstride}, n);
+    }
+  }
+
+  static double lq_flops(int m, int n) {
+    int K = m < n ? m : n;
+    double f = 0;
+    for (int j = 0; j < K; ++j) f += 4.0 * (double)(n - j) * (double)(m - j);
+    return f;
+  }
+
+  T* downrow(int r) const { return b.envD + (long long)r * L2 * b.ENV; }
+  T* uprow(int r) const { return b.envU + (long long)r * L2 * b.ENV; }
+
+  void trivial(T* row, long long stride, int n) {
+    for (int c = 0; c < L2; ++c) be.set(row, stride, (long long)c * b.ENV, (T)1, n);
+  }
+
+  void build_down(const uint8_t* S, int n) {
+    trivial(downrow(L1), b.sD, n);
+    be.setd(b.lsD, L1 + 1, L1, 0.0, n);
+    for (int r = L1 - 1; r >= 1; --r) {
+      be.copyd(b.lsD, L1 + 1, r, r + 1, n);   // lsD[r] = lsD[r+1]
+      compress(downrow(r + 1), b.sD, shp.down[r + 1], true, r, S, downrow(r), b.sD, b.lsD + r,
+               L1 + 1, n);
+    }
+  }
+
+  // ----------------------------------------------------------------- strips
+  // one-row strip pieces (U row = up env of row r, Dn row = down env r+1)
+  void s1_left(int r, int c, T* Lout, long long los, Operand<T> Lin, Operand<T> A, int n) {
+    const std::vector<int>&bu = shp.up[r], &bd = shp.down[r + 1];
+    Dims dm;
+    dm.set('a', bu[c]).set('x', bu[c + 1]).set('b', bd[c]).set('y', bd[c + 1]);
+    dm.set('l', dl(c)).set('r', dr(c)).set('u', du(r)).set('d', dd(r));
+    ein(b.t0, b.TMP, "lbux", Lin, "alb", envt(uprow(r), b.sU, c), "aux", dm, n);
+    ein(b.t1, b.TMP, "bxrd", bat(b.t0, b.TMP), "lbux", A, "lrud", dm, n);
+    ein(Lout, los, "xry", bat(b.t1, b.TMP), "bxrd", envt(downrow(r + 1), b.sD, c), "bdy", dm, n);
+  }
+  void s1_right(int r, int c, T* Rout, long long ros, Operand<T> Rin, Operand<T> A, int n) {
+    const std::vector<int>&bu = shp.up[r], &bd = shp.down[r + 1];
+    Dims dm;
+    dm.set('a', bu[c]).set('x', bu[c + 1]).set('b', bd[c]).set('y', bd[c + 1]);
+    dm.set('l', dl(c)).set('r', dr(c)).set('u', du(r)).set('d', dd(r));
+    ein(b.t0, b.TMP, "bdxr", envt(downrow(r + 1), b.sD, c), "bdy", Rin, "xry", dm, n);
+    ein(b.t1, b.TMP, "lubx", A, "lrud", bat(b.t0, b.TMP), "bdxr", dm, n);
+    ein(Rout, ros, "alb", envt(uprow(r), b.sU, c), "aux", bat(b.t1, b.TMP), "lubx", dm, n);
+  }
+  void s1_env(int r, int c, Operand<T> L, Operand<T> R, int n) {
+    const std::vector<int>&bu = shp.up[r], &bd = shp.down[r + 1];
+    Dims dm;
+    dm.set('a', bu[c]).set('x', bu[c + 1]).set('b', bd[c]).set('y', bd[c + 1]);
+    dm.set('l', dl(c)).set('r', dr(c)).set('u', du(r)).set('d', dd(r));
+    ein(b.t0, b.TMP, "lbux", L, "alb", envt(uprow(r), b.sU, c), "aux", dm, n);
+    ein(b.t1, b.TMP, "lbury", bat(b.t0, b.TMP), "lbux", R, "xry", dm, n);
+    ein(b.envo, b.D4, "lrud", bat(b.t1, b.TMP), "lbury", envt(downrow(r + 1), b.sD, c), "bdy", dm, n);
+  }
+  long long s1_len(int r, int c) const {
+    return (long long)shp.up[r][c] * (c < L2 ? dl(c) : 1) * shp.down[r + 1][c];
+  }
+  // two-row strip pieces (U = up env of row r, rows r and r+1, Dn = down env r+2)
+  void s2_left(int r, int c, T* Lout, long long los, Operand<T> Lin, Operand<T> A1, Operand<T> A2,
+               int n) {
+    const std::vector<int>&bu = shp.up[r], &bd = shp.down[r + 2];
+    Dims dm;
+    dm.set('a', bu[c]).set('x', bu[c + 1]).set('b', bd[c]).set('y', bd[c + 1]);
+    dm.set('i', dl(c)).set('r', dr(c)).set('j', dl(c)).set('s', dr(c));
+    dm.set('u', du(r)).set('m', dd(r)).set('d', dd(r + 1));
+    ein(b.t0, b.TMP, "ijbux", Lin, "aijb", envt(uprow(r), b.sU, c), "aux", dm, n);
+    ein(b.t1, b.TMP, "jbxrm", bat(b.t0, b.TMP), "ijbux", A1, "irum", dm, n);
+    ein(b.t0, b.TMP, "bxrsd", bat(b.t1, b.TMP), "jbxrm", A2, "jsmd", dm, n);
+    ein(Lout, los, "xrsy", bat(b.t0, b.TMP), "bxrsd", envt(downrow(r + 2), b.sD, c), "bdy", dm, n);
+  }
+  void s2_right(int r, int c, T* Rout, long long ros, Operand<T> Rin, Operand<T> A1,
+                Operand<T> A2, int n) {
+    const std::vector<int>&bu = shp.up[r], &bd = shp.down[r + 2];
+    Dims dm;
+    dm.set('a', bu[c]).set('x', bu[c + 1]).set('b', bd[c]).set('y', bd[c + 1]);
+    dm.set('i', dl(c)).set('r', dr(c)).set('j', dl(c)).set('s', dr(c));
+    dm.set('u', du(r)).set('m', dd(r)).set('d', dd(r + 1));
+    ein(b.t0, b.TMP, "bdxrs", envt(downrow(r + 2), b.sD, c), "bdy", Rin, "xrsy", dm, n);
+    ein(b.t1, b.TMP, "jmbxr", A2, "jsmd", bat(b.t0, b.TMP), "bdxrs", dm, n);
+    ein(b.t0, b.TMP, "iujbx", A1, "irum", bat(b.t1, b.TMP), "jmbxr", dm, n);
+    ein(Rout, ros, "aijb", envt(uprow(r), b.sU, c), "aux", bat(b.t0, b.TMP), "iujbx", dm, n);
+  }
+  long long s2_len(int r, int c) const {
+    long long l = c < L2 ? dl(c) : 1;
+    return (long long)shp.up[r][c] * l * l * shp.down[r + 2][c];
+  }
+
+  T* p1R(int c) const { return b.p1R + (long long)c * b.P1; }
+  T* p2R(int c) const { return b.p2R + (long long)c * b.P2; }
+
+  // ------------------------------------------------------------------- evaluation
+  void eval(const uint8_t* S, int n, double* log_abs, int8_t* sign, double* es, double* ea,
+            OT* O, long long No, bool cached) {
+    build_down(S, n);
+    // diagonal energies
+    be.diag(S, n, es, ea);
+    if (!cached) trivial(uprow(0), b.sU, n);
+    for (int r = 0; r < L1; ++r) {
+      // one-row strip: right partials, value, O, horizontal ratios with a rolling left partial
+      be.set(b.p1R, b.sp1R, (long long)L2 * b.P1, (T)1, n);
+      for (int c = L2 - 1; c >= 0; --c)
+        s1_right(r, c, p1R(c), b.sp1R, bat(p1R(c + 1), b.sp1R), site(r, c, S), n);
+      if (r == 0) be.amp(b.p1R, b.sp1R, b.lsD + 1, L1 + 1, log_abs, sign, n);
+      T* Lc = b.p1L;
+      T* Ln = b.p1L + b.P1;
+      be.set(b.p1L, b.sp1L, 0, (T)1, n);
+      for (int c = 0; c < L2; ++c) {
+        if (O) {
+          s1_env(r, c, bat(Lc, b.sp1L), bat(p1R(c + 1), b.sp1R), n);
+          be.writeO(O, No, ooff[r * L2 + c], b.envo, b.D4, szs(r, c), b.p1R, b.sp1R, n);
+        }
+        if (c + 1 < L2) {
+          for (int layer = 0; layer < 2; ++layer) {
+            be.sel(ElemSel{S, N, r * L2 + c, r * L2 + c + 1, 1 + layer, b.si, b.sj, b.valid}, n);
+            s1_left(r, c, b.m0, b.P2, bat(Lc, b.sp1L), site_sel(r, c, b.si), n);
+            s1_left(r, c + 1, b.m1, b.P2, bat(b.m0, b.P2), site_sel(r, c + 1, b.sj), n);
+            be.dot(OpDot<T>{b.m1, b.P2, p1R(c + 2), b.sp1R, s1_len(r, c + 2), b.num}, n);
+            be.ratio(b.num, b.p1R, b.sp1R, b.valid, 0.5 * J1, layer == 0 ? es : ea, n);
+          }
+          s1_left(r, c, Ln, b.sp1L, bat(Lc, b.sp1L), site(r, c, S), n);
+          T* t = Lc;
+          Lc = Ln;
+          Ln = t;
+        }
+      }
+      if (r + 1 < L1) {
+        be.set(b.p2R, b.sp2R, (long long)L2 * b.P2, (T)1, n);
+        for (int c = L2 - 1; c >= 0; --c)
+          s2_right(r, c, p2R(c), b.sp2R, bat(p2R(c + 1), b.sp2R), site(r, c, S), site(r + 1, c, S), n);
+        T* L2c = b.p2L;
+        T* L2n = b.p2L + b.P2;
+        be.set(b.p2L, b.sp2L, 0, (T)1, n);
+        for (int c = 0; c < L2; ++c) {
+          int i = r * L2 + c, j = i + L2;
+          for (int layer = 0; layer < 2; ++layer) {
+            be.sel(ElemSel{S, N, i, j, 1 + layer, b.si, b.sj, b.valid}, n);
+            s2_left(r, c, b.m0, b.P2, bat(L2c, b.sp2L), site_sel(r, c, b.si), site_sel(r + 1, c, b.sj), n);
+            be.dot(OpDot<T>{b.m0, b.P2, p2R(c + 1), b.sp2R, s2_len(r, c + 1), b.num}, n);
+            be.ratio(b.num, b.p2R, b.sp2R, b.valid, 0.5 * J1, layer == 0 ? es : ea, n);
+          }
+          if (J2 != 0.0 && c + 1 < L2) {
+            for (int diag = 0; diag < 2; ++diag) {
+              int a = diag == 0 ? r * L2 + c : r * L2 + c + 1;
+              int bb = diag == 0 ? (r + 1) * L2 + c + 1 : (r + 1) * L2 + c;
+              for (int layer = 0; layer < 2; ++layer) {
+                be.sel(ElemSel{S, N, a, bb, 1 + layer, b.si, b.sj, b.valid}, n);
+                // columns c and c+1 of both rows with the two changed sites
+                Operand<T> s00 = diag == 0 ? site_sel(r, c, b.si) : site(r, c, S);
+                Operand<T> s10 = diag == 0 ? site(r + 1, c, S) : site_sel(r + 1, c, b.sj);
+                Operand<T> s01 = diag == 0 ? site(r, c + 1, S) : site_sel(r, c + 1, b.si);
+                Operand<T> s11 = diag == 0 ? site_sel(r + 1, c + 1, b.sj) : site(r + 1, c + 1, S);
+                s2_left(r, c, b.m0, b.P2, bat(L2c, b.sp2L), s00, s10, n);
+                s2_left(r, c + 1, b.m1, b.P2, bat(b.m0, b.P2), s01, s11, n);
+                be.dot(OpDot<T>{b.m1, b.P2, p2R(c + 2), b.sp2R, s2_len(r, c + 2), b.num}, n);
+                be.ratio(b.num, b.p2R, b.sp2R, b.valid, 0.5 * J2, layer == 0 ? es : ea, n);
+              }
+            }
+          }
+          s2_left(r, c, L2n, b.sp2L, bat(L2c, b.sp2L), site(r, c, S), site(r + 1, c, S), n);
+          T* t = L2c;
+          L2c = L2n;
+          L2n = t;
+        }
+        if (!cached)
+          compress(uprow(r), b.sU, shp.up[r], false, r, S, uprow(r + 1), b.sU, b.lsU, 1, n);
+      }
+    }
+  }
+
+  // -------------------------------------------------------------------- Metropolis
+  void mc(uint8_t* S, int n, int p, uint64_t seed, int chain0, uint32_t sweep, int* acc,
+          int* prop) {
+    build_down(S, n);
+    trivial(uprow(0), b.sU, n);
+    for (int r = 0; r < L1; ++r) {
+      be.set(b.p1R, b.sp1R, (long long)L2 * b.P1, (T)1, n);
+      for (int c = L2 - 1; c >= 0; --c)
+        s1_right(r, c, p1R(c), b.sp1R, bat(p1R(c + 1), b.sp1R), site(r, c, S), n);
+      T* Lc = b.p1L;
+      T* Ln = b.p1L + b.P1;
+      be.set(b.p1L, b.sp1L, 0, (T)1, n);
+      // P = Lc x column c at the current S (m0); X, Y proposals (m2, m3); Q = P x column c+1 (m1)
+      s1_left(r, 0, b.m0, b.P2, bat(Lc, b.sp1L), site(r, 0, S), n);
+      for (int c = 0; c < L2; ++c) {
+        int i = r * L2 + c;
+        be.dot(OpDot<T>{b.m0, b.P2, p1R(c + 1), b.sp1R, s1_len(r, c + 1), b.den}, n);
+        be.sel(ElemSel{S, N, i, -1, 0, b.si, b.sj, b.valid}, n);
+        s1_left(r, c, b.m2, b.P2, bat(Lc, b.sp1L), site_sel(r, c, b.si), n);
+        be.dot(OpDot<T>{b.m2, b.P2, p1R(c + 1), b.sp1R, s1_len(r, c + 1), b.num}, n);
+        be.accept(ElemAccept<T>{S, N, i, -1, b.si, b.sj, b.valid, b.num, b.den, p, seed, chain0,
+                                sweep, (uint32_t)(8 * i), acc, prop, b.accepted}, n);
+        be.copy_masked(b.m0, b.P2, b.m2, b.P2, s1_len(r, c + 1), b.accepted, n);
+        if (c + 1 < L2) {
+          s1_left(r, c + 1, b.m1, b.P2, bat(b.m0, b.P2), site(r, c + 1, S), n);
+          be.dot(OpDot<T>{b.m1, b.P2, p1R(c + 2), b.sp1R, s1_len(r, c + 2), b.den}, n);
+          for (int layer = 0; layer < 2; ++layer) {
+            be.sel(ElemSel{S, N, i, i + 1, 1 + layer, b.si, b.sj, b.valid}, n);
+            s1_left(r, c, b.m2, b.P2, bat(Lc, b.sp1L), site_sel(r, c, b.si), n);
+            s1_left(r, c + 1, b.m3, b.P2, bat(b.m2, b.P2), site_sel(r, c + 1, b.sj), n);
+            be.dot(OpDot<T>{b.m3, b.P2, p1R(c + 2), b.sp1R, s1_len(r, c + 2), b.num}, n);
+            be.accept(ElemAccept<T>{S, N, i, i + 1, b.si, b.sj, b.valid, b.num, b.den, p, seed,
+                                    chain0, sweep, (uint32_t)(8 * i + 1 + layer), acc, prop,
+                                    b.accepted}, n);
+            be.copy_masked(b.m0, b.P2, b.m2, b.P2, s1_len(r, c + 1), b.accepted, n);
+            be.copy_masked(b.m1, b.P2, b.m3, b.P2, s1_len(r, c + 2), b.accepted, n);
+          }
+        }
+        // advance: left partial past column c is P; the next P is Q
+        be.copy_masked(Ln, b.sp1L, b.m0, b.P2, s1_len(r, c + 1), nullptr, n);
+        T* t = Lc;
+        Lc = Ln;
+        Ln = t;
+        if (c + 1 < L2) be.copy_masked(b.m0, b.P2, b.m1, b.P2, s1_len(r, c + 2), nullptr, n);
+      }
+      if (r + 1 < L1) {
+        be.set(b.p2R, b.sp2R, (long long)L2 * b.P2, (T)1, n);
+        for (int c = L2 - 1; c >= 0; --c)
+          s2_right(r, c, p2R(c), b.sp2R, bat(p2R(c + 1), b.sp2R), site(r, c, S), site(r + 1, c, S), n);
+        T* L2c = b.p2L;
+        T* L2n = b.p2L + b.P2;
+        be.set(b.p2L, b.sp2L, 0, (T)1, n);
+        for (int c = 0; c < L2; ++c) {
+          int i = r * L2 + c, j = i + L2;
+          s2_left(r, c, b.m0, b.P2, bat(L2c, b.sp2L), site(r, c, S), site(r + 1, c, S), n);
+          be.dot(OpDot<T>{b.m0, b.P2, p2R(c + 1), b.sp2R, s2_len(r, c + 1), b.den}, n);
+          for (int layer = 0; layer < 2; ++layer) {
+            be.sel(ElemSel{S, N, i, j, 1 + layer, b.si, b.sj, b.valid}, n);
+            s2_left(r, c, b.m1, b.P2, bat(L2c, b.sp2L), site_sel(r, c, b.si), site_sel(r + 1, c, b.sj), n);
+            be.dot(OpDot<T>{b.m1, b.P2, p2R(c + 1), b.sp2R, s2_len(r, c + 1), b.num}, n);
+            be.accept(ElemAccept<T>{S, N, i, j, b.si, b.sj, b.valid, b.num, b.den, p, seed, chain0,
+                                    sweep, (uint32_t)(8 * i + 3 + layer), acc, prop, b.accepted}, n);
+            be.copy_masked(b.m0, b.P2, b.m1, b.P2, s2_len(r, c + 1), b.accepted, n);
+          }
+          be.copy_masked(L2n, b.sp2L, b.m0, b.P2, s2_len(r, c + 1), nullptr, n);
+          T* t = L2c;
+          L2c = L2n;
+          L2n = t;
+        }
+        compress(uprow(r), b.sU, shp.up[r], false, r, S, uprow(r + 1), b.sU, b.lsU, 1, n);
+      }
+    }
+  }
+};
+
+}  // namespace pv
+
+namespace pv {
+
+// Bonds of Eq. 12 as (site i, site j, coupling) lists, the diagonal part of E_loc.
+inline void bond_lists(int L1, int L2, double J1, double J2, std::vector<int>& bi,
+                       std::vector<int>& bj, std::vector<double>& bJ) {
+  bi.clear();
+  bj.clear();
+  bJ.clear();
+  for (int r = 0; r < L1; ++r)
+    for (int c = 0; c + 1 < L2; ++c) {
+      bi.push_back(r * L2 + c);
+      bj.push_back(r * L2 + c + 1);
+      bJ.push_back(J1);
+    }
+  for (int r = 0; r + 1 < L1; ++r)
+    for (int c = 0; c < L2; ++c) {
+      bi.push_back(r * L2 + c);
+      bj.push_back((r + 1) * L2 + c);
+      bJ.push_back(J1);
+    }
+  if (J2 != 0.0)
+    for (int r = 0; r + 1 < L1; ++r)
+      for (int c = 0; c + 1 < L2; ++c) {
+        bi.push_back(r * L2 + c);
+        bj.push_back((r + 1) * L2 + c + 1);
+        bJ.push_back(J2);
+        bi.push_back(r * L2 + c + 1);
+        bj.push_back((r + 1) * L2 + c);
+        bJ.push_back(J2);
+      }
+}
+
+}  // namespace pv
+
+#if defined(__CUDACC__)
+namespace pv {
+
+constexpr int BT = 256;   // threads of the per-sample blocks
+
+template <typename T>
+__global__ void __launch_bounds__(256) kb_ein(MSpec m, T* out, long long os, Operand<T> A,
+                                              Operand<T> B, int n, int quad) {
+  int s = blockIdx.y;
+  if (s >= n) return;
+  const T* pa = A.at(s);
+  const T* pb = B.at(s);
+  T* po = out + (long long)s * os;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (quad) {
+    int idx = t << 2;
+    if (idx < m.total) ein_quad(m, po, pa, pb, idx);
+  } else {
+    if (t < m.total) ein_one(m, po, pa, pb, t);
+  }
+}
+
+// Batched strided GEMM: one thread block computes a TM x TN tile of G samples'
+// contractions (G > 1 when one sample's tile is smaller than the block); operand chunks
+// of KC contraction indices are gathered into shared memory (each element loaded once per
+// tile) and every thread accumulates a 4 x 4 register tile.  The index maps are the same
+// for every sample and are built once per block.
+template <typename T>
+__global__ void __launch_bounds__(256) kb_gemm(GSpec g, T* C, long long cs, Operand<T> A,
+                                               Operand<T> B, int n, int TM, int TN, int KC,
+                                               int tilesN, int G) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const int tid = threadIdx.x;
+  const int tm = blockIdx.x / tilesN, tn = blockIdx.x % tilesN;
+  const int m0 = tm * TM, n0 = tn * TN;
+  const int chunkA = KC * TM, chunkB = KC * TN;
+  T* As = (T*)dyn;                  // [G][KC][TM]
+  T* Bs = As + G * chunkA;          // [G][KC][TN]
+  int* rowA = (int*)(Bs + G * chunkB);
+  int* rowC = rowA + TM;
+  int* colB = rowC + TM;
+  int* colC = colB + TN;
+  int* kAo = colC + TN;
+  int* kBo = kAo + g.K;
+  for (int i = tid; i < TM; i += 256) {
+    int m = m0 + i;
+    if (m < g.M) gemm_offsets(m, g.nm, g.ms, g.mA, g.mC, rowA[i], rowC[i]);
+    else rowA[i] = rowC[i] = -1;
+  }
+  for (int i = tid; i < TN; i += 256) {
+    int c = n0 + i;
+    if (c < g.N) gemm_offsets(c, g.nn, g.ns, g.nB, g.nC, colB[i], colC[i]);
+    else colB[i] = colC[i] = -1;
+  }
+  for (int k = tid; k < g.K; k += 256) gemm_offsets(k, g.nk, g.ks, g.kA, g.kB, kAo[k], kBo[k]);
+  __syncthreads();
+  const int tnx = TN >> 2;
+  const int per = (TM >> 2) * tnx;          // compute threads per sample
+  const int slot = tid / per, loc = tid - slot * per;
+  const int tx = loc % tnx, ty = loc / tnx;
+  for (int sbase = blockIdx.y * G; sbase < n; sbase += gridDim.y * G) {
+    const int ns = min(G, n - sbase);
+    const int s = sbase + slot;
+    const bool comp = slot < ns;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int k0 = 0; k0 < g.K; k0 += KC) {
+      for (int idx = tid; idx < ns * chunkA; idx += 256) {
+        int gs = idx / chunkA, r = idx - gs * chunkA;
+        int kk = r / TM, mm = r - kk * TM, k = k0 + kk;
+        As[idx] = (k < g.K && rowA[mm] >= 0) ? A.at(sbase + gs)[rowA[mm] + kAo[k]] : (T)0;
+      }
+      for (int idx = tid; idx < ns * chunkB; idx += 256) {
+        int gs = idx / chunkB, r = idx - gs * chunkB;
+        int kk = r / TN, nn = r - kk * TN, k = k0 + kk;
+        Bs[idx] = (k < g.K && colB[nn] >= 0) ? B.at(sbase + gs)[colB[nn] + kBo[k]] : (T)0;
+      }
+      __syncthreads();
+      if (comp) {
+        const T* as = As + slot * chunkA;
+        const T* bs = Bs + slot * chunkB;
+        const int kend = min(KC, g.K - k0);
+        for (int kk = 0; kk < kend; ++kk) {
+          T a[4], b[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = as[kk * TM + ty * 4 + i];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) b[j] = bs[kk * TN + tx * 4 + j];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+      }
+      __syncthreads();
+    }
+    if (comp) {
+      T* pc = C + (long long)s * cs;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        int r = rowC[ty * 4 + i];
+        if (r < 0) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          int c = colC[tx * 4 + j];
+          if (c >= 0) pc[r + c] = acc[i][j];
+        }
+      }
+    }
+  }
+}
+
+// Householder factor per sample; the sample's matrix is first copied to shared memory
+// when it fits (use_smem), so the column sweeps run out of shared memory.
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_lq(OpLq<T> op, int n, int use_smem) {
+  __shared__ T red[32];
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* Ws = (T*)dyn;
+  const long long len = (long long)op.m * op.nn;
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    T* W = op.W + (long long)s * op.ws;
+    if (use_smem) {
+      for (long long i = threadIdx.x; i < len; i += blockDim.x) Ws[i] = W[i];
+      __syncthreads();
+      W = Ws;
+    }
+    lq_factor(op.Lf + (long long)s * op.ls, W, op.m, op.nn, red, red);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long cap) {
+  __shared__ T red[32];
+  __shared__ int flag;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* smem = (T*)dyn;
+  T* sig = smem + cap;
+  int* order = (int*)(sig + op.nc + 4);
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    op(s, red, &flag, smem, cap, order, sig);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_norm(OpNorm<T> op, int n) {
+  __shared__ T red[32];
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    op(s, red);
+    __syncthreads();
+  }
+}
+
+// One warp per sample.
+template <typename T>
+__global__ void __launch_bounds__(256) kb_dot(OpDot<T> op, int n) {
+  int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
+  if (s >= n) return;
+  const T* a = op.a + (long long)s * op.as;
+  const T* b = op.b + (long long)s * op.bs;
+  T acc = 0;
+  for (long long k = lane; k < op.len; k += 32) acc += a[k] * b[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) op.out[s] = acc;
+}
+
+template <typename F>
+__global__ void kb_elem(F f, int n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) f(s);
+}
+
+template <typename T>
+__global__ void kb_set(T* x, long long xs, long long off, T v, int n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) x[(long long)s * xs + off] = v;
+}
+
+__global__ void kb_copyd(double* x, long long xs, int dst, int src, int n) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n) x[(long long)s * xs + dst] = x[(long long)s * xs + src];
+}
+
+template <typename T>
+__global__ void kb_copy(T* dst, long long ds, const T* src, long long ss, long long len,
+                        const int8_t* mask, int n) {
+  int s = blockIdx.y;
+  if (s >= n || (mask && !mask[s])) return;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < len) dst[(long long)s * ds + k] = src[(long long)s * ss + k];
+}
+
+template <typename T, typename OT>
+__global__ void kb_O(OT* O, long long No, long long o_off, const T* env, long long es,
+                     long long sz, const T* val, long long vs, int n) {
+  int s = blockIdx.y;
+  if (s >= n) return;
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < sz) O[(long long)s * No + o_off + k] = (OT)((double)env[(long long)s * es + k] / (double)val[(long long)s * vs]);
+}
+
+// Launch back end of the batched runner: one kernel per batched operation on `stream`.
+template <typename T, typename OT>
+struct CudaBE {
+  cudaStream_t st;
+  const int *bi, *bj;
+  const double* bJ;
+  int nb, N;
+  long long trunc_cap;   // elements of the Jacobi work area in shared memory
+  int sms;
+  int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
+
+  static int gx(long long n, int t) { return (int)((n + t - 1) / t); }
+  int gblocks(int n) const { return n < 8 * sms ? n : 8 * sms; }
+
+  void ein(const Spec& raw, const MSpec& m, T* out, long long os, Operand<T> A, Operand<T> B,
+           int n) {
+    GSpec gs = gemm_spec(raw);
+    if (gs.ok && gs.K > 1) {
+      int Np = ((gs.N + 3) / 4) * 4;
+      int TN = 4;
+      while (TN < Np && TN < 64) TN <<= 1;
+      int TM = 4096 / TN;
+      int Mp = ((gs.M + 3) / 4) * 4;
+      if (Mp < TM) TM = Mp;
+      int G = 256 / ((TM / 4) * (TN / 4));   // samples per block when one tile is small
+      if (G < 1) G = 1;
+      int budget = (int)(6144 * 4 / sizeof(T));   // 24 KB of operand tiles
+      int KC = budget / (G * (TM + TN));
+      KC = KC < 1 ? 1 : (KC > 32 ? 32 : KC);
+      if (KC > gs.K) KC = gs.K;
+      int tilesN = (gs.N + TN - 1) / TN, tilesM = (gs.M + TM - 1) / TM;
+      size_t bytes = (size_t)G * KC * (TM + TN) * sizeof(T) +
+                     (size_t)(2 * TM + 2 * TN + 2 * gs.K) * 4;
+      int gy = (n + G - 1) / G;
+      if (gy > 65535) gy = 65535;
+      dim3 gr(tilesN * tilesM, gy);
+      kb_gemm<T><<<gr, 256, bytes, st>>>(gs, out, os, A, B, n, TM, TN, KC, tilesN, G);
+      return;
+    }
+    int quad = quad_ok(m) ? 1 : 0;
+    long long work = quad ? (m.total >> 2) : m.total;
+    dim3 g(gx(work, 256), n);
+    kb_ein<T><<<g, 256, 0, st>>>(m, out, os, A, B, n, quad);
+  }
+  void lq(OpLq<T> op, int n) {
+    size_t bytes = (size_t)op.m * op.nn * sizeof(T);
+    int use = bytes <= (size_t)lq_smem_max ? 1 : 0;
+    kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use);
+  }
+  void trunc(OpTrunc<T> op, int n) {
+    size_t bytes = (size_t)trunc_cap * sizeof(T) + (size_t)(op.nc + 4) * sizeof(T) +
+                   (size_t)(op.nc + 4) * sizeof(int) + 16;
+    kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap);
+  }
+  void norm(OpNorm<T> op, int n) { kb_norm<T><<<gblocks(n), BT, 0, st>>>(op, n); }
+  void dot(OpDot<T> op, int n) { kb_dot<T><<<gx(n, 8), 256, 0, st>>>(op, n); }
+  void set(T* x, long long xs, long long off, T v, int n) { kb_set<T><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n); }
+  void setd(double* x, long long xs, long long off, double v, int n) {
+    kb_set<double><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n);
+  }
+  void copyd(double* x, long long xs, int dst, int src, int n) {
+    kb_copyd<<<gx(n, 256), 256, 0, st>>>(x, xs, dst, src, n);
+  }
+  void copy_masked(T* dst, long long ds, const T* src, long long ss, long long len,
+                   const int8_t* mask, int n) {
+    dim3 g(gx(len, 256), n);
+    kb_copy<T><<<g, 256, 0, st>>>(dst, ds, src, ss, len, mask, n);
+  }
+  void diag(const uint8_t* S, int n, double* es, double* ea) {
+    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemDiag{S, N, nb, bi, bj, bJ, es, ea}, n);
+  }
+  void amp(const T* val, long long vs, const double* lsd, int lstride, double* la, int8_t* sg, int n) {
+    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemAmp<T>{val, vs, lsd, lstride, la, sg}, n);
+  }
+  void writeO(OT* O, long long No, long long o_off, const T* env, long long es, long long sz,
+              const T* val, long long vs, int n) {
+    dim3 g(gx(sz, 256), n);
+    kb_O<T, OT><<<g, 256, 0, st>>>(O, No, o_off, env, es, sz, val, vs, n);
+  }
+  void sel(ElemSel f, int n) { kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n); }
+  void ratio(const T* num, const T* den, long long dens, const int8_t* valid, double coef,
+             double* e, int n) {
+    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemRatio<T>{num, den, dens, valid, coef, e}, n);
+  }
+  void accept(ElemAccept<T> f, int n) { kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n); }
+};
+
+}  // namespace pv
+#endif

@@ -46,7 +46,7 @@ CASES = [  # (L1, L2, D, chi, J2, n): exact chi, truncated chi, ragged tails, NN
 ]
 
 
-MODES = [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_WIDE]
+MODES = [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_WIDE, binding.PEPS_BLOCKS_BATCHED]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -61,13 +61,14 @@ def test_eval_fp64_matches_oracle(case, mode):
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-9)
 
 
-def test_eval_fp64_heis8_shape():
+@pytest.mark.parametrize("mode", [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_BATCHED])
+def test_eval_fp64_heis8_shape(mode):
     # 8x8, D=4, chi=16: the bench workload's contraction sizes (truncating chi), sampled rows.
     L, D, chi = 8, 4, 16
     lat = Lattice(L, L, D)
     th = wl.random_theta(L, L, D, seed=81, scale=0.2, diag_bias=1.0)
     S = wl.random_configs(L, L, 3, seed=82)
-    ctx = _ctx(L, L, D, chi, 3, mode=binding.PEPS_BLOCKS_NARROW)
+    ctx = _ctx(L, L, D, chi, 3, mode=mode)
     ctx.set_theta(th)
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-10, 1e-9, 1e-8)
 
@@ -129,12 +130,13 @@ def test_mc_sweep_matches_oracle(p, mode):
     assert ctx.sweeps_done == 5
 
 
-def test_mc_sweep_truncated_chi_matches_oracle():
+@pytest.mark.parametrize("mode", [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_BATCHED])
+def test_mc_sweep_truncated_chi_matches_oracle(mode):
     L1, L2, D, chi, n = 4, 4, 3, 4, 6
     lat = Lattice(L1, L2, D)
     th = wl.random_theta(L1, L2, D, seed=17, scale=0.4, diag_bias=1.0)
     S0 = wl.random_configs(L1, L2, n, seed=18)
-    ctx = _ctx(L1, L2, D, chi, n, seed=5)
+    ctx = _ctx(L1, L2, D, chi, n, seed=5, mode=mode)
     ctx.set_theta(th)
     ctx.set_configs(S0)
     ctx.mc_sweep(1, 2)
@@ -248,12 +250,13 @@ def test_checkpoint_resume_is_bit_exact(tmp_path):
     assert e.value.code == binding.PEPS_ECORRUPT
 
 
+@pytest.mark.parametrize("mode", [binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_BATCHED])
 @pytest.mark.parametrize("prec", [binding.PEPS_FP64, binding.PEPS_FP32])
-def test_eval_with_cached_up_environments_is_identical(prec):
+def test_eval_with_cached_up_environments_is_identical(prec, mode):
     # eval_chains after a sweep reuses the sweep's up environments; the values must be the
     # same bits as an evaluation of the same configurations from scratch.
     L1, L2, D, chi, n = 5, 4, 3, 4, 12
-    ctx = _ctx(L1, L2, D, chi, n, J2=0.5, prec=prec, seed=3, noise=0.05)
+    ctx = _ctx(L1, L2, D, chi, n, J2=0.5, prec=prec, seed=3, noise=0.05, mode=mode)
     ctx.mc_sweep(2, p=2)
     S = ctx.get_configs()
     la0, sg0, es0, ea0, O0 = ctx.eval_batch(None)
