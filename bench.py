@@ -94,6 +94,32 @@ def measured_peaks():
         return {}
 
 
+def kernel_roofline(kstats, peaks, prec, binding):
+    """Roofline of the dominant kernel of the timed region from the library's per-launch CUDA
+    events: achieved = its algorithmic bytes (or flops) per launch / its mean launch time."""
+    total = sum(v[1] for v in kstats.values()) or 1.0
+    kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
+                   "GB_s": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None}
+               for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])[:12]}
+    if not kstats:
+        return None, kernels
+    name, (n, ms, nbytes, flops) = max(kstats.items(), key=lambda kv: kv[1][1])
+    hbm = peaks.get("hbm_gbs")
+    if nbytes > 0:
+        peak, src = (hbm, "measured") if hbm else (6800.0, "fallback")
+        achieved = nbytes / n / (ms / n / 1e3) / 1e9
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "bytes_per_launch": nbytes / n, "mean_launch_us": ms / n * 1e3,
+                "launches": n, "share_of_timed_kernels": ms / total,
+                "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % src}, kernels
+    peak = PEAK_FP64_TFLOPS if prec == binding.PEPS_FP64 else PEAK_FP32_TFLOPS
+    achieved = flops / (ms / 1e3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": "derived: FMA/clk/SM x 152 SMs x 2070 MHz"}, kernels
+
+
 def cooled_state(ctx, steps, tau, p_switch_t):
     """Cools the fresh context for `steps` SR steps (p = 1 while beta_obs < 0.3)."""
     t = 0.0
@@ -122,7 +148,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     wl = WORKLOADS[args.workload]
-    prec = binding.PEPS_FP32 if args.precision == "fp32" else binding.PEPS_FP64
+    prec = {"fp32": binding.PEPS_FP32, "tf32": binding.PEPS_TF32, "fp64": binding.PEPS_FP64}[args.precision]
     stream = torch.cuda.Stream()
     n = args.chains or wl.n_samples
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
@@ -142,6 +168,10 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # CUDA events on the context's stream around every launch of the batched GEMM kernels
+    # (--profile-all: of every kernel, which costs a few per cent of the step time)
+    ctx.profile(True, gemm_only=not args.profile_all)
+    launches0 = ctx.launches()
     e_start, e_end = ev(), ev()
     e_start.record(stream)
     for _ in range(args.steps):
@@ -167,6 +197,9 @@ def run_ours(args):
     e_end.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    kstats = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launches() - launches0
     total_ms = e_start.elapsed_time(e_end)
     if ws > 1:
         t = torch.tensor([total_ms], device="cuda")
@@ -194,13 +227,10 @@ def run_ours(args):
     e2e_step = statistics.median(e2e_ms)
 
     fp64_check = None
-    if prec == binding.PEPS_FP32 and not args.no_fp64_check:
+    if prec != binding.PEPS_FP64 and not args.no_fp64_check:
         fp64_check = compare_fp64(ctx, wl, binding, min(n, args.fp64_chains), stream, torch)
     peaks = measured_peaks()
-    dom_flops = statistics.mean(eval_flops)
-    dom_ms = statistics.mean(eval_ms)
-    achieved = dom_flops / (dom_ms / 1e3) / 1e12
-    peak = PEAK_FP64_TFLOPS if prec == binding.PEPS_FP64 else PEAK_FP32_TFLOPS
+    roofline, kernels = kernel_roofline(kstats, peaks, prec, binding)
     step_sorted = sorted(step_ms)
     out = {
         "metric": METRIC,
@@ -213,7 +243,8 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if prec == binding.PEPS_FP64 else "f32",
+        "dtype": {binding.PEPS_FP64: "f64", binding.PEPS_FP32: "f32",
+                  binding.PEPS_TF32: "tf32 (contractions; f32 storage, f64 SR)"}[prec],
         "data": "synthetic (seeded beta=0 PEPS cooled in-run; no dataset)",
         "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg J1={wl.J1} J2={wl.J2}, d2=4, "
                                f"D={wl.D}, chi={wl.chi}, chains={n} per GPU",
@@ -229,20 +260,15 @@ def run_ours(args):
         "eval_gflop_per_sample": statistics.mean(eval_flops) / n / 1e9,
         "jacobi_sweeps_per_sample": statistics.mean(jac),
         "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"],
-        "roofline": {"kernel": "k_eval (per-sample contraction)", "bound": "alu",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "peak_source": "derived: %s FMA/clk/SM x 152 SMs x 2070 MHz" % ("2 FP64" if prec == 0 else "128 FP32")},
+        "roofline": roofline,
+        "kernels": kernels,
         "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(ctx.Np * 8 + n * ctx.N),
                 "d2h_bytes_per_step": int(ctx.Np * 8 + n * ctx.N)},
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "clocks": clk,
         "fp64_check": fp64_check,
     }
-    # kernel launches per step: 1 k_mc + 1 k_eval + SR (weights, colsum x2, dot, init, dot,
-    # 6 per CG iteration, update) -- the CUDA kernels of this library
-    out["gpu_launches"] = int(args.steps * (2 + 6 + 6 * statistics.mean(cg_its) + 1))
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, n, args.cpu_samples)
     ctx.close()
@@ -253,7 +279,7 @@ def run_ours(args):
 
 
 def compare_fp64(ctx, wl, binding, m, stream, torch):
-    """The FP32 path against the FP64 path on the same parameters and the same m chain
+    """The mixed-precision path against the FP64 path on the same parameters and the same m chain
     configurations: amplitude and local-energy differences, and the evaluation throughput
     of both paths on those configurations."""
     import numpy as np
@@ -264,7 +290,7 @@ def compare_fp64(ctx, wl, binding, m, stream, torch):
                           stream=ctypes_stream(stream))
     ref.set_theta(th)
     out = {}
-    for name, c in (("fp32", ctx), ("fp64", ref)):
+    for name, c in (("mixed", ctx), ("fp64", ref)):
         c.eval_batch(S[: min(m, 8)], with_O=False)   # warm-up
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -272,16 +298,16 @@ def compare_fp64(ctx, wl, binding, m, stream, torch):
         torch.cuda.synchronize()
         out[name] = (la, sg, es + ea, m / (time.perf_counter() - t0))
     ref.close()
-    la32, sg32, e32, r32 = out["fp32"]
+    la32, sg32, e32, r32 = out["mixed"]
     la64, sg64, e64, r64 = out["fp64"]
     N = wl.L * wl.L
     return {"chains": m, "max_abs_dlog_amp": float(np.max(np.abs(la32 - la64))),
             "sign_mismatch": int(np.sum(sg32 != sg64)),
-            "E_site_fp32": float(np.mean(e32) / (2 * N)), "E_site_fp64": float(np.mean(e64) / (2 * N)),
+            "E_site_mixed": float(np.mean(e32) / (2 * N)), "E_site_fp64": float(np.mean(e64) / (2 * N)),
             "dE_site": float(abs(np.mean(e32) - np.mean(e64)) / (2 * N)),
             "max_dEloc_site": float(np.max(np.abs(e32 - e64)) / (2 * N)),
-            "eval_samples_per_s_fp32": r32, "eval_samples_per_s_fp64": r64,
-            "speedup_fp32_over_fp64": r32 / r64}
+            "eval_samples_per_s_mixed": r32, "eval_samples_per_s_fp64": r64,
+            "speedup_mixed_over_fp64": r32 / r64}
 
 
 def ctypes_stream(stream):
@@ -425,7 +451,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heis8")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "fp64"])
+    ap.add_argument("--profile-all", action="store_true",
+                    help="time every kernel of the timed region (default: the GEMM kernels)")
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0, help="persistent blocks of the sample kernels (0 = auto)")
     ap.add_argument("--block-mode", default="auto", choices=list(BLOCK_MODES))

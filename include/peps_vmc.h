@@ -48,12 +48,17 @@ extern "C" {
 #define PEPS_ENOTFINITE (-5) /* non-finite amplitude, energy or CG scalar */
 #define PEPS_ECORRUPT (-6)   /* checkpoint unreadable, of another problem, or failing its checksum */
 #define PEPS_EIO (-7)        /* checkpoint file could not be written */
+#define PEPS_ETIMEOUT (-8)   /* a bounded device wait ran out; the call's results are invalid */
 
 /* Arithmetic of the per-sample contraction (environment, amplitude, E_loc, O).  The
  * log-amplitude accumulation, the SR reductions and CG, and the observables are float64
  * in every mode. */
 #define PEPS_FP64 0 /* float64 throughout */
 #define PEPS_FP32 1 /* float32 contraction and truncation, float32 O storage */
+#define PEPS_TF32 2 /* as PEPS_FP32, but the GEMM-shaped environment and strip contractions
+                       of the batched engine run on the tensor cores (tcgen05, TF32 operands
+                       rounded to nearest, FP32 accumulation); needs block_mode
+                       PEPS_BLOCKS_BATCHED, which PEPS_BLOCKS_AUTO then selects */
 
 #define PEPS_MODEL_J1J2 0 /* Eq. 12: J1 sum_<ij> S_i.S_j + J2 sum_<<ij>> S_i.S_j */
 
@@ -68,7 +73,7 @@ typedef struct {
   int D;             /* PEPS bond dimension, 1 <= D <= 8 */
   int chi;           /* boundary-MPS bond dimension, 1 <= chi <= 64 */
   int n_chains;      /* chains advanced per sweep and samples per SR step, >= 1 */
-  int precision;     /* PEPS_FP64 | PEPS_FP32 */
+  int precision;     /* PEPS_FP64 | PEPS_FP32 | PEPS_TF32 */
   double init_noise; /* amplitude a of the U[-a, a] perturbation of the zero entries */
   uint64_t seed;     /* Philox key for the perturbation, the chain starts and Metropolis */
   int n_blocks;      /* persistent blocks of the sample kernels; 0 = automatic */
@@ -173,6 +178,27 @@ double peps_time(const peps_ctx* ctx);
 /* Device counters of the last peps_eval_batch / peps_mc_sweep launch: algorithmic
  * flops (contractions, Householder, Jacobi), Jacobi sweeps. */
 int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
+
+/* Kernel launches this context has made since peps_init (every kernel of the library). */
+long long peps_launches(const peps_ctx* ctx);
+
+/* Per-kernel statistics for roofline reports.  peps_profile(ctx, 1) clears them and starts
+ * bracketing every launch of the context with CUDA events on its stream; peps_profile(ctx,
+ * 2) does the same for the batched GEMM kernels only (kb_gemm_tc, kb_gemm: fewer events in
+ * the stream); peps_profile(ctx, 0) stops.  peps_profile_read synchronises the stream and
+ * returns, per kernel name, the launches, the summed event time and the algorithmic bytes
+ * (each operand read once, each result written once) and flops of those launches; up to
+ * `cap` entries are written to `out` (caller-owned) and the number of kernels to *n_out.
+ * EINVAL on bad arguments. */
+typedef struct {
+  char name[32];
+  long long launches;
+  double ms;
+  double bytes;
+  double flops;
+} peps_kernel_stat;
+int peps_profile(peps_ctx* ctx, int enable);
+int peps_profile_read(peps_ctx* ctx, peps_kernel_stat* out, int cap, int* n_out);
 
 /* ---------------------------------------------------------------- serving loop
  *

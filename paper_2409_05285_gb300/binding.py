@@ -20,8 +20,10 @@ PEPS_ESTATE = -4
 PEPS_ENOTFINITE = -5
 PEPS_ECORRUPT = -6
 PEPS_EIO = -7
+PEPS_ETIMEOUT = -8
 PEPS_FP64 = 0
 PEPS_FP32 = 1
+PEPS_TF32 = 2
 PEPS_MODEL_J1J2 = 0
 PEPS_BLOCKS_AUTO = 0
 PEPS_BLOCKS_NARROW = 1
@@ -35,7 +37,7 @@ EXPORTS = [
     "peps_last_counters", "peps_free", "peps_last_error", "peps_version", "peps_checkpoint",
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
-    "peps_srv_metrics", "peps_srv_free",
+    "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
 ]
 
 
@@ -45,6 +47,11 @@ class Params(ctypes.Structure):
                 ("chi", ctypes.c_int), ("n_chains", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init_noise", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_blocks", ctypes.c_int), ("block_mode", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double), ("flops", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -121,6 +128,10 @@ def load(path=None):
     lib.peps_last_error.argtypes = [vp]
     lib.peps_last_error.restype = ctypes.c_char_p
     lib.peps_version.restype = ctypes.c_char_p
+    lib.peps_launches.argtypes = [vp]
+    lib.peps_launches.restype = ctypes.c_longlong
+    lib.peps_profile.argtypes = [vp, ip]
+    lib.peps_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ip)]
     _lib = lib
     return lib
 
@@ -163,6 +174,24 @@ class Context:
         if rc not in allow:
             raise PepsError(rc, self.lib.peps_last_error(self.ctx).decode())
         return rc
+
+    def launches(self):
+        """Kernel launches this context has made so far."""
+        return int(self.lib.peps_launches(self.ctx))
+
+    def profile(self, enable, gemm_only=False):
+        """Starts (True: cleared) or stops per-kernel event timing of this context; with
+        gemm_only, only the batched GEMM kernels are timed."""
+        self._check(self.lib.peps_profile(self.ctx, (2 if gemm_only else 1) if enable else 0))
+
+    def profile_read(self):
+        """Per-kernel {name: (launches, ms, bytes, flops)} since profiling started."""
+        cap = 64
+        buf = (KernelStat * cap)()
+        n = ctypes.c_int()
+        self._check(self.lib.peps_profile_read(self.ctx, buf, cap, ctypes.byref(n)))
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].ms, buf[i].bytes, buf[i].flops)
+                for i in range(min(cap, n.value))}
 
     def close(self):
         if self.ctx:

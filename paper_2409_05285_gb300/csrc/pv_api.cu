@@ -193,6 +193,7 @@ namespace {
 // Type-erased batched engine of a context (float64 or float32 arithmetic).
 struct BatchIface {
   virtual ~BatchIface() {}
+  virtual int* err_flag() = 0;
   virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
@@ -209,6 +210,7 @@ struct BatchImpl : BatchIface {
   long long No = 0;
   double *es_tmp = nullptr, *ea_tmp = nullptr;
   BatchImpl() : run(be) {}
+  int* err_flag() override { return be.tc_err; }
 
   void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
             bool cached) override {
@@ -289,6 +291,7 @@ struct peps_ctx {
   std::string err;
   std::vector<void*> allocs;
   std::unique_ptr<BatchIface> batch;   // batched engine (block_mode PEPS_BLOCKS_BATCHED)
+  pv::KProf kprof;                      // launch counter, optional per-kernel timing
 };
 
 namespace {
@@ -353,6 +356,17 @@ int ensure_batch(peps_ctx* c, int nb) {
   return PEPS_OK;
 }
 
+// Reads (and clears) the batched engine's device error flag after a synchronised call.
+int batch_status(peps_ctx* c) {
+  int* d = c->batch ? c->batch->err_flag() : nullptr;
+  if (!d) return PEPS_OK;
+  int h = 0;
+  PV_CUDA(c, cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return PEPS_OK;
+  PV_CUDA(c, cudaMemset(d, 0, sizeof(int)));
+  return fail(c, PEPS_ETIMEOUT, "tensor-core contraction: completion wait ran out");
+}
+
 // Launches the evaluation kernel on device buffers.
 int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, double* es,
                 double* ea, void* O, bool use_cache = false) {
@@ -366,14 +380,15 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
     PV_CUDA(c, cudaMemcpyAsync(c->d_flops, &f, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     PV_CUDA(c, cudaStreamSynchronize(c->stream));   // f lives on this stack frame
     PV_CUDA(c, cudaGetLastError());
-    return PEPS_OK;
+    return batch_status(c);
   }
   int grid = std::min(c->nblk, nb);
 #define PV_EVAL_LAUNCH(T, TH, THETA)                                                         \
+  PV_KLAUNCH(&c->kprof, c->stream, "k_eval", 0.0, 0.0,                                      \
   k_eval<T, T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                  \
       g, THETA, dS, nb, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, la, sg, es, ea, (T*)O, \
       c->No, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32, JAC_MAX_SWEEPS, c->d_flops, c->d_jsw,   \
-      c->smem_bytes, (T*)ucache, c->d_ubond, c->ustride, c->ubstride)
+      c->smem_bytes, (T*)ucache, c->d_ubond, c->ustride, c->ubstride))
   if (fp64(c)) {
     if (c->wide) PV_EVAL_LAUNCH(double, WIDE_THREADS, c->d_theta);
     else PV_EVAL_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
@@ -439,6 +454,7 @@ int make_batch_t(peps_ctx* c, int sms) {
     cudaMemcpy(dbJ, bJ.data(), bJ.size() * sizeof(double), cudaMemcpyHostToDevice);
   }
   b->be.st = c->stream;
+  b->be.prof = &c->kprof;
   b->be.bi = dbi;
   b->be.bj = dbj;
   b->be.bJ = dbJ;
@@ -451,6 +467,16 @@ int make_batch_t(peps_ctx* c, int sms) {
     cudaError_t e = cudaFuncSetAttribute(kb_lq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq_max);
     b->be.lq_smem_max = e == cudaSuccess ? lq_max : 48 * 1024;
     if (e != cudaSuccess) cudaGetLastError();
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (P->precision == PEPS_TF32) {
+      if ((rc = dalloc(c, &b->be.tc_err, sizeof(int)))) return rc;
+      cudaError_t e = cudaMemsetAsync(b->be.tc_err, 0, sizeof(int), c->stream);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
+      b->be.tc = true;
+    }
   }
   b->N = c->N;
   b->No = c->No;
@@ -471,6 +497,27 @@ int make_batch_t(peps_ctx* c, int sms) {
   r.sweeps = c->d_jsw;
   r.b.bind(real, chunk, i8, dbl, P->L1, P->L2, P->D, P->chi);
   return PEPS_OK;
+}
+
+// Block layout peps_init takes for automatic mode: the batched engine (measured faster on
+// GB300 in every precision at 8x8, D=4, chi=16) when its per-chain Jacobi work area fits in
+// shared memory, else persistent narrow blocks.  TF32 exists only in the batched engine.
+int resolve_block_mode(const peps_params* P) {
+  if (P->block_mode != PEPS_BLOCKS_AUTO) return P->block_mode;
+  const long long cD = (long long)P->chi * P->D;
+  const size_t real = P->precision == PEPS_FP64 ? 8 : 4;
+  const size_t trunc_bytes = (size_t)(2 * cD * (cD + 1)) * real + (size_t)(cD + 4) * (real + 4) + 16;
+  return trunc_bytes <= 200 * 1024 ? PEPS_BLOCKS_BATCHED : PEPS_BLOCKS_NARROW;
+}
+
+// Device bytes of one chain's batched-engine buffers.
+size_t batched_chain_bytes(const peps_params* P) {
+  std::vector<long long> sz;
+  long long n8 = 0, nd = 0, per = 0;
+  BatchBufs<double>::sizes(P->L1, P->L2, P->D, P->chi, sz, n8, nd);
+  for (long long x : sz) per += x;
+  const size_t real = P->precision == PEPS_FP64 ? 8 : 4;
+  return (size_t)per * real + (size_t)n8 + (size_t)nd * 8 + 16 + 2 * 8;
 }
 
 int make_batch(peps_ctx* c, int sms) {
@@ -496,13 +543,17 @@ void peps_free(peps_ctx* ctx) {
   delete ctx;
 }
 
-int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
-  if (!P || !out) return PEPS_EINVAL;
+int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
+  if (!Pin || !out) return PEPS_EINVAL;
   *out = nullptr;
+  peps_params Pl = *Pin;
+  Pl.block_mode = resolve_block_mode(&Pl);
+  const peps_params* P = &Pl;
+  if (P->precision == PEPS_TF32 && P->block_mode != PEPS_BLOCKS_BATCHED) return PEPS_EINVAL;
   if (P->L1 < 2 || P->L2 < 2 || P->L1 > MAX_L || P->L2 > MAX_L || P->D < 1 || P->D > 8 ||
       P->chi < 1 || P->chi > 64 || P->n_chains < 1 || P->model != PEPS_MODEL_J1J2 ||
-      (P->precision != PEPS_FP64 && P->precision != PEPS_FP32) || P->n_blocks < 0 ||
-      !(P->init_noise >= 0) || P->block_mode < PEPS_BLOCKS_AUTO || P->block_mode > PEPS_BLOCKS_BATCHED)
+      (P->precision != PEPS_FP64 && P->precision != PEPS_FP32 && P->precision != PEPS_TF32) ||
+      P->n_blocks < 0 || !(P->init_noise >= 0) || P->block_mode < PEPS_BLOCKS_AUTO || P->block_mode > PEPS_BLOCKS_BATCHED)
     return PEPS_EINVAL;
   peps_ctx* c = new peps_ctx();
   c->P = *P;
@@ -630,11 +681,11 @@ int peps_init(const peps_params* P, void* stream, peps_ctx** out) {
     e = cudaMemcpyAsync(c->d_o2site, o2site.data(), c->No * sizeof(int), cudaMemcpyHostToDevice,
                         c->stream);
   if (e != cudaSuccess) return bail(fail(c, PEPS_ECUDA, cudaGetErrorString(e)));
-  k_init_theta<<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->N, c->d_toff,
+  PV_KLAUNCH(&c->kprof, c->stream, "k_init_theta", 0.0, 0.0, k_init_theta<<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->N, c->d_toff,
                                                              P->init_noise, P->seed, c->d_theta,
-                                                             c->d_theta_f);
-  k_init_configs<<<grid_for((long long)n * c->N, 256), 256, 0, c->stream>>>(n, c->N, P->seed,
-                                                                            c->d_S);
+                                                             c->d_theta_f));
+  PV_KLAUNCH(&c->kprof, c->stream, "k_init_configs", 0.0, 0.0, k_init_configs<<<grid_for((long long)n * c->N, 256), 256, 0, c->stream>>>(n, c->N, P->seed,
+                                                                            c->d_S));
   e = cudaStreamSynchronize(c->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return bail(fail(c, PEPS_ECUDA, cudaGetErrorString(e)));
@@ -661,14 +712,17 @@ size_t peps_footprint(const peps_params* P) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   ScratchDims sd = scratch_dims(P->L1, P->L2, P->D, P->chi);
   long long sreal = (sd.n_real + 31) & ~31LL, sint = (sd.n_int + 31) & ~31LL;
-  long long nblk = P->n_blocks > 0 ? P->n_blocks : (P->block_mode == PEPS_BLOCKS_WIDE ? sms : 4LL * sms);
-  nblk = std::max(1LL, std::min(nblk, n));
+  const int mode = resolve_block_mode(P);
+  const bool batched = mode == PEPS_BLOCKS_BATCHED;
+  long long nblk = P->n_blocks > 0 ? P->n_blocks : (mode == PEPS_BLOCKS_WIDE ? sms : 4LL * sms);
+  nblk = batched ? 1 : std::max(1LL, std::min(nblk, n));
   long long nch = (n + OTV_CHUNK - 1) / OTV_CHUNK;
   size_t b = 0;
   b += 2 * (N + 1) * 8 + No * 4 + Np * 8 + (real == 4 ? Np * 4 : 0);   // tables, theta
   b += n * N + n * (8 * 3 + 1 + 4 * 2) + (size_t)n * No * real;       // chains, outputs, O
   b += (size_t)nblk * (sreal * real + sint * 4);                       // sample scratch
-  b += (size_t)n * ((long long)P->L1 * P->L2 * sd.ENV * real + (long long)P->L1 * (P->L2 + 1) * 4);
+  if (batched) b += (size_t)n * batched_chain_bytes(P);                 // batched buffers
+  else b += (size_t)n * ((long long)P->L1 * P->L2 * sd.ENV * real + (long long)P->L1 * (P->L2 + 1) * 4);
   b += n * 8 * 3 + 6 * Np * 8 + (real == 4 ? Np * 4 : 0) + 2 * (size_t)nch * Np * 8;   // SR
   return b + (1 << 20);
 }
@@ -695,8 +749,8 @@ int peps_set_theta(peps_ctx* c, const double* host, size_t n) {
   PV_CUDA(c, cudaMemcpyAsync(c->d_theta, host, n * sizeof(double), cudaMemcpyHostToDevice,
                              c->stream));
   if (c->d_theta_f)
-    k_to_real<float><<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->d_theta,
-                                                                   c->d_theta_f);
+    PV_KLAUNCH(&c->kprof, c->stream, "k_to_real", 0.0, 0.0, k_to_real<float><<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->d_theta,
+                                                                   c->d_theta_f));
   PV_CUDA(c, cudaGetLastError());
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_eval = false;
@@ -737,13 +791,15 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
     double f = c->batch->flops;
     PV_CUDA(c, cudaMemcpyAsync(c->d_flops, &f, sizeof(double), cudaMemcpyHostToDevice, c->stream));
     PV_CUDA(c, cudaStreamSynchronize(c->stream));
+    PV_TRY(batch_status(c));
   } else {
 #define PV_MC_LAUNCH(T, TH, THETA)                                                            \
+  PV_KLAUNCH(&c->kprof, c->stream, "k_mc", 0.0, 0.0,                                          \
   k_mc<T, TH><<<grid, TH, c->smem_bytes, c->stream>>>(                                        \
       g, THETA, c->d_S, n, (T*)c->d_scr, c->d_iscr, c->sreal, c->sint, p, c->P.seed,          \
       c->sweeps, n_sweeps, c->d_acc, c->d_prop, fp64(c) ? (T)JTOL_F64 : (T)JTOL_F32,          \
       JAC_MAX_SWEEPS, c->d_flops, c->d_jsw, c->smem_bytes, (T*)c->d_ucache, c->d_ubond,       \
-      c->ustride, c->ubstride)
+      c->ustride, c->ubstride))
   if (fp64(c)) {
     if (c->wide) PV_MC_LAUNCH(double, WIDE_THREADS, c->d_theta);
     else PV_MC_LAUNCH(double, SAMPLE_THREADS, c->d_theta);
@@ -853,9 +909,9 @@ static int fill_stats(peps_ctx* c, int p, peps_stats* st, bool with_cg) {
 }
 
 static int launch_weights(peps_ctx* c, int p) {
-  k_sr_weights<<<1, SR_WEIGHT_THREADS, 0, c->stream>>>(c->P.n_chains, c->N, p, c->d_log_abs,
+  PV_KLAUNCH(&c->kprof, c->stream, "k_sr_weights", 0.0, 0.0, k_sr_weights<<<1, SR_WEIGHT_THREADS, 0, c->stream>>>(c->P.n_chains, c->N, p, c->d_log_abs,
                                                        c->d_es, c->d_ea, c->d_S, c->d_w, c->d_E,
-                                                       c->d_sc);
+                                                       c->d_sc));
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
 }
@@ -880,49 +936,49 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   // mean and gradient (one pass over O)
   dim3 cgrid((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
   if (fp64(c))
-    k_colsum1<double, true><<<cgrid, SR_THREADS, 0, s>>>(
+    PV_KLAUNCH(&c->kprof, s, "k_colsum1", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1<double, true><<<cgrid, SR_THREADS, 0, s>>>(
         n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
-        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr);
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
   else
-    k_colsum1_f32<true><<<cgrid, SR_THREADS, 0, s>>>(
+    PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32<true><<<cgrid, SR_THREADS, 0, s>>>(
         n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
-        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr);
-  k_colsum2_grad<<<grid_for(Np, SR_THREADS, 1 << 20), SR_THREADS, 0, s>>>(
-      Np, c->nch, c->d_part, c->d_part2, c->d_obar, c->d_g);
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
+  PV_KLAUNCH(&c->kprof, s, "k_colsum2_grad", (2.0 * c->nch * Np * 8.0 + 2.0 * Np * 8.0), 0.0, k_colsum2_grad<<<grid_for(Np, SR_THREADS, 1 << 20), SR_THREADS, 0, s>>>(
+      Np, c->nch, c->d_part, c->d_part2, c->d_obar, c->d_g));
   PV_CUDA(c, cudaGetLastError());
   // CG
   const int nvb = c->nvb;
-  k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_g, c->d_bp1, nullptr);
-  k_cg_init<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_x, c->d_r, c->d_p, c->d_pf, nvb,
-                                       c->d_bp1, c->d_sc, max_cg, cg_tol, eps);
-  k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_obar, c->d_p, c->d_bp2, nullptr);   // obar.p
+  PV_KLAUNCH(&c->kprof, s, "k_dot_part", (2.0 * Np * 8.0), 0.0, k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_g, c->d_bp1, nullptr));
+  PV_KLAUNCH(&c->kprof, s, "k_cg_init", (5.0 * Np * 8.0), 0.0, k_cg_init<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_g, c->d_x, c->d_r, c->d_p, c->d_pf, nvb,
+                                       c->d_bp1, c->d_sc, max_cg, cg_tol, eps));
+  PV_KLAUNCH(&c->kprof, s, "k_dot_part", (2.0 * Np * 8.0), 0.0, k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_obar, c->d_p, c->d_bp2, nullptr));   // obar.p
   PV_CUDA(c, cudaGetLastError());
   const int ov_blocks = c->nyb;
   for (int it = 0; it < max_cg; ++it) {
     if (fp64(c))
-      k_ov<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const double*)c->d_O, c->d_S,
+      PV_KLAUNCH(&c->kprof, s, "k_ov", ((double)n * No * (fp64(c) ? 8.0 : 4.0) + (double)Np * (fp64(c) ? 8.0 : 4.0)), 0.0, k_ov<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const double*)c->d_O, c->d_S,
                                                     c->d_toff, c->d_ooff, c->d_p, c->d_pf,
                                                     c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2,
-                                                    c->d_sc);
+                                                    c->d_sc));
     else
-      k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
+      PV_KLAUNCH(&c->kprof, s, "k_ov", ((double)n * No * (fp64(c) ? 8.0 : 4.0) + (double)Np * (fp64(c) ? 8.0 : 4.0)), 0.0, k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
                                                    c->d_toff, c->d_ooff, c->d_p, c->d_pf, c->d_w,
-                                                   c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc);
+                                                   c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
     if (fp64(c))
-      k_colsum1<double, false><<<cgrid, SR_THREADS, 0, s>>>(
+      PV_KLAUNCH(&c->kprof, s, "k_colsum1", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1<double, false><<<cgrid, SR_THREADS, 0, s>>>(
           n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
-          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done);
+          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
     else
-      k_colsum1_f32<false><<<cgrid, SR_THREADS, 0, s>>>(
+      PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32<false><<<cgrid, SR_THREADS, 0, s>>>(
           n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
-          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done);
-    k_otv2<<<nvb, SR_THREADS, 0, s>>>(Np, c->nch, c->d_part, c->d_obar, c->d_p, c->d_q,
-                                      ov_blocks, c->d_ypart, c->d_bp1, c->d_sc);
-    k_cg_a<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_x, c->d_r, c->d_p, c->d_q, nvb, c->d_bp1,
-                                      c->d_bp2, c->d_sc);
-    k_cg_b<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_r, c->d_p, c->d_pf, c->d_obar, nvb, c->d_bp2,
-                                      c->d_bp1, c->d_sc);
-    k_cg_scalars<<<1, 1, 0, s>>>(nvb, c->d_bp2, c->d_sc);
+          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+    PV_KLAUNCH(&c->kprof, s, "k_otv2", ((double)c->nch * Np * 8.0 + 3.0 * Np * 8.0), 0.0, k_otv2<<<nvb, SR_THREADS, 0, s>>>(Np, c->nch, c->d_part, c->d_obar, c->d_p, c->d_q,
+                                      ov_blocks, c->d_ypart, c->d_bp1, c->d_sc));
+    PV_KLAUNCH(&c->kprof, s, "k_cg_a", (5.0 * Np * 8.0), 0.0, k_cg_a<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_x, c->d_r, c->d_p, c->d_q, nvb, c->d_bp1,
+                                      c->d_bp2, c->d_sc));
+    PV_KLAUNCH(&c->kprof, s, "k_cg_b", (5.0 * Np * 8.0), 0.0, k_cg_b<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_r, c->d_p, c->d_pf, c->d_obar, nvb, c->d_bp2,
+                                      c->d_bp1, c->d_sc));
+    PV_KLAUNCH(&c->kprof, s, "k_cg_scalars", 0.0, 0.0, k_cg_scalars<<<1, 1, 0, s>>>(nvb, c->d_bp2, c->d_sc));
     // obar.p partials for the next k_ov are in d_bp1; swap roles
     std::swap(c->d_bp1, c->d_bp2);
     PV_CUDA(c, cudaGetLastError());
@@ -933,7 +989,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
       if (done) break;
     }
   }
-  k_update<<<grid_for(Np, 256), 256, 0, s>>>(Np, tau, c->d_x, c->d_theta, c->d_theta_f);
+  PV_KLAUNCH(&c->kprof, s, "k_update", (3.0 * Np * 8.0), 0.0, k_update<<<grid_for(Np, 256), 256, 0, s>>>(Np, tau, c->d_x, c->d_theta, c->d_theta_f));
   PV_CUDA(c, cudaGetLastError());
   int rc = fill_stats(c, p, st, true);
   if (rc != PEPS_OK) return rc;
@@ -951,6 +1007,39 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
 }
 
 double peps_time(const peps_ctx* c) { return c ? c->t : 0.0; }
+
+long long peps_launches(const peps_ctx* c) { return c ? c->kprof.launches : 0; }
+
+int peps_profile(peps_ctx* c, int enable) {
+  if (!c || enable < 0 || enable > 2) return fail(c, PEPS_EINVAL, "profile: args");
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (enable) {
+    c->kprof.reset();
+    c->kprof.on = true;
+    c->kprof.gemm_only = enable == 2;
+  } else {
+    c->kprof.fold();
+    c->kprof.on = false;
+  }
+  return PEPS_OK;
+}
+
+int peps_profile_read(peps_ctx* c, peps_kernel_stat* out, int cap, int* n_out) {
+  if (!c || cap < 0 || (cap > 0 && !out) || !n_out) return fail(c, PEPS_EINVAL, "profile_read: args");
+  PV_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->kprof.fold();
+  const auto& acc = c->kprof.acc;
+  *n_out = (int)acc.size();
+  for (int i = 0; i < cap && i < (int)acc.size(); ++i) {
+    memset(&out[i], 0, sizeof(out[i]));
+    strncpy(out[i].name, acc[i].name.c_str(), sizeof(out[i].name) - 1);
+    out[i].launches = acc[i].launches;
+    out[i].ms = acc[i].ms;
+    out[i].bytes = acc[i].bytes;
+    out[i].flops = acc[i].flops;
+  }
+  return PEPS_OK;
+}
 
 namespace {
 struct CkptHeader {

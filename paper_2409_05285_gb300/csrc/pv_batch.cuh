@@ -12,6 +12,7 @@
 #include <cstdint>
 #include <cmath>
 #include <vector>
+#include <type_traits>
 
 #include "pv_coop.cuh"
 #include "pv_philox.cuh"
@@ -1050,6 +1051,9 @@ inline void bond_lists(int L1, int L2, double J1, double J2, std::vector<int>& b
 
 }  // namespace pv
 
+#include "pv_tc.cuh"
+#include "pv_prof.cuh"
+
 #if defined(__CUDACC__)
 namespace pv {
 
@@ -1120,15 +1124,39 @@ __global__ void __launch_bounds__(256) kb_gemm(GSpec g, T* C, long long cs, Oper
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0;
     for (int k0 = 0; k0 < g.K; k0 += KC) {
-      for (int idx = tid; idx < ns * chunkA; idx += 256) {
-        int gs = idx / chunkA, r = idx - gs * chunkA;
-        int kk = r / TM, mm = r - kk * TM, k = k0 + kk;
-        As[idx] = (k < g.K && rowA[mm] >= 0) ? A.at(sbase + gs)[rowA[mm] + kAo[k]] : (T)0;
+      // four independent loads per thread before the stores
+      const int totA = ns * chunkA, totB = ns * chunkB;
+      for (int i0 = tid; i0 < totA; i0 += 1024) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = i0 + u * 256;
+          v[u] = (T)0;
+          if (idx < totA) {
+            int gs = idx / chunkA, r = idx - gs * chunkA;
+            int kk = r / TM, mm = r - kk * TM, k = k0 + kk;
+            if (k < g.K && rowA[mm] >= 0) v[u] = A.at(sbase + gs)[rowA[mm] + kAo[k]];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u * 256 < totA) As[i0 + u * 256] = v[u];
       }
-      for (int idx = tid; idx < ns * chunkB; idx += 256) {
-        int gs = idx / chunkB, r = idx - gs * chunkB;
-        int kk = r / TN, nn = r - kk * TN, k = k0 + kk;
-        Bs[idx] = (k < g.K && colB[nn] >= 0) ? B.at(sbase + gs)[colB[nn] + kBo[k]] : (T)0;
+      for (int i0 = tid; i0 < totB; i0 += 1024) {
+        T v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int idx = i0 + u * 256;
+          v[u] = (T)0;
+          if (idx < totB) {
+            int gs = idx / chunkB, r = idx - gs * chunkB;
+            int kk = r / TN, nn = r - kk * TN, k = k0 + kk;
+            if (k < g.K && colB[nn] >= 0) v[u] = B.at(sbase + gs)[colB[nn] + kBo[k]];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (i0 + u * 256 < totB) Bs[i0 + u * 256] = v[u];
       }
       __syncthreads();
       if (comp) {
@@ -1257,6 +1285,13 @@ __global__ void kb_O(OT* O, long long No, long long o_off, const T* env, long lo
   if (k < sz) O[(long long)s * No + o_off + k] = (OT)((double)env[(long long)s * es + k] / (double)val[(long long)s * vs]);
 }
 
+// Whether every chain's slice of a float operand starts on a 16-byte boundary.
+inline bool op_al16(const Operand<float>& o) {
+  if ((uintptr_t)o.base % 16) return false;
+  if (o.mode == OP_BATCH) return o.stride % 4 == 0;
+  return o.site_off % 4 == 0 && o.site_sz % 4 == 0;
+}
+
 // Launch back end of the batched runner: one kernel per batched operation on `stream`.
 template <typename T, typename OT>
 struct CudaBE {
@@ -1267,6 +1302,43 @@ struct CudaBE {
   long long trunc_cap;   // elements of the Jacobi work area in shared memory
   int sms;
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
+  bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
+  int* tc_err = nullptr; // raised by a tensor-core kernel whose completion wait ran out
+  void (*tc_form_override)(TcSpec&) = nullptr;   // test hook: restrict the operand forms
+  KProf* prof = nullptr; // launch counter and optional per-kernel timing
+
+  // Algorithmic bytes of one batched contraction: each chain's operand slices read once
+  // (a site tensor once per local index in use), the output written once.
+  static double ein_bytes(const Spec& s, const Operand<T>& A, const Operand<T>& B, int n) {
+    double a = 1, b = 1, c = 1;
+    for (int d = 0; d < s.no; ++d) {
+      c *= s.os[d];
+      if (s.ao[d]) a *= s.os[d];
+      if (s.bo[d]) b *= s.os[d];
+    }
+    for (int d = 0; d < s.nk; ++d) {
+      a *= s.ks[d];
+      b *= s.ks[d];
+    }
+    const double sites = n < 4 ? n : 4;
+    return (a * (A.mode == OP_BATCH ? n : sites) + b * (B.mode == OP_BATCH ? n : sites) + c * n) *
+           sizeof(T);
+  }
+  // resident tensor-core GEMM CTAs per SM allowed by registers and threads (cached)
+  int tc_by_regs = 0;
+  int tc_reg_limit() {
+    if (!tc_by_regs) {
+      cudaFuncAttributes fa;
+      int regs = 64;
+      if (cudaFuncGetAttributes(&fa, kb_gemm_tc) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      else cudaGetLastError();
+      regs = (regs + 7) & ~7;   // per-warp allocation granularity
+      tc_by_regs = 65536 / (regs * TC_THREADS);
+      if (tc_by_regs > 2048 / TC_THREADS) tc_by_regs = 2048 / TC_THREADS;
+      if (tc_by_regs < 1) tc_by_regs = 1;
+    }
+    return tc_by_regs;
+  }
 
   static int gx(long long n, int t) { return (int)((n + t - 1) / t); }
   int gblocks(int n) const { return n < 8 * sms ? n : 8 * sms; }
@@ -1274,6 +1346,34 @@ struct CudaBE {
   void ein(const Spec& raw, const MSpec& m, T* out, long long os, Operand<T> A, Operand<T> B,
            int n) {
     GSpec gs = gemm_spec(raw);
+    if constexpr (std::is_same<T, float>::value) {
+      TcSpec t;
+      bool swap = false;
+      if (tc && tc_plan(gs, t, swap)) {
+        tc_forms(t, op_al16(swap ? B : A), op_al16(swap ? A : B),
+                 ((uintptr_t)out % 16 == 0) && os % 4 == 0);
+        if (tc_form_override) tc_form_override(t);
+        const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
+        const size_t bytes = tc_smem_bytes(t);
+        // persistent grid of the CTAs that can be resident at once (shared memory, tensor
+        // memory columns, registers)
+        int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
+        int by_tmem = 512 / tc_cols(t.TN);
+        int by_regs = tc_reg_limit();
+        per_sm = per_sm < by_tmem ? per_sm : by_tmem;
+        per_sm = per_sm < by_regs ? per_sm : by_regs;
+        per_sm = per_sm < 16 ? per_sm : 16;
+        per_sm = per_sm < 1 ? 1 : per_sm;
+        long long gy = (long long)sms * per_sm / (tilesM * tilesN);
+        gy = gy < 1 ? 1 : (gy > n ? n : gy);
+        gy = gy > 65535 ? 65535 : gy;
+        dim3 gr(tilesM * tilesN, (unsigned)gy);
+        PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                   kb_gemm_tc<<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A, swap ? A : B,
+                                                             n, tilesN, tc_err));
+        return;
+      }
+    }
     if (gs.ok && gs.K > 1) {
       int Np = ((gs.N + 3) / 4) * 4;
       int TN = 4;
@@ -1293,55 +1393,62 @@ struct CudaBE {
       int gy = (n + G - 1) / G;
       if (gy > 65535) gy = 65535;
       dim3 gr(tilesN * tilesM, gy);
-      kb_gemm<T><<<gr, 256, bytes, st>>>(gs, out, os, A, B, n, TM, TN, KC, tilesN, G);
+      PV_KLAUNCH(prof, st, "kb_gemm", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                 kb_gemm<T><<<gr, 256, bytes, st>>>(gs, out, os, A, B, n, TM, TN, KC, tilesN, G));
       return;
     }
     int quad = quad_ok(m) ? 1 : 0;
     long long work = quad ? (m.total >> 2) : m.total;
     dim3 g(gx(work, 256), n);
-    kb_ein<T><<<g, 256, 0, st>>>(m, out, os, A, B, n, quad);
+    PV_KLAUNCH(prof, st, "kb_ein", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+               kb_ein<T><<<g, 256, 0, st>>>(m, out, os, A, B, n, quad));
   }
   void lq(OpLq<T> op, int n) {
     size_t bytes = (size_t)op.m * op.nn * sizeof(T);
     int use = bytes <= (size_t)lq_smem_max ? 1 : 0;
-    kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use);
+    const int K = op.m < op.nn ? op.m : op.nn;
+    double fl = 0;
+    for (int j = 0; j < K; ++j) fl += 4.0 * (op.nn - j) * (op.m - j);
+    PV_KLAUNCH(prof, st, "kb_lq", (double)n * ((double)op.m * op.nn + (double)op.m * K) * sizeof(T),
+               fl * n, kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
     size_t bytes = (size_t)trunc_cap * sizeof(T) + (size_t)(op.nc + 4) * sizeof(T) +
                    (size_t)(op.nc + 4) * sizeof(int) + 16;
-    kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap);
+    PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
+               kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap));
   }
-  void norm(OpNorm<T> op, int n) { kb_norm<T><<<gblocks(n), BT, 0, st>>>(op, n); }
-  void dot(OpDot<T> op, int n) { kb_dot<T><<<gx(n, 8), 256, 0, st>>>(op, n); }
-  void set(T* x, long long xs, long long off, T v, int n) { kb_set<T><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n); }
+  void norm(OpNorm<T> op, int n) { PV_KLAUNCH(prof, st, "kb_norm", 0.0, 0.0, kb_norm<T><<<gblocks(n), BT, 0, st>>>(op, n)); }
+  void dot(OpDot<T> op, int n) { PV_KLAUNCH(prof, st, "kb_dot", 0.0, 0.0, kb_dot<T><<<gx(n, 8), 256, 0, st>>>(op, n)); }
+  void set(T* x, long long xs, long long off, T v, int n) { PV_KLAUNCH(prof, st, "kb_set", 0.0, 0.0, kb_set<T><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n)); }
   void setd(double* x, long long xs, long long off, double v, int n) {
-    kb_set<double><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n);
+    PV_KLAUNCH(prof, st, "kb_set", 0.0, 0.0, kb_set<double><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n));
   }
   void copyd(double* x, long long xs, int dst, int src, int n) {
-    kb_copyd<<<gx(n, 256), 256, 0, st>>>(x, xs, dst, src, n);
+    PV_KLAUNCH(prof, st, "kb_copyd", 0.0, 0.0, kb_copyd<<<gx(n, 256), 256, 0, st>>>(x, xs, dst, src, n));
   }
   void copy_masked(T* dst, long long ds, const T* src, long long ss, long long len,
                    const int8_t* mask, int n) {
     dim3 g(gx(len, 256), n);
-    kb_copy<T><<<g, 256, 0, st>>>(dst, ds, src, ss, len, mask, n);
+    PV_KLAUNCH(prof, st, "kb_copy", 0.0, 0.0, kb_copy<T><<<g, 256, 0, st>>>(dst, ds, src, ss, len, mask, n));
   }
   void diag(const uint8_t* S, int n, double* es, double* ea) {
-    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemDiag{S, N, nb, bi, bj, bJ, es, ea}, n);
+    PV_KLAUNCH(prof, st, "kb_elem_diag", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemDiag{S, N, nb, bi, bj, bJ, es, ea}, n));
   }
   void amp(const T* val, long long vs, const double* lsd, int lstride, double* la, int8_t* sg, int n) {
-    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemAmp<T>{val, vs, lsd, lstride, la, sg}, n);
+    PV_KLAUNCH(prof, st, "kb_elem_amp", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemAmp<T>{val, vs, lsd, lstride, la, sg}, n));
   }
   void writeO(OT* O, long long No, long long o_off, const T* env, long long es, long long sz,
               const T* val, long long vs, int n) {
     dim3 g(gx(sz, 256), n);
-    kb_O<T, OT><<<g, 256, 0, st>>>(O, No, o_off, env, es, sz, val, vs, n);
+    PV_KLAUNCH(prof, st, "kb_O", 0.0, 0.0, kb_O<T, OT><<<g, 256, 0, st>>>(O, No, o_off, env, es, sz, val, vs, n));
   }
-  void sel(ElemSel f, int n) { kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n); }
+  void sel(ElemSel f, int n) { PV_KLAUNCH(prof, st, "kb_elem_sel", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n)); }
   void ratio(const T* num, const T* den, long long dens, const int8_t* valid, double coef,
              double* e, int n) {
-    kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemRatio<T>{num, den, dens, valid, coef, e}, n);
+    PV_KLAUNCH(prof, st, "kb_elem_ratio", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemRatio<T>{num, den, dens, valid, coef, e}, n));
   }
-  void accept(ElemAccept<T> f, int n) { kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n); }
+  void accept(ElemAccept<T> f, int n) { PV_KLAUNCH(prof, st, "kb_elem_accept", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n)); }
 };
 
 }  // namespace pv

@@ -1,0 +1,422 @@
+// Tensor-core contractions of the batched engine (float32 storage, TF32 multiplies, FP32
+// accumulation): one strided GEMM per chain, C[m][n] = sum_k P[m][k] Q[n][k], where the row,
+// column and contraction indices are multi-indices with arbitrary strides (the transfer
+// contractions of the boundary-MPS environments and strips, Sec. II).
+//
+// A CTA of four warps owns one 128-row tile of one chain at a time and loops over chains.
+// Per contraction chunk of Kc (<= 64) indices every thread gathers operand elements from
+// global memory, rounds them to TF32 and writes them into shared memory in the canonical
+// K-major layout without swizzle (core matrices of 8 rows x 16 bytes stored as 128
+// contiguous bytes); one thread issues Kc/8 `tcgen05.mma.kind::tf32` instructions
+// (M = 128, N = the tile width) into an accumulator in tensor memory and commits them to an
+// mbarrier; after the last chunk each warp reads its 32 accumulator lanes with
+// `tcgen05.ld` and scatters them to C.  Every wait on the mbarrier is bounded: when it runs
+// out the kernel raises `err`, waits once more, frees its tensor memory and returns.
+#ifndef PV_TC_CUH
+#define PV_TC_CUH
+#include <cstdint>
+
+namespace pv {
+
+// Index plan of one tensor-core contraction; rows are the larger of the two free sides.
+struct TcSpec {
+  int nr, nc, nk;
+  int rs[4], rP[4], rC[4];   // row dims: sizes, strides in P, strides in C
+  int cs[4], cQ[4], cC[4];   // column dims: sizes, strides in Q, strides in C
+  int ks[4], kP[4], kQ[4];   // contraction dims: sizes, strides in P and in Q
+  int M, N, K;
+  int TN;                    // tile width: a multiple of 16, at most 256
+  int Kc;                    // contraction chunk: a multiple of 8, at most 64
+  int modeP, modeQ;          // operand gather forms (TC_SCALAR, TC_VEC_K, TC_VEC_T)
+  int vecC;                  // 16-byte stores of four consecutive columns of C
+};
+
+constexpr int TC_ROWS = 128;
+constexpr int TC_THREADS = 128;
+constexpr int TC_KMAX = 64;
+constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+constexpr int TC_SCALAR = 0, TC_VEC_K = 1, TC_VEC_T = 2;
+
+// Plans C = A.B of a GEMM-shaped contraction for the tensor cores; false when the shape
+// does not suit them (no contraction worth the name, or both free sides small).
+inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap) {
+  if (!g.ok || g.K < 4 || g.K > 4096) return false;
+  swap = g.N > g.M;
+  const int M = swap ? g.N : g.M, N = swap ? g.M : g.N;
+  if (M < 64) return false;
+  t.M = M;
+  t.N = N;
+  t.K = g.K;
+  t.nr = swap ? g.nn : g.nm;
+  t.nc = swap ? g.nm : g.nn;
+  t.nk = g.nk;
+  for (int d = 0; d < 4; ++d) {
+    t.rs[d] = swap ? g.ns[d] : g.ms[d];
+    t.rP[d] = swap ? g.nB[d] : g.mA[d];
+    t.rC[d] = swap ? g.nC[d] : g.mC[d];
+    t.cs[d] = swap ? g.ms[d] : g.ns[d];
+    t.cQ[d] = swap ? g.mA[d] : g.nB[d];
+    t.cC[d] = swap ? g.mC[d] : g.nC[d];
+    t.ks[d] = g.ks[d];
+    t.kP[d] = swap ? g.kB[d] : g.kA[d];
+    t.kQ[d] = swap ? g.kA[d] : g.kB[d];
+  }
+  int n16 = ((N + 15) / 16) * 16;
+  t.TN = n16 < 256 ? n16 : 256;
+  int k8 = ((g.K + 7) / 8) * 8;
+  t.Kc = k8 < TC_KMAX ? k8 : TC_KMAX;
+  t.modeP = t.modeQ = TC_SCALAR;
+  t.vecC = 0;
+  return true;
+}
+
+inline bool tc_all4(const int* st, int n) {
+  for (int d = 0; d < n; ++d)
+    if (st[d] % 4) return false;
+  return true;
+}
+
+// Operand form: 16-byte loads along the contraction index or along the rows when the
+// operand is unit-stride there in blocks of four and every other stride keeps 16-byte
+// alignment (`al`: the operand's base and per-chain offsets are multiples of 16 bytes).
+inline int tc_mode(bool al, int nr, const int* rsz, const int* rst, int nk, const int* ksz,
+                   const int* kst) {
+  if (!al) return TC_SCALAR;
+  if (nk > 0 && kst[nk - 1] == 1 && ksz[nk - 1] % 4 == 0 && tc_all4(kst, nk - 1) &&
+      tc_all4(rst, nr))
+    return TC_VEC_K;
+  if (nr > 0 && rst[nr - 1] == 1 && rsz[nr - 1] % 4 == 0 && tc_all4(rst, nr - 1) &&
+      tc_all4(kst, nk))
+    return TC_VEC_T;
+  return TC_SCALAR;
+}
+
+inline void tc_forms(TcSpec& t, bool p_al, bool q_al, bool c_al) {
+  t.modeP = tc_mode(p_al, t.nr, t.rs, t.rP, t.nk, t.ks, t.kP);
+  t.modeQ = tc_mode(q_al, t.nc, t.cs, t.cQ, t.nk, t.ks, t.kQ);
+  t.vecC = (c_al && t.nc > 0 && t.cC[t.nc - 1] == 1 && t.cs[t.nc - 1] % 4 == 0 &&
+            tc_all4(t.cC, t.nc - 1) && tc_all4(t.rC, t.nr)) ? 1 : 0;
+}
+
+inline size_t tc_smem_bytes(const TcSpec& t) {
+  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) +
+         (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int);
+}
+
+PV_HD int tc_cols(int TN) {
+  int c = 32;
+  while (c < TN) c <<= 1;
+  return c;
+}
+
+#if defined(__CUDACC__)
+
+__device__ __forceinline__ uint32_t tc_smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading-dimension byte offset (between
+// core matrices along K), stride-dimension byte offset (between 8-row groups), descriptor
+// version 1 (bits 46-47), base offset 0, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D float32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
+// 10-12 = 2), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float tc_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       int accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  for (long long i = 0; i < TC_WAIT_LIMIT; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// 16 consecutive accumulator columns of this thread's lane.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Operand chunk (rows x Kc) to shared memory, rounded to TF32, in the canonical K-major
+// layout without swizzle: core matrix (g, q) of rows 8g..8g+7 and contraction indices
+// 4q..4q+3 at element offset (g * Kc/4 + q) * 32, row-major inside (16 bytes per row).
+// Three gather forms fill it:
+//  TC_SCALAR  element loads;
+//  TC_VEC_K   16-byte loads of four consecutive contraction indices (the operand is
+//             unit-stride in its innermost contraction index), one 16-byte store each;
+//  TC_VEC_T   16-byte loads of four consecutive rows (the operand is unit-stride in its
+//             innermost row index): four lanes load a 4 x 4 block at four contraction
+//             indices, transpose it with shuffles and store one row each.
+// Each thread issues TC_UNROLL independent loads before it stores.
+constexpr int TC_UNROLL = 4;
+
+__device__ __forceinline__ float4 tc_round4(float4 v) {
+  return make_float4(tc_round(v.x), tc_round(v.y), tc_round(v.z), tc_round(v.w));
+}
+
+__device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ src, int mode,
+                                          int rows, int Kc, int k0, int K, const int* roff,
+                                          const int* koff, int tid) {
+  if (mode == TC_SCALAR) {
+    const int qn = Kc >> 2, total = rows * Kc;
+    for (int e0 = tid; e0 < total; e0 += TC_THREADS * TC_UNROLL) {
+      float v[TC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int e = e0 + u * TC_THREADS;
+        v[u] = 0.f;
+        if (e < total) {
+          const int cm = e >> 5, j = e & 31;
+          const int g = cm / qn, q = cm - g * qn;
+          const int ro = roff[g * 8 + (j >> 2)], k = k0 + q * 4 + (j & 3);
+          if (ro >= 0 && k < K) v[u] = __ldg(src + ro + koff[k]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int e = e0 + u * TC_THREADS;
+        if (e < total) dst[e] = tc_round(v[u]);
+      }
+    }
+  } else if (mode == TC_VEC_K) {
+    const int qn = Kc >> 2, total = (rows * Kc) >> 2;
+    float4* d4 = (float4*)dst;
+    for (int e0 = tid; e0 < total; e0 += TC_THREADS * TC_UNROLL) {
+      float4 v[TC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int e = e0 + u * TC_THREADS;
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e < total) {
+          const int cm = e >> 3;
+          const int g = cm / qn, q = cm - g * qn;
+          const int ro = roff[g * 8 + (e & 7)], k = k0 + q * 4;
+          if (ro >= 0 && k < K) v[u] = __ldg((const float4*)(src + ro + koff[k]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int e = e0 + u * TC_THREADS;
+        if (e < total) d4[e] = tc_round4(v[u]);
+      }
+    }
+  } else {
+    // blocks of 4 rows x 4 contraction indices; lane j of a quad holds index 4kq + j
+    const int qn = Kc >> 2, nrb = rows >> 2, total = nrb * qn;
+    const int lane = tid & 31, j = lane & 3;
+    float4* d4 = (float4*)dst;
+    for (int b0 = tid >> 2; b0 - (lane >> 2) < total; b0 += (TC_THREADS / 4) * TC_UNROLL) {
+      float4 v[TC_UNROLL];
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int blk = b0 + u * (TC_THREADS / 4);
+        v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (blk < total) {
+          const int kq = blk / nrb, rb = blk - kq * nrb;
+          const int ro = roff[rb * 4], k = k0 + kq * 4 + j;
+          if (ro >= 0 && k < K) v[u] = __ldg((const float4*)(src + ro + koff[k]));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < TC_UNROLL; ++u) {
+        const int blk = b0 + u * (TC_THREADS / 4);
+        float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int c = (j - r) & 3;   // component this lane sends: row c of its column
+          const float send = c == 0 ? v[u].x : (c == 1 ? v[u].y : (c == 2 ? v[u].z : v[u].w));
+          const float got = __shfl_sync(0xffffffffu, send, (lane & ~3) | ((j + r) & 3));
+          const int idx = (j + r) & 3;   // row j at contraction index 4kq + idx
+          o0 = idx == 0 ? got : o0;
+          o1 = idx == 1 ? got : o1;
+          o2 = idx == 2 ? got : o2;
+          o3 = idx == 3 ? got : o3;
+        }
+        if (blk < total) {
+          const int kq = blk / nrb, rb = blk - kq * nrb;
+          const int r = rb * 4 + j;
+          d4[((r >> 3) * qn + kq) * 8 + (r & 7)] =
+              make_float4(tc_round(o0), tc_round(o1), tc_round(o2), tc_round(o3));
+        }
+      }
+    }
+  }
+}
+
+// Descriptor of k-block kb (8 contraction indices = two core matrices along K).
+__device__ __forceinline__ uint64_t tc_kdesc(uint32_t base, int Kc, int kb) {
+  return tc_desc(base + kb * 256, 128, (uint32_t)Kc * 32u);
+}
+
+__global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, long long cs,
+                                                         Operand<float> P, Operand<float> Q,
+                                                         int n, int tilesN, int* err) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tm = blockIdx.x / tilesN, tn = blockIdx.x - (blockIdx.x / tilesN) * tilesN;
+  const int TN = t.TN, Kc = t.Kc;
+  const int m0 = tm * TC_ROWS, n0 = tn * TN;
+  float* As = (float*)dyn;
+  float* Bs = As + TC_ROWS * Kc;
+  int* rowP = (int*)(Bs + TN * Kc);
+  int* rowC = rowP + TC_ROWS;
+  int* colQ = rowC + TC_ROWS;
+  int* colC = colQ + TN;
+  int* kPo = colC + TN;
+  int* kQo = kPo + t.K;
+  for (int i = tid; i < TC_ROWS; i += TC_THREADS) {
+    int m = m0 + i;
+    if (m < t.M) gemm_offsets(m, t.nr, t.rs, t.rP, t.rC, rowP[i], rowC[i]);
+    else rowP[i] = rowC[i] = -1;
+  }
+  for (int i = tid; i < TN; i += TC_THREADS) {
+    int c = n0 + i;
+    if (c < t.N) gemm_offsets(c, t.nc, t.cs, t.cQ, t.cC, colQ[i], colC[i]);
+    else colQ[i] = colC[i] = -1;
+  }
+  for (int k = tid; k < t.K; k += TC_THREADS) gemm_offsets(k, t.nk, t.ks, t.kP, t.kQ, kPo[k], kQo[k]);
+  const uint32_t ncols = (uint32_t)tc_cols(TN);
+  const uint32_t bar_a = tc_smem_addr(&bar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     tc_smem_addr(&tslot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    abort_flag = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_a), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint32_t idesc = tc_idesc(TC_ROWS, TN);
+  const uint32_t a_addr = tc_smem_addr(As), b_addr = tc_smem_addr(Bs);
+  const int Kp = ((t.K + 7) >> 3) << 3;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int s = blockIdx.y; s < n && ok; s += gridDim.y) {
+    const float* pp = P.at(s);
+    const float* pq = Q.at(s);
+    for (int k0 = 0; k0 < t.K; k0 += Kc) {
+      tc_gather(As, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
+      tc_gather(Bs, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const int nkb = (Kp - k0 < Kc ? Kp - k0 : Kc) >> 3;
+        for (int kb = 0; kb < nkb; ++kb)
+          tc_mma(tmem, tc_kdesc(a_addr, Kc, kb), tc_kdesc(b_addr, Kc, kb), idesc,
+                 (k0 > 0 || kb > 0) ? 1 : 0);
+        tc_commit(bar_a);
+      }
+      if (!tc_wait(bar_a, phase)) {
+        tc_wait(bar_a, phase);
+        abort_flag = 1;
+      }
+      phase ^= 1;
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+    }
+    if (!ok) break;
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const int oc = rowC[r];
+    float* pc = C + (long long)s * cs;
+    for (int c0 = 0; c0 < TN; c0 += 16) {
+      uint32_t v[16];
+      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (oc >= 0) {
+        if (t.vecC) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const int cc = colC[c0 + j];
+            if (cc >= 0)
+              *(float4*)(pc + oc + cc) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                     __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int cc = colC[c0 + j];
+            if (cc >= 0) pc[oc + cc] = __uint_as_float(v[j]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+  }
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
+                 : "memory");
+  }
+  if (tid == 0 && abort_flag) atomicOr(err, 1);
+}
+
+#endif  // __CUDACC__
+
+}  // namespace pv
+#endif

@@ -97,6 +97,54 @@ def test_eval_fp32_heis8_near_product_state(mode):
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-3, 1e-3, 5e-3)
 
 
+TF32_CASES = [  # sizes at which the transfer contractions reach the tensor-core path
+    (6, 6, 4, 16, 0.0, 8),
+    (4, 5, 4, 12, 0.5, 6),
+]
+
+
+@pytest.mark.parametrize("case", TF32_CASES)
+def test_eval_tf32_matches_oracle(case):
+    # TF32 operands carry 11 significant bits (unit roundoff u = 2^-11 after round-to-
+    # nearest); an amplitude is a chain of ~2 L1 L2 contractions, each adding ~u sqrt(K)
+    # relative error, so |d log rho| stays within ~1e-2 and E_loc, O within a few 1e-2.
+    L1, L2, D, chi, J2, n = case
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=L1 * 7 + L2, scale=0.2, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=D + 11)
+    ctx = _ctx(L1, L2, D, chi, n, J2=J2, prec=binding.PEPS_TF32)
+    ctx.set_theta(th)
+    _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 2e-2, 3e-2, 5e-2)
+
+
+def test_tf32_energy_per_site_within_1e3_of_fp64():
+    # The mixed-precision bound at the bench workload's sizes, on a cooled state (four SR
+    # steps of tau = 0.1 from beta = 0 in FP64): local energy per site of the TF32 path
+    # against the FP64 path on the same parameters and configurations.
+    L, D, chi, n = 8, 4, 16, 64
+    ref = _ctx(L, L, D, chi, n, prec=binding.PEPS_FP64, seed=3, mode=binding.PEPS_BLOCKS_BATCHED)
+    ref.mc_sweep(2, p=1)
+    for _ in range(4):
+        ref.step(n_sweeps=1, p=2, tau=0.1, eps=1e-4, max_cg=100, cg_tol=1e-10)
+    th, S = ref.get_theta(), ref.get_configs()
+    la64, sg64, es, ea, _ = ref.eval_batch(S, with_O=False)
+    e64 = es + ea
+    tf = _ctx(L, L, D, chi, n, prec=binding.PEPS_TF32, seed=3)
+    tf.set_theta(th)
+    la32, sg32, es, ea, _ = tf.eval_batch(S, with_O=False)
+    e32 = es + ea
+    N = L * L
+    assert np.all(sg64 == sg32)
+    assert np.max(np.abs(la64 - la32)) <= 1e-1
+    assert abs(np.mean(e64) - np.mean(e32)) / (2 * N) <= 1e-3
+    assert np.max(np.abs(e64 - e32)) / (2 * N) <= 1e-3
+
+
+def test_tf32_needs_batched_blocks():
+    with pytest.raises(RuntimeError):
+        _ctx(3, 3, 2, 4, 2, prec=binding.PEPS_TF32, mode=binding.PEPS_BLOCKS_NARROW)
+
+
 def test_init_matches_oracle_bit_exact():
     L1, L2, D, n, seed = 4, 5, 3, 9, 1234
     lat = Lattice(L1, L2, D)

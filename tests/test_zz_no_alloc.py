@@ -30,7 +30,9 @@ def test_noalloc_matches_eval_batch_twice(prec):
     from paper_2409_05285_gb300.build import build
     build()
     L1, L2, D, chi, J2, nb = 4, 5, 3, 5, 0.4, 23
-    ref = binding.Context(L1, L2, D, chi, 4, J1=1.0, J2=J2, precision=prec, seed=1)
+    # the entry point runs the per-chain (narrow-block) engine: compare with the same engine
+    ref = binding.Context(L1, L2, D, chi, 4, J1=1.0, J2=J2, precision=prec, seed=1,
+                          block_mode=binding.PEPS_BLOCKS_NARROW)
     th = wl.random_theta(L1, L2, D, seed=3, scale=0.3, diag_bias=1.0)
     ref.set_theta(th)
     dev = torch.device("cuda:0")
