@@ -94,6 +94,23 @@ def measured_peaks():
         return {}
 
 
+def kdelta(cum, base, acc):
+    """Adds to `acc` the per-kernel sums accumulated since `base` (both updated in place)."""
+    for k, v in cum.items():
+        b = base.get(k, (0, 0.0, 0.0, 0.0))
+        d = tuple(x - y for x, y in zip(v, b))
+        a = acc.get(k, (0, 0.0, 0.0, 0.0))
+        acc[k] = tuple(x + y for x, y in zip(a, d))
+        base[k] = v
+    return acc
+
+
+def kernel_shares(ks):
+    tot = sum(v[1] for v in ks.values()) or 1.0
+    return {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / tot, 4)}
+            for k, v in sorted(ks.items(), key=lambda kv: -kv[1][1]) if v[0] > 0}
+
+
 def kernel_roofline(kstats, peaks, prec, binding):
     """Roofline of the dominant kernel of the timed region from the library's per-launch CUDA
     events: achieved = its algorithmic bytes (or flops) per launch / its mean launch time."""
@@ -172,6 +189,8 @@ def run_ours(args):
     # (--profile-all: of every kernel, which costs a few per cent of the step time)
     ctx.profile(True, gemm_only=not args.profile_all)
     launches0 = ctx.launches()
+    phase_k = {"mc_sweep": {}, "eval": {}, "sr_step": {}}   # per-phase kernel sums
+    phase_base = {}
     e_start, e_end = ev(), ev()
     e_start.record(stream)
     for _ in range(args.steps):
@@ -180,9 +199,13 @@ def run_ours(args):
         ctx.mc_sweep(1, p)
         e1.record(stream)
         mc_flops.append(ctx.counters()[0])
+        if args.profile_all:
+            phase_k["mc_sweep"] = kdelta(ctx.profile_read(), phase_base, phase_k["mc_sweep"])
         ctx.eval_chains()
         e2.record(stream)
         f_ev, j_ev = ctx.counters()
+        if args.profile_all:
+            phase_k["eval"] = kdelta(ctx.profile_read(), phase_base, phase_k["eval"])
         eval_flops.append(f_ev)
         jac.append(j_ev / n)
         st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=p)
@@ -190,6 +213,8 @@ def run_ours(args):
         stats.append(st)
         cg_its.append(st["cg_iters"])
         e3.synchronize()
+        if args.profile_all:
+            phase_k["sr_step"] = kdelta(ctx.profile_read(), phase_base, phase_k["sr_step"])
         mc_ms.append(e0.elapsed_time(e1))
         eval_ms.append(e1.elapsed_time(e2))
         sr_ms.append(e2.elapsed_time(e3))
@@ -262,6 +287,8 @@ def run_ours(args):
         "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"],
         "roofline": roofline,
         "kernels": kernels,
+        "kernels_by_phase": ({ph: kernel_shares(v) for ph, v in phase_k.items()}
+                             if args.profile_all else None),
         "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(ctx.Np * 8 + n * ctx.N),
                 "d2h_bytes_per_step": int(ctx.Np * 8 + n * ctx.N)},
