@@ -467,6 +467,10 @@ int make_batch_t(peps_ctx* c, int sms) {
     cudaError_t e = cudaFuncSetAttribute(kb_lq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq_max);
     b->be.lq_smem_max = e == cudaSuccess ? lq_max : 48 * 1024;
     if (e != cudaSuccess) cudaGetLastError();
+    const int lq2_max = 200 * 1024;
+    e = cudaFuncSetAttribute(kb_lq2<T, LQ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq2_max);
+    b->be.lq2_smem_max = e == cudaSuccess ? lq2_max : 0;
+    if (e != cudaSuccess) cudaGetLastError();
   }
   if constexpr (std::is_same<T, float>::value) {
     if (P->precision == PEPS_TF32) {

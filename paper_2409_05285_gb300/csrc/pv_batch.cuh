@@ -1058,6 +1058,7 @@ inline void bond_lists(int L1, int L2, double J1, double J2, std::vector<int>& b
 namespace pv {
 
 constexpr int BT = 256;   // threads of the per-sample blocks
+constexpr int LQ_THREADS = 512;   // threads of the shared-memory Householder kernel
 
 template <typename T>
 __global__ void __launch_bounds__(256) kb_ein(MSpec m, T* out, long long os, Operand<T> A,
@@ -1213,6 +1214,119 @@ __global__ void __launch_bounds__(BT) kb_lq(OpLq<T> op, int n, int use_smem) {
   }
 }
 
+// Householder factor with the chain's matrix in shared memory (row stride ld, chosen so
+// that the row groups of one warp fall on disjoint banks), 4-wide vector accesses.  Step j
+// reflects the tail of row j onto e_j: alpha = -sign(x0) |x|, v = x - alpha e_j; v is kept
+// in place of row j (its entries left of column j zeroed inside the first vector, so whole
+// 4-wide vectors can be used).  Every later row jj is updated by a group of G threads (a
+// partial dot v.a over the group's vectors, a shuffle reduction inside the group, then
+// a -= (2 v.a / |v|^2) v) and L[jj][j] = a_j.  The group holding row j+1 also forms that
+// row's tail norm and its reflector for step j+1, so each step costs one barrier.
+// Needs nn and ld multiples of 4.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) kb_lq2(OpLq<T> op, int n, int ld, int G) {
+  typedef typename std::conditional<sizeof(T) == 8, double2, float4>::type V2;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* Wm = (T*)dyn;
+  __shared__ T s_alpha[2], s_vn2[2];
+  const int m = op.m, nn = op.nn, K = m < nn ? m : nn;
+  const int tid = threadIdx.x, grp = tid / G, gl = tid - grp * G, ngrp = NT / G;
+  const int nq = nn >> 2;   // 4-wide vectors per row
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const T* W = op.W + (long long)s * op.ws;
+    T* Lo = op.Lf + (long long)s * op.ls;
+    for (int i = tid; i < m * nn; i += NT) {
+      const int r = i / nn;
+      Wm[r * ld + (i - r * nn)] = W[i];
+    }
+    for (int i = tid; i < m * K; i += NT) Lo[i] = (T)0;
+    __syncthreads();
+    if (tid < 32) {   // reflector of row 0
+      T p = 0;
+      for (int c = tid; c < nn; c += 32) p += Wm[c] * Wm[c];
+      p = warp_sum(p);
+      if (tid == 0) {
+        const T x0 = Wm[0], nrm = sqrt(p), ax0 = x0 < 0 ? -x0 : x0;
+        const T alpha = x0 >= 0 ? -nrm : nrm;
+        s_alpha[0] = alpha;
+        s_vn2[0] = (p > 0) ? (T)2 * (p + nrm * ax0) : (T)0;
+        Wm[0] = x0 - alpha;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {
+      const T* x = Wm + (long long)j * ld;
+      const T vn2 = s_vn2[j & 1];
+      const bool active = vn2 > 0;
+      if (tid == 0) Lo[(long long)j * K + j] = s_alpha[j & 1];
+      const int q0 = j >> 2;
+      for (int base = j + 1; base < m; base += ngrp) {   // uniform trip count: shuffles below
+        const int jj = base + grp;
+        const bool valid = jj < m;
+        T* a = Wm + (long long)(valid ? jj : j) * ld;
+        T p0 = 0, p1 = 0;
+        if (valid && active) {
+#pragma unroll 2
+          for (int q = q0 + gl; q < nq; q += G) {
+            V2 xv, av;
+            if constexpr (sizeof(T) == 8) {
+              xv = *(const V2*)(x + 4 * q);
+              av = *(const V2*)(a + 4 * q);
+              p0 += xv.x * av.x + xv.y * av.y;
+              xv = *(const V2*)(x + 4 * q + 2);
+              av = *(const V2*)(a + 4 * q + 2);
+              p1 += xv.x * av.x + xv.y * av.y;
+            } else {
+              xv = *(const V2*)(x + 4 * q);
+              av = *(const V2*)(a + 4 * q);
+              p0 += xv.x * av.x + xv.y * av.y;
+              p1 += xv.z * av.z + xv.w * av.w;
+            }
+          }
+        }
+        T p = p0 + p1;
+        for (int o = G >> 1; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+        const T g = active ? (T)2 * p / vn2 : (T)0;
+        const bool first = base == j + 1;   // group 0 of the first pass holds row j + 1
+        T t2 = 0;
+        if (valid) {
+          for (int q = q0 + gl; q < nq; q += G) {
+            T* ap = a + 4 * q;
+            T e[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) e[u] = ap[u] - g * x[4 * q + u];
+            if constexpr (sizeof(T) == 8) {
+              *(V2*)ap = V2{e[0], e[1]};
+              *(V2*)(ap + 2) = V2{e[2], e[3]};
+            } else {
+              *(V2*)ap = V2{e[0], e[1], e[2], e[3]};
+            }
+            if (first)
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                if (4 * q + u > j) t2 += e[u] * e[u];
+          }
+          if (gl == 0) Lo[(long long)jj * K + j] = a[j];
+        }
+        if (first) {
+          for (int o = G >> 1; o > 0; o >>= 1) t2 += __shfl_xor_sync(0xffffffffu, t2, o);
+          // the lane holding column j + 1 of row j + 1 forms the next reflector
+          const int c1 = j + 1;
+          if (grp == 0 && c1 < nn && jj < m && gl == (c1 >> 2) - q0) {
+            const T x0 = a[c1], nrm = sqrt(t2), ax0 = x0 < 0 ? -x0 : x0;
+            const T alpha = x0 >= 0 ? -nrm : nrm;
+            s_alpha[c1 & 1] = alpha;
+            s_vn2[c1 & 1] = (t2 > 0) ? (T)2 * (t2 + nrm * ax0) : (T)0;
+            a[c1] = x0 - alpha;
+            for (int c = c1 & ~3; c < c1; ++c) a[c] = (T)0;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long cap) {
   __shared__ T red[32];
@@ -1302,6 +1416,7 @@ struct CudaBE {
   long long trunc_cap;   // elements of the Jacobi work area in shared memory
   int sms;
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
+  int lq2_smem_max = 0;  // ... and its shared-memory variant (kb_lq2; 0: not used)
   bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
   int* tc_err = nullptr; // raised by a tensor-core kernel whose completion wait ran out
   void (*tc_form_override)(TcSpec&) = nullptr;   // test hook: restrict the operand forms
@@ -1404,13 +1519,27 @@ struct CudaBE {
                kb_ein<T><<<g, 256, 0, st>>>(m, out, os, A, B, n, quad));
   }
   void lq(OpLq<T> op, int n) {
-    size_t bytes = (size_t)op.m * op.nn * sizeof(T);
-    int use = bytes <= (size_t)lq_smem_max ? 1 : 0;
     const int K = op.m < op.nn ? op.m : op.nn;
     double fl = 0;
     for (int j = 0; j < K; ++j) fl += 4.0 * (op.nn - j) * (op.m - j);
-    PV_KLAUNCH(prof, st, "kb_lq", (double)n * ((double)op.m * op.nn + (double)op.m * K) * sizeof(T),
-               fl * n, kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
+    const double lq_bytes = (double)n * ((double)op.m * op.nn + (double)op.m * K) * sizeof(T);
+    // shared-memory factorisation: G threads per row, row stride ld = G (mod 32)
+    const int G = op.nn >= 128 ? 16 : (op.nn >= 32 ? 8 : 4);
+    const int ld = op.nn + ((G - op.nn % 32) % 32 + 32) % 32;
+    const size_t bytes2 = (size_t)op.m * ld * sizeof(T);
+    if (op.nn % 4 == 0 && bytes2 <= (size_t)lq2_smem_max) {
+      int per_sm = (int)((size_t)(227 * 1024) / (bytes2 + 1024));
+      per_sm = per_sm < 2048 / LQ_THREADS ? per_sm : 2048 / LQ_THREADS;
+      per_sm = per_sm < 1 ? 1 : per_sm;
+      const int grid = n < sms * per_sm ? n : sms * per_sm;
+      PV_KLAUNCH(prof, st, "kb_lq", lq_bytes, fl * n,
+                 (kb_lq2<T, LQ_THREADS><<<grid, LQ_THREADS, bytes2, st>>>(op, n, ld, G)));
+      return;
+    }
+    size_t bytes = (size_t)op.m * op.nn * sizeof(T);
+    int use = bytes <= (size_t)lq_smem_max ? 1 : 0;
+    PV_KLAUNCH(prof, st, "kb_lq", lq_bytes, fl * n,
+               kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
     size_t bytes = (size_t)trunc_cap * sizeof(T) + (size_t)(op.nc + 4) * sizeof(T) +
