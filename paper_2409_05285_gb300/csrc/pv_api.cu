@@ -477,7 +477,9 @@ int make_batch_t(peps_ctx* c, int sms) {
       if ((rc = dalloc(c, &b->be.tc_err, sizeof(int)))) return rc;
       cudaError_t e = cudaMemsetAsync(b->be.tc_err, 0, sizeof(int), c->stream);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaFuncSetAttribute(kb_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kb_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
       b->be.tc = true;
     }

@@ -1440,19 +1440,22 @@ struct CudaBE {
            sizeof(T);
   }
   // resident tensor-core GEMM CTAs per SM allowed by registers and threads (cached)
-  int tc_by_regs = 0;
-  int tc_reg_limit() {
-    if (!tc_by_regs) {
+  int tc_by_regs[2] = {0, 0};
+  int tc_reg_limit(bool pref) {
+    int& lim = tc_by_regs[pref ? 1 : 0];
+    if (!lim) {
       cudaFuncAttributes fa;
       int regs = 64;
-      if (cudaFuncGetAttributes(&fa, kb_gemm_tc) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      cudaError_t e = pref ? cudaFuncGetAttributes(&fa, kb_gemm_tc<true>)
+                           : cudaFuncGetAttributes(&fa, kb_gemm_tc<false>);
+      if (e == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
       else cudaGetLastError();
       regs = (regs + 7) & ~7;   // per-warp allocation granularity
-      tc_by_regs = 65536 / (regs * TC_THREADS);
-      if (tc_by_regs > 2048 / TC_THREADS) tc_by_regs = 2048 / TC_THREADS;
-      if (tc_by_regs < 1) tc_by_regs = 1;
+      lim = 65536 / (regs * TC_THREADS);
+      if (lim > 2048 / TC_THREADS) lim = 2048 / TC_THREADS;
+      if (lim < 1) lim = 1;
     }
-    return tc_by_regs;
+    return lim;
   }
 
   static int gx(long long n, int t) { return (int)((n + t - 1) / t); }
@@ -1474,7 +1477,7 @@ struct CudaBE {
         // memory columns, registers)
         int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
         int by_tmem = 512 / tc_cols(t.TN);
-        int by_regs = tc_reg_limit();
+        int by_regs = tc_reg_limit(t.pref != 0);
         per_sm = per_sm < by_tmem ? per_sm : by_tmem;
         per_sm = per_sm < by_regs ? per_sm : by_regs;
         per_sm = per_sm < 16 ? per_sm : 16;
@@ -1483,9 +1486,14 @@ struct CudaBE {
         gy = gy < 1 ? 1 : (gy > n ? n : gy);
         gy = gy > 65535 ? 65535 : gy;
         dim3 gr(tilesM * tilesN, (unsigned)gy);
-        PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
-                   kb_gemm_tc<<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A, swap ? A : B,
-                                                             n, tilesN, tc_err));
+        if (t.pref)
+          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                     kb_gemm_tc<true><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
+                                                                     swap ? A : B, n, tilesN, tc_err));
+        else
+          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                     kb_gemm_tc<false><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
+                                                                      swap ? A : B, n, tilesN, tc_err));
         return;
       }
     }

@@ -29,6 +29,7 @@ struct TcSpec {
   int Kc;                    // contraction chunk: a multiple of 8, at most 64
   int modeP, modeQ;          // operand gather forms (TC_SCALAR, TC_VEC_K, TC_VEC_T)
   int vecC;                  // 16-byte stores of four consecutive columns of C
+  int pref;                  // one chunk small enough to stage in registers (next chain prefetched)
 };
 
 constexpr int TC_ROWS = 128;
@@ -67,6 +68,8 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap) {
   t.Kc = k8 < TC_KMAX ? k8 : TC_KMAX;
   t.modeP = t.modeQ = TC_SCALAR;
   t.vecC = 0;
+  // register staging holds 16 values of P and 8 of Q per thread
+  t.pref = (g.K <= t.Kc && t.Kc <= 16 && t.TN * t.Kc <= 1024) ? 1 : 0;
   return true;
 }
 
@@ -96,6 +99,7 @@ inline void tc_forms(TcSpec& t, bool p_al, bool q_al, bool c_al) {
   t.modeQ = tc_mode(q_al, t.nc, t.cs, t.cQ, t.nk, t.ks, t.kQ);
   t.vecC = (c_al && t.nc > 0 && t.cC[t.nc - 1] == 1 && t.cs[t.nc - 1] % 4 == 0 &&
             tc_all4(t.cC, t.nc - 1) && tc_all4(t.rC, t.nr)) ? 1 : 0;
+  if (t.modeP == TC_SCALAR || t.modeQ == TC_SCALAR) t.pref = 0;
 }
 
 inline size_t tc_smem_bytes(const TcSpec& t) {
@@ -294,11 +298,117 @@ __device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ 
   }
 }
 
+// Register-staged gather for chunks small enough to prefetch (at most 4 * NV elements or
+// NV 16-byte vectors per thread): tc_pload issues the global loads of one chunk into
+// registers, tc_pstore rounds them and writes the canonical layout, so the loads of the
+// next chain can be in flight while the current chain's MMA and epilogue run.
+template <int NV>
+__device__ __forceinline__ void tc_pload(float4 (&r)[NV], const float* __restrict__ src, int mode,
+                                         int rows, int Kc, int K, const int* roff,
+                                         const int* koff, int tid) {
+  const int qn = Kc >> 2;
+  if (mode == TC_VEC_K) {
+    const int total = (rows * Kc) >> 2;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int e = tid + u * TC_THREADS;
+      r[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (e < total) {
+        const int cm = e >> 3;
+        const int g = cm / qn, q = cm - g * qn;
+        const int ro = roff[g * 8 + (e & 7)], k = q * 4;
+        if (ro >= 0 && k < K) r[u] = __ldg((const float4*)(src + ro + koff[k]));
+      }
+    }
+  } else {
+    const int nrb = rows >> 2, total = nrb * qn, j = tid & 3;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int blk = (tid >> 2) + u * (TC_THREADS / 4);
+      r[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (blk < total) {
+        const int kq = blk / nrb, rb = blk - kq * nrb;
+        const int ro = roff[rb * 4], k = kq * 4 + j;
+        if (ro >= 0 && k < K) r[u] = __ldg((const float4*)(src + ro + koff[k]));
+      }
+    }
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void tc_pstore(const float4 (&r)[NV], float* dst, int mode, int rows,
+                                          int Kc, int tid) {
+  const int qn = Kc >> 2;
+  if (mode == TC_VEC_K) {
+    const int total = (rows * Kc) >> 2;
+    float4* d4 = (float4*)dst;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int e = tid + u * TC_THREADS;
+      if (e < total) d4[e] = tc_round4(r[u]);
+    }
+  } else {
+    const int nrb = rows >> 2, total = nrb * qn, lane = tid & 31, j = lane & 3;
+    float4* d4 = (float4*)dst;
+#pragma unroll
+    for (int u = 0; u < NV; ++u) {
+      const int blk = (tid >> 2) + u * (TC_THREADS / 4);
+      float o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int c = (j - rr) & 3;
+        const float send = c == 0 ? r[u].x : (c == 1 ? r[u].y : (c == 2 ? r[u].z : r[u].w));
+        const float got = __shfl_sync(0xffffffffu, send, (lane & ~3) | ((j + rr) & 3));
+        const int idx = (j + rr) & 3;
+        o0 = idx == 0 ? got : o0;
+        o1 = idx == 1 ? got : o1;
+        o2 = idx == 2 ? got : o2;
+        o3 = idx == 3 ? got : o3;
+      }
+      if (blk < total) {
+        const int kq = blk / nrb, rb = blk - kq * nrb;
+        const int row = rb * 4 + j;
+        d4[((row >> 3) * qn + kq) * 8 + (row & 7)] =
+            make_float4(tc_round(o0), tc_round(o1), tc_round(o2), tc_round(o3));
+      }
+    }
+  }
+}
+
 // Descriptor of k-block kb (8 contraction indices = two core matrices along K).
 __device__ __forceinline__ uint64_t tc_kdesc(uint32_t base, int Kc, int kb) {
   return tc_desc(base + kb * 256, 128, (uint32_t)Kc * 32u);
 }
 
+// Accumulator rows of this warp's lane quarter to C (16-byte stores when C is unit-stride
+// in its columns).
+__device__ __forceinline__ void tc_epilogue(const TcSpec& t, uint32_t tmem, float* pc,
+                                            const int* rowC, const int* colC, int warp, int lane) {
+  const int oc = rowC[warp * 32 + lane];
+  for (int c0 = 0; c0 < t.TN; c0 += 16) {
+    uint32_t v[16];
+    tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+    if (oc >= 0) {
+      if (t.vecC) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const int cc = colC[c0 + j];
+          if (cc >= 0)
+            *(float4*)(pc + oc + cc) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                   __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cc = colC[c0 + j];
+          if (cc >= 0) pc[oc + cc] = __uint_as_float(v[j]);
+        }
+      }
+    }
+  }
+}
+
+template <bool PREF>
 __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, long long cs,
                                                          Operand<float> P, Operand<float> Q,
                                                          int n, int tilesN, int* err) {
@@ -352,7 +462,47 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   const int Kp = ((t.K + 7) >> 3) << 3;
   uint32_t phase = 0;
   bool ok = true;
-  for (int s = blockIdx.y; s < n && ok; s += gridDim.y) {
+  if constexpr (PREF) {
+    // one chunk per chain, operands staged in registers: the next chain's loads are issued
+    // right after this chain's MMA, before its completion wait and epilogue
+    float4 ra[4], rb[2];
+    int s = blockIdx.y;
+    if (s < n) {
+      tc_pload(ra, P.at(s), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
+      tc_pload(rb, Q.at(s), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+    }
+    for (; s < n && ok; s += gridDim.y) {
+      tc_pstore(ra, As, t.modeP, TC_ROWS, Kc, tid);
+      tc_pstore(rb, Bs, t.modeQ, TN, Kc, tid);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        for (int kb = 0; kb < (Kp >> 3); ++kb)
+          tc_mma(tmem, tc_kdesc(a_addr, Kc, kb), tc_kdesc(b_addr, Kc, kb), idesc, kb > 0 ? 1 : 0);
+        tc_commit(bar_a);
+      }
+      const int sn = s + gridDim.y;
+      if (sn < n) {
+        tc_pload(ra, P.at(sn), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
+        tc_pload(rb, Q.at(sn), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+      }
+      if (!tc_wait(bar_a, phase)) {
+        tc_wait(bar_a, phase);
+        abort_flag = 1;
+      }
+      phase ^= 1;
+      __syncthreads();
+      if (abort_flag) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      tc_epilogue(t, tmem, C + (long long)s * cs, rowC, colC, warp, lane);
+      tc_fence_before();
+    }
+  }
+  for (int s = blockIdx.y; s < n && ok && !PREF; s += gridDim.y) {
     const float* pp = P.at(s);
     const float* pq = Q.at(s);
     for (int k0 = 0; k0 < t.K; k0 += Kc) {
@@ -381,30 +531,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
     }
     if (!ok) break;
     tc_fence_after();
-    const int r = warp * 32 + lane;
-    const int oc = rowC[r];
-    float* pc = C + (long long)s * cs;
-    for (int c0 = 0; c0 < TN; c0 += 16) {
-      uint32_t v[16];
-      tc_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (oc >= 0) {
-        if (t.vecC) {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            const int cc = colC[c0 + j];
-            if (cc >= 0)
-              *(float4*)(pc + oc + cc) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
-                                                     __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int cc = colC[c0 + j];
-            if (cc >= 0) pc[oc + cc] = __uint_as_float(v[j]);
-          }
-        }
-      }
-    }
+    tc_epilogue(t, tmem, C + (long long)s * cs, rowC, colC, warp, lane);
     tc_fence_before();
   }
   __syncthreads();
