@@ -97,6 +97,34 @@ def test_eval_fp32_heis8_near_product_state(mode):
     _compare_eval(lat, th, S, chi, ctx.eval_batch(S), 1e-3, 1e-3, 5e-3)
 
 
+def test_eval_config_10x10_d6_chi36_spot_check():
+    # The 10x10 J1-J2 workload's sizes (D=6, chi=36: absorbed bond 216, truncated to 36) on
+    # the per-block engine, the one that takes them: two sampled configurations against the
+    # oracle in FP64 (about 15 s of oracle time each), then FP32 against FP64 on eight.
+    L, D, chi, J2 = 10, 6, 36, 0.5
+    lat = Lattice(L, L, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L, L, D, seed=101, scale=0.1, diag_bias=1.0)
+    S = wl.random_configs(L, L, 8, seed=102)
+    ctx = _ctx(L, L, D, chi, 8, J2=J2)
+    ctx.set_theta(th)
+    got = ctx.eval_batch(S)
+    la, sg, es, ea, O = got
+    _compare_eval(lat, th, S[:2], chi, (la[:2], sg[:2], es[:2], ea[:2], O[:2]), 1e-10, 1e-9, 1e-8)
+    f32 = _ctx(L, L, D, chi, 8, J2=J2, prec=binding.PEPS_FP32)
+    f32.set_theta(th)
+    la32, sg32, es32, ea32, _ = f32.eval_batch(S, with_O=False)
+    # Configurations with amplitudes e^-60 below the largest (the uniformly drawn half) are
+    # beyond float32's resolution of the truncated environments and are never sampled; the
+    # comparison takes the ones within e^-10 of the largest.
+    keep = la >= la.max() - 10.0
+    assert keep.sum() >= 4
+    assert np.all(sg32[keep] == sg[keep])
+    assert np.max(np.abs(la32 - la)[keep]) <= 2e-3
+    scale = max(1.0, float(np.max(np.abs(es[keep]))), float(np.max(np.abs(ea[keep]))))
+    assert np.max(np.abs(es32 - es)[keep]) <= 2e-3 * scale
+    assert np.max(np.abs(ea32 - ea)[keep]) <= 2e-3 * scale
+
+
 TF32_CASES = [  # sizes at which the transfer contractions reach the tensor-core path
     (6, 6, 4, 16, 0.0, 8),
     (4, 5, 4, 12, 0.5, 6),
