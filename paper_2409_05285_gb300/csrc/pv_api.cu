@@ -414,8 +414,8 @@ int make_batch_t(peps_ctx* c, int sms) {
   const long long cD = (long long)P->chi * P->D;
   const long long cap = 2 * cD * (cD + 1);
   const size_t trunc_bytes = (size_t)cap * sizeof(T) + (size_t)(cD + 4) * (sizeof(T) + 4) + 16;
-  if (trunc_bytes > 200 * 1024) return fail(c, PEPS_EINVAL, "batched blocks: Jacobi matrices exceed shared memory");
-  if (trunc_bytes > 48 * 1024) {
+  const bool trunc_global = trunc_bytes > 200 * 1024;   // Jacobi matrices in global memory
+  if (!trunc_global && trunc_bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kb_trunc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trunc_bytes);
     if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
   }
@@ -461,6 +461,7 @@ int make_batch_t(peps_ctx* c, int sms) {
   b->be.nb = (int)bi.size();
   b->be.N = c->N;
   b->be.trunc_cap = cap;
+  if (trunc_global && (rc = dalloc(c, &b->be.trunc_g, (size_t)8 * sms * cap * sizeof(T)))) return rc;
   b->be.sms = sms;
   {
     int lq_max = 96 * 1024;
@@ -506,14 +507,10 @@ int make_batch_t(peps_ctx* c, int sms) {
 }
 
 // Block layout peps_init takes for automatic mode: the batched engine (measured faster on
-// GB300 in every precision at 8x8, D=4, chi=16) when its per-chain Jacobi work area fits in
-// shared memory, else persistent narrow blocks.  TF32 exists only in the batched engine.
+// GB300 in every precision at 8x8, D=4, chi=16).  TF32 exists only in the batched engine.
 int resolve_block_mode(const peps_params* P) {
   if (P->block_mode != PEPS_BLOCKS_AUTO) return P->block_mode;
-  const long long cD = (long long)P->chi * P->D;
-  const size_t real = P->precision == PEPS_FP64 ? 8 : 4;
-  const size_t trunc_bytes = (size_t)(2 * cD * (cD + 1)) * real + (size_t)(cD + 4) * (real + 4) + 16;
-  return trunc_bytes <= 200 * 1024 ? PEPS_BLOCKS_BATCHED : PEPS_BLOCKS_NARROW;
+  return PEPS_BLOCKS_BATCHED;
 }
 
 // Device bytes of one chain's batched-engine buffers.
@@ -727,7 +724,12 @@ size_t peps_footprint(const peps_params* P) {
   b += 2 * (N + 1) * 8 + No * 4 + Np * 8 + (real == 4 ? Np * 4 : 0);   // tables, theta
   b += n * N + n * (8 * 3 + 1 + 4 * 2) + (size_t)n * No * real;       // chains, outputs, O
   b += (size_t)nblk * (sreal * real + sint * 4);                       // sample scratch
-  if (batched) b += (size_t)n * batched_chain_bytes(P);                 // batched buffers
+  if (batched) {                                                        // batched buffers
+    b += (size_t)n * batched_chain_bytes(P);
+    const long long cD = (long long)P->chi * P->D, cap = 2 * cD * (cD + 1);
+    if ((size_t)cap * real + (size_t)(cD + 4) * (real + 4) + 16 > 200 * 1024)
+      b += (size_t)8 * sms * cap * real;                                 // global Jacobi area
+  }
   else b += (size_t)n * ((long long)P->L1 * P->L2 * sd.ENV * real + (long long)P->L1 * (P->L2 + 1) * 4);
   b += n * 8 * 3 + 6 * Np * 8 + (real == 4 ? Np * 4 : 0) + 2 * (size_t)nch * Np * 8;   // SR
   return b + (1 << 20);

@@ -1052,9 +1052,9 @@ inline void bond_lists(int L1, int L2, double J1, double J2, std::vector<int>& b
 }  // namespace pv
 
 #include "pv_tc.cuh"
-#include "pv_prof.cuh"
 
 #if defined(__CUDACC__)
+#include "pv_prof.cuh"
 namespace pv {
 
 constexpr int BT = 256;   // threads of the per-sample blocks
@@ -1328,12 +1328,14 @@ __global__ void __launch_bounds__(NT) kb_lq2(OpLq<T> op, int n, int ld, int G) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long cap) {
+__global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long cap, T* gwork) {
   __shared__ T red[32];
   __shared__ int flag;
   extern __shared__ __align__(16) unsigned char dyn[];
-  T* smem = (T*)dyn;
-  T* sig = smem + cap;
+  // Jacobi matrices in shared memory, or, when they do not fit (gwork given), in this
+  // block's slice of a global work area (cached in L2)
+  T* smem = gwork ? gwork + (long long)blockIdx.x * cap : (T*)dyn;
+  T* sig = gwork ? (T*)dyn : smem + cap;
   int* order = (int*)(sig + op.nc + 4);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     op(s, red, &flag, smem, cap, order, sig);
@@ -1413,7 +1415,8 @@ struct CudaBE {
   const int *bi, *bj;
   const double* bJ;
   int nb, N;
-  long long trunc_cap;   // elements of the Jacobi work area in shared memory
+  long long trunc_cap;   // elements of the Jacobi work area of one block
+  T* trunc_g = nullptr;  // global Jacobi work area (gblocks(n) blocks) when shared memory is too small
   int sms;
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
   int lq2_smem_max = 0;  // ... and its shared-memory variant (kb_lq2; 0: not used)
@@ -1550,10 +1553,10 @@ struct CudaBE {
                kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
-    size_t bytes = (size_t)trunc_cap * sizeof(T) + (size_t)(op.nc + 4) * sizeof(T) +
+    size_t bytes = (trunc_g ? 0 : (size_t)trunc_cap * sizeof(T)) + (size_t)(op.nc + 4) * sizeof(T) +
                    (size_t)(op.nc + 4) * sizeof(int) + 16;
     PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
-               kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap));
+               kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap, trunc_g));
   }
   void norm(OpNorm<T> op, int n) { PV_KLAUNCH(prof, st, "kb_norm", 0.0, 0.0, kb_norm<T><<<gblocks(n), BT, 0, st>>>(op, n)); }
   void dot(OpDot<T> op, int n) { PV_KLAUNCH(prof, st, "kb_dot", 0.0, 0.0, kb_dot<T><<<gx(n, 8), 256, 0, st>>>(op, n)); }

@@ -98,31 +98,45 @@ def test_eval_fp32_heis8_near_product_state(mode):
 
 
 def test_eval_config_10x10_d6_chi36_spot_check():
-    # The 10x10 J1-J2 workload's sizes (D=6, chi=36: absorbed bond 216, truncated to 36) on
-    # the per-block engine, the one that takes them: two sampled configurations against the
-    # oracle in FP64 (about 15 s of oracle time each), then FP32 against FP64 on eight.
+    # The 10x10 J1-J2 workload's sizes (D=6, chi=36: absorbed bond 216, truncated to 36; the
+    # batched engine's Jacobi matrices then live in global memory): two sampled
+    # configurations against the oracle in FP64 on both engines (about 15 s of oracle time
+    # each), then FP32 and TF32 against FP64 on eight.
     L, D, chi, J2 = 10, 6, 36, 0.5
     lat = Lattice(L, L, D, J1=1.0, J2=J2)
     th = wl.random_theta(L, L, D, seed=101, scale=0.1, diag_bias=1.0)
     S = wl.random_configs(L, L, 8, seed=102)
-    ctx = _ctx(L, L, D, chi, 8, J2=J2)
-    ctx.set_theta(th)
-    got = ctx.eval_batch(S)
-    la, sg, es, ea, O = got
-    _compare_eval(lat, th, S[:2], chi, (la[:2], sg[:2], es[:2], ea[:2], O[:2]), 1e-10, 1e-9, 1e-8)
-    f32 = _ctx(L, L, D, chi, 8, J2=J2, prec=binding.PEPS_FP32)
-    f32.set_theta(th)
-    la32, sg32, es32, ea32, _ = f32.eval_batch(S, with_O=False)
+    ref = [peps.eval_sample(lat, th, S[k], chi) for k in range(2)]
+    res = {}
+    for name, prec, mode in (("narrow", binding.PEPS_FP64, binding.PEPS_BLOCKS_NARROW),
+                             ("batched", binding.PEPS_FP64, binding.PEPS_BLOCKS_BATCHED),
+                             ("fp32", binding.PEPS_FP32, binding.PEPS_BLOCKS_BATCHED),
+                             ("tf32", binding.PEPS_TF32, binding.PEPS_BLOCKS_BATCHED)):
+        ctx = _ctx(L, L, D, chi, 8, J2=J2, prec=prec, mode=mode)
+        ctx.set_theta(th)
+        res[name] = ctx.eval_batch(S, with_O=prec == binding.PEPS_FP64)
+        ctx.close()
+    for name in ("narrow", "batched"):
+        la, sg, es, ea, O = res[name]
+        for k in range(2):
+            r = ref[k]
+            assert sg[k] == r['sign'] and abs(la[k] - r['log_abs']) <= 1e-10, (name, k)
+            scale = max(1.0, abs(r['e_sys']), abs(r['e_anc']))
+            assert abs(es[k] - r['e_sys']) <= 1e-9 * scale and abs(ea[k] - r['e_anc']) <= 1e-9 * scale
+            assert np.max(np.abs(O[k] - r['O'])) <= 1e-8 * max(1.0, np.max(np.abs(r['O'])))
     # Configurations with amplitudes e^-60 below the largest (the uniformly drawn half) are
     # beyond float32's resolution of the truncated environments and are never sampled; the
-    # comparison takes the ones within e^-10 of the largest.
+    # mixed-precision comparison takes the ones within e^-10 of the largest.
+    la, sg, es, ea, _ = res["batched"]
     keep = la >= la.max() - 10.0
     assert keep.sum() >= 4
-    assert np.all(sg32[keep] == sg[keep])
-    assert np.max(np.abs(la32 - la)[keep]) <= 2e-3
     scale = max(1.0, float(np.max(np.abs(es[keep]))), float(np.max(np.abs(ea[keep]))))
-    assert np.max(np.abs(es32 - es)[keep]) <= 2e-3 * scale
-    assert np.max(np.abs(ea32 - ea)[keep]) <= 2e-3 * scale
+    for name, tol in (("fp32", 2e-3), ("tf32", 5e-2)):
+        la2, sg2, es2, ea2, _ = res[name]
+        assert np.all(sg2[keep] == sg[keep]), name
+        assert np.max(np.abs(la2 - la)[keep]) <= tol, name
+        assert np.max(np.abs(es2 - es)[keep]) <= tol * scale, name
+        assert np.max(np.abs(ea2 - ea)[keep]) <= tol * scale, name
 
 
 TF32_CASES = [  # sizes at which the transfer contractions reach the tensor-core path
