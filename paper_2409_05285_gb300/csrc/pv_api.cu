@@ -474,16 +474,21 @@ int make_batch_t(peps_ctx* c, int sms) {
     if (e != cudaSuccess) cudaGetLastError();
   }
   if constexpr (std::is_same<T, float>::value) {
-    if (P->precision == PEPS_TF32) {
-      if ((rc = dalloc(c, &b->be.tc_err, sizeof(int)))) return rc;
-      cudaError_t e = cudaMemsetAsync(b->be.tc_err, 0, sizeof(int), c->stream);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kb_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
-      b->be.tc = true;
-    }
+    // float32 storage: GEMM-shaped contractions on the tensor cores, with split (3xTF32)
+    // operands in PEPS_FP32 (float32-accurate products) and plain TF32 in PEPS_TF32, which
+    // also takes the right factors from the Gram matrix
+    if ((rc = dalloc(c, &b->be.tc_err, sizeof(int)))) return rc;
+    cudaError_t e = cudaMemsetAsync(b->be.tc_err, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
+    b->be.tc = true;
+    b->be.tc_split = P->precision == PEPS_FP32;
+    b->run.gram_lq = P->precision == PEPS_TF32;
   }
   b->N = c->N;
   b->No = c->No;

@@ -393,6 +393,15 @@ struct OpTrunc {
 };
 
 template <typename T>
+struct OpChol {   // Lf[s] (m x m, lower) with Lf Lf^T = G[s] (symmetric positive semidefinite)
+  const T* G;
+  long long gs;
+  T* Lf;
+  long long ls;
+  int m;
+};
+
+template <typename T>
 struct OpNorm {   // x[s] /= max|x[s]|, ls[s] += log max
   T* x;
   long long xs, len;
@@ -649,6 +658,7 @@ struct BatchRunner {
   T jtol;
   int max_sweeps;
   double flops = 0;
+  bool gram_lq = false;   // right factors from the Gram matrix (the TF32 path)
   unsigned long long* sweeps;   // Jacobi sweep counter (device or host)
 
   BatchRunner(BE& be_) : be(be_) {}
@@ -678,11 +688,11 @@ struct BatchRunner {
   static Operand<T> bat(const T* base, long long stride) { return batch_op<T>(base, stride); }
 
   void ein(T* out, long long os, const char* so, Operand<T> A, const char* sa, Operand<T> B,
-           const char* sb, const Dims& d, int n) {
+           const char* sb, const Dims& d, int n, bool exact = false) {
     Spec raw = make_spec(so, sa, sb, d);
     MSpec m = merge_spec(raw);
     flops += m.flops * n;
-    be.ein(raw, m, out, os, A, B, n);
+    be.ein(raw, m, out, os, A, B, n, exact);
   }
 
   // ---------------------------------------------------------------- environments
@@ -729,8 +739,17 @@ struct BatchRunner {
       ein(b.W, b.CB, "apk", bat(b.Cs, b.CB), "apb", bat(b.Lf + (long long)(c + 1) * b.LB, b.sLf),
           "bk", dm, n);
       int m = bc[c], nn = p * kf[c + 1];
-      be.lq(OpLq<T>{b.Lf + (long long)c * b.LB, b.sLf, b.W, b.CB, m, nn, nullptr}, n);
-      flops += lq_flops(m, nn) * n;
+      if (gram_lq && nn >= m && m >= 16) {
+        // a factor of the right Gram matrix W W^T (float32 products, semidefinite Cholesky)
+        Dims dg;
+        dg.set('a', m).set('e', m).set('p', p).set('k', kf[c + 1]);
+        ein(b.Y, b.LB, "ae", bat(b.W, b.CB), "apk", bat(b.W, b.CB), "epk", dg, n, true);
+        be.chol(OpChol<T>{b.Y, b.LB, b.Lf + (long long)c * b.LB, b.sLf, m}, n);
+        flops += (double)m * m * m / 3.0 * n;
+      } else {
+        be.lq(OpLq<T>{b.Lf + (long long)c * b.LB, b.sLf, b.W, b.CB, m, nn, nullptr}, n);
+        flops += lq_flops(m, nn) * n;
+      }
       kf[c] = m < nn ? m : nn;
     }
     be.set(b.carry, (long long)chi * (chi * D), 0, (T)1, n);
@@ -1327,6 +1346,53 @@ __global__ void __launch_bounds__(NT) kb_lq2(OpLq<T> op, int n, int ld, int G) {
   }
 }
 
+// Semidefinite Cholesky factor of each chain's m x m Gram matrix in shared memory (row
+// stride m + 1): pivots below m eps max(diag) zero their column (rank-deficient Grams).
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  T* A = (T*)dyn;
+  __shared__ T red[32];
+  __shared__ T s_piv;
+  const int m = op.m, ld = m + 1;
+  const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    const T* G = op.G + (long long)s * op.gs;
+    T* L = op.Lf + (long long)s * op.ls;
+    T dmax = 0;
+    for (int i = threadIdx.x; i < m * m; i += BT) {
+      const int r = i / m, c = i - r * m;
+      const T v = G[i];
+      A[r * ld + c] = v;
+      if (r == c) dmax = v > dmax ? v : dmax;
+    }
+    dmax = cta_max(dmax, red);
+    const T tol = (T)m * eps * dmax;
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+      if (threadIdx.x == 0) {
+        const T d = A[j * ld + j];
+        s_piv = d > tol ? sqrt(d) : (T)0;
+      }
+      __syncthreads();
+      const T l = s_piv, inv = l > 0 ? (T)1 / l : (T)0;
+      for (int i = j + threadIdx.x; i < m; i += BT) A[i * ld + j] = i == j ? l : A[i * ld + j] * inv;
+      __syncthreads();
+      const int w = m - j - 1;
+      for (int idx = threadIdx.x; idx < w * w; idx += BT) {
+        const int i = j + 1 + idx / w, k = j + 1 + idx % w;
+        A[i * ld + k] -= A[i * ld + j] * A[k * ld + j];
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < m * m; i += BT) {
+      const int r = i / m, c = i - r * m;
+      L[i] = c <= r ? A[r * ld + c] : (T)0;
+    }
+    __syncthreads();
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long cap, T* gwork) {
   __shared__ T red[32];
@@ -1421,6 +1487,7 @@ struct CudaBE {
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
   int lq2_smem_max = 0;  // ... and its shared-memory variant (kb_lq2; 0: not used)
   bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
+  bool tc_split = false; // ... with every operand split into two TF32 parts (3xTF32)
   int* tc_err = nullptr; // raised by a tensor-core kernel whose completion wait ran out
   void (*tc_form_override)(TcSpec&) = nullptr;   // test hook: restrict the operand forms
   KProf* prof = nullptr; // launch counter and optional per-kernel timing
@@ -1465,7 +1532,7 @@ struct CudaBE {
   int gblocks(int n) const { return n < 8 * sms ? n : 8 * sms; }
 
   void ein(const Spec& raw, const MSpec& m, T* out, long long os, Operand<T> A, Operand<T> B,
-           int n) {
+           int n, bool exact = false) {
     GSpec gs = gemm_spec(raw);
     if constexpr (std::is_same<T, float>::value) {
       TcSpec t;
@@ -1473,6 +1540,7 @@ struct CudaBE {
       if (tc && tc_plan(gs, t, swap)) {
         tc_forms(t, op_al16(swap ? B : A), op_al16(swap ? A : B),
                  ((uintptr_t)out % 16 == 0) && os % 4 == 0);
+        t.split = (exact || tc_split) ? 1 : 0;   // float32-accurate products (3xTF32)
         if (tc_form_override) tc_form_override(t);
         const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
         const size_t bytes = tc_smem_bytes(t);
@@ -1557,6 +1625,12 @@ struct CudaBE {
                    (size_t)(op.nc + 4) * sizeof(int) + 16;
     PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
                kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap, trunc_g));
+  }
+  void chol(OpChol<T> op, int n) {
+    const size_t bytes = (size_t)op.m * (op.m + 1) * sizeof(T);
+    PV_KLAUNCH(prof, st, "kb_chol", (double)n * 2.0 * op.m * op.m * sizeof(T),
+               (double)op.m * op.m * op.m / 3.0 * n,
+               kb_chol<T><<<gblocks(n), BT, bytes, st>>>(op, n));
   }
   void norm(OpNorm<T> op, int n) { PV_KLAUNCH(prof, st, "kb_norm", 0.0, 0.0, kb_norm<T><<<gblocks(n), BT, 0, st>>>(op, n)); }
   void dot(OpDot<T> op, int n) { PV_KLAUNCH(prof, st, "kb_dot", 0.0, 0.0, kb_dot<T><<<gx(n, 8), 256, 0, st>>>(op, n)); }

@@ -30,6 +30,7 @@ struct TcSpec {
   int modeP, modeQ;          // operand gather forms (TC_SCALAR, TC_VEC_K, TC_VEC_T)
   int vecC;                  // 16-byte stores of four consecutive columns of C
   int pref;                  // one chunk small enough to stage in registers (next chain prefetched)
+  int split;                 // 3xTF32: operands as hi + lo TF32 parts, products hi.hi + hi.lo + lo.hi
 };
 
 constexpr int TC_ROWS = 128;
@@ -70,6 +71,7 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap) {
   t.vecC = 0;
   // register staging holds 16 values of P and 8 of Q per thread
   t.pref = (g.K <= t.Kc && t.Kc <= 16 && t.TN * t.Kc <= 1024) ? 1 : 0;
+  t.split = 0;
   return true;
 }
 
@@ -103,7 +105,7 @@ inline void tc_forms(TcSpec& t, bool p_al, bool q_al, bool c_al) {
 }
 
 inline size_t tc_smem_bytes(const TcSpec& t) {
-  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) +
+  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1) +
          (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int);
 }
 
@@ -209,9 +211,21 @@ __device__ __forceinline__ float4 tc_round4(float4 v) {
   return make_float4(tc_round(v.x), tc_round(v.y), tc_round(v.z), tc_round(v.w));
 }
 
-__device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ src, int mode,
-                                          int rows, int Kc, int k0, int K, const int* roff,
-                                          const int* koff, int tid) {
+// Stores the TF32 rounding of v, and, for split operands, the rounding of the remainder.
+__device__ __forceinline__ void tc_st(float* hi, float* lo, int e, float v) {
+  const float h = tc_round(v);
+  hi[e] = h;
+  if (lo) lo[e] = tc_round(v - h);
+}
+__device__ __forceinline__ void tc_st4(float* hi, float* lo, int e, float4 v) {
+  const float4 h = tc_round4(v);
+  ((float4*)hi)[e] = h;
+  if (lo) ((float4*)lo)[e] = tc_round4(make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w));
+}
+
+__device__ __forceinline__ void tc_gather(float* dst, float* dlo, const float* __restrict__ src,
+                                          int mode, int rows, int Kc, int k0, int K,
+                                          const int* roff, const int* koff, int tid) {
   if (mode == TC_SCALAR) {
     const int qn = Kc >> 2, total = rows * Kc;
     for (int e0 = tid; e0 < total; e0 += TC_THREADS * TC_UNROLL) {
@@ -230,12 +244,11 @@ __device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ 
 #pragma unroll
       for (int u = 0; u < TC_UNROLL; ++u) {
         const int e = e0 + u * TC_THREADS;
-        if (e < total) dst[e] = tc_round(v[u]);
+        if (e < total) tc_st(dst, dlo, e, v[u]);
       }
     }
   } else if (mode == TC_VEC_K) {
     const int qn = Kc >> 2, total = (rows * Kc) >> 2;
-    float4* d4 = (float4*)dst;
     for (int e0 = tid; e0 < total; e0 += TC_THREADS * TC_UNROLL) {
       float4 v[TC_UNROLL];
 #pragma unroll
@@ -252,14 +265,13 @@ __device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ 
 #pragma unroll
       for (int u = 0; u < TC_UNROLL; ++u) {
         const int e = e0 + u * TC_THREADS;
-        if (e < total) d4[e] = tc_round4(v[u]);
+        if (e < total) tc_st4(dst, dlo, e, v[u]);
       }
     }
   } else {
     // blocks of 4 rows x 4 contraction indices; lane j of a quad holds index 4kq + j
     const int qn = Kc >> 2, nrb = rows >> 2, total = nrb * qn;
     const int lane = tid & 31, j = lane & 3;
-    float4* d4 = (float4*)dst;
     for (int b0 = tid >> 2; b0 - (lane >> 2) < total; b0 += (TC_THREADS / 4) * TC_UNROLL) {
       float4 v[TC_UNROLL];
 #pragma unroll
@@ -290,8 +302,7 @@ __device__ __forceinline__ void tc_gather(float* dst, const float* __restrict__ 
         if (blk < total) {
           const int kq = blk / nrb, rb = blk - kq * nrb;
           const int r = rb * 4 + j;
-          d4[((r >> 3) * qn + kq) * 8 + (r & 7)] =
-              make_float4(tc_round(o0), tc_round(o1), tc_round(o2), tc_round(o3));
+          tc_st4(dst, dlo, ((r >> 3) * qn + kq) * 8 + (r & 7), make_float4(o0, o1, o2, o3));
         }
       }
     }
@@ -336,20 +347,18 @@ __device__ __forceinline__ void tc_pload(float4 (&r)[NV], const float* __restric
 }
 
 template <int NV>
-__device__ __forceinline__ void tc_pstore(const float4 (&r)[NV], float* dst, int mode, int rows,
-                                          int Kc, int tid) {
+__device__ __forceinline__ void tc_pstore(const float4 (&r)[NV], float* dst, float* dlo, int mode,
+                                          int rows, int Kc, int tid) {
   const int qn = Kc >> 2;
   if (mode == TC_VEC_K) {
     const int total = (rows * Kc) >> 2;
-    float4* d4 = (float4*)dst;
 #pragma unroll
     for (int u = 0; u < NV; ++u) {
       const int e = tid + u * TC_THREADS;
-      if (e < total) d4[e] = tc_round4(r[u]);
+      if (e < total) tc_st4(dst, dlo, e, r[u]);
     }
   } else {
     const int nrb = rows >> 2, total = nrb * qn, lane = tid & 31, j = lane & 3;
-    float4* d4 = (float4*)dst;
 #pragma unroll
     for (int u = 0; u < NV; ++u) {
       const int blk = (tid >> 2) + u * (TC_THREADS / 4);
@@ -368,8 +377,7 @@ __device__ __forceinline__ void tc_pstore(const float4 (&r)[NV], float* dst, int
       if (blk < total) {
         const int kq = blk / nrb, rb = blk - kq * nrb;
         const int row = rb * 4 + j;
-        d4[((row >> 3) * qn + kq) * 8 + (row & 7)] =
-            make_float4(tc_round(o0), tc_round(o1), tc_round(o2), tc_round(o3));
+        tc_st4(dst, dlo, ((row >> 3) * qn + kq) * 8 + (row & 7), make_float4(o0, o1, o2, o3));
       }
     }
   }
@@ -378,6 +386,17 @@ __device__ __forceinline__ void tc_pstore(const float4 (&r)[NV], float* dst, int
 // Descriptor of k-block kb (8 contraction indices = two core matrices along K).
 __device__ __forceinline__ uint64_t tc_kdesc(uint32_t base, int Kc, int kb) {
   return tc_desc(base + kb * 256, 128, (uint32_t)Kc * 32u);
+}
+
+// The MMAs of k-block kb: hi.hi, and for split operands also hi.lo and lo.hi.
+__device__ __forceinline__ void tc_mma_k(int split, uint32_t tmem, uint32_t a, uint32_t b,
+                                         uint32_t al, uint32_t bl, int Kc, int kb,
+                                         uint32_t idesc, bool accumulate) {
+  tc_mma(tmem, tc_kdesc(a, Kc, kb), tc_kdesc(b, Kc, kb), idesc, accumulate ? 1 : 0);
+  if (split) {
+    tc_mma(tmem, tc_kdesc(a, Kc, kb), tc_kdesc(bl, Kc, kb), idesc, 1);
+    tc_mma(tmem, tc_kdesc(al, Kc, kb), tc_kdesc(b, Kc, kb), idesc, 1);
+  }
 }
 
 // Accumulator rows of this warp's lane quarter to C (16-byte stores when C is unit-stride
@@ -422,7 +441,9 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   const int m0 = tm * TC_ROWS, n0 = tn * TN;
   float* As = (float*)dyn;
   float* Bs = As + TC_ROWS * Kc;
-  int* rowP = (int*)(Bs + TN * Kc);
+  float* Al = t.split ? Bs + TN * Kc : nullptr;   // low parts of split operands
+  float* Bl = t.split ? Al + TC_ROWS * Kc : nullptr;
+  int* rowP = (int*)(t.split ? Bl + TN * Kc : Bs + TN * Kc);
   int* rowC = rowP + TC_ROWS;
   int* colQ = rowC + TC_ROWS;
   int* colC = colQ + TN;
@@ -459,6 +480,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   const uint32_t tmem = tslot;
   const uint32_t idesc = tc_idesc(TC_ROWS, TN);
   const uint32_t a_addr = tc_smem_addr(As), b_addr = tc_smem_addr(Bs);
+  const uint32_t al_addr = t.split ? tc_smem_addr(Al) : 0, bl_addr = t.split ? tc_smem_addr(Bl) : 0;
   const int Kp = ((t.K + 7) >> 3) << 3;
   uint32_t phase = 0;
   bool ok = true;
@@ -472,14 +494,14 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       tc_pload(rb, Q.at(s), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
     }
     for (; s < n && ok; s += gridDim.y) {
-      tc_pstore(ra, As, t.modeP, TC_ROWS, Kc, tid);
-      tc_pstore(rb, Bs, t.modeQ, TN, Kc, tid);
+      tc_pstore(ra, As, Al, t.modeP, TC_ROWS, Kc, tid);
+      tc_pstore(rb, Bs, Bl, t.modeQ, TN, Kc, tid);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
         for (int kb = 0; kb < (Kp >> 3); ++kb)
-          tc_mma(tmem, tc_kdesc(a_addr, Kc, kb), tc_kdesc(b_addr, Kc, kb), idesc, kb > 0 ? 1 : 0);
+          tc_mma_k(t.split, tmem, a_addr, b_addr, al_addr, bl_addr, Kc, kb, idesc, kb > 0);
         tc_commit(bar_a);
       }
       const int sn = s + gridDim.y;
@@ -506,16 +528,15 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
     const float* pp = P.at(s);
     const float* pq = Q.at(s);
     for (int k0 = 0; k0 < t.K; k0 += Kc) {
-      tc_gather(As, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
-      tc_gather(Bs, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
+      tc_gather(As, Al, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
+      tc_gather(Bs, Bl, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
         const int nkb = (Kp - k0 < Kc ? Kp - k0 : Kc) >> 3;
         for (int kb = 0; kb < nkb; ++kb)
-          tc_mma(tmem, tc_kdesc(a_addr, Kc, kb), tc_kdesc(b_addr, Kc, kb), idesc,
-                 (k0 > 0 || kb > 0) ? 1 : 0);
+          tc_mma_k(t.split, tmem, a_addr, b_addr, al_addr, bl_addr, Kc, kb, idesc, k0 > 0 || kb > 0);
         tc_commit(bar_a);
       }
       if (!tc_wait(bar_a, phase)) {
