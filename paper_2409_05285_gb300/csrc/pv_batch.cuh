@@ -1378,10 +1378,11 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
       const T l = s_piv, inv = l > 0 ? (T)1 / l : (T)0;
       for (int i = j + threadIdx.x; i < m; i += BT) A[i * ld + j] = i == j ? l : A[i * ld + j] * inv;
       __syncthreads();
-      const int w = m - j - 1;
-      for (int idx = threadIdx.x; idx < w * w; idx += BT) {
-        const int i = j + 1 + idx / w, k = j + 1 + idx % w;
-        A[i * ld + k] -= A[i * ld + j] * A[k * ld + j];
+      // trailing update on a 16 x 16 thread grid (BT = 256)
+      const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+      for (int i = j + 1 + ty; i < m; i += 16) {
+        const T lij = A[i * ld + j];
+        for (int k = j + 1 + tx; k < m; k += 16) A[i * ld + k] -= lij * A[k * ld + j];
       }
       __syncthreads();
     }
@@ -1488,6 +1489,7 @@ struct CudaBE {
   int lq2_smem_max = 0;  // ... and its shared-memory variant (kb_lq2; 0: not used)
   bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
   bool tc_split = false; // ... with every operand split into two TF32 parts (3xTF32)
+  int tc_min_rows = 64;  // smallest larger free side sent to the tensor cores
   int* tc_err = nullptr; // raised by a tensor-core kernel whose completion wait ran out
   void (*tc_form_override)(TcSpec&) = nullptr;   // test hook: restrict the operand forms
   KProf* prof = nullptr; // launch counter and optional per-kernel timing
@@ -1537,7 +1539,7 @@ struct CudaBE {
     if constexpr (std::is_same<T, float>::value) {
       TcSpec t;
       bool swap = false;
-      if (tc && tc_plan(gs, t, swap)) {
+      if (tc && tc_plan(gs, t, swap, tc_min_rows)) {
         tc_forms(t, op_al16(swap ? B : A), op_al16(swap ? A : B),
                  ((uintptr_t)out % 16 == 0) && os % 4 == 0);
         t.split = (exact || tc_split) ? 1 : 0;   // float32-accurate products (3xTF32)

@@ -41,11 +41,11 @@ constexpr int TC_SCALAR = 0, TC_VEC_K = 1, TC_VEC_T = 2;
 
 // Plans C = A.B of a GEMM-shaped contraction for the tensor cores; false when the shape
 // does not suit them (no contraction worth the name, or both free sides small).
-inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap) {
+inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap, int tc_min_rows = 64) {
   if (!g.ok || g.K < 4 || g.K > 4096) return false;
   swap = g.N > g.M;
   const int M = swap ? g.N : g.M, N = swap ? g.M : g.N;
-  if (M < 64) return false;
+  if (M < tc_min_rows) return false;
   t.M = M;
   t.N = N;
   t.K = g.K;
