@@ -1544,30 +1544,38 @@ struct CudaBE {
                  ((uintptr_t)out % 16 == 0) && os % 4 == 0);
         t.split = (exact || tc_split) ? 1 : 0;   // float32-accurate products (3xTF32)
         if (tc_form_override) tc_form_override(t);
-        const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
-        const size_t bytes = tc_smem_bytes(t);
-        // persistent grid of the CTAs that can be resident at once (shared memory, tensor
-        // memory columns, registers)
-        int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
-        int by_tmem = 512 / tc_cols(t.TN);
-        int by_regs = tc_reg_limit(t.pref != 0);
-        per_sm = per_sm < by_tmem ? per_sm : by_tmem;
-        per_sm = per_sm < by_regs ? per_sm : by_regs;
-        per_sm = per_sm < 16 ? per_sm : 16;
-        per_sm = per_sm < 1 ? 1 : per_sm;
-        long long gy = (long long)sms * per_sm / (tilesM * tilesN);
-        gy = gy < 1 ? 1 : (gy > n ? n : gy);
-        gy = gy > 65535 ? 65535 : gy;
-        dim3 gr(tilesM * tilesN, (unsigned)gy);
-        if (t.pref)
-          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
-                     kb_gemm_tc<true><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
-                                                                     swap ? A : B, n, tilesN, tc_err));
-        else
-          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
-                     kb_gemm_tc<false><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
-                                                                      swap ? A : B, n, tilesN, tc_err));
-        return;
+        // stay within the 200 KB of shared memory the kernel is configured for
+        const size_t smem_cap = 200 * 1024;
+        while (tc_smem_bytes(t) > smem_cap && t.Kc > 8) {
+          t.Kc -= 8;
+          t.pref = 0;
+        }
+        if (tc_smem_bytes(t) <= smem_cap) {
+          const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
+          const size_t bytes = tc_smem_bytes(t);
+          // persistent grid of the CTAs that can be resident at once (shared memory, tensor
+          // memory columns, registers)
+          int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
+          int by_tmem = 512 / tc_cols(t.TN);
+          int by_regs = tc_reg_limit(t.pref != 0);
+          per_sm = per_sm < by_tmem ? per_sm : by_tmem;
+          per_sm = per_sm < by_regs ? per_sm : by_regs;
+          per_sm = per_sm < 16 ? per_sm : 16;
+          per_sm = per_sm < 1 ? 1 : per_sm;
+          long long gy = (long long)sms * per_sm / (tilesM * tilesN);
+          gy = gy < 1 ? 1 : (gy > n ? n : gy);
+          gy = gy > 65535 ? 65535 : gy;
+          dim3 gr(tilesM * tilesN, (unsigned)gy);
+          if (t.pref)
+            PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                       kb_gemm_tc<true><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
+                                                                       swap ? A : B, n, tilesN, tc_err));
+          else
+            PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                       kb_gemm_tc<false><<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A,
+                                                                        swap ? A : B, n, tilesN, tc_err));
+          return;
+        }
       }
     }
     if (gs.ok && gs.K > 1) {
