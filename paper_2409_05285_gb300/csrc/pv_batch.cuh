@@ -1550,13 +1550,20 @@ struct CudaBE {
           t.Kc -= 8;
           t.pref = 0;
         }
+        {
+          // two operand stages and accumulators (consecutive chains pipelined) only for small
+          // single-chunk stages: larger ones cost more in resident CTAs than they gain
+          const size_t stage = (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1);
+          t.nst = (t.K <= t.Kc && stage <= 12 * 1024) ? 2 : 1;
+          if (tc_smem_bytes(t) > smem_cap) t.nst = 1;
+        }
         if (tc_smem_bytes(t) <= smem_cap) {
           const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
           const size_t bytes = tc_smem_bytes(t);
           // persistent grid of the CTAs that can be resident at once (shared memory, tensor
           // memory columns, registers)
           int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
-          int by_tmem = 512 / tc_cols(t.TN);
+          int by_tmem = 512 / tc_cols(t.TN * tc_stages(t));
           int by_regs = tc_reg_limit(t.pref != 0);
           per_sm = per_sm < by_tmem ? per_sm : by_tmem;
           per_sm = per_sm < by_regs ? per_sm : by_regs;

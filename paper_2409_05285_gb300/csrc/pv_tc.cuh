@@ -31,6 +31,7 @@ struct TcSpec {
   int vecC;                  // 16-byte stores of four consecutive columns of C
   int pref;                  // one chunk small enough to stage in registers (next chain prefetched)
   int split;                 // 3xTF32: operands as hi + lo TF32 parts, products hi.hi + hi.lo + lo.hi
+  int nst;                   // operand stages / accumulators: 2 pipelines consecutive chains
 };
 
 constexpr int TC_ROWS = 128;
@@ -72,6 +73,7 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap, int tc_min_rows = 64)
   // register staging holds 16 values of P and 8 of Q per thread
   t.pref = (g.K <= t.Kc && t.Kc <= 16 && t.TN * t.Kc <= 1024) ? 1 : 0;
   t.split = 0;
+  t.nst = 1;
   return true;
 }
 
@@ -104,8 +106,12 @@ inline void tc_forms(TcSpec& t, bool p_al, bool q_al, bool c_al) {
   if (t.modeP == TC_SCALAR || t.modeQ == TC_SCALAR) t.pref = 0;
 }
 
+// Operand stages: two (double buffering across chains) when the planner chose it (one
+// chunk per chain, small stages), else one.
+PV_HD int tc_stages(const TcSpec& t) { return t.nst; }
+
 inline size_t tc_smem_bytes(const TcSpec& t) {
-  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1) +
+  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1) * tc_stages(t) +
          (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int);
 }
 
@@ -432,18 +438,18 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
                                                          Operand<float> P, Operand<float> Q,
                                                          int n, int tilesN, int* err) {
   extern __shared__ __align__(16) unsigned char dyn[];
-  __shared__ __align__(8) uint64_t bar;
+  __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = blockIdx.x / tilesN, tn = blockIdx.x - (blockIdx.x / tilesN) * tilesN;
   const int TN = t.TN, Kc = t.Kc;
   const int m0 = tm * TC_ROWS, n0 = tn * TN;
-  float* As = (float*)dyn;
-  float* Bs = As + TC_ROWS * Kc;
-  float* Al = t.split ? Bs + TN * Kc : nullptr;   // low parts of split operands
-  float* Bl = t.split ? Al + TC_ROWS * Kc : nullptr;
-  int* rowP = (int*)(t.split ? Bl + TN * Kc : Bs + TN * Kc);
+  const int nst = tc_stages(t);
+  // per stage: A hi, B hi, then (split) A lo, B lo
+  const int sa = TC_ROWS * Kc, sb = TN * Kc, sst = (sa + sb) * (t.split ? 2 : 1);
+  float* stage0 = (float*)dyn;
+  int* rowP = (int*)(stage0 + (long long)nst * sst);
   int* rowC = rowP + TC_ROWS;
   int* colQ = rowC + TC_ROWS;
   int* colC = colQ + TN;
@@ -460,8 +466,8 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
     else colQ[i] = colC[i] = -1;
   }
   for (int k = tid; k < t.K; k += TC_THREADS) gemm_offsets(k, t.nk, t.ks, t.kP, t.kQ, kPo[k], kQo[k]);
-  const uint32_t ncols = (uint32_t)tc_cols(TN);
-  const uint32_t bar_a = tc_smem_addr(&bar);
+  const uint32_t ncols = (uint32_t)tc_cols(TN * nst);
+  const uint32_t bar0 = tc_smem_addr(&bar[0]), bar1 = tc_smem_addr(&bar[1]);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      tc_smem_addr(&tslot)),
@@ -471,7 +477,8 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   }
   if (tid == 0) {
     abort_flag = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar_a), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -479,81 +486,123 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   tc_fence_after();
   const uint32_t tmem = tslot;
   const uint32_t idesc = tc_idesc(TC_ROWS, TN);
-  const uint32_t a_addr = tc_smem_addr(As), b_addr = tc_smem_addr(Bs);
-  const uint32_t al_addr = t.split ? tc_smem_addr(Al) : 0, bl_addr = t.split ? tc_smem_addr(Bl) : 0;
   const int Kp = ((t.K + 7) >> 3) << 3;
-  uint32_t phase = 0;
-  bool ok = true;
-  if constexpr (PREF) {
-    // one chunk per chain, operands staged in registers: the next chain's loads are issued
-    // right after this chain's MMA, before its completion wait and epilogue
-    float4 ra[4], rb[2];
+  uint32_t ph = 0u;   // phase bits of the two barriers (bit i: barrier i)
+
+  if (nst == 2) {
+    // One contraction chunk per chain, two operand stages and two accumulators: the MMA of
+    // chain i runs while the operands of chain i+1 are gathered (or, with PREF, while
+    // their prefetched registers are stored), and chain i's epilogue follows the next MMA.
+    float4 ra[PREF ? 4 : 1], rb[PREF ? 2 : 1];
+    int it = 0, prev = -1;
     int s = blockIdx.y;
-    if (s < n) {
-      tc_pload(ra, P.at(s), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
-      tc_pload(rb, Q.at(s), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+    if constexpr (PREF) {
+      if (s < n) {
+        tc_pload(ra, P.at(s), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
+        tc_pload(rb, Q.at(s), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+      }
     }
-    for (; s < n && ok; s += gridDim.y) {
-      tc_pstore(ra, As, Al, t.modeP, TC_ROWS, Kc, tid);
-      tc_pstore(rb, Bs, Bl, t.modeQ, TN, Kc, tid);
+    for (; s < n; s += gridDim.y, ++it) {
+      const int st = it & 1;
+      float* As = stage0 + (long long)st * sst;
+      float* Bs = As + sa;
+      float* Al = t.split ? Bs + sb : nullptr;
+      float* Bl = t.split ? Al + sa : nullptr;
+      if constexpr (PREF) {
+        tc_pstore(ra, As, Al, t.modeP, TC_ROWS, Kc, tid);
+        tc_pstore(rb, Bs, Bl, t.modeQ, TN, Kc, tid);
+      } else {
+        tc_gather(As, Al, P.at(s), t.modeP, TC_ROWS, Kc, 0, t.K, rowP, kPo, tid);
+        tc_gather(Bs, Bl, Q.at(s), t.modeQ, TN, Kc, 0, t.K, colQ, kQo, tid);
+      }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
       __syncthreads();
+      if (abort_flag) break;
       if (tid == 0) {
         tc_fence_after();
+        const uint32_t a = tc_smem_addr(As), b = tc_smem_addr(Bs);
+        const uint32_t al = t.split ? tc_smem_addr(Al) : 0, bl = t.split ? tc_smem_addr(Bl) : 0;
         for (int kb = 0; kb < (Kp >> 3); ++kb)
-          tc_mma_k(t.split, tmem, a_addr, b_addr, al_addr, bl_addr, Kc, kb, idesc, kb > 0);
-        tc_commit(bar_a);
+          tc_mma_k(t.split, tmem + (uint32_t)(st * TN), a, b, al, bl, Kc, kb, idesc, kb > 0);
+        tc_commit(st ? bar1 : bar0);
       }
-      const int sn = s + gridDim.y;
-      if (sn < n) {
-        tc_pload(ra, P.at(sn), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
-        tc_pload(rb, Q.at(sn), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+      if constexpr (PREF) {
+        const int sn = s + gridDim.y;
+        if (sn < n) {
+          tc_pload(ra, P.at(sn), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
+          tc_pload(rb, Q.at(sn), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+        }
       }
-      if (!tc_wait(bar_a, phase)) {
-        tc_wait(bar_a, phase);
+      if (it > 0) {   // the previous chain: its MMA was issued one iteration ago
+        const int ps = st ^ 1;
+        const uint32_t pb = (ph >> ps) & 1u;
+        if (!tc_wait(ps ? bar1 : bar0, pb)) {
+          tc_wait(ps ? bar1 : bar0, pb);
+          abort_flag = 1;
+        }
+        ph ^= 1u << ps;
+        tc_fence_after();
+        tc_epilogue(t, tmem + (uint32_t)(ps * TN), C + (long long)prev * cs, rowC, colC, warp, lane);
+      }
+      prev = s;
+    }
+    // the last MMA issued (iteration it - 1) has not been waited for yet
+    if (it > 0) {
+      const int ls = (it - 1) & 1;
+      const uint32_t pb = (ph >> ls) & 1u;
+      if (!tc_wait(ls ? bar1 : bar0, pb)) {
+        tc_wait(ls ? bar1 : bar0, pb);
         abort_flag = 1;
       }
-      phase ^= 1;
+      ph ^= 1u << ls;
       __syncthreads();
-      if (abort_flag) {
-        ok = false;
-        break;
+      if (!abort_flag) {
+        tc_fence_after();
+        tc_epilogue(t, tmem + (uint32_t)(ls * TN), C + (long long)prev * cs, rowC, colC, warp, lane);
       }
+    }
+    tc_fence_before();
+  } else {
+    // several chunks per chain: one stage, accumulate over the chunks, then the epilogue
+    float* As = stage0;
+    float* Bs = As + sa;
+    float* Al = t.split ? Bs + sb : nullptr;
+    float* Bl = t.split ? Al + sa : nullptr;
+    const uint32_t a = tc_smem_addr(As), b = tc_smem_addr(Bs);
+    const uint32_t al = t.split ? tc_smem_addr(Al) : 0, bl = t.split ? tc_smem_addr(Bl) : 0;
+    bool ok = true;
+    for (int s = blockIdx.y; s < n && ok; s += gridDim.y) {
+      const float* pp = P.at(s);
+      const float* pq = Q.at(s);
+      for (int k0 = 0; k0 < t.K; k0 += Kc) {
+        tc_gather(As, Al, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
+        tc_gather(Bs, Bl, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+          tc_fence_after();
+          const int nkb = (Kp - k0 < Kc ? Kp - k0 : Kc) >> 3;
+          for (int kb = 0; kb < nkb; ++kb)
+            tc_mma_k(t.split, tmem, a, b, al, bl, Kc, kb, idesc, k0 > 0 || kb > 0);
+          tc_commit(bar0);
+        }
+        if (!tc_wait(bar0, ph & 1u)) {
+          tc_wait(bar0, ph & 1u);
+          abort_flag = 1;
+        }
+        ph ^= 1u;
+        __syncthreads();
+        if (abort_flag) {
+          ok = false;
+          break;
+        }
+      }
+      if (!ok) break;
       tc_fence_after();
       tc_epilogue(t, tmem, C + (long long)s * cs, rowC, colC, warp, lane);
       tc_fence_before();
     }
-  }
-  for (int s = blockIdx.y; s < n && ok && !PREF; s += gridDim.y) {
-    const float* pp = P.at(s);
-    const float* pq = Q.at(s);
-    for (int k0 = 0; k0 < t.K; k0 += Kc) {
-      tc_gather(As, Al, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
-      tc_gather(Bs, Bl, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        const int nkb = (Kp - k0 < Kc ? Kp - k0 : Kc) >> 3;
-        for (int kb = 0; kb < nkb; ++kb)
-          tc_mma_k(t.split, tmem, a_addr, b_addr, al_addr, bl_addr, Kc, kb, idesc, k0 > 0 || kb > 0);
-        tc_commit(bar_a);
-      }
-      if (!tc_wait(bar_a, phase)) {
-        tc_wait(bar_a, phase);
-        abort_flag = 1;
-      }
-      phase ^= 1;
-      __syncthreads();
-      if (abort_flag) {
-        ok = false;
-        break;
-      }
-    }
-    if (!ok) break;
-    tc_fence_after();
-    tc_epilogue(t, tmem, C + (long long)s * cs, rowC, colC, warp, lane);
-    tc_fence_before();
   }
   __syncthreads();
   if (warp == 0) {
