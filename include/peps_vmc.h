@@ -200,6 +200,17 @@ typedef struct {
 int peps_profile(peps_ctx* ctx, int enable);
 int peps_profile_read(peps_ctx* ctx, peps_kernel_stat* out, int cap, int* n_out);
 
+/* Failure-detection self-test of the bounded waits in the tensor-core kernels (the paper
+ * has no counterpart).  Launches a small contraction on its own stream with its MMAs
+ * withheld, so its completion barrier never fires: the kernel's waits give up after their
+ * time limit (1 s each, about 2 s in all), it frees its tensor memory and raises its error
+ * flag; then a normal contraction on the same stream is checked against a host product.
+ * Returns PEPS_OK when both happen, PEPS_ESTATE if the withheld MMAs went unnoticed,
+ * PEPS_ETIMEOUT if the normal contraction timed out, PEPS_ENOTFINITE if its result is
+ * wrong, PEPS_ENOMEM / PEPS_ECUDA on allocation or CUDA errors.  Allocates and frees its
+ * own small buffers. */
+int peps_selftest_tc_timeout(void);
+
 /* ---------------------------------------------------------------- serving loop
  *
  * Continuous batching of cooling runs.  Requests are queued by peps_srv_submit (any host

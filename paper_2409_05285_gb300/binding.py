@@ -38,6 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
+    "peps_selftest_tc_timeout",
 ]
 
 
@@ -128,6 +129,7 @@ def load(path=None):
     lib.peps_last_error.argtypes = [vp]
     lib.peps_last_error.restype = ctypes.c_char_p
     lib.peps_version.restype = ctypes.c_char_p
+    lib.peps_selftest_tc_timeout.argtypes = []
     lib.peps_launches.argtypes = [vp]
     lib.peps_launches.restype = ctypes.c_longlong
     lib.peps_profile.argtypes = [vp, ip]

@@ -1307,3 +1307,77 @@ extern "C" int peps_eval_batch_noalloc(const peps_params* P, const double* theta
   if (e != cudaSuccess) return noalloc_fail(PEPS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
   return PEPS_OK;
 }
+
+namespace {
+void tc_selftest_no_mma(TcSpec& t) { t.no_mma = 1; }
+}  // namespace
+
+// Failure-detection self-test of the tensor-core kernels' bounded waits (the paper has no
+// counterpart).  A small contraction is launched with its MMAs withheld, so no arrival
+// ever reaches the completion barrier: every wait must give up after its time limit, the
+// kernel must free its tensor memory and raise its error flag, and a normal contraction on
+// the same stream must then succeed and match a host product.
+extern "C" int peps_selftest_tc_timeout(void) {
+  const int n = 4, M = 128, N = 16, K = 16;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreate(&st) != cudaSuccess) return PEPS_ECUDA;
+  float *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  int* derr = nullptr;
+  int rc = PEPS_OK;
+  std::vector<float> A((size_t)n * M * K), B((size_t)n * N * K), Cg((size_t)n * M * N);
+  for (size_t i = 0; i < A.size(); ++i) A[i] = (float)((i * 37) % 17) / 17.0f - 0.5f;
+  for (size_t i = 0; i < B.size(); ++i) B[i] = (float)((i * 11) % 13) / 13.0f - 0.5f;
+  auto done = [&](int code) {
+    cudaStreamSynchronize(st);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dC);
+    cudaFree(derr);
+    cudaStreamDestroy(st);
+    return code;
+  };
+  if (cudaMalloc(&dA, A.size() * 4) != cudaSuccess || cudaMalloc(&dB, B.size() * 4) != cudaSuccess ||
+      cudaMalloc(&dC, Cg.size() * 4) != cudaSuccess || cudaMalloc(&derr, sizeof(int)) != cudaSuccess)
+    return done(PEPS_ENOMEM);
+  cudaMemcpy(dA, A.data(), A.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, B.data(), B.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemset(derr, 0, sizeof(int));
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  CudaBE<float, float> be;
+  be.st = st;
+  be.sms = sms;
+  be.tc = true;
+  be.tc_err = derr;
+  Dims d;
+  d.set('x', M).set('y', N).set('k', K);
+  Spec raw = make_spec("xy", "xk", "yk", d);
+  MSpec m = merge_spec(raw);
+  for (int pass = 0; pass < 2 && rc == PEPS_OK; ++pass) {
+    be.tc_form_override = pass == 0 ? tc_selftest_no_mma : nullptr;
+    cudaMemsetAsync(dC, 0, Cg.size() * 4, st);
+    be.ein(raw, m, dC, (long long)M * N, batch_op<float>(dA, (long long)M * K),
+           batch_op<float>(dB, (long long)N * K), n);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return done(PEPS_ECUDA);
+    int h = -1;
+    cudaMemcpy(&h, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemset(derr, 0, sizeof(int));
+    if (pass == 0 && h != 1) rc = PEPS_ESTATE;       // the withheld MMAs went unnoticed
+    if (pass == 1 && h != 0) rc = PEPS_ETIMEOUT;     // a normal contraction timed out
+  }
+  if (rc != PEPS_OK) return done(rc);
+  cudaMemcpy(Cg.data(), dC, Cg.size() * 4, cudaMemcpyDeviceToHost);
+  for (int s = 0; s < n; ++s)
+    for (int x = 0; x < M; ++x)
+      for (int y = 0; y < N; ++y) {
+        double ref = 0, mag = 0;
+        for (int k = 0; k < K; ++k) {
+          const double p = (double)A[((size_t)s * M + x) * K + k] * B[((size_t)s * N + y) * K + k];
+          ref += p;
+          mag += std::fabs(p);
+        }
+        if (std::fabs(Cg[((size_t)s * M + x) * N + y] - ref) > 2e-3 * mag + 1e-6) rc = PEPS_ENOTFINITE;
+      }
+  return done(rc);
+}

@@ -32,12 +32,13 @@ struct TcSpec {
   int pref;                  // one chunk small enough to stage in registers (next chain prefetched)
   int split;                 // 3xTF32: operands as hi + lo TF32 parts, products hi.hi + hi.lo + lo.hi
   int nst;                   // operand stages / accumulators: 2 pipelines consecutive chains
+  int no_mma;                // self-test only: issue no MMA and no commit, so every wait runs out
 };
 
 constexpr int TC_ROWS = 128;
 constexpr int TC_THREADS = 128;
 constexpr int TC_KMAX = 64;
-constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of one completion wait (1 s)
 constexpr int TC_SCALAR = 0, TC_VEC_K = 1, TC_VEC_T = 2;
 
 // Plans C = A.B of a GEMM-shaped contraction for the tensor cores; false when the shape
@@ -74,6 +75,7 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap, int tc_min_rows = 64)
   t.pref = (g.K <= t.Kc && t.Kc <= 16 && t.TN * t.Kc <= 1024) ? 1 : 0;
   t.split = 0;
   t.nst = 1;
+  t.no_mma = 0;
   return true;
 }
 
@@ -173,8 +175,16 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
       : "memory");
 }
 
+__device__ __forceinline__ unsigned long long tc_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits for the phase `parity` of an mbarrier to complete; false after TC_WAIT_NS.
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  for (long long i = 0; i < TC_WAIT_LIMIT; ++i) {
+  const unsigned long long t0 = tc_now();
+  for (;;) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -183,8 +193,8 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (ok) return true;
+    if (tc_now() - t0 > TC_WAIT_NS) return false;
   }
-  return false;
 }
 
 // 16 consecutive accumulator columns of this thread's lane.
@@ -519,7 +529,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       tc_fence_before();
       __syncthreads();
       if (abort_flag) break;
-      if (tid == 0) {
+      if (tid == 0 && !t.no_mma) {
         tc_fence_after();
         const uint32_t a = tc_smem_addr(As), b = tc_smem_addr(Bs);
         const uint32_t al = t.split ? tc_smem_addr(Al) : 0, bl = t.split ? tc_smem_addr(Bl) : 0;
@@ -537,13 +547,17 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       if (it > 0) {   // the previous chain: its MMA was issued one iteration ago
         const int ps = st ^ 1;
         const uint32_t pb = (ph >> ps) & 1u;
-        if (!tc_wait(ps ? bar1 : bar0, pb)) {
+        bool good = tc_wait(ps ? bar1 : bar0, pb);
+        if (!good) {
           tc_wait(ps ? bar1 : bar0, pb);
           abort_flag = 1;
         }
+        good = __all_sync(0xffffffffu, good);   // tcgen05.ld below is warp-collective
         ph ^= 1u << ps;
-        tc_fence_after();
-        tc_epilogue(t, tmem + (uint32_t)(ps * TN), C + (long long)prev * cs, rowC, colC, warp, lane);
+        if (good) {
+          tc_fence_after();
+          tc_epilogue(t, tmem + (uint32_t)(ps * TN), C + (long long)prev * cs, rowC, colC, warp, lane);
+        }
       }
       prev = s;
     }
@@ -580,7 +594,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
         tc_gather(Bs, Bl, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && !t.no_mma) {
           tc_fence_after();
           const int nkb = (Kp - k0 < Kc ? Kp - k0 : Kc) >> 3;
           for (int kb = 0; kb < nkb; ++kb)
