@@ -292,6 +292,7 @@ struct peps_ctx {
   std::vector<void*> allocs;
   std::unique_ptr<BatchIface> batch;   // batched engine (block_mode PEPS_BLOCKS_BATCHED)
   pv::KProf kprof;                      // launch counter, optional per-kernel timing
+  bool o_vec4 = false;                  // every site slice of O holds a multiple of 4 entries
 };
 
 namespace {
@@ -579,6 +580,8 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
   }
   c->Np = c->toff[c->N];
   c->No = c->ooff[c->N];
+  c->o_vec4 = true;
+  for (int i = 0; i < c->N; ++i) c->o_vec4 = c->o_vec4 && (c->ooff[i + 1] - c->ooff[i]) % 4 == 0;
   std::vector<int> o2site(c->No);
   for (int i = 0; i < c->N; ++i)
     for (long long o = c->ooff[i]; o < c->ooff[i + 1]; ++o) o2site[o] = i;
@@ -948,9 +951,14 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   PV_TRY(launch_weights(c, p));
   // mean and gradient (one pass over O)
   dim3 cgrid((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
+  dim3 cgrid4((unsigned)((No / 4 + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);   // 4 columns a thread
   if (fp64(c))
     PV_KLAUNCH(&c->kprof, s, "k_colsum1", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1<double, true><<<cgrid, SR_THREADS, 0, s>>>(
         n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
+  else if (c->o_vec4)
+    PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32v<true><<<cgrid4, SR_THREADS, 0, s>>>(
+        n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
         c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
   else
     PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32<true><<<cgrid, SR_THREADS, 0, s>>>(
@@ -973,6 +981,10 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
                                                     c->d_toff, c->d_ooff, c->d_p, c->d_pf,
                                                     c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2,
                                                     c->d_sc));
+    else if (c->o_vec4)
+      PV_KLAUNCH(&c->kprof, s, "k_ov", ((double)n * No * 4.0 + (double)Np * 4.0), 0.0, k_ov_f32v<<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
+                                                   c->d_toff, c->d_ooff, c->d_pf, c->d_w,
+                                                   c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
     else
       PV_KLAUNCH(&c->kprof, s, "k_ov", ((double)n * No * (fp64(c) ? 8.0 : 4.0) + (double)Np * (fp64(c) ? 8.0 : 4.0)), 0.0, k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
                                                    c->d_toff, c->d_ooff, c->d_p, c->d_pf, c->d_w,
@@ -980,6 +992,10 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
     if (fp64(c))
       PV_KLAUNCH(&c->kprof, s, "k_colsum1", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1<double, false><<<cgrid, SR_THREADS, 0, s>>>(
           n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+          nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+    else if (c->o_vec4)
+      PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32v<false><<<cgrid4, SR_THREADS, 0, s>>>(
+          n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
           nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
     else
       PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32<false><<<cgrid, SR_THREADS, 0, s>>>(

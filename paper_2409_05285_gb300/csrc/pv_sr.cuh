@@ -190,6 +190,81 @@ __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restric
   }
 }
 
+// Float rows, 16-byte vectors: every site slice holds a multiple of four entries, so each
+// thread takes four consecutive columns of one site; the chunk's coefficients are staged in
+// shared memory and four rows are loaded before they are accumulated.
+template <bool TWO>
+__global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
+    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
+    const int* __restrict__ o2site, const long long* __restrict__ toff,
+    const long long* __restrict__ ooff, const double* __restrict__ c1,
+    const double* __restrict__ c2, const double* __restrict__ shift, double* __restrict__ part1,
+    double* __restrict__ part2, long long Np, const int* done) {
+  if (done && *done) return;
+  __shared__ float cx[OTV_CHUNK], cy[OTV_CHUNK];
+  const int ch = blockIdx.y;
+  const int i0 = ch * OTV_CHUNK, i1 = min(n, i0 + OTV_CHUNK);
+  const double Ebar_shift = TWO ? *shift : 0.0;
+  for (int i = threadIdx.x; i < i1 - i0; i += blockDim.x) {
+    cx[i] = (float)c1[i0 + i];
+    cy[i] = TWO ? (float)(c1[i0 + i] * (c2[i0 + i] - Ebar_shift)) : 0.f;
+  }
+  __syncthreads();
+  const long long o = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (o >= No) return;
+  const int j = o2site[o];
+  const long long k = o - ooff[j], sz = ooff[j + 1] - ooff[j];
+  float a[4][4], b[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a[q][c] = b[q][c] = 0.f;
+  int i = i0;
+  for (; i + 4 <= i1; i += 4) {
+    float4 v[4];
+    int st[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      v[u] = __ldg((const float4*)(O + (long long)(i + u) * No + o));
+      st[u] = S[(long long)(i + u) * N + j];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float x = cx[i + u - i0], y = cy[i + u - i0];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {   // branch-free: the other three states add zero
+        const float xq = st[u] == q ? x : 0.f, yq = st[u] == q ? y : 0.f;
+        a[q][0] += xq * v[u].x; a[q][1] += xq * v[u].y; a[q][2] += xq * v[u].z; a[q][3] += xq * v[u].w;
+        if (TWO) { b[q][0] += yq * v[u].x; b[q][1] += yq * v[u].y; b[q][2] += yq * v[u].z; b[q][3] += yq * v[u].w; }
+      }
+    }
+  }
+  for (; i < i1; ++i) {
+    const float4 v = __ldg((const float4*)(O + (long long)i * No + o));
+    const int sq = S[(long long)i * N + j];
+    const float x = cx[i - i0], y = cy[i - i0];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float xq = sq == q ? x : 0.f, yq = sq == q ? y : 0.f;
+      a[q][0] += xq * v.x; a[q][1] += xq * v.y; a[q][2] += xq * v.z; a[q][3] += xq * v.w;
+      if (TWO) { b[q][0] += yq * v.x; b[q][1] += yq * v.y; b[q][2] += yq * v.z; b[q][3] += yq * v.w; }
+    }
+  }
+  const long long t = toff[j] + k;
+  double* p1 = part1 + (long long)ch * Np;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p1[t + q * sz + c] = (double)a[q][c];
+  if (TWO) {
+    double* p2 = part2 + (long long)ch * Np;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p2[t + q * sz + c] = (double)b[q][c];
+  }
+}
+
 // Stage 2 for the mean and gradient: obar = sum_ch part1, g = sum_ch part2.
 __global__ void k_colsum2_grad(long long Np, int nch, const double* __restrict__ part1,
                                const double* __restrict__ part2, double* __restrict__ obar,
@@ -285,6 +360,48 @@ __global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
   double contrib = (lane == 0) ? yi : 0.0;
   double s = blk_sum(contrib, red);
   if (threadIdx.x == 0) ypart[blockIdx.x] = s;
+}
+
+// Float rows, 16-byte vectors (site slices of multiples of four entries): y_i = w_i (O_i.p - obar.p).
+__global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
+    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
+    const long long* __restrict__ toff, const long long* __restrict__ ooff,
+    const float* __restrict__ pf, const double* __restrict__ w, double* __restrict__ y,
+    double* __restrict__ ypart, int ndp, const double* __restrict__ dpart, const SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double obp = sum_parts(dpart, ndp);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  double yi = 0;
+  if (i < n) {
+    const float4* row = (const float4*)(O + (long long)i * No);
+    double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      const int s = S[(long long)i * N + j];
+      const long long o0 = ooff[j] >> 2, sz = (ooff[j + 1] - ooff[j]) >> 2;
+      const float4* pv = (const float4*)(pf + toff[j] + (long long)s * (sz << 2));
+      float a0 = 0.f, a1 = 0.f;
+      long long kk = lane;
+      for (; kk + 32 < sz; kk += 64) {
+        const float4 r0 = __ldg(row + o0 + kk), q0 = __ldg(pv + kk);
+        const float4 r1 = __ldg(row + o0 + kk + 32), q1 = __ldg(pv + kk + 32);
+        a0 += r0.x * q0.x + r0.y * q0.y + r0.z * q0.z + r0.w * q0.w;
+        a1 += r1.x * q1.x + r1.y * q1.y + r1.z * q1.z + r1.w * q1.w;
+      }
+      if (kk < sz) {
+        const float4 r0 = __ldg(row + o0 + kk), q0 = __ldg(pv + kk);
+        a0 += r0.x * q0.x + r0.y * q0.y + r0.z * q0.z + r0.w * q0.w;
+      }
+      acc += (double)(a0 + a1);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    yi = w[i] * (acc - obp);
+    if (lane == 0) y[i] = yi;
+  }
+  double contrib = (lane == 0) ? yi : 0.0;
+  double sm = blk_sum(contrib, red);
+  if (threadIdx.x == 0) ypart[blockIdx.x] = sm;
 }
 
 // q = sum_ch part - (sum y) obar + eps p ; block partials of p.q.

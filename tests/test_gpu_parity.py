@@ -273,6 +273,32 @@ def test_sr_step_matches_oracle(p):
     assert st['diag_frac'] == pytest.approx(o['diag_frac'])
 
 
+@pytest.mark.parametrize("prec", [binding.PEPS_FP32, binding.PEPS_TF32])
+def test_sr_step_float_o_rows_match_oracle(prec):
+    # Float O rows (the 16-byte vector O passes when every site slice holds a multiple of
+    # four entries, as at D=2 on 4x4): the SR update from the GPU's own evaluation against
+    # the oracle's SR step on those same float values.  Float32 products in the O passes
+    # (per-chunk sums of 128 samples, float64 across chunks) keep CG's attainable relative
+    # residual near 1e-6, which leaves x within a few 1e-3 of the float64 solution (2.7e-3
+    # seen with both the vector and the element-wise passes).
+    L, D, chi, n = 4, 2, 4, 256
+    lat = Lattice(L, L, D, J1=1.0)
+    th = wl.random_theta(L, L, D, seed=31, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L, L, n, seed=32)
+    ctx = _ctx(L, L, D, chi, n, prec=prec, mode=binding.PEPS_BLOCKS_BATCHED)
+    ctx.set_theta(th)
+    ctx.set_configs(S)
+    la, sg, es, ea, O = ctx.eval_batch(S)
+    ctx.eval_chains()
+    tau, eps = 0.05, 1e-1
+    ctx.sr_step(tau, eps=eps, max_cg=500, cg_tol=1e-6, p=2)
+    x_gpu = (th - ctx.get_theta()) / tau
+    O = O.astype(np.float64)
+    _, x, g, it, resid = sr.sr_step(lat, th, S, la, es, ea, O, 2, tau, eps, 1e-10, 500)
+    assert resid <= 1e-10
+    assert np.max(np.abs(x_gpu - x)) <= 1e-2 * np.max(np.abs(x))
+
+
 def test_sr_step_cg_maxit_warning_and_observables():
     L1, L2, D, chi, n = 3, 3, 2, 4, 24
     lat = Lattice(L1, L2, D)
