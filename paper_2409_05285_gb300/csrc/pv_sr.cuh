@@ -300,6 +300,14 @@ __device__ __forceinline__ double sum_parts(const double* part, int n) {
   return s;
 }
 
+// The same sum formed by the whole block (strided partials, then a tree): every thread of
+// the block must call it; all blocks get the same value.
+__device__ __forceinline__ double blk_sum_parts(const double* part, int n, double* red) {
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  return blk_sum(s, red);
+}
+
 // CG set-up: x = 0, r = p = g, rr = g.g, gnorm, done flag.
 __global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __restrict__ x,
                           double* __restrict__ r, double* __restrict__ p, float* __restrict__ pf,
@@ -334,7 +342,7 @@ __global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
                      const double* __restrict__ dpart, const SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
-  double obp = sum_parts(dpart, ndp);
+  double obp = blk_sum_parts(dpart, ndp, red);
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int i = blockIdx.x * (blockDim.x >> 5) + warp;
   double yi = 0;
@@ -370,7 +378,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
     double* __restrict__ ypart, int ndp, const double* __restrict__ dpart, const SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
-  double obp = sum_parts(dpart, ndp);
+  double obp = blk_sum_parts(dpart, ndp, red);
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int i = blockIdx.x * (blockDim.x >> 5) + warp;
   double yi = 0;
@@ -411,13 +419,19 @@ __global__ void k_otv2(long long Np, int nch, const double* __restrict__ part,
                        double* __restrict__ pqpart, SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
-  double sumy = sum_parts(ypart, nyp);
+  double sumy = blk_sum_parts(ypart, nyp, red);
   double eps = sc->eps;
   double s = 0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
        t += (long long)gridDim.x * blockDim.x) {
-    double a = 0;
-    for (int c = 0; c < nch; ++c) a += part[(long long)c * Np + t];
+    // eight chunk partials in flight at a time (fixed order: the sum is reproducible)
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int c = 0;
+    for (; c + 8 <= nch; c += 8)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += part[(long long)(c + u) * Np + t];
+    for (; c < nch; ++c) acc[0] += part[(long long)c * Np + t];
+    double a = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     double qt = a - sumy * obar[t] + eps * p[t];
     q[t] = qt;
     s += p[t] * qt;
@@ -433,7 +447,7 @@ __global__ void k_cg_a(long long Np, double* __restrict__ x, double* __restrict_
                        SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
-  double alpha = sc->rr / sum_parts(pqpart, npq);
+  double alpha = sc->rr / blk_sum_parts(pqpart, npq, red);
   double s = 0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
        t += (long long)gridDim.x * blockDim.x) {
@@ -454,7 +468,7 @@ __global__ void k_cg_b(long long Np, const double* __restrict__ r, double* __res
                        SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
-  double rr_new = sum_parts(rrpart, nrr);
+  double rr_new = blk_sum_parts(rrpart, nrr, red);
   double beta = rr_new / sc->rr;
   double s = 0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
