@@ -454,7 +454,7 @@ def run_serve(args):
         d = ta - (time.perf_counter() - t0)
         if d > 0:
             time.sleep(d)
-        ids.append(srv.submit(precision=binding.PEPS_FP32, **kw))
+        ids.append(srv.submit(precision=binding.PEPS_TF32, **kw))
     srv.drain()
     wall = time.perf_counter() - t0
     m = srv.metrics()
@@ -463,7 +463,7 @@ def run_serve(args):
                      "Poisson stream of cooling requests", "value": m["samples_per_s"],
            "unit": "samples/s", "n_gpus": 1, "latency_ms": {"p50": m["p50_ms"], "p99": m["p99_ms"]},
            "steps": m["steps"], "requests": len(ids), "wall_s": wall, "higher_is_better": True,
-           "dtype": "f32", "data": "synthetic",
+           "dtype": "tf32", "data": "synthetic",
            "config": {"workload": f"Poisson arrivals {args.rate}/s over {args.window} s, seed "
                                   f"{args.seed}; L in {{4,6,8}}, D in {{2,4}}, chi=D^2, J2~U[0,0.6], "
                                   "t_end in {0.02..0.1}, 1024 chains, tau=0.02",
