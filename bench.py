@@ -40,6 +40,27 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, device="cuda"):
+    """The slowest rank's time (replicas: the job ends when the last rank does)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank, world, ms_per_step):
+    """Whole-job samples/s: every rank advances its own n chains per step (weak scaling)."""
+    return world * n_per_rank / (ms_per_step / 1e3)
+
+
+def rank_seed(base, rank):
+    """Seed of a replica's chains and initial noise: independent chains on every rank."""
+    return base + rank
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during the timed region."""
 
@@ -169,7 +190,7 @@ def run_ours(args):
     stream = torch.cuda.Stream()
     n = args.chains or wl.n_samples
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
-                          init_noise=wl.init_noise, seed=wl.seed + rank, n_blocks=args.blocks,
+                          init_noise=wl.init_noise, seed=rank_seed(wl.seed, rank), n_blocks=args.blocks,
                           stream=ctypes_stream(stream), block_mode=BLOCK_MODES[args.block_mode])
     ctx.mc_sweep(args.burn, p=1)
     t0 = cooled_state(ctx, args.precool, wl.tau, 0.3)
@@ -225,13 +246,9 @@ def run_ours(args):
     kstats = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.launches() - launches0
-    total_ms = e_start.elapsed_time(e_end)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(e_start.elapsed_time(e_end))
     ms_per_step = total_ms / args.steps
-    samples_per_s = ws * n / (ms_per_step / 1e3)
+    samples_per_s = job_throughput(n, ws, ms_per_step)
 
     # end to end through the public API with host buffers: upload theta and the chain
     # configurations from pinned host memory, run the step, read theta' and S' back.
