@@ -199,6 +199,8 @@ def run_ours(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
         ctx.step(n_sweeps=1, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+    # launch shapes tuned on this context's chains (results do not depend on them)
+    tune = ctx.autotune(reps=1) if args.block_mode in ("auto", "batched") and not args.no_autotune else None
     clocks = Clocks(local)
     step_ms, mc_ms, eval_ms, sr_ms, eval_flops, mc_flops, cg_its, stats = [], [], [], [], [], [], [], []
     jac = []
@@ -304,6 +306,7 @@ def run_ours(args):
         "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"],
         "roofline": roofline,
         "kernels": kernels,
+        "autotune": tune,
         "kernels_by_phase": ({ph: kernel_shares(v) for ph, v in phase_k.items()}
                              if args.profile_all else None),
         "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
@@ -496,6 +499,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heis8")
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "fp64"])
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes of the batched engine")
     ap.add_argument("--profile-all", action="store_true",
                     help="time every kernel of the timed region (default: the GEMM kernels)")
     ap.add_argument("--chains", type=int, default=0)

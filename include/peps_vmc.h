@@ -182,6 +182,23 @@ int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
 /* Kernel launches this context has made since peps_init (every kernel of the library). */
 long long peps_launches(const peps_ctx* ctx);
 
+/* Autotuner of the batched engine's launch shapes, keyed on the problem geometry (d^2 = 4,
+ * D, chi, L1, L2, precision).  peps_autotune times `reps` evaluations of the context's
+ * chains per candidate (coordinate descent over the tensor-core grid size, the operand
+ * stage count, the chains per FFMA block) and keeps the fastest; the choice is stored in a
+ * process-wide table that later contexts of the same geometry start from.  No candidate
+ * changes any result.  reps = 0 only reports the current choice.  On return the chain
+ * buffers hold an evaluation of the current state.  `out` (caller-owned, may be NULL)
+ * receives the choice and the evaluation times before and after (ms).  ESTATE for a
+ * context without the batched engine. */
+typedef struct {
+  int grid_pct;    /* persistent tensor-core grid, per cent of the resident CTAs */
+  int db_bytes;    /* largest operand stage that is double-buffered */
+  int ffma_g;      /* most chains per block of the FFMA contraction kernel */
+  double ms_before, ms_after;
+} peps_tune;
+int peps_autotune(peps_ctx* ctx, int reps, peps_tune* out);
+
 /* Per-kernel statistics for roofline reports.  peps_profile(ctx, 1) clears them and starts
  * bracketing every launch of the context with CUDA events on its stream; peps_profile(ctx,
  * 2) does the same for the batched GEMM kernels only (kb_gemm_tc, kb_gemm: fewer events in

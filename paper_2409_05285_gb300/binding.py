@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout",
+    "peps_selftest_tc_timeout", "peps_autotune",
 ]
 
 
@@ -48,6 +48,11 @@ class Params(ctypes.Structure):
                 ("chi", ctypes.c_int), ("n_chains", ctypes.c_int), ("precision", ctypes.c_int),
                 ("init_noise", ctypes.c_double), ("seed", ctypes.c_uint64),
                 ("n_blocks", ctypes.c_int), ("block_mode", ctypes.c_int)]
+
+
+class Tune(ctypes.Structure):
+    _fields_ = [("grid_pct", ctypes.c_int), ("db_bytes", ctypes.c_int), ("ffma_g", ctypes.c_int),
+                ("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -130,6 +135,7 @@ def load(path=None):
     lib.peps_last_error.restype = ctypes.c_char_p
     lib.peps_version.restype = ctypes.c_char_p
     lib.peps_selftest_tc_timeout.argtypes = []
+    lib.peps_autotune.argtypes = [vp, ip, ctypes.POINTER(Tune)]
     lib.peps_launches.argtypes = [vp]
     lib.peps_launches.restype = ctypes.c_longlong
     lib.peps_profile.argtypes = [vp, ip]
@@ -176,6 +182,13 @@ class Context:
         if rc not in allow:
             raise PepsError(rc, self.lib.peps_last_error(self.ctx).decode())
         return rc
+
+    def autotune(self, reps=1):
+        """Tunes the batched engine's launch shapes on this context's chains (results are
+        unchanged); reps=0 reports the current choice."""
+        t = Tune()
+        self._check(self.lib.peps_autotune(self.ctx, reps, ctypes.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tune._fields_}
 
     def launches(self):
         """Kernel launches this context has made so far."""

@@ -15,6 +15,9 @@
 #include "pv_batch.cuh"
 
 #include <memory>
+#include <map>
+#include <mutex>
+#include <array>
 
 using namespace pv;
 
@@ -194,6 +197,7 @@ namespace {
 struct BatchIface {
   virtual ~BatchIface() {}
   virtual int* err_flag() = 0;
+  virtual BatchTune& tuning() = 0;
   virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
@@ -211,6 +215,7 @@ struct BatchImpl : BatchIface {
   double *es_tmp = nullptr, *ea_tmp = nullptr;
   BatchImpl() : run(be) {}
   int* err_flag() override { return be.tc_err; }
+  BatchTune& tuning() override { return be.tune; }
 
   void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
             bool cached) override {
@@ -529,6 +534,15 @@ size_t batched_chain_bytes(const peps_params* P) {
   return (size_t)per * real + (size_t)n8 + (size_t)nd * 8 + 16 + 2 * 8;
 }
 
+// Autotuned launch shapes per problem geometry (d^2, D, chi, L1, L2, precision), shared by
+// every context of the process.
+std::mutex g_tune_mu;
+std::map<std::array<int, 6>, BatchTune> g_tune;
+
+std::array<int, 6> tune_key(const peps_params* P) {
+  return {4, P->D, P->chi, P->L1, P->L2, P->precision};
+}
+
 int make_batch(peps_ctx* c, int sms) {
   return fp64(c) ? make_batch_t<double>(c, sms) : make_batch_t<float>(c, sms);
 }
@@ -681,6 +695,9 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
   if ((rc = dalloc(c, &c->d_sc, sizeof(SRScalars)))) return bail(rc);
   if (P->block_mode == PEPS_BLOCKS_BATCHED) {
     if ((rc = make_batch(c, sms))) return bail(rc);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(P));
+    if (it != g_tune.end()) c->batch->tuning() = it->second;
   }
   cudaError_t e;
   e = cudaMemcpyAsync(c->d_toff, c->toff.data(), (c->N + 1) * sizeof(long long),
@@ -1038,6 +1055,71 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
 double peps_time(const peps_ctx* c) { return c ? c->t : 0.0; }
 
 long long peps_launches(const peps_ctx* c) { return c ? c->kprof.launches : 0; }
+
+int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
+  if (!c || reps < 0) return fail(c, PEPS_EINVAL, "autotune: args");
+  if (!c->batch) return fail(c, PEPS_ESTATE, "autotune: only the batched engine has launch shapes to tune");
+  BatchTune& tu = c->batch->tuning();
+  const int n = c->P.n_chains;
+  auto timed = [&](double* ms) -> int {
+    double best = 1e300;
+    for (int r = 0; r < (reps > 0 ? reps : 1); ++r) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, c->stream);
+      int rc = launch_eval(c, c->d_S, n, c->d_log_abs, c->d_sign, c->d_es, c->d_ea, c->d_O, false);
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      if (rc != PEPS_OK) return rc;
+      best = t < best ? t : best;
+    }
+    *ms = best;
+    return PEPS_OK;
+  };
+  double before = 0, cur = 0;
+  if (reps > 0) {
+    PV_TRY(timed(&before));
+    cur = before;
+    // coordinate descent over the launch-shape parameters (results are the same for all)
+    const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, g_c[] = {1, 16, 256};
+    for (int knob = 0; knob < 3; ++knob) {
+      int* field = knob == 0 ? &tu.grid_pct : (knob == 1 ? &tu.db_bytes : &tu.ffma_g);
+      const int* cand = knob == 0 ? grid_c : (knob == 1 ? db_c : g_c);
+      int best_v = *field;
+      for (int i = 0; i < 3; ++i) {
+        if (cand[i] == best_v) continue;
+        const int keep = *field;
+        *field = cand[i];
+        double ms = 0;
+        PV_TRY(timed(&ms));
+        if (ms < cur * 0.99) {
+          cur = ms;
+          best_v = cand[i];
+        } else {
+          *field = keep;
+        }
+        *field = best_v;
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(&c->P)] = tu;
+    c->have_eval = true;   // the chain buffers hold an evaluation of the current state
+    c->ucache_valid = false;
+  }
+  if (out) {
+    out->grid_pct = tu.grid_pct;
+    out->db_bytes = tu.db_bytes;
+    out->ffma_g = tu.ffma_g;
+    out->ms_before = before;
+    out->ms_after = cur;
+  }
+  return PEPS_OK;
+}
 
 int peps_profile(peps_ctx* c, int enable) {
   if (!c || enable < 0 || enable > 2) return fail(c, PEPS_EINVAL, "profile: args");

@@ -1468,6 +1468,14 @@ __global__ void kb_O(OT* O, long long No, long long o_off, const T* env, long lo
   if (k < sz) O[(long long)s * No + o_off + k] = (OT)((double)env[(long long)s * es + k] / (double)val[(long long)s * vs]);
 }
 
+// Launch-shape parameters of the batched engine, chosen by the autotuner; none of them
+// changes any result (each chain's arithmetic is the same in every choice).
+struct BatchTune {
+  int grid_pct = 100;          // persistent tensor-core grid, per cent of the resident CTAs
+  int db_bytes = 12 * 1024;    // largest operand stage that gets two stages
+  int ffma_g = 256;            // most chains per block of the FFMA GEMM
+};
+
 // Whether every chain's slice of a float operand starts on a 16-byte boundary.
 inline bool op_al16(const Operand<float>& o) {
   if ((uintptr_t)o.base % 16) return false;
@@ -1490,6 +1498,7 @@ struct CudaBE {
   bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
   bool tc_split = false; // ... with every operand split into two TF32 parts (3xTF32)
   int tc_min_rows = 64;  // smallest larger free side sent to the tensor cores
+  BatchTune tune;        // launch shapes (autotuned; results do not depend on them)
   int* tc_err = nullptr; // raised by a tensor-core kernel whose completion wait ran out
   void (*tc_form_override)(TcSpec&) = nullptr;   // test hook: restrict the operand forms
   KProf* prof = nullptr; // launch counter and optional per-kernel timing
@@ -1554,7 +1563,7 @@ struct CudaBE {
           // two operand stages and accumulators (consecutive chains pipelined) only for small
           // single-chunk stages: larger ones cost more in resident CTAs than they gain
           const size_t stage = (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1);
-          t.nst = (t.K <= t.Kc && stage <= 12 * 1024) ? 2 : 1;
+          t.nst = (t.K <= t.Kc && stage <= (size_t)tune.db_bytes) ? 2 : 1;
           if (tc_smem_bytes(t) > smem_cap) t.nst = 1;
         }
         if (tc_smem_bytes(t) <= smem_cap) {
@@ -1569,7 +1578,7 @@ struct CudaBE {
           per_sm = per_sm < by_regs ? per_sm : by_regs;
           per_sm = per_sm < 16 ? per_sm : 16;
           per_sm = per_sm < 1 ? 1 : per_sm;
-          long long gy = (long long)sms * per_sm / (tilesM * tilesN);
+          long long gy = (long long)sms * per_sm * tune.grid_pct / (100LL * tilesM * tilesN);
           gy = gy < 1 ? 1 : (gy > n ? n : gy);
           gy = gy > 65535 ? 65535 : gy;
           dim3 gr(tilesM * tilesN, (unsigned)gy);
@@ -1593,6 +1602,7 @@ struct CudaBE {
       int Mp = ((gs.M + 3) / 4) * 4;
       if (Mp < TM) TM = Mp;
       int G = 256 / ((TM / 4) * (TN / 4));   // samples per block when one tile is small
+      if (G > tune.ffma_g) G = tune.ffma_g;
       if (G < 1) G = 1;
       int budget = (int)(6144 * 4 / sizeof(T));   // 24 KB of operand tiles
       int KC = budget / (G * (TM + TN));
