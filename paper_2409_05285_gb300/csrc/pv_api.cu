@@ -198,6 +198,7 @@ struct BatchIface {
   virtual ~BatchIface() {}
   virtual int* err_flag() = 0;
   virtual BatchTune& tuning() = 0;
+  virtual bool uses_tensor_cores() const = 0;
   virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
@@ -216,6 +217,7 @@ struct BatchImpl : BatchIface {
   BatchImpl() : run(be) {}
   int* err_flag() override { return be.tc_err; }
   BatchTune& tuning() override { return be.tune; }
+  bool uses_tensor_cores() const override { return be.tc; }
 
   void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
             bool cached) override {
@@ -1060,7 +1062,9 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
   if (!c || reps < 0) return fail(c, PEPS_EINVAL, "autotune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "autotune: only the batched engine has launch shapes to tune");
   BatchTune& tu = c->batch->tuning();
-  const int n = c->P.n_chains;
+  // time on at most 2048 chains (the tuned shapes scale with the chain count only through
+  // the grid, which the candidates express as fractions of the resident CTAs)
+  const int n = c->P.n_chains < 2048 ? c->P.n_chains : 2048;
   auto timed = [&](double* ms) -> int {
     double best = 1e300;
     for (int r = 0; r < (reps > 0 ? reps : 1); ++r) {
@@ -1087,7 +1091,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     cur = before;
     // coordinate descent over the launch-shape parameters (results are the same for all)
     const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, g_c[] = {1, 16, 256};
-    for (int knob = 0; knob < 3; ++knob) {
+    for (int knob = c->batch->uses_tensor_cores() ? 0 : 2; knob < 3; ++knob) {
       int* field = knob == 0 ? &tu.grid_pct : (knob == 1 ? &tu.db_bytes : &tu.ffma_g);
       const int* cand = knob == 0 ? grid_c : (knob == 1 ? db_c : g_c);
       int best_v = *field;
@@ -1108,7 +1112,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(&c->P)] = tu;
-    c->have_eval = true;   // the chain buffers hold an evaluation of the current state
+    c->have_eval = n == c->P.n_chains;   // all chains evaluated for the current state
     c->ucache_valid = false;
   }
   if (out) {
