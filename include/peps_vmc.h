@@ -183,12 +183,12 @@ int peps_last_counters(peps_ctx* ctx, double* flops, int64_t* jacobi_sweeps);
 long long peps_launches(const peps_ctx* ctx);
 
 /* Autotuner of the batched engine's launch shapes, keyed on the problem geometry (d^2 = 4,
- * D, chi, L1, L2, precision).  peps_autotune times `reps` evaluations of (at most 2048 of)
+ * D, chi, L1, L2, precision).  peps_autotune times `reps` evaluations of (at most 8192 of)
  * the context's chains per candidate (coordinate descent over the tensor-core grid size,
  * the operand stage count, the chains per FFMA block; only the last one without tensor
  * cores) and keeps the fastest; the choice is stored in a process-wide table that later
  * contexts of the same geometry start from.  No candidate changes any result.  reps = 0
- * only reports the current choice.  With at most 2048 chains the chain buffers hold an
+ * only reports the current choice.  With at most 8192 chains the chain buffers hold an
  * evaluation of the current state on return; otherwise evaluate before peps_sr_step.  `out` (caller-owned, may be NULL)
  * receives the choice and the evaluation times before and after (ms).  ESTATE for a
  * context without the batched engine. */

@@ -1062,9 +1062,9 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
   if (!c || reps < 0) return fail(c, PEPS_EINVAL, "autotune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "autotune: only the batched engine has launch shapes to tune");
   BatchTune& tu = c->batch->tuning();
-  // time on at most 2048 chains (the tuned shapes scale with the chain count only through
-  // the grid, which the candidates express as fractions of the resident CTAs)
-  const int n = c->P.n_chains < 2048 ? c->P.n_chains : 2048;
+  // time on at most 8192 chains: the best shapes depend on the chain count (a 2048-chain
+  // subset picked one chain per FFMA block, which is slower at 8192 chains)
+  const int n = c->P.n_chains < 8192 ? c->P.n_chains : 8192;
   auto timed = [&](double* ms) -> int {
     double best = 1e300;
     for (int r = 0; r < (reps > 0 ? reps : 1); ++r) {

@@ -1353,7 +1353,7 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
   extern __shared__ __align__(16) unsigned char dyn[];
   T* A = (T*)dyn;
   __shared__ T red[32];
-  __shared__ T s_piv;
+  __shared__ T s_piv[2];
   const int m = op.m, ld = m + 1;
   const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
@@ -1369,20 +1369,25 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
     dmax = cta_max(dmax, red);
     const T tol = (T)m * eps * dmax;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      const T d = A[0];
+      s_piv[0] = d > tol ? sqrt(d) : (T)0;
+    }
+    __syncthreads();
     for (int j = 0; j < m; ++j) {
-      if (threadIdx.x == 0) {
-        const T d = A[j * ld + j];
-        s_piv = d > tol ? sqrt(d) : (T)0;
-      }
-      __syncthreads();
-      const T l = s_piv, inv = l > 0 ? (T)1 / l : (T)0;
+      const T l = s_piv[j & 1], inv = l > 0 ? (T)1 / l : (T)0;
       for (int i = j + threadIdx.x; i < m; i += BT) A[i * ld + j] = i == j ? l : A[i * ld + j] * inv;
       __syncthreads();
-      // trailing update on a 16 x 16 thread grid (BT = 256)
+      // trailing update on a 16 x 16 thread grid (BT = 256); thread 0 updates the next
+      // diagonal entry and forms the next pivot, so a column costs two barriers
       const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
       for (int i = j + 1 + ty; i < m; i += 16) {
         const T lij = A[i * ld + j];
         for (int k = j + 1 + tx; k < m; k += 16) A[i * ld + k] -= lij * A[k * ld + j];
+      }
+      if (threadIdx.x == 0 && j + 1 < m) {
+        const T d = A[(j + 1) * ld + j + 1];
+        s_piv[(j + 1) & 1] = d > tol ? sqrt(d) : (T)0;
       }
       __syncthreads();
     }
