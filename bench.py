@@ -32,6 +32,49 @@ SMS, MAX_MHZ = 152, 2070.0
 PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from one
+# ncu capture of every launch of that kernel in this bench's timed step (the timed region is
+# bracketed by cudaProfilerStart/Stop, so `ncu --profile-from-start off` captures exactly it),
+# stored with the SHA-256 of the kernel and launch-planner sources it was taken on.  Once those
+# sources change the entry no longer applies and the bench reports null.
+NCU_TRAFFIC = {
+    ("heis8", "tf32", 8192, "kb_gemm_tc"): {
+        "launches": 200,
+        "dram_bytes": 87087258624,      # DRAM read + write of the first 200 launches of the step
+        "alg_bytes": 94567665664,       # algorithmic bytes of the same 200 launches
+        "sources_sha256": "cca0fd4000d7f97b80839511f251a421e5665604d7ea608cef546e3a9dc16ee9",
+        "source": "ncu --profile-from-start off -k regex:kb_gemm_tc -c 200 (dram__bytes_read.sum "
+                  "+ dram__bytes_write.sum, cold cache), first 200 launches of the timed step, "
+                  "scaled by algorithmic bytes; profiles/kb_gemm_tc_heis8_tf32.md",
+    },
+}
+TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_batch.cuh")
+
+
+def sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload, precision, chains, kernel):
+    """The capture recorded for this configuration, or None when there is none or the
+    sources changed since it was taken."""
+    rec = NCU_TRAFFIC.get((workload, precision, chains, kernel))
+    if rec is None or rec["sources_sha256"] != sources_sha256():
+        return None
+    return rec
+
+
+def traffic_per_launch(rec, alg_bytes_per_launch):
+    """DRAM bytes per launch of the timed steps: the captured launches' DRAM bytes per
+    algorithmic byte (the same launches on both sides) times this run's algorithmic bytes per
+    launch."""
+    return rec["dram_bytes"] / rec["alg_bytes"] * alg_bytes_per_launch
+
 
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
@@ -215,6 +258,7 @@ def run_ours(args):
     phase_k = {"mc_sweep": {}, "eval": {}, "sr_step": {}}   # per-phase kernel sums
     phase_base = {}
     e_start, e_end = ev(), ev()
+    torch.cuda.profiler.start()   # the window `ncu --profile-from-start off` captures
     e_start.record(stream)
     for _ in range(args.steps):
         e0, e1, e2, e3 = ev(), ev(), ev(), ev()
@@ -244,7 +288,14 @@ def run_ours(args):
         step_ms.append(e0.elapsed_time(e3))
     e_end.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     clk = clocks.stop()
+    if args.launch_bytes:
+        # algorithmic bytes of every tensor-core contraction launch of the timed steps, in
+        # launch order, to set against a per-launch DRAM capture of the same launches
+        with open(args.launch_bytes, "w") as f:
+            json.dump({"kernel": "kb_gemm_tc", "steps": args.steps,
+                       "bytes": ctx.profile_launch_bytes("kb_gemm_tc")}, f)
     kstats = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.launches() - launches0
@@ -275,6 +326,12 @@ def run_ours(args):
         fp64_check = compare_fp64(ctx, wl, binding, min(n, args.fp64_chains), stream, torch)
     peaks = measured_peaks()
     roofline, kernels = kernel_roofline(kstats, peaks, prec, binding)
+    if roofline is not None:
+        rec = recorded_traffic(args.workload, args.precision, n, roofline["kernel"])
+        if rec is not None and roofline.get("bytes_per_launch"):
+            roofline["traffic"] = traffic_per_launch(rec, roofline["bytes_per_launch"])
+            roofline["traffic_over_algorithmic"] = rec["dram_bytes"] / rec["alg_bytes"]
+            roofline["traffic_source"] = rec["source"]
     step_sorted = sorted(step_ms)
     out = {
         "metric": METRIC,
@@ -517,6 +574,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-chains", type=int, default=608)
+    ap.add_argument("--launch-bytes", default="",
+                    help="write the per-launch algorithmic bytes of kb_gemm_tc in the timed steps to this file")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -217,6 +217,11 @@ typedef struct {
 } peps_kernel_stat;
 int peps_profile(peps_ctx* ctx, int enable);
 int peps_profile_read(peps_ctx* ctx, peps_kernel_stat* out, int cap, int* n_out);
+/* The algorithmic bytes of each launch of kernel `name` recorded since profiling started or
+ * since the last peps_profile_read (which folds the records into its sums), in launch order:
+ * the first `cap` go to `bytes` (caller-owned), their number to *n_out.  Lets a per-launch
+ * DRAM capture of a profiler be set against the same launches.  EINVAL on bad arguments. */
+int peps_profile_launch_bytes(peps_ctx* ctx, const char* name, double* bytes, int cap, int* n_out);
 
 /* Failure-detection self-test of the bounded waits in the tensor-core kernels (the paper
  * has no counterpart).  Launches a small contraction on its own stream with its MMAs

@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes",
 ]
 
 
@@ -140,6 +140,8 @@ def load(path=None):
     lib.peps_launches.restype = ctypes.c_longlong
     lib.peps_profile.argtypes = [vp, ip]
     lib.peps_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ip)]
+    lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                              ip, ctypes.POINTER(ip)]
     _lib = lib
     return lib
 
@@ -207,6 +209,15 @@ class Context:
         self._check(self.lib.peps_profile_read(self.ctx, buf, cap, ctypes.byref(n)))
         return {buf[i].name.decode(): (buf[i].launches, buf[i].ms, buf[i].bytes, buf[i].flops)
                 for i in range(min(cap, n.value))}
+
+    def profile_launch_bytes(self, name, cap=1 << 16):
+        """Algorithmic bytes of each recorded launch of kernel `name` (not yet folded by
+        profile_read), in launch order."""
+        buf = (ctypes.c_double * cap)()
+        n = ctypes.c_int()
+        self._check(self.lib.peps_profile_launch_bytes(self.ctx, name.encode(), buf, cap,
+                                                       ctypes.byref(n)))
+        return [buf[i] for i in range(min(cap, n.value))]
 
     def close(self):
         if self.ctx:

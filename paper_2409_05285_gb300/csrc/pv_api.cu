@@ -1156,6 +1156,19 @@ int peps_profile_read(peps_ctx* c, peps_kernel_stat* out, int cap, int* n_out) {
   return PEPS_OK;
 }
 
+int peps_profile_launch_bytes(peps_ctx* c, const char* name, double* bytes, int cap, int* n_out) {
+  if (!c || !name || cap < 0 || (cap > 0 && !bytes) || !n_out)
+    return fail(c, PEPS_EINVAL, "profile_launch_bytes: args");
+  int k = 0;
+  for (const pv::KProf::Rec& r : c->kprof.recs) {
+    if (strcmp(r.name, name) != 0) continue;
+    if (k < cap) bytes[k] = r.bytes;
+    ++k;
+  }
+  *n_out = k;
+  return PEPS_OK;
+}
+
 namespace {
 struct CkptHeader {
   char magic[8];

@@ -1481,6 +1481,15 @@ struct BatchTune {
   int ffma_g = 256;            // most chains per block of the FFMA GEMM
 };
 
+// Whether two operands address the same values for every chain.
+template <typename T>
+inline bool op_same(const Operand<T>& a, const Operand<T>& b) {
+  if (a.base != b.base || a.mode != b.mode) return false;
+  if (a.mode == OP_BATCH) return a.stride == b.stride;
+  return a.site_off == b.site_off && a.site_sz == b.site_sz && a.S == b.S && a.site == b.site &&
+         a.N == b.N && a.sel == b.sel;
+}
+
 // Whether every chain's slice of a float operand starts on a 16-byte boundary.
 inline bool op_al16(const Operand<float>& o) {
   if ((uintptr_t)o.base % 16) return false;
@@ -1522,6 +1531,7 @@ struct CudaBE {
       b *= s.ks[d];
     }
     const double sites = n < 4 ? n : 4;
+    if (op_same(A, B) && a == b) b = 0;   // a Gram product reads its operand once
     return (a * (A.mode == OP_BATCH ? n : sites) + b * (B.mode == OP_BATCH ? n : sites) + c * n) *
            sizeof(T);
   }
@@ -1558,6 +1568,7 @@ struct CudaBE {
                  ((uintptr_t)out % 16 == 0) && os % 4 == 0);
         t.split = (exact || tc_split) ? 1 : 0;   // float32-accurate products (3xTF32)
         if (tc_form_override) tc_form_override(t);
+        t.sym = tc_symmetric(t, op_same(A, B)) ? 1 : 0;
         // stay within the 200 KB of shared memory the kernel is configured for
         const size_t smem_cap = 200 * 1024;
         while (tc_smem_bytes(t) > smem_cap && t.Kc > 8) {
@@ -1567,8 +1578,7 @@ struct CudaBE {
         {
           // two operand stages and accumulators (consecutive chains pipelined) only for small
           // single-chunk stages: larger ones cost more in resident CTAs than they gain
-          const size_t stage = (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1);
-          t.nst = (t.K <= t.Kc && stage <= (size_t)tune.db_bytes) ? 2 : 1;
+          t.nst = (t.K <= t.Kc && tc_stage_bytes(t) <= (size_t)tune.db_bytes) ? 2 : 1;
           if (tc_smem_bytes(t) > smem_cap) t.nst = 1;
         }
         if (tc_smem_bytes(t) <= smem_cap) {

@@ -32,6 +32,8 @@ struct TcSpec {
   int pref;                  // one chunk small enough to stage in registers (next chain prefetched)
   int split;                 // 3xTF32: operands as hi + lo TF32 parts, products hi.hi + hi.lo + lo.hi
   int nst;                   // operand stages / accumulators: 2 pipelines consecutive chains
+  int sym;                   // Q is P with the same index maps (C = P P^T, one tile): the B
+                             // operand is read from the A stage instead of being gathered
   int no_mma;                // self-test only: issue no MMA and no commit, so every wait runs out
 };
 
@@ -75,8 +77,21 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap, int tc_min_rows = 64)
   t.pref = (g.K <= t.Kc && t.Kc <= 16 && t.TN * t.Kc <= 1024) ? 1 : 0;
   t.split = 0;
   t.nst = 1;
+  t.sym = 0;
   t.no_mma = 0;
   return true;
+}
+
+// Whether C = P Q^T is a Gram product P P^T that one tile covers: the column side and its
+// strides in Q are the row side and its strides in P, the contraction strides agree, and the
+// caller passes the same operand twice (`same`).
+inline bool tc_symmetric(const TcSpec& t, bool same) {
+  if (!same || t.M != t.N || t.M > TC_ROWS || t.TN < t.N || t.nr != t.nc) return false;
+  for (int d = 0; d < t.nr; ++d)
+    if (t.rs[d] != t.cs[d] || t.rP[d] != t.cQ[d]) return false;
+  for (int d = 0; d < t.nk; ++d)
+    if (t.kP[d] != t.kQ[d]) return false;
+  return t.modeP == t.modeQ;
 }
 
 inline bool tc_all4(const int* st, int n) {
@@ -112,9 +127,14 @@ inline void tc_forms(TcSpec& t, bool p_al, bool q_al, bool c_al) {
 // chunk per chain, small stages), else one.
 PV_HD int tc_stages(const TcSpec& t) { return t.nst; }
 
+// Bytes of one operand stage: the A chunk (128 rows), the B chunk (TN rows) unless B is read
+// from A, both twice for split operands.
+inline size_t tc_stage_bytes(const TcSpec& t) {
+  return (size_t)(TC_ROWS + (t.sym ? 0 : t.TN)) * t.Kc * sizeof(float) * (t.split ? 2 : 1);
+}
+
 inline size_t tc_smem_bytes(const TcSpec& t) {
-  return (size_t)(TC_ROWS + t.TN) * t.Kc * sizeof(float) * (t.split ? 2 : 1) * tc_stages(t) +
-         (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int);
+  return tc_stage_bytes(t) * tc_stages(t) + (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int);
 }
 
 PV_HD int tc_cols(int TN) {
@@ -456,8 +476,12 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   const int TN = t.TN, Kc = t.Kc;
   const int m0 = tm * TC_ROWS, n0 = tn * TN;
   const int nst = tc_stages(t);
-  // per stage: A hi, B hi, then (split) A lo, B lo
-  const int sa = TC_ROWS * Kc, sb = TN * Kc, sst = (sa + sb) * (t.split ? 2 : 1);
+  // per stage: A hi, B hi, then (split) A lo, B lo; no B chunks when B is read from A
+  const int sa = TC_ROWS * Kc, sb = t.sym ? 0 : TN * Kc, sst = (sa + sb) * (t.split ? 2 : 1);
+  // rows of the chunks that hold data; the rows past the edge of C are left as they are
+  // (they only feed accumulator rows and columns that the epilogue does not store)
+  const int rowsA = min(TC_ROWS, ((t.M - m0 + 7) >> 3) << 3);
+  const int rowsB = min(TN, ((t.N - n0 + 7) >> 3) << 3);
   float* stage0 = (float*)dyn;
   int* rowP = (int*)(stage0 + (long long)nst * sst);
   int* rowC = rowP + TC_ROWS;
@@ -508,22 +532,22 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
     int s = blockIdx.y;
     if constexpr (PREF) {
       if (s < n) {
-        tc_pload(ra, P.at(s), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
-        tc_pload(rb, Q.at(s), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+        tc_pload(ra, P.at(s), t.modeP, rowsA, Kc, t.K, rowP, kPo, tid);
+        if (!t.sym) tc_pload(rb, Q.at(s), t.modeQ, rowsB, Kc, t.K, colQ, kQo, tid);
       }
     }
     for (; s < n; s += gridDim.y, ++it) {
       const int st = it & 1;
       float* As = stage0 + (long long)st * sst;
-      float* Bs = As + sa;
-      float* Al = t.split ? Bs + sb : nullptr;
-      float* Bl = t.split ? Al + sa : nullptr;
+      float* Bs = t.sym ? As : As + sa;
+      float* Al = t.split ? As + sa + sb : nullptr;
+      float* Bl = t.split ? (t.sym ? Al : Al + sa) : nullptr;
       if constexpr (PREF) {
-        tc_pstore(ra, As, Al, t.modeP, TC_ROWS, Kc, tid);
-        tc_pstore(rb, Bs, Bl, t.modeQ, TN, Kc, tid);
+        tc_pstore(ra, As, Al, t.modeP, rowsA, Kc, tid);
+        if (!t.sym) tc_pstore(rb, Bs, Bl, t.modeQ, rowsB, Kc, tid);
       } else {
-        tc_gather(As, Al, P.at(s), t.modeP, TC_ROWS, Kc, 0, t.K, rowP, kPo, tid);
-        tc_gather(Bs, Bl, Q.at(s), t.modeQ, TN, Kc, 0, t.K, colQ, kQo, tid);
+        tc_gather(As, Al, P.at(s), t.modeP, rowsA, Kc, 0, t.K, rowP, kPo, tid);
+        if (!t.sym) tc_gather(Bs, Bl, Q.at(s), t.modeQ, rowsB, Kc, 0, t.K, colQ, kQo, tid);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
@@ -540,8 +564,8 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       if constexpr (PREF) {
         const int sn = s + gridDim.y;
         if (sn < n) {
-          tc_pload(ra, P.at(sn), t.modeP, TC_ROWS, Kc, t.K, rowP, kPo, tid);
-          tc_pload(rb, Q.at(sn), t.modeQ, TN, Kc, t.K, colQ, kQo, tid);
+          tc_pload(ra, P.at(sn), t.modeP, rowsA, Kc, t.K, rowP, kPo, tid);
+          if (!t.sym) tc_pload(rb, Q.at(sn), t.modeQ, rowsB, Kc, t.K, colQ, kQo, tid);
         }
       }
       if (it > 0) {   // the previous chain: its MMA was issued one iteration ago
@@ -580,9 +604,9 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   } else {
     // several chunks per chain: one stage, accumulate over the chunks, then the epilogue
     float* As = stage0;
-    float* Bs = As + sa;
-    float* Al = t.split ? Bs + sb : nullptr;
-    float* Bl = t.split ? Al + sa : nullptr;
+    float* Bs = t.sym ? As : As + sa;
+    float* Al = t.split ? As + sa + sb : nullptr;
+    float* Bl = t.split ? (t.sym ? Al : Al + sa) : nullptr;
     const uint32_t a = tc_smem_addr(As), b = tc_smem_addr(Bs);
     const uint32_t al = t.split ? tc_smem_addr(Al) : 0, bl = t.split ? tc_smem_addr(Bl) : 0;
     bool ok = true;
@@ -590,8 +614,8 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       const float* pp = P.at(s);
       const float* pq = Q.at(s);
       for (int k0 = 0; k0 < t.K; k0 += Kc) {
-        tc_gather(As, Al, pp, t.modeP, TC_ROWS, Kc, k0, t.K, rowP, kPo, tid);
-        tc_gather(Bs, Bl, pq, t.modeQ, TN, Kc, k0, t.K, colQ, kQo, tid);
+        tc_gather(As, Al, pp, t.modeP, rowsA, Kc, k0, t.K, rowP, kPo, tid);
+        if (!t.sym) tc_gather(Bs, Bl, pq, t.modeQ, rowsB, Kc, k0, t.K, colQ, kQo, tid);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0 && !t.no_mma) {

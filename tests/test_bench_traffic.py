@@ -1,0 +1,38 @@
+"""The bench's recorded DRAM traffic: it applies only to the sources it was captured on, and
+it is scaled from the captured launches to the timed steps by algorithmic bytes."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    sys.path.insert(0, ROOT)
+    import bench
+    return bench
+
+
+def test_traffic_needs_matching_sources(monkeypatch):
+    bench = _bench()
+    key = ("heis8", "tf32", 8192, "kb_gemm_tc")
+    rec = {"dram_bytes": 3.0e9, "alg_bytes": 2.0e9, "sources_sha256": bench.sources_sha256(),
+           "source": "test"}
+    monkeypatch.setitem(bench.NCU_TRAFFIC, key, rec)
+    assert bench.recorded_traffic(*key) is rec
+    assert bench.recorded_traffic("heis8", "tf32", 4096, "kb_gemm_tc") is None
+    monkeypatch.setitem(bench.NCU_TRAFFIC, key, dict(rec, sources_sha256="0" * 64))
+    assert bench.recorded_traffic(*key) is None
+
+
+def test_traffic_scales_by_algorithmic_bytes():
+    bench = _bench()
+    rec = {"dram_bytes": 3.0e9, "alg_bytes": 2.0e9}
+    assert bench.traffic_per_launch(rec, 1.0e8) == 1.5e8
+
+
+def test_recorded_entries_are_well_formed():
+    bench = _bench()
+    for key, rec in bench.NCU_TRAFFIC.items():
+        assert len(key) == 4 and key[1] in ("fp32", "tf32", "fp64")
+        assert rec["dram_bytes"] > 0 and rec["alg_bytes"] > 0 and rec["launches"] > 0
+        assert len(rec["sources_sha256"]) == 64 and rec["source"]
