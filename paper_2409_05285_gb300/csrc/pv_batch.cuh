@@ -712,6 +712,24 @@ struct BatchRunner {
       ein(out, os, "aldbr", envt(envrow, es, c), "aub", site(r, c, S), "lrud", dm, n);
   }
 
+  // out[x][p][(b,r)] = sum_(a,l) carry[x][(a,l)] (env_c x site)[(a,l)][p][(b,r)] for column c
+  // of row r, contracted as (carry . env_c) . site: the absorbed tensor (bond x D x D x bond x D)
+  // is never formed, only the bprev x D x D x bond intermediate (in the Cs work buffer)
+  void carry_absorb(const T* envrow, long long es, const std::vector<int>& bond, bool down, int r,
+                    int c, const uint8_t* S, int bprev, T* out, long long os, int n) {
+    Dims dm;
+    dm.set('x', bprev).set('a', bond[c]).set('b', bond[c + 1]).set('l', dl(c)).set('r', dr(c));
+    dm.set('u', du(r)).set('d', dd(r));
+    const Operand<T> cy = bat(b.carry, (long long)chi * chi * D);
+    if (down) {
+      ein(b.Cs, b.CB, "xldb", cy, "xal", envt(envrow, es, c), "adb", dm, n);
+      ein(out, os, "xubr", bat(b.Cs, b.CB), "xldb", site(r, c, S), "lrud", dm, n);
+    } else {
+      ein(b.Cs, b.CB, "xlub", cy, "xal", envt(envrow, es, c), "aub", dm, n);
+      ein(out, os, "xdbr", bat(b.Cs, b.CB), "xlub", site(r, c, S), "lrud", dm, n);
+    }
+  }
+
   // Compress (env x row r) into outrow (same stride es); log-scales ls[s*lstride] += ...
   void compress(const T* envrow, long long es, const std::vector<int>& bond, bool down, int r,
                 const uint8_t* S, T* outrow, long long os, double* ls, int lstride, int n) {
@@ -755,12 +773,8 @@ struct BatchRunner {
     be.set(b.carry, (long long)chi * (chi * D), 0, (T)1, n);
     int bprev = 1;
     for (int c = 0; c < L2 - 1; ++c) {
-      int a = bc[c], bb = bc[c + 1], k = kf[c + 1];
-      absorb_site(envrow, es, bond, down, r, c, S, b.Cs, b.CB, n);
-      Dims dm;
-      dm.set('x', bprev).set('a', a).set('p', p).set('b', bb);
-      ein(b.Am, b.P2, "xpb", bat(b.carry, (long long)chi * chi * D), "xa", bat(b.Cs, b.CB), "apb",
-          dm, n);
+      int bb = bc[c + 1], k = kf[c + 1];
+      carry_absorb(envrow, es, bond, down, r, c, S, bprev, b.Am, b.P2, n);
       int m = bprev * p;
       bool tall = k <= m;
       Dims dq;
@@ -782,11 +796,8 @@ struct BatchRunner {
     }
     {
       int c = L2 - 1;
-      absorb_site(envrow, es, bond, down, r, c, S, b.Cs, b.CB, n);
-      Dims dm;
-      dm.set('x', bprev).set('a', bc[c]).set('p', p).set('b', bc[c + 1]);
       T* o = outrow + (long long)c * b.ENV;
-      ein(o, os, "xpb", bat(b.carry, (long long)chi * chi * D), "xa", bat(b.Cs, b.CB), "apb", dm, n);
+      carry_absorb(envrow, es, bond, down, r, c, S, bprev, o, os, n);
       be.norm(OpNorm<T>{o, os, (long long)bprev * p * bc[c + 1], ls, lstride}, n);
     }
   }
