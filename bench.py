@@ -40,12 +40,13 @@ PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 NCU_TRAFFIC = {
     ("heis8", "tf32", 8192, "kb_gemm_tc"): {
         "launches": 200,
-        "dram_bytes": 67225239808,      # DRAM read + write of the first 200 launches of the step
+        "dram_bytes": 66987750144,      # DRAM read + write of the first 200 launches of the step
         "alg_bytes": 75240312832,       # algorithmic bytes of the same 200 launches
-        "sources_sha256": "61f908719bb69caf60a1d7db90995787ca144b9ecd9b73918776ac6faff776de",
+        "sources_sha256": "7044afc585d3148fbf14162c480277f2c374c81eaccae1b2b2038d9531142c53",
         "source": "ncu --profile-from-start off -k regex:kb_gemm_tc -c 200 (dram__bytes_read.sum "
-                  "+ dram__bytes_write.sum, cold cache), first 200 launches of the timed step, "
-                  "scaled by algorithmic bytes; profiles/kb_gemm_tc_heis8_tf32.md",
+                  "+ dram__bytes_write.sum, cold cache), first 200 launches of the timed step with "
+                  "the autotuned shapes 100,12288,16,32, scaled by algorithmic bytes; "
+                  "profiles/kb_gemm_tc_heis8_tf32.md",
     },
 }
 TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_batch.cuh")
@@ -242,8 +243,15 @@ def run_ours(args):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for _ in range(args.warmup):
         ctx.step(n_sweeps=1, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
-    # launch shapes tuned on this context's chains (results do not depend on them)
-    tune = ctx.autotune(reps=1) if args.block_mode in ("auto", "batched") and not args.no_autotune else None
+    # launch shapes tuned on this context's chains, or pinned (results do not depend on them)
+    if args.tune:
+        g, db, fg, kc = (int(v) for v in args.tune.split(","))
+        ctx.set_tune(g, db, fg, kc)
+        tune = ctx.autotune(reps=0)
+    elif args.block_mode in ("auto", "batched") and not args.no_autotune:
+        tune = ctx.autotune(reps=1)
+    else:
+        tune = None
     clocks = Clocks(local)
     step_ms, mc_ms, eval_ms, sr_ms, eval_flops, mc_flops, cg_its, stats = [], [], [], [], [], [], [], []
     jac = []
@@ -574,6 +582,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-chains", type=int, default=608)
+    ap.add_argument("--tune", default="",
+                    help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max")
     ap.add_argument("--launch-bytes", default="",
                     help="write the per-launch algorithmic bytes of kb_gemm_tc in the timed steps to this file")
     args = ap.parse_args()

@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune",
 ]
 
 
@@ -52,7 +52,7 @@ class Params(ctypes.Structure):
 
 class Tune(ctypes.Structure):
     _fields_ = [("grid_pct", ctypes.c_int), ("db_bytes", ctypes.c_int), ("ffma_g", ctypes.c_int),
-                ("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double)]
+                ("kc_max", ctypes.c_int), ("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -140,6 +140,7 @@ def load(path=None):
     lib.peps_launches.restype = ctypes.c_longlong
     lib.peps_profile.argtypes = [vp, ip]
     lib.peps_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ip)]
+    lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
     lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ip, ctypes.POINTER(ip)]
     _lib = lib
@@ -191,6 +192,11 @@ class Context:
         t = Tune()
         self._check(self.lib.peps_autotune(self.ctx, reps, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in Tune._fields_}
+
+    def set_tune(self, grid_pct, db_bytes, ffma_g, kc_max):
+        """Pins the batched engine's launch shapes (results are unchanged)."""
+        t = Tune(grid_pct=grid_pct, db_bytes=db_bytes, ffma_g=ffma_g, kc_max=kc_max)
+        self._check(self.lib.peps_set_tune(self.ctx, ctypes.byref(t)))
 
     def launches(self):
         """Kernel launches this context has made so far."""

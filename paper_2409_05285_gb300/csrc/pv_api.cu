@@ -1090,10 +1090,13 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     PV_TRY(timed(&before));
     cur = before;
     // coordinate descent over the launch-shape parameters (results are the same for all)
-    const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, g_c[] = {1, 16, 256};
-    for (int knob = c->batch->uses_tensor_cores() ? 0 : 2; knob < 3; ++knob) {
-      int* field = knob == 0 ? &tu.grid_pct : (knob == 1 ? &tu.db_bytes : &tu.ffma_g);
-      const int* cand = knob == 0 ? grid_c : (knob == 1 ? db_c : g_c);
+    const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, kc_c[] = {16, 32, 64},
+              g_c[] = {1, 16, 256};
+    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.ffma_g};
+    const int* cands[] = {grid_c, db_c, kc_c, g_c};
+    for (int knob = c->batch->uses_tensor_cores() ? 0 : 3; knob < 4; ++knob) {
+      int* field = fields[knob];
+      const int* cand = cands[knob];
       int best_v = *field;
       for (int i = 0; i < 3; ++i) {
         if (cand[i] == best_v) continue;
@@ -1119,9 +1122,24 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     out->grid_pct = tu.grid_pct;
     out->db_bytes = tu.db_bytes;
     out->ffma_g = tu.ffma_g;
+    out->kc_max = tu.kc_max;
     out->ms_before = before;
     out->ms_after = cur;
   }
+  return PEPS_OK;
+}
+
+int peps_set_tune(peps_ctx* c, const peps_tune* t) {
+  if (!c || !t || t->grid_pct < 1 || t->grid_pct > 400 || t->db_bytes < 0 ||
+      t->db_bytes > 200 * 1024 || t->ffma_g < 1 || t->ffma_g > 256 || t->kc_max < 8 ||
+      t->kc_max > 64 || t->kc_max % 8)
+    return fail(c, PEPS_EINVAL, "set_tune: args");
+  if (!c->batch) return fail(c, PEPS_ESTATE, "set_tune: only the batched engine has launch shapes");
+  BatchTune& tu = c->batch->tuning();
+  tu.grid_pct = t->grid_pct;
+  tu.db_bytes = t->db_bytes;
+  tu.ffma_g = t->ffma_g;
+  tu.kc_max = t->kc_max;
   return PEPS_OK;
 }
 

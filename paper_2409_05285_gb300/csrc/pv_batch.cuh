@@ -1490,6 +1490,7 @@ struct BatchTune {
   int grid_pct = 100;          // persistent tensor-core grid, per cent of the resident CTAs
   int db_bytes = 12 * 1024;    // largest operand stage that gets two stages
   int ffma_g = 256;            // most chains per block of the FFMA GEMM
+  int kc_max = 64;             // largest contraction chunk of the tensor-core GEMM
 };
 
 // Whether two operands address the same values for every chain.
@@ -1580,6 +1581,10 @@ struct CudaBE {
         t.split = (exact || tc_split) ? 1 : 0;   // float32-accurate products (3xTF32)
         if (tc_form_override) tc_form_override(t);
         t.sym = tc_symmetric(t, op_same(A, B)) ? 1 : 0;
+        if (t.Kc > tune.kc_max) {   // smaller chunks: smaller stages, more resident CTAs
+          t.Kc = tune.kc_max;
+          if (t.K > t.Kc) t.pref = 0;
+        }
         // stay within the 200 KB of shared memory the kernel is configured for
         const size_t smem_cap = 200 * 1024;
         while (tc_smem_bytes(t) > smem_cap && t.Kc > 8) {

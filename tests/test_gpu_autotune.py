@@ -23,11 +23,32 @@ def test_autotune_keeps_results_and_is_shared_by_geometry():
     assert tune["grid_pct"] in (50, 100, 200)
     assert tune["db_bytes"] in (0, 12 * 1024, 48 * 1024)
     assert tune["ffma_g"] in (1, 16, 256)
+    assert tune["kc_max"] in (16, 32, 64)
     assert 0 < tune["ms_after"] <= tune["ms_before"]
     ctx.sr_step(0.02)   # the tuner left a valid evaluation of the chains behind
     ctx2 = binding.Context(L, L, D, chi, 64, precision=binding.PEPS_TF32, seed=5)
     t2 = ctx2.autotune(reps=0)
-    assert (t2["grid_pct"], t2["db_bytes"], t2["ffma_g"]) == \
-        (tune["grid_pct"], tune["db_bytes"], tune["ffma_g"])
+    keys = ("grid_pct", "db_bytes", "ffma_g", "kc_max")
+    assert [t2[k] for k in keys] == [tune[k] for k in keys]
     ctx.close()
     ctx2.close()
+
+
+def test_pinned_shapes_keep_results():
+    from paper_2409_05285_gb300.build import build
+    build()
+    ctx = binding.Context(6, 6, 4, 16, 256, precision=binding.PEPS_TF32, seed=6)
+    ctx.mc_sweep(1, p=1)
+    S = ctx.get_configs()
+    ctx.set_tune(100, 12 * 1024, 256, 64)
+    ref = ctx.eval_batch(S)
+    for shapes in ((50, 0, 16, 16), (200, 48 * 1024, 1, 32), (100, 12 * 1024, 256, 8)):
+        ctx.set_tune(*shapes)
+        got = ctx.autotune(reps=0)
+        assert (got["grid_pct"], got["db_bytes"], got["ffma_g"], got["kc_max"]) == shapes
+        for a, b in zip(ref, ctx.eval_batch(S)):
+            assert np.array_equal(a, b)
+    for bad in ((0, 0, 16, 64), (100, 0, 0, 64), (100, 0, 16, 12), (100, 0, 16, 72)):
+        with pytest.raises(RuntimeError):
+            ctx.set_tune(*bad)
+    ctx.close()
