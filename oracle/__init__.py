@@ -17,6 +17,8 @@ Modules:
   peps         PEPS of the vectorised density matrix (Eq. 4); exact contraction;
                boundary-MPS contraction at bond chi; amplitude, E_loc (Eq. 9), O_k (Eq. 8).
   sampler      Metropolis sampling of |rho|^p, p = 2 (normal) or 1 (reweighted, Eq. A1).
+  direct       direct (autoregressive) sampling from double-layer marginals and its
+               reweighted form p_4 with the adaptive diagonal factor b_d (Eqs. A2-A7).
   sr           weights, Eq. 6/7/10 reductions, CG solve, parameter update (Eq. 5).
   observables  energy (Eq. 11), specific heat, susceptibility (Eq. 13).
   ed           exact diagonalisation and full-state imaginary-time evolution (Eqs. 1-3).
