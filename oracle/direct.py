@@ -32,7 +32,8 @@ Readings (the appendix leaves these open):
 """
 import numpy as np
 
-from .peps import amplitude_exact
+from .peps import (absorb_down, absorb_up, amplitude_exact, compress, normalize, strip1_partials,
+                   strip1_step, trivial_env)
 
 
 def double_layer(lat, theta, fixed):
@@ -139,3 +140,74 @@ def update_bd(b_d, S_batch, N):
     if f > 0.5:
         b_d = b_d * (0.5 / f) ** (1.0 / N)
     return min(b_d, 1.0)
+
+
+# ------------------------------------------------- boundary-MPS form (the method's steps)
+#
+# The sums over unsampled sites are double-layer contractions, so the boundary-MPS scheme of
+# Sec. III.A (with the truncation reading of peps.compress) applies with bonds D^2:
+#   * down[r] (rows r..nrow-1, every site summed) does not depend on the sample: built once;
+#   * row by row, up[r] holds the sampled rows above (site tensors T^S (x) T^S);
+#   * in row r the sites left of c are sampled, site c takes each candidate state, the sites
+#     right of c are summed: the candidate's weight is the one-row strip
+#     (up[r], row r, down[r+1]), evaluated as left partial x site x right partial;
+#   * after the row is drawn it is absorbed into up[r+1] and truncated to chi.
+# At chi >= the largest exact bond this equals the exact form above.
+
+def _rows(lat, E):
+    return [[E[lat.site(r, c)] for c in range(lat.ncol)] for r in range(lat.nrow)]
+
+
+def summed_down_envs(lat, theta, chi):
+    """down[r] of the double layer with every site summed, r = 1..nrow (down[nrow] trivial)."""
+    rows = _rows(lat, double_layer(lat, theta, -np.ones(lat.N, dtype=np.int64)))
+    envs = [None] * (lat.nrow + 1)
+    envs[lat.nrow] = trivial_env(lat.ncol)
+    for r in range(lat.nrow - 1, 0, -1):
+        t, ls = envs[r + 1]
+        envs[r] = normalize(compress(absorb_down(t, rows[r]), chi), ls)
+    return envs
+
+
+def draw_bmps(lat, theta, u, chi, b_d=1.0, exponent=0.5, down=None):
+    """draw() with the marginals from boundary-MPS environments at bond chi.  Returns
+    (S, log q(S)); q is the probability of the draw under these (truncated) marginals."""
+    if down is None:
+        down = summed_down_envs(lat, theta, chi)
+    T = lat.tensors(theta)
+    summed = double_layer(lat, theta, -np.ones(lat.N, dtype=np.int64))
+    S = np.zeros(lat.N, dtype=np.int64)
+    logq = 0.0
+    up, ls_up = trivial_env(lat.ncol)
+    for r in range(lat.nrow):
+        Dt = down[r + 1][0]
+        row_sum = [summed[lat.site(r, c)] for c in range(lat.ncol)]
+        _, R = strip1_partials(up, row_sum, Dt)
+        L = np.ones((1, 1, 1))
+        fixed_row = []
+        for c in range(lat.ncol):
+            i = lat.site(r, c)
+            m = np.empty(4)
+            cand = []
+            for s in range(4):
+                A = T[i][s]
+                dl, dr, du, dd = lat.dims[i]
+                E = np.einsum('lrud,LRUD->lLrRuUdD', A, A).reshape(dl * dl, dr * dr, du * du, dd * dd)
+                Ls = strip1_step(L, up[c], E, Dt[c])
+                m[s] = float(np.tensordot(Ls, R[c + 1], axes=([0, 1, 2], [0, 1, 2])))
+                cand.append((E, Ls))
+            m = np.maximum(m, 0.0)          # truncation can leave tiny negative sums
+            p2c = m / m.sum() if m.sum() > 0 else np.zeros(4)
+            w = site_weights(p2c, b_d, exponent)
+            w = w / w.sum()
+            cdf = np.cumsum(w)
+            s = min(int(np.searchsorted(cdf, u[i] * cdf[-1], side='right')), 3)
+            while w[s] == 0.0:
+                s -= 1
+            S[i] = s
+            logq += np.log(w[s])
+            fixed_row.append(cand[s][0])
+            L = cand[s][1]
+        if r < lat.nrow - 1:
+            up, ls_up = normalize(compress(absorb_up(up, fixed_row), chi), ls_up)
+    return S, logq

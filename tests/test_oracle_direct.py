@@ -164,3 +164,30 @@ def test_update_bd():
     assert direct.update_bd(1.0, mixed, N) == 1.0
     three_quarters = np.vstack([diag[:6], np.ones((2, N), dtype=np.int64)])
     assert direct.update_bd(1.0, three_quarters, N) == pytest.approx((0.5 / 0.75) ** 0.25)
+
+
+@pytest.mark.parametrize("b_d,exponent", [(1.0, 1.0), (0.4, 0.5)])
+def test_boundary_mps_form_equals_exact_at_large_chi(b_d, exponent):
+    # the method's steps (summed down environments, up environments of the sampled rows,
+    # one-row strips per candidate) at chi above every exact bond reproduce the exact draws
+    lat = Lattice(3, 3, 2)
+    th = _theta(lat, 11)
+    rng = np.random.default_rng(12)
+    down = direct.summed_down_envs(lat, th, 64)
+    for _ in range(6):
+        u = rng.random(lat.N)
+        S, lq, _ = direct.draw(lat, th, u, b_d, exponent)
+        Sb, lqb = direct.draw_bmps(lat, th, u, 64, b_d, exponent, down=down)
+        assert np.array_equal(S, Sb)
+        assert lqb == pytest.approx(lq, rel=1e-9, abs=1e-12)
+
+
+def test_boundary_mps_truncation_changes_the_marginals():
+    # at chi below the exact bond the truncated marginals differ (a check that chi is used)
+    lat = Lattice(3, 3, 2)
+    th = _theta(lat, 13)
+    u = np.random.default_rng(14).random(lat.N)
+    _, lq_exact, _ = direct.draw(lat, th, u, 1.0, 1.0)
+    S2, lq2 = direct.draw_bmps(lat, th, u, 2, 1.0, 1.0)
+    q_exact_S2 = np.log(direct.sample_prob(lat, th, S2, 1.0, 1.0))
+    assert abs(lq2 - q_exact_S2) > 1e-8
