@@ -19,6 +19,8 @@ Modules:
   sampler      Metropolis sampling of |rho|^p, p = 2 (normal) or 1 (reweighted, Eq. A1).
   direct       direct (autoregressive) sampling from double-layer marginals and its
                reweighted form p_4 with the adaptive diagonal factor b_d (Eqs. A2-A7).
+  simple_update  bond-gate evolution with bond weights (the simple-update warm start of
+               App. A) and its conversion to PEPS parameters.
   sr           weights, Eq. 6/7/10 reductions, CG solve, parameter update (Eq. 5).
   observables  energy (Eq. 11), specific heat, susceptibility (Eq. 13).
   ed           exact diagonalisation and full-state imaginary-time evolution (Eqs. 1-3).
