@@ -10,6 +10,9 @@ state is (rho rho^T + rho^T rho) / (2 Tr rho rho^T); with w_i the sample weights
   <H^2> = 1/2 sum_i w_i (E_sys,i^2 + E_anc,i^2)             (||H rho||^2 = sum |rho|^2 E_sys^2)
   C/N   = beta_obs^2 (<H^2> - <H>^2) / N
   <Mz^2>= 1/2 sum_i w_i (M(s_i)^2 + M(s'_i)^2),  chi = beta_obs <Mz^2> / N, <Mz>^2 := 0 (Eq. 13)
+
+The paper's own C_v (Sec. III.A) is the derivative of a B-spline fitted to E(beta):
+cv_from_energy_curve, a post-processing cross-check of the fluctuation estimate above.
 """
 import numpy as np
 
@@ -30,3 +33,17 @@ def observables(lat, t, w, e_sys, e_anc, S_batch):
     diag = np.all(spin_sys(S_batch) == spin_anc(S_batch), axis=1)
     return dict(t=t, beta_obs=beta_obs, E_site=H1 / N, C_site=beta_obs ** 2 * (H2 - H1 * H1) / N,
                 chi=beta_obs * M2 / N, Mz2=M2, diag_frac=float(np.mean(diag)))
+
+
+def cv_from_energy_curve(betas, E_site, smoothing=0.0, k=3):
+    """Specific heat per site from a curve of E/N against beta_obs (Sec. III.A, Fig. 2b):
+    a B-spline of degree k fitted to the points (smoothing factor `smoothing`, 0 for
+    interpolation), then C/N = dE/dT = -beta^2 dE/dbeta from the spline's derivative.
+    Returns a function of beta."""
+    from scipy.interpolate import UnivariateSpline
+    betas = np.asarray(betas, dtype=np.float64)
+    order = np.argsort(betas)
+    spl = UnivariateSpline(betas[order], np.asarray(E_site, dtype=np.float64)[order], k=k,
+                           s=smoothing)
+    dE = spl.derivative()
+    return lambda b: -np.asarray(b, dtype=np.float64) ** 2 * dE(b)

@@ -41,3 +41,28 @@ def test_beta0_values():
     obs = observables.observables(lat, 0.0, w, zeros, zeros, cfgs)
     assert obs['Mz2'] == pytest.approx(N / 4)
     assert obs['diag_frac'] == 1.0 and obs['E_site'] == 0.0 and obs['chi'] == 0.0
+
+
+def test_spline_cv_matches_fluctuation_formula():
+    # Sec. III.A: C from the derivative of a B-spline through E(beta) equals the fluctuation
+    # formula beta^2 (<H^2> - <H>^2)/N of exact diagonalisation (2x3 Heisenberg)
+    lat = Lattice(2, 3, 1, J1=1.0)
+    spec = ed.spectrum(lat)
+    betas = np.linspace(0.05, 4.0, 80)
+    th = ed.thermal(spec, lat.N, betas)
+    cv = observables.cv_from_energy_curve(betas, th[:, 0])
+    probe = np.linspace(0.3, 3.7, 15)
+    assert np.allclose(cv(probe), ed.thermal(spec, lat.N, probe)[:, 1], atol=2e-4)
+
+
+def test_spline_cv_two_level_closed_form_and_noise():
+    # two levels at -+1: E = -tanh(beta), C = beta^2 / cosh(beta)^2; with noise of 1e-4 on
+    # E a smoothing spline (smoothing factor n sigma^2) still gives C within 1e-2
+    betas = np.linspace(0.0, 3.0, 121)
+    cv = observables.cv_from_energy_curve(betas, -np.tanh(betas))
+    probe = np.linspace(0.2, 2.8, 14)
+    assert np.allclose(cv(probe), probe ** 2 / np.cosh(probe) ** 2, atol=1e-5)
+    rng = np.random.default_rng(3)
+    noisy = -np.tanh(betas) + 1e-4 * rng.standard_normal(betas.size)
+    cvn = observables.cv_from_energy_curve(betas, noisy, smoothing=betas.size * 1e-8)
+    assert np.allclose(cvn(probe), probe ** 2 / np.cosh(probe) ** 2, atol=1e-2)
