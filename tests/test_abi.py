@@ -48,3 +48,31 @@ def test_invalid_params_rejected_without_gpu_work():
     p.chi, p.precision = 4, 7
     assert lib.peps_init(ctypes.byref(p), None, ctypes.byref(ctx)) == binding.PEPS_EINVAL
     assert not ctx.value
+
+
+def test_footprint_is_host_arithmetic():
+    # admission by footprint needs no device work: 0 for invalid parameters, and the bytes
+    # grow with the chain count (chain-outermost buffers) and with chi
+    lib = binding.load()
+    lib.peps_footprint.restype = ctypes.c_size_t
+    p = binding.Params(L1=8, L2=8, model=0, J1=1.0, J2=0.0, D=4, chi=16, n_chains=8192,
+                       precision=binding.PEPS_TF32, init_noise=1e-3, seed=0, n_blocks=0)
+    big = lib.peps_footprint(ctypes.byref(p))
+    p.n_chains = 4096
+    half = lib.peps_footprint(ctypes.byref(p))
+    assert 0 < half < big <= 2 * half + (1 << 26)
+    p.chi = 8
+    assert lib.peps_footprint(ctypes.byref(p)) < half
+    p.L1 = 1
+    assert lib.peps_footprint(ctypes.byref(p)) == 0
+
+
+def test_tuning_and_profile_calls_reject_a_null_context():
+    lib = binding.load()
+    t = binding.Tune(grid_pct=100, db_bytes=0, ffma_g=16, kc_max=64)
+    assert lib.peps_set_tune(None, ctypes.byref(t)) == binding.PEPS_EINVAL
+    assert lib.peps_autotune(None, 0, ctypes.byref(t)) == binding.PEPS_EINVAL
+    buf = (ctypes.c_double * 4)()
+    n = ctypes.c_int()
+    assert lib.peps_profile_launch_bytes(None, b"kb_gemm_tc", buf, 4, ctypes.byref(n)) == \
+        binding.PEPS_EINVAL
