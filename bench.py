@@ -202,6 +202,14 @@ def kernel_roofline(kstats, peaks, prec, binding):
             "peak_source": "derived: FMA/clk/SM x 152 SMs x 2070 MHz"}, kernels
 
 
+def workload_config(wl, n, ws):
+    """The `config` object both arms report for a workload at n chains per GPU."""
+    return {"workload": f"{wl.L}x{wl.L} OBC Heisenberg J1={wl.J1} J2={wl.J2}, d2=4, "
+                        f"D={wl.D}, chi={wl.chi}, chains={n} per GPU",
+            "global_batch": ws * n, "tau": wl.tau, "eps": wl.eps, "max_cg": wl.max_cg,
+            "cg_tol": wl.cg_tol, "parallelism": f"replicas{ws}"}
+
+
 def cooled_state(ctx, steps, tau, p_switch_t):
     """Cools the fresh context for `steps` SR steps (p = 1 while beta_obs < 0.3)."""
     t = 0.0
@@ -355,11 +363,8 @@ def run_ours(args):
         "dtype": {binding.PEPS_FP64: "f64", binding.PEPS_FP32: "f32",
                   binding.PEPS_TF32: "tf32 (contractions; f32 storage, f64 SR)"}[prec],
         "data": "synthetic (seeded beta=0 PEPS cooled in-run; no dataset)",
-        "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg J1={wl.J1} J2={wl.J2}, d2=4, "
-                               f"D={wl.D}, chi={wl.chi}, chains={n} per GPU",
-                   "global_batch": ws * n, "tau": tau, "eps": eps, "max_cg": max_cg,
-                   "cg_tol": tol, "t_start": t0, "parallelism": f"replicas{ws}",
-                   "l2": "inputs larger than L2 (O rows %.0f MB)" % (n * ctx.No * (8 if prec == 0 else 4) / 1e6)},
+        "config": dict(workload_config(wl, n, ws), t_start=t0,
+                       l2="inputs larger than L2 (O rows %.0f MB)" % (n * ctx.No * (8 if prec == 0 else 4) / 1e6)),
         "sr_steps_per_s": ws / (ms_per_step / 1e3),
         "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
                        "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
@@ -500,10 +505,10 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg D={wl.D} "
-                                                       f"chi={wl.chi}, {n_s} chains per step (bounded sample)"},
+           "data": "synthetic", "config": workload_config(wl, args.chains or wl.n_samples, ws),
            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": cores, "kind": "oracle",
-                            "sample": f"{n_s} chains per step: sweep + evaluation + SR step"},
+                            "sample": f"{n_s} of the workload's chains per timed step: one sweep + "
+                                      f"evaluation each, then one SR step on them"},
            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
