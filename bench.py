@@ -35,14 +35,15 @@ PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from one
 # ncu capture of every launch of that kernel in this bench's timed step (the timed region is
 # bracketed by cudaProfilerStart/Stop, so `ncu --profile-from-start off` captures exactly it),
-# stored with the SHA-256 of the kernel and launch-planner sources it was taken on.  Once those
-# sources change the entry no longer applies and the bench reports null.
+# stored with the SHA-256 of the kernel and launch-planner sources it was taken on (their code,
+# comments excluded).  Once that code changes the entry no longer applies and the bench
+# reports null.
 NCU_TRAFFIC = {
     ("heis8", "tf32", 8192, "kb_gemm_tc"): {
         "launches": 200,
         "dram_bytes": 66987750144,      # DRAM read + write of the first 200 launches of the step
         "alg_bytes": 75240312832,       # algorithmic bytes of the same 200 launches
-        "sources_sha256": "7044afc585d3148fbf14162c480277f2c374c81eaccae1b2b2038d9531142c53",
+        "sources_sha256": "e8d43633e2acafda7bccf83a7be4e273ee7509167182314757cace304cc7978a",
         "source": "ncu --profile-from-start off -k regex:kb_gemm_tc -c 200 (dram__bytes_read.sum "
                   "+ dram__bytes_write.sum, cold cache), first 200 launches of the timed step with "
                   "the autotuned shapes 100,12288,16,32, scaled by algorithmic bytes; "
@@ -52,12 +53,21 @@ NCU_TRAFFIC = {
 TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_batch.cuh")
 
 
+def code_text(src):
+    """C++ source without comments and with whitespace runs collapsed: what the compiler sees
+    of it, so that editing a comment does not invalidate a recorded measurement."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return " ".join(src.split())
+
+
 def sources_sha256():
     import hashlib
     h = hashlib.sha256()
     for rel in TRAFFIC_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel)) as f:
+            h.update(code_text(f.read()).encode())
     return h.hexdigest()
 
 

@@ -10,8 +10,11 @@
 // contiguous bytes); one thread issues Kc/8 `tcgen05.mma.kind::tf32` instructions
 // (M = 128, N = the tile width) into an accumulator in tensor memory and commits them to an
 // mbarrier; after the last chunk each warp reads its 32 accumulator lanes with
-// `tcgen05.ld` and scatters them to C.  Every wait on the mbarrier is bounded: when it runs
-// out the kernel raises `err`, waits once more, frees its tensor memory and returns.
+// `tcgen05.ld` and scatters them to C.  Rows of a chunk past the edge of C are not gathered
+// (they only reach accumulator rows and columns that are not stored), and a Gram product
+// C = P P^T that one tile covers gathers P once: the B descriptor points at the A stage.
+// Every wait on the mbarrier is bounded: when it runs out the kernel raises `err`, waits once
+// more, frees its tensor memory and returns.
 #ifndef PV_TC_CUH
 #define PV_TC_CUH
 #include <cstdint>

@@ -36,3 +36,12 @@ def test_recorded_entries_are_well_formed():
         assert len(key) == 4 and key[1] in ("fp32", "tf32", "fp64")
         assert rec["dram_bytes"] > 0 and rec["alg_bytes"] > 0 and rec["launches"] > 0
         assert len(rec["sources_sha256"]) == 64 and rec["source"]
+
+
+def test_source_hash_ignores_comments_only():
+    bench = _bench()
+    a = "int f(int x) {  // doubles x\n  return 2 * x; /* no overflow check */ }\n"
+    b = "int f(int x) {\n  // a different comment\n  return 2 * x;\n}\n"
+    c = "int f(int x) { return 3 * x; }"
+    assert bench.code_text(a) == bench.code_text(b)
+    assert bench.code_text(a) != bench.code_text(c)
