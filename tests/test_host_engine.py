@@ -1,0 +1,114 @@
+"""The batched engine's orchestration (BatchRunner: environments, compression, strips,
+ratios, O rows, Metropolis moves) built for the host over plain loops
+(tests/host_engine/host_engine.cpp) and checked against the FP64 oracle on the CPU, with the
+tolerances of the FP64 GPU parity tests.  The GPU kernels themselves are covered by the
+`-m gpu` parity tests; this covers the sequence of operations without a GPU."""
+import os
+import shutil
+import struct
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import peps, sampler
+from oracle.lattice import Lattice
+from paper_2409_05285_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "tests", "host_engine", "host_engine.cpp")
+CSRC = os.path.join(ROOT, "paper_2409_05285_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def engine(tmp_path_factory):
+    if shutil.which("g++") is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("host_engine") / "host_engine")
+    subprocess.run(["g++", "-std=c++17", "-O2", "-I", CSRC, SRC, "-o", exe], check=True)
+    return exe
+
+
+def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
+    n = S.shape[0]
+    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+    with open(fin, "wb") as f:
+        f.write(struct.pack("<7i", mode, lat.nrow, lat.ncol, lat.D, chi, n, p))
+        f.write(struct.pack("<2d", lat.J1, lat.J2))
+        f.write(struct.pack("<Qi", seed, sweep))
+        f.write(np.asarray(th, dtype=np.float64).tobytes())
+        f.write(np.asarray(S, dtype=np.uint8).tobytes())
+    subprocess.run([exe, fin, fout], check=True)
+    raw = open(fout, "rb").read()
+    if mode == 0:
+        o = 0
+        la = np.frombuffer(raw, np.float64, n, o); o += 8 * n
+        sg = np.frombuffer(raw, np.int8, n, o); o += n
+        es = np.frombuffer(raw, np.float64, n, o); o += 8 * n
+        ea = np.frombuffer(raw, np.float64, n, o); o += 8 * n
+        O = np.frombuffer(raw, np.float64, n * lat.No, o).reshape(n, lat.No)
+        return la, sg, es, ea, O
+    N = lat.N
+    S2 = np.frombuffer(raw, np.uint8, n * N, 0).reshape(n, N)
+    acc = np.frombuffer(raw, np.int32, n, n * N)
+    prop = np.frombuffer(raw, np.int32, n, n * N + 4 * n)
+    return S2, acc, prop
+
+
+CASES = [  # (L1, L2, D, chi, J2, n): exact chi (first two), truncated chi, NNN bonds
+    (2, 2, 2, 4, 0.0, 4),
+    (3, 3, 2, 4, 0.0, 5),
+    (3, 4, 2, 3, 0.5, 4),
+    (4, 3, 3, 5, 0.2, 3),
+]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_host_engine_eval_matches_oracle(engine, tmp_path, case):
+    L1, L2, D, chi, J2, n = case
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=L1 * 10 + L2, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=D)
+    la, sg, es, ea, O = _run(engine, tmp_path, 0, lat, chi, th, S)
+    for k in range(n):
+        r = peps.eval_sample(lat, th, S[k], chi)
+        assert sg[k] == r['sign']
+        assert abs(la[k] - r['log_abs']) <= 1e-10
+        scale = max(1.0, abs(r['e_sys']), abs(r['e_anc']))
+        assert abs(es[k] - r['e_sys']) <= 1e-9 * scale
+        assert abs(ea[k] - r['e_anc']) <= 1e-9 * scale
+        assert np.max(np.abs(O[k] - r['O'])) <= 1e-9 * max(1.0, np.max(np.abs(r['O'])))
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 2, 4, 0.0), (3, 4, 2, 3, 0.5)])
+@pytest.mark.parametrize("p", [2, 1])
+def test_host_engine_sweep_matches_oracle(engine, tmp_path, p, shape):
+    # one Metropolis sweep per chain with the same Philox stream: the same accepted moves
+    # (exact chi, and a truncating chi with next-nearest-neighbour bonds)
+    L1, L2, D, chi, J2 = shape
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=33, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, 6, seed=34)
+    seed, sweep = 11, 5
+    S2, acc, prop = _run(engine, tmp_path, 1, lat, chi, th, S, p=p, seed=seed, sweep=sweep)
+    for ch in range(S.shape[0]):
+        So, a, b = sampler.mc_sweep(lat, th, S[ch], chi, p, seed, ch, sweep)
+        assert np.array_equal(S2[ch], So), ch
+        assert (acc[ch], prop[ch]) == (a, b)
+
+
+def test_host_engine_eval_heis8_shape(engine, tmp_path):
+    # 8x8, D=4, chi=16: the bench workload's contraction sizes and truncations
+    L, D, chi = 8, 4, 16
+    lat = Lattice(L, L, D)
+    th = wl.random_theta(L, L, D, seed=81, scale=0.2, diag_bias=1.0)
+    S = wl.random_configs(L, L, 2, seed=82)
+    la, sg, es, ea, O = _run(engine, tmp_path, 0, lat, chi, th, S)
+    for k in range(S.shape[0]):
+        r = peps.eval_sample(lat, th, S[k], chi)
+        assert sg[k] == r['sign']
+        assert abs(la[k] - r['log_abs']) <= 1e-10
+        scale = max(1.0, abs(r['e_sys']), abs(r['e_anc']))
+        assert abs(es[k] - r['e_sys']) <= 1e-9 * scale
+        assert abs(ea[k] - r['e_anc']) <= 1e-9 * scale
+        assert np.max(np.abs(O[k] - r['O'])) <= 1e-8 * max(1.0, np.max(np.abs(r['O'])))
