@@ -207,6 +207,18 @@ int peps_autotune(peps_ctx* ctx, int reps, peps_tune* out);
  * engine. */
 int peps_set_tune(peps_ctx* ctx, const peps_tune* t);
 
+/* Simple-update warm start (App. A): from the beta = 0 state, n_steps first-order Trotter
+ * steps of length tau of the nearest-neighbour Heisenberg bond gates e^{-tau calH_ij}
+ * (Eq. 3 per bond of Eq. 12, coupling J1) with bond weights standing in for the
+ * environment, bonds truncated to D; writes the N_p parameters of the resulting PEPS
+ * (bond weights split over both tensors, legs zero-padded to D) to the caller-owned host
+ * buffer `theta` in the layout of peps_set_theta, which then hands the state to SR at
+ * t = n_steps * tau (beta_obs = 4t).  Runs on the host (one state, small dense
+ * factorisations); no context or GPU is needed.  EINVAL for bad sizes or arguments
+ * (n must equal N_p for L1 x L2 at bond dimension D). */
+int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, double* theta,
+                  size_t n);
+
 /* Per-kernel statistics for roofline reports.  peps_profile(ctx, 1) clears them and starts
  * bracketing every launch of the context with CUDA events on its stream; peps_profile(ctx,
  * 2) does the same for the batched GEMM kernels only (kb_gemm_tc, kb_gemm: fewer events in

@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta",
 ]
 
 
@@ -141,6 +141,8 @@ def load(path=None):
     lib.peps_profile.argtypes = [vp, ip]
     lib.peps_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ip)]
     lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
+    lib.peps_su_theta.argtypes = [ip, ip, ip, dp, dp, ip, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_size_t]
     lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                               ip, ctypes.POINTER(ip)]
     _lib = lib
@@ -151,6 +153,23 @@ class PepsError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"peps error {code}: {msg}")
         self.code = code
+
+
+def su_theta(L1, L2, D, J1, tau, n_steps):
+    """Parameters after the library's simple-update warm start (peps_su_theta: host-side,
+    no GPU); hand them to Context.set_theta for SR from t = n_steps * tau."""
+    lib = load()
+    n = 0
+    for r in range(L1):
+        for c in range(L2):
+            n += 4 * (1 if c == 0 else D) * (1 if c == L2 - 1 else D) * (1 if r == 0 else D) * \
+                (1 if r == L1 - 1 else D)
+    out = np.zeros(n)
+    rc = lib.peps_su_theta(L1, L2, D, J1, tau, n_steps,
+                           out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n)
+    if rc != PEPS_OK:
+        raise PepsError(rc, "su_theta: invalid arguments")
+    return out
 
 
 def _ptr(a):

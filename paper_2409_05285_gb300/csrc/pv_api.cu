@@ -13,6 +13,7 @@
 #include "pv_sample.cuh"
 #include "pv_sr.cuh"
 #include "pv_batch.cuh"
+#include "pv_su.cuh"
 
 #include <memory>
 #include <map>
@@ -1126,6 +1127,22 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     out->ms_before = before;
     out->ms_after = cur;
   }
+  return PEPS_OK;
+}
+
+int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, double* theta,
+                  size_t n) {
+  if (L1 < 2 || L2 < 2 || L1 > MAX_L || L2 > MAX_L || D < 1 || D > 8 || n_steps < 0 ||
+      !(tau >= 0.0) || !std::isfinite(J1) || !theta)
+    return PEPS_EINVAL;
+  size_t Np = 0;
+  for (int r = 0; r < L1; ++r)
+    for (int c = 0; c < L2; ++c)
+      Np += (size_t)4 * (c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) * (r == L1 - 1 ? 1 : D);
+  if (n != Np) return PEPS_EINVAL;
+  pv::SimpleUpdate su(L1, L2, D, J1);
+  for (int k = 0; k < n_steps; ++k) su.step(tau);
+  su.theta(theta);
   return PEPS_OK;
 }
 
