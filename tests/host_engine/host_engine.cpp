@@ -7,15 +7,17 @@
 // GEMMs, shared-memory Householder, Cholesky) are not part of this build.
 //
 // Usage: host_engine <in.bin> <out.bin>
-//   in:  int32 mode (0 eval, 1 one Metropolis sweep), L1, L2, D, chi, n, p; float64 J1, J2;
-//        uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N]
+//   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw), L1, L2, D, chi, n, p;
+//        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
+//        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
 //        mc:   uint8 S[n][N], int32 acc[n], int32 prop[n]
+//        draw: uint8 S[n][N], float64 log_q[n]  (direct sampling, pv_direct.cuh)
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
 
-#include "pv_batch.cuh"
+#include "pv_direct.cuh"
 
 using namespace pv;
 using T = double;
@@ -95,6 +97,12 @@ struct HostBE {
   void accept(ElemAccept<T> f, int n) {
     for (int s = 0; s < n; ++s) f(s);
   }
+  void set_i8(int8_t* x, int8_t v, int n) {
+    for (int s = 0; s < n; ++s) x[s] = v;
+  }
+  void draw(ElemDraw<T> f, int n) {
+    for (int s = 0; s < n; ++s) f(s);
+  }
 };
 
 template <typename X>
@@ -131,7 +139,28 @@ int main(int argc, char** argv) {
   rd(fi, theta.data(), theta.size());
   std::vector<uint8_t> S((size_t)n * N);
   rd(fi, S.data(), S.size());
+  double bx[2] = {1.0, 0.5};
+  std::vector<double> u;
+  if (mode == 2) {
+    rd(fi, bx, 2);
+    u.resize((size_t)n * N);
+    rd(fi, u.data(), u.size());
+  }
   std::fclose(fi);
+  // direct sampling contracts the double-layer network: bond D^2, five local tensors per site
+  const int Dn = mode == 2 ? D * D : D;
+  std::vector<T> theta2;
+  if (mode == 2) {
+    toff.assign(N + 1, 0);
+    for (int i = 0; i < N; ++i) {
+      const int r = i / L2, c = i % L2;
+      const long long sz = (long long)(c == 0 ? 1 : Dn) * (c == L2 - 1 ? 1 : Dn) * (r == 0 ? 1 : Dn) *
+                           (r == L1 - 1 ? 1 : Dn);
+      toff[i + 1] = toff[i] + 5 * sz;
+    }
+    theta2.resize((size_t)toff[N]);
+    double_layer_theta(L1, L2, D, theta.data(), theta2.data());
+  }
 
   HostBE be;
   std::vector<int> bi, bj;
@@ -142,33 +171,33 @@ int main(int argc, char** argv) {
   be.bi = bi.data();
   be.bj = bj.data();
   be.bJ = bJ.data();
-  const long long cD = (long long)chi * D;
+  const long long cD = (long long)chi * Dn;
   be.trunc_cap = 2 * cD * (cD + 1);
 
   BatchRunner<T, HostBE, T> run(be);
   std::vector<long long> sz;
   long long n8 = 0, nd = 0, per = 0;
-  BatchBufs<T>::sizes(L1, L2, D, chi, sz, n8, nd);
+  BatchBufs<T>::sizes(L1, L2, Dn, chi, sz, n8, nd);
   for (long long x : sz) per += x;
   std::vector<T> real((size_t)per * n, 0.0);
   std::vector<int8_t> i8((size_t)n8 * n, 0);
   std::vector<double> dbl((size_t)nd * n, 0.0);
   unsigned long long jsw = 0;
-  run.shp.build(L1, L2, D, chi);
+  run.shp.build(L1, L2, Dn, chi);
   run.L1 = L1;
   run.L2 = L2;
-  run.D = D;
+  run.D = Dn;
   run.chi = chi;
   run.N = N;
   run.J1 = J[0];
   run.J2 = J[1];
-  run.theta = theta.data();
+  run.theta = mode == 2 ? theta2.data() : theta.data();
   run.toff = toff;
   run.ooff = ooff;
   run.jtol = 1e-15;
   run.max_sweeps = 60;
   run.sweeps = &jsw;
-  run.b.bind(real.data(), n, i8.data(), dbl.data(), L1, L2, D, chi);
+  run.b.bind(real.data(), n, i8.data(), dbl.data(), L1, L2, Dn, chi);
 
   FILE* fo = std::fopen(argv[2], "wb");
   if (!fo) return 2;
@@ -183,6 +212,11 @@ int main(int argc, char** argv) {
     std::fwrite(es.data(), 8, n, fo);
     std::fwrite(ea.data(), 8, n, fo);
     std::fwrite(O.data(), 8, O.size(), fo);
+  } else if (mode == 2) {
+    std::vector<double> logq(n, 0.0);
+    direct_draw(run, S.data(), n, u.data(), bx[0], bx[1], logq.data());
+    std::fwrite(S.data(), 1, S.size(), fo);
+    std::fwrite(logq.data(), 8, n, fo);
   } else {
     std::vector<int> acc(n, 0), prop(n, 0);
     run.mc(S.data(), n, p, seed, 0, (uint32_t)sweep, acc.data(), prop.data());

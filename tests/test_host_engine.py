@@ -112,3 +112,39 @@ def test_host_engine_eval_heis8_shape(engine, tmp_path):
         assert abs(es[k] - r['e_sys']) <= 1e-9 * scale
         assert abs(ea[k] - r['e_anc']) <= 1e-9 * scale
         assert np.max(np.abs(O[k] - r['O'])) <= 1e-8 * max(1.0, np.max(np.abs(r['O'])))
+
+
+def _run_draw(exe, tmp, lat, chi, th, u, b_d, expo):
+    n, N = u.shape
+    fin, fout = str(tmp / "in.bin"), str(tmp / "out.bin")
+    with open(fin, "wb") as f:
+        f.write(struct.pack("<7i", 2, lat.nrow, lat.ncol, lat.D, chi, n, 2))
+        f.write(struct.pack("<2d", lat.J1, lat.J2))
+        f.write(struct.pack("<Qi", 0, 0))
+        f.write(np.asarray(th, dtype=np.float64).tobytes())
+        f.write(np.zeros(n * N, dtype=np.uint8).tobytes())
+        f.write(struct.pack("<2d", b_d, expo))
+        f.write(np.asarray(u, dtype=np.float64).tobytes())
+    subprocess.run([exe, fin, fout], check=True)
+    raw = open(fout, "rb").read()
+    return (np.frombuffer(raw, np.uint8, n * N, 0).reshape(n, N),
+            np.frombuffer(raw, np.float64, n, n * N))
+
+
+@pytest.mark.parametrize("case", [(2, 3, 2, 16, 1.0, 1.0), (3, 3, 2, 16, 0.4, 0.5),
+                                  (3, 3, 2, 4, 0.6, 0.5), (3, 4, 2, 6, 1.0, 0.5)])
+def test_host_engine_direct_draw_matches_oracle(engine, tmp_path, case):
+    # reweighted direct sampling (App. A) through the engine's own environments and strips
+    # over double-layer tensors (pv_direct.cuh) against the oracle's boundary-MPS form: the
+    # same samples and log q for the same uniforms, at exact and at truncating chi
+    from oracle import direct
+    L1, L2, D, chi, b_d, expo = case
+    lat = Lattice(L1, L2, D)
+    th = wl.random_theta(L1, L2, D, seed=L1 * 7 + L2, scale=0.4, diag_bias=1.0)
+    u = np.random.default_rng(L1 + 10 * L2 + chi).random((5, lat.N))
+    S, lq = _run_draw(engine, tmp_path, lat, chi, th, u, b_d, expo)
+    down = direct.summed_down_envs(lat, th, chi)
+    for k in range(u.shape[0]):
+        So, lqo = direct.draw_bmps(lat, th, u[k], chi, b_d, expo, down=down)
+        assert np.array_equal(S[k], So), k
+        assert lq[k] == pytest.approx(lqo, rel=1e-9, abs=1e-11)
