@@ -1,5 +1,6 @@
-"""The bench's recorded DRAM traffic: it applies only to the sources it was captured on, and
-it is scaled from the captured launches to the timed steps by algorithmic bytes."""
+"""Host-side logic of bench.py: the recorded DRAM traffic (it applies only to the code it was
+captured on and is scaled from the captured launches to the timed steps by algorithmic
+bytes), the roofline arithmetic, and the config object both arms report."""
 import os
 import sys
 
@@ -45,3 +46,30 @@ def test_source_hash_ignores_comments_only():
     c = "int f(int x) { return 3 * x; }"
     assert bench.code_text(a) == bench.code_text(b)
     assert bench.code_text(a) != bench.code_text(c)
+
+
+def test_kernel_roofline_arithmetic():
+    # achieved = algorithmic bytes per launch / mean launch time; frac against the measured
+    # HBM copy bandwidth; the dominant kernel is the one with the most event time
+    bench = _bench()
+
+    class B:
+        PEPS_FP64 = 0
+
+    ks = {"kb_gemm_tc": (100, 50.0, 100 * 2.0e8, 0.0), "kb_gemm": (40, 10.0, 40 * 1.0e7, 0.0)}
+    roof, kernels = bench.kernel_roofline(ks, {"hbm_gbs": 6000.0}, 2, B)
+    assert roof["kernel"] == "kb_gemm_tc" and roof["bound"] == "hbm"
+    assert roof["achieved"] == 2.0e8 / 0.5e-3 / 1e9
+    assert roof["frac"] == roof["achieved"] / 6000.0
+    assert roof["mean_launch_us"] == 500.0 and roof["launches"] == 100
+    assert abs(roof["share_of_timed_kernels"] - 50.0 / 60.0) < 1e-15
+    assert list(kernels) == ["kb_gemm_tc", "kb_gemm"]
+
+
+def test_both_arms_share_the_config_object():
+    bench = _bench()
+    from paper_2409_05285_gb300.workloads import WORKLOADS
+    wl = WORKLOADS["heis8"]
+    c = bench.workload_config(wl, wl.n_samples, 1)
+    assert "chains=8192 per GPU" in c["workload"] and c["global_batch"] == 8192
+    assert bench.workload_config(wl, wl.n_samples, 4)["global_batch"] == 4 * 8192
