@@ -20,6 +20,8 @@ Scheme (the paper gives no details; the standard SU written out here):
     gate on (S_A, S_B), split by SVD, keep the D largest singular values (those above 1e-14 of
     the largest), store them divided by their largest as the new lam_AB, and divide the outer
     weights back out of the two new tensors.
+  * Next-nearest-neighbour bonds (J2) through a site of their plaquette with exchange gates
+    (su_step).
   * to_theta: sqrt(lam) of each bond multiplied into both of its tensors, legs zero-padded to
     the lattice's bond dimension D (trimmed open boundaries keep dimension 1), in the layout
     of oracle.lattice.  The overall scale of the state is arbitrary (ratios, O and the
@@ -80,8 +82,18 @@ def _inv(w):
     return np.where(w > 0, 1.0 / np.where(w > 0, w, 1.0), 0.0)
 
 
-def apply_bond(st, r, c, horizontal, J, tau, D):
-    """Gate on the bond from (r, c) to its right (horizontal) or lower neighbour."""
+def swap_gate():
+    """Exchange of the whole local states of two sites, 16 x 16 on (S_i, S_j)."""
+    G = np.zeros((16, 16))
+    for a in range(4):
+        for b in range(4):
+            G[4 * b + a, 4 * a + b] = 1.0
+    return G
+
+
+def apply_bond(st, r, c, horizontal, J, tau, D, gate=None):
+    """Gate on the bond from (r, c) to its right (horizontal) or lower neighbour
+    (e^{-tau calH_ij} with coupling J, or the 16 x 16 `gate` when given)."""
     lat = st.lat
     ia = lat.site(r, c)
     rb, cb = (r, c + 1) if horizontal else (r + 1, c)
@@ -106,7 +118,7 @@ def apply_bond(st, r, c, horizontal, J, tau, D):
     theta = np.tensordot(A2, B2, axes=([4], [1]))  # S_A, oa..., S_B, ob...
     theta = np.moveaxis(theta, 4, 1)               # S_A, S_B, oa..., ob...
     th = theta.reshape(16, -1)
-    th = (bond_gate(J, tau) @ th).reshape((4, 4) + sa + sb)
+    th = ((bond_gate(J, tau) if gate is None else gate) @ th).reshape((4, 4) + sa + sb)
     th = np.moveaxis(th, 1, 4)                     # S_A, oa..., S_B, ob...
     M = th.reshape(4 * int(np.prod(sa)), 4 * int(np.prod(sb)))
     U, s, Vt = np.linalg.svd(M, full_matrices=False)
@@ -131,17 +143,27 @@ def apply_bond(st, r, c, horizontal, J, tau, D):
 
 
 def su_step(st, tau, D):
-    """One first-order Trotter step of length tau: every bond of Eq. 12 once (nearest
-    neighbours only; J2 bonds are not nearest-neighbour gates and are not supported here)."""
+    """One first-order Trotter step of length tau: every bond of Eq. 12 once.  Nearest-
+    neighbour bonds directly; a next-nearest-neighbour bond of plaquette (r, c) through the
+    plaquette's top-right site (r, c+1) for the diagonal (r,c)-(r+1,c+1), or top-left site
+    (r, c) for the anti-diagonal (r,c+1)-(r+1,c): exchange the local states across the top
+    bond, apply the gate on the vertical bond that then joins the two sites' states, and
+    exchange back (each exchange a bond update with truncation to D)."""
     lat = st.lat
-    if lat.J2 != 0.0:
-        raise ValueError("simple update here covers nearest-neighbour bonds only")
     for r in range(lat.nrow):
         for c in range(lat.ncol - 1):
             apply_bond(st, r, c, True, lat.J1, tau, D)
     for r in range(lat.nrow - 1):
         for c in range(lat.ncol):
             apply_bond(st, r, c, False, lat.J1, tau, D)
+    if lat.J2 != 0.0:
+        sw, g2 = swap_gate(), bond_gate(lat.J2, tau)
+        for r in range(lat.nrow - 1):
+            for c in range(lat.ncol - 1):
+                for via in (c + 1, c):            # diagonal, then anti-diagonal
+                    apply_bond(st, r, c, True, 0.0, 0.0, D, gate=sw)
+                    apply_bond(st, r, via, False, 0.0, 0.0, D, gate=g2)
+                    apply_bond(st, r, c, True, 0.0, 0.0, D, gate=sw)
 
 
 def to_theta(st):

@@ -78,6 +78,22 @@ def test_high_temperature_energy_tracks_exact(shape):
     assert errs[0] < errs[1] < errs[2]
 
 
-def test_next_nearest_neighbour_bonds_are_rejected():
-    with pytest.raises(ValueError):
-        su.su_step(su.SUState(Lattice(2, 2, 2, J2=0.5)), 0.01, 2)
+def test_swap_gate_exchanges_local_states():
+    G = su.swap_gate()
+    v = np.random.default_rng(3).standard_normal((4, 4))    # amplitudes over (S_i, S_j)
+    assert np.array_equal((G @ v.reshape(-1)).reshape(4, 4), v.T)
+    assert np.array_equal(G @ G, np.eye(16))
+
+
+def test_next_nearest_neighbour_bonds_converge_to_exact():
+    # J2 bonds routed through a plaquette site with exchange gates: with bonds large enough
+    # for the exchanges (D = 32 on 2x2) the SU state tracks ED like the J1-only one; at D = 4
+    # the exchanges are truncated and the error is three orders larger
+    errs = {}
+    for D in (4, 32):
+        lat = Lattice(2, 2, D, J1=1.0, J2=0.5)
+        Hd = ed.doubled_hamiltonian(lat)
+        v = _vec(lat, _evolved(lat, 0.05, 0.01, D))
+        e = v @ Hd @ v / (2 * (v @ v)) / lat.N
+        errs[D] = abs(e - ed.thermal(ed.spectrum(lat), lat.N, [0.2])[0][0])
+    assert errs[32] < 1e-6 and errs[4] > 1e-4
