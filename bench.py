@@ -29,6 +29,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 BLOCK_MODES = {"auto": 0, "narrow": 1, "wide": 2, "batched": 3}
 # Per-SM issue rates of GB300 (sm_103): 128 FP32 FMA/clk, 2 FP64 FMA/clk; 152 SMs; 2070 MHz.
 SMS, MAX_MHZ = 152, 2070.0
+SU_TAU = 0.01   # step of the simple-update warm start (--su-warmup)
 PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 
@@ -220,9 +221,10 @@ def workload_config(wl, n, ws):
             "cg_tol": wl.cg_tol, "parallelism": f"replicas{ws}"}
 
 
-def cooled_state(ctx, steps, tau, p_switch_t):
-    """Cools the fresh context for `steps` SR steps (p = 1 while beta_obs < 0.3)."""
-    t = 0.0
+def cooled_state(ctx, steps, tau, p_switch_t, t_start=0.0):
+    """Cools the context for `steps` SR steps from imaginary time t_start (p = 1 while
+    beta_obs < 0.3).  Returns the imaginary time reached."""
+    t = t_start
     for _ in range(steps):
         p = 1 if 4 * t < p_switch_t else 2
         ctx.step(n_sweeps=1, p=p, tau=tau, eps=1e-4, max_cg=100, cg_tol=1e-10)
@@ -254,8 +256,16 @@ def run_ours(args):
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
                           init_noise=wl.init_noise, seed=rank_seed(wl.seed, rank), n_blocks=args.blocks,
                           stream=ctypes_stream(stream), block_mode=BLOCK_MODES[args.block_mode])
-    ctx.mc_sweep(args.burn, p=1)
-    t0 = cooled_state(ctx, args.precool, wl.tau, 0.3)
+    t_su = 0.0
+    if args.su_warmup > 0:
+        # simple-update warm start (host-side, nearest-neighbour bonds) to t = su_warmup
+        if wl.J2 != 0.0:
+            raise SystemExit("--su-warmup: the simple-update warm start covers J1 bonds only")
+        n_su = max(1, int(round(args.su_warmup / SU_TAU)))
+        ctx.set_theta(binding.su_theta(wl.L, wl.L, wl.D, wl.J1, SU_TAU, n_su))
+        t_su = n_su * SU_TAU
+    ctx.mc_sweep(args.burn, p=1 if 4 * t_su < 0.3 else 2)
+    t0 = cooled_state(ctx, args.precool, wl.tau, 0.3, t_start=t_su)
     tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
     p = 2
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -374,6 +384,8 @@ def run_ours(args):
                   binding.PEPS_TF32: "tf32 (contractions; f32 storage, f64 SR)"}[prec],
         "data": "synthetic (seeded beta=0 PEPS cooled in-run; no dataset)",
         "config": dict(workload_config(wl, n, ws), t_start=t0,
+                       warm_start=(f"simple update to t={t_su:g} (tau {SU_TAU:g})" if t_su > 0
+                                   else "perturbed beta=0 state"),
                        l2="inputs larger than L2 (O rows %.0f MB)" % (n * ctx.No * (8 if prec == 0 else 4) / 1e6)),
         "sr_steps_per_s": ws / (ms_per_step / 1e3),
         "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
@@ -383,7 +395,7 @@ def run_ours(args):
         "cg_iters": statistics.mean(cg_its),
         "eval_gflop_per_sample": statistics.mean(eval_flops) / n / 1e9,
         "jacobi_sweeps_per_sample": statistics.mean(jac),
-        "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"],
+        "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"] + 4.0 * t_su,
         "roofline": roofline,
         "kernels": kernels,
         "autotune": tune,
@@ -597,6 +609,8 @@ def main():
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-chains", type=int, default=608)
+    ap.add_argument("--su-warmup", type=float, default=0.0,
+                    help="start from the simple-update state at this imaginary time (J1 workloads)")
     ap.add_argument("--tune", default="",
                     help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max")
     ap.add_argument("--launch-bytes", default="",

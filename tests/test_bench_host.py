@@ -73,3 +73,23 @@ def test_both_arms_share_the_config_object():
     c = bench.workload_config(wl, wl.n_samples, 1)
     assert "chains=8192 per GPU" in c["workload"] and c["global_batch"] == 8192
     assert bench.workload_config(wl, wl.n_samples, 4)["global_batch"] == 4 * 8192
+
+
+def test_cooling_starts_from_the_warm_start_time():
+    # the sampling exponent switches from 1 to 2 at beta_obs = 4t = 0.3, counting the
+    # imaginary time of a simple-update warm start
+    bench = _bench()
+
+    class Ctx:
+        def __init__(self):
+            self.ps = []
+
+        def step(self, n_sweeps, p, tau, eps, max_cg, cg_tol):
+            self.ps.append(p)
+
+    c = Ctx()
+    assert bench.cooled_state(c, 5, 0.02, 0.3) == 5 * 0.02
+    assert c.ps == [1, 1, 1, 1, 2]
+    c = Ctx()
+    t = bench.cooled_state(c, 3, 0.02, 0.3, t_start=0.1)
+    assert abs(t - 0.16) < 1e-12 and c.ps == [2, 2, 2]
