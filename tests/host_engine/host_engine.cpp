@@ -4,15 +4,19 @@
 // the CPU so that tests/test_host_engine.py can check that sequence against the oracle
 // without a GPU.  The operations use the same per-chain functors the device kernels call
 // (ein_one, OpLq, OpTrunc, OpNorm, OpDot, Elem*); the GPU-only kernels (tensor-core and FFMA
-// GEMMs, shared-memory Householder, Cholesky) are not part of this build.
+// GEMMs, shared-memory Householder, Cholesky) are not part of this build (the Gram path's
+// Cholesky is a plain loop here).
 //
 // Usage: host_engine <in.bin> <out.bin>
-//   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw), L1, L2, D, chi, n, p;
+//   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw, 3 eval with the
+//        compression's right factors from Gram matrices), L1, L2, D, chi, n, p;
 //        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
 //        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
 //        mc:   uint8 S[n][N], int32 acc[n], int32 prop[n]
 //        draw: uint8 S[n][N], float64 log_q[n]  (direct sampling, pv_direct.cuh)
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -46,9 +50,29 @@ struct HostBE {
     int flag = 0;
     for (int s = 0; s < n; ++s) op(s, red.data(), &flag, work.data(), trunc_cap, order.data(), sig.data());
   }
-  void chol(OpChol<T>, int) {
-    std::fprintf(stderr, "host_engine: the Gram/Cholesky path is float32-only\n");
-    std::exit(3);
+  // Semidefinite Cholesky of each chain's m x m Gram matrix, lower factor Lf (pivots below
+  // m eps max(diag) zero their column), as the Gram path of the compression expects.
+  void chol(OpChol<T> op, int n) {
+    const int m = op.m;
+    const T eps = 2.220446049250313e-16;
+    std::vector<T> A((size_t)m * m);
+    for (int s = 0; s < n; ++s) {
+      const T* G = op.G + (long long)s * op.gs;
+      T dmax = 0;
+      for (int i = 0; i < m * m; ++i) A[i] = G[i];
+      for (int i = 0; i < m; ++i) dmax = std::max(dmax, A[(size_t)i * m + i]);
+      const T tol = (T)m * eps * dmax;
+      for (int j = 0; j < m; ++j) {
+        const T d = A[(size_t)j * m + j];
+        const T l = d > tol ? std::sqrt(d) : (T)0, inv = l > 0 ? (T)1 / l : (T)0;
+        for (int i = j; i < m; ++i) A[(size_t)i * m + j] = i == j ? l : A[(size_t)i * m + j] * inv;
+        for (int i = j + 1; i < m; ++i)   // trailing update of the lower triangle
+          for (int k = j + 1; k <= i; ++k) A[(size_t)i * m + k] -= A[(size_t)i * m + j] * A[(size_t)k * m + j];
+      }
+      T* L = op.Lf + (long long)s * op.ls;
+      for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) L[(size_t)r * m + c] = c <= r ? A[(size_t)r * m + c] : (T)0;
+    }
   }
   void norm(OpNorm<T> op, int n) {
     for (int s = 0; s < n; ++s) op(s, red.data());
@@ -198,10 +222,11 @@ int main(int argc, char** argv) {
   run.max_sweeps = 60;
   run.sweeps = &jsw;
   run.b.bind(real.data(), n, i8.data(), dbl.data(), L1, L2, Dn, chi);
+  run.gram_lq = mode == 3;
 
   FILE* fo = std::fopen(argv[2], "wb");
   if (!fo) return 2;
-  if (mode == 0) {
+  if (mode == 0 || mode == 3) {
     const long long No = ooff[N];
     std::vector<double> la(n), es(n), ea(n);
     std::vector<int8_t> sg(n);

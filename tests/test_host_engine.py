@@ -40,7 +40,7 @@ def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
         f.write(np.asarray(S, dtype=np.uint8).tobytes())
     subprocess.run([exe, fin, fout], check=True)
     raw = open(fout, "rb").read()
-    if mode == 0:
+    if mode in (0, 3):
         o = 0
         la = np.frombuffer(raw, np.float64, n, o); o += 8 * n
         sg = np.frombuffer(raw, np.int8, n, o); o += n
@@ -148,3 +148,23 @@ def test_host_engine_direct_draw_matches_oracle(engine, tmp_path, case):
         So, lqo = direct.draw_bmps(lat, th, u[k], chi, b_d, expo, down=down)
         assert np.array_equal(S[k], So), k
         assert lq[k] == pytest.approx(lqo, rel=1e-9, abs=1e-11)
+
+
+@pytest.mark.parametrize("case", [(3, 4, 2, 3, 0.5, 4), (4, 3, 3, 5, 0.2, 3), (8, 8, 4, 16, 0.0, 2)])
+def test_host_engine_gram_path_matches_oracle(engine, tmp_path, case):
+    # the compression's right factors from the Gram matrices W W^T (the path the TF32 mode
+    # takes on the GPU, here in float64 with a plain Cholesky): the truncation depends on the
+    # factor only through L L^T, so the results match the oracle's Householder factors
+    L1, L2, D, chi, J2, n = case
+    lat = Lattice(L1, L2, D, J1=1.0, J2=J2)
+    th = wl.random_theta(L1, L2, D, seed=L1 * 10 + L2, scale=0.3, diag_bias=1.0)
+    S = wl.random_configs(L1, L2, n, seed=D)
+    la, sg, es, ea, O = _run(engine, tmp_path, 3, lat, chi, th, S)
+    for k in range(n):
+        r = peps.eval_sample(lat, th, S[k], chi)
+        assert sg[k] == r['sign']
+        assert abs(la[k] - r['log_abs']) <= 1e-9
+        scale = max(1.0, abs(r['e_sys']), abs(r['e_anc']))
+        assert abs(es[k] - r['e_sys']) <= 1e-8 * scale
+        assert abs(ea[k] - r['e_anc']) <= 1e-8 * scale
+        assert np.max(np.abs(O[k] - r['O'])) <= 1e-7 * max(1.0, np.max(np.abs(r['O'])))
