@@ -16,6 +16,19 @@ def _built():
     build()
 
 
+def test_coupling_enters_the_gate():
+    lat = Lattice(2, 3, 4, J1=0.7)
+    th = binding.su_theta(2, 3, 4, 0.7, 0.03, 6)
+    tho = _oracle_theta(lat, 0.03, 6)
+    cfgs = [ed.config_of_index(k, lat.N) for k in range(4 ** lat.N)]
+    v = np.array([peps.amplitude_exact(lat, th, S) for S in cfgs])
+    w = np.array([peps.amplitude_exact(lat, tho, S) for S in cfgs])
+    assert np.allclose(_unit(v), _unit(w), atol=1e-12)
+    th1 = binding.su_theta(2, 3, 4, 1.0, 0.03, 6)
+    v1 = np.array([peps.amplitude_exact(lat, th1, S) for S in cfgs])
+    assert np.max(np.abs(_unit(v1) - _unit(v))) > 1e-4
+
+
 def _oracle_theta(lat, tau, n):
     st = su.SUState(lat)
     for _ in range(n):
