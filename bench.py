@@ -34,8 +34,9 @@ PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from one
-# ncu capture of every launch of that kernel in this bench's timed step (the timed region is
-# bracketed by cudaProfilerStart/Stop, so `ncu --profile-from-start off` captures exactly it),
+# ncu capture of the first launches of that kernel in this bench's timed step (the timed region
+# is bracketed by cudaProfilerStart/Stop, so `ncu --profile-from-start off` starts there), set
+# against the algorithmic bytes of the same launches (`--launch-bytes`),
 # stored with the SHA-256 of the kernel and launch-planner sources it was taken on (their code,
 # comments excluded).  Once that code changes the entry no longer applies and the bench
 # reports null.

@@ -1,8 +1,12 @@
 """Host-side logic of bench.py: the recorded DRAM traffic (it applies only to the code it was
 captured on and is scaled from the captured launches to the timed steps by algorithmic
-bytes), the roofline arithmetic, and the config object both arms report."""
+bytes), the roofline arithmetic, the config object both arms report, the cooling schedule,
+and the whole default run against a stand-in library (the JSON contract line)."""
+import json
 import os
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -93,3 +97,123 @@ def test_cooling_starts_from_the_warm_start_time():
     c = Ctx()
     t = bench.cooled_state(c, 3, 0.02, 0.3, t_start=0.1)
     assert abs(t - 0.16) < 1e-12 and c.ps == [2, 2, 2]
+
+
+def test_default_run_prints_the_contract_line(monkeypatch, capsys):
+    # bench.py's own arm end to end on the CPU with a stand-in library and stand-in CUDA
+    # events: the JSON line carries every key of the contract, with the recorded traffic
+    import sys as _sys
+    import numpy as np
+    import torch
+    bench = _bench()
+    from paper_2409_05285_gb300 import binding, build as build_mod
+
+    class Ev:
+        n = 0
+
+        def __init__(self, enable_timing=True):
+            Ev.n += 1
+            self.t = float(Ev.n)
+
+        def record(self, stream=None):
+            Ev.n += 1
+            self.t = float(Ev.n)
+
+        def elapsed_time(self, other):
+            return 100.0 * (other.t - self.t)
+
+        def synchronize(self):
+            pass
+
+    class Stream:
+        cuda_stream = 0
+
+    class Ctx:
+        def __init__(self, L1, L2, D, chi, n, **kw):
+            self.n, self.N = n, L1 * L2
+            self.Np, self.No = 4 * self.N * D ** 4, self.N * D ** 4
+            self.k = 0
+
+        def mc_sweep(self, n_sweeps=1, p=2):
+            self.k += 10
+
+        def step(self, **kw):
+            self.k += 30
+            return {"cg_iters": 5, "E_site": -0.1, "beta_obs": 0.1}
+
+        def autotune(self, reps=1):
+            return {"grid_pct": 100, "db_bytes": 12288, "ffma_g": 16, "kc_max": 32,
+                    "ms_before": 2.0, "ms_after": 1.0}
+
+        def profile(self, on, gemm_only=False):
+            pass
+
+        def launches(self):
+            return self.k
+
+        def counters(self):
+            return 1.0e9, 100.0 * self.n
+
+        def eval_chains(self):
+            self.k += 20
+
+        def sr_step(self, tau, eps, max_cg, cg_tol, p):
+            return {"cg_iters": 7, "E_site": -0.05, "beta_obs": 0.56}
+
+        def profile_read(self):
+            return {"kb_gemm_tc": (3288, 400.0, 3288 * 2.9584155e8, 0.0),
+                    "kb_gemm": (1221, 40.0, 1221 * 1.0e7, 0.0)}
+
+        def get_theta(self):
+            return np.zeros(self.Np)
+
+        def get_configs(self):
+            return np.zeros((self.n, self.N), dtype=np.uint8)
+
+        def set_theta(self, th):
+            pass
+
+        def set_configs(self, S):
+            pass
+
+        def close(self):
+            pass
+
+    class Clocks:
+        def __init__(self, index):
+            pass
+
+        def start(self):
+            pass
+
+        def stop(self):
+            return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda i: None)
+    monkeypatch.setattr(torch.cuda, "Stream", Stream)
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    monkeypatch.setattr(torch.cuda.profiler, "start", lambda: None)
+    monkeypatch.setattr(torch.cuda.profiler, "stop", lambda: None)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
+    monkeypatch.setattr(build_mod, "build", lambda *a, **k: None)
+    monkeypatch.setattr(binding, "Context", Ctx)
+    monkeypatch.setattr(bench, "Clocks", Clocks)
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 6794.1})
+    monkeypatch.setattr(_sys, "argv", ["bench.py", "--steps", "2", "--no-cpu-baseline",
+                                       "--no-fp64-check"])
+    bench.main()
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "e2e", "gpu_launches", "clocks"):
+        assert key in out, key
+    assert out["n_gpus"] == 1 and out["steps"] == 2 and out["warmup"] == 3
+    assert out["config"]["workload"].startswith("8x8 OBC Heisenberg") and out["unit"] == "samples/s"
+    assert out["value"] == pytest.approx(8192 / (out["ms_per_step"] / 1e3))
+    roof = out["roofline"]
+    assert roof["kernel"] == "kb_gemm_tc" and roof["peak"] == 6794.1
+    if bench.recorded_traffic("heis8", "tf32", 8192, "kb_gemm_tc") is not None:
+        assert roof["traffic"] == pytest.approx(0.8903172730497985 * roof["bytes_per_launch"], rel=1e-9)
+    assert set(out["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
+    assert out["gpu_launches"] > 0
