@@ -24,6 +24,9 @@ Modules:
   sr           weights, Eq. 6/7/10 reductions, CG solve, parameter update (Eq. 5).
   observables  energy (Eq. 11), specific heat, susceptibility (Eq. 13).
   ed           exact diagonalisation and full-state imaginary-time evolution (Eqs. 1-3).
+  hubbard_ed   exact diagonalisation of the Fermi-Hubbard model (Eq. 14): energy, double
+               occupancy and next-nearest-neighbour spin correlation (checks for a
+               fermionic PEPS; no PEPS of it is built yet).
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a
 closed form, an invariant, brute force or exact diagonalisation (see tests/test_oracle_*.py).
