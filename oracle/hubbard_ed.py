@@ -145,3 +145,39 @@ def thermal(nrow, ncol, t, U, mu, betas):
             Fn += (w * fk).sum()
         out.append((E / Z / N, Dn / Z / N, Fn / Z / Mp))
     return np.array(out)
+
+
+# ----------------------------------------------------------- the doubled (vectorised) state
+#
+# Eqs. 2-3 for fermions: rho(t) = e^{-t calH}|I> with calH = H x I + I x H^T is the Fock-basis
+# matrix e^{-2tH} (up to normalisation), its entries rho(s, s') the amplitudes the method
+# samples; the local energy of configuration S = (s, s') is
+#     E_loc(S) = [(H rho)(s, s') + (rho H)(s, s')] / rho(s, s')  (E_sys + E_anc, Eq. 9)
+# and Eq. 11 gives E = <E_loc>_{|rho|^2} / 2 at beta_obs = 4t.
+
+def full_hamiltonian(nrow, ncol, t, U, mu):
+    """Dense H on the whole Fock space (4^N states), Fock state = basis index."""
+    N = nrow * ncol
+    H = np.zeros((4 ** N, 4 ** N))
+    for n_up in range(N + 1):
+        for n_dn in range(N + 1):
+            Hs, basis = sector_hamiltonian(nrow, ncol, t, U, mu, n_up, n_dn)
+            idx = np.array(basis)
+            H[np.ix_(idx, idx)] = Hs
+    return H
+
+
+def evolved_rho(H, t):
+    """e^{-2tH} (shifted by the ground energy), the amplitudes of e^{-t calH}|I>."""
+    ev, V = np.linalg.eigh(H)
+    return (V * np.exp(-2.0 * t * (ev - ev.min()))) @ V.T
+
+
+def local_energies(H, rho):
+    """E_sys(s, s') = (H rho)(s, s') / rho(s, s'), E_anc = (rho H)(s, s') / rho(s, s'), where
+    rho(s, s') != 0 (NaN elsewhere)."""
+    with np.errstate(divide="ignore", invalid="ignore"):
+        nz = rho != 0
+        es = np.where(nz, (H @ rho) / np.where(nz, rho, 1.0), np.nan)
+        ea = np.where(nz, (rho @ H) / np.where(nz, rho, 1.0), np.nan)
+    return es, ea

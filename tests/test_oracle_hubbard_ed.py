@@ -58,3 +58,21 @@ def test_large_U_plaquette_spin_correlation():
     E, D, F = h.thermal(2, 2, 1.0, U, U / 2, [400.0])[0]
     assert F == pytest.approx(0.25, abs=0.02)
     assert D < 0.01
+
+
+def test_sampled_energy_of_the_evolved_state_is_thermal():
+    # Eq. 11 for fermions: <E_sys + E_anc>_{|rho|^2} / 2 of e^{-t calH}|I> is the thermal
+    # energy at beta_obs = 4t, and at t = 0 the state is the identity with E_loc = 2 H_ss
+    nrow, ncol, t_hop, U, mu = 2, 2, 1.0, 4.0, 1.5
+    H = h.full_hamiltonian(nrow, ncol, t_hop, U, mu)
+    rho0 = h.evolved_rho(H, 0.0)
+    assert np.allclose(rho0, np.eye(H.shape[0]), atol=1e-12)
+    es0, ea0 = h.local_energies(H, rho0)
+    assert np.allclose(np.diag(es0) + np.diag(ea0), 2 * np.diag(H), atol=1e-12)
+    for t in (0.05, 0.3):
+        rho = h.evolved_rho(H, t)
+        es, ea = h.local_energies(H, rho)
+        w = rho ** 2
+        ok = rho != 0
+        E = np.sum(w[ok] * (es[ok] + ea[ok])) / (2 * np.sum(w)) / (nrow * ncol)
+        assert E == pytest.approx(h.thermal(nrow, ncol, t_hop, U, mu, [4 * t])[0][0], abs=1e-10)
