@@ -76,3 +76,17 @@ def test_tuning_and_profile_calls_reject_a_null_context():
     n = ctypes.c_int()
     assert lib.peps_profile_launch_bytes(None, b"kb_gemm_tc", buf, 4, ctypes.byref(n)) == \
         binding.PEPS_EINVAL
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header compiles as C99 (no C++ or torch types)
+    import shutil
+    import subprocess
+    import pytest
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror",
+                            os.path.join(ROOT, "include", fn)], check=True)
