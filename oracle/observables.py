@@ -47,3 +47,44 @@ def cv_from_energy_curve(betas, E_site, smoothing=0.0, k=3):
                            s=smoothing)
     dE = spl.derivative()
     return lambda b: -np.asarray(b, dtype=np.float64) ** 2 * dE(b)
+
+
+def cv_from_energy_gpr(betas, E_site, noise=1e-8, length=None):
+    """Specific heat per site from E/N against beta by Gaussian-process regression (the
+    scheme named for the Hubbard data, Sec. III.B): a GP with the squared-exponential kernel
+    k(b, b') = s^2 exp(-(b - b')^2 / (2 l^2)) around the data mean, noise variance `noise`
+    (the variance of the E/N errors), s^2 the data variance, and the length scale l given or
+    chosen on a grid by the largest log marginal likelihood; the posterior mean's derivative
+    is analytic, and C/N = -beta^2 dE/dbeta.  Returns a function of beta."""
+    b = np.asarray(betas, dtype=np.float64)
+    y = np.asarray(E_site, dtype=np.float64)
+    m = y.mean()
+    s2 = max(float(np.var(y)), 1e-12)
+    r = y - m
+
+    def fit(l):
+        K = s2 * np.exp(-(b[:, None] - b[None, :]) ** 2 / (2 * l * l)) + noise * np.eye(len(b))
+        L = np.linalg.cholesky(K)
+        a = np.linalg.solve(L.T, np.linalg.solve(L, r))
+        return a, -0.5 * r @ a - np.sum(np.log(np.diag(L)))
+
+    if length is None:
+        span = b.max() - b.min()
+        best = None
+        for l in span * np.logspace(-2, 0, 25):
+            try:
+                a, lml = fit(l)
+            except np.linalg.LinAlgError:
+                continue
+            if best is None or lml > best[2]:
+                best = (l, a, lml)
+        length, alpha = best[0], best[1]
+    else:
+        alpha = fit(length)[0]
+
+    def cv(q):
+        q = np.atleast_1d(np.asarray(q, dtype=np.float64))
+        d = q[:, None] - b[None, :]
+        dk = -d / length ** 2 * s2 * np.exp(-d ** 2 / (2 * length ** 2))
+        return -q ** 2 * (dk @ alpha)
+    return cv

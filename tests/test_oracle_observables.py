@@ -66,3 +66,22 @@ def test_spline_cv_two_level_closed_form_and_noise():
     noisy = -np.tanh(betas) + 1e-4 * rng.standard_normal(betas.size)
     cvn = observables.cv_from_energy_curve(betas, noisy, smoothing=betas.size * 1e-8)
     assert np.allclose(cvn(probe), probe ** 2 / np.cosh(probe) ** 2, atol=1e-2)
+
+
+def test_gpr_cv_matches_fluctuation_formula_and_closed_form():
+    # Sec. III.B's Gaussian-process form of C = -beta^2 dE/dbeta: on the ED energy curve it
+    # reproduces the fluctuation formula; on the two-level curve the closed form, also with
+    # noise of 1e-4 on E (noise variance given as 1e-8)
+    lat = Lattice(2, 3, 1, J1=1.0)
+    spec = ed.spectrum(lat)
+    betas = np.linspace(0.05, 4.0, 60)
+    cv = observables.cv_from_energy_gpr(betas, ed.thermal(spec, lat.N, betas)[:, 0], noise=1e-12)
+    probe = np.linspace(0.3, 3.7, 15)
+    assert np.allclose(cv(probe), ed.thermal(spec, lat.N, probe)[:, 1], atol=1e-4)
+    b2 = np.linspace(0.0, 3.0, 121)
+    pr = np.linspace(0.2, 2.8, 14)
+    exact = pr ** 2 / np.cosh(pr) ** 2
+    assert np.allclose(observables.cv_from_energy_gpr(b2, -np.tanh(b2), noise=1e-12)(pr), exact,
+                       atol=1e-4)
+    noisy = -np.tanh(b2) + 1e-4 * np.random.default_rng(3).standard_normal(b2.size)
+    assert np.allclose(observables.cv_from_energy_gpr(b2, noisy, noise=1e-8)(pr), exact, atol=3e-3)
