@@ -60,6 +60,8 @@ CASES = [  # (L1, L2, D, chi, J2, n): exact chi (first two), truncated chi, NNN 
     (3, 3, 2, 4, 0.0, 5),
     (3, 4, 2, 3, 0.5, 4),
     (4, 3, 3, 5, 0.2, 3),
+    (5, 4, 3, 6, 0.3, 2),
+    (4, 6, 2, 3, 0.0, 2),
 ]
 
 
@@ -80,7 +82,7 @@ def test_host_engine_eval_matches_oracle(engine, tmp_path, case):
         assert np.max(np.abs(O[k] - r['O'])) <= 1e-9 * max(1.0, np.max(np.abs(r['O'])))
 
 
-@pytest.mark.parametrize("shape", [(3, 3, 2, 4, 0.0), (3, 4, 2, 3, 0.5)])
+@pytest.mark.parametrize("shape", [(3, 3, 2, 4, 0.0), (3, 4, 2, 3, 0.5), (4, 3, 3, 5, 0.2)])
 @pytest.mark.parametrize("p", [2, 1])
 def test_host_engine_sweep_matches_oracle(engine, tmp_path, p, shape):
     # one Metropolis sweep per chain with the same Philox stream: the same accepted moves
