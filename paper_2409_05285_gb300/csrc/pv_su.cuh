@@ -192,6 +192,7 @@ class SimpleUpdate {
       return k;
     };
     const int na = rank(sA, oA), nb = rank(sB, oB);
+    if (na == 0 || nb == 0) return;   // a vanishing side: the gate leaves the product zero
     // core: T[(S_A0, a)][(S_B0, b)] = sum_k R_A[a][(S_A0, k)] R_B[b][(S_B0, k)], then the gate
     const int m = 4 * na, n = 4 * nb;
     std::vector<double> Tc((size_t)m * n, 0.0), C((size_t)m * n, 0.0);
