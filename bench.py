@@ -46,10 +46,10 @@ NCU_TRAFFIC = {
         "dram_bytes": 66987750144,      # DRAM read + write of the first 200 launches of the step
         "alg_bytes": 75240312832,       # algorithmic bytes of the same 200 launches
         "sources_sha256": "e8d43633e2acafda7bccf83a7be4e273ee7509167182314757cace304cc7978a",
-        "source": "ncu --profile-from-start off -k regex:kb_gemm_tc -c 200 (dram__bytes_read.sum "
-                  "+ dram__bytes_write.sum, cold cache), first 200 launches of the timed step with "
-                  "the autotuned shapes 100,12288,16,32, scaled by algorithmic bytes; "
-                  "profiles/kb_gemm_tc_heis8_tf32.md",
+        "source": "ncu --profile-from-start off --clock-control none --metrics "
+                  "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                  "-k regex:kb_gemm_tc -c 200 (cold cache): the first 200 launches of the timed "
+                  "step with the autotuned shapes 100,12288,16,32, scaled by algorithmic bytes",
     },
 }
 TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_batch.cuh")

@@ -48,7 +48,9 @@ extern "C" {
 #define PEPS_ENOTFINITE (-5) /* non-finite amplitude, energy or CG scalar */
 #define PEPS_ECORRUPT (-6)   /* checkpoint unreadable, of another problem, or failing its checksum */
 #define PEPS_EIO (-7)        /* checkpoint file could not be written */
-#define PEPS_ETIMEOUT (-8)   /* a bounded device wait ran out; the call's results are invalid */
+#define PEPS_ETIMEOUT (-8)   /* a bounded device wait ran out; the call's results are invalid.
+                               When the message says that an MMA may have been in flight,
+                               every later result of the context is undefined: free it */
 
 /* Arithmetic of the per-sample contraction (environment, amplitude, E_loc, O).  The
  * log-amplitude accumulation, the SR reductions and CG, and the observables are float64
@@ -124,7 +126,9 @@ int peps_mc_sweep(peps_ctx* ctx, int n_sweeps, int p);
  * sum) and, when O is non-null, the O rows (Eq. 8).  S == NULL evaluates the context's
  * own chains (nb must equal n_chains) and keeps the results for peps_sr_step /
  * peps_observables.  on_device != 0: S and every output pointer are device pointers;
- * otherwise host pointers (copies are made on the context stream).  Null output
+ * otherwise host pointers (copies are made on the context stream).  PEPS_EINVAL, before
+ * any evaluation, when a configuration entry exceeds 3 (device batches are checked by a
+ * kernel).  Null output
  * pointers are skipped.  O has the element type of the precision (double for
  * PEPS_FP64, float otherwise). */
 int peps_eval_batch(peps_ctx* ctx, const uint8_t* S, int nb, int on_device, double* log_abs,
@@ -309,6 +313,10 @@ void peps_srv_free(peps_server* srv);
  * running inside a host framework that owns the whole device memory pool, a plug-in that is
  * called while a CUDA graph is being captured, or a process whose memory budget is fixed
  * at start-up.  The paper has no counterpart; this is a library convenience.
+ *
+ * Configuration entries must lie in 0..3.  A sample holding an entry outside that range is
+ * not evaluated (the kernel checks before it reads any parameter): its log_abs, e_sys and
+ * e_anc are NaN, its sign 0, and its O row is left as it was.
  *
  * Same results as peps_eval_batch on device pointers (the same kernel runs), for the
  * problem in *params (n_chains, seed, init_noise, n_blocks and block_mode are ignored; the

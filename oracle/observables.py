@@ -11,6 +11,14 @@ state is (rho rho^T + rho^T rho) / (2 Tr rho rho^T); with w_i the sample weights
   C/N   = beta_obs^2 (<H^2> - <H>^2) / N
   <Mz^2>= 1/2 sum_i w_i (M(s_i)^2 + M(s'_i)^2),  chi = beta_obs <Mz^2> / N, <Mz>^2 := 0 (Eq. 13)
 
+Standard error of <H> (the paper states none; this is the reading used): with
+h_i = (E_sys,i + E_anc,i)/2 the per-sample energy of Eq. 11, the estimate <H> = sum_i w_i h_i
+is a self-normalised weighted mean, and for independent samples its first-order (delta
+method) variance is sum_i w_i^2 (h_i - <H>)^2.  For p = 2 (w_i = 1/n) that is the plain
+sigma/sqrt(n) with the population variance; for p = 1 (w_i = |rho_i| / sum |rho|, Eq. A1)
+it is the standard error of a ratio estimate.  Correlations between successive samples of
+a chain are not included: every chain contributes one sample per step.
+
 The paper's own C_v (Sec. III.A) is the derivative of a B-spline fitted to E(beta):
 cv_from_energy_curve, a post-processing cross-check of the fluctuation estimate above.
 """
@@ -31,8 +39,20 @@ def observables(lat, t, w, e_sys, e_anc, S_batch):
     M2 = 0.5 * float(w @ (Ms * Ms + Ma * Ma))
     N = lat.N
     diag = np.all(spin_sys(S_batch) == spin_anc(S_batch), axis=1)
-    return dict(t=t, beta_obs=beta_obs, E_site=H1 / N, C_site=beta_obs ** 2 * (H2 - H1 * H1) / N,
+    E_err = standard_error(w, 0.5 * (es + ea))
+    return dict(t=t, beta_obs=beta_obs, E_site=H1 / N, E_err=E_err / N,
+                C_site=beta_obs ** 2 * (H2 - H1 * H1) / N,
                 chi=beta_obs * M2 / N, Mz2=M2, diag_frac=float(np.mean(diag)))
+
+
+def standard_error(w, h):
+    """Standard error of the weighted mean sum_i w_i h_i (weights summing to one) from
+    independent samples: sqrt(sum_i w_i^2 (h_i - mean)^2), the first-order variance of a
+    self-normalised estimate (reading stated in the module docstring)."""
+    w = np.asarray(w, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    mean = float(w @ h)
+    return float(np.sqrt(np.sum(w * w * (h - mean) ** 2)))
 
 
 def cv_from_energy_curve(betas, E_site, smoothing=0.0, k=3):
@@ -47,44 +67,3 @@ def cv_from_energy_curve(betas, E_site, smoothing=0.0, k=3):
                            s=smoothing)
     dE = spl.derivative()
     return lambda b: -np.asarray(b, dtype=np.float64) ** 2 * dE(b)
-
-
-def cv_from_energy_gpr(betas, E_site, noise=1e-8, length=None):
-    """Specific heat per site from E/N against beta by Gaussian-process regression (the
-    scheme named for the Hubbard data, Sec. III.B): a GP with the squared-exponential kernel
-    k(b, b') = s^2 exp(-(b - b')^2 / (2 l^2)) around the data mean, noise variance `noise`
-    (the variance of the E/N errors), s^2 the data variance, and the length scale l given or
-    chosen on a grid by the largest log marginal likelihood; the posterior mean's derivative
-    is analytic, and C/N = -beta^2 dE/dbeta.  Returns a function of beta."""
-    b = np.asarray(betas, dtype=np.float64)
-    y = np.asarray(E_site, dtype=np.float64)
-    m = y.mean()
-    s2 = max(float(np.var(y)), 1e-12)
-    r = y - m
-
-    def fit(l):
-        K = s2 * np.exp(-(b[:, None] - b[None, :]) ** 2 / (2 * l * l)) + noise * np.eye(len(b))
-        L = np.linalg.cholesky(K)
-        a = np.linalg.solve(L.T, np.linalg.solve(L, r))
-        return a, -0.5 * r @ a - np.sum(np.log(np.diag(L)))
-
-    if length is None:
-        span = b.max() - b.min()
-        best = None
-        for l in span * np.logspace(-2, 0, 25):
-            try:
-                a, lml = fit(l)
-            except np.linalg.LinAlgError:
-                continue
-            if best is None or lml > best[2]:
-                best = (l, a, lml)
-        length, alpha = best[0], best[1]
-    else:
-        alpha = fit(length)[0]
-
-    def cv(q):
-        q = np.atleast_1d(np.asarray(q, dtype=np.float64))
-        d = q[:, None] - b[None, :]
-        dk = -d / length ** 2 * s2 * np.exp(-d ** 2 / (2 * length ** 2))
-        return -q ** 2 * (dk @ alpha)
-    return cv

@@ -147,7 +147,7 @@ __global__ void k_colsum1(int n, int N, long long No, const OT* __restrict__ O,
   }
 }
 
-// Float rows: products and the per-chunk sums in float32, chunk totals in float64.
+// Float rows: each float32 entry is widened and multiplied and summed in float64.
 template <bool TWO>
 __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restrict__ O,
                               const uint8_t* __restrict__ S, const int* __restrict__ o2site,
@@ -165,12 +165,12 @@ __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restric
   int j = o2site[o];
   long long k = o - ooff[j];
   long long sz = (ooff[j + 1] - ooff[j]);
-  float a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
+  double a[4] = {0, 0, 0, 0}, b[4] = {0, 0, 0, 0};
   for (int i = i0; i < i1; ++i) {
-    float v = O[(long long)i * No + o];
-    int s = S[(long long)i * N + j];
-    float x = (float)c1[i] * v;
-    float y = TWO ? (float)(c1[i] * (c2[i] - Ebar_shift)) * v : 0.f;
+    const double v = (double)O[(long long)i * No + o];
+    const int s = S[(long long)i * N + j];
+    const double x = c1[i] * v;
+    const double y = TWO ? c1[i] * (c2[i] - Ebar_shift) * v : 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (s == q) {
@@ -182,17 +182,17 @@ __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restric
   long long t = toff[j] + k;
   double* p1 = part1 + (long long)ch * Np;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) p1[t + q * sz] = (double)a[q];
+  for (int q = 0; q < 4; ++q) p1[t + q * sz] = a[q];
   if (TWO) {
     double* p2 = part2 + (long long)ch * Np;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) p2[t + q * sz] = (double)b[q];
+    for (int q = 0; q < 4; ++q) p2[t + q * sz] = b[q];
   }
 }
 
 // Float rows, 16-byte vectors: every site slice holds a multiple of four entries, so each
-// thread takes four consecutive columns of one site; the chunk's coefficients are staged in
-// shared memory and four rows are loaded before they are accumulated.
+// thread takes four consecutive columns of one site; four rows are loaded before they are
+// accumulated; products and sums in float64.
 template <bool TWO>
 __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
@@ -201,24 +201,24 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     const double* __restrict__ c2, const double* __restrict__ shift, double* __restrict__ part1,
     double* __restrict__ part2, long long Np, const int* done) {
   if (done && *done) return;
-  __shared__ float cx[OTV_CHUNK], cy[OTV_CHUNK];
+  __shared__ double cx[OTV_CHUNK], cy[OTV_CHUNK];
   const int ch = blockIdx.y;
   const int i0 = ch * OTV_CHUNK, i1 = min(n, i0 + OTV_CHUNK);
   const double Ebar_shift = TWO ? *shift : 0.0;
   for (int i = threadIdx.x; i < i1 - i0; i += blockDim.x) {
-    cx[i] = (float)c1[i0 + i];
-    cy[i] = TWO ? (float)(c1[i0 + i] * (c2[i0 + i] - Ebar_shift)) : 0.f;
+    cx[i] = c1[i0 + i];
+    cy[i] = TWO ? c1[i0 + i] * (c2[i0 + i] - Ebar_shift) : 0.0;
   }
   __syncthreads();
   const long long o = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
   if (o >= No) return;
   const int j = o2site[o];
   const long long k = o - ooff[j], sz = ooff[j + 1] - ooff[j];
-  float a[4][4], b[4][4];
+  double a[4][4], b[4][4];
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) a[q][c] = b[q][c] = 0.f;
+    for (int c = 0; c < 4; ++c) a[q][c] = b[q][c] = 0.0;
   int i = i0;
   for (; i + 4 <= i1; i += 4) {
     float4 v[4];
@@ -230,24 +230,26 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const float x = cx[i + u - i0], y = cy[i + u - i0];
+      const double x = cx[i + u - i0], y = cy[i + u - i0];
+      const double v0 = v[u].x, v1 = v[u].y, v2 = v[u].z, v3 = v[u].w;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {   // branch-free: the other three states add zero
-        const float xq = st[u] == q ? x : 0.f, yq = st[u] == q ? y : 0.f;
-        a[q][0] += xq * v[u].x; a[q][1] += xq * v[u].y; a[q][2] += xq * v[u].z; a[q][3] += xq * v[u].w;
-        if (TWO) { b[q][0] += yq * v[u].x; b[q][1] += yq * v[u].y; b[q][2] += yq * v[u].z; b[q][3] += yq * v[u].w; }
+        const double xq = st[u] == q ? x : 0.0, yq = st[u] == q ? y : 0.0;
+        a[q][0] += xq * v0; a[q][1] += xq * v1; a[q][2] += xq * v2; a[q][3] += xq * v3;
+        if (TWO) { b[q][0] += yq * v0; b[q][1] += yq * v1; b[q][2] += yq * v2; b[q][3] += yq * v3; }
       }
     }
   }
   for (; i < i1; ++i) {
     const float4 v = __ldg((const float4*)(O + (long long)i * No + o));
     const int sq = S[(long long)i * N + j];
-    const float x = cx[i - i0], y = cy[i - i0];
+    const double x = cx[i - i0], y = cy[i - i0];
+    const double v0 = v.x, v1 = v.y, v2 = v.z, v3 = v.w;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const float xq = sq == q ? x : 0.f, yq = sq == q ? y : 0.f;
-      a[q][0] += xq * v.x; a[q][1] += xq * v.y; a[q][2] += xq * v.z; a[q][3] += xq * v.w;
-      if (TWO) { b[q][0] += yq * v.x; b[q][1] += yq * v.y; b[q][2] += yq * v.z; b[q][3] += yq * v.w; }
+      const double xq = sq == q ? x : 0.0, yq = sq == q ? y : 0.0;
+      a[q][0] += xq * v0; a[q][1] += xq * v1; a[q][2] += xq * v2; a[q][3] += xq * v3;
+      if (TWO) { b[q][0] += yq * v0; b[q][1] += yq * v1; b[q][2] += yq * v2; b[q][3] += yq * v3; }
     }
   }
   const long long t = toff[j] + k;
@@ -255,13 +257,13 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) p1[t + q * sz + c] = (double)a[q][c];
+    for (int c = 0; c < 4; ++c) p1[t + q * sz + c] = a[q][c];
   if (TWO) {
     double* p2 = part2 + (long long)ch * Np;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) p2[t + q * sz + c] = (double)b[q][c];
+      for (int c = 0; c < 4; ++c) p2[t + q * sz + c] = b[q][c];
   }
 }
 
@@ -310,7 +312,7 @@ __device__ __forceinline__ double blk_sum_parts(const double* part, int n, doubl
 
 // CG set-up: x = 0, r = p = g, rr = g.g, gnorm, done flag.
 __global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __restrict__ x,
-                          double* __restrict__ r, double* __restrict__ p, float* __restrict__ pf,
+                          double* __restrict__ r, double* __restrict__ p,
                           int ndp, const double* __restrict__ dpart, SRScalars* sc, int maxit,
                           double tol, double eps) {
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
@@ -318,7 +320,6 @@ __global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __
     x[t] = 0;
     r[t] = g[t];
     p[t] = g[t];
-    if (pf) pf[t] = (float)g[t];
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     double rr = sum_parts(dpart, ndp);
@@ -330,114 +331,6 @@ __global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __
     sc->eps = eps;
     sc->done = (maxit <= 0 || !(sqrt(rr) > tol * sqrt(rr))) ? 1 : 0;
   }
-}
-
-// y_i = w_i [ (O_i . p) - obar . p ], one warp per sample; per-block partials of sum y.
-template <typename OT>
-__global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
-                     const uint8_t* __restrict__ S, const long long* __restrict__ toff,
-                     const long long* __restrict__ ooff, const double* __restrict__ p,
-                     const float* __restrict__ pf, const double* __restrict__ w,
-                     double* __restrict__ y, double* __restrict__ ypart, int ndp,
-                     const double* __restrict__ dpart, const SRScalars* sc) {
-  __shared__ double red[32];
-  if (sc->done) return;
-  double obp = blk_sum_parts(dpart, ndp, red);
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  double yi = 0;
-  if (i < n) {
-    const OT* row = O + (long long)i * No;
-    double acc = 0;
-    for (int j = 0; j < N; ++j) {
-      int s = S[(long long)i * N + j];
-      long long o0 = ooff[j], sz = ooff[j + 1] - o0;
-      long long t0 = toff[j] + (long long)s * sz;
-      if (sizeof(OT) == 4) {
-        float a = 0;
-        for (long long k = lane; k < sz; k += 32) a += (float)row[o0 + k] * pf[t0 + k];
-        acc += (double)a;
-      } else {
-        for (long long k = lane; k < sz; k += 32) acc += (double)row[o0 + k] * p[t0 + k];
-      }
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    yi = w[i] * (acc - obp);
-    if (lane == 0) y[i] = yi;
-  }
-  double contrib = (lane == 0) ? yi : 0.0;
-  double s = blk_sum(contrib, red);
-  if (threadIdx.x == 0) ypart[blockIdx.x] = s;
-}
-
-// Float rows, 16-byte vectors (site slices of multiples of four entries): y_i = w_i (O_i.p - obar.p).
-__global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
-    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
-    const long long* __restrict__ toff, const long long* __restrict__ ooff,
-    const float* __restrict__ pf, const double* __restrict__ w, double* __restrict__ y,
-    double* __restrict__ ypart, int ndp, const double* __restrict__ dpart, const SRScalars* sc) {
-  __shared__ double red[32];
-  if (sc->done) return;
-  double obp = blk_sum_parts(dpart, ndp, red);
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int i = blockIdx.x * (blockDim.x >> 5) + warp;
-  double yi = 0;
-  if (i < n) {
-    const float4* row = (const float4*)(O + (long long)i * No);
-    double acc = 0;
-    for (int j = 0; j < N; ++j) {
-      const int s = S[(long long)i * N + j];
-      const long long o0 = ooff[j] >> 2, sz = (ooff[j + 1] - ooff[j]) >> 2;
-      const float4* pv = (const float4*)(pf + toff[j] + (long long)s * (sz << 2));
-      float a0 = 0.f, a1 = 0.f;
-      long long kk = lane;
-      for (; kk + 32 < sz; kk += 64) {
-        const float4 r0 = __ldg(row + o0 + kk), q0 = __ldg(pv + kk);
-        const float4 r1 = __ldg(row + o0 + kk + 32), q1 = __ldg(pv + kk + 32);
-        a0 += r0.x * q0.x + r0.y * q0.y + r0.z * q0.z + r0.w * q0.w;
-        a1 += r1.x * q1.x + r1.y * q1.y + r1.z * q1.z + r1.w * q1.w;
-      }
-      if (kk < sz) {
-        const float4 r0 = __ldg(row + o0 + kk), q0 = __ldg(pv + kk);
-        a0 += r0.x * q0.x + r0.y * q0.y + r0.z * q0.z + r0.w * q0.w;
-      }
-      acc += (double)(a0 + a1);
-    }
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    yi = w[i] * (acc - obp);
-    if (lane == 0) y[i] = yi;
-  }
-  double contrib = (lane == 0) ? yi : 0.0;
-  double sm = blk_sum(contrib, red);
-  if (threadIdx.x == 0) ypart[blockIdx.x] = sm;
-}
-
-// q = sum_ch part - (sum y) obar + eps p ; block partials of p.q.
-__global__ void k_otv2(long long Np, int nch, const double* __restrict__ part,
-                       const double* __restrict__ obar, const double* __restrict__ p,
-                       double* __restrict__ q, int nyp, const double* __restrict__ ypart,
-                       double* __restrict__ pqpart, SRScalars* sc) {
-  __shared__ double red[32];
-  if (sc->done) return;
-  double sumy = blk_sum_parts(ypart, nyp, red);
-  double eps = sc->eps;
-  double s = 0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
-       t += (long long)gridDim.x * blockDim.x) {
-    // eight chunk partials in flight at a time (fixed order: the sum is reproducible)
-    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    int c = 0;
-    for (; c + 8 <= nch; c += 8)
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc[u] += part[(long long)(c + u) * Np + t];
-    for (; c < nch; ++c) acc[0] += part[(long long)c * Np + t];
-    double a = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
-    double qt = a - sumy * obar[t] + eps * p[t];
-    q[t] = qt;
-    s += p[t] * qt;
-  }
-  s = blk_sum(s, red);
-  if (threadIdx.x == 0) pqpart[blockIdx.x] = s;
 }
 
 // alpha = rr / p.q ; x += alpha p ; r -= alpha q ; block partials of r.r
@@ -463,7 +356,7 @@ __global__ void k_cg_a(long long Np, double* __restrict__ x, double* __restrict_
 // beta = rr_new / rr ; p = r + beta p ; block partials of obar.p for the next pass.
 // The last block to finish updates the scalars (iteration count, convergence flag).
 __global__ void k_cg_b(long long Np, const double* __restrict__ r, double* __restrict__ p,
-                       float* __restrict__ pf, const double* __restrict__ obar, int nrr,
+                       const double* __restrict__ obar, int nrr,
                        const double* __restrict__ rrpart, double* __restrict__ obpart,
                        SRScalars* sc) {
   __shared__ double red[32];
@@ -475,7 +368,6 @@ __global__ void k_cg_b(long long Np, const double* __restrict__ r, double* __res
        t += (long long)gridDim.x * blockDim.x) {
     double pt = r[t] + beta * p[t];
     p[t] = pt;
-    if (pf) pf[t] = (float)pt;
     s += obar[t] * pt;
   }
   s = blk_sum(s, red);
@@ -489,6 +381,215 @@ __global__ void k_cg_scalars(int nrr, const double* __restrict__ rrpart, SRScala
   sc->rr = rr_new;
   sc->iters += 1;
   if (sc->iters >= sc->maxit || !(sqrt(rr_new) > sc->tol * sc->gnorm)) sc->done = 1;
+}
+
+// ---------------------------------------------------------------- fused CG product
+//
+// q = (G + eps) p = sum_i y_i O_i - (sum_i y_i) obar + eps p with y_i = w_i (O_i.p - obar.p)
+// (Eq. 10, two passes over the O rows), formed with one read of O from DRAM.  Every block
+// owns a fixed slice of the compressed columns (and the four q entries of each) for the
+// whole product.  The samples are taken in chunks of R = gridDim.x * rpb rows, small enough
+// to stay in L2: in phase A every block forms the complete dot products of its own rpb rows
+// of the chunk; after a grid barrier every block, in phase B, adds y_i O_i[o] over the
+// chunk's rows for its own columns o, rows that the chunk's phase A has just brought into
+// L2.  Products and sums are float64 (float32 entries are widened); every sum has a fixed
+// order, so the result does not depend on timing.  The kernel must run with every block
+// resident (cooperative launch); its barrier waits are bounded (GV_WAIT_NS), and a wait that
+// runs out raises *err and makes every block return.
+
+constexpr int GV_THREADS = 1024;
+constexpr unsigned long long GV_WAIT_NS = 1000000000ull;
+
+__device__ __forceinline__ unsigned long long gv_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid barrier over the resident blocks: bar[0] counts arrivals, bar[1] is the generation
+// (both zero at launch).  Returns false when a wait ran out here or in another block.
+__device__ __forceinline__ bool gv_barrier(unsigned* bar, unsigned& gen, int* err, int* ok_sh) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned g = gen;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicExch(bar + 1, g + 1);
+    } else {
+      volatile unsigned* vg = bar + 1;
+      volatile int* ve = err;
+      const unsigned long long t0 = gv_now();
+      while (*vg == g) {
+        if (*ve) { ok = 0; break; }
+        if (gv_now() - t0 > GV_WAIT_NS) {
+          atomicOr(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen = g + 1;
+    *ok_sh = ok;
+  }
+  __syncthreads();
+  return *ok_sh != 0;
+}
+
+// Entry of p / q (full parameter space) of compressed column o for state s.
+__device__ __forceinline__ long long gv_tidx(long long o, int s, const int* __restrict__ o2site,
+                                             const long long* __restrict__ toff,
+                                             const long long* __restrict__ ooff, int& j) {
+  j = o2site[o];
+  const long long o0 = ooff[j];
+  return toff[j] + (long long)s * (ooff[j + 1] - o0) + (o - o0);
+}
+
+template <typename OT, bool VEC>
+__global__ void __launch_bounds__(GV_THREADS) k_gv(
+    int n, int N, long long No, const OT* __restrict__ O, const uint8_t* __restrict__ S,
+    const int* __restrict__ o2site, const long long* __restrict__ toff,
+    const long long* __restrict__ ooff, const double* __restrict__ p,
+    const double* __restrict__ obar, const double* __restrict__ w, int ndp,
+    const double* __restrict__ dpart, double* __restrict__ y, double* __restrict__ q,
+    double* __restrict__ pqpart, int rpb, unsigned* bar, int* err, const SRScalars* sc) {
+  __shared__ double red[32];
+  __shared__ int ok_sh;
+  extern __shared__ double gacc[];   // phase B: [4][blockDim] partial sums of the row groups
+  if (sc->done) return;
+  const int tid = threadIdx.x, nt = blockDim.x, G = gridDim.x, b = blockIdx.x;
+  const double obp = blk_sum_parts(dpart, ndp, red);
+  const double eps = sc->eps;
+  // this block's columns [c0, c1)
+  const long long segw = (No + G - 1) / G;
+  const long long c0 = min(No, (long long)b * segw), c1 = min(No, c0 + segw);
+  const int ncol = (int)(c1 - c0);
+  // phase B layout: thread (col, rg); ncolp column slots of nrg row groups
+  const int nrg = ncol > 0 ? max(1, nt / ncol) : 1;
+  const int ncolp = ncol > 0 ? (nt / nrg) : 0;
+  const int mycol = tid % max(1, ncolp), rg = tid / max(1, ncolp);
+  const bool bthread = ncol > 0 && rg < nrg;
+  // q for this block's columns starts at zero
+  for (long long o = c0 + tid; o < c1; o += nt) {
+    int j;
+    const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+    const long long sz = ooff[j + 1] - ooff[j];
+    q[t] = 0.0;
+    q[t + sz] = 0.0;
+    q[t + 2 * sz] = 0.0;
+    q[t + 3 * sz] = 0.0;
+  }
+  const long long R = (long long)G * rpb;
+  unsigned gen = 0;
+  for (long long cbase = 0; cbase < n; cbase += R) {
+    // ---- phase A: dot products of this block's rows of the chunk
+    for (int r = 0; r < rpb; ++r) {
+      const long long i = cbase + (long long)b * rpb + r;
+      if (i >= n) break;
+      const OT* row = O + i * No;
+      const uint8_t* Si = S + i * N;
+      double acc = 0.0;
+      if (VEC) {   // four columns of one site per thread (site slices of multiples of four)
+        for (long long o = 4LL * tid; o < No; o += 4LL * nt) {
+          int j;
+          const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+          const long long sz = ooff[j + 1] - ooff[j];
+          const double* pp = p + t + (long long)Si[j] * sz;
+          if (sizeof(OT) == 4) {
+            const float4 v = __ldg((const float4*)(row + o));
+            acc += (double)v.x * pp[0] + (double)v.y * pp[1] + (double)v.z * pp[2] + (double)v.w * pp[3];
+          } else {
+            const double2 v0 = __ldg((const double2*)(row + o)), v1 = __ldg((const double2*)(row + o + 2));
+            acc += v0.x * pp[0] + v0.y * pp[1] + v1.x * pp[2] + v1.y * pp[3];
+          }
+        }
+      } else {
+        for (long long o = tid; o < No; o += nt) {
+          int j;
+          const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+          const long long sz = ooff[j + 1] - ooff[j];
+          acc += (double)row[o] * p[t + (long long)Si[j] * sz];
+        }
+      }
+      acc = blk_sum(acc, red);
+      if (tid == 0) y[i] = w[i] * (acc - obp);
+    }
+    if (!gv_barrier(bar, gen, err, &ok_sh)) return;
+    // ---- phase B: this block's columns, summed over the chunk's rows
+    const long long cend = min((long long)n, cbase + R);
+    if (bthread) {
+      for (int col = mycol; col < ncol; col += ncolp) {
+        const long long o = c0 + col;
+        int j;
+        const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+        const long long sz = ooff[j + 1] - ooff[j];
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (long long i = cbase + rg; i < cend; i += nrg) {
+          const double v = (double)O[i * No + o] * __ldcg(y + i);
+          const int st = S[i * N + j];
+          a0 += st == 0 ? v : 0.0;
+          a1 += st == 1 ? v : 0.0;
+          a2 += st == 2 ? v : 0.0;
+          a3 += st == 3 ? v : 0.0;
+        }
+        if (nrg == 1) {
+          q[t] += a0;
+          q[t + sz] += a1;
+          q[t + 2 * sz] += a2;
+          q[t + 3 * sz] += a3;
+        } else {
+          // row groups of this column meet in shared memory (this column slot's entries only)
+          gacc[0 * nt + tid] = a0;
+          gacc[1 * nt + tid] = a1;
+          gacc[2 * nt + tid] = a2;
+          gacc[3 * nt + tid] = a3;
+        }
+        if (nrg > 1) break;   // with several row groups every slot holds exactly one column
+      }
+    }
+    if (nrg > 1) {
+      __syncthreads();
+      if (bthread && rg == 0 && mycol < ncol) {
+        const long long o = c0 + mycol;
+        int j;
+        const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+        const long long sz = ooff[j + 1] - ooff[j];
+        double a[4] = {0, 0, 0, 0};
+        for (int g2 = 0; g2 < nrg; ++g2)
+#pragma unroll
+          for (int s4 = 0; s4 < 4; ++s4) a[s4] += gacc[s4 * nt + g2 * ncolp + mycol];
+        q[t] += a[0];
+        q[t + sz] += a[1];
+        q[t + 2 * sz] += a[2];
+        q[t + 3 * sz] += a[3];
+      }
+      __syncthreads();
+    }
+  }
+  // sum_i y_i in one fixed order (the same value in every block)
+  double sy = 0.0;
+  for (int i = tid; i < n; i += nt) sy += __ldcg(y + i);
+  sy = blk_sum(sy, red);
+  // q = sum y O - (sum y) obar + eps p on this block's entries; partial p.q
+  double pq = 0.0;
+  for (long long o = c0 + tid; o < c1; o += nt) {
+    int j;
+    const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
+    const long long sz = ooff[j + 1] - ooff[j];
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const long long ts = t + s4 * sz;
+      const double qt = q[ts] - sy * obar[ts] + eps * p[ts];
+      q[ts] = qt;
+      pq += p[ts] * qt;
+    }
+  }
+  pq = blk_sum(pq, red);
+  if (tid == 0) pqpart[b] = pq;
 }
 
 // theta -= tau x (and the float32 copy).

@@ -14,7 +14,7 @@
 // (they only reach accumulator rows and columns that are not stored), and a Gram product
 // C = P P^T that one tile covers gathers P once: the B descriptor points at the A stage.
 // Every wait on the mbarrier is bounded: when it runs out the kernel raises `err`, waits once
-// more, frees its tensor memory and returns.
+// more, frees its tensor memory and returns (err bit 2 when that second wait ran out too).
 #ifndef PV_TC_CUH
 #define PV_TC_CUH
 #include <cstdint>
@@ -474,6 +474,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   __shared__ __align__(8) uint64_t bar[2];
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
+  __shared__ int stuck;   // a grace wait ran out too: an MMA may still be writing tensor memory
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tm = blockIdx.x / tilesN, tn = blockIdx.x - (blockIdx.x / tilesN) * tilesN;
   const int TN = t.TN, Kc = t.Kc;
@@ -514,6 +515,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
   }
   if (tid == 0) {
     abort_flag = 0;
+    stuck = 0;
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar0), "r"(1) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar1), "r"(1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -576,7 +578,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
         const uint32_t pb = (ph >> ps) & 1u;
         bool good = tc_wait(ps ? bar1 : bar0, pb);
         if (!good) {
-          tc_wait(ps ? bar1 : bar0, pb);
+          if (!tc_wait(ps ? bar1 : bar0, pb)) stuck = 1;
           abort_flag = 1;
         }
         good = __all_sync(0xffffffffu, good);   // tcgen05.ld below is warp-collective
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
       const int ls = (it - 1) & 1;
       const uint32_t pb = (ph >> ls) & 1u;
       if (!tc_wait(ls ? bar1 : bar0, pb)) {
-        tc_wait(ls ? bar1 : bar0, pb);
+        if (!tc_wait(ls ? bar1 : bar0, pb)) stuck = 1;
         abort_flag = 1;
       }
       ph ^= 1u << ls;
@@ -629,7 +631,7 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
           tc_commit(bar0);
         }
         if (!tc_wait(bar0, ph & 1u)) {
-          tc_wait(bar0, ph & 1u);
+          if (!tc_wait(bar0, ph & 1u)) stuck = 1;
           abort_flag = 1;
         }
         ph ^= 1u;
@@ -646,12 +648,15 @@ __global__ void __launch_bounds__(TC_THREADS) kb_gemm_tc(TcSpec t, float* C, lon
     }
   }
   __syncthreads();
+  // Tensor memory must be released before the CTA exits.  After a timeout whose grace wait
+  // also ran out, an MMA may still be writing it: the flag then carries bit 2, and the
+  // host reports that every result of the context is undefined from this call on.
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols)
                  : "memory");
   }
-  if (tid == 0 && abort_flag) atomicOr(err, 1);
+  if (tid == 0 && abort_flag) atomicOr(err, stuck ? 3 : 1);
 }
 
 #endif  // __CUDACC__

@@ -186,6 +186,87 @@ def test_tf32_energy_per_site_within_1e3_of_fp64():
     assert np.max(np.abs(e64 - e32)) / (2 * N) <= 1e-3
 
 
+def _sampled_configs(th, L, D, chi, n, seed, sweeps):
+    """Configurations typical of |rho|^2: FP64 Metropolis chains after `sweeps` sweeps."""
+    ref = _ctx(L, L, D, chi, n, prec=binding.PEPS_FP64, seed=seed, mode=binding.PEPS_BLOCKS_BATCHED)
+    ref.set_theta(th)
+    ref.mc_sweep(sweeps, p=2)
+    return ref
+
+
+def test_tf32_generic_state_8x8():
+    # A generic state at the 8x8 D=4 chi=16 shape: entries of scale 0.3 and no diagonal bias,
+    # configurations drawn from |rho|^2 by FP64 chains.  Such a state is far from what chi=16
+    # resolves: the FP64 amplitudes at chi=16 and chi=32 differ by a median of ~0.7 in
+    # log|rho|, and where a truncation cuts through a nearly flat spectrum any perturbation of
+    # the kept subspace (float32 rounding in FP32 mode as much as TF32 operands) moves the
+    # amplitude by a similar amount.  Tolerances: TF32's unit roundoff u = 2^-11 amplified by
+    # ~2 L^2 chained contractions gives ~1e-2 in log|rho| (median bound 2e-2); on the samples
+    # whose chi=16 amplitude is converged (within 0.1 of chi=32) the per-sample bounds are 5e-2
+    # in log|rho| and 1e-2 in E_loc/(2N), and the mean energy per site is within 1e-3 (the
+    # mixed-precision bound); and every sample off by more than 0.1 is one whose chi=16
+    # amplitude is itself uncertain by more than a factor e.
+    L, D, chi, n = 8, 4, 16, 256
+    N = L * L
+    th = wl.random_theta(L, L, D, seed=85, scale=0.3, diag_bias=0.0)
+    ref = _sampled_configs(th, L, D, chi, n, seed=86, sweeps=3)
+    S = ref.get_configs()
+    la64, sg64, es64, ea64, _ = ref.eval_batch(S, with_O=False)
+    wide = _ctx(L, L, D, 2 * chi, n, prec=binding.PEPS_FP64, seed=86, mode=binding.PEPS_BLOCKS_BATCHED)
+    wide.set_theta(th)
+    lachi = wide.eval_batch(S, with_O=False)[0]
+    tf = _ctx(L, L, D, chi, n, prec=binding.PEPS_TF32, seed=86)
+    tf.set_theta(th)
+    la32, sg32, es32, ea32, _ = tf.eval_batch(S, with_O=False)
+    dla = np.abs(la32 - la64)
+    de = np.abs((es32 + ea32) - (es64 + ea64)) / (2 * N)
+    sens = np.abs(lachi - la64)
+    good = sens <= 0.1
+    print(f"\ngeneric 8x8 TF32 vs FP64: {int(good.sum())} of {n} samples converged in chi; "
+          f"|dlog rho| median {np.median(dla):.2e} p90 {np.quantile(dla, 0.9):.2e} max {dla.max():.2e}; "
+          f"converged: max {dla[good].max():.2e}, |dE_loc|/2N max {de[good].max():.2e}, "
+          f"dE/site {abs(np.mean((es32 + ea32 - es64 - ea64)[good])) / (2 * N):.2e}")
+    assert np.all(sg32 == sg64)
+    assert np.median(dla) <= 2e-2
+    assert good.sum() >= 8
+    assert dla[good].max() <= 5e-2
+    assert de[good].max() <= 1e-2
+    assert abs(np.mean((es32 + ea32 - es64 - ea64)[good])) / (2 * N) <= 1e-3
+    assert np.all(sens[dla > 0.1] > 1.0)
+
+
+def test_tf32_metropolis_decisions_on_a_cooled_state():
+    # Metropolis decisions on the same Philox stream: one sweep of every chain in TF32 and in
+    # FP64 from the same configurations of a cooled 8x8 D=4 chi=16 state (six SR steps of
+    # tau = 0.05 in FP64).  A chain's sweep differs as soon as one of its M decisions differs,
+    # so the fraction F of differing chains gives the per-decision disagreement rate
+    # f = -ln(1 - F) / M.  A decision flips when u falls between the two precisions'
+    # acceptance probabilities, |q32 - q64| ~ 2 q |d log ratio| with |d log ratio| ~ 1e-3 on
+    # such states: f <= 2e-3.
+    L, D, chi, n = 8, 4, 16, 256
+    N = L * L
+    ref = _ctx(L, L, D, chi, n, prec=binding.PEPS_FP64, seed=87, mode=binding.PEPS_BLOCKS_BATCHED)
+    ref.mc_sweep(2, p=1)
+    for k in range(6):
+        ref.step(n_sweeps=1, p=1 if k < 2 else 2, tau=0.05, eps=1e-4, max_cg=100, cg_tol=1e-10)
+    S = ref.get_configs()
+    tf = _ctx(L, L, D, chi, n, prec=binding.PEPS_TF32, seed=87)
+    tf.set_theta(ref.get_theta())
+    tf.set_configs(S)
+    tf.sweeps_done = ref.sweeps_done
+    ref.mc_sweep(1, p=2)
+    tf.mc_sweep(1, p=2)
+    diff = np.any(ref.get_configs() != tf.get_configs(), axis=1)
+    # decisions per sweep: N both-flips, and of the 4 L (L - 1) exchanges (two layers on every
+    # horizontal and vertical bond) the ones between unequal spins, about half
+    M = N + 2 * L * (L - 1)
+    F = float(np.mean(diff))
+    f = -np.log(max(1e-12, 1.0 - min(F, 1.0 - 1.0 / n))) / M
+    print(f"\nMetropolis: {int(diff.sum())} of {n} chains differ after one sweep (~{M} decisions "
+          f"each): per-decision disagreement rate {f:.2e}")
+    assert f <= 2e-3
+
+
 def test_tf32_needs_batched_blocks():
     with pytest.raises(RuntimeError):
         _ctx(3, 3, 2, 4, 2, prec=binding.PEPS_TF32, mode=binding.PEPS_BLOCKS_NARROW)
@@ -247,6 +328,11 @@ def test_sr_step_matches_oracle(p):
     th = wl.random_theta(L1, L2, D, seed=21, scale=0.3, diag_bias=1.0)
     S = wl.random_configs(L1, L2, n, seed=22)
     ctx = _ctx(L1, L2, D, chi, n, J2=J2)
+    # one step of tau0 first, so that the compared step reports at beta_obs = 4 tau0 != 0
+    # (C and chi carry beta_obs factors), then back to the test state
+    tau0 = 0.3
+    ctx.eval_chains()
+    ctx.sr_step(tau0, eps=1e-2, max_cg=5, cg_tol=1e-6, p=p)
     ctx.set_theta(th)
     ctx.set_configs(S)
     ctx.eval_chains()
@@ -268,20 +354,27 @@ def test_sr_step_matches_oracle(p):
     assert np.max(np.abs(x_gpu - x)) <= 1e-8 * np.max(np.abs(xd))
     assert st['cg_resid'] <= tol and not st['cg_maxit']
     assert abs(st['cg_iters'] - it) <= 2
-    o = obs_mod.observables(lat, 0.0, w, es, ea, S)
+    o = obs_mod.observables(lat, tau0, w, es, ea, S)
+    assert st['beta_obs'] == pytest.approx(4 * tau0, rel=1e-15)
     assert st['E_site'] == pytest.approx(o['E_site'], rel=1e-10, abs=1e-12)
+    # specific heat, susceptibility and the standard error of E (Eqs. 11, 13; weighted for
+    # p = 1, Eq. A1), all float64 reductions: 1e-10 relative
+    assert o['C_site'] > 0 and o['chi'] > 0 and o['E_err'] > 0
+    assert st['C_site'] == pytest.approx(o['C_site'], rel=1e-10)
+    assert st['chi_sus'] == pytest.approx(o['chi'], rel=1e-10)
+    assert st['E_err'] == pytest.approx(o['E_err'], rel=1e-10)
     assert st['diag_frac'] == pytest.approx(o['diag_frac'])
 
 
 @pytest.mark.parametrize("prec", [binding.PEPS_FP32, binding.PEPS_TF32])
-def test_sr_step_float_o_rows_match_oracle(prec):
-    # Float O rows (the 16-byte vector O passes when every site slice holds a multiple of
-    # four entries, as at D=2 on 4x4): the SR update from the GPU's own evaluation against
-    # the oracle's SR step on those same float values.  Float32 products in the O passes
-    # (per-chunk sums of 128 samples, float64 across chunks) keep CG's attainable relative
-    # residual near 1e-6, which leaves x within a few 1e-3 of the float64 solution (2.7e-3
-    # seen with both the vector and the element-wise passes).
-    L, D, chi, n = 4, 2, 4, 256
+@pytest.mark.parametrize("shape", [(4, 2, 4, 256), (3, 3, 4, 300)])
+def test_sr_step_float_o_rows_match_oracle(prec, shape):
+    # Float32 O rows (16-byte vector passes when every site slice holds a multiple of four
+    # entries, as at D=2 on 4x4; element passes at D=3): the SR update from the GPU's own
+    # evaluation against the oracle's SR step on those same float values.  The O passes widen
+    # every float32 entry and multiply and sum in float64, so both sides solve the same
+    # float64 system: CG to 1e-12 on both, x within 1e-8 relative.
+    L, D, chi, n = shape
     lat = Lattice(L, L, D, J1=1.0)
     th = wl.random_theta(L, L, D, seed=31, scale=0.3, diag_bias=1.0)
     S = wl.random_configs(L, L, n, seed=32)
@@ -290,13 +383,15 @@ def test_sr_step_float_o_rows_match_oracle(prec):
     ctx.set_configs(S)
     la, sg, es, ea, O = ctx.eval_batch(S)
     ctx.eval_chains()
-    tau, eps = 0.05, 1e-1
-    ctx.sr_step(tau, eps=eps, max_cg=500, cg_tol=1e-6, p=2)
+    tau, eps, tol = 0.05, 1e-1, 1e-12
+    st = ctx.sr_step(tau, eps=eps, max_cg=500, cg_tol=tol, p=2)
+    assert st['cg_resid'] <= tol and not st['cg_maxit']
     x_gpu = (th - ctx.get_theta()) / tau
     O = O.astype(np.float64)
-    _, x, g, it, resid = sr.sr_step(lat, th, S, la, es, ea, O, 2, tau, eps, 1e-10, 500)
-    assert resid <= 1e-10
-    assert np.max(np.abs(x_gpu - x)) <= 1e-2 * np.max(np.abs(x))
+    _, x, g, it, resid = sr.sr_step(lat, th, S, la, es, ea, O, 2, tau, eps, tol, 500)
+    assert resid <= tol
+    assert np.max(np.abs(x_gpu - x)) <= 1e-8 * np.max(np.abs(x))
+    assert abs(st['cg_iters'] - it) <= 2
 
 
 def test_sr_step_cg_maxit_warning_and_observables():
@@ -331,6 +426,25 @@ def test_errors_and_edge_cases():
         ctx.mc_sweep(1, p=3)
     la, sg, es, ea, O = ctx.eval_batch(np.zeros((0, 9), np.uint8))
     assert la.size == 0
+    # configuration entries above 3 are rejected before any evaluation, for host batches
+    # (checked on the host) and device batches (checked by a kernel), in both engines
+    import torch
+    for mode in (binding.PEPS_BLOCKS_NARROW, binding.PEPS_BLOCKS_BATCHED):
+        cm = _ctx(3, 3, 2, 4, 4, mode=mode)
+        bad = np.zeros((2, 9), np.uint8)
+        bad[1, 4] = 4
+        with pytest.raises(binding.PepsError) as e:
+            cm.eval_batch(bad)
+        assert e.value.code == binding.PEPS_EINVAL
+        dev = torch.device("cuda:0")
+        outs = [torch.empty(2, dtype=torch.float64, device=dev), torch.empty(2, dtype=torch.int8, device=dev),
+                torch.empty(2, dtype=torch.float64, device=dev), torch.empty(2, dtype=torch.float64, device=dev)]
+        with pytest.raises(binding.PepsError) as e:
+            cm.eval_batch_device(torch.from_numpy(bad).to(dev), *outs)
+        assert e.value.code == binding.PEPS_EINVAL
+        cm.eval_batch_device(torch.from_numpy(np.zeros((2, 9), np.uint8)).to(dev), *outs)
+        assert np.all(np.isfinite(outs[0].cpu().numpy()))
+        cm.close()
     # beta = 0 state with no noise: rho = 1 on diagonal configurations, 0 elsewhere
     ctx0 = _ctx(3, 3, 2, 4, 4, noise=0.0)
     S = np.array([[0] * 9, [3] * 9, [0, 3, 0, 3, 3, 0, 0, 0, 3], [1] + [0] * 8], np.uint8)

@@ -68,20 +68,45 @@ def test_spline_cv_two_level_closed_form_and_noise():
     assert np.allclose(cvn(probe), probe ** 2 / np.cosh(probe) ** 2, atol=1e-2)
 
 
-def test_gpr_cv_matches_fluctuation_formula_and_closed_form():
-    # Sec. III.B's Gaussian-process form of C = -beta^2 dE/dbeta: on the ED energy curve it
-    # reproduces the fluctuation formula; on the two-level curve the closed form, also with
-    # noise of 1e-4 on E (noise variance given as 1e-8)
-    lat = Lattice(2, 3, 1, J1=1.0)
-    spec = ed.spectrum(lat)
-    betas = np.linspace(0.05, 4.0, 60)
-    cv = observables.cv_from_energy_gpr(betas, ed.thermal(spec, lat.N, betas)[:, 0], noise=1e-12)
-    probe = np.linspace(0.3, 3.7, 15)
-    assert np.allclose(cv(probe), ed.thermal(spec, lat.N, probe)[:, 1], atol=1e-4)
-    b2 = np.linspace(0.0, 3.0, 121)
-    pr = np.linspace(0.2, 2.8, 14)
-    exact = pr ** 2 / np.cosh(pr) ** 2
-    assert np.allclose(observables.cv_from_energy_gpr(b2, -np.tanh(b2), noise=1e-12)(pr), exact,
-                       atol=1e-4)
-    noisy = -np.tanh(b2) + 1e-4 * np.random.default_rng(3).standard_normal(b2.size)
-    assert np.allclose(observables.cv_from_energy_gpr(b2, noisy, noise=1e-8)(pr), exact, atol=3e-3)
+def test_standard_error_iid_plain_weights():
+    # p = 2 weights (1/n) on independent normal samples of variance sigma^2: the estimate
+    # is sigma_hat / sqrt(n); over many repetitions its mean matches the observed spread of
+    # the sample means and sigma / sqrt(n) (to the few per cent of 4000 repetitions)
+    rng = np.random.default_rng(11)
+    n, sigma, reps = 50, 1.7, 4000
+    w = np.full(n, 1.0 / n)
+    means, ses = [], []
+    for _ in range(reps):
+        h = 3.0 + sigma * rng.standard_normal(n)
+        means.append(float(w @ h))
+        ses.append(observables.standard_error(w, h))
+    exact = sigma / np.sqrt(n)
+    assert np.std(means) == pytest.approx(exact, rel=0.04)
+    # the population-variance form is biased low by sqrt((n-1)/n) on average, plus the
+    # Jensen gap of a square root: both under 2 % at n = 50
+    assert np.mean(ses) == pytest.approx(exact, rel=0.03)
+
+
+def test_standard_error_weighted_ratio_estimate():
+    # p = 1 weights (Eq. A1): samples drawn from q, weights proportional to p/q, normalised.
+    # Target p = N(1, 1), proposal q = N(0, 1.5^2), h(x) = x^2: the weighted mean estimates
+    # E_p[x^2] = 2, and the delta-method error matches the observed spread of the estimates
+    rng = np.random.default_rng(12)
+    n, reps = 400, 3000
+    est, ses = [], []
+    for _ in range(reps):
+        x = 1.5 * rng.standard_normal(n)
+        logr = -0.5 * (x - 1.0) ** 2 + 0.5 * (x / 1.5) ** 2
+        r = np.exp(logr - logr.max())
+        w = r / r.sum()
+        h = x * x
+        est.append(float(w @ h))
+        ses.append(observables.standard_error(w, h))
+    assert np.mean(est) == pytest.approx(2.0, abs=0.02)
+    assert np.mean(ses) == pytest.approx(np.std(est), rel=0.06)
+
+
+def test_standard_error_special_cases():
+    # one distinct value: zero error; two equally weighted values a, b: abs(a - b) / (2 sqrt 2)
+    assert observables.standard_error([0.25] * 4, [2.0] * 4) == 0.0
+    assert observables.standard_error([0.5, 0.5], [1.0, 3.0]) == pytest.approx(np.sqrt(2.0) / 2)
