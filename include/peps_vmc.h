@@ -150,6 +150,15 @@ int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
 int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
               double cg_tol, peps_stats* stats);
 
+/* How peps_sr_step applies (G + eps) in CG (Eq. 10): 1 = one cooperative kernel that reads
+ * the O rows once per product (each block owns a slice of the columns; samples are taken in
+ * chunks that stay in L2, one grid barrier per chunk); 2 = two streaming passes (O_i.p, then
+ * the column sums of y_i O_i); 0 (default) = the fused product when a product needs at most
+ * 16 chunks, else the two passes (long rows leave few samples per chunk).  Every choice uses
+ * float64 products and fixed summation orders; the results agree to rounding.  EINVAL for
+ * other modes. */
+int peps_set_cg_product(peps_ctx* ctx, int mode);
+
 /* Parameter vector and chain configurations (host buffers).  n must equal N_p, or
  * n_chains * L1 * L2 for the configurations. */
 int peps_get_theta(peps_ctx* ctx, double* host, size_t n);
@@ -222,6 +231,19 @@ int peps_set_tune(peps_ctx* ctx, const peps_tune* t);
  * (n must equal N_p for L1 x L2 at bond dimension D). */
 int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, double* theta,
                   size_t n);
+
+/* The same simple-update warm start run on the device into the context: theta becomes the
+ * simple-update state after n_steps steps of length tau from beta = 0 (App. A; the bond
+ * update described at peps_su_theta, nearest-neighbour bonds with coupling J1), and the
+ * context's imaginary time becomes t = n_steps * tau (beta_obs = 4t), from which SR steps
+ * continue.  In each half of a step (horizontal bonds, then vertical bonds) every row (or
+ * column) is one thread block that takes its bonds in order; lines share no site or
+ * changing weight, so this is the host scheme's order, and the state equals peps_su_theta's
+ * up to the summation order of the factorisations (bonds whose truncation cuts through a
+ * degenerate spectrum may keep a different, equally valid, subspace).  Allocates and frees
+ * its own work arrays (at D = 4 about 0.5 MB per block); synchronises the context stream.
+ * EINVAL for bad arguments or J2 != 0; ENOMEM, ECUDA on device failures. */
+int peps_su_warm_start(peps_ctx* ctx, double tau, int n_steps);
 
 /* Per-kernel statistics for roofline reports.  peps_profile(ctx, 1) clears them and starts
  * bracketing every launch of the context with CUDA events on its stream; peps_profile(ctx,

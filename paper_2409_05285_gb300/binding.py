@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product",
 ]
 
 
@@ -141,6 +141,8 @@ def load(path=None):
     lib.peps_profile.argtypes = [vp, ip]
     lib.peps_profile_read.argtypes = [vp, ctypes.POINTER(KernelStat), ip, ctypes.POINTER(ip)]
     lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
+    lib.peps_su_warm_start.argtypes = [vp, dp, ip]
+    lib.peps_set_cg_product.argtypes = [vp, ip]
     lib.peps_su_theta.argtypes = [ip, ip, ip, dp, dp, ip, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_size_t]
     lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -342,6 +344,15 @@ class Context:
         d = st.as_dict()
         d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
         return d
+
+    def set_cg_product(self, mode):
+        """CG product form (peps_set_cg_product): 0 automatic, 1 fused single read, 2 two passes."""
+        self._check(self.lib.peps_set_cg_product(self.ctx, int(mode)))
+
+    def su_warm_start(self, tau, n_steps):
+        """Simple-update warm start on the device (peps_su_warm_start): theta becomes the SU
+        state at t = n_steps * tau and the context's time t with it."""
+        self._check(self.lib.peps_su_warm_start(self.ctx, float(tau), int(n_steps)))
 
     def counters(self):
         f = ctypes.c_double()

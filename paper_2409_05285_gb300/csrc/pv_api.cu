@@ -14,6 +14,7 @@
 #include "pv_sr.cuh"
 #include "pv_batch.cuh"
 #include "pv_su.cuh"
+#include "pv_su_dev.cuh"
 
 #include <memory>
 #include <map>
@@ -315,13 +316,14 @@ struct peps_ctx {
   // SR
   double *d_w = nullptr, *d_E = nullptr, *d_obar = nullptr, *d_g = nullptr, *d_x = nullptr;
   double *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_y = nullptr, *d_part = nullptr;
-  double *d_part2 = nullptr, *d_bp1 = nullptr, *d_bp2 = nullptr;
+  double *d_part2 = nullptr, *d_bp1 = nullptr, *d_bp2 = nullptr, *d_ypart = nullptr;
   double* d_pqpart = nullptr;   // per-block partials of p.q of the fused CG product
   unsigned* d_gvbar = nullptr;  // grid-barrier counter and generation of the fused product
   int* d_gverr = nullptr;       // raised when a grid-barrier wait ran out
   int gv_grid = 0, gv_rpb = 1;   // fused product: resident blocks, rows per block per chunk
+  int cg_mode = 0;               // CG product: 0 automatic, 1 fused single read, 2 two passes
   SRScalars* d_sc = nullptr;
-  int nch = 0, nvb = 0;
+  int nch = 0, nvb = 0, nyb = 0;
   double t = 0;
   int64_t sweeps = 0;
   double last_accept = 0;
@@ -511,6 +513,15 @@ int make_batch_t(peps_ctx* c, int sms) {
     cudaError_t e = cudaFuncSetAttribute(kb_lq<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq_max);
     b->be.lq_smem_max = e == cudaSuccess ? lq_max : 48 * 1024;
     if (e != cudaSuccess) cudaGetLastError();
+    if constexpr (std::is_same<T, float>::value) {
+      const int tw_max = 220 * 1024;
+      e = cudaFuncSetAttribute(kb_trunc_wide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, tw_max);
+      b->be.trunc_wide_max = e == cudaSuccess ? tw_max : 0;
+      if (e != cudaSuccess) cudaGetLastError();
+      e = cudaFuncSetAttribute(kb_chol<T, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, tw_max);
+      b->be.chol_wide_max = e == cudaSuccess ? tw_max : 0;
+      if (e != cudaSuccess) cudaGetLastError();
+    }
     const int lq2_max = 200 * 1024;
     e = cudaFuncSetAttribute(kb_lq2<T, LQ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq2_max);
     b->be.lq2_smem_max = e == cudaSuccess ? lq2_max : 0;
@@ -718,6 +729,7 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
   // SR buffers
   c->nch = (n + OTV_CHUNK - 1) / OTV_CHUNK;
   c->nvb = grid_for(c->Np, SR_THREADS, 1024);
+  c->nyb = (n + (SR_THREADS / 32) - 1) / (SR_THREADS / 32);
   if ((rc = dalloc(c, &c->d_w, n * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_E, n * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_y, n * sizeof(double)))) return bail(rc);
@@ -742,13 +754,14 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
     const double rows = 48e6 / ((double)c->gv_grid * (double)c->No * elt);
     c->gv_rpb = std::max(1, std::min(64, (int)rows));
   }
-  if ((rc = dalloc(c, &c->d_pqpart, (size_t)c->gv_grid * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_pqpart, (size_t)std::max(c->gv_grid, c->nvb) * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_gvbar, 2 * sizeof(unsigned)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_gverr, sizeof(int)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_part, (size_t)c->nch * c->Np * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_part2, (size_t)c->nch * c->Np * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_bp1, c->nvb * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_bp2, c->nvb * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_ypart, c->nyb * sizeof(double)))) return bail(rc);
   if ((rc = dalloc(c, &c->d_sc, sizeof(SRScalars)))) return bail(rc);
   if (P->block_mode == PEPS_BLOCKS_BATCHED) {
     if ((rc = make_batch(c, sms))) return bail(rc);
@@ -1062,31 +1075,66 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   PV_KLAUNCH(&c->kprof, s, "k_dot_part", (2.0 * Np * 8.0), 0.0, k_dot_part<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_obar, c->d_p, c->d_bp2, nullptr));   // obar.p
   PV_CUDA(c, cudaGetLastError());
   PV_CUDA(c, cudaMemsetAsync(c->d_gverr, 0, sizeof(int), s));
+  // the fused product reads O once but synchronises the grid once per L2-sized chunk of
+  // samples; with long rows (few rows per chunk) the two streaming passes are faster
+  const long long gv_rows = (long long)c->gv_grid * c->gv_rpb;
+  const bool fused = c->cg_mode == 1 || (c->cg_mode == 0 && (n + gv_rows - 1) / gv_rows <= 16);
+  const int ov_blocks = c->nyb;
+  dim3 cgrid_y((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
+  dim3 cgrid4_y((unsigned)((No / 4 + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
   for (int it = 0; it < max_cg; ++it) {
-    // q = (G + eps) p in one cooperative launch (one read of O), then the vector updates
-    PV_CUDA(c, cudaMemsetAsync(c->d_gvbar, 0, 2 * sizeof(unsigned), s));
-    {
-      int n_ = n, N_ = c->N, ndp = nvb, rpb = c->gv_rpb;
-      long long No_ = No;
-      const void* Op = c->d_O;
-      const uint8_t* Sp = c->d_S;
-      const int* o2s = c->d_o2site;
-      const long long *tof = c->d_toff, *oof = c->d_ooff;
-      const double *pp = c->d_p, *obp = c->d_obar, *wp = c->d_w, *dp = c->d_bp2;
-      double *yp = c->d_y, *qp = c->d_q, *pqp = c->d_pqpart;
-      unsigned* barp = c->d_gvbar;
-      int* errp = c->d_gverr;
-      const SRScalars* scp = c->d_sc;
-      void* args[] = {&n_, &N_, &No_, &Op, &Sp, &o2s, &tof, &oof, &pp, &obp, &wp, &ndp, &dp,
-                      &yp, &qp, &pqp, &rpb, &barp, &errp, &scp};
-      const void* fn = fp64(c) ? (c->o_vec4 ? (const void*)k_gv<double, true> : (const void*)k_gv<double, false>)
-                               : (c->o_vec4 ? (const void*)k_gv<float, true> : (const void*)k_gv<float, false>);
-      const double obytes = (double)n * No * (fp64(c) ? 8.0 : 4.0);
-      PV_KLAUNCH(&c->kprof, s, "k_gv", obytes + (double)n * c->N + 4.0 * Np * 8.0, 4.0 * (double)n * No,
-                 PV_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(c->gv_grid), dim3(GV_THREADS), args,
-                                                        4 * GV_THREADS * sizeof(double), s)));
+    if (!fused) {
+      // y_i = w_i (O_i.p - obar.p), then the column sums part = sum_i y_i O_i, then q
+      const double ob = (double)n * No * (fp64(c) ? 8.0 : 4.0);
+      if (fp64(c))
+        PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const double*)c->d_O, c->d_S,
+            c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
+      else if (c->o_vec4)
+        PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov_f32v<<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
+            c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
+      else
+        PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
+            c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
+      if (fp64(c))
+        PV_KLAUNCH(&c->kprof, s, "k_colsum1", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1<double, false><<<cgrid_y, SR_THREADS, 0, s>>>(
+            n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+            nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+      else if (c->o_vec4)
+        PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1_f32v<false><<<cgrid4_y, SR_THREADS, 0, s>>>(
+            n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+            nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+      else
+        PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1_f32<false><<<cgrid_y, SR_THREADS, 0, s>>>(
+            n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+            nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+      PV_KLAUNCH(&c->kprof, s, "k_otv2", ((double)c->nch * Np * 8.0 + 3.0 * Np * 8.0), 0.0, k_otv2<<<nvb, SR_THREADS, 0, s>>>(Np, c->nch, c->d_part, c->d_obar, c->d_p, c->d_q,
+          ov_blocks, c->d_ypart, c->d_pqpart, c->d_sc));
+    } else {
+      // q = (G + eps) p in one cooperative launch (one read of O)
+      PV_CUDA(c, cudaMemsetAsync(c->d_gvbar, 0, 2 * sizeof(unsigned), s));
+      {
+        int n_ = n, N_ = c->N, ndp = nvb, rpb = c->gv_rpb;
+        long long No_ = No;
+        const void* Op = c->d_O;
+        const uint8_t* Sp = c->d_S;
+        const int* o2s = c->d_o2site;
+        const long long *tof = c->d_toff, *oof = c->d_ooff;
+        const double *pp = c->d_p, *obp = c->d_obar, *wp = c->d_w, *dp = c->d_bp2;
+        double *yp = c->d_y, *qp = c->d_q, *pqp = c->d_pqpart;
+        unsigned* barp = c->d_gvbar;
+        int* errp = c->d_gverr;
+        const SRScalars* scp = c->d_sc;
+        void* args[] = {&n_, &N_, &No_, &Op, &Sp, &o2s, &tof, &oof, &pp, &obp, &wp, &ndp, &dp,
+                        &yp, &qp, &pqp, &rpb, &barp, &errp, &scp};
+        const void* fn = fp64(c) ? (c->o_vec4 ? (const void*)k_gv<double, true> : (const void*)k_gv<double, false>)
+                                 : (c->o_vec4 ? (const void*)k_gv<float, true> : (const void*)k_gv<float, false>);
+        const double obytes = (double)n * No * (fp64(c) ? 8.0 : 4.0);
+        PV_KLAUNCH(&c->kprof, s, "k_gv", obytes + (double)n * c->N + 4.0 * Np * 8.0, 4.0 * (double)n * No,
+                   PV_CUDA(c, cudaLaunchCooperativeKernel(fn, dim3(c->gv_grid), dim3(GV_THREADS), args,
+                                                          4 * GV_THREADS * sizeof(double), s)));
+      }
     }
-    PV_KLAUNCH(&c->kprof, s, "k_cg_a", (5.0 * Np * 8.0), 0.0, k_cg_a<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_x, c->d_r, c->d_p, c->d_q, c->gv_grid, c->d_pqpart,
+    PV_KLAUNCH(&c->kprof, s, "k_cg_a", (5.0 * Np * 8.0), 0.0, k_cg_a<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_x, c->d_r, c->d_p, c->d_q, fused ? c->gv_grid : nvb, c->d_pqpart,
                                       c->d_bp1, c->d_sc));
     PV_KLAUNCH(&c->kprof, s, "k_cg_b", (5.0 * Np * 8.0), 0.0, k_cg_b<<<nvb, SR_THREADS, 0, s>>>(Np, c->d_r, c->d_p, c->d_obar, nvb, c->d_bp1,
                                       c->d_bp2, c->d_sc));
@@ -1210,6 +1258,76 @@ int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, dou
   pv::SimpleUpdate su(L1, L2, D, J1);
   for (int k = 0; k < n_steps; ++k) su.step(tau);
   su.theta(theta);
+  return PEPS_OK;
+}
+
+int peps_set_cg_product(peps_ctx* c, int mode) {
+  if (!c || mode < 0 || mode > 2) return fail(c, PEPS_EINVAL, "set_cg_product: mode");
+  c->cg_mode = mode;
+  return PEPS_OK;
+}
+
+int peps_su_warm_start(peps_ctx* c, double tau, int n_steps) {
+  if (!c || n_steps < 0 || !(tau >= 0.0) || !std::isfinite(tau))
+    return fail(c, PEPS_EINVAL, "su_warm_start: args");
+  if (c->P.J2 != 0.0)
+    return fail(c, PEPS_EINVAL, "su_warm_start: the simple update covers nearest-neighbour (J1) bonds only");
+  const int L1 = c->P.L1, L2 = c->P.L2, D = c->P.D, N = L1 * L2;
+  const long long D4 = (long long)D * D * D * D;
+  const int nblk = std::max(L1, L2);
+  const long long wds = SuScratch::doubles(D), wis = SuScratch::ints(D);
+  SuDev sd;
+  sd.L1 = L1;
+  sd.L2 = L2;
+  sd.D = D;
+  double* wd = nullptr;
+  int* wi = nullptr;
+  std::vector<void*> mine;
+  auto cleanup = [&]() {
+    cudaStreamSynchronize(c->stream);
+    for (void* q : mine) cudaFree(q);
+  };
+  auto get = [&](void** q, size_t bytes) {
+    if (cudaMalloc(q, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    mine.push_back(*q);
+    return true;
+  };
+  if (!get((void**)&sd.T, (size_t)N * 4 * D4 * sizeof(double)) || !get((void**)&sd.dims, (size_t)N * 4 * sizeof(int)) ||
+      !get((void**)&sd.lh, (size_t)N * D * sizeof(double)) || !get((void**)&sd.nlh, (size_t)N * sizeof(int)) ||
+      !get((void**)&sd.lv, (size_t)N * D * sizeof(double)) || !get((void**)&sd.nlv, (size_t)N * sizeof(int)) ||
+      !get((void**)&sd.gate, 256 * sizeof(double)) || !get((void**)&wd, (size_t)nblk * wds * sizeof(double)) ||
+      !get((void**)&wi, (size_t)nblk * wis * sizeof(int))) {
+    cleanup();
+    return fail(c, PEPS_ENOMEM, "su_warm_start: device allocation failed");
+  }
+  double gate[256];
+  pv::SimpleUpdate::bond_gate(c->P.J1, tau, gate);
+  cudaError_t e = cudaMemcpyAsync(sd.gate, gate, sizeof(gate), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) {
+    k_su_init<<<grid_for(N, 128), 128, 0, c->stream>>>(sd);
+    c->kprof.launches += 1;
+    for (int k = 0; k < n_steps; ++k) {
+      k_su_half<<<L1, SU_THREADS, 0, c->stream>>>(sd, wd, wi, wds, wis, 1);
+      k_su_half<<<L2, SU_THREADS, 0, c->stream>>>(sd, wd, wi, wds, wis, 0);
+      c->kprof.launches += 2;
+    }
+    k_su_theta<<<N, 128, 0, c->stream>>>(sd, c->d_toff, c->d_theta);
+    c->kprof.launches += 1;
+    if (c->d_theta_f) {
+      k_to_real<float><<<grid_for(c->Np, 256), 256, 0, c->stream>>>(c->Np, c->d_theta, c->d_theta_f);
+      c->kprof.launches += 1;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cleanup();
+  if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("su_warm_start: ") + cudaGetErrorString(e));
+  c->t = n_steps * tau;
+  c->have_eval = false;
+  c->ucache_valid = false;
   return PEPS_OK;
 }
 

@@ -1359,8 +1359,8 @@ __global__ void __launch_bounds__(NT) kb_lq2(OpLq<T> op, int n, int ld, int G) {
 
 // Semidefinite Cholesky factor of each chain's m x m Gram matrix in shared memory (row
 // stride m + 1): pivots below m eps max(diag) zero their column (rank-deficient Grams).
-template <typename T>
-__global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
+template <typename T, int NT = BT>
+__global__ void __launch_bounds__(NT) kb_chol(OpChol<T> op, int n) {
   extern __shared__ __align__(16) unsigned char dyn[];
   T* A = (T*)dyn;
   __shared__ T red[32];
@@ -1371,7 +1371,7 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
     const T* G = op.G + (long long)s * op.gs;
     T* L = op.Lf + (long long)s * op.ls;
     T dmax = 0;
-    for (int i = threadIdx.x; i < m * m; i += BT) {
+    for (int i = threadIdx.x; i < m * m; i += NT) {
       const int r = i / m, c = i - r * m;
       const T v = G[i];
       A[r * ld + c] = v;
@@ -1387,14 +1387,16 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
     __syncthreads();
     for (int j = 0; j < m; ++j) {
       const T l = s_piv[j & 1], inv = l > 0 ? (T)1 / l : (T)0;
-      for (int i = j + threadIdx.x; i < m; i += BT) A[i * ld + j] = i == j ? l : A[i * ld + j] * inv;
+      for (int i = j + threadIdx.x; i < m; i += NT) A[i * ld + j] = i == j ? l : A[i * ld + j] * inv;
       __syncthreads();
-      // trailing update on a 16 x 16 thread grid (BT = 256); thread 0 updates the next
-      // diagonal entry and forms the next pivot, so a column costs two barriers
-      const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
-      for (int i = j + 1 + ty; i < m; i += 16) {
+      // trailing update on a TW x TW thread grid (TW = 16 for 256 threads, 32 for 1024);
+      // thread 0 updates the next diagonal entry and forms the next pivot, so a column costs
+      // two barriers
+      constexpr int TW = NT >= 1024 ? 32 : 16;
+      const int ty = threadIdx.x / TW, tx = threadIdx.x % TW;
+      for (int i = j + 1 + ty; i < m; i += TW) {
         const T lij = A[i * ld + j];
-        for (int k = j + 1 + tx; k < m; k += 16) A[i * ld + k] -= lij * A[k * ld + j];
+        for (int k = j + 1 + tx; k < m; k += TW) A[i * ld + k] -= lij * A[k * ld + j];
       }
       if (threadIdx.x == 0 && j + 1 < m) {
         const T d = A[(j + 1) * ld + j + 1];
@@ -1402,7 +1404,7 @@ __global__ void __launch_bounds__(BT) kb_chol(OpChol<T> op, int n) {
       }
       __syncthreads();
     }
-    for (int i = threadIdx.x; i < m * m; i += BT) {
+    for (int i = threadIdx.x; i < m * m; i += NT) {
       const int r = i / m, c = i - r * m;
       L[i] = c <= r ? A[r * ld + c] : (T)0;
     }
@@ -1419,6 +1421,24 @@ __global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long c
   // block's slice of a global work area (cached in L2)
   T* smem = gwork ? gwork + (long long)blockIdx.x * cap : (T*)dyn;
   T* sig = gwork ? (T*)dyn : smem + cap;
+  int* order = (int*)(sig + op.nc + 4);
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    op(s, red, &flag, smem, cap, order, sig);
+    __syncthreads();
+  }
+}
+
+// Truncation of a tall bond (no rotations to accumulate) with its Jacobi matrix in shared
+// memory, one 1024-thread block per SM: the column pairs of a round are spread over all
+// threads and every round runs at shared-memory latency.
+template <typename T>
+__global__ void __launch_bounds__(1024) kb_trunc_wide(OpTrunc<T> op, int n) {
+  __shared__ T red[32];
+  __shared__ int flag;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  const long long cap = (long long)op.nc * (op.len | 1);
+  T* smem = (T*)dyn;
+  T* sig = smem + cap;
   int* order = (int*)(sig + op.nc + 4);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
     op(s, red, &flag, smem, cap, order, sig);
@@ -1521,6 +1541,8 @@ struct CudaBE {
   int sms;
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
   int lq2_smem_max = 0;  // ... and its shared-memory variant (kb_lq2; 0: not used)
+  int trunc_wide_max = 0;  // shared memory kb_trunc_wide may take (0: not used)
+  int chol_wide_max = 0;   // shared memory the 1024-thread kb_chol may take (0: not used)
   bool tc = false;       // float32: GEMM-shaped contractions on the tensor cores (TF32)
   bool tc_split = false; // ... with every operand split into two TF32 parts (3xTF32)
   int tc_min_rows = 64;  // smallest larger free side sent to the tensor cores
@@ -1679,6 +1701,15 @@ struct CudaBE {
                kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
+    if (op.tall) {
+      const size_t wb = (size_t)op.nc * (op.len | 1) * sizeof(T) + (size_t)(op.nc + 4) * (sizeof(T) + sizeof(int)) + 16;
+      if (wb <= (size_t)trunc_wide_max) {
+        const int grid = n < sms ? n : sms;
+        PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
+                   kb_trunc_wide<T><<<grid, 1024, wb, st>>>(op, n));
+        return;
+      }
+    }
     size_t bytes = (trunc_g ? 0 : (size_t)trunc_cap * sizeof(T)) + (size_t)(op.nc + 4) * sizeof(T) +
                    (size_t)(op.nc + 4) * sizeof(int) + 16;
     PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
@@ -1686,6 +1717,14 @@ struct CudaBE {
   }
   void chol(OpChol<T> op, int n) {
     const size_t bytes = (size_t)op.m * (op.m + 1) * sizeof(T);
+    if (bytes > 96 * 1024 && (int)bytes <= chol_wide_max) {
+      // at most one block fits per SM: 1024 threads share the trailing updates
+      const int grid = n < sms ? n : sms;
+      PV_KLAUNCH(prof, st, "kb_chol", (double)n * 2.0 * op.m * op.m * sizeof(T),
+                 (double)op.m * op.m * op.m / 3.0 * n,
+                 (kb_chol<T, 1024><<<grid, 1024, bytes, st>>>(op, n)));
+      return;
+    }
     PV_KLAUNCH(prof, st, "kb_chol", (double)n * 2.0 * op.m * op.m * sizeof(T),
                (double)op.m * op.m * op.m / 3.0 * n,
                kb_chol<T><<<gblocks(n), BT, bytes, st>>>(op, n));

@@ -333,6 +333,111 @@ __global__ void k_cg_init(long long Np, const double* __restrict__ g, double* __
   }
 }
 
+// y_i = w_i [ (O_i . p) - obar . p ], one warp per sample; per-block partials of sum y.
+template <typename OT>
+__global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
+                     const uint8_t* __restrict__ S, const long long* __restrict__ toff,
+                     const long long* __restrict__ ooff, const double* __restrict__ p,
+                     const double* __restrict__ w,
+                     double* __restrict__ y, double* __restrict__ ypart, int ndp,
+                     const double* __restrict__ dpart, const SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double obp = blk_sum_parts(dpart, ndp, red);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  double yi = 0;
+  if (i < n) {
+    const OT* row = O + (long long)i * No;
+    double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      int s = S[(long long)i * N + j];
+      long long o0 = ooff[j], sz = ooff[j + 1] - o0;
+      long long t0 = toff[j] + (long long)s * sz;
+      for (long long k = lane; k < sz; k += 32) acc += (double)row[o0 + k] * p[t0 + k];
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    yi = w[i] * (acc - obp);
+    if (lane == 0) y[i] = yi;
+  }
+  double contrib = (lane == 0) ? yi : 0.0;
+  double s = blk_sum(contrib, red);
+  if (threadIdx.x == 0) ypart[blockIdx.x] = s;
+}
+
+// Float rows, 16-byte vectors (site slices of multiples of four entries): y_i = w_i (O_i.p - obar.p),
+// every entry widened to float64.
+__global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
+    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
+    const long long* __restrict__ toff, const long long* __restrict__ ooff,
+    const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ y,
+    double* __restrict__ ypart, int ndp, const double* __restrict__ dpart, const SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double obp = blk_sum_parts(dpart, ndp, red);
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int i = blockIdx.x * (blockDim.x >> 5) + warp;
+  double yi = 0;
+  if (i < n) {
+    const float4* row = (const float4*)(O + (long long)i * No);
+    double acc = 0;
+    for (int j = 0; j < N; ++j) {
+      const int s = S[(long long)i * N + j];
+      const long long o0 = ooff[j] >> 2, sz = (ooff[j + 1] - ooff[j]) >> 2;
+      const double2* pv = (const double2*)(p + toff[j] + (long long)s * (sz << 2));
+      double a0 = 0.0, a1 = 0.0;
+      long long kk = lane;
+      for (; kk + 32 < sz; kk += 64) {
+        const float4 r0 = __ldg(row + o0 + kk), r1 = __ldg(row + o0 + kk + 32);
+        const double2 q0 = __ldg(pv + 2 * kk), q1 = __ldg(pv + 2 * kk + 1);
+        const double2 q2 = __ldg(pv + 2 * (kk + 32)), q3 = __ldg(pv + 2 * (kk + 32) + 1);
+        a0 += (double)r0.x * q0.x + (double)r0.y * q0.y + (double)r0.z * q1.x + (double)r0.w * q1.y;
+        a1 += (double)r1.x * q2.x + (double)r1.y * q2.y + (double)r1.z * q3.x + (double)r1.w * q3.y;
+      }
+      if (kk < sz) {
+        const float4 r0 = __ldg(row + o0 + kk);
+        const double2 q0 = __ldg(pv + 2 * kk), q1 = __ldg(pv + 2 * kk + 1);
+        a0 += (double)r0.x * q0.x + (double)r0.y * q0.y + (double)r0.z * q1.x + (double)r0.w * q1.y;
+      }
+      acc += a0 + a1;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    yi = w[i] * (acc - obp);
+    if (lane == 0) y[i] = yi;
+  }
+  double contrib = (lane == 0) ? yi : 0.0;
+  double sm = blk_sum(contrib, red);
+  if (threadIdx.x == 0) ypart[blockIdx.x] = sm;
+}
+
+// q = sum_ch part - (sum y) obar + eps p ; block partials of p.q.
+__global__ void k_otv2(long long Np, int nch, const double* __restrict__ part,
+                       const double* __restrict__ obar, const double* __restrict__ p,
+                       double* __restrict__ q, int nyp, const double* __restrict__ ypart,
+                       double* __restrict__ pqpart, SRScalars* sc) {
+  __shared__ double red[32];
+  if (sc->done) return;
+  double sumy = blk_sum_parts(ypart, nyp, red);
+  double eps = sc->eps;
+  double s = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < Np;
+       t += (long long)gridDim.x * blockDim.x) {
+    // eight chunk partials in flight at a time (fixed order: the sum is reproducible)
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int c = 0;
+    for (; c + 8 <= nch; c += 8)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc[u] += part[(long long)(c + u) * Np + t];
+    for (; c < nch; ++c) acc[0] += part[(long long)c * Np + t];
+    double a = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    double qt = a - sumy * obar[t] + eps * p[t];
+    q[t] = qt;
+    s += p[t] * qt;
+  }
+  s = blk_sum(s, red);
+  if (threadIdx.x == 0) pqpart[blockIdx.x] = s;
+}
+
 // alpha = rr / p.q ; x += alpha p ; r -= alpha q ; block partials of r.r
 __global__ void k_cg_a(long long Np, double* __restrict__ x, double* __restrict__ r,
                        const double* __restrict__ p, const double* __restrict__ q, int npq,
