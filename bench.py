@@ -2,13 +2,19 @@
 
 A step is the whole hot path of one stochastic-reconfiguration step (arXiv:2409.05285,
 Sec. II): one Metropolis sweep of every chain, the evaluation of every chain (boundary-MPS
-environments, amplitude, E_loc, O rows), and the SR update (weights, gradient, CG solve
-with two passes over the O rows per iteration, theta update).
+environments, amplitude, E_loc, O rows), and the SR update (weights, gradient, CG solve of
+(G + eps) x = g with G applied to the O rows, theta update).
 
-Workload (default): 8x8 open Heisenberg J=1, d^2 = 4, D = 4, chi = 16, 8192 chains, the
-state after a short cooling run from the perturbed beta = 0 state; tau = 0.02, eps = 1e-4,
-CG tolerance 1e-10 relative, at most 100 CG iterations.  The O rows (8192 x 10816 values,
-709 MB in float64) are larger than L2, so no L2 flush is needed between steps.
+Headline workload (default): 8x8 open Heisenberg J=1, d^2 = 4, D = 4, chi = 16, 8192 chains,
+the state after a short cooling run from the perturbed beta = 0 state; tau = 0.02, eps = 1e-4,
+CG tolerance 1e-10 relative, at most 100 CG iterations; TF32 tensor-core contractions.  The O
+rows (8192 x 10816 values) are larger than L2, so no L2 flush is needed between steps.  The
+last warm-up step carries CUDA events around every kernel launch (kernel shares, roofline);
+the timed steps run without them.
+
+With --largest 1 (default) the line also carries `largest_workload`: the 10x10 J1-J2 D=6
+chi=36 workload at 16384 samples per SR step, one warm-up and one timed step (a step takes
+minutes on one GPU, so the headline's step counts do not apply to it).
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload.
@@ -32,6 +38,9 @@ SMS, MAX_MHZ = 152, 2070.0
 SU_TAU = 0.01   # step of the simple-update warm start (--su-warmup)
 PEAK_FP32_TFLOPS = 128 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
 PEAK_FP64_TFLOPS = 2 * 2 * SMS * MAX_MHZ * 1e6 / 1e12
+# dense tensor-core rates of GB300 (nominal, per GPU): TF32 1.1 PFLOP/s against BF16 2.25; a
+# TF32 peak is the measured BF16 figure times this ratio
+TF32_OVER_BF16 = 1.1 / 2.25
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel, from one
 # ncu capture of the first launches of that kernel in this bench's timed step (the timed region
@@ -188,25 +197,50 @@ def kernel_shares(ks):
             for k, v in sorted(ks.items(), key=lambda kv: -kv[1][1]) if v[0] > 0}
 
 
+def tf32_peak(peaks):
+    """TF32 dense peak (TFLOP/s) for a kernel timed inside a long step: the measured sustained
+    BF16 rate times the nominal TF32/BF16 ratio, else the recipe's fallback."""
+    bf = peaks.get("bf16_tflops_sustained")
+    if bf:
+        return bf * TF32_OVER_BF16, "measured BF16 sustained %.1f TFLOP/s x %.3f (nominal TF32/BF16)" % (bf, TF32_OVER_BF16)
+    return 1700.0 * TF32_OVER_BF16, "fallback BF16 sustained 1700 TFLOP/s x %.3f (nominal TF32/BF16)" % TF32_OVER_BF16
+
+
 def kernel_roofline(kstats, peaks, prec, binding):
-    """Roofline of the dominant kernel of the timed region from the library's per-launch CUDA
-    events: achieved = its algorithmic bytes (or flops) per launch / its mean launch time."""
+    """Roofline of the dominant kernel from the library's per-launch CUDA events (taken on an
+    untimed step): achieved = algorithmic flops (tensor-core contractions) or bytes per launch /
+    mean launch time.  The tensor-core contraction is bounded by the tensor pipe (TF32 peak);
+    its HBM view (algorithmic bytes / time against the measured copy bandwidth) is given too."""
     total = sum(v[1] for v in kstats.values()) or 1.0
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
-                   "GB_s": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None}
+                   "GB_s": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None,
+                   "TFLOP_s": round(v[3] / (v[1] / 1e3) / 1e12, 2) if v[1] > 0 and v[3] > 0 else None}
                for k, v in sorted(kstats.items(), key=lambda kv: -kv[1][1])[:12]}
     if not kstats:
         return None, kernels
     name, (n, ms, nbytes, flops) = max(kstats.items(), key=lambda kv: kv[1][1])
     hbm = peaks.get("hbm_gbs")
+    hpeak, hsrc = (hbm, "measured") if hbm else (6800.0, "fallback")
+    if name == "kb_gemm_tc" and flops > 0:
+        peak, src = tf32_peak(peaks)
+        achieved = flops / n / (ms / n / 1e3) / 1e12
+        out = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
+               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+               "flops_per_launch": flops / n, "bytes_per_launch": nbytes / n,
+               "mean_launch_us": ms / n * 1e3, "launches": n, "share_of_kernel_time": ms / total,
+               "peak_source": src}
+        if nbytes > 0:
+            gbs = nbytes / n / (ms / n / 1e3) / 1e9
+            out["hbm_view"] = {"achieved_GB_s": gbs, "peak_GB_s": hpeak, "frac": gbs / hpeak,
+                               "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % hsrc}
+        return out, kernels
     if nbytes > 0:
-        peak, src = (hbm, "measured") if hbm else (6800.0, "fallback")
         achieved = nbytes / n / (ms / n / 1e3) / 1e9
-        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": hpeak,
+                "unit": "GB/s", "frac": achieved / hpeak, "traffic": None,
                 "bytes_per_launch": nbytes / n, "mean_launch_us": ms / n * 1e3,
-                "launches": n, "share_of_timed_kernels": ms / total,
-                "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % src}, kernels
+                "launches": n, "share_of_kernel_time": ms / total,
+                "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % hsrc}, kernels
     peak = PEAK_FP64_TFLOPS if prec == binding.PEPS_FP64 else PEAK_FP32_TFLOPS
     achieved = flops / (ms / 1e3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
@@ -270,30 +304,29 @@ def run_ours(args):
     tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
     p = 2
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    for _ in range(args.warmup):
+    for _ in range(args.warmup - 1):
         ctx.step(n_sweeps=1, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
     # launch shapes tuned on this context's chains, or pinned (results do not depend on them)
     if args.tune:
-        g, db, fg, kc = (int(v) for v in args.tune.split(","))
-        ctx.set_tune(g, db, fg, kc)
+        ctx.set_tune(*(int(v) for v in args.tune.split(",")))
         tune = ctx.autotune(reps=0)
     elif args.block_mode in ("auto", "batched") and not args.no_autotune:
         tune = ctx.autotune(reps=1)
     else:
         tune = None
+    # the last warm-up step: CUDA events around every launch of the context (per-kernel time,
+    # algorithmic bytes and flops, per phase) and the algorithmic flop counters; the timed
+    # steps below run without them
+    kstats, phase_k, prof = profiled_step(ctx, p, tau, eps, max_cg, tol, n)
     clocks = Clocks(local)
-    step_ms, mc_ms, eval_ms, sr_ms, eval_flops, mc_flops, cg_its, stats = [], [], [], [], [], [], [], []
-    jac = []
+    step_ms, mc_ms, eval_ms, sr_ms, cg_its, stats = [], [], [], [], [], []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    # CUDA events on the context's stream around every launch of the batched GEMM kernels
-    # (--profile-all: of every kernel, which costs a few per cent of the step time)
-    ctx.profile(True, gemm_only=not args.profile_all)
+    if args.launch_bytes:
+        ctx.profile(True, gemm_only=True)
     launches0 = ctx.launches()
-    phase_k = {"mc_sweep": {}, "eval": {}, "sr_step": {}}   # per-phase kernel sums
-    phase_base = {}
     e_start, e_end = ev(), ev()
     torch.cuda.profiler.start()   # the window `ncu --profile-from-start off` captures
     e_start.record(stream)
@@ -302,23 +335,13 @@ def run_ours(args):
         e0.record(stream)
         ctx.mc_sweep(1, p)
         e1.record(stream)
-        mc_flops.append(ctx.counters()[0])
-        if args.profile_all:
-            phase_k["mc_sweep"] = kdelta(ctx.profile_read(), phase_base, phase_k["mc_sweep"])
         ctx.eval_chains()
         e2.record(stream)
-        f_ev, j_ev = ctx.counters()
-        if args.profile_all:
-            phase_k["eval"] = kdelta(ctx.profile_read(), phase_base, phase_k["eval"])
-        eval_flops.append(f_ev)
-        jac.append(j_ev / n)
         st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=p)
         e3.record(stream)
         stats.append(st)
         cg_its.append(st["cg_iters"])
         e3.synchronize()
-        if args.profile_all:
-            phase_k["sr_step"] = kdelta(ctx.profile_read(), phase_base, phase_k["sr_step"])
         mc_ms.append(e0.elapsed_time(e1))
         eval_ms.append(e1.elapsed_time(e2))
         sr_ms.append(e2.elapsed_time(e3))
@@ -327,15 +350,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     torch.cuda.profiler.stop()
     clk = clocks.stop()
+    launches = ctx.launches() - launches0
     if args.launch_bytes:
         # algorithmic bytes of every tensor-core contraction launch of the timed steps, in
         # launch order, to set against a per-launch DRAM capture of the same launches
         with open(args.launch_bytes, "w") as f:
             json.dump({"kernel": "kb_gemm_tc", "steps": args.steps,
                        "bytes": ctx.profile_launch_bytes("kb_gemm_tc")}, f)
-    kstats = ctx.profile_read()
-    ctx.profile(False)
-    launches = ctx.launches() - launches0
+        ctx.profile(False)
     total_ms = max_over_ranks(e_start.elapsed_time(e_end))
     ms_per_step = total_ms / args.steps
     samples_per_s = job_throughput(n, ws, ms_per_step)
@@ -394,14 +416,16 @@ def run_ours(args):
         "phase_ms": {"mc_sweep": statistics.mean(mc_ms), "eval": statistics.mean(eval_ms),
                      "sr_step": statistics.mean(sr_ms)},
         "cg_iters": statistics.mean(cg_its),
-        "eval_gflop_per_sample": statistics.mean(eval_flops) / n / 1e9,
-        "jacobi_sweeps_per_sample": statistics.mean(jac),
+        "sr_step_ms": statistics.mean(sr_ms),
+        "eval_gflop_per_sample": prof["eval_flops"] / n / 1e9,
+        "sweep_gflop_per_sample": prof["mc_flops"] / n / 1e9,
+        "jacobi_sweeps_per_sample": prof["jacobi_sweeps"] / n,
         "E_site": stats[-1]["E_site"], "beta_obs": stats[-1]["beta_obs"] + 4.0 * t_su,
         "roofline": roofline,
         "kernels": kernels,
         "autotune": tune,
-        "kernels_by_phase": ({ph: kernel_shares(v) for ph, v in phase_k.items()}
-                             if args.profile_all else None),
+        "kernels_by_phase": {ph: kernel_shares(v) for ph, v in phase_k.items()},
+        "kernel_stats_from": "one untimed step with CUDA events around every launch (the last warm-up step)",
         "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
                 "h2d_bytes_per_step": int(ctx.Np * 8 + n * ctx.N),
                 "d2h_bytes_per_step": int(ctx.Np * 8 + n * ctx.N)},
@@ -412,10 +436,84 @@ def run_ours(args):
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, n, args.cpu_samples)
     ctx.close()
+    if rank == 0 and args.largest and args.workload != "j1j2_10":
+        out["largest_workload"] = largest_workload(args, binding, stream, torch, peaks)
     if ws > 1:
         torch.distributed.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def profiled_step(ctx, p, tau, eps, max_cg, tol, n):
+    """One cooling step with CUDA events around every kernel launch: per-kernel sums (launches,
+    ms, algorithmic bytes and flops) over the step and per phase, and the algorithmic flop
+    and Jacobi counters of the sweep and the evaluation."""
+    ctx.profile(True, gemm_only=False)
+    base, phase_k = {}, {"mc_sweep": {}, "eval": {}, "sr_step": {}}
+    ctx.mc_sweep(1, p)
+    mc_flops = ctx.counters()[0]
+    phase_k["mc_sweep"] = kdelta(ctx.profile_read(), base, phase_k["mc_sweep"])
+    ctx.eval_chains()
+    ev_flops, jsw = ctx.counters()
+    phase_k["eval"] = kdelta(ctx.profile_read(), base, phase_k["eval"])
+    ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=p)
+    phase_k["sr_step"] = kdelta(ctx.profile_read(), base, phase_k["sr_step"])
+    ctx.profile(False)
+    total = {}
+    for ph in phase_k.values():
+        for k, v in ph.items():
+            a = total.get(k, (0, 0.0, 0.0, 0.0))
+            total[k] = tuple(x + y for x, y in zip(a, v))
+    return total, phase_k, {"mc_flops": mc_flops, "eval_flops": ev_flops, "jacobi_sweeps": jsw}
+
+
+def largest_workload(args, binding, stream, torch, peaks):
+    """The largest single-GPU workload (10x10 J1-J2 D=6 chi=36, 16384 samples per SR step,
+    TF32) measured within a bounded time: one warm-up step (CUDA events around every launch:
+    kernel shares and roofline), then one timed step.  One step takes minutes on one GPU, so
+    the step counts of the headline line do not apply to it."""
+    from paper_2409_05285_gb300.workloads import WORKLOADS
+    wl = WORKLOADS["j1j2_10"]
+    n = wl.n_samples
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=binding.PEPS_TF32,
+                          init_noise=wl.init_noise, seed=wl.seed, stream=ctypes_stream(stream))
+    tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
+    t0 = time.perf_counter()
+    kstats, phase_k, prof = profiled_step(ctx, 1, tau, eps, max_cg, tol, n)
+    warm_s = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    e = [ev() for _ in range(4)]
+    e[0].record(stream)
+    ctx.mc_sweep(1, 1)
+    e[1].record(stream)
+    ctx.eval_chains()
+    e[2].record(stream)
+    st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=1)
+    e[3].record(stream)
+    e[3].synchronize()
+    ms = e[0].elapsed_time(e[3])
+    roofline, kernels = kernel_roofline(kstats, peaks, binding.PEPS_TF32, binding)
+    fp64 = None
+    if not args.no_fp64_check:
+        fp64 = compare_fp64(ctx, wl, binding, 64, stream, torch)
+    ctx.close()
+    out = {"config": workload_config(wl, n, 1), "dtype": "tf32 (contractions; f32 storage, f64 SR)",
+           "value": n / (ms / 1e3), "unit": "samples/s", "ms_per_step": ms,
+           "sr_steps_per_s": 1e3 / ms, "steps": 1, "warmup": 1, "warmup_s": warm_s,
+           "phase_ms": {"mc_sweep": e[0].elapsed_time(e[1]), "eval": e[1].elapsed_time(e[2]),
+                        "sr_step": e[2].elapsed_time(e[3])},
+           "cg_iters": st["cg_iters"], "E_site": st["E_site"], "beta_obs": st["beta_obs"],
+           "eval_gflop_per_sample": prof["eval_flops"] / n / 1e9,
+           "sweep_gflop_per_sample": prof["mc_flops"] / n / 1e9,
+           "roofline": roofline, "kernels": kernels,
+           "kernels_by_phase": {ph: kernel_shares(v) for ph, v in phase_k.items()},
+           "fp64_check": fp64,
+           "note": "p = 1 sampling from the perturbed beta = 0 state (t < 0.075); one warm-up "
+                   "step of 16384 chains (kernel statistics taken on it) and one timed step"}
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, n, 16)
+    return out
 
 
 def compare_fp64(ctx, wl, binding, m, stream, torch):
@@ -594,8 +692,6 @@ def main():
     ap.add_argument("--precision", default="tf32", choices=["fp32", "tf32", "fp64"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes of the batched engine")
-    ap.add_argument("--profile-all", action="store_true",
-                    help="time every kernel of the timed region (default: the GEMM kernels)")
     ap.add_argument("--chains", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0, help="persistent blocks of the sample kernels (0 = auto)")
     ap.add_argument("--block-mode", default="auto", choices=list(BLOCK_MODES))
@@ -613,7 +709,9 @@ def main():
     ap.add_argument("--su-warmup", type=float, default=0.0,
                     help="start from the simple-update state at this imaginary time (J1 workloads)")
     ap.add_argument("--tune", default="",
-                    help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max")
+                    help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max[,pipelined]")
+    ap.add_argument("--largest", type=int, default=1,
+                    help="also measure the 10x10 D=6 chi=36 workload at 16384 samples (1 warm-up + 1 timed step)")
     ap.add_argument("--launch-bytes", default="",
                     help="write the per-launch algorithmic bytes of kb_gemm_tc in the timed steps to this file")
     args = ap.parse_args()

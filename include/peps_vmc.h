@@ -198,8 +198,8 @@ long long peps_launches(const peps_ctx* ctx);
 /* Autotuner of the batched engine's launch shapes, keyed on the problem geometry (d^2 = 4,
  * D, chi, L1, L2, precision).  peps_autotune times `reps` evaluations of (at most 8192 of)
  * the context's chains per candidate (coordinate descent over the tensor-core grid size,
- * the operand stage count, the contraction chunk, the chains per FFMA block; only the last one without tensor
- * cores) and keeps the fastest; the choice is stored in a process-wide table that later
+ * the operand stage count, the contraction chunk, the tensor-core kernel form, the chains
+ * per FFMA block; only the last one without tensor cores) and keeps the fastest; the choice is stored in a process-wide table that later
  * contexts of the same geometry start from.  No candidate changes any result.  reps = 0
  * only reports the current choice.  With at most 8192 chains the chain buffers hold an
  * evaluation of the current state on return; otherwise evaluate before peps_sr_step.  `out` (caller-owned, may be NULL)
@@ -211,13 +211,14 @@ typedef struct {
   int ffma_g;      /* most chains per block of the FFMA contraction kernel */
   int kc_max;      /* largest contraction chunk of the tensor-core kernel (8, 16, ..., 64) */
   double ms_before, ms_after;
+  int pipelined;   /* 1: short contractions with vector operands take the cp.async-pipelined
+                      tensor-core kernel; 0: every contraction takes the register-staged one */
 } peps_tune;
 int peps_autotune(peps_ctx* ctx, int reps, peps_tune* out);
-/* Sets the batched engine's launch shapes (the first four fields of `t`; the times are
- * ignored) for this context, e.g. to repeat a run with the shapes an earlier autotune chose.
- * No choice changes any result.  EINVAL for values outside grid_pct 1..400, db_bytes
- * 0..200 KB, ffma_g 1..256, kc_max a multiple of 8 in 8..64; ESTATE without the batched
- * engine. */
+/* Sets the batched engine's launch shapes (every field of `t` but the times) for this
+ * context, e.g. to repeat a run with the shapes an earlier autotune chose.  No choice changes
+ * any result.  EINVAL for values outside grid_pct 1..400, db_bytes 0..200 KB, ffma_g 1..256,
+ * kc_max a multiple of 8 in 8..64, pipelined 0..1; ESTATE without the batched engine. */
 int peps_set_tune(peps_ctx* ctx, const peps_tune* t);
 
 /* Simple-update warm start (App. A): from the beta = 0 state, n_steps first-order Trotter

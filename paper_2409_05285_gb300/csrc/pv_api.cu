@@ -536,6 +536,8 @@ int make_batch_t(peps_ctx* c, int sms) {
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kb_gemm_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_gemm_tc2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kb_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kb_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1207,10 +1209,10 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     cur = before;
     // coordinate descent over the launch-shape parameters (results are the same for all)
     const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, kc_c[] = {16, 32, 64},
-              g_c[] = {1, 16, 256};
-    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.ffma_g};
-    const int* cands[] = {grid_c, db_c, kc_c, g_c};
-    for (int knob = c->batch->uses_tensor_cores() ? 0 : 3; knob < 4; ++knob) {
+              p_c[] = {0, 1, 1}, g_c[] = {1, 16, 256};
+    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.pipelined, &tu.ffma_g};
+    const int* cands[] = {grid_c, db_c, kc_c, p_c, g_c};
+    for (int knob = c->batch->uses_tensor_cores() ? 0 : 4; knob < 5; ++knob) {
       int* field = fields[knob];
       const int* cand = cands[knob];
       int best_v = *field;
@@ -1239,6 +1241,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     out->db_bytes = tu.db_bytes;
     out->ffma_g = tu.ffma_g;
     out->kc_max = tu.kc_max;
+    out->pipelined = tu.pipelined;
     out->ms_before = before;
     out->ms_after = cur;
   }
@@ -1334,7 +1337,7 @@ int peps_su_warm_start(peps_ctx* c, double tau, int n_steps) {
 int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   if (!c || !t || t->grid_pct < 1 || t->grid_pct > 400 || t->db_bytes < 0 ||
       t->db_bytes > 200 * 1024 || t->ffma_g < 1 || t->ffma_g > 256 || t->kc_max < 8 ||
-      t->kc_max > 64 || t->kc_max % 8)
+      t->kc_max > 64 || t->kc_max % 8 || t->pipelined < 0 || t->pipelined > 1)
     return fail(c, PEPS_EINVAL, "set_tune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "set_tune: only the batched engine has launch shapes");
   BatchTune& tu = c->batch->tuning();
@@ -1342,6 +1345,7 @@ int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   tu.db_bytes = t->db_bytes;
   tu.ffma_g = t->ffma_g;
   tu.kc_max = t->kc_max;
+  tu.pipelined = t->pipelined;
   return PEPS_OK;
 }
 

@@ -1082,6 +1082,7 @@ inline void bond_lists(int L1, int L2, double J1, double J2, std::vector<int>& b
 }  // namespace pv
 
 #include "pv_tc.cuh"
+#include "pv_tc2.cuh"
 
 #if defined(__CUDACC__)
 #include "pv_prof.cuh"
@@ -1511,6 +1512,8 @@ struct BatchTune {
   int db_bytes = 12 * 1024;    // largest operand stage that gets two stages
   int ffma_g = 256;            // most chains per block of the FFMA GEMM
   int kc_max = 64;             // largest contraction chunk of the tensor-core GEMM
+  int pipelined = 1;           // tensor-core GEMM: the cp.async pipeline (kb_gemm_tc2)
+  int stage_budget = 96 * 1024;   // ... bytes of copy stages per CTA
 };
 
 // Whether two operands address the same values for every chain.
@@ -1569,6 +1572,20 @@ struct CudaBE {
     return (a * (A.mode == OP_BATCH ? n : sites) + b * (B.mode == OP_BATCH ? n : sites) + c * n) *
            sizeof(T);
   }
+  int tc2_regs = 0;
+  int tc2_reg_limit() {
+    if (!tc2_regs) {
+      cudaFuncAttributes fa;
+      int regs = 64;
+      if (cudaFuncGetAttributes(&fa, kb_gemm_tc2) == cudaSuccess && fa.numRegs > 0) regs = fa.numRegs;
+      else cudaGetLastError();
+      regs = (regs + 7) & ~7;
+      int lim = 65536 / (regs * TC_THREADS);
+      lim = lim > 2048 / TC_THREADS ? 2048 / TC_THREADS : lim;
+      tc2_regs = lim < 1 ? 1 : lim;
+    }
+    return tc2_regs;
+  }
   // resident tensor-core GEMM CTAs per SM allowed by registers and threads (cached)
   int tc_by_regs[2] = {0, 0};
   int tc_reg_limit(bool pref) {
@@ -1606,6 +1623,33 @@ struct CudaBE {
         if (t.Kc > tune.kc_max) {   // smaller chunks: smaller stages, more resident CTAs
           t.Kc = tune.kc_max;
           if (t.K > t.Kc) t.pref = 0;
+        }
+        // the pipelined kernel wins (measured at the 10x10 D=6 chi=36 shapes) on short
+        // contractions (K <= 64) whose operands are both vector copies, and on those of at most
+        // 8 indices; element-wise gathers, long and split contractions stay on the
+        // register-staged kernel
+        const bool vec = t.modeP != TC_SCALAR && t.modeQ != TC_SCALAR;
+        if (tune.pipelined && ((vec && !t.split && t.K <= 64) || t.K <= 8)) {
+          // pipelined kernel: cp.async ring of stages over (chain, contraction chunk) items
+          if (t.Kc > tune.kc_max) t.Kc = tune.kc_max;
+          tc2_shape(t, (size_t)tune.stage_budget);
+          const int tilesM = (t.M + TC_ROWS - 1) / TC_ROWS, tilesN = (t.N + t.TN - 1) / t.TN;
+          const size_t bytes = tc2_smem_bytes(t);
+          int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
+          const int by_tmem = 512 / tc_cols(t.TN * t.nacc);
+          const int by_regs = tc2_reg_limit();
+          per_sm = per_sm < by_tmem ? per_sm : by_tmem;
+          per_sm = per_sm < by_regs ? per_sm : by_regs;
+          per_sm = per_sm < 16 ? per_sm : 16;
+          per_sm = per_sm < 1 ? 1 : per_sm;
+          long long gy = (long long)sms * per_sm * tune.grid_pct / (100LL * tilesM * tilesN);
+          gy = gy < 1 ? 1 : (gy > n ? n : gy);
+          gy = gy > 65535 ? 65535 : gy;
+          dim3 gr(tilesM * tilesN, (unsigned)gy);
+          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+                     kb_gemm_tc2<<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A, swap ? A : B, n,
+                                                                tilesN, tc_err));
+          return;
         }
         // stay within the 200 KB of shared memory the kernel is configured for
         const size_t smem_cap = 200 * 1024;

@@ -38,6 +38,8 @@ struct TcSpec {
   int sym;                   // Q is P with the same index maps (C = P P^T, one tile): the B
                              // operand is read from the A stage instead of being gathered
   int no_mma;                // self-test only: issue no MMA and no commit, so every wait runs out
+  int ns;                    // pipelined kernel: shared-memory stages of the copy ring
+  int nacc;                  // pipelined kernel: accumulators in tensor memory (1 or 2)
 };
 
 constexpr int TC_ROWS = 128;
@@ -82,6 +84,8 @@ inline bool tc_plan(const GSpec& g, TcSpec& t, bool& swap, int tc_min_rows = 64)
   t.nst = 1;
   t.sym = 0;
   t.no_mma = 0;
+  t.ns = 2;
+  t.nacc = 1;
   return true;
 }
 

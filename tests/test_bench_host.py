@@ -53,21 +53,29 @@ def test_source_hash_ignores_comments_only():
 
 
 def test_kernel_roofline_arithmetic():
-    # achieved = algorithmic bytes per launch / mean launch time; frac against the measured
-    # HBM copy bandwidth; the dominant kernel is the one with the most event time
+    # the tensor-core contraction: achieved = algorithmic flops per launch / mean launch time,
+    # frac against the TF32 peak (measured sustained BF16 x the nominal TF32/BF16 ratio), with
+    # its HBM view beside it; a kernel with bytes only is HBM-bound; the dominant kernel is the
+    # one with the most event time
     bench = _bench()
 
     class B:
         PEPS_FP64 = 0
 
-    ks = {"kb_gemm_tc": (100, 50.0, 100 * 2.0e8, 0.0), "kb_gemm": (40, 10.0, 40 * 1.0e7, 0.0)}
-    roof, kernels = bench.kernel_roofline(ks, {"hbm_gbs": 6000.0}, 2, B)
-    assert roof["kernel"] == "kb_gemm_tc" and roof["bound"] == "hbm"
-    assert roof["achieved"] == 2.0e8 / 0.5e-3 / 1e9
-    assert roof["frac"] == roof["achieved"] / 6000.0
+    ks = {"kb_gemm_tc": (100, 50.0, 100 * 2.0e8, 100 * 4.0e9), "kb_gemm": (40, 10.0, 40 * 1.0e7, 0.0)}
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1700.0}
+    roof, kernels = bench.kernel_roofline(ks, peaks, 2, B)
+    assert roof["kernel"] == "kb_gemm_tc" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    assert roof["achieved"] == pytest.approx(4.0e9 / 0.5e-3 / 1e12)
+    assert roof["peak"] == pytest.approx(1700.0 * 1.1 / 2.25)
+    assert roof["frac"] == pytest.approx(roof["achieved"] / roof["peak"])
+    assert roof["hbm_view"]["achieved_GB_s"] == pytest.approx(2.0e8 / 0.5e-3 / 1e9)
     assert roof["mean_launch_us"] == 500.0 and roof["launches"] == 100
-    assert abs(roof["share_of_timed_kernels"] - 50.0 / 60.0) < 1e-15
+    assert abs(roof["share_of_kernel_time"] - 50.0 / 60.0) < 1e-15
     assert list(kernels) == ["kb_gemm_tc", "kb_gemm"]
+    ks = {"k_gv": (10, 5.0, 10 * 3.0e9, 0.0)}
+    roof, _ = bench.kernel_roofline(ks, peaks, 2, B)
+    assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(3.0e9 / 0.5e-3 / 1e9)
 
 
 def test_both_arms_share_the_config_object():
@@ -161,8 +169,8 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
             return {"cg_iters": 7, "E_site": -0.05, "beta_obs": 0.56}
 
         def profile_read(self):
-            return {"kb_gemm_tc": (3288, 400.0, 3288 * 2.9584155e8, 0.0),
-                    "kb_gemm": (1221, 40.0, 1221 * 1.0e7, 0.0)}
+            return {"kb_gemm_tc": (3288, 400.0, 3288 * 2.9584155e8, 3288 * 1.0e9),
+                    "kb_gemm": (1221, 40.0, 1221 * 1.0e7, 1221 * 1.0e6)}
 
         def get_theta(self):
             return np.zeros(self.Np)
@@ -201,7 +209,7 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
     monkeypatch.setattr(bench, "Clocks", Clocks)
     monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 6794.1})
     monkeypatch.setattr(_sys, "argv", ["bench.py", "--steps", "2", "--no-cpu-baseline",
-                                       "--no-fp64-check"])
+                                       "--no-fp64-check", "--largest", "1"])
     bench.main()
     out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -212,7 +220,12 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
     assert out["config"]["workload"].startswith("8x8 OBC Heisenberg") and out["unit"] == "samples/s"
     assert out["value"] == pytest.approx(8192 / (out["ms_per_step"] / 1e3))
     roof = out["roofline"]
-    assert roof["kernel"] == "kb_gemm_tc" and roof["peak"] == 6794.1
+    assert roof["kernel"] == "kb_gemm_tc" and roof["bound"] == "tensor"
+    assert roof["hbm_view"]["peak_GB_s"] == 6794.1
+    big = out["largest_workload"]
+    assert "10x10" in big["config"]["workload"] and "chains=16384" in big["config"]["workload"]
+    assert big["value"] == pytest.approx(16384 / (big["ms_per_step"] / 1e3))
+    assert big["roofline"]["bound"] == "tensor"
     if bench.recorded_traffic("heis8", "tf32", 8192, "kb_gemm_tc") is not None:
         assert roof["traffic"] == pytest.approx(0.8903172730497985 * roof["bytes_per_launch"], rel=1e-9)
     assert set(out["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
