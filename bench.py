@@ -291,6 +291,8 @@ def run_ours(args):
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
                           init_noise=wl.init_noise, seed=rank_seed(wl.seed, rank), n_blocks=args.blocks,
                           stream=ctypes_stream(stream), block_mode=BLOCK_MODES[args.block_mode])
+    if args.cg_product:
+        ctx.set_cg_product(args.cg_product)
     t_su = 0.0
     if args.su_warmup > 0:
         # simple-update warm start (host-side, nearest-neighbour bonds) to t = su_warmup
@@ -710,6 +712,8 @@ def main():
                     help="start from the simple-update state at this imaginary time (J1 workloads)")
     ap.add_argument("--tune", default="",
                     help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max[,pipelined]")
+    ap.add_argument("--cg-product", type=int, default=0, choices=[0, 1, 2],
+                    help="CG product form: 0 automatic, 1 fused single read, 2 two passes")
     ap.add_argument("--largest", type=int, default=1,
                     help="also measure the 10x10 D=6 chi=36 workload at 16384 samples (1 warm-up + 1 timed step)")
     ap.add_argument("--launch-bytes", default="",

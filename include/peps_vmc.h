@@ -153,10 +153,10 @@ int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int ma
 /* How peps_sr_step applies (G + eps) in CG (Eq. 10): 1 = one cooperative kernel that reads
  * the O rows once per product (each block owns a slice of the columns; samples are taken in
  * chunks that stay in L2, one grid barrier per chunk); 2 = two streaming passes (O_i.p, then
- * the column sums of y_i O_i); 0 (default) = the fused product when a product needs at most
- * 16 chunks, else the two passes (long rows leave few samples per chunk).  Every choice uses
- * float64 products and fixed summation orders; the results agree to rounding.  EINVAL for
- * other modes. */
+ * the column sums of y_i O_i); 0 (default) = the two passes, measured faster on GB300 at
+ * 8x8 and 10x10 (float64 FMA issue bounds both forms, and the fused one adds a grid barrier
+ * per chunk).  Every choice uses float64 products and fixed summation orders; the results
+ * agree to rounding.  EINVAL for other modes. */
 int peps_set_cg_product(peps_ctx* ctx, int mode);
 
 /* Parameter vector and chain configurations (host buffers).  n must equal N_p, or

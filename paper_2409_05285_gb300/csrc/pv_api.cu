@@ -751,6 +751,9 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
     if (e1 == cudaSuccess)
       e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gv<double, false>, GV_THREADS, gsm);
     if (e1 != cudaSuccess || occ < 1) return bail(fail(c, PEPS_ECUDA, "fused CG product: no resident block"));
+    if (cudaFuncSetAttribute(k_colsum1_f32v<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(32 * SR_THREADS * sizeof(double))) != cudaSuccess)
+      return bail(fail(c, PEPS_ECUDA, "column-sum kernel: shared-memory attribute"));
     c->gv_grid = sms;
     const double elt = fp64(c) ? 8.0 : 4.0;
     const double rows = 48e6 / ((double)c->gv_grid * (double)c->No * elt);
@@ -1059,7 +1062,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
         n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
         c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
   else if (c->o_vec4)
-    PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32v<true><<<cgrid4, SR_THREADS, 0, s>>>(
+    PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 4.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32v<true><<<cgrid4, SR_THREADS, 32 * SR_THREADS * sizeof(double), s>>>(
         n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
         c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
   else
@@ -1078,9 +1081,12 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   PV_CUDA(c, cudaGetLastError());
   PV_CUDA(c, cudaMemsetAsync(c->d_gverr, 0, sizeof(int), s));
   // the fused product reads O once but synchronises the grid once per L2-sized chunk of
-  // samples; with long rows (few rows per chunk) the two streaming passes are faster
+  // samples
   const long long gv_rows = (long long)c->gv_grid * c->gv_rpb;
-  const bool fused = c->cg_mode == 1 || (c->cg_mode == 0 && (n + gv_rows - 1) / gv_rows <= 16);
+  // automatic: the two passes (measured faster at 8x8 and 10x10: float64 issue bounds both
+  // forms, and the fused one adds a grid barrier per chunk)
+  const bool fused = c->cg_mode == 1;
+  (void)gv_rows;
   const int ov_blocks = c->nyb;
   dim3 cgrid_y((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
   dim3 cgrid4_y((unsigned)((No / 4 + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
@@ -1093,7 +1099,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
             c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
       else if (c->o_vec4)
         PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov_f32v<<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
-            c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
+            c->d_o2site, c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
       else
         PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
             c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
@@ -1102,7 +1108,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
             n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
             nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
       else if (c->o_vec4)
-        PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1_f32v<false><<<cgrid4_y, SR_THREADS, 0, s>>>(
+        PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1_f32v<false><<<cgrid4_y, SR_THREADS, 16 * SR_THREADS * sizeof(double), s>>>(
             n, c->N, No, (const float*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
             nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
       else

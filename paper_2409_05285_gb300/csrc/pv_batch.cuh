@@ -1745,7 +1745,10 @@ struct CudaBE {
                kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
-    if (op.tall) {
+    if (op.tall && trunc_g) {
+      // matrices too large for the shared-memory work area of the 256-thread kernel (which
+      // would keep them in global memory): one 1024-thread block per SM holds one in shared
+      // memory; smaller ones keep eight 256-thread blocks per SM
       const size_t wb = (size_t)op.nc * (op.len | 1) * sizeof(T) + (size_t)(op.nc + 4) * (sizeof(T) + sizeof(int)) + 16;
       if (wb <= (size_t)trunc_wide_max) {
         const int grid = n < sms ? n : sms;

@@ -192,7 +192,9 @@ __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restric
 
 // Float rows, 16-byte vectors: every site slice holds a multiple of four entries, so each
 // thread takes four consecutive columns of one site; four rows are loaded before they are
-// accumulated; products and sums in float64.
+// accumulated.  Products and sums in float64, one FMA per entry: the per-state sums live in
+// shared memory, [sum][state][column][thread], and each row adds into the four sums of its
+// state (float64 issue, about 1/60 of float32 on GB300, bounds this pass).
 template <bool TWO>
 __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
@@ -201,24 +203,23 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     const double* __restrict__ c2, const double* __restrict__ shift, double* __restrict__ part1,
     double* __restrict__ part2, long long Np, const int* done) {
   if (done && *done) return;
+  extern __shared__ double cs_acc[];   // [TWO ? 2 : 1][4 states][4 columns][SR_THREADS]
   __shared__ double cx[OTV_CHUNK], cy[OTV_CHUNK];
-  const int ch = blockIdx.y;
+  const int ch = blockIdx.y, tid = threadIdx.x;
   const int i0 = ch * OTV_CHUNK, i1 = min(n, i0 + OTV_CHUNK);
   const double Ebar_shift = TWO ? *shift : 0.0;
-  for (int i = threadIdx.x; i < i1 - i0; i += blockDim.x) {
+  for (int i = tid; i < i1 - i0; i += blockDim.x) {
     cx[i] = c1[i0 + i];
     cy[i] = TWO ? c1[i0 + i] * (c2[i0 + i] - Ebar_shift) : 0.0;
   }
+  for (int e = tid; e < (TWO ? 32 : 16) * SR_THREADS; e += SR_THREADS) cs_acc[e] = 0.0;
   __syncthreads();
-  const long long o = 4 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  const long long o = 4 * ((long long)blockIdx.x * blockDim.x + tid);
   if (o >= No) return;
   const int j = o2site[o];
   const long long k = o - ooff[j], sz = ooff[j + 1] - ooff[j];
-  double a[4][4], b[4][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) a[q][c] = b[q][c] = 0.0;
+  double* A = cs_acc + tid;                       // A[(q * 4 + c) * SR_THREADS]
+  double* B = cs_acc + 16 * SR_THREADS + tid;
   int i = i0;
   for (; i + 4 <= i1; i += 4) {
     float4 v[4];
@@ -230,26 +231,38 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const double x = cx[i + u - i0], y = cy[i + u - i0];
-      const double v0 = v[u].x, v1 = v[u].y, v2 = v[u].z, v3 = v[u].w;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {   // branch-free: the other three states add zero
-        const double xq = st[u] == q ? x : 0.0, yq = st[u] == q ? y : 0.0;
-        a[q][0] += xq * v0; a[q][1] += xq * v1; a[q][2] += xq * v2; a[q][3] += xq * v3;
-        if (TWO) { b[q][0] += yq * v0; b[q][1] += yq * v1; b[q][2] += yq * v2; b[q][3] += yq * v3; }
+      double* a = A + st[u] * 4 * SR_THREADS;
+      const double x = cx[i + u - i0];
+      a[0] += x * v[u].x;
+      a[SR_THREADS] += x * v[u].y;
+      a[2 * SR_THREADS] += x * v[u].z;
+      a[3 * SR_THREADS] += x * v[u].w;
+      if (TWO) {
+        double* b = B + st[u] * 4 * SR_THREADS;
+        const double y = cy[i + u - i0];
+        b[0] += y * v[u].x;
+        b[SR_THREADS] += y * v[u].y;
+        b[2 * SR_THREADS] += y * v[u].z;
+        b[3 * SR_THREADS] += y * v[u].w;
       }
     }
   }
   for (; i < i1; ++i) {
     const float4 v = __ldg((const float4*)(O + (long long)i * No + o));
-    const int sq = S[(long long)i * N + j];
-    const double x = cx[i - i0], y = cy[i - i0];
-    const double v0 = v.x, v1 = v.y, v2 = v.z, v3 = v.w;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const double xq = sq == q ? x : 0.0, yq = sq == q ? y : 0.0;
-      a[q][0] += xq * v0; a[q][1] += xq * v1; a[q][2] += xq * v2; a[q][3] += xq * v3;
-      if (TWO) { b[q][0] += yq * v0; b[q][1] += yq * v1; b[q][2] += yq * v2; b[q][3] += yq * v3; }
+    const int s0 = S[(long long)i * N + j];
+    double* a = A + s0 * 4 * SR_THREADS;
+    const double x = cx[i - i0];
+    a[0] += x * v.x;
+    a[SR_THREADS] += x * v.y;
+    a[2 * SR_THREADS] += x * v.z;
+    a[3 * SR_THREADS] += x * v.w;
+    if (TWO) {
+      double* b = B + s0 * 4 * SR_THREADS;
+      const double y = cy[i - i0];
+      b[0] += y * v.x;
+      b[SR_THREADS] += y * v.y;
+      b[2 * SR_THREADS] += y * v.z;
+      b[3 * SR_THREADS] += y * v.w;
     }
   }
   const long long t = toff[j] + k;
@@ -257,13 +270,13 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) p1[t + q * sz + c] = a[q][c];
+    for (int c = 0; c < 4; ++c) p1[t + q * sz + c] = A[(q * 4 + c) * SR_THREADS];
   if (TWO) {
     double* p2 = part2 + (long long)ch * Np;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) p2[t + q * sz + c] = b[q][c];
+      for (int c = 0; c < 4; ++c) p2[t + q * sz + c] = B[(q * 4 + c) * SR_THREADS];
   }
 }
 
@@ -366,12 +379,14 @@ __global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
 }
 
 // Float rows, 16-byte vectors (site slices of multiples of four entries): y_i = w_i (O_i.p - obar.p),
-// every entry widened to float64.
+// every entry widened to float64.  One warp per sample; the lanes walk the row's 16-byte column
+// groups directly (site and state looked up per group), four groups in flight per lane.
 __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
     int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
-    const long long* __restrict__ toff, const long long* __restrict__ ooff,
-    const double* __restrict__ p, const double* __restrict__ w, double* __restrict__ y,
-    double* __restrict__ ypart, int ndp, const double* __restrict__ dpart, const SRScalars* sc) {
+    const int* __restrict__ o2site, const long long* __restrict__ toff,
+    const long long* __restrict__ ooff, const double* __restrict__ p, const double* __restrict__ w,
+    double* __restrict__ y, double* __restrict__ ypart, int ndp, const double* __restrict__ dpart,
+    const SRScalars* sc) {
   __shared__ double red[32];
   if (sc->done) return;
   double obp = blk_sum_parts(dpart, ndp, red);
@@ -380,26 +395,35 @@ __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
   double yi = 0;
   if (i < n) {
     const float4* row = (const float4*)(O + (long long)i * No);
-    double acc = 0;
-    for (int j = 0; j < N; ++j) {
-      const int s = S[(long long)i * N + j];
-      const long long o0 = ooff[j] >> 2, sz = (ooff[j + 1] - ooff[j]) >> 2;
-      const double2* pv = (const double2*)(p + toff[j] + (long long)s * (sz << 2));
-      double a0 = 0.0, a1 = 0.0;
-      long long kk = lane;
-      for (; kk + 32 < sz; kk += 64) {
-        const float4 r0 = __ldg(row + o0 + kk), r1 = __ldg(row + o0 + kk + 32);
-        const double2 q0 = __ldg(pv + 2 * kk), q1 = __ldg(pv + 2 * kk + 1);
-        const double2 q2 = __ldg(pv + 2 * (kk + 32)), q3 = __ldg(pv + 2 * (kk + 32) + 1);
-        a0 += (double)r0.x * q0.x + (double)r0.y * q0.y + (double)r0.z * q1.x + (double)r0.w * q1.y;
-        a1 += (double)r1.x * q2.x + (double)r1.y * q2.y + (double)r1.z * q3.x + (double)r1.w * q3.y;
+    const uint8_t* Si = S + (long long)i * N;
+    const long long nq = No >> 2;
+    double acc = 0.0;
+    long long q = lane;
+    for (; q + 96 < nq; q += 128) {
+      float4 r[4];
+      const double* pp[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long o = (q + 32 * u) << 2;
+        const int j = o2site[o];
+        const long long o0 = ooff[j];
+        pp[u] = p + toff[j] + (long long)Si[j] * (ooff[j + 1] - o0) + (o - o0);
+        r[u] = __ldg(row + q + 32 * u);
       }
-      if (kk < sz) {
-        const float4 r0 = __ldg(row + o0 + kk);
-        const double2 q0 = __ldg(pv + 2 * kk), q1 = __ldg(pv + 2 * kk + 1);
-        a0 += (double)r0.x * q0.x + (double)r0.y * q0.y + (double)r0.z * q1.x + (double)r0.w * q1.y;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double2 a = __ldg((const double2*)pp[u]), b = __ldg((const double2*)pp[u] + 1);
+        acc += (double)r[u].x * a.x + (double)r[u].y * a.y + (double)r[u].z * b.x + (double)r[u].w * b.y;
       }
-      acc += a0 + a1;
+    }
+    for (; q < nq; q += 32) {
+      const long long o = q << 2;
+      const int j = o2site[o];
+      const long long o0 = ooff[j];
+      const double* pp = p + toff[j] + (long long)Si[j] * (ooff[j + 1] - o0) + (o - o0);
+      const float4 r = __ldg(row + q);
+      const double2 a = __ldg((const double2*)pp), b = __ldg((const double2*)pp + 1);
+      acc += (double)r.x * a.x + (double)r.y * a.y + (double)r.z * b.x + (double)r.w * b.y;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     yi = w[i] * (acc - obp);
@@ -633,13 +657,35 @@ __global__ void __launch_bounds__(GV_THREADS) k_gv(
         const long long t = gv_tidx(o, 0, o2site, toff, ooff, j);
         const long long sz = ooff[j + 1] - ooff[j];
         double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (long long i = cbase + rg; i < cend; i += nrg) {
-          const double v = (double)O[i * No + o] * __ldcg(y + i);
+        long long i = cbase + rg;
+        // eight rows' loads in flight before they are accumulated (the rows come from L2)
+        for (; i + 7LL * nrg < cend; i += 8LL * nrg) {
+          OT v[8];
+          double yy[8];
+          int st[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const long long iu = i + (long long)u * nrg;
+            v[u] = O[iu * No + o];
+            yy[u] = __ldcg(y + iu);
+            st[u] = S[iu * N + j];
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {   // one FMA per entry: the state selects the sum
+            const double vv = (double)v[u];
+            if (st[u] == 0) a0 += vv * yy[u];
+            else if (st[u] == 1) a1 += vv * yy[u];
+            else if (st[u] == 2) a2 += vv * yy[u];
+            else a3 += vv * yy[u];
+          }
+        }
+        for (; i < cend; i += nrg) {
+          const double x = (double)O[i * No + o] * __ldcg(y + i);
           const int st = S[i * N + j];
-          a0 += st == 0 ? v : 0.0;
-          a1 += st == 1 ? v : 0.0;
-          a2 += st == 2 ? v : 0.0;
-          a3 += st == 3 ? v : 0.0;
+          a0 += st == 0 ? x : 0.0;
+          a1 += st == 1 ? x : 0.0;
+          a2 += st == 2 ? x : 0.0;
+          a3 += st == 3 ? x : 0.0;
         }
         if (nrg == 1) {
           q[t] += a0;
