@@ -636,10 +636,33 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def serve_stream(seed, rate, window):
+    """The mixed request stream of the serving workload: Poisson arrivals at `rate` per s over
+    `window` s; per request L in {4, 6, 8, 10, 12}, D in {2, 4, 6}, chi = D^2, J1 = 1,
+    J2 ~ U[0, 0.6], t_end ~ U[0.5, 4] (beta_obs = 4 t_end)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    out, t = [], 0.0
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > window:
+            break
+        L = int(rng.choice([4, 6, 8, 10, 12]))
+        D = int(rng.choice([2, 4, 6]))
+        out.append((t, dict(L1=L, L2=L, D=D, chi=D * D, J2=float(rng.uniform(0.0, 0.6)),
+                            t_end=float(rng.uniform(0.5, 4.0)), seed=int(rng.integers(1 << 30)))))
+    return out
+
+
 def run_serve(args):
-    """Serving loop under a seeded Poisson stream of cooling requests (bounded version of the
-    mixed-request workload: arrivals at `--rate` per s over `--window` s; L in {4, 6, 8},
-    D in {2, 4}, chi = D^2, J1 = 1, J2 ~ U[0, 0.6], t_end ~ U[0.02, 0.1], 1024 chains)."""
+    """Serving loop under the mixed request stream (serve_stream): requests arrive at `--rate`
+    per s over `--window` s and are admitted by device-memory footprint (at most --max-active
+    running, each on its own context and stream); after `--duration` s from the first
+    arrival the server is stopped (queued requests cancelled, running ones end after their
+    current step).  Per-step latency p50/p99 and aggregate samples/s are over every step that
+    finished; a request of this stream runs for tens to hundreds of SR steps of up to seconds
+    each, far beyond a bounded measurement, so most requests are still running or queued when
+    it ends."""
     import numpy as np
     import torch
 
@@ -648,39 +671,49 @@ def run_serve(args):
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
     build()
-    rng = np.random.default_rng(args.seed)
-    arrivals, t = [], 0.0
-    while True:
-        t += rng.exponential(1.0 / args.rate)
-        if t > args.window:
-            break
-        L = int(rng.choice([4, 6, 8]))
-        D = int(rng.choice([2, 4]))
-        arrivals.append((t, dict(L1=L, L2=L, D=D, chi=D * D, n_chains=1024,
-                                 J2=float(rng.uniform(0, 0.6)),
-                                 t_end=0.02 * int(rng.integers(1, 6)),
-                                 seed=int(rng.integers(1 << 30)))))
+    arrivals = serve_stream(args.seed, args.rate, args.window)
     srv = binding.Server(max_active=args.max_active)
     t0 = time.perf_counter()
-    ids = []
+    ids, geo = [], {}
     for ta, kw in arrivals:
         d = ta - (time.perf_counter() - t0)
         if d > 0:
             time.sleep(d)
-        ids.append(srv.submit(precision=binding.PEPS_TF32, **kw))
+        if time.perf_counter() - t0 > args.duration:
+            break
+        rid = srv.submit(precision=binding.PEPS_TF32, n_chains=args.serve_chains, tau=args.serve_tau, **kw)
+        ids.append(rid)
+        geo[rid] = (kw["L1"], kw["D"])
+    rest = args.duration - (time.perf_counter() - t0)
+    if rest > 0:
+        time.sleep(rest)
+    srv.stop()
     srv.drain()
     wall = time.perf_counter() - t0
     m = srv.metrics()
+    states = {}
+    per_geo = {}
+    for rid in ids:
+        st, steps = srv.poll(rid)
+        states[st] = states.get(st, 0) + 1
+        g = "L%d_D%d" % geo[rid]
+        per_geo.setdefault(g, 0)
+        per_geo[g] += len(steps)
     srv.close()
+    names = {binding.PEPS_REQ_DONE: "done", binding.PEPS_REQ_CANCELLED: "cancelled",
+             binding.PEPS_REQ_FAILED: "failed", binding.PEPS_REQ_QUEUED: "queued",
+             binding.PEPS_REQ_RUNNING: "running"}
     out = {"metric": "serving: per-SR-step latency p50/p99 and aggregate samples/s under a "
                      "Poisson stream of cooling requests", "value": m["samples_per_s"],
            "unit": "samples/s", "n_gpus": 1, "latency_ms": {"p50": m["p50_ms"], "p99": m["p99_ms"]},
            "steps": m["steps"], "requests": len(ids), "wall_s": wall, "higher_is_better": True,
-           "dtype": "tf32", "data": "synthetic",
+           "request_states": {names.get(k, str(k)): v for k, v in states.items()},
+           "steps_by_geometry": per_geo, "dtype": "tf32", "data": "synthetic",
            "config": {"workload": f"Poisson arrivals {args.rate}/s over {args.window} s, seed "
-                                  f"{args.seed}; L in {{4,6,8}}, D in {{2,4}}, chi=D^2, J2~U[0,0.6], "
-                                  "t_end in {0.02..0.1}, 1024 chains, tau=0.02",
-                      "max_active": args.max_active}}
+                                  f"{args.seed}; L in {{4,6,8,10,12}}, D in {{2,4,6}}, chi=D^2, "
+                                  f"J1=1, J2~U[0,0.6], t_end~U[0.5,4]; {args.serve_chains} samples "
+                                  f"per SR step, tau={args.serve_tau}",
+                      "max_active": args.max_active, "measured_for_s": args.duration}}
     print(json.dumps(out))
 
 
@@ -704,7 +737,10 @@ def main():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
     ap.add_argument("--rate", type=float, default=20.0)
-    ap.add_argument("--window", type=float, default=1.0)
+    ap.add_argument("--window", type=float, default=10.0, help="serving: arrival window (s)")
+    ap.add_argument("--duration", type=float, default=60.0, help="serving: measured time (s)")
+    ap.add_argument("--serve-chains", type=int, default=1024, help="serving: samples per SR step")
+    ap.add_argument("--serve-tau", type=float, default=0.02, help="serving: imaginary-time step")
     ap.add_argument("--max-active", type=int, default=4)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--fp64-chains", type=int, default=608)

@@ -307,6 +307,7 @@ typedef struct {
 #define PEPS_REQ_RUNNING 1
 #define PEPS_REQ_DONE 2
 #define PEPS_REQ_FAILED 3
+#define PEPS_REQ_CANCELLED 4 /* ended by peps_srv_stop: queued, or after its last finished step */
 
 /* Creates a server.  hbm_budget: device bytes available to admitted requests (0 = 80% of
  * the free memory); max_active: concurrently running requests (>= 1); blocks_per_request:
@@ -323,6 +324,11 @@ int peps_srv_poll(peps_server* srv, int req_id, int* state, int* n_steps, peps_s
 int peps_srv_theta(peps_server* srv, int req_id, double* host, size_t n);
 /* Blocks until every submitted request has finished. */
 int peps_srv_drain(peps_server* srv);
+/* Ends the serving run: requests still queued are cancelled, running ones end after the step
+ * they are in (PEPS_REQ_CANCELLED; their finished steps stay in the statistics and metrics),
+ * and later submissions return PEPS_ESTATE.  Returns at once; peps_srv_drain then waits for
+ * the running steps.  Bounds a measurement under a stream whose requests would outlast it. */
+int peps_srv_stop(peps_server* srv);
 /* Step latency over all finished steps (ms, p50 and p99), aggregate samples/s between the
  * first admission and the last finished step, and the number of steps measured. */
 int peps_srv_metrics(peps_server* srv, double* p50_ms, double* p99_ms, double* samples_per_s,

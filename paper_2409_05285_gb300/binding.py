@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop",
 ]
 
 
@@ -78,7 +78,7 @@ class Request(ctypes.Structure):
                 ("p1_until_beta", ctypes.c_double)]
 
 
-PEPS_REQ_QUEUED, PEPS_REQ_RUNNING, PEPS_REQ_DONE, PEPS_REQ_FAILED = 0, 1, 2, 3
+PEPS_REQ_QUEUED, PEPS_REQ_RUNNING, PEPS_REQ_DONE, PEPS_REQ_FAILED, PEPS_REQ_CANCELLED = 0, 1, 2, 3, 4
 
 _lib = None
 
@@ -126,6 +126,7 @@ def load(path=None):
                                   ctypes.POINTER(Stats), ip]
     lib.peps_srv_theta.argtypes = [vp, ip, vp, ctypes.c_size_t]
     lib.peps_srv_drain.argtypes = [vp]
+    lib.peps_srv_stop.argtypes = [vp]
     lib.peps_srv_metrics.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(dp),
                                      ctypes.POINTER(dp), ctypes.POINTER(ctypes.c_int64)]
     lib.peps_srv_free.argtypes = [vp]
@@ -410,6 +411,12 @@ class Server:
         rc = self.lib.peps_srv_drain(self.srv)
         if rc != PEPS_OK:
             raise PepsError(rc, "a request failed")
+
+    def stop(self):
+        """Cancels queued requests and ends running ones after their current step."""
+        rc = self.lib.peps_srv_stop(self.srv)
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_srv_stop failed")
 
     def metrics(self):
         a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()

@@ -45,6 +45,7 @@ struct peps_server {
   std::vector<double> all_ms;
   long long samples = 0;
   bool started = false;
+  bool stopping = false;   // peps_srv_stop: cancel the queue, end running requests after a step
   Clock::time_point t_first, t_last;
 };
 
@@ -69,6 +70,13 @@ void run_request(peps_server* s, Request* r) {
       state = PEPS_REQ_FAILED;
     double t = 0;
     while (state == PEPS_REQ_DONE && t < q.t_end - 1e-12) {
+      {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->stopping) {
+          state = PEPS_REQ_CANCELLED;
+          break;
+        }
+      }
       int p = (4.0 * t < q.p1_until_beta) ? 1 : 2;
       peps_stats stt{};
       auto t0 = Clock::now();
@@ -110,6 +118,11 @@ void run_request(peps_server* s, Request* r) {
 
 // Admits queued requests while they fit (caller holds the lock).
 void admit(peps_server* s) {
+  if (s->stopping) {
+    for (int id : s->queue) s->reqs[id]->state = PEPS_REQ_CANCELLED;
+    s->queue.clear();
+    return;
+  }
   while (!s->queue.empty() && s->active < s->max_active) {
     Request* r = s->reqs[s->queue.front()].get();
     if (s->used + r->footprint > s->budget) break;   // arrival order: wait for memory
@@ -152,6 +165,10 @@ int peps_srv_create(size_t budget, int max_active, int blocks, peps_server** out
 
 int peps_srv_submit(peps_server* s, const peps_request* q, int* id) {
   if (!s || !q || !id || !(q->tau > 0) || !(q->t_end >= 0) || q->max_cg < 0) return PEPS_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stopping) return PEPS_ESTATE;
+  }
   peps_params P = q->params;
   if (s->blocks > 0 && P.n_blocks == 0) P.n_blocks = s->blocks;
   size_t fp = peps_footprint(&P);
@@ -188,6 +205,15 @@ int peps_srv_theta(peps_server* s, int id, double* host, size_t n) {
   if (it == s->reqs.end() || it->second->state != PEPS_REQ_DONE || it->second->theta.size() != n)
     return PEPS_EINVAL;
   std::copy(it->second->theta.begin(), it->second->theta.end(), host);
+  return PEPS_OK;
+}
+
+int peps_srv_stop(peps_server* s) {
+  if (!s) return PEPS_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->stopping = true;
+  admit(s);   // cancels what is still queued
+  s->cv.notify_all();
   return PEPS_OK;
 }
 

@@ -71,3 +71,28 @@ def test_submit_rejects_invalid_and_oversized_requests():
     with pytest.raises(binding.PepsError):
         srv.submit(8, 8, 4, 16, 4096, t_end=0.02)      # footprint above the budget
     srv.close()
+
+
+def test_stop_cancels_queued_and_ends_running_requests():
+    # a request that would run for many steps and a queue behind it (one slot): stop ends
+    # the running one after a finished step and cancels the queued ones; the finished steps
+    # stay in the statistics, and later submissions are refused
+    import time
+    srv = binding.Server(max_active=1, blocks_per_request=8)
+    long_id = srv.submit(4, 4, 2, 4, 64, t_end=50.0, seed=7)
+    queued = [srv.submit(3, 3, 2, 4, 32, t_end=0.04, seed=8 + k) for k in range(3)]
+    t0 = time.time()
+    while srv.poll(long_id)[0] == binding.PEPS_REQ_RUNNING and len(srv.poll(long_id)[1]) < 2:
+        assert time.time() - t0 < 60
+        time.sleep(0.05)
+    srv.stop()
+    srv.drain()
+    st, steps = srv.poll(long_id)
+    assert st == binding.PEPS_REQ_CANCELLED and 2 <= len(steps) < 2500
+    for rid in queued:
+        assert srv.poll(rid)[0] == binding.PEPS_REQ_CANCELLED
+    m = srv.metrics()
+    assert m["steps"] == len(steps) and m["p50_ms"] > 0
+    with pytest.raises(binding.PepsError):
+        srv.submit(3, 3, 2, 4, 32, t_end=0.04, seed=1)
+    srv.close()
