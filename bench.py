@@ -50,18 +50,31 @@ TF32_OVER_BF16 = 1.1 / 2.25
 # comments excluded).  Once that code changes the entry no longer applies and the bench
 # reports null.
 NCU_TRAFFIC = {
-    ("heis8", "tf32", 8192, "kb_gemm_tc"): {
-        "launches": 200,
-        "dram_bytes": 66987750144,      # DRAM read + write of the first 200 launches of the step
-        "alg_bytes": 75240312832,       # algorithmic bytes of the same 200 launches
-        "sources_sha256": "e8d43633e2acafda7bccf83a7be4e273ee7509167182314757cace304cc7978a",
+    ("heis8", "tf32", "kb_gemm_tc"): {
+        "chains": 2048,
+        "launches": 100,
+        "dram_bytes": 6965e6,           # DRAM read + write of the first 100 launches of the step
+        "alg_bytes": 9975e6,            # algorithmic bytes of the same 100 launches
+        "sources_sha256": "0a7834951acc17bd53fb798cd3adefde3078011f7453a66229223be56b5ce7b5",
         "source": "ncu --profile-from-start off --clock-control none --metrics "
                   "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                  "-k regex:kb_gemm_tc -c 200 (cold cache): the first 200 launches of the timed "
-                  "step with the autotuned shapes 100,12288,16,32, scaled by algorithmic bytes",
+                  "-k regex:kb_gemm_tc -c 100 (cold cache): the first 100 launches of the timed "
+                  "step at 2048 chains (shapes 100,12288,16,16,0), scaled by algorithmic bytes",
+    },
+    ("j1j2_10", "tf32", "kb_gemm_tc"): {
+        "chains": 2048,
+        "launches": 100,
+        "dram_bytes": 156892e6,
+        "alg_bytes": 156946e6,
+        "sources_sha256": "0a7834951acc17bd53fb798cd3adefde3078011f7453a66229223be56b5ce7b5",
+        "source": "ncu --profile-from-start off --clock-control none --metrics "
+                  "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
+                  "-k regex:kb_gemm_tc -c 100 (cold cache): the first 100 launches of the timed "
+                  "step at 2048 chains (default shapes), scaled by algorithmic bytes",
     },
 }
-TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_batch.cuh")
+TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_tc2.cuh",
+                   "paper_2409_05285_gb300/csrc/pv_batch.cuh")
 
 
 def code_text(src):
@@ -82,10 +95,11 @@ def sources_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic(workload, precision, chains, kernel):
-    """The capture recorded for this configuration, or None when there is none or the
-    sources changed since it was taken."""
-    rec = NCU_TRAFFIC.get((workload, precision, chains, kernel))
+def recorded_traffic(workload, precision, kernel):
+    """The capture recorded for this workload and kernel (taken at the chain count it states;
+    the DRAM bytes per algorithmic byte carry over to other chain counts of the same launch
+    shapes), or None when there is none or the sources changed since it was taken."""
+    rec = NCU_TRAFFIC.get((workload, precision, kernel))
     if rec is None or rec["sources_sha256"] != sources_sha256():
         return None
     return rec
@@ -388,7 +402,7 @@ def run_ours(args):
     peaks = measured_peaks()
     roofline, kernels = kernel_roofline(kstats, peaks, prec, binding)
     if roofline is not None:
-        rec = recorded_traffic(args.workload, args.precision, n, roofline["kernel"])
+        rec = recorded_traffic(args.workload, args.precision, roofline["kernel"])
         if rec is not None and roofline.get("bytes_per_launch"):
             roofline["traffic"] = traffic_per_launch(rec, roofline["bytes_per_launch"])
             roofline["traffic_over_algorithmic"] = rec["dram_bytes"] / rec["alg_bytes"]
@@ -418,6 +432,7 @@ def run_ours(args):
         "phase_ms": {"mc_sweep": statistics.mean(mc_ms), "eval": statistics.mean(eval_ms),
                      "sr_step": statistics.mean(sr_ms)},
         "cg_iters": statistics.mean(cg_its),
+        "cg_resid": statistics.mean(st["cg_resid"] for st in stats),
         "sr_step_ms": statistics.mean(sr_ms),
         "eval_gflop_per_sample": prof["eval_flops"] / n / 1e9,
         "sweep_gflop_per_sample": prof["mc_flops"] / n / 1e9,
@@ -496,6 +511,12 @@ def largest_workload(args, binding, stream, torch, peaks):
     e[3].synchronize()
     ms = e[0].elapsed_time(e[3])
     roofline, kernels = kernel_roofline(kstats, peaks, binding.PEPS_TF32, binding)
+    if roofline is not None:
+        rec = recorded_traffic("j1j2_10", "tf32", roofline["kernel"])
+        if rec is not None and roofline.get("bytes_per_launch"):
+            roofline["traffic"] = traffic_per_launch(rec, roofline["bytes_per_launch"])
+            roofline["traffic_over_algorithmic"] = rec["dram_bytes"] / rec["alg_bytes"]
+            roofline["traffic_source"] = rec["source"]
     fp64 = None
     if not args.no_fp64_check:
         fp64 = compare_fp64(ctx, wl, binding, 64, stream, torch)

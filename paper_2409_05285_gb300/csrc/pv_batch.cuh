@@ -1646,7 +1646,7 @@ struct CudaBE {
           gy = gy < 1 ? 1 : (gy > n ? n : gy);
           gy = gy > 65535 ? 65535 : gy;
           dim3 gr(tilesM * tilesN, (unsigned)gy);
-          PV_KLAUNCH(prof, st, "kb_gemm_tc", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
+          PV_KLAUNCH(prof, st, "kb_gemm_tc2", ein_bytes(raw, A, B, n), 2.0 * raw.total * raw.kprod * n,
                      kb_gemm_tc2<<<gr, TC_THREADS, bytes, st>>>(t, out, os, swap ? B : A, swap ? A : B, n,
                                                                 tilesN, tc_err));
           return;

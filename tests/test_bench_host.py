@@ -19,12 +19,12 @@ def _bench():
 
 def test_traffic_needs_matching_sources(monkeypatch):
     bench = _bench()
-    key = ("heis8", "tf32", 8192, "kb_gemm_tc")
+    key = ("heis8", "tf32", "kb_gemm_tc")
     rec = {"dram_bytes": 3.0e9, "alg_bytes": 2.0e9, "sources_sha256": bench.sources_sha256(),
            "source": "test"}
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, rec)
     assert bench.recorded_traffic(*key) is rec
-    assert bench.recorded_traffic("heis8", "tf32", 4096, "kb_gemm_tc") is None
+    assert bench.recorded_traffic("heis8", "tf32", "kb_gemm") is None
     monkeypatch.setitem(bench.NCU_TRAFFIC, key, dict(rec, sources_sha256="0" * 64))
     assert bench.recorded_traffic(*key) is None
 
@@ -38,8 +38,9 @@ def test_traffic_scales_by_algorithmic_bytes():
 def test_recorded_entries_are_well_formed():
     bench = _bench()
     for key, rec in bench.NCU_TRAFFIC.items():
-        assert len(key) == 4 and key[1] in ("fp32", "tf32", "fp64")
+        assert len(key) == 3 and key[1] in ("fp32", "tf32", "fp64")
         assert rec["dram_bytes"] > 0 and rec["alg_bytes"] > 0 and rec["launches"] > 0
+        assert rec["chains"] > 0
         assert len(rec["sources_sha256"]) == 64 and rec["source"]
 
 
@@ -147,7 +148,7 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
 
         def step(self, **kw):
             self.k += 30
-            return {"cg_iters": 5, "E_site": -0.1, "beta_obs": 0.1}
+            return {"cg_iters": 5, "E_site": -0.1, "beta_obs": 0.1, "cg_resid": 1e-3}
 
         def autotune(self, reps=1):
             return {"grid_pct": 100, "db_bytes": 12288, "ffma_g": 16, "kc_max": 32,
@@ -166,7 +167,7 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
             self.k += 20
 
         def sr_step(self, tau, eps, max_cg, cg_tol, p):
-            return {"cg_iters": 7, "E_site": -0.05, "beta_obs": 0.56}
+            return {"cg_iters": 7, "E_site": -0.05, "beta_obs": 0.56, "cg_resid": 1e-3}
 
         def profile_read(self):
             return {"kb_gemm_tc": (3288, 400.0, 3288 * 2.9584155e8, 3288 * 1.0e9),
@@ -226,7 +227,8 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
     assert "10x10" in big["config"]["workload"] and "chains=16384" in big["config"]["workload"]
     assert big["value"] == pytest.approx(16384 / (big["ms_per_step"] / 1e3))
     assert big["roofline"]["bound"] == "tensor"
-    if bench.recorded_traffic("heis8", "tf32", 8192, "kb_gemm_tc") is not None:
-        assert roof["traffic"] == pytest.approx(0.8903172730497985 * roof["bytes_per_launch"], rel=1e-9)
+    rec = bench.recorded_traffic("heis8", "tf32", "kb_gemm_tc")
+    if rec is not None:
+        assert roof["traffic"] == pytest.approx(rec["dram_bytes"] / rec["alg_bytes"] * roof["bytes_per_launch"], rel=1e-9)
     assert set(out["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert out["gpu_launches"] > 0
