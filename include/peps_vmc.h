@@ -246,6 +246,15 @@ int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, dou
  * EINVAL for bad arguments or J2 != 0; ENOMEM, ECUDA on device failures. */
 int peps_su_warm_start(peps_ctx* ctx, double tau, int n_steps);
 
+/* Specific heat per site from an energy curve (Sec. III.A: C_v from the derivative of a
+ * spline through E against beta): fits a natural cubic smoothing spline to the n points
+ * (beta[k], E_site[k]) (any order, distinct beta, n >= 3) whose residual sum of squares is at
+ * most `smoothing` (0 interpolates; with independent errors sigma per point, n sigma^2 is the
+ * usual choice) and writes C/N = -beta^2 dE/dbeta of the spline at the m points beta_eval to
+ * cv (caller-owned).  Host code; no context or GPU is needed.  EINVAL for bad arguments. */
+int peps_cv_spline(const double* beta, const double* E_site, int n, double smoothing,
+                   const double* beta_eval, double* cv, int m);
+
 /* Per-kernel statistics for roofline reports.  peps_profile(ctx, 1) clears them and starts
  * bracketing every launch of the context with CUDA events on its stream; peps_profile(ctx,
  * 2) does the same for the batched GEMM kernels only (kb_gemm_tc, kb_gemm: fewer events in

@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline",
 ]
 
 
@@ -145,6 +145,7 @@ def load(path=None):
     lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
     lib.peps_su_warm_start.argtypes = [vp, dp, ip]
     lib.peps_set_cg_product.argtypes = [vp, ip]
+    lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
     lib.peps_su_theta.argtypes = [ip, ip, ip, dp, dp, ip, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_size_t]
     lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -182,6 +183,20 @@ def _ptr(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def cv_spline(betas, E_site, beta_eval, smoothing=0.0):
+    """C/N = -beta^2 dE/dbeta from a natural cubic smoothing spline through (betas, E_site)
+    (peps_cv_spline; smoothing bounds the residual sum of squares, 0 interpolates)."""
+    b = np.ascontiguousarray(betas, dtype=np.float64)
+    e = np.ascontiguousarray(E_site, dtype=np.float64)
+    q = np.ascontiguousarray(np.atleast_1d(beta_eval), dtype=np.float64)
+    out = np.empty(q.size, np.float64)
+    rc = load().peps_cv_spline(_ptr(b), _ptr(e), int(b.size), float(smoothing), _ptr(q), _ptr(out),
+                               int(q.size))
+    if rc != PEPS_OK:
+        raise PepsError(rc, "peps_cv_spline failed")
+    return out
 
 
 class Context:
