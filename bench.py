@@ -307,6 +307,8 @@ def run_ours(args):
                           stream=ctypes_stream(stream), block_mode=BLOCK_MODES[args.block_mode])
     if args.cg_product:
         ctx.set_cg_product(args.cg_product)
+    if args.graphs and args.block_mode in ("auto", "batched"):
+        ctx.set_graphs(True)   # the sweep's and the evaluation's launch sequences as graphs
     t_su = 0.0
     if args.su_warmup > 0:
         # simple-update warm start (host-side, nearest-neighbour bonds) to t = su_warmup
@@ -495,6 +497,8 @@ def largest_workload(args, binding, stream, torch, peaks):
     ev = lambda: torch.cuda.Event(enable_timing=True)
     ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=binding.PEPS_TF32,
                           init_noise=wl.init_noise, seed=wl.seed, stream=ctypes_stream(stream))
+    if args.graphs:
+        ctx.set_graphs(True)
     tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
     t0 = time.perf_counter()
     kstats, phase_k, prof = profiled_step(ctx, 1, tau, eps, max_cg, tol, n)
@@ -771,6 +775,8 @@ def main():
                     help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max[,pipelined]")
     ap.add_argument("--cg-product", type=int, default=0, choices=[0, 1, 2],
                     help="CG product form: 0 automatic, 1 fused single read, 2 two passes")
+    ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
+                    help="replay the batched engine's launch sequences as CUDA graphs")
     ap.add_argument("--largest", type=int, default=1,
                     help="also measure the 10x10 D=6 chi=36 workload at 16384 samples (1 warm-up + 1 timed step)")
     ap.add_argument("--launch-bytes", default="",

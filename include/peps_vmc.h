@@ -150,6 +150,21 @@ int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
 int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
               double cg_tol, peps_stats* stats);
 
+/* CUDA graphs for the batched engine (enable = 1; 0 = direct launches, the default): the
+ * launch sequence of a Metropolis sweep (per exponent p) and of an evaluation of the chains
+ * (per use of the sweep's cached environments) is captured into a graph on first use and
+ * replayed on later calls, one graph per chunk of chains; the sweep number reaches the
+ * kernels through device memory, so replays draw the same random numbers as direct launches
+ * and every result is the same bits.  Replays skip the host's per-launch work, which counts
+ * for small problems.  Per-launch profiling (peps_profile) and autotuning run without them;
+ * changing the launch shapes discards the captured graphs.  EINVAL for bad arguments, ESTATE
+ * without the batched engine. */
+int peps_set_graphs(peps_ctx* ctx, int enable);
+/* Number of launch sequences captured so far (0 with graphs off, without the batched engine,
+ * or when capture is not possible on the context's stream, e.g. the legacy default stream,
+ * where the engine launches directly). */
+int peps_graphs_captured(const peps_ctx* ctx);
+
 /* How peps_sr_step applies (G + eps) in CG (Eq. 10): 1 = one cooperative kernel that reads
  * the O rows once per product (each block owns a slice of the columns; samples are taken in
  * chunks that stay in L2, one grid barrier per chunk); 2 = two streaming passes (O_i.p, then

@@ -38,7 +38,7 @@ EXPORTS = [
     "peps_restore", "peps_time", "peps_eval_batch_noalloc", "peps_footprint",
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
-    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline",
+    "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline", "peps_set_graphs", "peps_graphs_captured",
 ]
 
 
@@ -145,6 +145,8 @@ def load(path=None):
     lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
     lib.peps_su_warm_start.argtypes = [vp, dp, ip]
     lib.peps_set_cg_product.argtypes = [vp, ip]
+    lib.peps_set_graphs.argtypes = [vp, ip]
+    lib.peps_graphs_captured.argtypes = [vp]
     lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
     lib.peps_su_theta.argtypes = [ip, ip, ip, dp, dp, ip, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_size_t]
@@ -362,6 +364,13 @@ class Context:
         d = st.as_dict()
         d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
         return d
+
+    def set_graphs(self, on):
+        """Captures and replays the batched engine's launch sequences (peps_set_graphs)."""
+        self._check(self.lib.peps_set_graphs(self.ctx, 1 if on else 0))
+
+    def graphs_captured(self):
+        return int(self.lib.peps_graphs_captured(self.ctx))
 
     def set_cg_product(self, mode):
         """CG product form (peps_set_cg_product): 0 automatic, 1 fused single read, 2 two passes."""

@@ -19,6 +19,7 @@
 #include <memory>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <array>
 
 using namespace pv;
@@ -33,6 +34,10 @@ constexpr float JTOL_F32 = 2e-7f;
 constexpr int JAC_MAX_SWEEPS = 60;
 
 // ------------------------------------------------------------------ sample kernels
+
+// The Metropolis sweep number the batched engine's accept kernels read (set before every
+// sweep, outside any captured graph).
+__global__ void k_set_sweep(uint32_t* d, uint32_t v) { *d = v; }
 
 // Initial parameters: the beta = 0 state with its zero entries perturbed (App. A):
 // entry t = noise (2u - 1), u = Philox(seed; t lo, t hi, 0, TAG_INIT); the [0,0,0,0]
@@ -226,6 +231,10 @@ struct BatchIface {
   virtual int* err_flag() = 0;
   virtual BatchTune& tuning() = 0;
   virtual bool uses_tensor_cores() const = 0;
+  virtual void set_graphs(bool on) = 0;   // capture and replay the launch sequences
+  virtual bool graphs_on() const = 0;
+  virtual int graphs_captured() const = 0;
+  virtual void drop_graphs() = 0;         // launch shapes changed: recapture on next use
   virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
@@ -241,30 +250,106 @@ struct BatchImpl : BatchIface {
   int N = 0;
   long long No = 0;
   double *es_tmp = nullptr, *ea_tmp = nullptr;
+  uint32_t* d_sweep = nullptr;   // the sweep number the accept kernels read
+  // CUDA graphs: one captured launch sequence per (operation, exponent or cache use, chunk,
+  // buffers), replayed on later calls; its flops and launch count are those of the capture
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    double flops = 0;
+    long long launches = 0;
+  };
+  bool graphs = false;
+  std::map<std::tuple<int, int, long long, const void*, const void*>, Graph> gcache;
   BatchImpl() : run(be) {}
+  ~BatchImpl() override { drop_graphs(); }
   int* err_flag() override { return be.tc_err; }
   BatchTune& tuning() override { return be.tune; }
   bool uses_tensor_cores() const override { return be.tc; }
+  void set_graphs(bool on) override {
+    if (!on) drop_graphs();
+    graphs = on;
+  }
+  bool graphs_on() const override { return graphs; }
+  int graphs_captured() const override { return (int)gcache.size(); }
+  void drop_graphs() override {
+    for (auto& kv : gcache)
+      if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    gcache.clear();
+  }
+
+  // Runs fn's launch sequence on the engine's stream: directly, or (graphs on, no per-launch
+  // profiling) from a graph captured on first use.  A capture that fails leaves graphs off.
+  template <typename F>
+  void launch(const std::tuple<int, int, long long, const void*, const void*>& key, F&& fn) {
+    if (!graphs || (be.prof && be.prof->on)) {
+      fn();
+      return;
+    }
+    auto it = gcache.find(key);
+    if (it == gcache.end()) {
+      const double f0 = run.flops;
+      const long long l0 = be.prof ? be.prof->launches : 0;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamBeginCapture(be.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        graphs = false;
+        fn();
+        return;
+      }
+      fn();
+      Graph rec;
+      cudaError_t e = cudaStreamEndCapture(be.st, &g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&rec.exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        // nothing ran: run the sequence directly and stay without graphs
+        cudaGetLastError();
+        graphs = false;
+        run.flops = f0;
+        if (be.prof) be.prof->launches = l0;
+        fn();
+        return;
+      }
+      rec.flops = run.flops - f0;
+      rec.launches = be.prof ? be.prof->launches - l0 : 0;
+      it = gcache.emplace(key, rec).first;
+      run.flops = f0;
+      if (be.prof) be.prof->launches = l0;
+    }
+    cudaGraphLaunch(it->second.exec, be.st);
+    run.flops += it->second.flops;
+    if (be.prof) be.prof->launches += it->second.launches;
+  }
 
   void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
             bool cached) override {
     run.flops = 0;
     for (int off = 0; off < nb; off += chunk) {
       int n = std::min(chunk, nb - off);
-      run.eval(S + (long long)off * N, n, la ? la + off : nullptr, sg ? sg + off : nullptr,
-               es ? es + off : es_tmp, ea ? ea + off : ea_tmp,
-               O ? (T*)O + (long long)off * No : nullptr, No, cached && nb <= chunk);
+      const bool cu = cached && nb <= chunk;
+      launch(std::make_tuple(0, cu ? 1 : 0, (long long)off, (const void*)S, (const void*)O),
+             [&]() {
+               run.eval(S + (long long)off * N, n, la ? la + off : nullptr, sg ? sg + off : nullptr,
+                        es ? es + off : es_tmp, ea ? ea + off : ea_tmp,
+                        O ? (T*)O + (long long)off * No : nullptr, No, cu);
+             });
     }
     flops = run.flops;
   }
   void mc(uint8_t* S, int n_all, int p, uint64_t seed, long long sweep0, int n_sweeps, int* acc,
           int* prop) override {
     run.flops = 0;
+    run.sweep_dev = d_sweep;
     for (int off = 0; off < n_all; off += chunk) {
       int n = std::min(chunk, n_all - off);
-      for (int k = 0; k < n_sweeps; ++k)
-        run.mc(S + (long long)off * N, n, p, seed, off, (uint32_t)(sweep0 + k), acc + off,
-               prop + off);
+      for (int k = 0; k < n_sweeps; ++k) {
+        k_set_sweep<<<1, 1, 0, be.st>>>(d_sweep, (uint32_t)(sweep0 + k));
+        if (be.prof) be.prof->launches += 1;
+        launch(std::make_tuple(1, p, (long long)off, (const void*)S, (const void*)acc), [&]() {
+          run.mc(S + (long long)off * N, n, p, seed, off, (uint32_t)(sweep0 + k), acc + off,
+                 prop + off);
+        });
+      }
     }
     flops = run.flops;
   }
@@ -483,6 +568,7 @@ int make_batch_t(peps_ctx* c, int sms) {
   if ((rc = dalloc(c, &i8, (size_t)n8 * chunk))) return rc;
   if ((rc = dalloc(c, &dbl, (size_t)nd * chunk * sizeof(double)))) return rc;
   if ((rc = dalloc(c, &b->es_tmp, (size_t)chunk * sizeof(double)))) return rc;
+  if ((rc = dalloc(c, &b->d_sweep, sizeof(uint32_t)))) return rc;
   if ((rc = dalloc(c, &b->ea_tmp, (size_t)chunk * sizeof(double)))) return rc;
   std::vector<int> bi, bj;
   std::vector<double> bJ;
@@ -1186,6 +1272,15 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
   if (!c || reps < 0) return fail(c, PEPS_EINVAL, "autotune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "autotune: only the batched engine has launch shapes to tune");
   BatchTune& tu = c->batch->tuning();
+  // every candidate is timed with direct launches (a graph would replay the shapes it was
+  // captured with)
+  const bool had_graphs = c->batch->graphs_on();
+  c->batch->set_graphs(false);
+  struct Restore {
+    peps_ctx* c;
+    bool on;
+    ~Restore() { c->batch->set_graphs(on); }
+  } restore{c, had_graphs};
   // time on at most 8192 chains: the best shapes depend on the chain count (a 2048-chain
   // subset picked one chain per FFMA block, which is slower at 8192 chains)
   const int n = c->P.n_chains < 8192 ? c->P.n_chains : 8192;
@@ -1237,6 +1332,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
         *field = best_v;
       }
     }
+    c->batch->drop_graphs();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[tune_key(&c->P)] = tu;
     c->have_eval = n == c->P.n_chains;   // all chains evaluated for the current state
@@ -1268,6 +1364,17 @@ int peps_su_theta(int L1, int L2, int D, double J1, double tau, int n_steps, dou
   for (int k = 0; k < n_steps; ++k) su.step(tau);
   su.theta(theta);
   return PEPS_OK;
+}
+
+int peps_set_graphs(peps_ctx* c, int enable) {
+  if (!c || enable < 0 || enable > 1) return fail(c, PEPS_EINVAL, "set_graphs: args");
+  if (!c->batch) return fail(c, PEPS_ESTATE, "set_graphs: only the batched engine captures graphs");
+  c->batch->set_graphs(enable != 0);
+  return PEPS_OK;
+}
+
+int peps_graphs_captured(const peps_ctx* c) {
+  return (c && c->batch) ? c->batch->graphs_captured() : 0;
 }
 
 int peps_set_cg_product(peps_ctx* c, int mode) {
@@ -1352,6 +1459,7 @@ int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   tu.ffma_g = t->ffma_g;
   tu.kc_max = t->kc_max;
   tu.pipelined = t->pipelined;
+  c->batch->drop_graphs();   // the captured sequences used the old shapes
   return PEPS_OK;
 }
 

@@ -544,10 +544,12 @@ struct ElemAccept {
   uint32_t sweep, id;
   int *acc, *prop;
   int8_t* accepted;
+  const uint32_t* sweep_dev;   // when set, the sweep number is read here (graph replays)
   PV_HD void operator()(int s) const {
     accepted[s] = 0;
     if (!valid[s]) return;
-    double u = philox_uniform(seed, (uint32_t)(chain0 + s), sweep, id, TAG_MC);
+    const uint32_t sw = sweep_dev ? *sweep_dev : sweep;
+    double u = philox_uniform(seed, (uint32_t)(chain0 + s), sw, id, TAG_MC);
     double ratio = (double)num[s] / (double)den[s];
     double q = p == 2 ? ratio * ratio : (ratio < 0 ? -ratio : ratio);
     prop[s] += 1;
@@ -659,6 +661,7 @@ struct BatchRunner {
   int max_sweeps;
   double flops = 0;
   bool gram_lq = false;   // right factors from the Gram matrix (the TF32 path)
+  const uint32_t* sweep_dev = nullptr;   // Metropolis sweep number in device memory, if set
   unsigned long long* sweeps;   // Jacobi sweep counter (device or host)
 
   BatchRunner(BE& be_) : be(be_) {}
@@ -991,7 +994,7 @@ struct BatchRunner {
         s1_left(r, c, b.m2, b.P2, bat(Lc, b.sp1L), site_sel(r, c, b.si), n);
         be.dot(OpDot<T>{b.m2, b.P2, p1R(c + 1), b.sp1R, s1_len(r, c + 1), b.num}, n);
         be.accept(ElemAccept<T>{S, N, i, -1, b.si, b.sj, b.valid, b.num, b.den, p, seed, chain0,
-                                sweep, (uint32_t)(8 * i), acc, prop, b.accepted}, n);
+                                sweep, (uint32_t)(8 * i), acc, prop, b.accepted, sweep_dev}, n);
         be.copy_masked(b.m0, b.P2, b.m2, b.P2, s1_len(r, c + 1), b.accepted, n);
         if (c + 1 < L2) {
           s1_left(r, c + 1, b.m1, b.P2, bat(b.m0, b.P2), site(r, c + 1, S), n);
@@ -1003,7 +1006,7 @@ struct BatchRunner {
             be.dot(OpDot<T>{b.m3, b.P2, p1R(c + 2), b.sp1R, s1_len(r, c + 2), b.num}, n);
             be.accept(ElemAccept<T>{S, N, i, i + 1, b.si, b.sj, b.valid, b.num, b.den, p, seed,
                                     chain0, sweep, (uint32_t)(8 * i + 1 + layer), acc, prop,
-                                    b.accepted}, n);
+                                    b.accepted, sweep_dev}, n);
             be.copy_masked(b.m0, b.P2, b.m2, b.P2, s1_len(r, c + 1), b.accepted, n);
             be.copy_masked(b.m1, b.P2, b.m3, b.P2, s1_len(r, c + 2), b.accepted, n);
           }
@@ -1031,7 +1034,7 @@ struct BatchRunner {
             s2_left(r, c, b.m1, b.P2, bat(L2c, b.sp2L), site_sel(r, c, b.si), site_sel(r + 1, c, b.sj), n);
             be.dot(OpDot<T>{b.m1, b.P2, p2R(c + 1), b.sp2R, s2_len(r, c + 1), b.num}, n);
             be.accept(ElemAccept<T>{S, N, i, j, b.si, b.sj, b.valid, b.num, b.den, p, seed, chain0,
-                                    sweep, (uint32_t)(8 * i + 3 + layer), acc, prop, b.accepted}, n);
+                                    sweep, (uint32_t)(8 * i + 3 + layer), acc, prop, b.accepted, sweep_dev}, n);
             be.copy_masked(b.m0, b.P2, b.m1, b.P2, s2_len(r, c + 1), b.accepted, n);
           }
           be.copy_masked(L2n, b.sp2L, b.m0, b.P2, s2_len(r, c + 1), nullptr, n);

@@ -65,6 +65,9 @@ void run_request(peps_server* s, Request* r) {
       peps_init(&P, st, &ctx) != PEPS_OK) {
     state = PEPS_REQ_FAILED;
   } else {
+    // small requests spend much of a step in host-side launch work: replay captured graphs
+    // (batched engine only; the per-block engine launches one kernel per phase anyway)
+    peps_set_graphs(ctx, 1);
     const peps_request& q = r->req;
     if (q.n_burn > 0 && peps_mc_sweep(ctx, q.n_burn, q.p1_until_beta > 0.0 ? 1 : 2) < 0)
       state = PEPS_REQ_FAILED;

@@ -157,6 +157,9 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
         def profile(self, on, gemm_only=False):
             pass
 
+        def set_graphs(self, on):
+            pass
+
         def launches(self):
             return self.k
 
