@@ -108,7 +108,7 @@ typedef struct {
   double diag_frac; /* fraction of samples with s = s' on every site */
   int cg_iters;     /* CG iterations of the last peps_sr_step */
   double cg_resid;  /* |r| / |g| at exit */
-  int p;            /* sampling exponent of the samples (2 or 1) */
+  int p;            /* sampling exponent of the samples (2 or 1; 0 for direct draws) */
 } peps_stats;
 
 /* Creates a context: allocates device buffers, sets theta to the perturbed beta = 0
@@ -135,7 +135,9 @@ int peps_eval_batch(peps_ctx* ctx, const uint8_t* S, int nb, int on_device, doub
                     int8_t* sign, double* e_sys, double* e_anc, void* O);
 
 /* One SR update from the last evaluation of the chains (sampled with exponent p):
- * weights (1/n for p = 2, |rho|/sum|rho| for p = 1), g = <O (E_loc - <E_loc>)>, CG solve
+ * weights (1/n for p = 2, |rho|/sum|rho| for p = 1, and for p = 0, chains that are the last
+ * peps_direct_draw, r_4/sum r_4 with r_4 = |rho|^2/q of App. A Eq. A7; ESTATE when p = 0
+ * and the chains or theta changed since that draw), g = <O (E_loc - <E_loc>)>, CG solve
  * of (G + eps I) x = g from x = 0 with the relative-residual test tol before each
  * iteration and at most max_cg iterations, theta -= tau x, t += tau.  stats (may be
  * NULL) receives the observables of those samples and the CG result.  Returns
@@ -143,12 +145,45 @@ int peps_eval_batch(peps_ctx* ctx, const uint8_t* S, int nb, int on_device, doub
 int peps_sr_step(peps_ctx* ctx, double tau, double eps, int max_cg, double cg_tol, int p,
                  peps_stats* stats);
 
-/* Observables of the last evaluation of the chains (sampled with exponent p). */
+/* Observables of the last evaluation of the chains (sampled with exponent p; p = 0 as in
+ * peps_sr_step). */
 int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
 
 /* One whole cooling step: n_sweeps sweeps, evaluation of the chains, SR update. */
 int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
               double cg_tol, peps_stats* stats);
+
+/* Reweighted direct sampling (App. A, Eqs. A2-A7): replaces every chain by an independent
+ * draw.  Sites are drawn one after another in row-major order; site i takes its local state
+ * s from p_4c(s) = b(s) p_2c(s)^exponent normalised over the four states, p_2c (Eq. A3) the
+ * conditional weight of s given the sites drawn before, b(s) = b_d for s = s' (S = 0, 3) and
+ * 1 otherwise (Eq. A5); exponent 1/2 is Eq. A4, exponent 1 with b_d = 1 is plain direct
+ * sampling (q = |rho|^2 / sum |rho|^2 up to truncation).  The sums of rho^2 over the sites
+ * not yet drawn are boundary-MPS contractions of the double-layer network (bond D^2, per site
+ * T^S (x) T^S or its sum over S) at the context's chi; candidate weights that truncation
+ * leaves negative count as zero.
+ *   u          uniforms [n_chains][L1*L2] in [0, 1): site i of chain k picks the first state
+ *              whose cumulative probability exceeds u[k][i] (values outside clamp to the
+ *              ends).  NULL: drawn from Philox with the context's seed, a new stream per call.
+ *   on_device  u and log_q are device pointers (else host).
+ *   b_d        in (0, 1];  exponent > 0.
+ *   log_q      [n_chains] (may be NULL): log of the probability q of each draw.
+ * The context keeps log q for peps_sr_step / peps_observables with p = 0.  Needs the batched
+ * engine (ESTATE otherwise); the first call allocates the double-layer runner (ENOMEM when it
+ * does not fit). */
+int peps_direct_draw(peps_ctx* ctx, const double* u, int on_device, double b_d, double exponent,
+                     double* log_q);
+
+/* The diagonal bias after a step whose samples held the fraction diag_frac of diagonal terms
+ * (s = s' on every site, peps_stats.diag_frac): b_d (1/2 / diag_frac)^(1/N) when diag_frac
+ * exceeds 1/2 (the diagonal fraction scales as b_d^N), else b_d; never above 1. */
+double peps_direct_next_bd(double b_d, double diag_frac, int N);
+
+/* One cooling step on direct samples: peps_direct_draw (Philox uniforms) with *b_d and
+ * exponent, evaluation of the chains, peps_sr_step with p = 0; then *b_d =
+ * peps_direct_next_bd(*b_d, stats diag_frac, L1*L2). */
+int peps_direct_step(peps_ctx* ctx, double* b_d, double exponent, double tau, double eps,
+                     int max_cg, double cg_tol, peps_stats* stats);
 
 /* CUDA graphs for the batched engine (enable = 1; 0 = direct launches, the default): the
  * launch sequence of a Metropolis sweep (per exponent p) and of an evaluation of the chains

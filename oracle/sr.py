@@ -4,6 +4,8 @@ TEST INFRASTRUCTURE (oracle): see oracle/__init__.py.
 
   weights   p = 2 (samples of |rho|^2): w_i = 1/N_s.
             p = 1 (samples of |rho|, Eq. A1): w_i = r_1(S_i) / sum_j r_1(S_j), r_1 = |rho|.
+            p = 0 (direct draws of probability q, App. A Eq. A7): w_i = r_4(S_i) / sum_j
+            r_4(S_j), r_4 = p_0 / q = |rho|^2 / q (oracle/direct.py, first reading).
   metric    G_kk' = <O_k O_k'> - <O_k><O_k'> (Eq. 6), written for samples as Eq. 10.
   gradient  g_k = <O_k E_loc> - <O_k><E_loc> (Eq. 7), E_loc the full calH local energy.
   solve     (G + eps I) x = g by conjugate gradient, x_0 = 0; G is applied as two passes
@@ -15,11 +17,15 @@ All vectors here live in the full parameter space (the compressed O rows are exp
 import numpy as np
 
 
-def weights(log_abs, p):
+def weights(log_abs, p, log_q=None):
     log_abs = np.asarray(log_abs, dtype=np.float64)
     n = log_abs.shape[0]
     if p == 2:
         return np.full(n, 1.0 / n)
+    if p == 0:
+        lr = 2.0 * log_abs - np.asarray(log_q, dtype=np.float64)
+        r4 = np.exp(lr - np.max(lr))
+        return r4 / np.sum(r4)
     r1 = np.exp(log_abs - np.max(log_abs))
     return r1 / np.sum(r1)
 
@@ -76,9 +82,11 @@ def cg(apply, b, tol, maxit):
     return x, it, (np.sqrt(rr) / bnorm if bnorm > 0 else 0.0)
 
 
-def sr_step(lat, theta, S_batch, log_abs, e_sys, e_anc, O_rows, p, tau, eps, tol, maxit):
-    """One SR update.  Returns (theta', x, g, cg iterations, relative residual)."""
-    w = weights(log_abs, p)
+def sr_step(lat, theta, S_batch, log_abs, e_sys, e_anc, O_rows, p, tau, eps, tol, maxit,
+            log_q=None):
+    """One SR update (p = 0: direct draws with log q given).  Returns (theta', x, g, cg
+    iterations, relative residual)."""
+    w = weights(log_abs, p, log_q)
     E = np.asarray(e_sys) + np.asarray(e_anc)
     Of = expand_O(lat, S_batch, O_rows)
     obar, _, g = sr_quantities(Of, w, E)

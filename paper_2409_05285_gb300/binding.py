@@ -39,6 +39,7 @@ EXPORTS = [
     "peps_srv_create", "peps_srv_submit", "peps_srv_poll", "peps_srv_theta", "peps_srv_drain",
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
     "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline", "peps_set_graphs", "peps_graphs_captured",
+    "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
 ]
 
 
@@ -148,6 +149,11 @@ def load(path=None):
     lib.peps_set_graphs.argtypes = [vp, ip]
     lib.peps_graphs_captured.argtypes = [vp]
     lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
+    lib.peps_direct_draw.argtypes = [vp, vp, ip, dp, dp, vp]
+    lib.peps_direct_next_bd.argtypes = [dp, dp, ip]
+    lib.peps_direct_next_bd.restype = ctypes.c_double
+    lib.peps_direct_step.argtypes = [vp, ctypes.POINTER(ctypes.c_double), dp, dp, dp, ip, dp,
+                                     ctypes.POINTER(Stats)]
     lib.peps_su_theta.argtypes = [ip, ip, ip, dp, dp, ip, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_size_t]
     lib.peps_profile_launch_bytes.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
@@ -365,6 +371,31 @@ class Context:
         d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
         return d
 
+    def direct_draw(self, u=None, b_d=1.0, exponent=0.5):
+        """Replaces the chains by reweighted direct draws (peps_direct_draw) with host
+        uniforms u (float64 [n_chains][N]) or, u=None, Philox uniforms.  Returns log q."""
+        logq = np.empty(self.n_chains, np.float64)
+        up = None
+        if u is not None:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            if u.shape != (self.n_chains, self.N):
+                raise ValueError("u must be [n_chains][L1*L2]")
+            up = _ptr(u)
+        self._check(self.lib.peps_direct_draw(self.ctx, up, 0, float(b_d), float(exponent),
+                                              _ptr(logq)))
+        return logq
+
+    def direct_step(self, b_d, exponent=0.5, tau=0.02, eps=1e-4, max_cg=100, cg_tol=1e-10):
+        """One cooling step on direct draws (peps_direct_step).  Returns (stats, next b_d)."""
+        st = Stats()
+        bd = ctypes.c_double(float(b_d))
+        rc = self._check(self.lib.peps_direct_step(self.ctx, ctypes.byref(bd), float(exponent),
+                                                   tau, eps, max_cg, cg_tol, ctypes.byref(st)),
+                         allow=(PEPS_OK, PEPS_WARN_CG_MAXIT))
+        d = st.as_dict()
+        d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
+        return d, bd.value
+
     def set_graphs(self, on):
         """Captures and replays the batched engine's launch sequences (peps_set_graphs)."""
         self._check(self.lib.peps_set_graphs(self.ctx, 1 if on else 0))
@@ -386,6 +417,11 @@ class Context:
         j = ctypes.c_int64()
         self._check(self.lib.peps_last_counters(self.ctx, ctypes.byref(f), ctypes.byref(j)))
         return f.value, j.value
+
+
+def direct_next_bd(b_d, diag_frac, N):
+    """The diagonal bias of the next direct draw (peps_direct_next_bd)."""
+    return float(load().peps_direct_next_bd(float(b_d), float(diag_frac), int(N)))
 
 
 class Server:

@@ -15,6 +15,7 @@
 #include "pv_batch.cuh"
 #include "pv_su.cuh"
 #include "pv_su_dev.cuh"
+#include "pv_direct.cuh"
 
 #include <memory>
 #include <map>
@@ -239,6 +240,9 @@ struct BatchIface {
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
                   int* acc, int* prop) = 0;
+  // direct draw of every chain (a runner built over double-layer tensors, pv_direct.cuh)
+  virtual void draw(uint8_t* S, int n, const double* u, double b_d, double expo,
+                    double* logq) = 0;
   double flops = 0;
   int chunk = 0;
 };
@@ -353,7 +357,57 @@ struct BatchImpl : BatchIface {
     }
     flops = run.flops;
   }
+  void draw(uint8_t* S, int n_all, const double* u, double b_d, double expo,
+            double* logq) override {
+    run.flops = 0;
+    for (int off = 0; off < n_all; off += chunk) {
+      const int n = std::min(chunk, n_all - off);
+      direct_draw(run, S + (long long)off * N, n, u + (long long)off * N, b_d, expo, logq + off);
+    }
+    flops = run.flops;
+  }
 };
+
+// Double-layer site tensors of direct sampling (the layout of double_layer_theta in
+// pv_direct.cuh): block y = site, threads over the fused element index of one slice.
+template <typename T>
+__global__ void k_double_layer(int L1, int L2, int D, const T* __restrict__ theta,
+                               const long long* __restrict__ toff, T* __restrict__ out,
+                               const long long* __restrict__ toff2) {
+  const int i = blockIdx.y, r = i / L2, c = i % L2;
+  const int d0 = c == 0 ? 1 : D, d1 = c == L2 - 1 ? 1 : D, d2 = r == 0 ? 1 : D, d3 = r == L1 - 1 ? 1 : D;
+  const long long sz = (long long)d0 * d1 * d2 * d3, sz2 = sz * sz;
+  const T* th = theta + toff[i];
+  T* o = out + toff2[i];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < sz2;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long t = e;
+    const int Dd = (int)(t % d3); t /= d3;
+    const int dd = (int)(t % d3); t /= d3;
+    const int U = (int)(t % d2); t /= d2;
+    const int u = (int)(t % d2); t /= d2;
+    const int R = (int)(t % d1); t /= d1;
+    const int rr = (int)(t % d1); t /= d1;
+    const int L = (int)(t % d0); t /= d0;
+    const int l = (int)t;
+    const long long ia = (((long long)l * d1 + rr) * d2 + u) * d3 + dd;
+    const long long ib = (((long long)L * d1 + R) * d2 + U) * d3 + Dd;
+    T acc = 0;
+    for (int s = 0; s < 4; ++s) {
+      const T x = th[s * sz + ia] * th[s * sz + ib];
+      o[s * sz2 + e] = x;
+      acc += x;
+    }
+    o[4 * sz2 + e] = acc;
+  }
+}
+
+// Uniforms of a direct draw: u[chain][site] = Philox(seed; chain, draw, site, TAG_DIRECT).
+__global__ void k_direct_uniforms(double* u, int n, int N, uint64_t seed, uint32_t draw) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < (long long)n * N;
+       k += (long long)gridDim.x * blockDim.x)
+    u[k] = philox_uniform(seed, (uint32_t)(k / N), draw, (uint32_t)(k % N), TAG_DIRECT);
+}
 
 }  // namespace
 
@@ -415,6 +469,15 @@ struct peps_ctx {
   std::string err;
   std::vector<void*> allocs;
   std::unique_ptr<BatchIface> batch;   // batched engine (block_mode PEPS_BLOCKS_BATCHED)
+  // direct sampling: a batched runner at bond D^2 over the double-layer tensors, built on
+  // the first draw
+  std::unique_ptr<BatchIface> dbatch;
+  void* d_theta2 = nullptr;             // double-layer tensors, element type of the engine
+  long long* d_toff2 = nullptr;
+  std::vector<long long> toff2;
+  double *d_logq = nullptr, *d_u = nullptr;
+  bool direct_valid = false;            // the chains are the last direct draw, unchanged
+  uint32_t n_draws = 0;
   pv::KProf kprof;                      // launch counter, optional per-kernel timing
   bool o_vec4 = false;                  // every site slice of O holds a multiple of 4 entries
 };
@@ -481,9 +544,11 @@ int ensure_batch(peps_ctx* c, int nb) {
   return PEPS_OK;
 }
 
-// Reads (and clears) the batched engine's device error flag after a synchronised call.
-int batch_status(peps_ctx* c) {
-  int* d = c->batch ? c->batch->err_flag() : nullptr;
+// Reads (and clears) the batched engine's device error flag after a synchronised call
+// (the context's own engine, or the one given).
+int batch_status(peps_ctx* c, BatchIface* eng = nullptr) {
+  if (!eng) eng = c->batch.get();
+  int* d = eng ? eng->err_flag() : nullptr;
   if (!d) return PEPS_OK;
   int h = 0;
   PV_CUDA(c, cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost));
@@ -535,23 +600,26 @@ int launch_eval(peps_ctx* c, const uint8_t* dS, int nb, double* la, int8_t* sg, 
 
 namespace {
 
+// Builds a batched runner at bond dimension Dn over the site tensors theta (offsets toff):
+// the context's own engine (Dn = D) or the direct sampler's double-layer one (Dn = D^2).
+// Work buffers for as many chains as half the free device memory holds, at most n_chains.
 template <typename T>
-int make_batch_t(peps_ctx* c, int sms) {
+int init_runner_t(peps_ctx* c, int sms, BatchImpl<T>* b, int Dn, const T* theta,
+                  const std::vector<long long>& toff) {
   const peps_params* P = &c->P;
-  auto* b = new BatchImpl<T>();
-  c->batch.reset(b);
   const int n = P->n_chains;
-  const long long cD = (long long)P->chi * P->D;
+  const long long cD = (long long)P->chi * Dn;
   const long long cap = 2 * cD * (cD + 1);
   const size_t trunc_bytes = (size_t)cap * sizeof(T) + (size_t)(cD + 4) * (sizeof(T) + 4) + 16;
   const bool trunc_global = trunc_bytes > 200 * 1024;   // Jacobi matrices in global memory
   if (!trunc_global && trunc_bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kb_trunc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trunc_bytes);
+    // one cap for every context of the process, so that none lowers it under another
+    cudaError_t e = cudaFuncSetAttribute(kb_trunc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
   }
   std::vector<long long> sz;
   long long n8, nd;
-  BatchBufs<T>::sizes(P->L1, P->L2, P->D, P->chi, sz, n8, nd);
+  BatchBufs<T>::sizes(P->L1, P->L2, Dn, P->chi, sz, n8, nd);
   long long per = 0;
   for (long long x : sz) per += x;
   size_t per_bytes = (size_t)per * sizeof(T) + (size_t)n8 + (size_t)nd * 8 + 16;
@@ -635,22 +703,55 @@ int make_batch_t(peps_ctx* c, int sms) {
   b->N = c->N;
   b->No = c->No;
   auto& r = b->run;
-  r.shp.build(P->L1, P->L2, P->D, P->chi);
+  r.shp.build(P->L1, P->L2, Dn, P->chi);
   r.L1 = P->L1;
   r.L2 = P->L2;
-  r.D = P->D;
+  r.D = Dn;
   r.chi = P->chi;
   r.N = c->N;
   r.J1 = P->J1;
   r.J2 = P->J2;
-  r.theta = fp64(c) ? (const T*)(const void*)c->d_theta : (const T*)(const void*)c->d_theta_f;
-  r.toff = c->toff;
+  r.theta = theta;
+  r.toff = toff;
   r.ooff = c->ooff;
   r.jtol = sizeof(T) == 8 ? (T)JTOL_F64 : (T)JTOL_F32;
   r.max_sweeps = JAC_MAX_SWEEPS;
   r.sweeps = c->d_jsw;
-  r.b.bind(real, chunk, i8, dbl, P->L1, P->L2, P->D, P->chi);
+  r.b.bind(real, chunk, i8, dbl, P->L1, P->L2, Dn, P->chi);
   return PEPS_OK;
+}
+
+template <typename T>
+int make_batch_t(peps_ctx* c, int sms) {
+  auto* b = new BatchImpl<T>();
+  c->batch.reset(b);
+  const T* theta = fp64(c) ? (const T*)(const void*)c->d_theta : (const T*)(const void*)c->d_theta_f;
+  return init_runner_t<T>(c, sms, b, c->P.D, theta, c->toff);
+}
+
+// The direct sampler's runner and buffers: double-layer tensors (five slices per site at
+// bond D^2), uniforms and log q of every chain.
+template <typename T>
+int make_direct_t(peps_ctx* c, int sms) {
+  const peps_params* P = &c->P;
+  const int N = c->N, D2 = P->D * P->D;
+  c->toff2.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) {
+    const int r = i / P->L2, q = i % P->L2;
+    const long long sz = (long long)(q == 0 ? 1 : D2) * (q == P->L2 - 1 ? 1 : D2) *
+                         (r == 0 ? 1 : D2) * (r == P->L1 - 1 ? 1 : D2);
+    c->toff2[i + 1] = c->toff2[i] + 5 * sz;
+  }
+  PV_TRY(dalloc(c, (T**)&c->d_theta2, (size_t)c->toff2[N] * sizeof(T)));
+  PV_TRY(dalloc(c, &c->d_toff2, (size_t)(N + 1) * sizeof(long long)));
+  PV_CUDA(c, cudaMemcpy(c->d_toff2, c->toff2.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  PV_TRY(dalloc(c, &c->d_logq, (size_t)P->n_chains * sizeof(double)));
+  PV_TRY(dalloc(c, &c->d_u, (size_t)P->n_chains * N * sizeof(double)));
+  auto* b = new BatchImpl<T>();
+  c->dbatch.reset(b);
+  const int rc = init_runner_t<T>(c, sms, b, D2, (const T*)c->d_theta2, c->toff2);
+  if (rc != PEPS_OK) c->dbatch.reset();
+  return rc;
 }
 
 // Block layout peps_init takes for automatic mode: the batched engine (measured faster on
@@ -948,6 +1049,7 @@ int peps_set_theta(peps_ctx* c, const double* host, size_t n) {
   PV_CUDA(c, cudaGetLastError());
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_eval = false;
+  c->direct_valid = false;
   c->ucache_valid = false;
   return PEPS_OK;
 }
@@ -966,6 +1068,7 @@ int peps_set_configs(peps_ctx* c, const uint8_t* host, size_t n) {
   PV_CUDA(c, cudaMemcpyAsync(c->d_S, host, n, cudaMemcpyHostToDevice, c->stream));
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->have_eval = false;
+  c->direct_valid = false;
   c->ucache_valid = false;
   return PEPS_OK;
 }
@@ -1006,6 +1109,7 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   PV_CUDA(c, cudaGetLastError());
   c->sweeps += n_sweeps;
   c->have_eval = false;
+  c->direct_valid = false;
   c->ucache_valid = c->batch ? (n <= c->batch->chunk) : (c->d_ucache != nullptr);
   std::vector<int> a(n), b(n);
   PV_CUDA(c, cudaMemcpyAsync(a.data(), c->d_acc, n * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1018,6 +1122,76 @@ int peps_mc_sweep(peps_ctx* c, int n_sweeps, int p) {
   }
   c->last_accept = sb > 0 ? (double)sa / (double)sb : 0.0;
   return PEPS_OK;
+}
+
+int peps_direct_draw(peps_ctx* c, const double* u, int on_device, double b_d, double exponent,
+                     double* log_q) {
+  if (!c || !(b_d > 0.0) || !(b_d <= 1.0) || !(exponent > 0.0) || !std::isfinite(exponent))
+    return fail(c, PEPS_EINVAL, "direct_draw: args");
+  if (!c->batch)
+    return fail(c, PEPS_ESTATE, "direct_draw: direct sampling runs on the batched engine");
+  const peps_params* P = &c->P;
+  const int n = P->n_chains, N = c->N;
+  cudaStream_t st = c->stream;
+  if (!c->dbatch) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    PV_TRY(fp64(c) ? make_direct_t<double>(c, sms) : make_direct_t<float>(c, sms));
+  }
+  c->have_eval = false;
+  c->ucache_valid = false;
+  c->direct_valid = false;
+  long long big = 0;
+  for (int i = 0; i < N; ++i) big = std::max(big, (c->toff2[i + 1] - c->toff2[i]) / 5);
+  dim3 g((unsigned)std::min<long long>((big + 255) / 256, 1024), (unsigned)N);
+  if (fp64(c))
+    PV_KLAUNCH(&c->kprof, st, "k_double_layer", 0.0, 0.0,
+               k_double_layer<double><<<g, 256, 0, st>>>(P->L1, P->L2, P->D, c->d_theta, c->d_toff,
+                                                         (double*)c->d_theta2, c->d_toff2));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_double_layer", 0.0, 0.0,
+               k_double_layer<float><<<g, 256, 0, st>>>(P->L1, P->L2, P->D, c->d_theta_f, c->d_toff,
+                                                        (float*)c->d_theta2, c->d_toff2));
+  const double* du = c->d_u;
+  if (u && on_device) {
+    du = u;
+  } else if (u) {
+    PV_CUDA(c, cudaMemcpyAsync(c->d_u, u, (size_t)n * N * sizeof(double), cudaMemcpyHostToDevice, st));
+  } else {
+    PV_KLAUNCH(&c->kprof, st, "k_direct_uniforms", 0.0, 0.0,
+               k_direct_uniforms<<<grid_for((long long)n * N, 256), 256, 0, st>>>(c->d_u, n, N, P->seed,
+                                                                                 c->n_draws));
+  }
+  c->dbatch->draw(c->d_S, n, du, b_d, exponent, c->d_logq);
+  PV_CUDA(c, cudaGetLastError());
+  if (log_q)
+    PV_CUDA(c, cudaMemcpyAsync(log_q, c->d_logq, (size_t)n * sizeof(double),
+                               on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  PV_TRY(batch_status(c, c->dbatch.get()));
+  c->n_draws += 1;
+  c->direct_valid = true;
+  return PEPS_OK;
+}
+
+double peps_direct_next_bd(double b_d, double diag_frac, int N) {
+  if (!(b_d > 0.0) || !(diag_frac >= 0.0) || N < 1) return b_d;
+  if (diag_frac > 0.5) b_d *= std::pow(0.5 / diag_frac, 1.0 / N);
+  return std::min(b_d, 1.0);
+}
+
+int peps_direct_step(peps_ctx* c, double* b_d, double exponent, double tau, double eps,
+                     int max_cg, double cg_tol, peps_stats* st) {
+  if (!c || !b_d) return fail(c, PEPS_EINVAL, "direct_step: args");
+  PV_TRY(peps_direct_draw(c, nullptr, 0, *b_d, exponent, nullptr));
+  PV_TRY(peps_eval_batch(c, nullptr, c->P.n_chains, 1, nullptr, nullptr, nullptr, nullptr, nullptr));
+  peps_stats tmp;
+  peps_stats* sp = st ? st : &tmp;
+  const int rc = peps_sr_step(c, tau, eps, max_cg, cg_tol, 0, sp);
+  if (rc < 0) return rc;
+  *b_d = peps_direct_next_bd(*b_d, sp->diag_frac, c->N);
+  return rc;
 }
 
 int peps_eval_batch(peps_ctx* c, const uint8_t* S, int nb, int on_device, double* log_abs,
@@ -1117,25 +1291,34 @@ static int fill_stats(peps_ctx* c, int p, peps_stats* st, bool with_cg) {
 
 static int launch_weights(peps_ctx* c, int p) {
   PV_KLAUNCH(&c->kprof, c->stream, "k_sr_weights", 0.0, 0.0, k_sr_weights<<<1, SR_WEIGHT_THREADS, 0, c->stream>>>(c->P.n_chains, c->N, p, c->d_log_abs,
-                                                       c->d_es, c->d_ea, c->d_S, c->d_w, c->d_E,
+                                                       c->d_logq, c->d_es, c->d_ea, c->d_S, c->d_w, c->d_E,
                                                        c->d_sc));
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
 }
 
+// p = 0 (direct draws) needs the chains to be the last peps_direct_draw, unchanged since.
+static int check_weights(peps_ctx* c, int p, const char* who) {
+  if (!c->have_eval) return fail(c, PEPS_ESTATE, std::string(who) + ": no evaluation of the chains");
+  if (p == 0 && !c->direct_valid)
+    return fail(c, PEPS_ESTATE, std::string(who) + ": p = 0 needs the chains of the last direct draw, "
+                "unchanged (no sweep, configuration or theta change since)");
+  return PEPS_OK;
+}
+
 int peps_observables(peps_ctx* c, int p, peps_stats* st) {
-  if (!c || (p != 1 && p != 2)) return fail(c, PEPS_EINVAL, "observables: args");
-  if (!c->have_eval) return fail(c, PEPS_ESTATE, "observables: no evaluation of the chains");
+  if (!c || p < 0 || p > 2) return fail(c, PEPS_EINVAL, "observables: args");
+  PV_TRY(check_weights(c, p, "observables"));
   PV_TRY(launch_weights(c, p));
   return fill_stats(c, p, st, false);
 }
 
 int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol, int p,
                  peps_stats* st) {
-  if (!c || (p != 1 && p != 2) || max_cg < 0 || !(eps >= 0) || !(cg_tol >= 0) ||
+  if (!c || p < 0 || p > 2 || max_cg < 0 || !(eps >= 0) || !(cg_tol >= 0) ||
       !std::isfinite(tau))
     return fail(c, PEPS_EINVAL, "sr_step: args");
-  if (!c->have_eval) return fail(c, PEPS_ESTATE, "sr_step: no evaluation of the chains");
+  PV_TRY(check_weights(c, p, "sr_step"));
   const int n = c->P.n_chains;
   const long long Np = c->Np, No = c->No;
   cudaStream_t s = c->stream;
@@ -1255,6 +1438,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   PV_CUDA(c, cudaMemcpy(&h, c->d_sc, sizeof(h), cudaMemcpyDeviceToHost));
   c->t += tau;
   c->have_eval = false;
+  c->direct_valid = false;
   c->ucache_valid = false;
   if (!std::isfinite(h.rr) || !std::isfinite(h.H1))
     return fail(c, PEPS_ENOTFINITE, "sr_step: non-finite energy or residual");
@@ -1443,6 +1627,7 @@ int peps_su_warm_start(peps_ctx* c, double tau, int n_steps) {
   if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("su_warm_start: ") + cudaGetErrorString(e));
   c->t = n_steps * tau;
   c->have_eval = false;
+  c->direct_valid = false;
   c->ucache_valid = false;
   return PEPS_OK;
 }

@@ -1485,6 +1485,12 @@ __global__ void kb_set(T* x, long long xs, long long off, T v, int n) {
   if (s < n) x[(long long)s * xs + off] = v;
 }
 
+__global__ void kb_fill_u8(uint8_t* x, uint8_t v, long long count) {
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x)
+    x[k] = v;
+}
+
 __global__ void kb_copyd(double* x, long long xs, int dst, int src, int n) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < n) x[(long long)s * xs + dst] = x[(long long)s * xs + src];
@@ -1810,6 +1816,17 @@ struct CudaBE {
     PV_KLAUNCH(prof, st, "kb_elem_ratio", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(ElemRatio<T>{num, den, dens, valid, coef, e}, n));
   }
   void accept(ElemAccept<T> f, int n) { PV_KLAUNCH(prof, st, "kb_elem_accept", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n)); }
+  // direct sampling (pv_direct.cuh): configuration fill, the candidate selector of every
+  // chain, and one draw
+  void fill_u8(uint8_t* x, uint8_t v, long long count) {
+    const long long g = std::min<long long>((count + 255) / 256, 4LL * sms > 0 ? 4LL * sms : 1);
+    PV_KLAUNCH(prof, st, "kb_fill", 0.0, 0.0, kb_fill_u8<<<(unsigned)(g > 0 ? g : 1), 256, 0, st>>>(x, v, count));
+  }
+  void set_i8(int8_t* x, int8_t v, int n) {
+    PV_KLAUNCH(prof, st, "kb_set", 0.0, 0.0, kb_set<int8_t><<<gx(n, 256), 256, 0, st>>>(x, 1, 0, v, n));
+  }
+  template <typename F>
+  void draw(F f, int n) { PV_KLAUNCH(prof, st, "kb_elem_draw", 0.0, 0.0, kb_elem<<<gx(n, 128), 128, 0, st>>>(f, n)); }
 };
 
 }  // namespace pv

@@ -19,7 +19,8 @@
 // slightly negative count as zero.
 //
 // This header holds the orchestration and the per-chain functor; a back end provides
-// set_i8(x, v, n) and draw(ElemDraw, n) besides the BatchRunner operations.
+// fill_u8(x, v, count), set_i8(x, v, n) and draw(ElemDraw, n) besides the BatchRunner
+// operations, and every pointer handed to direct_draw lives where its kernels run.
 #ifndef PV_DIRECT_CUH
 #define PV_DIRECT_CUH
 #include <cmath>
@@ -106,8 +107,8 @@ void direct_draw(BatchRunner<T, BE, OT>& run, uint8_t* S, int n, const double* u
   BE& be = run.be;
   auto& b = run.b;
   const int L1 = run.L1, L2 = run.L2, N = run.N;
-  for (long long k = 0; k < (long long)n * N; ++k) S[k] = 4;   // every site summed
-  for (int s = 0; s < n; ++s) logq[s] = 0.0;
+  be.fill_u8(S, 4, (long long)n * N);   // every site summed
+  be.setd(logq, 1, 0, 0.0, n);
   run.build_down(S, n);
   run.trivial(run.uprow(0), b.sU, n);
   be.setd(b.lsU, 1, 0, 0.0, n);

@@ -57,5 +57,6 @@ PX_HD uint32_t philox_bits(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
 constexpr uint32_t TAG_INIT = 0x494E4954u;
 constexpr uint32_t TAG_CFG = 0x43464731u;
 constexpr uint32_t TAG_MC = 0x4D435357u;
+constexpr uint32_t TAG_DIRECT = 0x44495231u;
 
 }  // namespace pv

@@ -41,16 +41,25 @@ __device__ __forceinline__ T blk_sum(T v, T* red) {
   return s;
 }
 
-// Weights and sample statistics (one block).  p = 2: w = 1/n; p = 1: w = |rho|/sum|rho|
-// (Eq. A1).  Observables: <H> = 1/2 sum w (Es + Ea), <H^2> = 1/2 sum w (Es^2 + Ea^2),
+// Log of the unnormalised weight of sample i: p = 2 (samples of |rho|^2) 0; p = 1 (samples
+// of |rho|, Eq. A1) log|rho|; p = 0 (direct draws of probability q, App. A Eq. A7 with
+// r_4 = p_0 / q) 2 log|rho| - log q.
+__device__ __forceinline__ double sr_log_weight(int p, const double* log_abs, const double* logq,
+                                                int i) {
+  return p == 2 ? 0.0 : p == 1 ? log_abs[i] : 2.0 * log_abs[i] - logq[i];
+}
+
+// Weights and sample statistics (one block): w_i = exp(lw_i) / sum_j exp(lw_j) with lw of
+// sr_log_weight.  Observables: <H> = 1/2 sum w (Es + Ea), <H^2> = 1/2 sum w (Es^2 + Ea^2),
 // <Mz^2> = 1/2 sum w (M(s)^2 + M(s')^2).
 __global__ void k_sr_weights(int n, int N, int p, const double* __restrict__ log_abs,
+                             const double* __restrict__ logq,
                              const double* __restrict__ es, const double* __restrict__ ea,
                              const uint8_t* __restrict__ S, double* __restrict__ w,
                              double* __restrict__ E, SRScalars* sc) {
   __shared__ double red[32];
   double mx = -INFINITY;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, log_abs[i]);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) mx = fmax(mx, sr_log_weight(p, log_abs, logq, i));
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ double redm[32];
   if ((threadIdx.x & 31) == 0) redm[threadIdx.x >> 5] = mx;
@@ -59,11 +68,11 @@ __global__ void k_sr_weights(int n, int N, int p, const double* __restrict__ log
   for (int i = 1; i < (int)(blockDim.x >> 5); ++i) mx = fmax(mx, redm[i]);
   double zs = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    zs += (p == 2) ? 1.0 : exp(log_abs[i] - mx);
+    zs += (p == 2) ? 1.0 : exp(sr_log_weight(p, log_abs, logq, i) - mx);
   double Z = blk_sum(zs, red);
   double e1 = 0, h1 = 0, h2 = 0, m2 = 0, dg = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double wi = ((p == 2) ? 1.0 : exp(log_abs[i] - mx)) / Z;
+    double wi = ((p == 2) ? 1.0 : exp(sr_log_weight(p, log_abs, logq, i) - mx)) / Z;
     w[i] = wi;
     double a = es[i], b = ea[i];
     E[i] = a + b;

@@ -124,6 +124,9 @@ struct HostBE {
   void set_i8(int8_t* x, int8_t v, int n) {
     for (int s = 0; s < n; ++s) x[s] = v;
   }
+  void fill_u8(uint8_t* x, uint8_t v, long long count) {
+    for (long long k = 0; k < count; ++k) x[k] = v;
+  }
   void draw(ElemDraw<T> f, int n) {
     for (int s = 0; s < n; ++s) f(s);
   }

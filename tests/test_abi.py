@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_2409_05285_gb300 import binding
 from paper_2409_05285_gb300.build import LIB, build
 
@@ -76,6 +78,24 @@ def test_tuning_and_profile_calls_reject_a_null_context():
     n = ctypes.c_int()
     assert lib.peps_profile_launch_bytes(None, b"kb_gemm_tc", buf, 4, ctypes.byref(n)) == \
         binding.PEPS_EINVAL
+
+
+def test_direct_calls_reject_a_null_context_and_next_bd_follows_the_oracle():
+    # host-only arithmetic of the direct sampler's diagonal bias against the oracle's rule
+    import numpy as np
+    from oracle import direct
+    lib = binding.load()
+    bd = ctypes.c_double(0.5)
+    assert lib.peps_direct_draw(None, None, 0, 0.5, 0.5, None) == binding.PEPS_EINVAL
+    assert lib.peps_direct_step(None, ctypes.byref(bd), 0.5, 0.01, 1e-4, 10, 1e-8, None) == \
+        binding.PEPS_EINVAL
+    N = 6
+    for b_d in (1.0, 0.7, 0.05):
+        for n_diag in range(0, 11):
+            S = np.vstack([np.zeros((n_diag, N), np.int64), np.ones((10 - n_diag, N), np.int64)])
+            f = direct.diagonal_fraction(S)
+            assert binding.direct_next_bd(b_d, f, N) == pytest.approx(
+                direct.update_bd(b_d, S, N), rel=1e-15)
 
 
 def test_header_is_plain_c():

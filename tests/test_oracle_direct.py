@@ -191,3 +191,36 @@ def test_boundary_mps_truncation_changes_the_marginals():
     S2, lq2 = direct.draw_bmps(lat, th, u, 2, 1.0, 1.0)
     q_exact_S2 = np.log(direct.sample_prob(lat, th, S2, 1.0, 1.0))
     assert abs(lq2 - q_exact_S2) > 1e-8
+
+
+def test_sr_weights_of_plain_direct_draws_are_uniform():
+    # exponent 1, b_d = 1 draws p_0 exactly (q = p_0 / sum p_0): r_4 = p_0 / q is the same
+    # for every sample, so the p = 0 weights of the SR step are 1/n
+    from oracle import sr
+    lat = Lattice(2, 2, 2)
+    th = _theta(lat, 11)
+    rng = np.random.default_rng(12)
+    lq, lp = [], []
+    for _ in range(12):
+        _, logq, logp0 = direct.draw(lat, th, rng.random(lat.N), 1.0, 1.0)
+        lq.append(logq)
+        lp.append(logp0)
+    w = sr.weights(0.5 * np.array(lp), 0, np.array(lq))
+    assert np.allclose(w, 1.0 / 12, rtol=1e-10)
+
+
+def test_sr_weights_of_reweighted_draws_give_exact_average():
+    # the p = 0 weights over every configuration, each counted with its probability q, give
+    # the exact p_0 average of any function (Eq. A7); they differ from uniform weights
+    from oracle import sr
+    lat = Lattice(2, 2, 2)
+    th = _theta(lat, 13)
+    cfgs = _all_configs(lat.N)
+    p0 = _p0(lat, th, cfgs)
+    q = np.array([direct.sample_prob(lat, th, S, 0.3, 0.5) for S in cfgs])
+    ok = q > 0
+    f = np.array([float(S[1] % 2) - 0.3 * float(S[2] // 2) for S in cfgs])[ok]
+    w = sr.weights(0.5 * np.log(p0[ok]), 0, np.log(q[ok]))
+    exact = np.sum(p0 * np.array([float(S[1] % 2) - 0.3 * float(S[2] // 2) for S in cfgs])) / p0.sum()
+    assert np.sum(q[ok] * w * f) / np.sum(q[ok] * w) == pytest.approx(exact, rel=1e-12)
+    assert not np.allclose(w, w[0])
