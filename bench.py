@@ -16,6 +16,11 @@ With --largest 1 (default) the line also carries `largest_workload`: the 10x10 J
 chi=36 workload at 16384 samples per SR step, one warm-up and one timed step (a step takes
 minutes on one GPU, so the headline's step counts do not apply to it).
 
+With --direct the step draws every chain anew by reweighted direct sampling (App. A, Eqs.
+A2-A7) instead of a sweep and weights the SR step by r_4 = rho^2 / q: workload direct6, 6x6
+Heisenberg D=2 chi=16, 30000 samples per step.  With --serve the serving loop runs a mixed
+request stream instead.
+
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a bounded
 sample of the same workload.
 """
@@ -243,6 +248,22 @@ def kernel_roofline(kstats, peaks, prec, binding):
                "flops_per_launch": flops / n, "bytes_per_launch": nbytes / n,
                "mean_launch_us": ms / n * 1e3, "launches": n, "share_of_kernel_time": ms / total,
                "peak_source": src}
+        if nbytes > 0:
+            gbs = nbytes / n / (ms / n / 1e3) / 1e9
+            out["hbm_view"] = {"achieved_GB_s": gbs, "peak_GB_s": hpeak, "frac": gbs / hpeak,
+                               "peak_source": "%s HBM copy bandwidth (MEASURED_PEAKS.json)" % hsrc}
+        return out, kernels
+    if name == "kb_trunc" and flops > 0:
+        # one-sided Jacobi SVD per chain: FMA-bound (float32, float64 in FP64 mode); its flops
+        # are those of the sweeps the matrices took, counted on the device
+        peak = PEAK_FP64_TFLOPS if prec == binding.PEPS_FP64 else PEAK_FP32_TFLOPS
+        achieved = flops / n / (ms / n / 1e3) / 1e12
+        out = {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak,
+               "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+               "flops_per_launch": flops / n, "bytes_per_launch": nbytes / n,
+               "mean_launch_us": ms / n * 1e3, "launches": n, "share_of_kernel_time": ms / total,
+               "peak_source": "derived: %s FMA/clk/SM x 152 SMs x 2070 MHz" %
+                              ("2 FP64" if prec == binding.PEPS_FP64 else "128 FP32")}
         if nbytes > 0:
             gbs = nbytes / n / (ms / n / 1e3) / 1e9
             out["hbm_view"] = {"achieved_GB_s": gbs, "peak_GB_s": hpeak, "frac": gbs / hpeak,
@@ -633,6 +654,219 @@ def cpu_baseline(wl, n, n_samples):
                       f"then one SR step on those samples; value = samples / wall time"}
 
 
+def _oracle_direct_chain(args):
+    """One direct draw of the oracle (boundary-MPS form, shared down environments) and its
+    evaluation (runs in a worker)."""
+    L, D, chi, J1, J2, theta, u, b_d, expo, down = args
+    sys.path.insert(0, ROOT)
+    from oracle import direct, peps
+    from oracle.lattice import Lattice
+    lat = Lattice(L, L, D, J1=J1, J2=J2)
+    S, lq = direct.draw_bmps(lat, theta, u, chi, b_d, expo, down=down)
+    r = peps.eval_sample(lat, theta, S, chi)
+    return S, lq, r["log_abs"], r["e_sys"], r["e_anc"], r["O"]
+
+
+def oracle_direct_step(wl, n_samples, pool, b_d, expo, seed=0):
+    """The oracle's cooling step on direct draws: the summed down environments once, then per
+    sample a draw and its evaluation in the pool, then the SR update with p = 0 weights.
+    Returns seconds."""
+    import numpy as np
+    from oracle import direct, peps, sr
+    from oracle.lattice import Lattice
+    lat = Lattice(wl.L, wl.L, wl.D, J1=wl.J1, J2=wl.J2)
+    theta = peps.init_theta(lat, wl.seed, wl.init_noise)
+    u = np.random.default_rng(seed).random((n_samples, lat.N))
+    t0 = time.perf_counter()
+    down = direct.summed_down_envs(lat, theta, wl.chi)
+    res = pool.map(_oracle_direct_chain, [(wl.L, wl.D, wl.chi, wl.J1, wl.J2, theta, u[k], b_d, expo,
+                                           down) for k in range(n_samples)])
+    S = np.array([r[0] for r in res])
+    lq = np.array([r[1] for r in res])
+    la = np.array([r[2] for r in res])
+    es = np.array([r[3] for r in res])
+    ea = np.array([r[4] for r in res])
+    O = np.array([r[5] for r in res])
+    sr.sr_step(lat, theta, S, la, es, ea, O, 0, wl.tau, wl.eps, wl.cg_tol, wl.max_cg, log_q=lq)
+    return time.perf_counter() - t0
+
+
+def run_direct(args):
+    """Cooling steps on reweighted direct draws (App. A, Eqs. A2-A7): per step every chain is
+    replaced by an independent draw (peps_direct_draw, Philox uniforms), evaluated, and the SR
+    update takes the p = 0 weights r_4 = rho^2 / q; b_d adapts between steps
+    (peps_direct_next_bd).  Workload direct6 (or --workload), TF32 by default."""
+    import numpy as np
+    import torch
+
+    from paper_2409_05285_gb300 import binding
+    from paper_2409_05285_gb300.build import build
+    from paper_2409_05285_gb300.workloads import WORKLOADS
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if ws > 1:
+        torch.distributed.barrier()
+    wl = WORKLOADS[args.workload if args.workload != "heis8" else "direct6"]
+    prec = {"fp32": binding.PEPS_FP32, "tf32": binding.PEPS_TF32, "fp64": binding.PEPS_FP64}[args.precision]
+    stream = torch.cuda.Stream()
+    n = args.chains or wl.n_samples
+    N = wl.L * wl.L
+    expo = wl.extra.get("exponent", 0.5)
+    ctx = binding.Context(wl.L, wl.L, wl.D, wl.chi, n, J1=wl.J1, J2=wl.J2, precision=prec,
+                          init_noise=wl.init_noise, seed=rank_seed(wl.seed, rank),
+                          stream=ctypes_stream(stream), block_mode=binding.PEPS_BLOCKS_BATCHED)
+    if args.graphs:
+        ctx.set_graphs(True)
+    su_t = wl.extra.get("su_t", 0.0)
+    n_su = int(round(su_t / SU_TAU))
+    if n_su > 0:
+        ctx.su_warm_start(SU_TAU, n_su)
+    tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
+    b_d = wl.extra.get("b_d0", 1.0)
+    for _ in range(args.warmup - 1):
+        _, b_d = ctx.direct_step(b_d, expo, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+    # the last warm-up step with CUDA events around every launch (per-kernel time, bytes, flops)
+    ctx.profile(True, gemm_only=False)
+    base, phase_k = {}, {"draw": {}, "eval": {}, "sr_step": {}}
+    ctx.direct_draw(None, b_d, expo)
+    draw_flops, draw_jsw = ctx.counters()
+    phase_k["draw"] = kdelta(ctx.profile_read(), base, phase_k["draw"])
+    ctx.eval_chains()
+    phase_k["eval"] = kdelta(ctx.profile_read(), base, phase_k["eval"])
+    st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=0)
+    phase_k["sr_step"] = kdelta(ctx.profile_read(), base, phase_k["sr_step"])
+    ctx.profile(False)
+    b_d = binding.direct_next_bd(b_d, st["diag_frac"], N)
+    kstats = {}
+    for ph in phase_k.values():
+        for k, v in ph.items():
+            a = kstats.get(k, (0, 0.0, 0.0, 0.0))
+            kstats[k] = tuple(x + y for x, y in zip(a, v))
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    step_ms, draw_ms, eval_ms, sr_ms, stats, bds = [], [], [], [], [], []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = ctx.launches()
+    e_start, e_end = ev(), ev()
+    torch.cuda.profiler.start()   # the window `ncu --profile-from-start off` captures
+    e_start.record(stream)
+    for _ in range(args.steps):
+        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0.record(stream)
+        ctx.direct_draw(None, b_d, expo)
+        e1.record(stream)
+        ctx.eval_chains()
+        e2.record(stream)
+        st = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=0)
+        e3.record(stream)
+        e3.synchronize()
+        stats.append(st)
+        bds.append(b_d)
+        b_d = binding.direct_next_bd(b_d, st["diag_frac"], N)
+        draw_ms.append(e0.elapsed_time(e1))
+        eval_ms.append(e1.elapsed_time(e2))
+        sr_ms.append(e2.elapsed_time(e3))
+        step_ms.append(e0.elapsed_time(e3))
+    e_end.record(stream)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    clk = clocks.stop()
+    launches = ctx.launches() - launches0
+    total_ms = max_over_ranks(e_start.elapsed_time(e_end))
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the public API with host buffers: the step's uniforms from pinned
+    # host memory (drawn on the host), log q and the step's statistics read back
+    u_h = torch.empty((n, N), dtype=torch.float64).pin_memory()
+    u_np = u_h.numpy()
+    rng = np.random.default_rng(rank_seed(wl.seed, rank) + 1)
+    e2e_ms = []
+    for _ in range(max(2, args.steps // 2)):
+        u_np[:] = rng.random((n, N))
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.direct_draw(u_np, b_d, expo)
+        ctx.eval_chains()
+        st2 = ctx.sr_step(tau, eps=eps, max_cg=max_cg, cg_tol=tol, p=0)
+        torch.cuda.synchronize()
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+        b_d = binding.direct_next_bd(b_d, st2["diag_frac"], N)
+    e2e_step = statistics.median(e2e_ms)
+
+    peaks = measured_peaks()
+    roofline, kernels = kernel_roofline(kstats, peaks, prec, binding)
+    step_sorted = sorted(step_ms)
+    out = {
+        "metric": "PEPS samples/s per SR cooling step on reweighted direct draws (App. A)",
+        "value": job_throughput(n, ws, ms_per_step),
+        "unit": "samples/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {binding.PEPS_FP64: "f64", binding.PEPS_FP32: "f32",
+                  binding.PEPS_TF32: "tf32 (contractions; f32 storage, f64 SR)"}[prec],
+        "data": "synthetic (seeded beta=0 PEPS cooled in-run; no dataset)",
+        "config": {"workload": f"{wl.L}x{wl.L} OBC Heisenberg J1={wl.J1} J2={wl.J2}, d2=4, D={wl.D}, "
+                               f"chi={wl.chi} (double layer: bond {wl.D * wl.D}), {n} direct samples "
+                               f"per SR step per GPU, exponent {expo}",
+                   "global_batch": ws * n, "tau": tau, "eps": eps, "max_cg": max_cg, "cg_tol": tol,
+                   "warm_start": (f"simple update to t={n_su * SU_TAU:g} (tau {SU_TAU:g})" if n_su
+                                  else "perturbed beta=0 state"),
+                   "parallelism": f"replicas{ws}",
+                   "l2": "inputs larger than L2 (O rows %.0f MB)" % (n * ctx.No * (8 if prec == 0 else 4) / 1e6)},
+        "sr_steps_per_s": ws / (ms_per_step / 1e3),
+        "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
+                       "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+        "phase_ms": {"direct_draw": statistics.mean(draw_ms), "eval": statistics.mean(eval_ms),
+                     "sr_step": statistics.mean(sr_ms)},
+        "draw_gflop_per_sample": draw_flops / n / 1e9,
+        "draw_jacobi_sweeps_per_sample": draw_jsw / n,
+        "b_d": bds, "diag_frac": [s_["diag_frac"] for s_ in stats],
+        "cg_iters": statistics.mean(s_["cg_iters"] for s_ in stats),
+        "E_site": stats[-1]["E_site"], "E_err": stats[-1]["E_err"],
+        "beta_obs": stats[-1]["beta_obs"],
+        "roofline": roofline,
+        "kernels": kernels,
+        "kernels_by_phase": {ph: kernel_shares(v) for ph, v in phase_k.items()},
+        "kernel_stats_from": "one untimed step with CUDA events around every launch (the last warm-up step)",
+        "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(n * N * 8), "d2h_bytes_per_step": int(n * 8)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    ctx.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        cores = os.cpu_count() or 1
+        _one_thread_workers()
+        with mp.get_context("spawn").Pool(cores) as pool:
+            m = max(args.cpu_samples, 150 * cores)   # ~10-20 s of oracle work
+            secs = oracle_direct_step(wl, m, pool, bds[-1], expo)
+        out["cpu_baseline"] = {"value": m / secs, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{m} direct samples of the {wl.L}x{wl.L} D={wl.D} chi={wl.chi} "
+                                         f"workload: summed down environments once, a boundary-MPS draw "
+                                         f"+ evaluation per sample (spawn pool over {cores} host cores), "
+                                         f"then one SR step with p = 0 weights; value = samples / wall time"}
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
@@ -761,6 +995,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
+    ap.add_argument("--direct", action="store_true",
+                    help="cooling steps on reweighted direct draws (workload direct6) instead")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--window", type=float, default=10.0, help="serving: arrival window (s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured time (s)")
@@ -787,6 +1023,8 @@ def main():
         run_reference(args)
     elif args.serve:
         run_serve(args)
+    elif args.direct:
+        run_direct(args)
     else:
         run_ours(args)
 

@@ -261,14 +261,18 @@ typedef struct {
   int ffma_g;      /* most chains per block of the FFMA contraction kernel */
   int kc_max;      /* largest contraction chunk of the tensor-core kernel (8, 16, ..., 64) */
   double ms_before, ms_after;
-  int pipelined;   /* 1: short contractions with vector operands take the cp.async-pipelined
-                      tensor-core kernel; 0: every contraction takes the register-staged one */
+  int pipelined;   /* contractions with vector operands on the cp.async-pipelined tensor-core
+                      kernel: 1 the short ones (K <= 64), 2 all; 0: every contraction takes
+                      the register-staged kernel */
+  int stage_kb;    /* shared memory of the pipelined kernel's stage ring per CTA, KB (32..200;
+                      0 in peps_set_tune keeps the current value) */
 } peps_tune;
 int peps_autotune(peps_ctx* ctx, int reps, peps_tune* out);
 /* Sets the batched engine's launch shapes (every field of `t` but the times) for this
  * context, e.g. to repeat a run with the shapes an earlier autotune chose.  No choice changes
  * any result.  EINVAL for values outside grid_pct 1..400, db_bytes 0..200 KB, ffma_g 1..256,
- * kc_max a multiple of 8 in 8..64, pipelined 0..1; ESTATE without the batched engine. */
+ * kc_max a multiple of 8 in 8..64, pipelined 0..2, stage_kb 0 or 32..200; ESTATE without the
+ * batched engine. */
 int peps_set_tune(peps_ctx* ctx, const peps_tune* t);
 
 /* Simple-update warm start (App. A): from the beta = 0 state, n_steps first-order Trotter
@@ -310,7 +314,10 @@ int peps_cv_spline(const double* beta, const double* E_site, int n, double smoot
  * 2) does the same for the batched GEMM kernels only (kb_gemm_tc, kb_gemm: fewer events in
  * the stream); peps_profile(ctx, 0) stops.  peps_profile_read synchronises the stream and
  * returns, per kernel name, the launches, the summed event time and the algorithmic bytes
- * (each operand read once, each result written once) and flops of those launches; up to
+ * (each operand read once, each result written once) and flops of those launches (for the
+ * truncation kernel kb_trunc: the flops of the Jacobi sweeps its matrices took, counted on
+ * the device, 6 nc (nc - 1) len per sweep of an nc-column matrix of column length len, plus
+ * 3 nc (nc - 1) m when its m x m right vectors are accumulated); up to
  * `cap` entries are written to `out` (caller-owned) and the number of kernels to *n_out.
  * EINVAL on bad arguments. */
 typedef struct {

@@ -255,6 +255,7 @@ struct BatchImpl : BatchIface {
   long long No = 0;
   double *es_tmp = nullptr, *ea_tmp = nullptr;
   uint32_t* d_sweep = nullptr;   // the sweep number the accept kernels read
+  double* jflops_dev = nullptr;  // Jacobi flop counter, fed while per-launch profiling is on
   // CUDA graphs: one captured launch sequence per (operation, exponent or cache use, chunk,
   // buffers), replayed on later calls; its flops and launch count are those of the capture
   struct Graph {
@@ -325,9 +326,11 @@ struct BatchImpl : BatchIface {
     if (be.prof) be.prof->launches += it->second.launches;
   }
 
+  void count_jacobi() { run.jflops = be.prof && be.prof->on ? jflops_dev : nullptr; }
   void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea, void* O,
             bool cached) override {
     run.flops = 0;
+    count_jacobi();
     for (int off = 0; off < nb; off += chunk) {
       int n = std::min(chunk, nb - off);
       const bool cu = cached && nb <= chunk;
@@ -343,6 +346,7 @@ struct BatchImpl : BatchIface {
   void mc(uint8_t* S, int n_all, int p, uint64_t seed, long long sweep0, int n_sweeps, int* acc,
           int* prop) override {
     run.flops = 0;
+    count_jacobi();
     run.sweep_dev = d_sweep;
     for (int off = 0; off < n_all; off += chunk) {
       int n = std::min(chunk, n_all - off);
@@ -360,6 +364,7 @@ struct BatchImpl : BatchIface {
   void draw(uint8_t* S, int n_all, const double* u, double b_d, double expo,
             double* logq) override {
     run.flops = 0;
+    count_jacobi();
     for (int off = 0; off < n_all; off += chunk) {
       const int n = std::min(chunk, n_all - off);
       direct_draw(run, S + (long long)off * N, n, u + (long long)off * N, b_d, expo, logq + off);
@@ -479,6 +484,7 @@ struct peps_ctx {
   bool direct_valid = false;            // the chains are the last direct draw, unchanged
   uint32_t n_draws = 0;
   pv::KProf kprof;                      // launch counter, optional per-kernel timing
+  double* d_jflops = nullptr;           // Jacobi flops of the truncations while profiling
   bool o_vec4 = false;                  // every site slice of O holds a multiple of 4 entries
 };
 
@@ -637,6 +643,11 @@ int init_runner_t(peps_ctx* c, int sms, BatchImpl<T>* b, int Dn, const T* theta,
   if ((rc = dalloc(c, &dbl, (size_t)nd * chunk * sizeof(double)))) return rc;
   if ((rc = dalloc(c, &b->es_tmp, (size_t)chunk * sizeof(double)))) return rc;
   if ((rc = dalloc(c, &b->d_sweep, sizeof(uint32_t)))) return rc;
+  if (!c->d_jflops) {
+    if ((rc = dalloc(c, &c->d_jflops, sizeof(double)))) return rc;
+    PV_CUDA(c, cudaMemset(c->d_jflops, 0, sizeof(double)));
+  }
+  b->jflops_dev = c->d_jflops;
   if ((rc = dalloc(c, &b->ea_tmp, (size_t)chunk * sizeof(double)))) return rc;
   std::vector<int> bi, bj;
   std::vector<double> bJ;
@@ -676,6 +687,8 @@ int init_runner_t(peps_ctx* c, int sms, BatchImpl<T>* b, int Dn, const T* theta,
       b->be.chol_wide_max = e == cudaSuccess ? tw_max : 0;
       if (e != cudaSuccess) cudaGetLastError();
     }
+    e = cudaFuncSetAttribute(kb_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
     const int lq2_max = 200 * 1024;
     e = cudaFuncSetAttribute(kb_lq2<T, LQ_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, lq2_max);
     b->be.lq2_smem_max = e == cudaSuccess ? lq2_max : 0;
@@ -1494,10 +1507,10 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     cur = before;
     // coordinate descent over the launch-shape parameters (results are the same for all)
     const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, kc_c[] = {16, 32, 64},
-              p_c[] = {0, 1, 1}, g_c[] = {1, 16, 256};
-    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.pipelined, &tu.ffma_g};
-    const int* cands[] = {grid_c, db_c, kc_c, p_c, g_c};
-    for (int knob = c->batch->uses_tensor_cores() ? 0 : 4; knob < 5; ++knob) {
+              p_c[] = {0, 1, 2}, sb_c[] = {64 * 1024, 96 * 1024, 192 * 1024}, g_c[] = {1, 16, 256};
+    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.pipelined, &tu.stage_budget, &tu.ffma_g};
+    const int* cands[] = {grid_c, db_c, kc_c, p_c, sb_c, g_c};
+    for (int knob = c->batch->uses_tensor_cores() ? 0 : 5; knob < 6; ++knob) {
       int* field = fields[knob];
       const int* cand = cands[knob];
       int best_v = *field;
@@ -1528,6 +1541,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     out->ffma_g = tu.ffma_g;
     out->kc_max = tu.kc_max;
     out->pipelined = tu.pipelined;
+    out->stage_kb = tu.stage_budget / 1024;
     out->ms_before = before;
     out->ms_after = cur;
   }
@@ -1635,7 +1649,8 @@ int peps_su_warm_start(peps_ctx* c, double tau, int n_steps) {
 int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   if (!c || !t || t->grid_pct < 1 || t->grid_pct > 400 || t->db_bytes < 0 ||
       t->db_bytes > 200 * 1024 || t->ffma_g < 1 || t->ffma_g > 256 || t->kc_max < 8 ||
-      t->kc_max > 64 || t->kc_max % 8 || t->pipelined < 0 || t->pipelined > 1)
+      t->kc_max > 64 || t->kc_max % 8 || t->pipelined < 0 || t->pipelined > 2 ||
+      (t->stage_kb != 0 && (t->stage_kb < 32 || t->stage_kb > 200)))
     return fail(c, PEPS_EINVAL, "set_tune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "set_tune: only the batched engine has launch shapes");
   BatchTune& tu = c->batch->tuning();
@@ -1644,6 +1659,7 @@ int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   tu.ffma_g = t->ffma_g;
   tu.kc_max = t->kc_max;
   tu.pipelined = t->pipelined;
+  if (t->stage_kb) tu.stage_budget = t->stage_kb * 1024;
   c->batch->drop_graphs();   // the captured sequences used the old shapes
   return PEPS_OK;
 }
@@ -1655,6 +1671,7 @@ int peps_profile(peps_ctx* c, int enable) {
     c->kprof.reset();
     c->kprof.on = true;
     c->kprof.gemm_only = enable == 2;
+    if (c->d_jflops) PV_CUDA(c, cudaMemset(c->d_jflops, 0, sizeof(double)));
   } else {
     c->kprof.fold();
     c->kprof.on = false;
@@ -1666,6 +1683,9 @@ int peps_profile_read(peps_ctx* c, peps_kernel_stat* out, int cap, int* n_out) {
   if (!c || cap < 0 || (cap > 0 && !out) || !n_out) return fail(c, PEPS_EINVAL, "profile_read: args");
   PV_CUDA(c, cudaStreamSynchronize(c->stream));
   c->kprof.fold();
+  // the truncations' flops depend on their Jacobi sweeps: counted on the device
+  double jf = 0;
+  if (c->d_jflops) PV_CUDA(c, cudaMemcpy(&jf, c->d_jflops, sizeof(double), cudaMemcpyDeviceToHost));
   const auto& acc = c->kprof.acc;
   *n_out = (int)acc.size();
   for (int i = 0; i < cap && i < (int)acc.size(); ++i) {
@@ -1674,7 +1694,7 @@ int peps_profile_read(peps_ctx* c, peps_kernel_stat* out, int cap, int* n_out) {
     out[i].launches = acc[i].launches;
     out[i].ms = acc[i].ms;
     out[i].bytes = acc[i].bytes;
-    out[i].flops = acc[i].flops;
+    out[i].flops = acc[i].flops + (acc[i].name == "kb_trunc" ? jf : 0.0);
   }
   return PEPS_OK;
 }

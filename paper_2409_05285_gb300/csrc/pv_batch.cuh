@@ -323,6 +323,7 @@ struct OpTrunc {
   T jtol;
   int max_sweeps;
   unsigned long long* sweeps;
+  double* jflops;   // when set: += flops of the Jacobi sweeps this matrix took
   PV_HD void operator()(int s, T* red, int* flag, T* smem, long long smem_cap, int* order,
                         T* sig) const {
     const T* Ys = Y + (long long)s * ys;
@@ -381,10 +382,15 @@ struct OpTrunc {
     double l = normalize_maxabs(o, (long long)m * kk, red);
     if (PV_TID == 0) {
       lsv[(long long)s * lstride] += l;
+      // a sweep visits nc (nc - 1) / 2 column pairs: three dot products and a rotation of two
+      // columns of length len, and of two columns of V when it is accumulated
+      const double jf = (double)sw * 0.5 * nc * (nc - 1) * (12.0 * len + (tall ? 0.0 : 6.0 * m));
 #if defined(__CUDA_ARCH__)
       atomicAdd(sweeps, (unsigned long long)sw);
+      if (jflops) atomicAdd(jflops, jf);
 #else
       *sweeps += (unsigned long long)sw;
+      if (jflops) *jflops += jf;
 #endif
     }
     PV_SYNC();
@@ -663,6 +669,7 @@ struct BatchRunner {
   bool gram_lq = false;   // right factors from the Gram matrix (the TF32 path)
   const uint32_t* sweep_dev = nullptr;   // Metropolis sweep number in device memory, if set
   unsigned long long* sweeps;   // Jacobi sweep counter (device or host)
+  double* jflops = nullptr;     // Jacobi flop counter (profiling), or none
 
   BatchRunner(BE& be_) : be(be_) {}
 
@@ -760,7 +767,7 @@ struct BatchRunner {
       ein(b.W, b.CB, "apk", bat(b.Cs, b.CB), "apb", bat(b.Lf + (long long)(c + 1) * b.LB, b.sLf),
           "bk", dm, n);
       int m = bc[c], nn = p * kf[c + 1];
-      if (gram_lq && nn >= m && m >= 16) {
+      if (gram_lq && nn >= m && m >= 16 && be.chol_fits(m)) {
         // a factor of the right Gram matrix W W^T (float32 products, semidefinite Cholesky)
         Dims dg;
         dg.set('a', m).set('e', m).set('p', p).set('k', kf[c + 1]);
@@ -789,7 +796,7 @@ struct BatchRunner {
       int kk = chi < kmax ? chi : kmax;
       T* o = outrow + (long long)c * b.ENV;
       be.trunc(OpTrunc<T>{b.Y, b.LB, tall, nc, len, m, kk, b.Uk, (long long)chi * chi * D, o, os,
-                          ls, lstride, jtol, max_sweeps, sweeps},
+                          ls, lstride, jtol, max_sweeps, sweeps, jflops},
                n);
       Dims dc;
       dc.set('q', m).set('j', kk).set('b', bb);
@@ -827,6 +834,14 @@ struct BatchRunner {
       compress(downrow(r + 1), b.sD, shp.down[r + 1], true, r, S, downrow(r), b.sD, b.lsD + r,
                L1 + 1, n);
     }
+  }
+
+  // Down environments that are the same for every chain (direct sampling's all-summed
+  // rows): chain 0's, with its log scales, copied to chains 1..n-1.
+  void broadcast_down(int n) {
+    if (n <= 1) return;
+    be.copy_masked(b.envD + b.sD, b.sD, b.envD, 0, b.sD, nullptr, n - 1);
+    be.bcastd(b.lsD, L1 + 1, L1 + 1, n);
   }
 
   // ----------------------------------------------------------------- strips
@@ -1491,6 +1506,12 @@ __global__ void kb_fill_u8(uint8_t* x, uint8_t v, long long count) {
     x[k] = v;
 }
 
+__global__ void kb_bcastd(double* x, long long xs, long long len, int n) {
+  const int s = blockIdx.y + 1;
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < n && k < len) x[(long long)s * xs + k] = x[k];
+}
+
 __global__ void kb_copyd(double* x, long long xs, int dst, int src, int n) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < n) x[(long long)s * xs + dst] = x[(long long)s * xs + src];
@@ -1514,6 +1535,10 @@ __global__ void kb_O(OT* O, long long No, long long o_off, const T* env, long lo
   if (k < sz) O[(long long)s * No + o_off + k] = (OT)((double)env[(long long)s * es + k] / (double)val[(long long)s * vs]);
 }
 
+// Longest contraction of the FFMA GEMM: its per-K offset tables and 24 KB of operand tiles
+// stay within the 96 KB of dynamic shared memory the kernel is given (kb_ein otherwise).
+constexpr int FFMA_K_MAX = 8192;
+
 // Launch-shape parameters of the batched engine, chosen by the autotuner; none of them
 // changes any result (each chain's arithmetic is the same in every choice).
 struct BatchTune {
@@ -1521,7 +1546,8 @@ struct BatchTune {
   int db_bytes = 12 * 1024;    // largest operand stage that gets two stages
   int ffma_g = 256;            // most chains per block of the FFMA GEMM
   int kc_max = 64;             // largest contraction chunk of the tensor-core GEMM
-  int pipelined = 1;           // tensor-core GEMM: the cp.async pipeline (kb_gemm_tc2)
+  int pipelined = 1;           // tensor-core GEMM on the cp.async pipeline (kb_gemm_tc2): 0 none,
+                               // 1 short vector contractions (K <= 64), 2 every vector one
   int stage_budget = 96 * 1024;   // ... bytes of copy stages per CTA
 };
 
@@ -1638,7 +1664,7 @@ struct CudaBE {
         // 8 indices; element-wise gathers, long and split contractions stay on the
         // register-staged kernel
         const bool vec = t.modeP != TC_SCALAR && t.modeQ != TC_SCALAR;
-        if (tune.pipelined && ((vec && !t.split && t.K <= 64) || t.K <= 8)) {
+        if (tune.pipelined && ((vec && !t.split && (t.K <= 64 || tune.pipelined == 2)) || t.K <= 8)) {
           // pipelined kernel: cp.async ring of stages over (chain, contraction chunk) items
           if (t.Kc > tune.kc_max) t.Kc = tune.kc_max;
           tc2_shape(t, (size_t)tune.stage_budget);
@@ -1700,7 +1726,7 @@ struct CudaBE {
         }
       }
     }
-    if (gs.ok && gs.K > 1) {
+    if (gs.ok && gs.K > 1 && gs.K <= FFMA_K_MAX) {
       int Np = ((gs.N + 3) / 4) * 4;
       int TN = 4;
       while (TN < Np && TN < 64) TN <<= 1;
@@ -1771,6 +1797,12 @@ struct CudaBE {
     PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
                kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap, trunc_g));
   }
+  // Whether an m x m Gram factorisation fits the shared memory of one kb_chol block (the
+  // compression takes the Householder factors otherwise).
+  bool chol_fits(int m) const {
+    const size_t bytes = (size_t)m * (m + 1) * sizeof(T);
+    return bytes <= 200 * 1024 || (int)bytes <= chol_wide_max;
+  }
   void chol(OpChol<T> op, int n) {
     const size_t bytes = (size_t)op.m * (op.m + 1) * sizeof(T);
     if (bytes > 96 * 1024 && (int)bytes <= chol_wide_max) {
@@ -1790,6 +1822,12 @@ struct CudaBE {
   void set(T* x, long long xs, long long off, T v, int n) { PV_KLAUNCH(prof, st, "kb_set", 0.0, 0.0, kb_set<T><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n)); }
   void setd(double* x, long long xs, long long off, double v, int n) {
     PV_KLAUNCH(prof, st, "kb_set", 0.0, 0.0, kb_set<double><<<gx(n, 256), 256, 0, st>>>(x, xs, off, v, n));
+  }
+  // x[s][0..len) = x[0][0..len) for s = 1..n-1
+  void bcastd(double* x, long long xs, long long len, int n) {
+    if (n <= 1) return;
+    dim3 g(gx(len, 128), n - 1);
+    PV_KLAUNCH(prof, st, "kb_copyd", 0.0, 0.0, kb_bcastd<<<g, 128, 0, st>>>(x, xs, len, n));
   }
   void copyd(double* x, long long xs, int dst, int src, int n) {
     PV_KLAUNCH(prof, st, "kb_copyd", 0.0, 0.0, kb_copyd<<<gx(n, 256), 256, 0, st>>>(x, xs, dst, src, n));

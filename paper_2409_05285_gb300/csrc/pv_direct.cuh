@@ -6,7 +6,7 @@
 // a BatchRunner built for bond dimension D^2 over those tensors draws the samples with the
 // operations it already has:
 //   * the down environments of the all-summed rows (local index 4 everywhere; the same for
-//     every chain);
+//     every chain, so built for one and copied);
 //   * row by row, the right partials of the one-row strip with the row still summed, then
 //     per site the four candidates' strip values (left partial x candidate x right partial),
 //     one elementwise draw (ElemDraw), and the left partial extended by the drawn tensor;
@@ -109,7 +109,8 @@ void direct_draw(BatchRunner<T, BE, OT>& run, uint8_t* S, int n, const double* u
   const int L1 = run.L1, L2 = run.L2, N = run.N;
   be.fill_u8(S, 4, (long long)n * N);   // every site summed
   be.setd(logq, 1, 0, 0.0, n);
-  run.build_down(S, n);
+  run.build_down(S, 1);   // every chain's down environments are the same: build one, copy
+  run.broadcast_down(n);
   run.trivial(run.uprow(0), b.sU, n);
   be.setd(b.lsU, 1, 0, 0.0, n);
   T* cand[4] = {b.val, b.num, b.den, b.val2};

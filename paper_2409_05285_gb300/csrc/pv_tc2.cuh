@@ -35,8 +35,13 @@ inline size_t tc2_smem_bytes(const TcSpec& t) {
 
 // Chooses the contraction chunk, the number of stages and of accumulators of the pipelined
 // kernel: about `budget` bytes of stages per CTA, at least three stages where chunks of 8
-// allow it, two accumulators when their columns fit in 256 (two CTAs per SM).
+// allow it, two accumulators when their columns fit in 256 (two CTAs per SM), or in 512 when
+// the stages take more than half the shared memory (one CTA per SM anyway).
 inline void tc2_shape(TcSpec& t, size_t budget) {
+  // the stages and the offset tables stay within the 200 KB the kernel is configured for
+  const size_t tables = (size_t)(2 * TC_ROWS + 2 * t.TN + 2 * t.K) * sizeof(int) + 128;
+  const size_t cap = 200 * 1024 > tables ? 200 * 1024 - tables : 0;
+  budget = budget < cap ? budget : cap;
   const int k8 = ((t.K + 7) / 8) * 8;
   t.Kc = k8 < t.Kc ? k8 : t.Kc;
   if (t.Kc > 32) t.Kc = 32;
@@ -49,7 +54,7 @@ inline void tc2_shape(TcSpec& t, size_t budget) {
     }
     t.Kc -= 8;
   }
-  t.nacc = tc_cols(2 * t.TN) <= 256 ? 2 : 1;
+  t.nacc = tc_cols(2 * t.TN) <= (budget > 114 * 1024 ? 512 : 256) ? 2 : 1;
 }
 
 #if defined(__CUDACC__)

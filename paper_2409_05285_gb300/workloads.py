@@ -8,6 +8,9 @@ Workloads (the paper's benchmark shapes, Sec. III.A; no dataset is involved):
   heis4   4x4 open Heisenberg (J1=1), D=2, chi=4, FP64; Ns=2000, eps=1e-4, tau=0.02, 50 steps.
   heis8   8x8 open Heisenberg (J1=1), D=4, chi=16; 8192 chains; tau=0.02, 200 steps.
   j1j2_10 10x10 open J1-J2 (J1=1, J2=0.5), D=6, chi=36; Ns=16384; eps=1e-4, <=100 CG its.
+  direct6 6x6 open Heisenberg (J1=1), D=2, chi=16, 30000 reweighted direct samples per SR
+          step (App. A, Eqs. A2-A7; the sample count and lattice of the paper's direct-sampled
+          runs, Sec. III.B, on the spin model), from the perturbed beta=0 state, b_d from 1.
 """
 from dataclasses import dataclass, field
 
@@ -38,6 +41,8 @@ WORKLOADS = {
     "heis8": Workload("heis8", L=8, D=4, chi=16, n_samples=8192, tau=0.02, n_steps=200),
     "j1j2_10": Workload("j1j2_10", L=10, D=6, chi=36, J2=0.5, n_samples=16384, tau=0.01,
                         n_steps=300),
+    "direct6": Workload("direct6", L=6, D=2, chi=16, n_samples=30000, tau=0.02, n_steps=100,
+                        extra={"exponent": 0.5, "b_d0": 1.0, "su_t": 0.0}),
 }
 
 

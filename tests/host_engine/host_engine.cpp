@@ -52,6 +52,7 @@ struct HostBE {
   }
   // Semidefinite Cholesky of each chain's m x m Gram matrix, lower factor Lf (pivots below
   // m eps max(diag) zero their column), as the Gram path of the compression expects.
+  bool chol_fits(int) const { return true; }
   void chol(OpChol<T> op, int n) {
     const int m = op.m;
     const T eps = 2.220446049250313e-16;
@@ -85,6 +86,10 @@ struct HostBE {
   }
   void setd(double* x, long long xs, long long off, double v, int n) {
     for (int s = 0; s < n; ++s) x[(long long)s * xs + off] = v;
+  }
+  void bcastd(double* x, long long xs, long long len, int n) {
+    for (int s = 1; s < n; ++s)
+      for (long long k = 0; k < len; ++k) x[(long long)s * xs + k] = x[k];
   }
   void copyd(double* x, long long xs, int dst, int src, int n) {
     for (int s = 0; s < n; ++s) x[(long long)s * xs + dst] = x[(long long)s * xs + src];

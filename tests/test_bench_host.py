@@ -77,6 +77,14 @@ def test_kernel_roofline_arithmetic():
     ks = {"k_gv": (10, 5.0, 10 * 3.0e9, 0.0)}
     roof, _ = bench.kernel_roofline(ks, peaks, 2, B)
     assert roof["bound"] == "hbm" and roof["achieved"] == pytest.approx(3.0e9 / 0.5e-3 / 1e9)
+    # the Jacobi truncation: FMA-bound against the derived FP32 (FP64) rate
+    ks = {"kb_trunc": (30, 200.0, 30 * 1.0e8, 30 * 4.0e11), "kb_gemm": (10, 1.0, 1.0e7, 0.0)}
+    roof, _ = bench.kernel_roofline(ks, peaks, 2, B)
+    assert roof["kernel"] == "kb_trunc" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    assert roof["achieved"] == pytest.approx(4.0e11 / (200.0 / 30 / 1e3) / 1e12)
+    assert roof["peak"] == pytest.approx(bench.PEAK_FP32_TFLOPS)
+    roof, _ = bench.kernel_roofline(ks, peaks, 0, B)
+    assert roof["peak"] == pytest.approx(bench.PEAK_FP64_TFLOPS)
 
 
 def test_both_arms_share_the_config_object():
@@ -108,13 +116,10 @@ def test_cooling_starts_from_the_warm_start_time():
     assert abs(t - 0.16) < 1e-12 and c.ps == [2, 2, 2]
 
 
-def test_default_run_prints_the_contract_line(monkeypatch, capsys):
-    # bench.py's own arm end to end on the CPU with a stand-in library and stand-in CUDA
-    # events: the JSON line carries every key of the contract, with the recorded traffic
+def _stand_in_cuda(monkeypatch, bench, Ctx, argv):
+    # stand-in CUDA events, stream, clocks and library build for bench.py's arms on the CPU
     import sys as _sys
-    import numpy as np
     import torch
-    bench = _bench()
     from paper_2409_05285_gb300 import binding, build as build_mod
 
     class Ev:
@@ -136,6 +141,36 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
 
     class Stream:
         cuda_stream = 0
+
+    class Clocks:
+        def __init__(self, index):
+            pass
+
+        def start(self):
+            pass
+
+        def stop(self):
+            return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+
+    monkeypatch.setattr(torch.cuda, "set_device", lambda i: None)
+    monkeypatch.setattr(torch.cuda, "Stream", Stream)
+    monkeypatch.setattr(torch.cuda, "Event", Ev)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
+    monkeypatch.setattr(torch.cuda.profiler, "start", lambda: None)
+    monkeypatch.setattr(torch.cuda.profiler, "stop", lambda: None)
+    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
+    monkeypatch.setattr(build_mod, "build", lambda *a, **k: None)
+    monkeypatch.setattr(binding, "Context", Ctx)
+    monkeypatch.setattr(bench, "Clocks", Clocks)
+    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 6794.1})
+    monkeypatch.setattr(_sys, "argv", argv)
+
+
+def test_default_run_prints_the_contract_line(monkeypatch, capsys):
+    # bench.py's own arm end to end on the CPU with a stand-in library and stand-in CUDA
+    # events: the JSON line carries every key of the contract, with the recorded traffic
+    import numpy as np
+    bench = _bench()
 
     class Ctx:
         def __init__(self, L1, L2, D, chi, n, **kw):
@@ -191,29 +226,8 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
         def close(self):
             pass
 
-    class Clocks:
-        def __init__(self, index):
-            pass
-
-        def start(self):
-            pass
-
-        def stop(self):
-            return {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
-
-    monkeypatch.setattr(torch.cuda, "set_device", lambda i: None)
-    monkeypatch.setattr(torch.cuda, "Stream", Stream)
-    monkeypatch.setattr(torch.cuda, "Event", Ev)
-    monkeypatch.setattr(torch.cuda, "synchronize", lambda: None)
-    monkeypatch.setattr(torch.cuda.profiler, "start", lambda: None)
-    monkeypatch.setattr(torch.cuda.profiler, "stop", lambda: None)
-    monkeypatch.setattr(torch.Tensor, "pin_memory", lambda self: self)
-    monkeypatch.setattr(build_mod, "build", lambda *a, **k: None)
-    monkeypatch.setattr(binding, "Context", Ctx)
-    monkeypatch.setattr(bench, "Clocks", Clocks)
-    monkeypatch.setattr(bench, "measured_peaks", lambda: {"hbm_gbs": 6794.1})
-    monkeypatch.setattr(_sys, "argv", ["bench.py", "--steps", "2", "--no-cpu-baseline",
-                                       "--no-fp64-check", "--largest", "1"])
+    _stand_in_cuda(monkeypatch, bench, Ctx, ["bench.py", "--steps", "2", "--no-cpu-baseline",
+                                             "--no-fp64-check", "--largest", "1"])
     bench.main()
     out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
@@ -235,3 +249,79 @@ def test_default_run_prints_the_contract_line(monkeypatch, capsys):
         assert roof["traffic"] == pytest.approx(rec["dram_bytes"] / rec["alg_bytes"] * roof["bytes_per_launch"], rel=1e-9)
     assert set(out["e2e"]) == {"value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"}
     assert out["gpu_launches"] > 0
+
+
+def test_direct_run_prints_the_contract_line(monkeypatch, capsys):
+    # bench.py --direct end to end on the CPU with a stand-in library: draw, evaluation and
+    # p = 0 SR per step, b_d carried between steps by the library's rule, the truncation's
+    # roofline on the FMA rate
+    import numpy as np
+    bench = _bench()
+    from paper_2409_05285_gb300 import binding
+    calls = []
+
+    class Ctx:
+        def __init__(self, L1, L2, D, chi, n, **kw):
+            self.n, self.N = n, L1 * L2
+            self.No = self.N * D ** 4
+            self.k = 0
+            assert kw["block_mode"] == binding.PEPS_BLOCKS_BATCHED
+
+        def set_graphs(self, on):
+            pass
+
+        def su_warm_start(self, tau, n_steps):
+            calls.append(("su", tau, n_steps))
+
+        def direct_step(self, b_d, exponent=0.5, **kw):
+            self.k += 50
+            return {"diag_frac": 0.9}, b_d * 0.9
+
+        def direct_draw(self, u=None, b_d=1.0, exponent=0.5):
+            calls.append(("draw", None if u is None else u.shape, b_d))
+            self.k += 40
+            return np.zeros(self.n)
+
+        def eval_chains(self):
+            self.k += 20
+
+        def sr_step(self, tau, eps, max_cg, cg_tol, p):
+            assert p == 0
+            return {"cg_iters": 7, "E_site": -0.05, "E_err": 1e-3, "beta_obs": 0.9,
+                    "cg_resid": 1e-9, "diag_frac": 0.75}
+
+        def profile(self, on, gemm_only=False):
+            pass
+
+        def profile_read(self):
+            return {"kb_trunc": (30, 200.0, 30 * 1.0e8, 30 * 4.0e11),
+                    "kb_gemm_tc2": (384, 150.0, 384 * 5.0e8, 384 * 2.5e9)}
+
+        def counters(self):
+            return 2.0e12, 5.0 * self.n
+
+        def launches(self):
+            return self.k
+
+        def close(self):
+            pass
+
+    _stand_in_cuda(monkeypatch, bench, Ctx, ["bench.py", "--direct", "--steps", "2",
+                                             "--no-cpu-baseline"])
+    bench.main()
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "e2e", "gpu_launches", "clocks"):
+        assert key in out, key
+    assert "6x6" in out["config"]["workload"] and "30000 direct samples" in out["config"]["workload"]
+    assert out["value"] == pytest.approx(30000 / (out["ms_per_step"] / 1e3))
+    assert out["roofline"]["kernel"] == "kb_trunc" and out["roofline"]["bound"] == "alu"
+    assert not any(c[0] == "su" for c in calls)   # direct6 starts from the beta = 0 state
+    # warm-up steps lower b_d by the stand-in's 0.9; then the library's rule on diag 0.75
+    b = [c[2] for c in calls if c[0] == "draw"]
+    assert b[0] == pytest.approx(0.81)
+    assert b[1] == pytest.approx(binding.direct_next_bd(0.81, 0.75, 36))
+    assert out["b_d"][0] == pytest.approx(b[1])
+    assert out["e2e"]["h2d_bytes_per_step"] == 30000 * 36 * 8
+    assert any(c[0] == "draw" and c[1] == (30000, 36) for c in calls)

@@ -24,12 +24,13 @@ def test_autotune_keeps_results_and_is_shared_by_geometry():
     assert tune["db_bytes"] in (0, 12 * 1024, 48 * 1024)
     assert tune["ffma_g"] in (1, 16, 256)
     assert tune["kc_max"] in (16, 32, 64)
-    assert tune["pipelined"] in (0, 1)
+    assert tune["pipelined"] in (0, 1, 2)
+    assert tune["stage_kb"] in (64, 96, 192)
     assert 0 < tune["ms_after"] <= tune["ms_before"]
     ctx.sr_step(0.02)   # the tuner left a valid evaluation of the chains behind
     ctx2 = binding.Context(L, L, D, chi, 64, precision=binding.PEPS_TF32, seed=5)
     t2 = ctx2.autotune(reps=0)
-    keys = ("grid_pct", "db_bytes", "ffma_g", "kc_max", "pipelined")
+    keys = ("grid_pct", "db_bytes", "ffma_g", "kc_max", "pipelined", "stage_kb")
     assert [t2[k] for k in keys] == [tune[k] for k in keys]
     ctx.close()
     ctx2.close()
@@ -43,15 +44,19 @@ def test_pinned_shapes_keep_results():
     S = ctx.get_configs()
     ctx.set_tune(100, 12 * 1024, 256, 64)
     ref = ctx.eval_batch(S)
-    # both tensor-core kernel forms (register-staged, cp.async-pipelined) give the same bits
-    for shapes in ((50, 0, 16, 16, 0), (200, 48 * 1024, 1, 32, 1), (100, 12 * 1024, 256, 8, 0),
-                   (100, 12 * 1024, 256, 64, 1)):
+    # both tensor-core kernel forms (register-staged, cp.async-pipelined for short or for all
+    # vector contractions, with stage rings of 64-192 KB) give the same bits
+    for shapes in ((50, 0, 16, 16, 0, 96), (200, 48 * 1024, 1, 32, 1, 64), (100, 12 * 1024, 256, 8, 0, 96),
+                   (100, 12 * 1024, 256, 64, 1, 192), (100, 12 * 1024, 256, 64, 2, 96),
+                   (100, 12 * 1024, 256, 32, 2, 192)):
         ctx.set_tune(*shapes)
         got = ctx.autotune(reps=0)
-        assert (got["grid_pct"], got["db_bytes"], got["ffma_g"], got["kc_max"], got["pipelined"]) == shapes
+        keys = ("grid_pct", "db_bytes", "ffma_g", "kc_max", "pipelined", "stage_kb")
+        assert tuple(got[k] for k in keys) == shapes
         for a, b in zip(ref, ctx.eval_batch(S)):
             assert np.array_equal(a, b)
-    for bad in ((0, 0, 16, 64), (100, 0, 0, 64), (100, 0, 16, 12), (100, 0, 16, 72), (100, 0, 16, 64, 2)):
+    for bad in ((0, 0, 16, 64), (100, 0, 0, 64), (100, 0, 16, 12), (100, 0, 16, 72), (100, 0, 16, 64, 3),
+                (100, 0, 16, 64, 1, 16), (100, 0, 16, 64, 1, 256)):
         with pytest.raises(RuntimeError):
             ctx.set_tune(*bad)
     ctx.close()

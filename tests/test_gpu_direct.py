@@ -61,6 +61,46 @@ def test_fp64_draws_match_oracle(case):
     ctx.close()
 
 
+def test_draws_at_the_bench_size():
+    # the bench's geometry and launch configuration (6x6, D=2, chi=16, 30000 chains, TF32,
+    # host uniforms): sampled chains against the oracle's boundary-MPS draws for the same
+    # uniforms, and the FP64 engine on the first 256 of those chains.  Here chi = 16 cuts the
+    # double layer's boundary bonds (exact: 64) through close singular values, so log q is
+    # ill-conditioned for any implementation: the oracle's own log q moves by up to 2e-3 when
+    # theta is perturbed by 1e-13 relative.  The bound on |d log q| is 5e-3 for FP64 and 3e-2
+    # for TF32 (36 sites, each a ratio of candidate sums carrying ~1e-3 TF32 rounding); a
+    # draw may differ where a uniform sits that close to a CDF edge.
+    L, D, chi, n = 6, 2, 16, 30000
+    lat = Lattice(L, L, D)
+    th = wl.random_theta(L, L, D, seed=61, scale=0.4, diag_bias=1.0)
+    u = np.random.default_rng(62).random((n, lat.N))
+    ctx = _ctx(L, L, D, chi, n, prec=binding.PEPS_TF32)
+    ctx.set_theta(th)
+    lq = ctx.direct_draw(u, 0.6, 0.5)
+    S = ctx.get_configs()
+    ctx.close()
+    ref = _ctx(L, L, D, chi, 256)
+    ref.set_theta(th)
+    lq64 = ref.direct_draw(u[:256], 0.6, 0.5)
+    S64 = ref.get_configs()
+    ref.close()
+    down = direct.summed_down_envs(lat, th, chi)
+    picks = [0, 1, 2, 3, 255, 4097, 17000, n - 1]
+    agree, agree64 = 0, 0
+    for k in picks:
+        So, lqo = direct.draw_bmps(lat, th, u[k], chi, 0.6, 0.5, down=down)
+        if k < 256 and np.array_equal(S64[k], So):
+            agree64 += 1
+            assert abs(lq64[k] - lqo) <= 5e-3, k
+        if np.array_equal(S[k], So):
+            agree += 1
+            assert abs(lq[k] - lqo) <= 3e-2, k
+    assert agree64 >= 4 and agree >= len(picks) - 1
+    assert np.mean(np.all(S[:256] == S64, axis=1)) >= 0.9
+    counts = np.bincount(S.ravel(), minlength=4)
+    assert np.all(counts > 0)   # every local state, s = s' and s != s', is drawn
+
+
 @pytest.mark.parametrize("prec", [binding.PEPS_FP32, binding.PEPS_TF32])
 def test_float_draws_follow_their_own_q(prec):
     # float engines: each draw is a valid state whose log q matches the oracle's exact q of
