@@ -266,13 +266,15 @@ typedef struct {
                       the register-staged kernel */
   int stage_kb;    /* shared memory of the pipelined kernel's stage ring per CTA, KB (32..200;
                       0 in peps_set_tune keeps the current value) */
+  int trunc_threads; /* threads of a Jacobi truncation block whose matrix fits in shared
+                        memory: 32, 64, 128 or 256 (0 in peps_set_tune keeps the value) */
 } peps_tune;
 int peps_autotune(peps_ctx* ctx, int reps, peps_tune* out);
 /* Sets the batched engine's launch shapes (every field of `t` but the times) for this
  * context, e.g. to repeat a run with the shapes an earlier autotune chose.  No choice changes
  * any result.  EINVAL for values outside grid_pct 1..400, db_bytes 0..200 KB, ffma_g 1..256,
- * kc_max a multiple of 8 in 8..64, pipelined 0..2, stage_kb 0 or 32..200; ESTATE without the
- * batched engine. */
+ * kc_max a multiple of 8 in 8..64, pipelined 0..2, stage_kb 0 or 32..200, trunc_threads 0, 32,
+ * 64, 128 or 256; ESTATE without the batched engine. */
 int peps_set_tune(peps_ctx* ctx, const peps_tune* t);
 
 /* Simple-update warm start (App. A): from the beta = 0 state, n_steps first-order Trotter

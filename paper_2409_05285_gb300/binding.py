@@ -54,7 +54,8 @@ class Params(ctypes.Structure):
 class Tune(ctypes.Structure):
     _fields_ = [("grid_pct", ctypes.c_int), ("db_bytes", ctypes.c_int), ("ffma_g", ctypes.c_int),
                 ("kc_max", ctypes.c_int), ("ms_before", ctypes.c_double), ("ms_after", ctypes.c_double),
-                ("pipelined", ctypes.c_int), ("stage_kb", ctypes.c_int)]
+                ("pipelined", ctypes.c_int), ("stage_kb", ctypes.c_int),
+                ("trunc_threads", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -239,11 +240,11 @@ class Context:
         self._check(self.lib.peps_autotune(self.ctx, reps, ctypes.byref(t)))
         return {f: getattr(t, f) for f, _ in Tune._fields_}
 
-    def set_tune(self, grid_pct, db_bytes, ffma_g, kc_max, pipelined=1, stage_kb=0):
-        """Pins the batched engine's launch shapes (results are unchanged); stage_kb=0 keeps
-        the pipelined kernel's stage ring as it is."""
+    def set_tune(self, grid_pct, db_bytes, ffma_g, kc_max, pipelined=1, stage_kb=0, trunc_threads=0):
+        """Pins the batched engine's launch shapes (results are unchanged); stage_kb=0 and
+        trunc_threads=0 keep those two as they are."""
         t = Tune(grid_pct=grid_pct, db_bytes=db_bytes, ffma_g=ffma_g, kc_max=kc_max,
-                 pipelined=pipelined, stage_kb=stage_kb)
+                 pipelined=pipelined, stage_kb=stage_kb, trunc_threads=trunc_threads)
         self._check(self.lib.peps_set_tune(self.ctx, ctypes.byref(t)))
 
     def launches(self):

@@ -1507,10 +1507,12 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     cur = before;
     // coordinate descent over the launch-shape parameters (results are the same for all)
     const int grid_c[] = {50, 100, 200}, db_c[] = {0, 12 * 1024, 48 * 1024}, kc_c[] = {16, 32, 64},
-              p_c[] = {0, 1, 2}, sb_c[] = {64 * 1024, 96 * 1024, 192 * 1024}, g_c[] = {1, 16, 256};
-    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.pipelined, &tu.stage_budget, &tu.ffma_g};
-    const int* cands[] = {grid_c, db_c, kc_c, p_c, sb_c, g_c};
-    for (int knob = c->batch->uses_tensor_cores() ? 0 : 5; knob < 6; ++knob) {
+              p_c[] = {0, 1, 2}, sb_c[] = {64 * 1024, 96 * 1024, 192 * 1024}, g_c[] = {1, 16, 256},
+              tt_c[] = {32, 64, 256};
+    int* fields[] = {&tu.grid_pct, &tu.db_bytes, &tu.kc_max, &tu.pipelined, &tu.stage_budget, &tu.ffma_g,
+                     &tu.trunc_threads};
+    const int* cands[] = {grid_c, db_c, kc_c, p_c, sb_c, g_c, tt_c};
+    for (int knob = c->batch->uses_tensor_cores() ? 0 : 5; knob < 7; ++knob) {
       int* field = fields[knob];
       const int* cand = cands[knob];
       int best_v = *field;
@@ -1542,6 +1544,7 @@ int peps_autotune(peps_ctx* c, int reps, peps_tune* out) {
     out->kc_max = tu.kc_max;
     out->pipelined = tu.pipelined;
     out->stage_kb = tu.stage_budget / 1024;
+    out->trunc_threads = tu.trunc_threads;
     out->ms_before = before;
     out->ms_after = cur;
   }
@@ -1650,7 +1653,9 @@ int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   if (!c || !t || t->grid_pct < 1 || t->grid_pct > 400 || t->db_bytes < 0 ||
       t->db_bytes > 200 * 1024 || t->ffma_g < 1 || t->ffma_g > 256 || t->kc_max < 8 ||
       t->kc_max > 64 || t->kc_max % 8 || t->pipelined < 0 || t->pipelined > 2 ||
-      (t->stage_kb != 0 && (t->stage_kb < 32 || t->stage_kb > 200)))
+      (t->stage_kb != 0 && (t->stage_kb < 32 || t->stage_kb > 200)) ||
+      (t->trunc_threads != 0 && t->trunc_threads != 32 && t->trunc_threads != 64 &&
+       t->trunc_threads != 128 && t->trunc_threads != 256))
     return fail(c, PEPS_EINVAL, "set_tune: args");
   if (!c->batch) return fail(c, PEPS_ESTATE, "set_tune: only the batched engine has launch shapes");
   BatchTune& tu = c->batch->tuning();
@@ -1660,6 +1665,7 @@ int peps_set_tune(peps_ctx* c, const peps_tune* t) {
   tu.kc_max = t->kc_max;
   tu.pipelined = t->pipelined;
   if (t->stage_kb) tu.stage_budget = t->stage_kb * 1024;
+  if (t->trunc_threads) tu.trunc_threads = t->trunc_threads;
   c->batch->drop_graphs();   // the captured sequences used the old shapes
   return PEPS_OK;
 }

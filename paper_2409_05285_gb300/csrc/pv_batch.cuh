@@ -325,7 +325,7 @@ struct OpTrunc {
   unsigned long long* sweeps;
   double* jflops;   // when set: += flops of the Jacobi sweeps this matrix took
   PV_HD void operator()(int s, T* red, int* flag, T* smem, long long smem_cap, int* order,
-                        T* sig) const {
+                        T* sig, int gref = 0) const {
     const T* Ys = Y + (long long)s * ys;
     int ldy = len | 1, ldv = m | 1;
     T* Yw = smem;
@@ -337,7 +337,7 @@ struct OpTrunc {
         Vw[(i / m) * ldv + i % m] = (i / m == i % m) ? (T)1 : (T)0;
     PV_SYNC();
     int sw = 0;
-    jacobi(Yw, ldy, nc, len, tall ? (T*)nullptr : Vw, ldv, m, jtol, max_sweeps, flag, &sw, red);
+    jacobi(Yw, ldy, nc, len, tall ? (T*)nullptr : Vw, ldv, m, jtol, max_sweeps, flag, &sw, red, gref);
     for (int j = PV_WARP; j < nc; j += PV_NWARP) {
       T s2 = 0;
       const T* y = Yw + (long long)j * ldy;
@@ -1442,7 +1442,7 @@ __global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long c
   T* sig = gwork ? (T*)dyn : smem + cap;
   int* order = (int*)(sig + op.nc + 4);
   for (int s = blockIdx.x; s < n; s += gridDim.x) {
-    op(s, red, &flag, smem, cap, order, sig);
+    op(s, red, &flag, smem, cap, order, sig, BT);   // the pairing of a 256-thread block
     __syncthreads();
   }
 }
@@ -1549,6 +1549,8 @@ struct BatchTune {
   int pipelined = 1;           // tensor-core GEMM on the cp.async pipeline (kb_gemm_tc2): 0 none,
                                // 1 short vector contractions (K <= 64), 2 every vector one
   int stage_budget = 96 * 1024;   // ... bytes of copy stages per CTA
+  int trunc_threads = 64;      // threads of a Jacobi truncation block (32..256) when its
+                               // matrix is in shared memory (the same bits for each)
 };
 
 // Whether two operands address the same values for every chain.
@@ -1792,8 +1794,22 @@ struct CudaBE {
         return;
       }
     }
-    size_t bytes = (trunc_g ? 0 : (size_t)trunc_cap * sizeof(T)) + (size_t)(op.nc + 4) * sizeof(T) +
-                   (size_t)(op.nc + 4) * sizeof(int) + 16;
+    if (!trunc_g) {
+      // the matrix (and, for a wide bond, its accumulated right vectors) in shared memory:
+      // as many blocks per SM as that memory and the block size allow
+      const long long need = (long long)op.nc * (op.len | 1) + (op.tall ? 0 : (long long)op.m * (op.m | 1));
+      const size_t bytes = (size_t)need * sizeof(T) + (size_t)(op.nc + 4) * (sizeof(T) + sizeof(int)) + 16;
+      const int tt = tune.trunc_threads;
+      int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
+      per_sm = per_sm < 2048 / tt ? per_sm : 2048 / tt;
+      per_sm = per_sm < 32 ? per_sm : 32;
+      per_sm = per_sm < 1 ? 1 : per_sm;
+      const int grid = n < sms * per_sm ? n : sms * per_sm;
+      PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
+                 kb_trunc<T><<<grid, tt, bytes, st>>>(op, n, need, nullptr));
+      return;
+    }
+    size_t bytes = (size_t)(op.nc + 4) * sizeof(T) + (size_t)(op.nc + 4) * sizeof(int) + 16;
     PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
                kb_trunc<T><<<gblocks(n), BT, bytes, st>>>(op, n, trunc_cap, trunc_g));
   }

@@ -400,8 +400,10 @@ PV_HDN double lq_factor(T* Lout, T* W, int m, int n, T* red, T* sh) {
 // len) until they are mutually orthogonal; when V is given the same rotations are applied
 // to its nc columns (column j at V + j*ldv, length vlen).  Columns are paired in parallel
 // round-robin order; each pair is handled by a group of G lanes (G a power of two, as many
-// lanes as the block allows).  Returns the flop count; *sweeps_out receives the number of
-// sweeps.  `flag` is one shared int, `red` PV_NWARP shared entries.
+// lanes as a block of `gref` threads allows, gref = 0: this block; the groups take the pairs
+// of a round in turn, so a smaller block with the same gref computes the same bits).
+// Returns the flop count; *sweeps_out receives the number of sweeps.  `flag` is one shared
+// int, `red` PV_NWARP shared entries.
 template <typename T>
 PV_HD T group_sum(T v, int G) {
 #if defined(__CUDA_ARCH__)
@@ -414,7 +416,7 @@ PV_HD T group_sum(T v, int G) {
 
 template <typename T>
 PV_HDN double jacobi(T* Y, int ldy, int nc, int len, T* V, int ldv, int vlen, T tol,
-                     int max_sweeps, int* flag, int* sweeps_out, T* red) {
+                     int max_sweeps, int* flag, int* sweeps_out, T* red, int gref = 0) {
   int np = nc + (nc & 1);   // even number of positions; position nc is empty when nc is odd
   double flops = 0;
   int sweep = 0;
@@ -427,15 +429,27 @@ PV_HDN double jacobi(T* Y, int ldy, int nc, int len, T* V, int ldv, int vlen, T 
   // (their directions carry no weight and rounding keeps them from converging).
   const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
   const T tol_eff = tol > (T)4 * len * eps ? tol : (T)4 * len * eps;
+  // squared norm of the matrix, by the first warp in a fixed order (the same in any block)
   T nf2 = 0;
-  for (int j = 0; j < nc; ++j)
-    for (int i = PV_TID; i < len; i += PV_NTHR) nf2 += Y[(long long)j * ldy + i] * Y[(long long)j * ldy + i];
-  nf2 = cta_sum(nf2, red);
+  if (PV_WARP == 0) {
+    for (int j = 0; j < nc; ++j)
+      for (int i = PV_LANE; i < len; i += PV_WSIZE) nf2 += Y[(long long)j * ldy + i] * Y[(long long)j * ldy + i];
+    nf2 = warp_sum(nf2);
+  }
+  PV_SYNC();
+  if (PV_TID == 0) red[0] = nf2;
+  PV_SYNC();
+  nf2 = red[0];
+  PV_SYNC();
   const T tiny = (eps * len) * (eps * len) * nf2;
   const int npair = np / 2;
   int G = 1;
 #if defined(__CUDA_ARCH__)
-  while (G < 32 && G * 2 * npair <= PV_NTHR) G *= 2;
+  const int gthr = gref > 0 ? gref : PV_NTHR;
+  while (G < 32 && G * 2 * npair <= gthr) G *= 2;
+  if (G > PV_NTHR) G = PV_NTHR;
+#else
+  (void)gref;
 #endif
   const int ngroups = PV_NTHR / G;
   const int grp = PV_TID / G, gl = PV_TID % G;
