@@ -153,6 +153,21 @@ int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
 int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
               double cg_tol, peps_stats* stats);
 
+/* Evaluation of several contexts' chains in one launch: lattices of different sizes (and
+ * D, chi, couplings) share one persistent grid of the per-block engine, chain by chain as
+ * each context's own evaluation would do it (the same results, bit for bit).  Every context
+ * must use narrow per-block kernels (block_mode PEPS_BLOCKS_NARROW) and the same precision
+ * (PEPS_FP64 or PEPS_FP32), and appear once; EINVAL otherwise.  peps_group_create allocates
+ * the group's scratch (ENOMEM / ECUDA on failure); peps_group_eval waits for each context's
+ * stream, evaluates every chain of every context into that context's own results (as
+ * peps_eval_batch with S = NULL, ready for peps_sr_step / peps_observables) on the first
+ * context's stream and synchronises it.  Free the group before its contexts. */
+typedef struct peps_group peps_group;
+int peps_group_create(peps_ctx* const* ctxs, int n_ctx, peps_group** out);
+int peps_group_eval(peps_group* group);
+const char* peps_group_last_error(const peps_group* group);
+void peps_group_free(peps_group* group);
+
 /* Reweighted direct sampling (App. A, Eqs. A2-A7): replaces every chain by an independent
  * draw.  Sites are drawn one after another in row-major order; site i takes its local state
  * s from p_4c(s) = b(s) p_2c(s)^exponent normalised over the four states, p_2c (Eq. A3) the

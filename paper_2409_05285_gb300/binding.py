@@ -40,6 +40,7 @@ EXPORTS = [
     "peps_srv_metrics", "peps_srv_free", "peps_launches", "peps_profile", "peps_profile_read",
     "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline", "peps_set_graphs", "peps_graphs_captured",
     "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
+    "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
 ]
 
 
@@ -151,6 +152,12 @@ def load(path=None):
     lib.peps_graphs_captured.argtypes = [vp]
     lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
     lib.peps_direct_draw.argtypes = [vp, vp, ip, dp, dp, vp]
+    lib.peps_group_create.argtypes = [ctypes.POINTER(vp), ip, ctypes.POINTER(vp)]
+    lib.peps_group_eval.argtypes = [vp]
+    lib.peps_group_last_error.argtypes = [vp]
+    lib.peps_group_last_error.restype = ctypes.c_char_p
+    lib.peps_group_free.argtypes = [vp]
+    lib.peps_group_free.restype = None
     lib.peps_direct_next_bd.argtypes = [dp, dp, ip]
     lib.peps_direct_next_bd.restype = ctypes.c_double
     lib.peps_direct_step.argtypes = [vp, ctypes.POINTER(ctypes.c_double), dp, dp, dp, ip, dp,
@@ -419,6 +426,37 @@ class Context:
         j = ctypes.c_int64()
         self._check(self.lib.peps_last_counters(self.ctx, ctypes.byref(f), ctypes.byref(j)))
         return f.value, j.value
+
+
+class Group:
+    """Several contexts whose chains are evaluated in one launch (peps_group_*): lattices of
+    different sizes on the per-block engine's narrow blocks, one precision."""
+
+    def __init__(self, contexts):
+        self.lib = load()
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c.ctx.value for c in self.contexts])
+        self.grp = ctypes.c_void_p()
+        rc = self.lib.peps_group_create(arr, len(self.contexts), ctypes.byref(self.grp))
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_group_create failed")
+
+    def eval(self):
+        """Evaluates every context's chains (kept on the device for sr_step/observables)."""
+        rc = self.lib.peps_group_eval(self.grp)
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_group_last_error(self.grp).decode())
+
+    def close(self):
+        if self.grp:
+            self.lib.peps_group_free(self.grp)
+            self.grp = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def direct_next_bd(b_d, diag_frac, N):

@@ -160,6 +160,61 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
   flush_counters(sh, flops, jsw);
 }
 
+// One problem of a group evaluation: a context's geometry, parameters, chains and outputs.
+struct GroupItem {
+  Geom g;
+  const void* theta;   // T
+  const uint8_t* S;
+  long long first;     // index of its first chain in the group's chain order
+  int n;
+  double *log_abs, *es, *ea;
+  int8_t* sign;
+  void* O;             // T
+  long long No;
+};
+
+// Evaluation of the chains of several problems of different lattice sizes in one launch:
+// chain q of the group (problems in order, each problem's chains in order) is evaluated by
+// block q mod grid exactly as k_eval evaluates it (the same per-sample routine, block size
+// and reduction order), its scratch laid out for its own geometry.
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+    k_eval_group(const GroupItem* __restrict__ items, int n_items, long long total, T* scratch,
+                 int* iscratch, long long sreal, long long sint, T jtol, int max_sweeps,
+                 double* flops, unsigned long long* jsw, int smem_bytes) {
+  __shared__ Shared<T> sh;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  init_shared(sh);
+  for (long long q = blockIdx.x; q < total; q += gridDim.x) {
+    int k = 0;
+    while (k + 1 < n_items && items[k + 1].first <= q) ++k;
+    const GroupItem& it = items[k];
+    const Geom g = it.g;
+    const long long s = q - it.first;
+    Scratch<T> sc;
+    sc.bind(scratch + (long long)blockIdx.x * sreal, iscratch + (long long)blockIdx.x * sint,
+            g.L1, g.L2, g.D, g.chi);
+    sc.alias_global();
+    sc.smem = smem_bytes > 0 ? (T*)dyn_smem : nullptr;
+    sc.smem_cap = smem_bytes / (int)sizeof(T);
+    const int N = g.N();
+    for (int j = threadIdx.x; j < N; j += blockDim.x) sh.S[j] = it.S[s * N + j];
+    __syncthreads();
+    UCache<T> uc{nullptr, nullptr};
+    T* O = (T*)it.O;
+    SampleOut r = eval_sample<T, T, T>(g, sc, sh, (const T*)it.theta, O ? O + s * it.No : nullptr,
+                                       jtol, max_sweeps, uc);
+    if (threadIdx.x == 0) {
+      it.log_abs[s] = r.log_abs;
+      it.sign[s] = (int8_t)r.sign;
+      it.es[s] = r.e_sys;
+      it.ea[s] = r.e_anc;
+    }
+    __syncthreads();
+  }
+  flush_counters(sh, flops, jsw);
+}
+
 template <typename T, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_mc(Geom g, const T* __restrict__ theta, uint8_t* __restrict__ S, int n, T* scratch,
@@ -1820,6 +1875,142 @@ int peps_step(peps_ctx* c, int n_sweeps, int p, double tau, double eps, int max_
   PV_TRY(peps_eval_batch(c, nullptr, c->P.n_chains, 1, nullptr, nullptr, nullptr, nullptr,
                          nullptr));
   return peps_sr_step(c, tau, eps, max_cg, cg_tol, p, st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ group evaluation
+
+struct peps_group {
+  std::vector<peps_ctx*> ctxs;
+  bool f64 = true;
+  long long total = 0, sreal = 0, sint = 0;
+  int nblk = 0, smem = 0;
+  GroupItem* d_items = nullptr;
+  void* d_scr = nullptr;
+  int* d_iscr = nullptr;
+  double* d_flops = nullptr;
+  unsigned long long* d_jsw = nullptr;
+  std::string err;
+  ~peps_group() {
+    if (d_items) cudaFree(d_items);
+    if (d_scr) cudaFree(d_scr);
+    if (d_iscr) cudaFree(d_iscr);
+    if (d_flops) cudaFree(d_flops);
+    if (d_jsw) cudaFree(d_jsw);
+  }
+};
+
+namespace {
+
+int gfail(peps_group* g, int code, const std::string& msg) {
+  g->err = msg;
+  return code;
+}
+
+template <typename P>
+cudaError_t galloc(P** p, size_t bytes) {
+  return cudaMalloc((void**)p, bytes ? bytes : 16);
+}
+
+}  // namespace
+
+extern "C" {
+
+int peps_group_create(peps_ctx* const* ctxs, int n, peps_group** out) {
+  if (!out) return PEPS_EINVAL;
+  *out = nullptr;
+  if (!ctxs || n < 1) return PEPS_EINVAL;
+  std::unique_ptr<peps_group> g(new peps_group());
+  for (int i = 0; i < n; ++i) {
+    peps_ctx* c = ctxs[i];
+    if (!c) return PEPS_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return PEPS_EINVAL;   // each context once
+    // the per-block engine's narrow blocks, one arithmetic for the whole group
+    if (c->batch || c->wide) return PEPS_EINVAL;
+    if (i > 0 && fp64(c) != fp64(ctxs[0])) return PEPS_EINVAL;
+    g->ctxs.push_back(c);
+  }
+  peps_group* G = g.get();
+  G->f64 = fp64(ctxs[0]);
+  const size_t real = G->f64 ? sizeof(double) : sizeof(float);
+  std::vector<GroupItem> items;
+  for (peps_ctx* c : G->ctxs) {
+    GroupItem it;
+    it.g = make_geom(c);
+    it.theta = G->f64 ? (const void*)c->d_theta : (const void*)c->d_theta_f;
+    it.S = c->d_S;
+    it.first = G->total;
+    it.n = c->P.n_chains;
+    it.log_abs = c->d_log_abs;
+    it.es = c->d_es;
+    it.ea = c->d_ea;
+    it.sign = c->d_sign;
+    it.O = c->d_O;
+    it.No = c->No;
+    items.push_back(it);
+    G->total += it.n;
+    G->sreal = std::max(G->sreal, c->sreal);
+    G->sint = std::max(G->sint, c->sint);
+    G->smem = std::max(G->smem, c->smem_bytes);
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  G->nblk = (int)std::min<long long>(G->total, 4LL * sms);
+  cudaError_t e = galloc(&G->d_items, items.size() * sizeof(GroupItem));
+  if (e == cudaSuccess) e = galloc(&G->d_scr, (size_t)G->nblk * G->sreal * real);
+  if (e == cudaSuccess) e = galloc(&G->d_iscr, (size_t)G->nblk * G->sint * sizeof(int));
+  if (e == cudaSuccess) e = galloc(&G->d_flops, sizeof(double));
+  if (e == cudaSuccess) e = galloc(&G->d_jsw, sizeof(unsigned long long));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(G->d_items, items.data(), items.size() * sizeof(GroupItem), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && G->smem > 48 * 1024)
+    e = G->f64 ? cudaFuncSetAttribute(k_eval_group<double, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024)
+               : cudaFuncSetAttribute(k_eval_group<float, SAMPLE_THREADS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? PEPS_ENOMEM : PEPS_ECUDA;
+  }
+  *out = g.release();
+  return PEPS_OK;
+}
+
+int peps_group_eval(peps_group* G) {
+  if (!G) return PEPS_EINVAL;
+  // every context's earlier work (sweeps, parameter updates) has finished
+  for (peps_ctx* c : G->ctxs) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return gfail(G, PEPS_ECUDA, std::string("group_eval: ") + cudaGetErrorString(e));
+  }
+  peps_ctx* c0 = G->ctxs[0];
+  cudaStream_t st = c0->stream;
+  cudaMemsetAsync(G->d_flops, 0, sizeof(double), st);
+  cudaMemsetAsync(G->d_jsw, 0, sizeof(unsigned long long), st);
+  if (G->f64)
+    PV_KLAUNCH(&c0->kprof, st, "k_eval_group", 0.0, 0.0,
+               (k_eval_group<double, SAMPLE_THREADS><<<G->nblk, SAMPLE_THREADS, G->smem, st>>>(
+                   G->d_items, (int)G->ctxs.size(), G->total, (double*)G->d_scr, G->d_iscr, G->sreal,
+                   G->sint, (double)JTOL_F64, JAC_MAX_SWEEPS, G->d_flops, G->d_jsw, G->smem)));
+  else
+    PV_KLAUNCH(&c0->kprof, st, "k_eval_group", 0.0, 0.0,
+               (k_eval_group<float, SAMPLE_THREADS><<<G->nblk, SAMPLE_THREADS, G->smem, st>>>(
+                   G->d_items, (int)G->ctxs.size(), G->total, (float*)G->d_scr, G->d_iscr, G->sreal,
+                   G->sint, (float)JTOL_F32, JAC_MAX_SWEEPS, G->d_flops, G->d_jsw, G->smem)));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return gfail(G, PEPS_ECUDA, std::string("group_eval: ") + cudaGetErrorString(e));
+  for (peps_ctx* c : G->ctxs) c->have_eval = true;
+  return PEPS_OK;
+}
+
+const char* peps_group_last_error(const peps_group* G) { return G ? G->err.c_str() : ""; }
+
+void peps_group_free(peps_group* G) {
+  if (!G) return;
+  if (!G->ctxs.empty()) cudaStreamSynchronize(G->ctxs[0]->stream);
+  delete G;
 }
 
 }  // extern "C"

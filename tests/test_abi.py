@@ -98,6 +98,17 @@ def test_direct_calls_reject_a_null_context_and_next_bd_follows_the_oracle():
                 direct.update_bd(b_d, S, N), rel=1e-15)
 
 
+def test_group_calls_reject_bad_arguments_without_gpu_work():
+    lib = binding.load()
+    out = ctypes.c_void_p()
+    assert lib.peps_group_create(None, 0, ctypes.byref(out)) == binding.PEPS_EINVAL
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.peps_group_create(arr, 1, ctypes.byref(out)) == binding.PEPS_EINVAL
+    assert not out.value
+    assert lib.peps_group_eval(None) == binding.PEPS_EINVAL
+    lib.peps_group_free(None)
+
+
 def test_header_is_plain_c():
     # the boundary is a C ABI: the header compiles as C99 (no C++ or torch types)
     import shutil
