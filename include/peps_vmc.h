@@ -200,6 +200,14 @@ double peps_direct_next_bd(double b_d, double diag_frac, int N);
 int peps_direct_step(peps_ctx* ctx, double* b_d, double exponent, double tau, double eps,
                      int max_cg, double cg_tol, peps_stats* stats);
 
+/* Truncation arithmetic of the float32 modes (PEPS_FP32, PEPS_TF32; batched engine):
+ * enable = 1 runs each bond's Jacobi SVD on a float64 working copy of its float32 matrix
+ * (rotations, singular values and kept vectors in float64, the truncated environment stored
+ * in float32); 0 (the default) runs it in float32.  The right factors that feed the SVD stay
+ * float32.  ESTATE for PEPS_FP64 or the per-block engine, EINVAL for other values, ENOMEM
+ * when the float64 work area of large bonds cannot be allocated. */
+int peps_set_trunc_fp64(peps_ctx* ctx, int enable);
+
 /* CUDA graphs for the batched engine (enable = 1; 0 = direct launches, the default): the
  * launch sequence of a Metropolis sweep (per exponent p) and of an evaluation of the chains
  * (per use of the sweep's cached environments) is captured into a graph on first use and

@@ -41,6 +41,7 @@ EXPORTS = [
     "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline", "peps_set_graphs", "peps_graphs_captured",
     "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
+    "peps_set_trunc_fp64",
 ]
 
 
@@ -148,6 +149,7 @@ def load(path=None):
     lib.peps_set_tune.argtypes = [vp, ctypes.POINTER(Tune)]
     lib.peps_su_warm_start.argtypes = [vp, dp, ip]
     lib.peps_set_cg_product.argtypes = [vp, ip]
+    lib.peps_set_trunc_fp64.argtypes = [vp, ip]
     lib.peps_set_graphs.argtypes = [vp, ip]
     lib.peps_graphs_captured.argtypes = [vp]
     lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
@@ -411,6 +413,10 @@ class Context:
 
     def graphs_captured(self):
         return int(self.lib.peps_graphs_captured(self.ctx))
+
+    def set_trunc_fp64(self, on):
+        """Float32 modes: Jacobi truncation on a float64 working copy (peps_set_trunc_fp64)."""
+        self._check(self.lib.peps_set_trunc_fp64(self.ctx, 1 if on else 0))
 
     def set_cg_product(self, mode):
         """CG product form (peps_set_cg_product): 0 automatic, 1 fused single read, 2 two passes."""

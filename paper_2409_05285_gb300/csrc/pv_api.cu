@@ -291,6 +291,10 @@ struct BatchIface {
   virtual bool graphs_on() const = 0;
   virtual int graphs_captured() const = 0;
   virtual void drop_graphs() = 0;         // launch shapes changed: recapture on next use
+  // float engines: truncate with a float64 working copy (g64: its global work area, or null)
+  virtual bool set_trunc64(bool on, double* g64) = 0;
+  virtual long long trunc_cap() const = 0;
+  virtual bool trunc_global() const = 0;
   virtual void eval(const uint8_t* S, int nb, double* la, int8_t* sg, double* es, double* ea,
                     void* O, bool cached) = 0;
   virtual void mc(uint8_t* S, int n, int p, uint64_t seed, long long sweep0, int n_sweeps,
@@ -331,6 +335,19 @@ struct BatchImpl : BatchIface {
   }
   bool graphs_on() const override { return graphs; }
   int graphs_captured() const override { return (int)gcache.size(); }
+  bool set_trunc64(bool on, double* g64) override {
+    if constexpr (std::is_same<T, float>::value) {
+      be.trunc64 = on;
+      if (g64) be.trunc_g64 = g64;
+      drop_graphs();
+      return true;
+    }
+    (void)on;
+    (void)g64;
+    return false;
+  }
+  long long trunc_cap() const override { return be.trunc_cap; }
+  bool trunc_global() const override { return be.trunc_g != nullptr; }
   void drop_graphs() override {
     for (auto& kv : gcache)
       if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -540,6 +557,7 @@ struct peps_ctx {
   uint32_t n_draws = 0;
   pv::KProf kprof;                      // launch counter, optional per-kernel timing
   double* d_jflops = nullptr;           // Jacobi flops of the truncations while profiling
+  double* d_trunc_g64 = nullptr;        // float64 Jacobi work area (peps_set_trunc_fp64)
   bool o_vec4 = false;                  // every site slice of O holds a multiple of 4 entries
 };
 
@@ -763,6 +781,8 @@ int init_runner_t(peps_ctx* c, int sms, BatchImpl<T>* b, int Dn, const T* theta,
       e = cudaFuncSetAttribute(kb_gemm_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kb_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kb_trunc64<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return fail(c, PEPS_ECUDA, std::string("tensor-core setup: ") + cudaGetErrorString(e));
     b->be.tc = true;
     b->be.tc_split = P->precision == PEPS_FP32;
@@ -1631,6 +1651,23 @@ int peps_set_graphs(peps_ctx* c, int enable) {
 
 int peps_graphs_captured(const peps_ctx* c) {
   return (c && c->batch) ? c->batch->graphs_captured() : 0;
+}
+
+int peps_set_trunc_fp64(peps_ctx* c, int enable) {
+  if (!c || enable < 0 || enable > 1) return fail(c, PEPS_EINVAL, "set_trunc_fp64: args");
+  if (!c->batch || fp64(c))
+    return fail(c, PEPS_ESTATE, "set_trunc_fp64: only the batched engine's float32 modes truncate in float32");
+  double* g64 = nullptr;
+  const long long cap = c->batch->trunc_cap();
+  if (enable && (size_t)cap * 8 + 16 > 200 * 1024 && !c->d_trunc_g64) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    PV_TRY(dalloc(c, &c->d_trunc_g64, (size_t)8 * sms * cap * sizeof(double)));
+  }
+  g64 = c->d_trunc_g64;
+  c->batch->set_trunc64(enable == 1, g64);
+  return PEPS_OK;
 }
 
 int peps_set_cg_product(peps_ctx* c, int mode) {

@@ -326,21 +326,29 @@ struct OpTrunc {
   double* jflops;   // when set: += flops of the Jacobi sweeps this matrix took
   PV_HD void operator()(int s, T* red, int* flag, T* smem, long long smem_cap, int* order,
                         T* sig, int gref = 0) const {
+    run<T>(s, red, flag, smem, order, sig, gref, jtol);
+    (void)smem_cap;
+  }
+  // The truncation with working type W (T, or double for float data: the rotations, the
+  // singular values and the vectors in float64, the results stored as T).  smem holds the
+  // working matrices, red 32 entries of W, sig nc + 4 of W.
+  template <typename W>
+  PV_HD void run(int s, W* red, int* flag, W* smem, int* order, W* sig, int gref, W tol) const {
     const T* Ys = Y + (long long)s * ys;
     int ldy = len | 1, ldv = m | 1;
-    T* Yw = smem;
-    T* Vw = smem + (long long)nc * ldy;
+    W* Yw = smem;
+    W* Vw = smem + (long long)nc * ldy;
     for (long long i = PV_TID; i < (long long)nc * len; i += PV_NTHR)
-      Yw[(i / len) * ldy + i % len] = Ys[i];
+      Yw[(i / len) * ldy + i % len] = (W)Ys[i];
     if (!tall)
       for (long long i = PV_TID; i < (long long)m * m; i += PV_NTHR)
-        Vw[(i / m) * ldv + i % m] = (i / m == i % m) ? (T)1 : (T)0;
+        Vw[(i / m) * ldv + i % m] = (i / m == i % m) ? (W)1 : (W)0;
     PV_SYNC();
     int sw = 0;
-    jacobi(Yw, ldy, nc, len, tall ? (T*)nullptr : Vw, ldv, m, jtol, max_sweeps, flag, &sw, red, gref);
+    jacobi(Yw, ldy, nc, len, tall ? (W*)nullptr : Vw, ldv, m, tol, max_sweeps, flag, &sw, red, gref);
     for (int j = PV_WARP; j < nc; j += PV_NWARP) {
-      T s2 = 0;
-      const T* y = Yw + (long long)j * ldy;
+      W s2 = 0;
+      const W* y = Yw + (long long)j * ldy;
       for (int i = PV_LANE; i < len; i += PV_WSIZE) s2 += y[i] * y[i];
       s2 = warp_sum(s2);
       if (PV_LANE == 0) sig[j] = sqrt(s2);
@@ -348,38 +356,38 @@ struct OpTrunc {
     PV_SYNC();
     for (int j = PV_TID; j < nc; j += PV_NTHR) {
       int rank = 0;
-      T sj = sig[j];
+      W sj = sig[j];
       for (int i = 0; i < nc; ++i) {
-        T si = sig[i];
+        W si = sig[i];
         rank += (si > sj || (si == sj && i < j)) ? 1 : 0;
       }
       order[rank] = j;
     }
     PV_SYNC();
-    T zero2 = 0;
+    W zero2 = 0;
     if (tall) {
-      T nf2 = 0;
+      W nf2 = 0;
       for (int j = 0; j < nc; ++j) nf2 += sig[j] * sig[j];
-      const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+      const W eps = sizeof(W) == 4 ? (W)1.1920929e-7 : (W)2.220446049250313e-16;
       zero2 = (eps * len) * (eps * len) * nf2;
     }
     T* U = Uk + (long long)s * uks;
     for (long long idx = PV_TID; idx < (long long)m * kk; idx += PV_NTHR) {
       int q = (int)(idx / kk), jp = (int)(idx % kk);
       int j = order[jp];
-      T v;
+      W v;
       if (tall) {
-        T sg = sig[j];
-        v = sg * sg > zero2 ? Yw[(long long)j * ldy + q] / sg : (T)0;
+        W sg = sig[j];
+        v = sg * sg > zero2 ? Yw[(long long)j * ldy + q] / sg : (W)0;
       } else {
         v = Vw[(long long)j * ldv + q];
       }
-      U[idx] = v;
+      U[idx] = (T)v;
     }
     PV_SYNC();
     T* o = out + (long long)s * outs;
     copy(o, U, (long long)m * kk);
-    double l = normalize_maxabs(o, (long long)m * kk, red);
+    double l = normalize_maxabs(o, (long long)m * kk, (T*)red);
     if (PV_TID == 0) {
       lsv[(long long)s * lstride] += l;
       // a sweep visits nc (nc - 1) / 2 column pairs: three dot products and a rotation of two
@@ -394,7 +402,6 @@ struct OpTrunc {
 #endif
     }
     PV_SYNC();
-    (void)smem_cap;
   }
 };
 
@@ -1447,6 +1454,24 @@ __global__ void __launch_bounds__(BT) kb_trunc(OpTrunc<T> op, int n, long long c
   }
 }
 
+// The truncation of float data with a float64 working copy (rotations, singular values and
+// vectors in float64): the matrices in shared memory, or, with gwork, in this block's slice
+// of a global float64 work area.
+template <typename T>
+__global__ void __launch_bounds__(BT) kb_trunc64(OpTrunc<T> op, int n, long long cap, double* gwork,
+                                                 double tol) {
+  __shared__ double red[32];
+  __shared__ int flag;
+  extern __shared__ __align__(16) unsigned char dyn[];
+  double* smem = gwork ? gwork + (long long)blockIdx.x * cap : (double*)dyn;
+  double* sig = gwork ? (double*)dyn : smem + cap;
+  int* order = (int*)(sig + op.nc + 4);
+  for (int s = blockIdx.x; s < n; s += gridDim.x) {
+    op.template run<double>(s, red, &flag, smem, order, sig, BT, tol);
+    __syncthreads();
+  }
+}
+
 // Truncation of a tall bond (no rotations to accumulate) with its Jacobi matrix in shared
 // memory, one 1024-thread block per SM: the column pairs of a round are spread over all
 // threads and every round runs at shared-memory latency.
@@ -1577,6 +1602,9 @@ struct CudaBE {
   const double* bJ;
   int nb, N;
   long long trunc_cap;   // elements of the Jacobi work area of one block
+  bool trunc64 = false;          // float data truncated with a float64 working copy
+  double* trunc_g64 = nullptr;   // its global work area (8 blocks per SM x trunc_cap)
+  double jtol64 = 1e-15;         // its Jacobi tolerance
   T* trunc_g = nullptr;  // global Jacobi work area (gblocks(n) blocks) when shared memory is too small
   int sms;
   int lq_smem_max = 0;   // bytes of shared memory the Householder kernel may take
@@ -1782,6 +1810,25 @@ struct CudaBE {
                kb_lq<T><<<gblocks(n), BT, use ? bytes : 0, st>>>(op, n, use));
   }
   void trunc(OpTrunc<T> op, int n) {
+    if (trunc64) {
+      const long long need = (long long)op.nc * (op.len | 1) + (op.tall ? 0 : (long long)op.m * (op.m | 1));
+      const size_t bytes = (size_t)need * 8 + (size_t)(op.nc + 4) * (8 + sizeof(int)) + 16;
+      if (bytes <= 200 * 1024 || !trunc_g64) {
+        const int tt = tune.trunc_threads;
+        int per_sm = (int)((size_t)(227 * 1024) / (bytes + 1024));
+        per_sm = per_sm < 2048 / tt ? per_sm : 2048 / tt;
+        per_sm = per_sm < 32 ? per_sm : 32;
+        per_sm = per_sm < 1 ? 1 : per_sm;
+        const int grid = n < sms * per_sm ? n : sms * per_sm;
+        PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
+                   kb_trunc64<T><<<grid, tt, bytes, st>>>(op, n, need, nullptr, jtol64));
+      } else {
+        const size_t b = (size_t)(op.nc + 4) * (8 + sizeof(int)) + 16;
+        PV_KLAUNCH(prof, st, "kb_trunc", (double)n * 2.0 * op.nc * op.len * sizeof(T), 0.0,
+                   kb_trunc64<T><<<gblocks(n), BT, b, st>>>(op, n, trunc_cap, trunc_g64, jtol64));
+      }
+      return;
+    }
     if (op.tall && trunc_g) {
       // matrices too large for the shared-memory work area of the 256-thread kernel (which
       // would keep them in global memory): one 1024-thread block per SM holds one in shared
