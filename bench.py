@@ -58,24 +58,24 @@ NCU_TRAFFIC = {
     ("heis8", "tf32", "kb_gemm_tc"): {
         "chains": 2048,
         "launches": 100,
-        "dram_bytes": 6965e6,           # DRAM read + write of the first 100 launches of the step
-        "alg_bytes": 9975e6,            # algorithmic bytes of the same 100 launches
-        "sources_sha256": "0a7834951acc17bd53fb798cd3adefde3078011f7453a66229223be56b5ce7b5",
+        "dram_bytes": 6969.22e6,        # DRAM read + write of the first 100 launches of the step
+        "alg_bytes": 9975.38e6,         # algorithmic bytes of the same 100 launches
+        "sources_sha256": "e7997e742bd0251c6223b3b09e0e0ea0a5c7b20f11f5fde0f50bb44526b564b0",
         "source": "ncu --profile-from-start off --clock-control none --metrics "
                   "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
                   "-k regex:kb_gemm_tc -c 100 (cold cache): the first 100 launches of the timed "
                   "step at 2048 chains (shapes 100,12288,16,16,0), scaled by algorithmic bytes",
     },
     ("j1j2_10", "tf32", "kb_gemm_tc"): {
-        "chains": 2048,
+        "chains": 512,
         "launches": 100,
-        "dram_bytes": 156892e6,
-        "alg_bytes": 156946e6,
-        "sources_sha256": "0a7834951acc17bd53fb798cd3adefde3078011f7453a66229223be56b5ce7b5",
+        "dram_bytes": 38160.7e6,
+        "alg_bytes": 41258.7e6,
+        "sources_sha256": "e7997e742bd0251c6223b3b09e0e0ea0a5c7b20f11f5fde0f50bb44526b564b0",
         "source": "ncu --profile-from-start off --clock-control none --metrics "
                   "dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum "
-                  "-k regex:kb_gemm_tc -c 100 (cold cache): the first 100 launches of the timed "
-                  "step at 2048 chains (default shapes), scaled by algorithmic bytes",
+                  "-k regex:^kb_gemm_tc$ -c 100 (cold cache): the first 100 launches of the timed "
+                  "step at 512 chains (default shapes, no autotune), scaled by algorithmic bytes",
     },
 }
 TRAFFIC_SOURCES = ("paper_2409_05285_gb300/csrc/pv_tc.cuh", "paper_2409_05285_gb300/csrc/pv_tc2.cuh",
