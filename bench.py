@@ -1009,7 +1009,7 @@ def main():
                     help="start from the simple-update state at this imaginary time (J1 workloads)")
     ap.add_argument("--tune", default="",
                     help="pin the launch shapes instead of autotuning: grid_pct,db_bytes,ffma_g,kc_max[,pipelined]")
-    ap.add_argument("--cg-product", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--cg-product", type=int, default=0, choices=[0, 1, 2, 3],
                     help="CG product form: 0 automatic, 1 fused single read, 2 two passes")
     ap.add_argument("--graphs", type=int, default=1, choices=[0, 1],
                     help="replay the batched engine's launch sequences as CUDA graphs")

@@ -226,10 +226,14 @@ int peps_graphs_captured(const peps_ctx* ctx);
 /* How peps_sr_step applies (G + eps) in CG (Eq. 10): 1 = one cooperative kernel that reads
  * the O rows once per product (each block owns a slice of the columns; samples are taken in
  * chunks that stay in L2, one grid barrier per chunk); 2 = two streaming passes (O_i.p, then
- * the column sums of y_i O_i); 0 (default) = the two passes, measured faster on GB300 at
- * 8x8 and 10x10 (float64 FMA issue bounds both forms, and the fused one adds a grid barrier
- * per chunk).  Every choice uses float64 products and fixed summation orders; the results
- * agree to rounding.  EINVAL for other modes. */
+ * the column sums of y_i O_i) over the O rows as stored; 3 = the two passes over a float64
+ * copy of float32 O rows made once per step (no float64 issue spent on widening in the
+ * passes; n_chains x N_o doubles, ENOMEM from peps_sr_step when they cannot be allocated);
+ * 0 (default) = 3 where the rows are float32 in 16-byte site slices and the copy fits, else
+ * 2 (the fused form was measured slower on GB300 at 8x8 and 10x10: float64 FMA issue bounds
+ * both forms, and it adds a grid barrier per chunk).  Every choice uses float64 products
+ * and fixed summation orders; 2 and 3 give the same bits, the others agree to rounding.
+ * EINVAL for other modes. */
 int peps_set_cg_product(peps_ctx* ctx, int mode);
 
 /* Parameter vector and chain configurations (host buffers).  n must equal N_p, or

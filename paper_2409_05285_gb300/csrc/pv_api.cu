@@ -537,7 +537,10 @@ struct peps_ctx {
   unsigned* d_gvbar = nullptr;  // grid-barrier counter and generation of the fused product
   int* d_gverr = nullptr;       // raised when a grid-barrier wait ran out
   int gv_grid = 0, gv_rpb = 1;   // fused product: resident blocks, rows per block per chunk
-  int cg_mode = 0;               // CG product: 0 automatic, 1 fused single read, 2 two passes
+  int cg_mode = 0;               // CG product: 0 automatic, 1 fused single read, 2 two passes,
+                                 // 3 two passes over a float64 copy of float32 O rows
+  double* d_O64 = nullptr;       // that copy (allocated on first use)
+  bool o64_failed = false;       // ... or its allocation failed once
   SRScalars* d_sc = nullptr;
   int nch = 0, nvb = 0, nyb = 0;
   double t = 0;
@@ -1027,6 +1030,8 @@ int peps_init(const peps_params* Pin, void* stream, peps_ctx** out) {
       e1 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_gv<double, false>, GV_THREADS, gsm);
     if (e1 != cudaSuccess || occ < 1) return bail(fail(c, PEPS_ECUDA, "fused CG product: no resident block"));
     if (cudaFuncSetAttribute(k_colsum1_f32v<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(32 * SR_THREADS * sizeof(double))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_colsum1_f32v<true, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(32 * SR_THREADS * sizeof(double))) != cudaSuccess)
       return bail(fail(c, PEPS_ECUDA, "column-sum kernel: shared-memory attribute"));
     c->gv_grid = sms;
@@ -1411,10 +1416,35 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   const long long Np = c->Np, No = c->No;
   cudaStream_t s = c->stream;
   PV_TRY(launch_weights(c, p));
+  // float32 rows with 16-byte site slices: the passes read a float64 copy of the rows made
+  // once per step (automatic and mode 3), so that no pass spends float64 issue on widening
+  bool o64 = !fp64(c) && c->o_vec4 && (c->cg_mode == 0 || c->cg_mode == 3);
+  if (o64 && !c->d_O64 && !c->o64_failed) {
+    if (cudaMalloc((void**)&c->d_O64, (size_t)n * No * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      c->d_O64 = nullptr;
+      c->o64_failed = true;
+    } else {
+      c->allocs.push_back(c->d_O64);
+    }
+  }
+  if (o64 && !c->d_O64) {
+    if (c->cg_mode == 3) return fail(c, PEPS_ENOMEM, "sr_step: no room for the float64 copy of O");
+    o64 = false;
+  }
+  if (o64) {
+    const long long n4 = (long long)n * No / 4;
+    PV_KLAUNCH(&c->kprof, s, "k_widen_o", (double)n * No * 12.0, 0.0,
+               k_widen_o<<<grid_for(n4, 256), 256, 0, s>>>(n4, (const float*)c->d_O, c->d_O64));
+  }
   // mean and gradient (one pass over O)
   dim3 cgrid((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);
   dim3 cgrid4((unsigned)((No / 4 + SR_THREADS - 1) / SR_THREADS), (unsigned)c->nch);   // 4 columns a thread
-  if (fp64(c))
+  if (o64)
+    PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1_f32v<true, double><<<cgrid4, SR_THREADS, 32 * SR_THREADS * sizeof(double), s>>>(
+        n, c->N, No, c->d_O64, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
+        c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
+  else if (fp64(c))
     PV_KLAUNCH(&c->kprof, s, "k_colsum1", ((double)n * No * 8.0 + (double)c->nch * Np * 8.0), 0.0, k_colsum1<double, true><<<cgrid, SR_THREADS, 0, s>>>(
         n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_w,
         c->d_E, &c->d_sc->Ebar, c->d_part, c->d_part2, Np, nullptr));
@@ -1441,7 +1471,7 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   // samples
   const long long gv_rows = (long long)c->gv_grid * c->gv_rpb;
   // automatic: the two passes (measured faster at 8x8 and 10x10: float64 issue bounds both
-  // forms, and the fused one adds a grid barrier per chunk)
+  // forms, and the fused one adds a grid barrier per chunk), over the float64 copy when made
   const bool fused = c->cg_mode == 1;
   (void)gv_rows;
   const int ov_blocks = c->nyb;
@@ -1450,8 +1480,11 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
   for (int it = 0; it < max_cg; ++it) {
     if (!fused) {
       // y_i = w_i (O_i.p - obar.p), then the column sums part = sum_i y_i O_i, then q
-      const double ob = (double)n * No * (fp64(c) ? 8.0 : 4.0);
-      if (fp64(c))
+      const double ob = (double)n * No * (fp64(c) || o64 ? 8.0 : 4.0);
+      if (o64)
+        PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov_f32v<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, c->d_O64, c->d_S,
+            c->d_o2site, c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
+      else if (fp64(c))
         PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov<double><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const double*)c->d_O, c->d_S,
             c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
       else if (c->o_vec4)
@@ -1460,7 +1493,11 @@ int peps_sr_step(peps_ctx* c, double tau, double eps, int max_cg, double cg_tol,
       else
         PV_KLAUNCH(&c->kprof, s, "k_ov", ob + (double)Np * 8.0, 2.0 * n * No, k_ov<float><<<ov_blocks, SR_THREADS, 0, s>>>(n, c->N, No, (const float*)c->d_O, c->d_S,
             c->d_toff, c->d_ooff, c->d_p, c->d_w, c->d_y, c->d_ypart, nvb, c->d_bp2, c->d_sc));
-      if (fp64(c))
+      if (o64)
+        PV_KLAUNCH(&c->kprof, s, "k_colsum1_f32", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1_f32v<false, double><<<cgrid4_y, SR_THREADS, 16 * SR_THREADS * sizeof(double), s>>>(
+            n, c->N, No, c->d_O64, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
+            nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
+      else if (fp64(c))
         PV_KLAUNCH(&c->kprof, s, "k_colsum1", ob + (double)c->nch * Np * 8.0, 2.0 * n * No, k_colsum1<double, false><<<cgrid_y, SR_THREADS, 0, s>>>(
             n, c->N, No, (const double*)c->d_O, c->d_S, c->d_o2site, c->d_toff, c->d_ooff, c->d_y,
             nullptr, nullptr, c->d_part, nullptr, Np, &c->d_sc->done));
@@ -1671,7 +1708,7 @@ int peps_set_trunc_fp64(peps_ctx* c, int enable) {
 }
 
 int peps_set_cg_product(peps_ctx* c, int mode) {
-  if (!c || mode < 0 || mode > 2) return fail(c, PEPS_EINVAL, "set_cg_product: mode");
+  if (!c || mode < 0 || mode > 3) return fail(c, PEPS_EINVAL, "set_cg_product: mode");
   c->cg_mode = mode;
   return PEPS_OK;
 }

@@ -199,14 +199,39 @@ __global__ void k_colsum1_f32(int n, int N, long long No, const float* __restric
   }
 }
 
+// Four consecutive O entries as float64: a 16-byte float32 load widened (exactly), or the
+// float64 copy of the rows (two 16-byte loads, no conversion in the pass).
+struct OV4 {
+  double x, y, z, w;
+};
+__device__ __forceinline__ OV4 ov_ld4(const float* p) {
+  const float4 f = __ldg((const float4*)p);
+  return OV4{(double)f.x, (double)f.y, (double)f.z, (double)f.w};
+}
+__device__ __forceinline__ OV4 ov_ld4(const double* p) {
+  const double2 a = __ldg((const double2*)p), b = __ldg((const double2*)p + 1);
+  return OV4{a.x, a.y, b.x, b.y};
+}
+
+// float32 rows widened into a float64 copy (one pass per SR step; the CG passes then read
+// the copy and spend no float64 issue on conversions)
+__global__ void k_widen_o(long long n4, const float* __restrict__ O, double* __restrict__ O64) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n4;
+       e += (long long)gridDim.x * blockDim.x) {
+    const float4 f = __ldg((const float4*)O + e);
+    ((double2*)O64)[2 * e] = make_double2(f.x, f.y);
+    ((double2*)O64)[2 * e + 1] = make_double2(f.z, f.w);
+  }
+}
+
 // Float rows, 16-byte vectors: every site slice holds a multiple of four entries, so each
 // thread takes four consecutive columns of one site; four rows are loaded before they are
 // accumulated.  Products and sums in float64, one FMA per entry: the per-state sums live in
 // shared memory, [sum][state][column][thread], and each row adds into the four sums of its
 // state (float64 issue, about 1/60 of float32 on GB300, bounds this pass).
-template <bool TWO>
+template <bool TWO, typename OT = float>
 __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
-    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
+    int n, int N, long long No, const OT* __restrict__ O, const uint8_t* __restrict__ S,
     const int* __restrict__ o2site, const long long* __restrict__ toff,
     const long long* __restrict__ ooff, const double* __restrict__ c1,
     const double* __restrict__ c2, const double* __restrict__ shift, double* __restrict__ part1,
@@ -231,11 +256,11 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
   double* B = cs_acc + 16 * SR_THREADS + tid;
   int i = i0;
   for (; i + 4 <= i1; i += 4) {
-    float4 v[4];
+    OV4 v[4];
     int st[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      v[u] = __ldg((const float4*)(O + (long long)(i + u) * No + o));
+      v[u] = ov_ld4(O + (long long)(i + u) * No + o);
       st[u] = S[(long long)(i + u) * N + j];
     }
 #pragma unroll
@@ -257,7 +282,7 @@ __global__ void __launch_bounds__(SR_THREADS) k_colsum1_f32v(
     }
   }
   for (; i < i1; ++i) {
-    const float4 v = __ldg((const float4*)(O + (long long)i * No + o));
+    const OV4 v = ov_ld4(O + (long long)i * No + o);
     const int s0 = S[(long long)i * N + j];
     double* a = A + s0 * 4 * SR_THREADS;
     const double x = cx[i - i0];
@@ -390,8 +415,9 @@ __global__ void k_ov(int n, int N, long long No, const OT* __restrict__ O,
 // Float rows, 16-byte vectors (site slices of multiples of four entries): y_i = w_i (O_i.p - obar.p),
 // every entry widened to float64.  One warp per sample; the lanes walk the row's 16-byte column
 // groups directly (site and state looked up per group), four groups in flight per lane.
+template <typename OT = float>
 __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
-    int n, int N, long long No, const float* __restrict__ O, const uint8_t* __restrict__ S,
+    int n, int N, long long No, const OT* __restrict__ O, const uint8_t* __restrict__ S,
     const int* __restrict__ o2site, const long long* __restrict__ toff,
     const long long* __restrict__ ooff, const double* __restrict__ p, const double* __restrict__ w,
     double* __restrict__ y, double* __restrict__ ypart, int ndp, const double* __restrict__ dpart,
@@ -403,13 +429,13 @@ __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
   int i = blockIdx.x * (blockDim.x >> 5) + warp;
   double yi = 0;
   if (i < n) {
-    const float4* row = (const float4*)(O + (long long)i * No);
+    const OT* row = O + (long long)i * No;
     const uint8_t* Si = S + (long long)i * N;
     const long long nq = No >> 2;
     double acc = 0.0;
     long long q = lane;
     for (; q + 96 < nq; q += 128) {
-      float4 r[4];
+      OV4 r[4];
       const double* pp[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -417,12 +443,12 @@ __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
         const int j = o2site[o];
         const long long o0 = ooff[j];
         pp[u] = p + toff[j] + (long long)Si[j] * (ooff[j + 1] - o0) + (o - o0);
-        r[u] = __ldg(row + q + 32 * u);
+        r[u] = ov_ld4(row + ((q + 32 * u) << 2));
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const double2 a = __ldg((const double2*)pp[u]), b = __ldg((const double2*)pp[u] + 1);
-        acc += (double)r[u].x * a.x + (double)r[u].y * a.y + (double)r[u].z * b.x + (double)r[u].w * b.y;
+        acc += r[u].x * a.x + r[u].y * a.y + r[u].z * b.x + r[u].w * b.y;
       }
     }
     for (; q < nq; q += 32) {
@@ -430,9 +456,9 @@ __global__ void __launch_bounds__(SR_THREADS) k_ov_f32v(
       const int j = o2site[o];
       const long long o0 = ooff[j];
       const double* pp = p + toff[j] + (long long)Si[j] * (ooff[j + 1] - o0) + (o - o0);
-      const float4 r = __ldg(row + q);
+      const OV4 r = ov_ld4(row + (q << 2));
       const double2 a = __ldg((const double2*)pp), b = __ldg((const double2*)pp + 1);
-      acc += (double)r.x * a.x + (double)r.y * a.y + (double)r.z * b.x + (double)r.w * b.y;
+      acc += r.x * a.x + r.y * a.y + r.z * b.x + r.w * b.y;
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     yi = w[i] * (acc - obp);

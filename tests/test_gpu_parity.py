@@ -425,12 +425,14 @@ def test_sr_step_float_o_rows_match_oracle(prec, shape):
 @pytest.mark.parametrize("prec", [binding.PEPS_FP64, binding.PEPS_FP32])
 def test_cg_product_forms_agree(prec):
     # the fused single-read product and the two streaming passes solve the same float64
-    # system with different summation orders: after CG to 1e-12, x equal to 1e-10 relative
+    # system with different summation orders: after CG to 1e-12, x equal to 1e-10 relative;
+    # the passes over a float64 copy of float32 rows (mode 3, the automatic choice there)
+    # widen each entry exactly as the passes over the rows do, in the same order: same bits
     L, D, chi, n = 4, 2, 4, 700
     th = wl.random_theta(L, L, D, seed=51, scale=0.3, diag_bias=1.0)
     S = wl.random_configs(L, L, n, seed=52)
     xs = []
-    for mode in (1, 2):
+    for mode in (1, 2, 3, 0):
         ctx = _ctx(L, L, D, chi, n, prec=prec, mode=binding.PEPS_BLOCKS_BATCHED)
         ctx.set_cg_product(mode)
         ctx.set_theta(th)
@@ -441,8 +443,11 @@ def test_cg_product_forms_agree(prec):
         xs.append((th - ctx.get_theta()) / 0.05)
         ctx.close()
     assert np.max(np.abs(xs[0] - xs[1])) <= 1e-10 * max(1.0, np.max(np.abs(xs[1])))
+    assert np.array_equal(xs[2], xs[3])
+    if prec != binding.PEPS_FP64:
+        assert np.array_equal(xs[1], xs[2])
     with pytest.raises(binding.PepsError):
-        _ctx(3, 3, 2, 4, 4).set_cg_product(3)
+        _ctx(3, 3, 2, 4, 4).set_cg_product(4)
 
 
 def test_sr_step_cg_maxit_warning_and_observables():
