@@ -32,6 +32,10 @@ constexpr int WIDE_THREADS = 1024;    // wide blocks (temporaries in shared memo
 constexpr int WIDE_SMEM_MAX = 220 * 1024;
 constexpr double JTOL_F64 = 1e-15;
 constexpr float JTOL_F32 = 2e-7f;
+// TF32 mode: the Jacobi truncation stops once every column pair is orthogonal to the
+// operands' own rounding (TF32 unit roundoff 2^-11 = 4.9e-4): the truncated subspace is
+// then as accurate as the contractions that produced the matrix
+constexpr float JTOL_TF32 = 4.8e-4f;
 constexpr int JAC_MAX_SWEEPS = 60;
 
 // ------------------------------------------------------------------ sample kernels
@@ -805,7 +809,7 @@ int init_runner_t(peps_ctx* c, int sms, BatchImpl<T>* b, int Dn, const T* theta,
   r.theta = theta;
   r.toff = toff;
   r.ooff = c->ooff;
-  r.jtol = sizeof(T) == 8 ? (T)JTOL_F64 : (T)JTOL_F32;
+  r.jtol = sizeof(T) == 8 ? (T)JTOL_F64 : (P->precision == PEPS_TF32 ? (T)JTOL_TF32 : (T)JTOL_F32);
   r.max_sweeps = JAC_MAX_SWEEPS;
   r.sweeps = c->d_jsw;
   r.b.bind(real, chunk, i8, dbl, P->L1, P->L2, Dn, P->chi);
