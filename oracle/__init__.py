@@ -26,7 +26,11 @@ Modules:
   ed           exact diagonalisation and full-state imaginary-time evolution (Eqs. 1-3).
   hubbard_ed   exact diagonalisation of the Fermi-Hubbard model (Eq. 14): energy, double
                occupancy and next-nearest-neighbour spin correlation (checks for a
-               fermionic PEPS; no PEPS of it is built yet).
+               fermionic PEPS).
+  fermion      the vectorised fermionic thermal state in the doubled Fock space (system and
+               ancilla modes, the identity |I>, calH = H(c) + H(d)), its evolution, local
+               energies and observables, and the amplitudes of a fermionic (Grassmann-graded)
+               PEPS of sixteen local states.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a
 closed form, an invariant, brute force or exact diagonalisation (see tests/test_oracle_*.py).

@@ -1,0 +1,102 @@
+"""Pins of the fermionic vectorisation oracle (oracle/fermion.py): the identity's pairing
+relations and closed form, the doubled Hamiltonian on it, the beta = 0 closed forms of
+Eq. 14, the thermal energy and double occupancy against the sector-by-sector exact
+diagonalisation, the local energies' average, and the amplitudes against the matrix
+e^(-2tH) of the diagonalisation up to a fixed sign per configuration."""
+import numpy as np
+import pytest
+
+from oracle import fermion as fm
+from oracle import hubbard_ed as hed
+
+
+def _fock_pairs(N):
+    # doubled Fock state -> (s, s') in the diagonalisation's mode order (mode 2 i + spin)
+    out = {}
+    for st in range(1 << (4 * N)):
+        S = fm.local_indices(st, N)
+        s = sum(int(S[i] & 3) << (2 * i) for i in range(N))
+        sp = sum(int(S[i] >> 2) << (2 * i) for i in range(N))
+        out[st] = (s, sp)
+    return out
+
+
+def test_identity_pairs_system_with_ancilla():
+    N = 2
+    M = fm.n_modes(N)
+    I = fm.identity_state(N)
+    for i in range(N):
+        for s in range(2):
+            c = fm.create(M, fm.mode(i, s))
+            d = fm.create(M, fm.mode(i, 2 + s))
+            assert np.allclose(c.T @ I, d @ I)          # c|I> = d+|I>
+            assert np.allclose(c @ I, -(d.T @ I))       # c+|I> = -d|I>
+    # closed form: nonzero where system and ancilla occupations agree site by site, sign -1
+    # per doubly occupied pair (c+_up d+_up c+_dn d+_dn brought into mode order)
+    for st in range(1 << M):
+        S = fm.local_indices(st, N)
+        a, b = S & 3, S >> 2
+        want = 0.0 if np.any(a != b) else float(np.prod([-1.0 if x == 3 else 1.0 for x in a]))
+        assert I[st] == want
+
+
+@pytest.mark.parametrize("shape", [(1, 2), (2, 2)])
+def test_doubled_hamiltonian_on_identity(shape):
+    # Eq. 3 read for fermions: H on the ancilla acts on |I> as H on the system
+    nrow, ncol = shape
+    I = fm.identity_state(nrow * ncol)
+    Hc = fm.hubbard_terms(nrow, ncol, 0.7, 3.1, 1.3, 0)
+    Hd = fm.hubbard_terms(nrow, ncol, 0.7, 3.1, 1.3, 1)
+    assert np.allclose(Hc @ I, Hd @ I, atol=1e-12)
+    assert np.allclose(fm.calH(nrow, ncol, 0.7, 3.1, 1.3) @ I, 2 * (Hc @ I), atol=1e-12)
+
+
+def test_beta0_closed_forms():
+    # infinite temperature: E/N = Tr H / 4^N / N = U/4 - mu, double occupancy 1/4
+    for U, mu in ((8.0, 4.0), (3.0, 0.5)):
+        E, D = fm.observables(2, 2, 1.0, U, mu, fm.identity_state(4))
+        assert E == pytest.approx(U / 4 - mu, abs=1e-12)
+        assert D == pytest.approx(0.25, abs=1e-12)
+
+
+@pytest.mark.parametrize("shape,U,mu", [((2, 2), 8.0, 4.0), ((1, 3), 4.0, 1.0)])
+def test_thermal_state_matches_exact_diagonalisation(shape, U, mu):
+    # e^(-tau calH)|I> sampled with |rho|^2 is the thermal state at beta = 4 tau (Eq. 11)
+    nrow, ncol = shape
+    taus = [0.05, 0.2, 0.5]
+    ref = hed.thermal(nrow, ncol, 1.0, U, mu, [4 * t for t in taus])
+    for k, tau in enumerate(taus):
+        v = fm.evolve(nrow, ncol, 1.0, U, mu, tau)
+        E, D = fm.observables(nrow, ncol, 1.0, U, mu, v)
+        assert E == pytest.approx(ref[k, 0], rel=1e-9, abs=1e-12)
+        assert D == pytest.approx(ref[k, 1], rel=1e-9, abs=1e-12)
+        # the estimator of Eq. 9-11: <(E_sys + E_anc)/2>_{|rho|^2} is the same energy
+        es, ea = fm.local_energies(nrow, ncol, 1.0, U, mu, v)
+        w = v ** 2
+        nz = v != 0
+        assert np.sum(w[nz] * 0.5 * (es[nz] + ea[nz])) / np.sum(w) / (nrow * ncol) == pytest.approx(
+            ref[k, 0], rel=1e-9, abs=1e-12)
+
+
+def test_amplitudes_are_the_matrix_up_to_a_fixed_sign():
+    # <S|e^(-tau calH)|I> against e^(-2 tau H)(s, s') of the diagonalisation: equal in size,
+    # with a sign that depends on the configuration alone (the same at every tau)
+    nrow, ncol, U, mu = 1, 2, 3.0, 1.0
+    N = nrow * ncol
+    H = hed.full_hamiltonian(nrow, ncol, 1.0, U, mu)
+    pairs = _fock_pairs(N)
+    signs = None
+    for tau in (0.1, 0.4):
+        v = fm.evolve(nrow, ncol, 1.0, U, mu, tau)
+        rho = hed.evolved_rho(H, tau)
+        m = np.array([rho[pairs[st]] for st in range(len(v))])
+        scale = np.linalg.norm(m)
+        nz = np.abs(m) > 1e-12 * scale
+        assert np.all(np.abs(v[~nz]) <= 1e-12)
+        ratio = v[nz] / (m[nz] / scale)
+        assert np.allclose(np.abs(ratio), 1.0, atol=1e-10)
+        sg = np.sign(ratio)
+        if signs is None:
+            signs = sg
+        else:
+            assert np.array_equal(sg, signs)
