@@ -22,7 +22,7 @@ Readings (the paper gives the vectorisation as a figure and a sentence):
     e^(-4tH) averages: beta_obs = 4 t (Eq. 11), as for spins.
 """
 import numpy as np
-from scipy.sparse import csr_matrix, identity
+from scipy.sparse import csr_matrix
 from scipy.sparse.linalg import expm_multiply
 
 from .hubbard_ed import _nn_bonds
@@ -135,3 +135,308 @@ def state_of(S):
     for i, v in enumerate(S):
         out |= int(v) << (4 * i)
     return out
+
+
+# ----------------------------------------------------------------- fermionic PEPS amplitudes
+#
+# Reading of the Fermi arrows (the paper names the scheme, PRB 99, 195153, and gives no
+# formula): every tensor is parity even, T_i[S, l, r, u, d] = 0 unless p(S) + p(l) + p(r) +
+# p(u) + p(d) is even, with p(S) = popcount(S) mod 2 for a local index and p(v) = v mod 2 for
+# a virtual index (index 0 even; the open edges have one even index).  The state is
+#     |psi> = sum_S psi(S)|S>,  psi(S) = sum_v prod_i T_i[S_i, v_i] sigma(S, v),
+# the Grassmann-ordered product of the site tensors: site i contributes, in site order, the
+# letters l_i, u_i, P_i, d_i, r_i (incoming legs, its physical creation string, outgoing legs),
+# odd letters anticommute, and sigma is the sign of the permutation of the odd letters that
+# brings every physical string to the front in site order (the Fock state |S>, modes in
+# increasing order) and every bond's two letters next to each other, the earlier site's
+# first (where the bond is integrated out).  A gate sum_k A_k B_k on sites i < j, A_k and B_k
+# of parity p_k on the sites' modes, acts on a state of even letters by attaching one virtual
+# index k to an outgoing leg of i and an incoming leg of j (tests/test_oracle_fermion.py).
+
+def _pv(v):
+    return int(v) & 1
+
+
+def _pS(s):
+    return bin(int(s)).count("1") & 1
+
+
+def fpeps_bonds(nrow, ncol):
+    """Bonds (i, j, 'h' or 'v'), i < j, horizontal (r of i, l of j) and vertical (d of i, u
+    of j), in a fixed order."""
+    out = []
+    for r in range(nrow):
+        for c in range(ncol):
+            i = r * ncol + c
+            if c + 1 < ncol:
+                out.append((i, i + 1, "h"))
+            if r + 1 < nrow:
+                out.append((i, i + ncol, "v"))
+    return out
+
+
+def fpeps_sign(nrow, ncol, S, vb):
+    """sigma(S, v) by its definition: the parity of the permutation of the odd letters.
+    vb[b] is the index of bond b of fpeps_bonds."""
+    N = nrow * ncol
+    bonds = fpeps_bonds(nrow, ncol)
+    legs = {}   # (site, leg) -> bond position
+    for b, (i, j, kind) in enumerate(bonds):
+        legs[(i, "r" if kind == "h" else "d")] = b
+        legs[(j, "l" if kind == "h" else "u")] = b
+    # target position of each letter: physical strings first, then the bonds' letter pairs
+    seq = []
+    for i in range(N):
+        for leg in ("l", "u", "P", "d", "r"):
+            if leg == "P":
+                if _pS(S[i]):
+                    seq.append(i)
+            elif (i, leg) in legs:
+                b = legs[(i, leg)]
+                if _pv(vb[b]):
+                    first = leg in ("r", "d")          # the earlier site's letter
+                    seq.append(N + 2 * b + (0 if first else 1))
+    inv = sum(1 for a in range(len(seq)) for c in range(a + 1, len(seq)) if seq[a] > seq[c])
+    return -1.0 if inv & 1 else 1.0
+
+
+def fpeps_sign_local(nrow, ncol, S, vb):
+    """sigma(S, v) from local factors: the physical strings among themselves, each site's
+    physical parity against its incoming legs, and every crossing of two vertical bonds
+    (the bond below (r, c) crosses those below (r, c') for c' > c and those below (r+1, c')
+    for c' < c)."""
+    N = nrow * ncol
+    bonds = fpeps_bonds(nrow, ncol)
+    idx = {(i, kind): b for b, (i, j, kind) in enumerate(bonds)}
+    inc = {}
+    for b, (i, j, kind) in enumerate(bonds):
+        inc[(j, kind)] = b
+    e = 0
+    pre = 0
+    for j in range(N):
+        pj = _pS(S[j])
+        pin = sum(_pv(vb[inc[(j, k)]]) for k in ("h", "v") if (j, k) in inc)
+        e += pj * (pre + pin)
+        pre += pj
+    def pvert(r, c):
+        b = idx.get((r * ncol + c, "v"))
+        return 0 if b is None else _pv(vb[b])
+    for r in range(nrow - 1):
+        for c in range(ncol):
+            pa = pvert(r, c)
+            if not pa:
+                continue
+            for c2 in range(c + 1, ncol):
+                e += pa * pvert(r, c2)
+            if r + 2 <= nrow - 1:
+                for c2 in range(c):
+                    e += pa * pvert(r + 1, c2)
+    return -1.0 if e & 1 else 1.0
+
+
+def fpeps_state(nrow, ncol, T):
+    """The whole state vector (2^(4N) amplitudes) of a fermionic PEPS by its definition:
+    every assignment of the virtual indices, every nonzero tensor entry.  T[i] has shape
+    (16, dl, dr, du, dd)."""
+    N = nrow * ncol
+    bonds = fpeps_bonds(nrow, ncol)
+    dims = []
+    for (i, j, kind) in bonds:
+        dims.append(T[i].shape[2] if kind == "h" else T[i].shape[4])
+    psi = np.zeros(1 << (4 * N))
+    legpos = {}
+    for b, (i, j, kind) in enumerate(bonds):
+        legpos[(i, 2 if kind == "h" else 4)] = b
+        legpos[(j, 1 if kind == "h" else 3)] = b
+    for vb in np.ndindex(*dims) if dims else [()]:
+        # per site: the vector over its sixteen local states at these virtual indices
+        slices = []
+        for i in range(N):
+            ix = [slice(None)] + [vb[legpos[(i, a)]] if (i, a) in legpos else 0 for a in (1, 2, 3, 4)]
+            slices.append(T[i][tuple(ix)])
+        nz = [np.nonzero(s)[0] for s in slices]
+        for S in np.ndindex(*[len(x) for x in nz]):
+            Sv = [int(nz[i][S[i]]) for i in range(N)]
+            amp = np.prod([slices[i][Sv[i]] for i in range(N)])
+            if amp == 0.0:
+                continue
+            psi[state_of(Sv)] += amp * fpeps_sign(nrow, ncol, Sv, vb)
+    return psi
+
+
+def random_even_fpeps(nrow, ncol, D, rng, scale=1.0):
+    """Seeded random parity-even tensors (16 local states, virtual dimension D inside, 1 on
+    the open edges)."""
+    T = []
+    for r in range(nrow):
+        for c in range(ncol):
+            dl, dr = (1 if c == 0 else D), (1 if c == ncol - 1 else D)
+            du, dd = (1 if r == 0 else D), (1 if r == nrow - 1 else D)
+            A = scale * rng.standard_normal((16, dl, dr, du, dd))
+            for idx in np.ndindex(*A.shape):
+                if (_pS(idx[0]) + sum(_pv(x) for x in idx[1:])) & 1:
+                    A[idx] = 0.0
+            T.append(A)
+    return T
+
+
+def fpeps_amplitude_brute(nrow, ncol, T, S):
+    """psi(S) by its definition: every assignment of the virtual indices."""
+    bonds = fpeps_bonds(nrow, ncol)
+    dims = [T[i].shape[2] if kind == "h" else T[i].shape[4] for (i, j, kind) in bonds]
+    legpos = {}
+    for b, (i, j, kind) in enumerate(bonds):
+        legpos[(i, 2 if kind == "h" else 4)] = b
+        legpos[(j, 1 if kind == "h" else 3)] = b
+    out = 0.0
+    for vb in np.ndindex(*dims) if dims else [()]:
+        amp = 1.0
+        for i in range(nrow * ncol):
+            ix = [int(S[i])] + [vb[legpos[(i, a)]] if (i, a) in legpos else 0 for a in (1, 2, 3, 4)]
+            amp *= T[i][tuple(ix)]
+            if amp == 0.0:
+                break
+        if amp != 0.0:
+            out += amp * fpeps_sign(nrow, ncol, S, vb)
+    return out
+
+
+def fpeps_amplitude_rows(nrow, ncol, T, S):
+    """psi(S) contracted row by row with the signs in local form (fpeps_sign_local): each
+    site's physical parity against its incoming legs folded into its tensor, the physical
+    strings' sign as one factor, and the crossings of vertical bonds applied to the indices
+    of the cuts (the bonds below one row among themselves, and those below row r against
+    those below row r+1 further left).  The contraction keeps the full index vector of a cut
+    (small lattices)."""
+    N = nrow * ncol
+    p = [_pS(s) for s in S]
+    gsign = 1.0
+    pre = 0
+    for j in range(N):
+        if p[j] and pre:
+            gsign = -gsign
+        pre ^= p[j]
+    # site tensors at S, with (-1)^(p(S) (p(l) + p(u)))
+    t = []
+    for i in range(N):
+        A = T[i][int(S[i])].copy()                    # (l, r, u, d)
+        if p[i]:
+            for idx in np.ndindex(*A.shape):
+                if (_pv(idx[0]) + _pv(idx[2])) & 1:
+                    A[idx] = -A[idx]
+        t.append(A)
+
+    def cut_sign(dims, other=None, other_dims=None):
+        # (-1)^(sum_{c<c'} p_c p_c') over one cut; with `other`, the cross term
+        # (-1)^(sum_{c'<c} p(this_c) p(next_c')) as an array over (this, next)
+        if other is None:
+            sg = np.ones(dims)
+            for idx in np.ndindex(*dims):
+                e = sum(_pv(idx[a]) * _pv(idx[b]) for a in range(len(idx)) for b in range(a + 1, len(idx)))
+                sg[idx] = -1.0 if e & 1 else 1.0
+            return sg
+        sg = np.ones(tuple(dims) + tuple(other_dims))
+        for idx in np.ndindex(*sg.shape):
+            a, b = idx[:len(dims)], idx[len(dims):]
+            e = sum(_pv(a[c]) * _pv(b[c2]) for c in range(len(a)) for c2 in range(c))
+            sg[idx] = -1.0 if e & 1 else 1.0
+        return sg
+
+    vec = np.ones([1] * ncol)                          # over the up legs of row 0
+    prev_dims = None
+    for r in range(nrow):
+        # row tensor over (up legs, down legs), horizontal bonds summed
+        R = t[r * ncol][0]                             # (h, u_0, d_0): left edge l = 0
+        for c in range(1, ncol):
+            k = c                                      # ups (and downs) gathered so far
+            R = np.tensordot(R, t[r * ncol + c], axes=([0], [0]))   # (u.., d.., h, u_c, d_c)
+            perm = [2 * k] + list(range(k)) + [2 * k + 1] + list(range(k, 2 * k)) + [2 * k + 2]
+            R = np.transpose(R, perm)                  # (h, u_0..u_c, d_0..d_c)
+        R = R[0]                                       # right edge: h of dimension 1
+        ups = R.shape[:ncol]
+        downs = R.shape[ncol:]
+        if r > 0:
+            # crossings of the bonds above this row (cut r-1) with the bonds below it (cut r)
+            R = R * cut_sign(ups, True, downs)
+        vec = np.tensordot(vec * cut_sign(ups), R, axes=(list(range(ncol)), list(range(ncol))))
+    return gsign * float(vec.reshape(()))
+
+
+def identity_fpeps(nrow, ncol):
+    """|I> as a fermionic PEPS of bond dimension 1: T_i[S] = <S_i|prod_s (1 + c+_s d+_s)|0>."""
+    T = []
+    for _ in range(nrow * ncol):
+        A = np.zeros((16, 1, 1, 1, 1))
+        for a in range(4):
+            A[a | (a << 2), 0, 0, 0, 0] = -1.0 if a == 3 else 1.0
+        T.append(A)
+    return T
+
+
+def hopping_gate_factors(t_hop, tau):
+    """exp(tau t sum_s (c+_is c_js + c+_js c_is)), the gate of the hopping term of Eq. 14 on
+    the system modes of two sites i < j, as sum_k A_k B_k: A_k, B_k 16 x 16 matrices on the
+    sites' local states (acting on their c modes), of parity p_k.  Obtained from the gate on
+    the two sites' eight modes (site i's first) by undoing the sign (-1)^(p_k p(a)) that
+    moving B_k past site i's string gives, then an SVD per parity."""
+    M = 8
+    cr = [create(M, m) for m in range(M)]
+    h = csr_matrix((1 << M, 1 << M))
+    for s in range(2):
+        hop = cr[s] @ cr[4 + s].T
+        h = h + (hop + hop.T)
+    from scipy.linalg import expm
+    G = expm(tau * t_hop * h.toarray())
+    par = np.array([_pS(x) for x in range(16)])
+    Gt = np.zeros((16, 16, 16, 16))                   # [a', a, b', b]
+    for a2 in range(16):
+        for a in range(16):
+            for b2 in range(16):
+                for b in range(16):
+                    v = G[a2 + 16 * b2, a + 16 * b]
+                    if v != 0.0 and (par[b2] ^ par[b]) & par[a]:
+                        v = -v
+                    Gt[a2, a, b2, b] = v
+    out = []
+    for q in (0, 1):
+        rows = [(a2, a) for a2 in range(16) for a in range(16) if par[a2] ^ par[a] == q]
+        cols = [(b2, b) for b2 in range(16) for b in range(16) if par[b2] ^ par[b] == q]
+        Mq = np.array([[Gt[a2, a, b2, b] for (b2, b) in cols] for (a2, a) in rows])
+        U, sv, Vt = np.linalg.svd(Mq)
+        for k in range(len(sv)):
+            if sv[k] <= 1e-13 * sv[0]:
+                break
+            A = np.zeros((16, 16))
+            B = np.zeros((16, 16))
+            for r_, (a2, a) in enumerate(rows):
+                A[a2, a] = U[r_, k] * np.sqrt(sv[k])
+            for c_, (b2, b) in enumerate(cols):
+                B[b2, b] = Vt[k, c_] * np.sqrt(sv[k])
+            out.append((q, A, B))
+    return out
+
+
+def apply_gate_to_product(T, i, j, kind, factors):
+    """Attaches a two-site gate sum_k A_k B_k (hopping_gate_factors) to the bond-dimension-1
+    tensors of sites i < j of a fermionic PEPS whose other legs at i and j are of dimension 1:
+    the virtual index of factor k (parity p_k; even factors on even indices, odd on odd) on
+    the outgoing leg of i (r for 'h', d for 'v') and the incoming leg of j (l or u)."""
+    ev = [f for f in factors if f[0] == 0]
+    od = [f for f in factors if f[0] == 1]
+    Dn = 2 * max(len(ev), len(od))
+    A_new = np.zeros((16, 1, Dn, 1, 1) if kind == "h" else (16, 1, 1, 1, Dn))
+    B_new = np.zeros((16, Dn, 1, 1, 1) if kind == "h" else (16, 1, 1, Dn, 1))
+    ti = T[i][:, 0, 0, 0, 0]
+    tj = T[j][:, 0, 0, 0, 0]
+    for q, lst in ((0, ev), (1, od)):
+        for n, (_, A, B) in enumerate(lst):
+            k = 2 * n + q
+            if kind == "h":
+                A_new[:, 0, k, 0, 0] = A @ ti
+                B_new[:, k, 0, 0, 0] = B @ tj
+            else:
+                A_new[:, 0, 0, 0, k] = A @ ti
+                B_new[:, 0, 0, k, 0] = B @ tj
+    T = list(T)
+    T[i], T[j] = A_new, B_new
+    return T

@@ -1,8 +1,10 @@
-"""Pins of the fermionic vectorisation oracle (oracle/fermion.py): the identity's pairing
+"""Pins of the fermionic oracle (oracle/fermion.py).  Vectorisation: the identity's pairing
 relations and closed form, the doubled Hamiltonian on it, the beta = 0 closed forms of
 Eq. 14, the thermal energy and double occupancy against the sector-by-sector exact
 diagonalisation, the local energies' average, and the amplitudes against the matrix
-e^(-2tH) of the diagonalisation up to a fixed sign per configuration."""
+e^(-2tH) of the diagonalisation up to a fixed sign per configuration.  Fermionic PEPS: the
+local form of the Grassmann sign against its definition, the row contraction against the
+sum over virtual indices, and PEPS carrying hopping gates against the Jordan-Wigner state."""
 import numpy as np
 import pytest
 
@@ -100,3 +102,90 @@ def test_amplitudes_are_the_matrix_up_to_a_fixed_sign():
             signs = sg
         else:
             assert np.array_equal(sg, signs)
+
+
+# ---------------------------------------------------------------- fermionic PEPS amplitudes
+
+def _consistent_assignment(nr, nc, rng):
+    bonds = fm.fpeps_bonds(nr, nc)
+    vb = rng.integers(0, 4, len(bonds))
+    S = []
+    for i in range(nr * nc):
+        par = 0
+        for b, (a, c, _) in enumerate(bonds):
+            if i in (a, c):
+                par ^= int(vb[b]) & 1
+        choices = [s for s in range(16) if (bin(s).count("1") & 1) == par]
+        S.append(int(rng.choice(choices)))
+    return S, vb
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (2, 3), (3, 3), (3, 4), (4, 3)])
+def test_fpeps_sign_local_form_equals_its_definition(shape):
+    # the permutation parity of the odd Grassmann letters against its local factors (the
+    # physical strings, each site's parity against its incoming legs, crossings of vertical
+    # bonds within a cut and with the next cut to the left)
+    nr, nc = shape
+    rng = np.random.default_rng(nr * 10 + nc)
+    for _ in range(200):
+        S, vb = _consistent_assignment(nr, nc, rng)
+        assert fm.fpeps_sign(nr, nc, S, vb) == fm.fpeps_sign_local(nr, nc, S, vb)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (2, 3), (3, 2), (3, 3)])
+def test_fpeps_row_contraction_equals_definition(shape):
+    # the contraction a sampler would run (signs on the cut indices) against the sum over
+    # every virtual assignment; odd-parity configurations vanish in both
+    nr, nc = shape
+    rng = np.random.default_rng(7 + nr + nc)
+    T = fm.random_even_fpeps(nr, nc, 2, rng)
+    nonzero = 0
+    for _ in range(8):
+        S = rng.integers(0, 16, nr * nc)
+        a = fm.fpeps_amplitude_brute(nr, nc, T, S)
+        b = fm.fpeps_amplitude_rows(nr, nc, T, S)
+        assert b == pytest.approx(a, rel=1e-12, abs=1e-14)
+        if sum(bin(int(s)).count("1") for s in S) % 2:
+            assert a == 0.0
+        else:
+            nonzero += a != 0.0
+    assert nonzero > 0
+
+
+def test_identity_fpeps():
+    assert np.array_equal(fm.fpeps_state(2, 2, fm.identity_fpeps(2, 2)), fm.identity_state(4))
+
+
+@pytest.mark.parametrize("shape,gates", [
+    ((1, 2), [(0, 1, "h")]),
+    ((2, 1), [(0, 1, "v")]),
+    ((2, 2), [(0, 2, "v")]),
+    ((2, 2), [(0, 1, "h"), (2, 3, "h")]),
+    ((2, 2), [(0, 2, "v"), (1, 3, "v")]),
+])
+def test_fpeps_of_gated_identity_is_the_fermionic_state(shape, gates):
+    # hopping gates of Eq. 14 applied to |I> on the state vector (Jordan-Wigner operators)
+    # against the fermionic PEPS that carries each gate on one bond: the same amplitudes,
+    # signs included, also where two vertical bonds cross in the Grassmann order
+    from scipy.sparse.linalg import expm_multiply
+    nr, nc = shape
+    tau, t_hop = 0.3, 1.0
+    f = fm.hopping_gate_factors(t_hop, tau)
+    assert sorted({q for q, _, _ in f}) == [0, 1]
+    N = nr * nc
+    M = fm.n_modes(N)
+    T = fm.identity_fpeps(nr, nc)
+    v = fm.identity_state(N)
+    for (i, j, kind) in gates:
+        T = fm.apply_gate_to_product(T, i, j, kind, f)
+        h = None
+        for s in range(2):
+            hop = fm.create(M, fm.mode(i, s)) @ fm.create(M, fm.mode(j, s)).T
+            h = (hop + hop.T) if h is None else h + hop + hop.T
+        v = expm_multiply(tau * t_hop * h, v)
+    psi = fm.fpeps_state(nr, nc, T)
+    assert np.max(np.abs(psi - v)) <= 1e-12 * np.max(np.abs(v))
+    # and its thermal content: the same energy as the state vector
+    E1, _ = fm.observables(nr, nc, t_hop, 8.0, 4.0, psi)
+    E2, _ = fm.observables(nr, nc, t_hop, 8.0, 4.0, v)
+    assert E1 == pytest.approx(E2, rel=1e-12)
