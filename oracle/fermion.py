@@ -440,3 +440,72 @@ def apply_gate_to_product(T, i, j, kind, factors):
     T = list(T)
     T[i], T[j] = A_new, B_new
     return T
+
+
+def _hop_sign(state, m_from, m_to):
+    """c+_{m_to} c_{m_from}|state>: (sign, new state) or None (Jordan-Wigner signs)."""
+    if not (state >> m_from) & 1:
+        return None
+    s1 = state & ~(1 << m_from)
+    sign = -1.0 if bin(state & ((1 << m_from) - 1)).count("1") % 2 else 1.0
+    if (s1 >> m_to) & 1:
+        return None
+    sign *= -1.0 if bin(s1 & ((1 << m_to) - 1)).count("1") % 2 else 1.0
+    return sign, s1 | (1 << m_to)
+
+
+def fpeps_local_energy(nrow, ncol, T, S, t_hop, U, mu):
+    """E_sys(S) and E_anc(S) of a fermionic PEPS (Eq. 9 with the terms of Eq. 14 on the system
+    and on the ancilla modes): the diagonal terms at S, plus every hop of one electron along a
+    nearest-neighbour bond with its Jordan-Wigner sign times psi(S') / psi(S), each amplitude
+    from the row contraction."""
+    N = nrow * ncol
+    st = state_of(S)
+    psi = fpeps_amplitude_rows(nrow, ncol, T, S)
+    out = []
+    for layer in (0, 1):
+        e = 0.0
+        for i in range(N):
+            nu = (st >> mode(i, 2 * layer)) & 1
+            nd = (st >> mode(i, 2 * layer + 1)) & 1
+            e += U * nu * nd - mu * (nu + nd)
+        for i, j in _nn_bonds(nrow, ncol):
+            for s in range(2):
+                for a, b in ((i, j), (j, i)):
+                    res = _hop_sign(st, mode(b, 2 * layer + s), mode(a, 2 * layer + s))
+                    if res is None:
+                        continue
+                    sign, st2 = res
+                    e += -t_hop * sign * fpeps_amplitude_rows(nrow, ncol, T, local_indices(st2, N)) / psi
+        out.append(e)
+    return out[0], out[1]
+
+
+def fpeps_log_derivative(nrow, ncol, T, S):
+    """O for configuration S (Eq. 8): d log psi(S) / d T_i[S_i, l, r, u, d] for every site, by
+    the definition (every virtual assignment; the entries of T_i at S_i)."""
+    N = nrow * ncol
+    bonds = fpeps_bonds(nrow, ncol)
+    dims = [T[i].shape[2] if kind == "h" else T[i].shape[4] for (i, j, kind) in bonds]
+    legpos = {}
+    for b, (i, j, kind) in enumerate(bonds):
+        legpos[(i, 2 if kind == "h" else 4)] = b
+        legpos[(j, 1 if kind == "h" else 3)] = b
+    grads = [np.zeros(T[i].shape[1:]) for i in range(N)]
+    psi = 0.0
+    for vb in np.ndindex(*dims) if dims else [()]:
+        ix = []
+        vals = []
+        for i in range(N):
+            leg = tuple(vb[legpos[(i, a)]] if (i, a) in legpos else 0 for a in (1, 2, 3, 4))
+            ix.append(leg)
+            vals.append(T[i][(int(S[i]),) + leg])
+        if sum(v != 0.0 for v in vals) < N - 1:
+            continue
+        sg = fpeps_sign(nrow, ncol, S, vb)
+        full = np.prod(vals)
+        psi += sg * full
+        for i in range(N):
+            rest = np.prod([vals[k] for k in range(N) if k != i])
+            grads[i][ix[i]] += sg * rest
+    return [g / psi for g in grads], psi

@@ -189,3 +189,37 @@ def test_fpeps_of_gated_identity_is_the_fermionic_state(shape, gates):
     E1, _ = fm.observables(nr, nc, t_hop, 8.0, 4.0, psi)
     E2, _ = fm.observables(nr, nc, t_hop, 8.0, 4.0, v)
     assert E1 == pytest.approx(E2, rel=1e-12)
+
+
+def test_fpeps_local_energy_and_log_derivative():
+    # a fermionic PEPS with hopping gates on two crossing vertical bonds (2x2): its local
+    # energies (Eq. 9, terms of Eq. 14, Jordan-Wigner signs, amplitudes of the row contraction)
+    # against the state vector's, and O (Eq. 8) against finite differences of the amplitude
+    nr, nc, t_hop, U, mu = 2, 2, 1.0, 8.0, 4.0
+    f = fm.hopping_gate_factors(t_hop, 0.3)
+    T = fm.identity_fpeps(nr, nc)
+    for (i, j, kind) in [(0, 2, "v"), (1, 3, "v")]:
+        T = fm.apply_gate_to_product(T, i, j, kind, f)
+    psi = fm.fpeps_state(nr, nc, T)
+    es, ea = fm.local_energies(nr, nc, t_hop, U, mu, psi)
+    rng = np.random.default_rng(3)
+    support = np.nonzero(np.abs(psi) > 1e-8 * np.max(np.abs(psi)))[0]
+    for st in rng.choice(support, 12, replace=False):
+        S = fm.local_indices(int(st), nr * nc)
+        e1, e2 = fm.fpeps_local_energy(nr, nc, T, S, t_hop, U, mu)
+        assert e1 == pytest.approx(es[st], rel=1e-10, abs=1e-10)
+        assert e2 == pytest.approx(ea[st], rel=1e-10, abs=1e-10)
+    # O against central differences of the amplitude on a random even PEPS
+    T = fm.random_even_fpeps(nr, nc, 2, rng)
+    S = [1, 3, 0, 2]   # even total parity
+    O, amp = fm.fpeps_log_derivative(nr, nc, T, S)
+    assert amp == pytest.approx(fm.fpeps_amplitude_rows(nr, nc, T, S), rel=1e-12)
+    h = 1e-6
+    for i in range(nr * nc):
+        for idx in list(np.ndindex(*T[i].shape[1:]))[:6]:
+            Tp = [x.copy() for x in T]
+            Tm = [x.copy() for x in T]
+            Tp[i][(S[i],) + idx] += h
+            Tm[i][(S[i],) + idx] -= h
+            d = (fm.fpeps_amplitude_rows(nr, nc, Tp, S) - fm.fpeps_amplitude_rows(nr, nc, Tm, S)) / (2 * h)
+            assert O[i][idx] == pytest.approx(d / amp, rel=1e-6, abs=1e-8)
