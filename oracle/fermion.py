@@ -509,3 +509,82 @@ def fpeps_log_derivative(nrow, ncol, T, S):
             rest = np.prod([vals[k] for k in range(N) if k != i])
             grads[i][ix[i]] += sg * rest
     return [g / psi for g in grads], psi
+
+
+# The Grassmann sign in fully local form (tests/test_oracle_fermion.py pins it against the
+# definition): with P_R the parity of the physical indices of rows 0..R (by parity evenness,
+# the parity of the vertical bonds below row R) and b_i the parity of the physical indices to
+# the left of site i in its row,
+#     sigma(S, v) = (-1)^(sum_(i<j) p_i p_j + sum_R P_(R-1) P_R)
+#                   * prod_i (-1)^((p(S_i) + p(d_i)) (p(l_i) + p(u_i)) + p(d_i) b_i),
+# a configuration sign times a sign per site that depends on its own legs, its local index
+# and one bit of the configuration.  So psi(S) is that configuration sign times the plain
+# contraction of the tensors T_i[S_i] with the per-site signs folded in: a PEPS of 32 slices
+# per site (S_i + 16 b_i) contracted as a bosonic one.
+
+def fpeps_config_sign(nrow, ncol, S):
+    """(-1)^(sum_(i<j) p_i p_j + sum_R P_(R-1) P_R)."""
+    p = [_pS(s) for s in S]
+    e = 0
+    pre = 0
+    for j in range(nrow * ncol):
+        e += p[j] * pre
+        pre ^= p[j]
+    prev = 0
+    acc = 0
+    for R in range(nrow):
+        acc ^= sum(p[R * ncol:(R + 1) * ncol]) & 1
+        e += prev * acc
+        prev = acc
+    return -1.0 if e & 1 else 1.0
+
+
+def fpeps_row_prefix_bits(nrow, ncol, S):
+    """b_i: the parity of the physical indices left of site i in its row."""
+    out = []
+    for r in range(nrow):
+        b = 0
+        for c in range(ncol):
+            out.append(b)
+            b ^= _pS(S[r * ncol + c])
+    return out
+
+
+def fpeps_signed_slices(T):
+    """The 32 signed slices per site: slice S + 16 b is T[S] times
+    (-1)^((p(S) + p(d)) (p(l) + p(u)) + p(d) b), shape (32, dl, dr, du, dd)."""
+    out = []
+    for A in T:
+        B = np.zeros((32,) + A.shape[1:])
+        for b in range(2):
+            for S in range(16):
+                for idx in np.ndindex(*A.shape[1:]):
+                    l, r, u, d = idx
+                    e = (_pS(S) + _pv(d)) * (_pv(l) + _pv(u)) + _pv(d) * b
+                    B[S + 16 * b][idx] = -A[S][idx] if e & 1 else A[S][idx]
+        out.append(B)
+    return out
+
+
+def plain_amplitude(nrow, ncol, tensors):
+    """Contraction of a plain (bosonic) PEPS whose site tensors are given at a fixed
+    configuration, each of shape (l, r, u, d): the row-vector method."""
+    vec = np.ones([1] * ncol)
+    for r in range(nrow):
+        R = tensors[r * ncol][0]
+        for c in range(1, ncol):
+            k = c
+            R = np.tensordot(R, tensors[r * ncol + c], axes=([0], [0]))
+            perm = [2 * k] + list(range(k)) + [2 * k + 1] + list(range(k, 2 * k)) + [2 * k + 2]
+            R = np.transpose(R, perm)
+        R = R[0]
+        vec = np.tensordot(vec, R, axes=(list(range(ncol)), list(range(ncol))))
+    return float(vec.reshape(()))
+
+
+def fpeps_amplitude_bosonic(nrow, ncol, T, S):
+    """psi(S) as the configuration sign times the plain contraction of the signed slices."""
+    Ts = fpeps_signed_slices(T)
+    b = fpeps_row_prefix_bits(nrow, ncol, S)
+    t = [Ts[i][int(S[i]) + 16 * b[i]] for i in range(nrow * ncol)]
+    return fpeps_config_sign(nrow, ncol, S) * plain_amplitude(nrow, ncol, t)

@@ -223,3 +223,16 @@ def test_fpeps_local_energy_and_log_derivative():
             Tm[i][(S[i],) + idx] -= h
             d = (fm.fpeps_amplitude_rows(nr, nc, Tp, S) - fm.fpeps_amplitude_rows(nr, nc, Tm, S)) / (2 * h)
             assert O[i][idx] == pytest.approx(d / amp, rel=1e-6, abs=1e-8)
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (2, 3), (3, 2), (3, 3)])
+def test_fpeps_bosonic_form(shape):
+    # the fully local form: a configuration sign times a plain contraction of 32 signed
+    # slices per site, against the sum over every virtual assignment (the definition)
+    nr, nc = shape
+    rng = np.random.default_rng(17 + nr * nc)
+    T = fm.random_even_fpeps(nr, nc, 2, rng)
+    for _ in range(8):
+        S = rng.integers(0, 16, nr * nc)
+        a = fm.fpeps_amplitude_brute(nr, nc, T, S)
+        assert fm.fpeps_amplitude_bosonic(nr, nc, T, S) == pytest.approx(a, rel=1e-12, abs=1e-14)
