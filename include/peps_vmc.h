@@ -153,6 +153,27 @@ int peps_observables(peps_ctx* ctx, int p, peps_stats* stats);
 int peps_step(peps_ctx* ctx, int n_sweeps, int p, double tau, double eps, int max_cg,
               double cg_tol, peps_stats* stats);
 
+/* Amplitudes of a fermionic PEPS of the doubled Hubbard lattice (Sec. II, fermionic
+ * vectorisation and Fig. 1b; Sec. III.B).  Sixteen local states per site: the modes c_up,
+ * c_dn (system) and d_up, d_dn (ancilla) in that order, S_i = their occupation bits (bit 0
+ * c_up ... bit 3 d_dn); sites row-major, and the Fock state of S has its creation operators
+ * in increasing mode order.  theta: float64, per site [16][dl][dr][du][dd] (n_theta = 16
+ * sum_i sz_i), parity even (p(S) + p(l) + p(r) + p(u) + p(d) even, p of a local index its
+ * popcount mod 2, of a virtual index its value mod 2; odd entries enter as given).  The Fermi
+ * arrows order each site's Grassmann letters l, u, P, d, r; the amplitude is the
+ * Grassmann-ordered contraction, evaluated as a configuration sign times the boundary-MPS
+ * contraction (bond chi) of 32 signed slices per site.  peps_famp_create builds an
+ * evaluator for up to n_max configurations (EINVAL for sizes outside the peps_init limits,
+ * ENOMEM); peps_famp_eval takes host theta and configurations [nb][L1*L2] (entries 0..15,
+ * EINVAL otherwise) and writes log|psi| and the sign (0 where psi = 0) to host arrays. */
+typedef struct peps_famp peps_famp;
+int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, void* stream,
+                     peps_famp** out);
+int peps_famp_eval(peps_famp* famp, const double* theta, size_t n_theta, const uint8_t* S, int nb,
+                   double* log_abs, int8_t* sign);
+const char* peps_famp_last_error(const peps_famp* famp);
+void peps_famp_free(peps_famp* famp);
+
 /* Evaluation of several contexts' chains in one launch: lattices of different sizes (and
  * D, chi, couplings) share one persistent grid of the per-block engine, chain by chain as
  * each context's own evaluation would do it (the same results, bit for bit).  Every context

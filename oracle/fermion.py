@@ -373,16 +373,17 @@ def identity_fpeps(nrow, ncol):
     return T
 
 
-def hopping_gate_factors(t_hop, tau):
-    """exp(tau t sum_s (c+_is c_js + c+_js c_is)), the gate of the hopping term of Eq. 14 on
-    the system modes of two sites i < j, as sum_k A_k B_k: A_k, B_k 16 x 16 matrices on the
+def hopping_gate_factors(t_hop, tau, spins=(0, 1)):
+    """exp(tau t sum_s (c+_is c_js + c+_js c_is)) over the given spins, the gate of the hopping
+    term of Eq. 14 on the system modes of two sites i < j, as sum_k A_k B_k: A_k, B_k 16 x 16
+    matrices on the
     sites' local states (acting on their c modes), of parity p_k.  Obtained from the gate on
     the two sites' eight modes (site i's first) by undoing the sign (-1)^(p_k p(a)) that
     moving B_k past site i's string gives, then an SVD per parity."""
     M = 8
     cr = [create(M, m) for m in range(M)]
     h = csr_matrix((1 << M, 1 << M))
-    for s in range(2):
+    for s in spins:
         hop = cr[s] @ cr[4 + s].T
         h = h + (hop + hop.T)
     from scipy.linalg import expm

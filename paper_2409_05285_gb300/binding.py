@@ -41,7 +41,8 @@ EXPORTS = [
     "peps_selftest_tc_timeout", "peps_autotune", "peps_profile_launch_bytes", "peps_set_tune", "peps_su_theta", "peps_su_warm_start", "peps_set_cg_product", "peps_srv_stop", "peps_cv_spline", "peps_set_graphs", "peps_graphs_captured",
     "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
-    "peps_set_trunc_fp64",
+    "peps_set_trunc_fp64", "peps_famp_create", "peps_famp_eval", "peps_famp_last_error",
+    "peps_famp_free",
 ]
 
 
@@ -150,6 +151,12 @@ def load(path=None):
     lib.peps_su_warm_start.argtypes = [vp, dp, ip]
     lib.peps_set_cg_product.argtypes = [vp, ip]
     lib.peps_set_trunc_fp64.argtypes = [vp, ip]
+    lib.peps_famp_create.argtypes = [ip, ip, ip, ip, ip, ip, vp, ctypes.POINTER(vp)]
+    lib.peps_famp_eval.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp, vp]
+    lib.peps_famp_last_error.argtypes = [vp]
+    lib.peps_famp_last_error.restype = ctypes.c_char_p
+    lib.peps_famp_free.argtypes = [vp]
+    lib.peps_famp_free.restype = None
     lib.peps_set_graphs.argtypes = [vp, ip]
     lib.peps_graphs_captured.argtypes = [vp]
     lib.peps_cv_spline.argtypes = [vp, vp, ip, dp, vp, vp, ip]
@@ -457,6 +464,42 @@ class Group:
         if self.grp:
             self.lib.peps_group_free(self.grp)
             self.grp = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FermionAmplitudes:
+    """Amplitudes of a fermionic PEPS of the doubled Hubbard lattice (peps_famp_*): sixteen
+    local states per site, parity-even float64 parameters [16][dl][dr][du][dd] per site."""
+
+    def __init__(self, L1, L2, D, chi, n_max, precision=PEPS_FP64, stream=None):
+        self.lib = load()
+        self.N = L1 * L2
+        self.h = ctypes.c_void_p()
+        rc = self.lib.peps_famp_create(L1, L2, D, chi, n_max, precision, stream, ctypes.byref(self.h))
+        if rc != PEPS_OK:
+            raise PepsError(rc, "peps_famp_create failed")
+
+    def eval(self, theta, S):
+        """(log|psi|, sign) of the configurations S (uint8 [nb][N], entries 0..15)."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        nb = int(S.shape[0])
+        la = np.empty(nb, np.float64)
+        sg = np.empty(nb, np.int8)
+        rc = self.lib.peps_famp_eval(self.h, _ptr(theta), theta.size, _ptr(S), nb, _ptr(la), _ptr(sg))
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        return la, sg
+
+    def close(self):
+        if self.h:
+            self.lib.peps_famp_free(self.h)
+            self.h = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -16,6 +16,7 @@
 #include "pv_su.cuh"
 #include "pv_su_dev.cuh"
 #include "pv_direct.cuh"
+#include "pv_fermion.cuh"
 
 #include <memory>
 #include <map>
@@ -1953,6 +1954,156 @@ int peps_step(peps_ctx* c, int n_sweeps, int p, double tau, double eps, int max_
   PV_TRY(peps_eval_batch(c, nullptr, c->P.n_chains, 1, nullptr, nullptr, nullptr, nullptr,
                          nullptr));
   return peps_sr_step(c, tau, eps, max_cg, cg_tol, p, st);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ fermionic amplitudes
+
+struct peps_famp {
+  peps_ctx* c = nullptr;   // internal context: stream, allocations, the batched runner
+  std::vector<long long> toff16, toff32;
+  long long n16 = 0;
+  int n_max = 0;
+  long long *d_toff16 = nullptr, *d_toff32 = nullptr;
+  double* d_th16 = nullptr;
+  void* d_th32 = nullptr;
+  uint8_t *d_S16 = nullptr, *d_S32 = nullptr;
+  int8_t *d_csign = nullptr, *d_sg = nullptr;
+  double* d_la = nullptr;
+  int* d_bad = nullptr;
+  BatchImpl<double>* b64 = nullptr;
+  BatchImpl<float>* b32 = nullptr;
+};
+
+extern "C" {
+
+int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, void* stream,
+                     peps_famp** out) {
+  if (!out) return PEPS_EINVAL;
+  *out = nullptr;
+  if (L1 < 2 || L2 < 2 || L1 > MAX_L || L2 > MAX_L || D < 1 || D > 8 || chi < 1 || chi > 64 ||
+      n_max < 1 || (precision != PEPS_FP64 && precision != PEPS_FP32 && precision != PEPS_TF32))
+    return PEPS_EINVAL;
+  std::unique_ptr<peps_famp> f(new peps_famp());
+  peps_ctx* c = new peps_ctx();
+  f->c = c;
+  c->P.L1 = L1;
+  c->P.L2 = L2;
+  c->P.D = D;
+  c->P.chi = chi;
+  c->P.n_chains = n_max;
+  c->P.precision = precision;
+  c->P.model = PEPS_MODEL_J1J2;
+  c->P.block_mode = PEPS_BLOCKS_BATCHED;
+  c->stream = (cudaStream_t)stream;
+  const int N = L1 * L2;
+  c->N = N;
+  f->n_max = n_max;
+  f->toff16.assign(N + 1, 0);
+  f->toff32.assign(N + 1, 0);
+  c->ooff.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) {
+    const int r = i / L2, q = i % L2;
+    const long long sz = (long long)(q == 0 ? 1 : D) * (q == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
+                         (r == L1 - 1 ? 1 : D);
+    f->toff16[i + 1] = f->toff16[i] + 16 * sz;
+    f->toff32[i + 1] = f->toff32[i] + 32 * sz;
+    c->ooff[i + 1] = c->ooff[i] + sz;
+  }
+  c->No = c->ooff[N];
+  f->n16 = f->toff16[N];
+  const size_t real = precision == PEPS_FP64 ? sizeof(double) : sizeof(float);
+  auto bail = [&](int rc) {
+    peps_free(c);
+    f->c = nullptr;
+    return rc;
+  };
+  int rc;
+  if ((rc = dalloc(c, &f->d_toff16, (N + 1) * sizeof(long long)))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_toff32, (N + 1) * sizeof(long long)))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_th16, (size_t)f->n16 * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, (unsigned char**)&f->d_th32, (size_t)f->toff32[N] * real))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_S16, (size_t)n_max * N))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_S32, (size_t)n_max * N))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_csign, (size_t)n_max))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_sg, (size_t)n_max))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_la, (size_t)n_max * sizeof(double)))) return bail(rc);
+  if ((rc = dalloc(c, &f->d_bad, sizeof(int)))) return bail(rc);
+  if ((rc = dalloc(c, &c->d_jsw, sizeof(unsigned long long)))) return bail(rc);
+  if (cudaMemcpy(f->d_toff16, f->toff16.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(f->d_toff32, f->toff32.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bail(PEPS_ECUDA);
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (precision == PEPS_FP64) {
+    f->b64 = new BatchImpl<double>();
+    c->batch.reset(f->b64);
+    rc = init_runner_t<double>(c, sms, f->b64, D, (const double*)f->d_th32, f->toff32);
+  } else {
+    f->b32 = new BatchImpl<float>();
+    c->batch.reset(f->b32);
+    rc = init_runner_t<float>(c, sms, f->b32, D, (const float*)f->d_th32, f->toff32);
+  }
+  if (rc != PEPS_OK) return bail(rc);
+  *out = f.release();
+  return PEPS_OK;
+}
+
+int peps_famp_eval(peps_famp* f, const double* theta, size_t n_theta, const uint8_t* S, int nb,
+                   double* log_abs, int8_t* sign) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && !S))
+    return fail(c, PEPS_EINVAL, "famp_eval: args");
+  if (nb == 0) return PEPS_OK;
+  const int N = c->N;
+  cudaStream_t st = c->stream;
+  PV_CUDA(c, cudaMemcpyAsync(f->d_th16, theta, (size_t)f->n16 * sizeof(double), cudaMemcpyHostToDevice, st));
+  long long big = 0;
+  for (int i = 0; i < N; ++i) big = std::max(big, f->toff32[i + 1] - f->toff32[i]);
+  dim3 g((unsigned)std::min<long long>((big + 255) / 256, 1024), (unsigned)N);
+  if (f->b64)
+    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
+               k_fsigned<double><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                    (double*)f->d_th32, f->d_toff32));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
+               k_fsigned<float><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                   (float*)f->d_th32, f->d_toff32));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
+  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
+  PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
+             k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
+                                                         f->d_csign, f->d_bad));
+  int bad = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (bad) return fail(c, PEPS_EINVAL, "famp_eval: a local index exceeds 15");
+  const int chunk = c->batch->chunk;
+  for (int off = 0; off < nb; off += chunk) {
+    const int n = std::min(chunk, nb - off);
+    if (f->b64)
+      plain_amplitude(f->b64->run, f->d_S32 + (long long)off * N, n, f->d_la + off, f->d_sg + off);
+    else
+      plain_amplitude(f->b32->run, f->d_S32 + (long long)off * N, n, f->d_la + off, f->d_sg + off);
+  }
+  PV_KLAUNCH(&c->kprof, st, "k_fapply", 0.0, 0.0,
+             k_fapply<<<(nb + 127) / 128, 128, 0, st>>>(nb, f->d_csign, f->d_sg, f->d_la));
+  PV_CUDA(c, cudaGetLastError());
+  if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, f->d_la, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, f->d_sg, (size_t)nb, cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  return batch_status(c);
+}
+
+const char* peps_famp_last_error(const peps_famp* f) { return f && f->c ? f->c->err.c_str() : ""; }
+
+void peps_famp_free(peps_famp* f) {
+  if (!f) return;
+  if (f->c) peps_free(f->c);
+  delete f;
 }
 
 }  // extern "C"

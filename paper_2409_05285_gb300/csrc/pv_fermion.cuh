@@ -1,0 +1,103 @@
+// Amplitudes of a fermionic PEPS of the doubled Hubbard lattice (Sec. II, Fig. 1b; Sec. III.B)
+// on the batched engine.
+//
+// The tensors are parity even with sixteen local states per site (system and ancilla modes
+// c_up, c_dn, d_up, d_dn; parity of a local index = popcount mod 2, of a virtual index = its
+// value mod 2) and the Fermi arrows order their Grassmann letters per site as l, u, P, d, r.
+// By parity evenness the sign of that order reduces to
+//     sign(S) * prod_i (-1)^((p(S_i) + p(d_i)) (p(l_i) + p(u_i)) + p(d_i) b_i),
+// with sign(S) = (-1)^(sum_(i<j) p_i p_j + sum_R P_(R-1) P_R) (P_R the parity of the physical
+// indices of rows 0..R) and b_i the parity of those left of site i in its row.  So the
+// amplitude is sign(S) times the plain contraction of 32 signed slices per site (slice
+// S_i + 16 b_i): the engine's own boundary-MPS contraction, unchanged.
+#ifndef PV_FERMION_CUH
+#define PV_FERMION_CUH
+#include <cstdint>
+
+#include "pv_batch.cuh"
+
+namespace pv {
+
+// log|psi| and the sign of the plain PEPS over `run`'s site tensors for the (extended)
+// local indices S: the down environments, the right partials of row 0, the amplitude.
+template <typename T, typename BE, typename OT>
+void plain_amplitude(BatchRunner<T, BE, OT>& run, const uint8_t* S, int n, double* la, int8_t* sg) {
+  auto& b = run.b;
+  run.build_down(S, n);
+  run.trivial(run.uprow(0), b.sU, n);
+  run.be.set(b.p1R, b.sp1R, (long long)run.L2 * b.P1, (T)1, n);
+  for (int c = run.L2 - 1; c >= 0; --c)
+    run.s1_right(0, c, run.p1R(c), b.sp1R, run.bat(run.p1R(c + 1), b.sp1R), run.site(0, c, S), n);
+  run.be.amp(b.p1R, b.sp1R, b.lsD + 1, run.L1 + 1, la, sg, n);
+}
+
+#if defined(__CUDACC__)
+
+// The 32 signed slices per site from the sixteen of theta (float64, per site
+// [16][dl][dr][du][dd]): block y = site, threads over slice x element.
+template <typename T>
+__global__ void k_fsigned(int L1, int L2, int D, const double* __restrict__ th16,
+                          const long long* __restrict__ toff16, T* __restrict__ th32,
+                          const long long* __restrict__ toff32) {
+  const int i = blockIdx.y, r = i / L2, c = i % L2;
+  const int dl = c == 0 ? 1 : D, dr = c == L2 - 1 ? 1 : D, du = r == 0 ? 1 : D, dd = r == L1 - 1 ? 1 : D;
+  const long long sz = (long long)dl * dr * du * dd;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 32 * sz;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int slice = (int)(e / sz), S = slice & 15, bb = slice >> 4;
+    const long long k = e - (long long)slice * sz;
+    long long t = k;
+    const int d = (int)(t % dd);
+    t /= dd;
+    const int u = (int)(t % du);
+    t /= du;
+    t /= dr;
+    const int l = (int)t;
+    const int pS = __popc(S) & 1;
+    const int ex = (pS + (d & 1)) * ((l & 1) + (u & 1)) + (d & 1) * bb;
+    const double v = th16[toff16[i] + (long long)S * sz + k];
+    th32[toff32[i] + e] = (T)((ex & 1) ? -v : v);
+  }
+}
+
+// Per chain: the extended local indices S_i + 16 b_i and sign(S); an entry above 15 raises
+// `bad` (the chain's sign is 0 and its indices are left at 0).
+__global__ void k_fconfigs(int n, int L1, int L2, const uint8_t* __restrict__ S,
+                           uint8_t* __restrict__ S32, int8_t* __restrict__ csign, int* bad) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int N = L1 * L2;
+  const uint8_t* x = S + (long long)s * N;
+  uint8_t* y = S32 + (long long)s * N;
+  int e = 0, pre = 0, prevP = 0, accP = 0, invalid = 0;
+  for (int r = 0; r < L1; ++r) {
+    int row = 0;
+    for (int c = 0; c < L2; ++c) {
+      const int v = x[r * L2 + c];
+      invalid |= v > 15;
+      const int p = __popc(v & 15) & 1;
+      y[r * L2 + c] = (uint8_t)(v > 15 ? 0 : v + 16 * row);
+      e += p * pre;
+      pre ^= p;
+      row ^= p;
+    }
+    accP ^= row;
+    e += prevP * accP;
+    prevP = accP;
+  }
+  csign[s] = invalid ? 0 : ((e & 1) ? -1 : 1);
+  if (invalid) atomicOr(bad, 1);
+}
+
+__global__ void k_fapply(int n, const int8_t* __restrict__ csign, int8_t* __restrict__ sign,
+                         double* __restrict__ la) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  sign[s] = (int8_t)(sign[s] * csign[s]);
+  if (csign[s] == 0) la[s] = NAN;
+}
+
+#endif  // __CUDACC__
+
+}  // namespace pv
+#endif
