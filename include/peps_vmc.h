@@ -171,6 +171,16 @@ int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, v
                      peps_famp** out);
 int peps_famp_eval(peps_famp* famp, const double* theta, size_t n_theta, const uint8_t* S, int nb,
                    double* log_abs, int8_t* sign);
+/* Local energies of the same configurations (Eq. 9 with the terms of Eq. 14: hopping t on
+ * nearest-neighbour bonds, U n_up n_dn, -mu n): e_sys from the terms on the system modes,
+ * e_anc from the same terms on the ancilla modes (calH = H(c) + H(d)); each hop's
+ * configuration is evaluated by the engine and enters with its Jordan-Wigner sign (modes
+ * ordered site by site, c_up c_dn d_up d_dn within a site).  Also log|psi| and the sign.
+ * NaN energies where psi = 0.  The first call allocates the hop workspace (8 x bonds
+ * configurations per chain). */
+int peps_famp_local_energy(peps_famp* famp, const double* theta, size_t n_theta, const uint8_t* S,
+                           int nb, double t, double U, double mu, double* log_abs, int8_t* sign,
+                           double* e_sys, double* e_anc);
 const char* peps_famp_last_error(const peps_famp* famp);
 void peps_famp_free(peps_famp* famp);
 

@@ -42,7 +42,7 @@ EXPORTS = [
     "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
     "peps_set_trunc_fp64", "peps_famp_create", "peps_famp_eval", "peps_famp_last_error",
-    "peps_famp_free",
+    "peps_famp_free", "peps_famp_local_energy",
 ]
 
 
@@ -153,6 +153,7 @@ def load(path=None):
     lib.peps_set_trunc_fp64.argtypes = [vp, ip]
     lib.peps_famp_create.argtypes = [ip, ip, ip, ip, ip, ip, vp, ctypes.POINTER(vp)]
     lib.peps_famp_eval.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp, vp]
+    lib.peps_famp_local_energy.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, vp, vp, vp, vp]
     lib.peps_famp_last_error.argtypes = [vp]
     lib.peps_famp_last_error.restype = ctypes.c_char_p
     lib.peps_famp_free.argtypes = [vp]
@@ -495,6 +496,21 @@ class FermionAmplitudes:
         if rc != PEPS_OK:
             raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
         return la, sg
+
+    def local_energy(self, theta, S, t_hop, U, mu):
+        """(log|psi|, sign, E_sys, E_anc) of the configurations S (peps_famp_local_energy)."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        nb = int(S.shape[0])
+        la = np.empty(nb, np.float64)
+        sg = np.empty(nb, np.int8)
+        es = np.empty(nb, np.float64)
+        ea = np.empty(nb, np.float64)
+        rc = self.lib.peps_famp_local_energy(self.h, _ptr(theta), theta.size, _ptr(S), nb, float(t_hop),
+                                             float(U), float(mu), _ptr(la), _ptr(sg), _ptr(es), _ptr(ea))
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        return la, sg, es, ea
 
     def close(self):
         if self.h:

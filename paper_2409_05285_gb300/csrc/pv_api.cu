@@ -1974,7 +1974,72 @@ struct peps_famp {
   int* d_bad = nullptr;
   BatchImpl<double>* b64 = nullptr;
   BatchImpl<float>* b32 = nullptr;
+  // local energies: nearest-neighbour bonds, and the connected configurations of up to
+  // x_cap chains (eight hop slots per bond) with their coefficients and amplitudes
+  int* d_bi = nullptr;
+  int* d_bj = nullptr;
+  int nbonds = 0;
+  long long x_cap = 0;
+  uint8_t* d_Sx = nullptr;
+  double *d_coef = nullptr, *d_lax = nullptr, *d_es = nullptr, *d_ea = nullptr;
+  int8_t* d_sgx = nullptr;
 };
+
+namespace {
+
+// log|psi| and sign of `count` configurations already on the device (entries checked): in
+// pieces of n_max through the extended indices and the engine.
+int famp_amplitudes(peps_famp* f, const uint8_t* dS, long long count, double* la, int8_t* sg) {
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  cudaStream_t st = c->stream;
+  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
+  for (long long off = 0; off < count; off += f->n_max) {
+    const int nb = (int)std::min<long long>(f->n_max, count - off);
+    PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
+               k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, dS + off * N,
+                                                           f->d_S32, f->d_csign, f->d_bad));
+    const int chunk = c->batch->chunk;
+    for (int o2 = 0; o2 < nb; o2 += chunk) {
+      const int n = std::min(chunk, nb - o2);
+      if (f->b64)
+        plain_amplitude(f->b64->run, f->d_S32 + (long long)o2 * N, n, la + off + o2, sg + off + o2);
+      else
+        plain_amplitude(f->b32->run, f->d_S32 + (long long)o2 * N, n, la + off + o2, sg + off + o2);
+    }
+    PV_KLAUNCH(&c->kprof, st, "k_fapply", 0.0, 0.0,
+               k_fapply<<<(nb + 127) / 128, 128, 0, st>>>(nb, f->d_csign, sg + off, la + off));
+  }
+  PV_CUDA(c, cudaGetLastError());
+  int bad = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (bad) return fail(c, PEPS_EINVAL, "famp: a local index exceeds 15");
+  return batch_status(c);
+}
+
+// theta (host, sixteen slices per site) into the signed slices on the device
+int famp_theta(peps_famp* f, const double* theta) {
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  cudaStream_t st = c->stream;
+  PV_CUDA(c, cudaMemcpyAsync(f->d_th16, theta, (size_t)f->n16 * sizeof(double), cudaMemcpyHostToDevice, st));
+  long long big = 0;
+  for (int i = 0; i < N; ++i) big = std::max(big, f->toff32[i + 1] - f->toff32[i]);
+  dim3 g((unsigned)std::min<long long>((big + 255) / 256, 1024), (unsigned)N);
+  if (f->b64)
+    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
+               k_fsigned<double><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                    (double*)f->d_th32, f->d_toff32));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
+               k_fsigned<float><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                   (float*)f->d_th32, f->d_toff32));
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -2058,44 +2123,76 @@ int peps_famp_eval(peps_famp* f, const double* theta, size_t n_theta, const uint
   if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && !S))
     return fail(c, PEPS_EINVAL, "famp_eval: args");
   if (nb == 0) return PEPS_OK;
-  const int N = c->N;
   cudaStream_t st = c->stream;
-  PV_CUDA(c, cudaMemcpyAsync(f->d_th16, theta, (size_t)f->n16 * sizeof(double), cudaMemcpyHostToDevice, st));
-  long long big = 0;
-  for (int i = 0; i < N; ++i) big = std::max(big, f->toff32[i + 1] - f->toff32[i]);
-  dim3 g((unsigned)std::min<long long>((big + 255) / 256, 1024), (unsigned)N);
-  if (f->b64)
-    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
-               k_fsigned<double><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
-                                                    (double*)f->d_th32, f->d_toff32));
-  else
-    PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
-               k_fsigned<float><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
-                                                   (float*)f->d_th32, f->d_toff32));
-  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
-  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
-  PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
-             k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
-                                                         f->d_csign, f->d_bad));
-  int bad = 0;
-  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PV_CUDA(c, cudaStreamSynchronize(st));
-  if (bad) return fail(c, PEPS_EINVAL, "famp_eval: a local index exceeds 15");
-  const int chunk = c->batch->chunk;
-  for (int off = 0; off < nb; off += chunk) {
-    const int n = std::min(chunk, nb - off);
-    if (f->b64)
-      plain_amplitude(f->b64->run, f->d_S32 + (long long)off * N, n, f->d_la + off, f->d_sg + off);
-    else
-      plain_amplitude(f->b32->run, f->d_S32 + (long long)off * N, n, f->d_la + off, f->d_sg + off);
-  }
-  PV_KLAUNCH(&c->kprof, st, "k_fapply", 0.0, 0.0,
-             k_fapply<<<(nb + 127) / 128, 128, 0, st>>>(nb, f->d_csign, f->d_sg, f->d_la));
-  PV_CUDA(c, cudaGetLastError());
+  PV_TRY(famp_theta(f, theta));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * c->N, cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
   if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, f->d_la, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, f->d_sg, (size_t)nb, cudaMemcpyDeviceToHost, st));
   PV_CUDA(c, cudaStreamSynchronize(st));
-  return batch_status(c);
+  return PEPS_OK;
+}
+
+int peps_famp_local_energy(peps_famp* f, const double* theta, size_t n_theta, const uint8_t* S,
+                           int nb, double t_hop, double U, double mu, double* log_abs,
+                           int8_t* sign, double* e_sys, double* e_anc) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && !S) ||
+      !std::isfinite(t_hop) || !std::isfinite(U) || !std::isfinite(mu))
+    return fail(c, PEPS_EINVAL, "famp_local_energy: args");
+  if (nb == 0) return PEPS_OK;
+  const int N = c->N;
+  cudaStream_t st = c->stream;
+  if (!f->d_bi) {
+    std::vector<int> bi, bj;
+    for (int r = 0; r < c->P.L1; ++r)
+      for (int q = 0; q < c->P.L2; ++q) {
+        const int i = r * c->P.L2 + q;
+        if (q + 1 < c->P.L2) {
+          bi.push_back(i);
+          bj.push_back(i + 1);
+        }
+        if (r + 1 < c->P.L1) {
+          bi.push_back(i);
+          bj.push_back(i + c->P.L2);
+        }
+      }
+    f->nbonds = (int)bi.size();
+    PV_TRY(dalloc(c, &f->d_bi, bi.size() * sizeof(int)));
+    PV_TRY(dalloc(c, &f->d_bj, bj.size() * sizeof(int)));
+    PV_CUDA(c, cudaMemcpy(f->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PV_CUDA(c, cudaMemcpy(f->d_bj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PV_TRY(dalloc(c, &f->d_es, (size_t)f->n_max * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_ea, (size_t)f->n_max * sizeof(double)));
+  }
+  const int K = 8 * f->nbonds;
+  const long long nx = (long long)nb * K;
+  if (nx > f->x_cap) {
+    // the connected configurations of the largest batch so far (kept for later calls)
+    PV_TRY(dalloc(c, &f->d_Sx, (size_t)nx * N));
+    PV_TRY(dalloc(c, &f->d_coef, (size_t)nx * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_lax, (size_t)nx * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_sgx, (size_t)nx));
+    f->x_cap = nx;
+  }
+  PV_TRY(famp_theta(f, theta));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  PV_KLAUNCH(&c->kprof, st, "k_fhops", 0.0, 0.0,
+             k_fhops<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj,
+                                                                 f->nbonds, t_hop, f->d_Sx, f->d_coef));
+  PV_TRY(famp_amplitudes(f, f->d_Sx, nx, f->d_lax, f->d_sgx));
+  PV_KLAUNCH(&c->kprof, st, "k_fsum", 0.0, 0.0,
+             k_fsum<<<(nb + 127) / 128, 128, 0, st>>>(nb, N, K, f->d_S16, U, mu, f->d_coef, f->d_lax,
+                                                     f->d_sgx, f->d_la, f->d_sg, f->d_es, f->d_ea));
+  PV_CUDA(c, cudaGetLastError());
+  if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, f->d_la, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, f->d_sg, (size_t)nb, cudaMemcpyDeviceToHost, st));
+  if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, f->d_es, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, f->d_ea, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  return PEPS_OK;
 }
 
 const char* peps_famp_last_error(const peps_famp* f) { return f && f->c ? f->c->err.c_str() : ""; }

@@ -97,6 +97,74 @@ __global__ void k_fapply(int n, const int8_t* __restrict__ csign, int8_t* __rest
   if (csign[s] == 0) la[s] = NAN;
 }
 
+// Local energies of the Hubbard terms of Eq. 14 on the system (layer 0) or ancilla (layer 1)
+// modes: for chain s and slot k = ((bond * 2 + spin) * 2 + direction) * 2 + layer, the
+// configuration reached by c+_a c_b (a, b the bond's sites in the slot's direction) and the
+// coefficient -t times its Jordan-Wigner sign (0 where the hop is blocked; the slot then
+// carries the configuration itself).  Modes are ordered site by site, c_up, c_dn, d_up,
+// d_dn within a site; a local index holds the site's four occupation bits.
+__global__ void k_fhops(int nb, int N, const uint8_t* __restrict__ S, const int* __restrict__ bi,
+                        const int* __restrict__ bj, int nbonds, double t_hop,
+                        uint8_t* __restrict__ Sx, double* __restrict__ coef) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int K = nbonds * 8;
+  if (q >= (long long)nb * K) return;
+  const int s = (int)(q / K), k = (int)(q % K);
+  const int layer = k & 1, dir = (k >> 1) & 1, spin = (k >> 2) & 1, bond = k >> 3;
+  const int a = dir ? bi[bond] : bj[bond], b = dir ? bj[bond] : bi[bond];   // c+_a c_b
+  const uint8_t* x = S + (long long)s * N;
+  uint8_t* y = Sx + q * N;
+  for (int i = 0; i < N; ++i) y[i] = x[i];
+  const int bit = 1 << (2 * layer + spin);
+  double cf = 0.0;
+  if ((x[b] & bit) && !(x[a] & bit)) {
+    // occupied modes below mode m = 4 site + local bit position
+    auto below = [&](const uint8_t* z, int site, int pos) {
+      int cnt = 0;
+      for (int i = 0; i < site; ++i) cnt += __popc(z[i]);
+      return cnt + __popc(z[site] & ((1 << pos) - 1));
+    };
+    const int pos = 2 * layer + spin;
+    int e = below(x, b, pos);
+    y[b] = (uint8_t)(x[b] & ~bit);
+    e += below(y, a, pos);
+    y[a] = (uint8_t)(x[a] | bit);
+    cf = -t_hop * ((e & 1) ? -1.0 : 1.0);
+  }
+  coef[q] = cf;
+}
+
+// E_sys and E_anc per chain: the diagonal terms (U n_up n_dn - mu (n_up + n_dn) per site and
+// layer) plus sum_k coef_k psi(S_k) / psi(S) over the chain's slots of that layer.
+__global__ void k_fsum(int nb, int N, int K, const uint8_t* __restrict__ S, double U, double mu,
+                       const double* __restrict__ coef, const double* __restrict__ la_x,
+                       const int8_t* __restrict__ sg_x, const double* __restrict__ la,
+                       const int8_t* __restrict__ sg, double* __restrict__ es,
+                       double* __restrict__ ea) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nb) return;
+  double e[2] = {0.0, 0.0};
+  const uint8_t* x = S + (long long)s * N;
+  for (int i = 0; i < N; ++i)
+    for (int layer = 0; layer < 2; ++layer) {
+      const int nu = (x[i] >> (2 * layer)) & 1, nd = (x[i] >> (2 * layer + 1)) & 1;
+      e[layer] += U * nu * nd - mu * (nu + nd);
+    }
+  if (sg[s] == 0) {
+    es[s] = NAN;
+    ea[s] = NAN;
+    return;
+  }
+  for (int k = 0; k < K; ++k) {
+    const long long q = (long long)s * K + k;
+    const double c = coef[q];
+    if (c == 0.0 || sg_x[q] == 0) continue;
+    e[k & 1] += c * (double)(sg_x[q] * sg[s]) * exp(la_x[q] - la[s]);
+  }
+  es[s] = e[0];
+  ea[s] = e[1];
+}
+
 #endif  // __CUDACC__
 
 }  // namespace pv

@@ -118,3 +118,51 @@ def test_gated_identity_against_the_fermionic_state():
     assert np.array_equal(sg, np.sign(ref).astype(np.int8))
     assert np.max(np.abs(la - np.log(np.abs(ref)))) <= 1e-10
     f.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.PEPS_FP64, 1e-9), (binding.PEPS_FP32, 1e-3)])
+def test_local_energies_match_oracle(prec, tol):
+    # E_sys and E_anc (Eq. 9, terms of Eq. 14 with Jordan-Wigner signs) against the oracle's
+    # row-contracted ratios, on a near-product state of 3x3 at exact chi
+    nr, nc, D, chi, t_hop, U, mu = 3, 3, 2, 8, 1.0, 8.0, 4.0
+    rng = np.random.default_rng(21)
+    T = _near_product(nr, nc, D, rng, 0.3)
+    ident = rng.integers(0, 4, (6, nr * nc))
+    S = np.concatenate([(ident | (ident << 2)).astype(np.uint8), _even_configs(nr * nc, 6, rng)])
+    f = binding.FermionAmplitudes(nr, nc, D, chi, len(S), precision=prec)
+    la, sg, es, ea = f.local_energy(_flat(T), S, t_hop, U, mu)
+    for k in range(len(S)):
+        r_es, r_ea = fm.fpeps_local_energy(nr, nc, T, S[k], t_hop, U, mu)
+        scale = max(1.0, abs(r_es), abs(r_ea))
+        assert abs(es[k] - r_es) <= tol * scale, k
+        assert abs(ea[k] - r_ea) <= tol * scale, k
+    f.close()
+
+
+def test_local_energies_of_the_gated_state_estimate_its_energy():
+    # the gated 2x2 state of the test above: the |psi|^2-weighted average of (E_sys + E_anc)/2
+    # over its whole support is its energy <H(c)> (Eq. 11 estimator, exact enumeration)
+    nr, nc, t_hop, U, mu = 2, 2, 1.0, 8.0, 4.0
+    fac = fm.hopping_gate_factors(1.0, 0.3, spins=(0,))
+    T = fm.identity_fpeps(nr, nc)
+    for (i, j, kind) in [(0, 2, "v"), (1, 3, "v")]:
+        T = fm.apply_gate_to_product(T, i, j, kind, fac)
+    psi = fm.fpeps_state(nr, nc, T)
+    support = np.nonzero(np.abs(psi) > 1e-12 * np.max(np.abs(psi)))[0]
+    S = np.array([fm.local_indices(int(st), nr * nc) for st in support], dtype=np.uint8)
+    D = max(max(t.shape[1:]) for t in T)
+    Tp = []
+    for r in range(nr):
+        for c in range(nc):
+            t = T[r * nc + c]
+            dims = (1 if c == 0 else D, 1 if c == nc - 1 else D, 1 if r == 0 else D, 1 if r == nr - 1 else D)
+            A = np.zeros((16,) + dims)
+            A[(slice(None),) + tuple(slice(0, x) for x in t.shape[1:])] = t
+            Tp.append(A)
+    f = binding.FermionAmplitudes(nr, nc, D, 16, len(S), precision=binding.PEPS_FP64)
+    la, sg, es, ea = f.local_energy(_flat(Tp), S, t_hop, U, mu)
+    w = np.exp(2 * (la - la.max()))
+    E = np.sum(w * 0.5 * (es + ea)) / np.sum(w) / (nr * nc)
+    E_ref, _ = fm.observables(nr, nc, t_hop, U, mu, psi)
+    assert E == pytest.approx(E_ref, rel=1e-10)
+    f.close()
