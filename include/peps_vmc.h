@@ -181,6 +181,12 @@ int peps_famp_eval(peps_famp* famp, const double* theta, size_t n_theta, const u
 int peps_famp_local_energy(peps_famp* famp, const double* theta, size_t n_theta, const uint8_t* S,
                            int nb, double t, double U, double mu, double* log_abs, int8_t* sign,
                            double* e_sys, double* e_anc);
+/* O rows of the same configurations (Eq. 8): d log psi / d theta at each site's slice S_i,
+ * [nb][N_o] with N_o = sum_i sz_i, per site [dl][dr][du][dd]; float64 for PEPS_FP64, float32
+ * otherwise (host array).  Each site's environment from the boundary-MPS strips divided by
+ * the amplitude, with the signs of the Fermi arrows. */
+int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_theta,
+                             const uint8_t* S, int nb, void* O);
 const char* peps_famp_last_error(const peps_famp* famp);
 void peps_famp_free(peps_famp* famp);
 

@@ -42,7 +42,7 @@ EXPORTS = [
     "peps_direct_draw", "peps_direct_next_bd", "peps_direct_step",
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
     "peps_set_trunc_fp64", "peps_famp_create", "peps_famp_eval", "peps_famp_last_error",
-    "peps_famp_free", "peps_famp_local_energy",
+    "peps_famp_free", "peps_famp_local_energy", "peps_famp_log_derivative",
 ]
 
 
@@ -154,6 +154,7 @@ def load(path=None):
     lib.peps_famp_create.argtypes = [ip, ip, ip, ip, ip, ip, vp, ctypes.POINTER(vp)]
     lib.peps_famp_eval.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp, vp]
     lib.peps_famp_local_energy.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, vp, vp, vp, vp]
+    lib.peps_famp_log_derivative.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp]
     lib.peps_famp_last_error.argtypes = [vp]
     lib.peps_famp_last_error.restype = ctypes.c_char_p
     lib.peps_famp_free.argtypes = [vp]
@@ -480,6 +481,9 @@ class FermionAmplitudes:
     def __init__(self, L1, L2, D, chi, n_max, precision=PEPS_FP64, stream=None):
         self.lib = load()
         self.N = L1 * L2
+        self.precision = precision
+        self.No = sum((1 if c == 0 else D) * (1 if c == L2 - 1 else D) * (1 if r == 0 else D) *
+                      (1 if r == L1 - 1 else D) for r in range(L1) for c in range(L2))
         self.h = ctypes.c_void_p()
         rc = self.lib.peps_famp_create(L1, L2, D, chi, n_max, precision, stream, ctypes.byref(self.h))
         if rc != PEPS_OK:
@@ -496,6 +500,17 @@ class FermionAmplitudes:
         if rc != PEPS_OK:
             raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
         return la, sg
+
+    def log_derivative(self, theta, S):
+        """O rows [nb][N_o] of the configurations S (peps_famp_log_derivative)."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        nb = int(S.shape[0])
+        O = np.empty((nb, self.No), np.float64 if self.precision == PEPS_FP64 else np.float32)
+        rc = self.lib.peps_famp_log_derivative(self.h, _ptr(theta), theta.size, _ptr(S), nb, _ptr(O))
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        return O
 
     def local_energy(self, theta, S, t_hop, U, mu):
         """(log|psi|, sign, E_sys, E_anc) of the configurations S (peps_famp_local_energy)."""

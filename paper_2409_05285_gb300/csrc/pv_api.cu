@@ -1983,6 +1983,8 @@ struct peps_famp {
   uint8_t* d_Sx = nullptr;
   double *d_coef = nullptr, *d_lax = nullptr, *d_es = nullptr, *d_ea = nullptr;
   int8_t* d_sgx = nullptr;
+  void* d_O = nullptr;             // O rows of up to n_max configurations
+  long long* d_ooff = nullptr;
 };
 
 namespace {
@@ -2193,6 +2195,57 @@ int peps_famp_local_energy(peps_famp* f, const double* theta, size_t n_theta, co
   if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, f->d_ea, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   PV_CUDA(c, cudaStreamSynchronize(st));
   return PEPS_OK;
+}
+
+int peps_famp_log_derivative(peps_famp* f, const double* theta, size_t n_theta, const uint8_t* S,
+                             int nb, void* O) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && (!S || !O)))
+    return fail(c, PEPS_EINVAL, "famp_log_derivative: args");
+  if (nb == 0) return PEPS_OK;
+  const int N = c->N;
+  const long long No = c->No;
+  cudaStream_t st = c->stream;
+  const size_t real = f->b64 ? sizeof(double) : sizeof(float);
+  if (!f->d_O) {
+    PV_TRY(dalloc(c, (unsigned char**)&f->d_O, (size_t)f->n_max * No * real));
+    PV_TRY(dalloc(c, &f->d_ooff, (N + 1) * sizeof(long long)));
+    PV_CUDA(c, cudaMemcpy(f->d_ooff, c->ooff.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  PV_TRY(famp_theta(f, theta));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
+  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
+  PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
+             k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
+                                                         f->d_csign, f->d_bad));
+  int bad = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (bad) return fail(c, PEPS_EINVAL, "famp_log_derivative: a local index exceeds 15");
+  const int chunk = c->batch->chunk;
+  for (int off = 0; off < nb; off += chunk) {
+    const int n = std::min(chunk, nb - off);
+    if (f->b64)
+      plain_log_derivative(f->b64->run, f->d_S32 + (long long)off * N, n, (double*)f->d_O + (long long)off * No, No);
+    else
+      plain_log_derivative(f->b32->run, f->d_S32 + (long long)off * N, n, (float*)f->d_O + (long long)off * No, No);
+  }
+  long long big = 0;
+  for (int i = 0; i < N; ++i) big = std::max(big, c->ooff[i + 1] - c->ooff[i]);
+  dim3 g((unsigned)std::min<long long>(((long long)nb * big + 255) / 256, 4096), (unsigned)N);
+  if (f->b64)
+    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
+               k_fosign<double><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (double*)f->d_O, No,
+                                                   f->d_ooff, f->d_S16));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
+               k_fosign<float><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (float*)f->d_O, No,
+                                                  f->d_ooff, f->d_S16));
+  PV_CUDA(c, cudaGetLastError());
+  PV_CUDA(c, cudaMemcpyAsync(O, f->d_O, (size_t)nb * No * real, cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  return batch_status(c);
 }
 
 const char* peps_famp_last_error(const peps_famp* f) { return f && f->c ? f->c->err.c_str() : ""; }

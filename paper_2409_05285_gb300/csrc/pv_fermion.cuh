@@ -31,7 +31,70 @@ void plain_amplitude(BatchRunner<T, BE, OT>& run, const uint8_t* S, int n, doubl
   run.be.amp(b.p1R, b.sp1R, b.lsD + 1, run.L1 + 1, la, sg, n);
 }
 
+// O rows of the plain PEPS (d log / d of the site tensor at its slice, Eq. 8): per row the
+// right partials, a rolling left partial, the environment of every site divided by the row
+// strip's value, then the row absorbed into the up environment (the evaluation's own steps).
+template <typename T, typename BE, typename OT>
+void plain_log_derivative(BatchRunner<T, BE, OT>& run, const uint8_t* S, int n, OT* O, long long No) {
+  auto& b = run.b;
+  run.build_down(S, n);
+  run.trivial(run.uprow(0), b.sU, n);
+  run.be.setd(b.lsU, 1, 0, 0.0, n);
+  for (int r = 0; r < run.L1; ++r) {
+    run.be.set(b.p1R, b.sp1R, (long long)run.L2 * b.P1, (T)1, n);
+    for (int c = run.L2 - 1; c >= 0; --c)
+      run.s1_right(r, c, run.p1R(c), b.sp1R, run.bat(run.p1R(c + 1), b.sp1R), run.site(r, c, S), n);
+    T* Lc = b.p1L;
+    T* Ln = b.p1L + b.P1;
+    run.be.set(b.p1L, b.sp1L, 0, (T)1, n);
+    for (int c = 0; c < run.L2; ++c) {
+      run.s1_env(r, c, run.bat(Lc, b.sp1L), run.bat(run.p1R(c + 1), b.sp1R), n);
+      run.be.writeO(O, No, run.ooff[r * run.L2 + c], b.envo, b.D4, run.szs(r, c), b.p1R, b.sp1R, n);
+      if (c + 1 < run.L2) {
+        run.s1_left(r, c, Ln, b.sp1L, run.bat(Lc, b.sp1L), run.site(r, c, S), n);
+        T* t = Lc;
+        Lc = Ln;
+        Ln = t;
+      }
+    }
+    if (r + 1 < run.L1)
+      run.compress(run.uprow(r), b.sU, run.shp.up[r], false, r, S, run.uprow(r + 1), b.sU, b.lsU, 1, n);
+  }
+}
+
 #if defined(__CUDACC__)
+
+// The plain O rows into those of the fermionic tensors: entry (l, r, u, d) of site i times
+// (-1)^((p(S_i) + p(d)) (p(l) + p(u)) + p(d) b_i), the derivative of the signed slice with
+// respect to the slice of theta.  Block y = site, threads over chains x entries.
+template <typename OT>
+__global__ void k_fosign(int n, int L1, int L2, int D, OT* __restrict__ O, long long No,
+                         const long long* __restrict__ ooff, const uint8_t* __restrict__ S) {
+  const int i = blockIdx.y, r = i / L2, c = i % L2, N = L1 * L2;
+  const int dr = c == L2 - 1 ? 1 : D, du = r == 0 ? 1 : D, dd = r == L1 - 1 ? 1 : D;
+  const long long sz = ooff[i + 1] - ooff[i];
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)n * sz;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / sz);
+    const long long k = e - (long long)s * sz;
+    long long t = k;
+    const int d = (int)(t % dd);
+    t /= dd;
+    const int u = (int)(t % du);
+    t /= du;
+    t /= dr;
+    const int l = (int)t;
+    const uint8_t* x = S + (long long)s * N;
+    int bb = 0;
+    for (int q = 0; q < c; ++q) bb ^= __popc(x[r * L2 + q]) & 1;
+    const int pS = __popc(x[i]) & 1;
+    const int ex = (pS + (d & 1)) * ((l & 1) + (u & 1)) + (d & 1) * bb;
+    if (ex & 1) {
+      OT* p = O + (long long)s * No + ooff[i] + k;
+      *p = -*p;
+    }
+  }
+}
 
 // The 32 signed slices per site from the sixteen of theta (float64, per site
 // [16][dl][dr][du][dd]): block y = site, threads over slice x element.

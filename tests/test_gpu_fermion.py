@@ -166,3 +166,21 @@ def test_local_energies_of_the_gated_state_estimate_its_energy():
     E_ref, _ = fm.observables(nr, nc, t_hop, U, mu, psi)
     assert E == pytest.approx(E_ref, rel=1e-10)
     f.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.PEPS_FP64, 1e-9), (binding.PEPS_FP32, 1e-3)])
+def test_log_derivatives_match_oracle(prec, tol):
+    # O (Eq. 8) of a random even PEPS (3x3, exact chi) against the oracle's sum over virtual
+    # assignments, entry by entry in the layout [site][dl][dr][du][dd]
+    nr, nc, D, chi = 3, 3, 2, 8
+    rng = np.random.default_rng(33)
+    T = fm.random_even_fpeps(nr, nc, D, rng, scale=0.5)
+    S = _even_configs(nr * nc, 4, rng)
+    f = binding.FermionAmplitudes(nr, nc, D, chi, 4, precision=prec)
+    O = f.log_derivative(_flat(T), S).astype(np.float64)
+    for k in range(len(S)):
+        grads, _ = fm.fpeps_log_derivative(nr, nc, T, S[k])
+        ref = np.concatenate([g.ravel() for g in grads])
+        scale = max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(O[k] - ref)) <= tol * scale, k
+    f.close()
