@@ -31,6 +31,9 @@ Modules:
                ancilla modes, the identity |I>, calH = H(c) + H(d)), its evolution, local
                energies and observables, and the amplitudes of a fermionic (Grassmann-graded)
                PEPS of sixteen local states.
+  fermion_vmc  Metropolis sampling of the fermionic PEPS (pair and hop moves, Philox
+               uniforms), the SR step on its samples (Eqs. 5-10) and the fermionic
+               estimators (energy, double occupancy, density).
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a
 closed form, an invariant, brute force or exact diagonalisation (see tests/test_oracle_*.py).
