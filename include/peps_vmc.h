@@ -187,6 +187,42 @@ int peps_famp_local_energy(peps_famp* famp, const double* theta, size_t n_theta,
  * the amplitude, with the signs of the Fermi arrows. */
 int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_theta,
                              const uint8_t* S, int nb, void* O);
+/* Metropolis sampling of the fermionic PEPS (Sec. II, MCMC; target |psi|^p, p = 2, or p = 1
+ * with the reweighting of Eq. A1).  One sweep proposes, in order: for every site (row-major)
+ * and spin s (up, then down), where c_s and d_s are equally occupied, both toggled (a
+ * system-ancilla pair created or removed); then for every nearest-neighbour bond (row-major,
+ * a site's horizontal bond before its vertical one) and mode k = 0..3 (c_up, c_dn, d_up,
+ * d_dn), one electron of mode k hopping across the bond, where the two occupations differ.
+ * A move that does not apply is skipped.  Move m (0 <= m < peps_famp_n_moves) of sweep k
+ * of chain c is accepted iff log u < p (log|psi'| - log|psi|) (float64; psi' = 0 rejected)
+ * with u = u[k][c][m] (host, [n_sweeps][nb][n_moves], values in (0, 1)) or, for u = NULL,
+ * Philox4x32-10 with key seed and counter (c, sweep0 + k, m, 0x464D4331).  Every proposal's
+ * amplitude is a full contraction.  S: host [nb][L1*L2], in (entries 0..15, EINVAL
+ * otherwise) and out; accepted (per chain, summed over the sweeps), log_abs and sign of the
+ * final configurations: host, NULL to skip.  EINVAL for p outside {1, 2}, negative
+ * n_sweeps or sweep counters beyond 32 bits. */
+int peps_famp_n_moves(const peps_famp* famp);
+int peps_famp_sweep(peps_famp* famp, const double* theta, size_t n_theta, uint8_t* S, int nb, int p,
+                    int n_sweeps, uint64_t seed, uint64_t sweep0, const double* u, int* accepted,
+                    double* log_abs, int8_t* sign);
+/* Observables of the samples of one SR step: E_site = sum_i w_i (E_sys + E_anc)/2 / N (Eq. 11),
+ * its standard error (delta method), the double occupancy and the density per site (n_up
+ * n_dn and n_up + n_dn, the two layers averaged); CG iterations and relative residual. */
+typedef struct {
+  double E_site, E_err, docc, density;
+  int cg_iters;
+  double cg_resid;
+} peps_fstats;
+/* One SR step of the fermionic PEPS on the nb configurations S (host [nb][L1*L2], all with
+ * psi != 0: EINVAL otherwise): E_sys, E_anc (the Hubbard terms of peps_famp_local_energy) and
+ * O rows; weights 1/nb (p = 2) or |psi|/sum|psi| (p = 1, Eq. A1); the mean, gradient (Eq. 7)
+ * and CG solve of (G + eps I) x = g (Eqs. 6 and 10, x_0 = 0, stop at |r| <= cg_tol |g| or
+ * max_cg iterations), then theta <- theta - tau x (Eq. 5).  theta: host float64, in and out.
+ * stats: host, NULL to skip (observables before the update).  Returns PEPS_WARN_CG_MAXIT
+ * when CG stopped at max_cg above the tolerance (theta is still updated). */
+int peps_famp_sr_step(peps_famp* famp, double* theta, size_t n_theta, const uint8_t* S, int nb,
+                      double t, double U, double mu, int p, double tau, double eps, int max_cg,
+                      double cg_tol, peps_fstats* stats);
 const char* peps_famp_last_error(const peps_famp* famp);
 void peps_famp_free(peps_famp* famp);
 

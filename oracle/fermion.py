@@ -583,9 +583,18 @@ def plain_amplitude(nrow, ncol, tensors):
     return float(vec.reshape(()))
 
 
+def fpeps_amplitude_function(nrow, ncol, T):
+    """S -> psi(S): the configuration sign times the plain contraction of the signed slices
+    (made once for T)."""
+    Ts = fpeps_signed_slices(T)
+
+    def amp(S):
+        b = fpeps_row_prefix_bits(nrow, ncol, S)
+        t = [Ts[i][int(S[i]) + 16 * b[i]] for i in range(nrow * ncol)]
+        return fpeps_config_sign(nrow, ncol, S) * plain_amplitude(nrow, ncol, t)
+    return amp
+
+
 def fpeps_amplitude_bosonic(nrow, ncol, T, S):
     """psi(S) as the configuration sign times the plain contraction of the signed slices."""
-    Ts = fpeps_signed_slices(T)
-    b = fpeps_row_prefix_bits(nrow, ncol, S)
-    t = [Ts[i][int(S[i]) + 16 * b[i]] for i in range(nrow * ncol)]
-    return fpeps_config_sign(nrow, ncol, S) * plain_amplitude(nrow, ncol, t)
+    return fpeps_amplitude_function(nrow, ncol, T)(S)

@@ -82,7 +82,7 @@ def sweep(nrow, ncol, T, S, p, u, amplitude=None):
     """One sweep of one chain with the uniforms u (one per move).  Returns (S, accepted,
     margin): margin is the smallest |log u - p (log|psi'| - log|psi|)| over the decisions
     taken (how close a decision came to its threshold)."""
-    amp = amplitude or (lambda X: fm.fpeps_amplitude_bosonic(nrow, ncol, T, X))
+    amp = amplitude or fm.fpeps_amplitude_function(nrow, ncol, T)
     S = [int(x) for x in S]
     la = _log_abs(amp(S))
     acc = 0

@@ -43,6 +43,7 @@ EXPORTS = [
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
     "peps_set_trunc_fp64", "peps_famp_create", "peps_famp_eval", "peps_famp_last_error",
     "peps_famp_free", "peps_famp_local_energy", "peps_famp_log_derivative",
+    "peps_famp_n_moves", "peps_famp_sweep", "peps_famp_sr_step",
 ]
 
 
@@ -155,6 +156,11 @@ def load(path=None):
     lib.peps_famp_eval.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp, vp]
     lib.peps_famp_local_energy.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, vp, vp, vp, vp]
     lib.peps_famp_log_derivative.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp]
+    lib.peps_famp_n_moves.argtypes = [vp]
+    lib.peps_famp_sweep.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, ip, ip, ctypes.c_uint64,
+                                    ctypes.c_uint64, vp, vp, vp, vp]
+    lib.peps_famp_sr_step.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, ip, dp, dp, ip,
+                                      dp, vp]
     lib.peps_famp_last_error.argtypes = [vp]
     lib.peps_famp_last_error.restype = ctypes.c_char_p
     lib.peps_famp_free.argtypes = [vp]
@@ -474,6 +480,15 @@ class Group:
             pass
 
 
+class FStats(ctypes.Structure):
+    _fields_ = [("E_site", ctypes.c_double), ("E_err", ctypes.c_double), ("docc", ctypes.c_double),
+                ("density", ctypes.c_double), ("cg_iters", ctypes.c_int),
+                ("cg_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FermionAmplitudes:
     """Amplitudes of a fermionic PEPS of the doubled Hubbard lattice (peps_famp_*): sixteen
     local states per site, parity-even float64 parameters [16][dl][dr][du][dd] per site."""
@@ -526,6 +541,48 @@ class FermionAmplitudes:
         if rc != PEPS_OK:
             raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
         return la, sg, es, ea
+
+    @property
+    def n_moves(self):
+        """Proposals in one Metropolis sweep (peps_famp_n_moves)."""
+        return int(self.lib.peps_famp_n_moves(self.h))
+
+    def sweep(self, theta, S, p=2, n_sweeps=1, seed=0, sweep0=0, u=None):
+        """n_sweeps Metropolis sweeps of the chains S (peps_famp_sweep): returns (S, accepted
+        per chain, log|psi|, sign) at the final configurations.  u: None (Philox) or
+        [n_sweeps][nb][n_moves] uniforms."""
+        theta = np.ascontiguousarray(theta, dtype=np.float64)
+        S = np.array(S, dtype=np.uint8, order="C", copy=True)
+        nb = int(S.shape[0])
+        acc = np.zeros(nb, np.int32)
+        la = np.empty(nb, np.float64)
+        sg = np.empty(nb, np.int8)
+        up = None
+        if u is not None:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+            if u.size != n_sweeps * nb * self.n_moves:
+                raise ValueError("u must hold n_sweeps x nb x n_moves uniforms")
+            up = _ptr(u)
+        rc = self.lib.peps_famp_sweep(self.h, _ptr(theta), theta.size, _ptr(S), nb, int(p),
+                                      int(n_sweeps), int(seed), int(sweep0), up, _ptr(acc),
+                                      _ptr(la), _ptr(sg))
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        return S, acc, la, sg
+
+    def sr_step(self, theta, S, t_hop, U, mu, p=2, tau=0.02, eps=1e-4, max_cg=100, cg_tol=1e-10):
+        """One SR step on the configurations S (peps_famp_sr_step): returns (theta', stats)."""
+        th = np.array(theta, dtype=np.float64, order="C", copy=True)
+        S = np.ascontiguousarray(S, dtype=np.uint8)
+        st = FStats()
+        rc = self.lib.peps_famp_sr_step(self.h, _ptr(th), th.size, _ptr(S), int(S.shape[0]),
+                                        float(t_hop), float(U), float(mu), int(p), float(tau),
+                                        float(eps), int(max_cg), float(cg_tol), ctypes.byref(st))
+        if rc not in (PEPS_OK, PEPS_WARN_CG_MAXIT):
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        d = st.as_dict()
+        d["cg_maxit"] = rc == PEPS_WARN_CG_MAXIT
+        return th, d
 
     def close(self):
         if self.h:

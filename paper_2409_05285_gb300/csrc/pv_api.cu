@@ -17,6 +17,7 @@
 #include "pv_su_dev.cuh"
 #include "pv_direct.cuh"
 #include "pv_fermion.cuh"
+#include "pv_fvmc.cuh"
 
 #include <memory>
 #include <map>
@@ -1985,17 +1986,36 @@ struct peps_famp {
   int8_t* d_sgx = nullptr;
   void* d_O = nullptr;             // O rows of up to n_max configurations
   long long* d_ooff = nullptr;
+  // sampling: the moves of one sweep, the proposed configurations and their amplitudes
+  std::vector<FMove> moves;
+  uint8_t *d_Sp = nullptr, *d_skip = nullptr;
+  double *d_la2 = nullptr, *d_u = nullptr;
+  int8_t* d_sg2 = nullptr;
+  int* d_acc = nullptr;
+  size_t u_cap = 0;
+  // SR over the sixteen-slice parameters: weights, chunk partials, CG vectors
+  int nvb = 0;
+  int* d_o2site = nullptr;
+  double *d_w = nullptr, *d_E = nullptr, *d_y = nullptr, *d_ypart = nullptr;
+  double *d_obar = nullptr, *d_g = nullptr, *d_x = nullptr, *d_r = nullptr, *d_p = nullptr,
+         *d_q = nullptr;
+  double *d_part = nullptr, *d_part2 = nullptr, *d_bp1 = nullptr, *d_bp2 = nullptr,
+         *d_pqpart = nullptr;
+  SRScalars* d_sc = nullptr;
+  FObs* d_fo = nullptr;
 };
 
 namespace {
 
-// log|psi| and sign of `count` configurations already on the device (entries checked): in
-// pieces of n_max through the extended indices and the engine.
-int famp_amplitudes(peps_famp* f, const uint8_t* dS, long long count, double* la, int8_t* sg) {
+// log|psi| and sign of `count` configurations already on the device (entries checked unless
+// `check` is off: the caller knows them valid): in pieces of n_max through the extended
+// indices and the engine.
+int famp_amplitudes(peps_famp* f, const uint8_t* dS, long long count, double* la, int8_t* sg,
+                    bool check = true) {
   peps_ctx* c = f->c;
   const int N = c->N;
   cudaStream_t st = c->stream;
-  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
+  if (check) PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
   for (long long off = 0; off < count; off += f->n_max) {
     const int nb = (int)std::min<long long>(f->n_max, count - off);
     PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
@@ -2013,6 +2033,7 @@ int famp_amplitudes(peps_famp* f, const uint8_t* dS, long long count, double* la
                k_fapply<<<(nb + 127) / 128, 128, 0, st>>>(nb, f->d_csign, sg + off, la + off));
   }
   PV_CUDA(c, cudaGetLastError());
+  if (!check) return PEPS_OK;
   int bad = 0;
   PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
   PV_CUDA(c, cudaStreamSynchronize(st));
@@ -2038,6 +2059,140 @@ int famp_theta(peps_famp* f, const double* theta) {
                k_fsigned<float><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
                                                    (float*)f->d_th32, f->d_toff32));
   PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+// log|psi|, sign, E_sys and E_anc of the nb configurations in d_S16 (theta's slices made):
+// the amplitudes, the configurations one hop away with their Jordan-Wigner coefficients, their
+// amplitudes, the sums.
+int famp_energies(peps_famp* f, int nb, double t_hop, double U, double mu) {
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  cudaStream_t st = c->stream;
+  if (!f->d_bi) {
+    std::vector<int> bi, bj;
+    for (int r = 0; r < c->P.L1; ++r)
+      for (int q = 0; q < c->P.L2; ++q) {
+        const int i = r * c->P.L2 + q;
+        if (q + 1 < c->P.L2) {
+          bi.push_back(i);
+          bj.push_back(i + 1);
+        }
+        if (r + 1 < c->P.L1) {
+          bi.push_back(i);
+          bj.push_back(i + c->P.L2);
+        }
+      }
+    f->nbonds = (int)bi.size();
+    PV_TRY(dalloc(c, &f->d_bi, bi.size() * sizeof(int)));
+    PV_TRY(dalloc(c, &f->d_bj, bj.size() * sizeof(int)));
+    PV_CUDA(c, cudaMemcpy(f->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PV_CUDA(c, cudaMemcpy(f->d_bj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice));
+    PV_TRY(dalloc(c, &f->d_es, (size_t)f->n_max * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_ea, (size_t)f->n_max * sizeof(double)));
+  }
+  const int K = 8 * f->nbonds;
+  const long long nx = (long long)nb * K;
+  if (nx > f->x_cap) {
+    // the connected configurations of the largest batch so far (kept for later calls)
+    PV_TRY(dalloc(c, &f->d_Sx, (size_t)nx * N));
+    PV_TRY(dalloc(c, &f->d_coef, (size_t)nx * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_lax, (size_t)nx * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_sgx, (size_t)nx));
+    f->x_cap = nx;
+  }
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  PV_KLAUNCH(&c->kprof, st, "k_fhops", 0.0, 0.0,
+             k_fhops<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj,
+                                                                 f->nbonds, t_hop, f->d_Sx, f->d_coef));
+  PV_TRY(famp_amplitudes(f, f->d_Sx, nx, f->d_lax, f->d_sgx, false));
+  PV_KLAUNCH(&c->kprof, st, "k_fsum", 0.0, 0.0,
+             k_fsum<<<(nb + 127) / 128, 128, 0, st>>>(nb, N, K, f->d_S16, U, mu, f->d_coef, f->d_lax,
+                                                     f->d_sgx, f->d_la, f->d_sg, f->d_es, f->d_ea));
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+// O rows of the nb configurations in d_S16 into d_O (theta's slices made): the plain rows of
+// the signed slices, then the per-entry signs.
+int famp_orows(peps_famp* f, int nb) {
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  const long long No = c->No;
+  cudaStream_t st = c->stream;
+  const size_t real = f->b64 ? sizeof(double) : sizeof(float);
+  if (!f->d_O) {
+    PV_TRY(dalloc(c, (unsigned char**)&f->d_O, (size_t)f->n_max * No * real));
+    PV_TRY(dalloc(c, &f->d_ooff, (N + 1) * sizeof(long long)));
+    PV_CUDA(c, cudaMemcpy(f->d_ooff, c->ooff.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
+  PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
+             k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
+                                                         f->d_csign, f->d_bad));
+  int bad = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (bad) return fail(c, PEPS_EINVAL, "famp: a local index exceeds 15");
+  const int chunk = c->batch->chunk;
+  for (int off = 0; off < nb; off += chunk) {
+    const int n = std::min(chunk, nb - off);
+    if (f->b64)
+      plain_log_derivative(f->b64->run, f->d_S32 + (long long)off * N, n, (double*)f->d_O + (long long)off * No, No);
+    else
+      plain_log_derivative(f->b32->run, f->d_S32 + (long long)off * N, n, (float*)f->d_O + (long long)off * No, No);
+  }
+  long long big = 0;
+  for (int i = 0; i < N; ++i) big = std::max(big, c->ooff[i + 1] - c->ooff[i]);
+  dim3 g((unsigned)std::min<long long>(((long long)nb * big + 255) / 256, 4096), (unsigned)N);
+  if (f->b64)
+    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
+               k_fosign<double><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (double*)f->d_O, No,
+                                                   f->d_ooff, f->d_S16));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
+               k_fosign<float><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (float*)f->d_O, No,
+                                                  f->d_ooff, f->d_S16));
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+// The sampling buffers (n_max chains), made once.
+int famp_sweep_buffers(peps_famp* f) {
+  if (f->d_Sp) return PEPS_OK;
+  peps_ctx* c = f->c;
+  const size_t n = (size_t)f->n_max;
+  PV_TRY(dalloc(c, &f->d_Sp, n * c->N));
+  PV_TRY(dalloc(c, &f->d_skip, n));
+  PV_TRY(dalloc(c, &f->d_la2, n * sizeof(double)));
+  PV_TRY(dalloc(c, &f->d_sg2, n));
+  PV_TRY(dalloc(c, &f->d_acc, n * sizeof(int)));
+  return PEPS_OK;
+}
+
+// The SR buffers (n_max samples, the sixteen-slice parameters), made once.
+int famp_sr_buffers(peps_famp* f) {
+  if (f->d_sc) return PEPS_OK;
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  const long long Np = f->n16, No = c->No;
+  const size_t n = (size_t)f->n_max;
+  const size_t nch = (n + OTV_CHUNK - 1) / OTV_CHUNK, nyb = (n + SR_THREADS / 32 - 1) / (SR_THREADS / 32);
+  f->nvb = grid_for(Np, SR_THREADS, 1024);
+  std::vector<int> o2s((size_t)No);
+  for (int i = 0; i < N; ++i)
+    for (long long o = c->ooff[i]; o < c->ooff[i + 1]; ++o) o2s[(size_t)o] = i;
+  PV_TRY(dalloc(c, &f->d_o2site, (size_t)No * sizeof(int)));
+  PV_CUDA(c, cudaMemcpy(f->d_o2site, o2s.data(), (size_t)No * sizeof(int), cudaMemcpyHostToDevice));
+  for (double** v : {&f->d_w, &f->d_E, &f->d_y}) PV_TRY(dalloc(c, v, n * sizeof(double)));
+  PV_TRY(dalloc(c, &f->d_ypart, nyb * sizeof(double)));
+  for (double** v : {&f->d_obar, &f->d_g, &f->d_x, &f->d_r, &f->d_p, &f->d_q})
+    PV_TRY(dalloc(c, v, (size_t)Np * sizeof(double)));
+  PV_TRY(dalloc(c, &f->d_part, nch * Np * sizeof(double)));
+  PV_TRY(dalloc(c, &f->d_part2, nch * Np * sizeof(double)));
+  for (double** v : {&f->d_bp1, &f->d_bp2, &f->d_pqpart}) PV_TRY(dalloc(c, v, (size_t)f->nvb * sizeof(double)));
+  PV_TRY(dalloc(c, &f->d_fo, sizeof(FObs)));
+  PV_TRY(dalloc(c, &f->d_sc, sizeof(SRScalars)));
   return PEPS_OK;
 }
 
@@ -2080,6 +2235,17 @@ int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, v
   }
   c->No = c->ooff[N];
   f->n16 = f->toff16[N];
+  // the moves of one sweep: pairs per site and spin, then hops per bond and mode (the
+  // horizontal bond of a site before its vertical one)
+  for (int i = 0; i < N; ++i)
+    for (int sp = 0; sp < 2; ++sp) f->moves.push_back(FMove{0, i, i, sp});
+  for (int i = 0; i < N; ++i) {
+    const int r = i / L2, q = i % L2;
+    if (q + 1 < L2)
+      for (int k = 0; k < 4; ++k) f->moves.push_back(FMove{1, i, i + 1, k});
+    if (r + 1 < L1)
+      for (int k = 0; k < 4; ++k) f->moves.push_back(FMove{1, i, i + L2, k});
+  }
   const size_t real = precision == PEPS_FP64 ? sizeof(double) : sizeof(float);
   auto bail = [&](int rc) {
     peps_free(c);
@@ -2144,57 +2310,16 @@ int peps_famp_local_energy(peps_famp* f, const double* theta, size_t n_theta, co
       !std::isfinite(t_hop) || !std::isfinite(U) || !std::isfinite(mu))
     return fail(c, PEPS_EINVAL, "famp_local_energy: args");
   if (nb == 0) return PEPS_OK;
-  const int N = c->N;
   cudaStream_t st = c->stream;
-  if (!f->d_bi) {
-    std::vector<int> bi, bj;
-    for (int r = 0; r < c->P.L1; ++r)
-      for (int q = 0; q < c->P.L2; ++q) {
-        const int i = r * c->P.L2 + q;
-        if (q + 1 < c->P.L2) {
-          bi.push_back(i);
-          bj.push_back(i + 1);
-        }
-        if (r + 1 < c->P.L1) {
-          bi.push_back(i);
-          bj.push_back(i + c->P.L2);
-        }
-      }
-    f->nbonds = (int)bi.size();
-    PV_TRY(dalloc(c, &f->d_bi, bi.size() * sizeof(int)));
-    PV_TRY(dalloc(c, &f->d_bj, bj.size() * sizeof(int)));
-    PV_CUDA(c, cudaMemcpy(f->d_bi, bi.data(), bi.size() * sizeof(int), cudaMemcpyHostToDevice));
-    PV_CUDA(c, cudaMemcpy(f->d_bj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice));
-    PV_TRY(dalloc(c, &f->d_es, (size_t)f->n_max * sizeof(double)));
-    PV_TRY(dalloc(c, &f->d_ea, (size_t)f->n_max * sizeof(double)));
-  }
-  const int K = 8 * f->nbonds;
-  const long long nx = (long long)nb * K;
-  if (nx > f->x_cap) {
-    // the connected configurations of the largest batch so far (kept for later calls)
-    PV_TRY(dalloc(c, &f->d_Sx, (size_t)nx * N));
-    PV_TRY(dalloc(c, &f->d_coef, (size_t)nx * sizeof(double)));
-    PV_TRY(dalloc(c, &f->d_lax, (size_t)nx * sizeof(double)));
-    PV_TRY(dalloc(c, &f->d_sgx, (size_t)nx));
-    f->x_cap = nx;
-  }
   PV_TRY(famp_theta(f, theta));
-  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
-  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
-  PV_KLAUNCH(&c->kprof, st, "k_fhops", 0.0, 0.0,
-             k_fhops<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj,
-                                                                 f->nbonds, t_hop, f->d_Sx, f->d_coef));
-  PV_TRY(famp_amplitudes(f, f->d_Sx, nx, f->d_lax, f->d_sgx));
-  PV_KLAUNCH(&c->kprof, st, "k_fsum", 0.0, 0.0,
-             k_fsum<<<(nb + 127) / 128, 128, 0, st>>>(nb, N, K, f->d_S16, U, mu, f->d_coef, f->d_lax,
-                                                     f->d_sgx, f->d_la, f->d_sg, f->d_es, f->d_ea));
-  PV_CUDA(c, cudaGetLastError());
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * c->N, cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_energies(f, nb, t_hop, U, mu));
   if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, f->d_la, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, f->d_sg, (size_t)nb, cudaMemcpyDeviceToHost, st));
   if (e_sys) PV_CUDA(c, cudaMemcpyAsync(e_sys, f->d_es, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (e_anc) PV_CUDA(c, cudaMemcpyAsync(e_anc, f->d_ea, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
   PV_CUDA(c, cudaStreamSynchronize(st));
-  return PEPS_OK;
+  return batch_status(c);
 }
 
 int peps_famp_log_derivative(peps_famp* f, const double* theta, size_t n_theta, const uint8_t* S,
@@ -2204,48 +2329,176 @@ int peps_famp_log_derivative(peps_famp* f, const double* theta, size_t n_theta, 
   if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && (!S || !O)))
     return fail(c, PEPS_EINVAL, "famp_log_derivative: args");
   if (nb == 0) return PEPS_OK;
-  const int N = c->N;
-  const long long No = c->No;
   cudaStream_t st = c->stream;
   const size_t real = f->b64 ? sizeof(double) : sizeof(float);
-  if (!f->d_O) {
-    PV_TRY(dalloc(c, (unsigned char**)&f->d_O, (size_t)f->n_max * No * real));
-    PV_TRY(dalloc(c, &f->d_ooff, (N + 1) * sizeof(long long)));
-    PV_CUDA(c, cudaMemcpy(f->d_ooff, c->ooff.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  PV_TRY(famp_theta(f, theta));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * c->N, cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_orows(f, nb));
+  PV_CUDA(c, cudaMemcpyAsync(O, f->d_O, (size_t)nb * c->No * real, cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  return batch_status(c);
+}
+
+int peps_famp_n_moves(const peps_famp* f) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  return (int)f->moves.size();
+}
+
+int peps_famp_sweep(peps_famp* f, const double* theta, size_t n_theta, uint8_t* S, int nb, int p,
+                    int n_sweeps, uint64_t seed, uint64_t sweep0, const double* u, int* accepted,
+                    double* log_abs, int8_t* sign) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && !S) ||
+      (p != 1 && p != 2) || n_sweeps < 0 || sweep0 + (uint64_t)n_sweeps > 0xFFFFFFFFull)
+    return fail(c, PEPS_EINVAL, "famp_sweep: args");
+  if (nb == 0) return PEPS_OK;
+  const int N = c->N, M = (int)f->moves.size();
+  cudaStream_t st = c->stream;
+  PV_TRY(famp_sweep_buffers(f));
+  const size_t nu = (size_t)n_sweeps * nb * M;
+  if (u && nu > f->u_cap) {
+    PV_TRY(dalloc(c, &f->d_u, nu * sizeof(double)));
+    f->u_cap = nu;
   }
   PV_TRY(famp_theta(f, theta));
   PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
-  PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
-  PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
-             k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
-                                                         f->d_csign, f->d_bad));
-  int bad = 0;
-  PV_CUDA(c, cudaMemcpyAsync(&bad, f->d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
-  PV_CUDA(c, cudaStreamSynchronize(st));
-  if (bad) return fail(c, PEPS_EINVAL, "famp_log_derivative: a local index exceeds 15");
-  const int chunk = c->batch->chunk;
-  for (int off = 0; off < nb; off += chunk) {
-    const int n = std::min(chunk, nb - off);
-    if (f->b64)
-      plain_log_derivative(f->b64->run, f->d_S32 + (long long)off * N, n, (double*)f->d_O + (long long)off * No, No);
-    else
-      plain_log_derivative(f->b32->run, f->d_S32 + (long long)off * N, n, (float*)f->d_O + (long long)off * No, No);
+  if (u && nu) PV_CUDA(c, cudaMemcpyAsync(f->d_u, u, nu * sizeof(double), cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  PV_CUDA(c, cudaMemsetAsync(f->d_acc, 0, (size_t)nb * sizeof(int), st));
+  const unsigned gb = (unsigned)((nb + 127) / 128);
+  for (int k = 0; k < n_sweeps; ++k) {
+    const double* uk = u ? f->d_u + (size_t)k * nb * M : nullptr;
+    for (int m = 0; m < M; ++m) {
+      PV_KLAUNCH(&c->kprof, st, "k_fpropose", 0.0, 0.0,
+                 k_fpropose<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_Sp, f->moves[m], f->d_skip));
+      PV_TRY(famp_amplitudes(f, f->d_Sp, nb, f->d_la2, f->d_sg2, false));
+      PV_KLAUNCH(&c->kprof, st, "k_faccept", 0.0, 0.0,
+                 k_faccept<<<gb, 128, 0, st>>>(nb, N, m, M, p, seed, (uint32_t)(sweep0 + k), uk,
+                                               f->d_skip, f->d_la2, f->d_sg2, f->d_S16, f->d_Sp,
+                                               f->d_la, f->d_sg, f->d_acc));
+    }
+    PV_CUDA(c, cudaGetLastError());
   }
-  long long big = 0;
-  for (int i = 0; i < N; ++i) big = std::max(big, c->ooff[i + 1] - c->ooff[i]);
-  dim3 g((unsigned)std::min<long long>(((long long)nb * big + 255) / 256, 4096), (unsigned)N);
-  if (f->b64)
-    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
-               k_fosign<double><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (double*)f->d_O, No,
-                                                   f->d_ooff, f->d_S16));
-  else
-    PV_KLAUNCH(&c->kprof, st, "k_fosign", 0.0, 0.0,
-               k_fosign<float><<<g, 256, 0, st>>>(nb, c->P.L1, c->P.L2, c->P.D, (float*)f->d_O, No,
-                                                  f->d_ooff, f->d_S16));
-  PV_CUDA(c, cudaGetLastError());
-  PV_CUDA(c, cudaMemcpyAsync(O, f->d_O, (size_t)nb * No * real, cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaMemcpyAsync(S, f->d_S16, (size_t)nb * N, cudaMemcpyDeviceToHost, st));
+  if (accepted) PV_CUDA(c, cudaMemcpyAsync(accepted, f->d_acc, (size_t)nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (log_abs) PV_CUDA(c, cudaMemcpyAsync(log_abs, f->d_la, (size_t)nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (sign) PV_CUDA(c, cudaMemcpyAsync(sign, f->d_sg, (size_t)nb, cudaMemcpyDeviceToHost, st));
   PV_CUDA(c, cudaStreamSynchronize(st));
   return batch_status(c);
+}
+
+int peps_famp_sr_step(peps_famp* f, double* theta, size_t n_theta, const uint8_t* S, int nb,
+                      double t_hop, double U, double mu, int p, double tau, double eps,
+                      int max_cg, double cg_tol, peps_fstats* out) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (!theta || n_theta != (size_t)f->n16 || nb < 1 || nb > f->n_max || !S || (p != 1 && p != 2) ||
+      !std::isfinite(t_hop) || !std::isfinite(U) || !std::isfinite(mu) || !std::isfinite(tau) ||
+      !(eps >= 0) || !(cg_tol >= 0) || max_cg < 0)
+    return fail(c, PEPS_EINVAL, "famp_sr_step: args");
+  const int N = c->N;
+  const long long Np = f->n16, No = c->No;
+  cudaStream_t st = c->stream;
+  PV_TRY(famp_sr_buffers(f));
+  PV_TRY(famp_theta(f, theta));
+  PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
+  PV_TRY(famp_energies(f, nb, t_hop, U, mu));
+  PV_TRY(famp_orows(f, nb));
+  PV_KLAUNCH(&c->kprof, st, "k_fweights", 0.0, 0.0,
+             k_fweights<<<1, SR_WEIGHT_THREADS, 0, st>>>(nb, N, p, f->d_la, f->d_sg, f->d_es, f->d_ea,
+                                                         f->d_S16, f->d_w, f->d_E, f->d_sc, f->d_fo));
+  FObs fo;
+  PV_CUDA(c, cudaMemcpyAsync(&fo, f->d_fo, sizeof(fo), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (fo.zero) return fail(c, PEPS_EINVAL, "famp_sr_step: a configuration has psi = 0");
+  // mean and gradient: one pass over the rows, then the chunk sums
+  const int nch = (nb + OTV_CHUNK - 1) / OTV_CHUNK, nyb = (nb + SR_THREADS / 32 - 1) / (SR_THREADS / 32);
+  const int nvb = f->nvb;
+  const dim3 cgrid((unsigned)((No + SR_THREADS - 1) / SR_THREADS), (unsigned)nch);
+  const bool f64 = f->b64 != nullptr;
+  if (f64)
+    PV_KLAUNCH(&c->kprof, st, "k_fcolsum1", 0.0, 0.0,
+               k_fcolsum1<double, true><<<cgrid, SR_THREADS, 0, st>>>(
+                   nb, N, No, (const double*)f->d_O, f->d_S16, f->d_o2site, f->d_toff16, f->d_ooff,
+                   f->d_w, f->d_E, &f->d_sc->Ebar, f->d_part, f->d_part2, Np, nullptr));
+  else
+    PV_KLAUNCH(&c->kprof, st, "k_fcolsum1", 0.0, 0.0,
+               k_fcolsum1<float, true><<<cgrid, SR_THREADS, 0, st>>>(
+                   nb, N, No, (const float*)f->d_O, f->d_S16, f->d_o2site, f->d_toff16, f->d_ooff,
+                   f->d_w, f->d_E, &f->d_sc->Ebar, f->d_part, f->d_part2, Np, nullptr));
+  PV_KLAUNCH(&c->kprof, st, "k_colsum2_grad", 0.0, 0.0,
+             k_colsum2_grad<<<grid_for(Np, SR_THREADS, 1 << 20), SR_THREADS, 0, st>>>(
+                 Np, nch, f->d_part, f->d_part2, f->d_obar, f->d_g));
+  // CG from x = 0 (Eq. 10 products as two passes over the rows)
+  PV_KLAUNCH(&c->kprof, st, "k_dot_part", 0.0, 0.0,
+             k_dot_part<<<nvb, SR_THREADS, 0, st>>>(Np, f->d_g, f->d_g, f->d_bp1, nullptr));
+  PV_KLAUNCH(&c->kprof, st, "k_cg_init", 0.0, 0.0,
+             k_cg_init<<<nvb, SR_THREADS, 0, st>>>(Np, f->d_g, f->d_x, f->d_r, f->d_p, nvb, f->d_bp1,
+                                                   f->d_sc, max_cg, cg_tol, eps));
+  PV_KLAUNCH(&c->kprof, st, "k_dot_part", 0.0, 0.0,
+             k_dot_part<<<nvb, SR_THREADS, 0, st>>>(Np, f->d_obar, f->d_p, f->d_bp2, nullptr));
+  PV_CUDA(c, cudaGetLastError());
+  for (int it = 0; it < max_cg; ++it) {
+    if (f64) {
+      PV_KLAUNCH(&c->kprof, st, "k_ov", 0.0, 0.0,
+                 k_ov<double><<<nyb, SR_THREADS, 0, st>>>(nb, N, No, (const double*)f->d_O, f->d_S16,
+                                                          f->d_toff16, f->d_ooff, f->d_p, f->d_w, f->d_y,
+                                                          f->d_ypart, nvb, f->d_bp2, f->d_sc));
+      PV_KLAUNCH(&c->kprof, st, "k_fcolsum1", 0.0, 0.0,
+                 k_fcolsum1<double, false><<<cgrid, SR_THREADS, 0, st>>>(
+                     nb, N, No, (const double*)f->d_O, f->d_S16, f->d_o2site, f->d_toff16, f->d_ooff,
+                     f->d_y, nullptr, nullptr, f->d_part, nullptr, Np, &f->d_sc->done));
+    } else {
+      PV_KLAUNCH(&c->kprof, st, "k_ov", 0.0, 0.0,
+                 k_ov<float><<<nyb, SR_THREADS, 0, st>>>(nb, N, No, (const float*)f->d_O, f->d_S16,
+                                                         f->d_toff16, f->d_ooff, f->d_p, f->d_w, f->d_y,
+                                                         f->d_ypart, nvb, f->d_bp2, f->d_sc));
+      PV_KLAUNCH(&c->kprof, st, "k_fcolsum1", 0.0, 0.0,
+                 k_fcolsum1<float, false><<<cgrid, SR_THREADS, 0, st>>>(
+                     nb, N, No, (const float*)f->d_O, f->d_S16, f->d_o2site, f->d_toff16, f->d_ooff,
+                     f->d_y, nullptr, nullptr, f->d_part, nullptr, Np, &f->d_sc->done));
+    }
+    PV_KLAUNCH(&c->kprof, st, "k_otv2", 0.0, 0.0,
+               k_otv2<<<nvb, SR_THREADS, 0, st>>>(Np, nch, f->d_part, f->d_obar, f->d_p, f->d_q, nyb,
+                                                  f->d_ypart, f->d_pqpart, f->d_sc));
+    PV_KLAUNCH(&c->kprof, st, "k_cg_a", 0.0, 0.0,
+               k_cg_a<<<nvb, SR_THREADS, 0, st>>>(Np, f->d_x, f->d_r, f->d_p, f->d_q, nvb, f->d_pqpart,
+                                                  f->d_bp1, f->d_sc));
+    PV_KLAUNCH(&c->kprof, st, "k_cg_b", 0.0, 0.0,
+               k_cg_b<<<nvb, SR_THREADS, 0, st>>>(Np, f->d_r, f->d_p, f->d_obar, nvb, f->d_bp1,
+                                                  f->d_bp2, f->d_sc));
+    PV_KLAUNCH(&c->kprof, st, "k_cg_scalars", 0.0, 0.0,
+               k_cg_scalars<<<1, 1, 0, st>>>(nvb, f->d_bp1, f->d_sc));
+    PV_CUDA(c, cudaGetLastError());
+    if ((it & 7) == 7) {
+      int done = 0;
+      PV_CUDA(c, cudaMemcpyAsync(&done, &f->d_sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+      PV_CUDA(c, cudaStreamSynchronize(st));
+      if (done) break;
+    }
+  }
+  PV_KLAUNCH(&c->kprof, st, "k_update", 0.0, 0.0,
+             k_update<<<grid_for(Np, 256), 256, 0, st>>>(Np, tau, f->d_x, f->d_th16, nullptr));
+  PV_CUDA(c, cudaGetLastError());
+  SRScalars h;
+  PV_CUDA(c, cudaMemcpyAsync(&h, f->d_sc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaMemcpyAsync(theta, f->d_th16, (size_t)Np * sizeof(double), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  PV_TRY(batch_status(c));
+  if (out) {
+    out->E_site = fo.H1 / N;
+    out->E_err = fo.Eerr / N;
+    out->docc = fo.docc / N;
+    out->density = fo.dens / N;
+    out->cg_iters = h.iters;
+    out->cg_resid = h.gnorm > 0 ? std::sqrt(h.rr) / h.gnorm : 0.0;
+  }
+  if (!std::isfinite(h.rr) || !std::isfinite(fo.H1))
+    return fail(c, PEPS_ENOTFINITE, "famp_sr_step: non-finite energy or residual");
+  return (h.iters >= max_cg && max_cg > 0 && h.gnorm > 0 && std::sqrt(h.rr) > cg_tol * h.gnorm)
+             ? PEPS_WARN_CG_MAXIT
+             : PEPS_OK;
 }
 
 const char* peps_famp_last_error(const peps_famp* f) { return f && f->c ? f->c->err.c_str() : ""; }
