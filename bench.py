@@ -976,6 +976,243 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def l2_flusher(stream):
+    """A function that writes a 256 MB device buffer (twice the 129 MB L2) on `stream`."""
+    import torch
+    buf = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+
+    def flush():
+        with torch.cuda.stream(stream):
+            buf.fill_(1.0)
+    return flush
+
+
+def _oracle_fermion_amps(args):
+    """Amplitudes of a few configurations by the oracle's exact row-vector contraction of the
+    signed slices (runs in a worker).  Returns (seconds, evaluations)."""
+    L, D, theta, S_list = args
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import fermion as fm
+    from oracle import fermion_vmc as fv
+    from paper_2409_05285_gb300.workloads import site_dims
+    like = [np.zeros((16,) + d) for d in site_dims(L, L, D)]
+    t0 = time.perf_counter()
+    amp = fm.fpeps_amplitude_function(L, L, fv.unflatten(theta, like))
+    for S in S_list:
+        amp(S)
+    return time.perf_counter() - t0, len(S_list)
+
+
+def oracle_fermion_baseline(wl, theta, S, per_worker=6):
+    """The oracle's cost per sample of the fermionic step, from a bounded sample: amplitude
+    evaluations (exact row-vector contraction) timed in a spawn pool over the host cores, and
+    the evaluations one sample needs (the proposals of a sweep that apply at its
+    configuration, its allowed hops for E_loc, its own amplitude) counted with the oracle's
+    move set.  The oracle's O rows (a sum over every virtual assignment) are left out."""
+    import multiprocessing as mp
+    from oracle import fermion_vmc as fv
+    cores = os.cpu_count() or 1
+    _one_thread_workers()
+    moves = fv.moves(wl.L, wl.L)
+    evals = []
+    for x in S[:64]:
+        app = [fv.propose(x, m) is not None for m in moves]
+        hops = sum(a for a, m in zip(app, moves) if m[0] == "hop")
+        evals.append(sum(app) + hops + 1)
+    per_sample = float(sum(evals)) / len(evals)
+    jobs = [(wl.L, wl.D, theta, [S[(w * per_worker + k) % len(S)] for k in range(per_worker)])
+            for w in range(cores)]
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_fermion_amps, jobs[:1])          # workers warm (imports)
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_fermion_amps, jobs)
+        wall = time.perf_counter() - t0
+    n_eval = sum(r[1] for r in res)
+    return {"value": n_eval / wall / per_sample, "unit": "samples/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"{n_eval} amplitude evaluations of the {wl.L}x{wl.L} D={wl.D} workload by the "
+                      f"oracle's exact row-vector contraction ({per_worker} per worker, spawn pool over "
+                      f"{cores} host cores, {wall:.1f} s), scaled by {per_sample:.1f} evaluations per "
+                      f"sample (applicable proposals of a sweep + allowed hops + 1); the oracle's O "
+                      f"rows and SR solve are not included (a lower bound on its cost)"}
+
+
+def run_fermion(args):
+    """Cooling steps of the fermionic thermal state (Sec. III.B: Hubbard t = 1, U = 8, mu = 4
+    on 6x6 OBC; fermionic PEPS of sixteen local states, D = 4, chi = 16): per step one
+    Metropolis sweep of every chain (peps_famp_sweep: pair and hop proposals, each proposal's
+    amplitude a full boundary-MPS contraction of the signed slices) and one SR step
+    (peps_famp_sr_step: local energies, O rows, weights, CG, update), from the perturbed |I>
+    (peps_famp_init_theta).  p = 1 while beta_obs < 0.3, then p = 2.  TF32 by default."""
+    import numpy as np
+    import torch
+
+    from paper_2409_05285_gb300 import binding
+    from paper_2409_05285_gb300.build import build
+    from paper_2409_05285_gb300.workloads import WORKLOADS, fermion_support_configs
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        build()
+    if ws > 1:
+        torch.distributed.barrier()
+    wl = WORKLOADS[args.workload if args.workload != "heis8" else "hubbard6"]
+    prec = {"fp32": binding.PEPS_FP32, "tf32": binding.PEPS_TF32, "fp64": binding.PEPS_FP64}[args.precision]
+    stream = torch.cuda.Stream()
+    n = args.chains or wl.n_samples
+    N = wl.L * wl.L
+    t_hop, U, mu = wl.extra["t"], wl.extra["U"], wl.extra["mu"]
+    tau, eps, max_cg, tol = wl.tau, wl.eps, wl.max_cg, wl.cg_tol
+    f = binding.FermionAmplitudes(wl.L, wl.L, wl.D, wl.chi, n, precision=prec,
+                                  stream=ctypes_stream(stream))
+    theta = binding.famp_init_theta(wl.L, wl.L, wl.D, wl.init_noise, rank_seed(wl.seed, rank))
+    theta0 = theta.copy()
+    S = fermion_support_configs(n, N, rank_seed(wl.seed, rank) + 1)
+    seed = rank_seed(wl.seed, rank) + 2
+    state = {"sweep": 0, "t": 0.0}
+
+    def step(theta, S, profile=None):
+        p = 1 if 4 * state["t"] < 0.3 else 2
+        S, acc, _, _ = f.sweep(theta, S, p=p, n_sweeps=1, seed=seed, sweep0=state["sweep"])
+        if profile is not None:
+            profile["sweep"] = kdelta(f.profile_read(), profile["base"], profile["sweep"])
+        theta, st = f.sr_step(theta, S, t_hop, U, mu, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+        if profile is not None:
+            profile["sr_step"] = kdelta(f.profile_read(), profile["base"], profile["sr_step"])
+        state["sweep"] += 1
+        state["t"] += tau
+        st["p"] = p
+        st["accept"] = float(acc.sum()) / (n * f.n_moves)
+        return theta, S, st
+
+    S, _, _, _ = f.sweep(theta, S, p=1, n_sweeps=args.burn, seed=seed, sweep0=0)
+    state["sweep"] = args.burn
+    for _ in range(args.warmup - 1):
+        theta, S, _ = step(theta, S)
+    # the last warm-up step with CUDA events around every launch (per-kernel time, bytes, flops)
+    f.profile(True)
+    prof = {"base": {}, "sweep": {}, "sr_step": {}}
+    theta, S, _ = step(theta, S, prof)
+    f.profile(False)
+    kstats = {}
+    for ph in ("sweep", "sr_step"):
+        for k, v in prof[ph].items():
+            a = kstats.get(k, (0, 0.0, 0.0, 0.0))
+            kstats[k] = tuple(x + y for x, y in zip(a, v))
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(local)
+    step_ms, sweep_ms, sr_ms, stats = [], [], [], []
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = f.launches()
+    flush = l2_flusher(stream)
+    torch.cuda.profiler.start()
+    for _ in range(args.steps):
+        e0, e1, e2 = ev(), ev(), ev()
+        p = 1 if 4 * state["t"] < 0.3 else 2
+        flush()
+        e0.record(stream)
+        S, acc, _, _ = f.sweep(theta, S, p=p, n_sweeps=1, seed=seed, sweep0=state["sweep"])
+        e1.record(stream)
+        theta, st = f.sr_step(theta, S, t_hop, U, mu, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+        e2.record(stream)
+        e2.synchronize()
+        state["sweep"] += 1
+        state["t"] += tau
+        st["p"] = p
+        st["accept"] = float(acc.sum()) / (n * f.n_moves)
+        stats.append(st)
+        sweep_ms.append(e0.elapsed_time(e1))
+        sr_ms.append(e1.elapsed_time(e2))
+        step_ms.append(e0.elapsed_time(e2))
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    clk = clocks.stop()
+    launches = f.launches() - launches0
+    del flush
+    total_ms = max_over_ranks(sum(step_ms))
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the public API: each step's host theta and configurations copied in
+    # (pinned host buffers), the updated theta, configurations and statistics read back
+    th_h = torch.empty(theta.size, dtype=torch.float64).pin_memory().numpy()
+    S_h = torch.empty(S.shape, dtype=torch.uint8).pin_memory().numpy()
+    th_h[:] = theta
+    S_h[:] = S
+    e2e_ms = []
+    for _ in range(max(2, args.steps // 2)):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        p = 1 if 4 * state["t"] < 0.3 else 2
+        S2, _, _, _ = f.sweep(th_h, S_h, p=p, n_sweeps=1, seed=seed, sweep0=state["sweep"])
+        th2, _ = f.sr_step(th_h, S2, t_hop, U, mu, p=p, tau=tau, eps=eps, max_cg=max_cg, cg_tol=tol)
+        e2e_ms.append((time.perf_counter() - t1) * 1e3)
+        th_h[:] = th2
+        S_h[:] = S2
+        state["sweep"] += 1
+        state["t"] += tau
+    e2e_step = statistics.median(e2e_ms)
+    np_ = theta.size
+    h2d = 2 * np_ * 8 + 2 * n * N
+    d2h = n * N + n * (4 + 8 + 1) + np_ * 8
+
+    peaks = measured_peaks()
+    roofline, kernels = kernel_roofline(kstats, peaks, prec, binding)
+    step_sorted = sorted(step_ms)
+    out = {
+        "metric": "fermionic PEPS samples/s per SR cooling step (Metropolis sweep + SR, Hubbard)",
+        "value": job_throughput(n, ws, ms_per_step),
+        "unit": "samples/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {binding.PEPS_FP64: "f64", binding.PEPS_FP32: "f32",
+                  binding.PEPS_TF32: "tf32 (contractions; f32 storage, f64 SR)"}[prec],
+        "data": "synthetic (seeded perturbed |I> cooled in-run; no dataset)",
+        "config": {"workload": f"{wl.L}x{wl.L} OBC Fermi-Hubbard t={t_hop} U={U} mu={mu}, d2=16 "
+                               f"(fermionic PEPS), D={wl.D}, chi={wl.chi}, {n} Metropolis chains per GPU",
+                   "global_batch": ws * n, "tau": tau, "eps": eps, "max_cg": max_cg, "cg_tol": tol,
+                   "moves_per_sweep": f.n_moves, "parallelism": f"replicas{ws}",
+                   "l2": "L2 flushed before every timed step (a 256 MB buffer written outside the "
+                         "step's events; O rows %.0f MB)" % (n * (np_ // 16) * (8 if prec == binding.PEPS_FP64 else 4) / 1e6)},
+        "sr_steps_per_s": ws / (ms_per_step / 1e3),
+        "latency_ms": {"p50": step_sorted[len(step_sorted) // 2],
+                       "p99": step_sorted[min(len(step_sorted) - 1, int(0.99 * len(step_sorted)))]},
+        "phase_ms": {"sweep": statistics.mean(sweep_ms), "sr_step": statistics.mean(sr_ms)},
+        "accept": statistics.mean(s_["accept"] for s_ in stats),
+        "cg_iters": statistics.mean(s_["cg_iters"] for s_ in stats),
+        "E_site": stats[-1]["E_site"], "E_err": stats[-1]["E_err"], "docc": stats[-1]["docc"],
+        "density": stats[-1]["density"], "beta_obs": 4 * (state["t"] - tau * len(e2e_ms)),
+        "roofline": roofline,
+        "kernels": kernels,
+        "kernels_by_phase": {ph: kernel_shares(prof[ph]) for ph in ("sweep", "sr_step")},
+        "kernel_stats_from": "one untimed step with CUDA events around every launch (the last warm-up step)",
+        "e2e": {"value": ws * n / (e2e_step / 1e3), "unit": "samples/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    f.close()
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = oracle_fermion_baseline(wl, theta0, S)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -997,6 +1234,8 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving-loop benchmark instead")
     ap.add_argument("--direct", action="store_true",
                     help="cooling steps on reweighted direct draws (workload direct6) instead")
+    ap.add_argument("--fermion", action="store_true",
+                    help="fermionic cooling steps (Hubbard, workload hubbard6) instead")
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--window", type=float, default=10.0, help="serving: arrival window (s)")
     ap.add_argument("--duration", type=float, default=60.0, help="serving: measured time (s)")
@@ -1025,6 +1264,8 @@ def main():
         run_serve(args)
     elif args.direct:
         run_direct(args)
+    elif args.fermion:
+        run_fermion(args)
     else:
         run_ours(args)
 

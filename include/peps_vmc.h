@@ -223,6 +223,14 @@ typedef struct {
 int peps_famp_sr_step(peps_famp* famp, double* theta, size_t n_theta, const uint8_t* S, int nb,
                       double t, double U, double mu, int p, double tau, double eps, int max_cg,
                       double cg_tol, peps_fstats* stats);
+/* The infinite-temperature state |I> = prod_(i,s) (1 + c+_is d+_is)|0> as fermionic PEPS
+ * parameters of bond dimension D (the fermionic counterpart of the beta = 0 state of Sec. II
+ * and App. A): per site, T[a | a << 2][0][0][0][0] = 1 for a = 0, 1, 2 and -1 for a = 3 (c+_dn
+ * moved past d+_up), every other parity-even entry noise (2u - 1) with u = Philox4x32-10(seed;
+ * site, entry index within the site's block, 0, 0x46494E54), parity-odd entries 0.  Host
+ * code; theta: host float64 of n_theta = 16 sum_i sz_i entries (EINVAL otherwise). */
+int peps_famp_init_theta(int L1, int L2, int D, double noise, uint64_t seed, double* theta,
+                         size_t n_theta);
 const char* peps_famp_last_error(const peps_famp* famp);
 void peps_famp_free(peps_famp* famp);
 
@@ -431,6 +439,11 @@ typedef struct {
 } peps_kernel_stat;
 int peps_profile(peps_ctx* ctx, int enable);
 int peps_profile_read(peps_ctx* ctx, peps_kernel_stat* out, int cap, int* n_out);
+/* The same timing for a fermionic evaluator's launches (peps_famp_*), and the number of
+ * kernels it has launched. */
+int peps_famp_profile(peps_famp* famp, int enable);
+int peps_famp_profile_read(peps_famp* famp, peps_kernel_stat* out, int cap, int* n_out);
+long long peps_famp_launches(const peps_famp* famp);
 /* The algorithmic bytes of each launch of kernel `name` recorded since profiling started or
  * since the last peps_profile_read (which folds the records into its sums), in launch order:
  * the first `cap` go to `bytes` (caller-owned), their number to *n_out.  Lets a per-launch

@@ -43,7 +43,8 @@ EXPORTS = [
     "peps_group_create", "peps_group_eval", "peps_group_last_error", "peps_group_free",
     "peps_set_trunc_fp64", "peps_famp_create", "peps_famp_eval", "peps_famp_last_error",
     "peps_famp_free", "peps_famp_local_energy", "peps_famp_log_derivative",
-    "peps_famp_n_moves", "peps_famp_sweep", "peps_famp_sr_step",
+    "peps_famp_n_moves", "peps_famp_sweep", "peps_famp_sr_step", "peps_famp_profile",
+    "peps_famp_profile_read", "peps_famp_launches", "peps_famp_init_theta",
 ]
 
 
@@ -157,6 +158,11 @@ def load(path=None):
     lib.peps_famp_local_energy.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, vp, vp, vp, vp]
     lib.peps_famp_log_derivative.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, vp]
     lib.peps_famp_n_moves.argtypes = [vp]
+    lib.peps_famp_profile.argtypes = [vp, ip]
+    lib.peps_famp_profile_read.argtypes = [vp, vp, ip, vp]
+    lib.peps_famp_launches.argtypes = [vp]
+    lib.peps_famp_launches.restype = ctypes.c_longlong
+    lib.peps_famp_init_theta.argtypes = [ip, ip, ip, dp, ctypes.c_uint64, vp, ctypes.c_size_t]
     lib.peps_famp_sweep.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, ip, ip, ctypes.c_uint64,
                                     ctypes.c_uint64, vp, vp, vp, vp]
     lib.peps_famp_sr_step.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, ip, dp, dp, ip,
@@ -542,6 +548,27 @@ class FermionAmplitudes:
             raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
         return la, sg, es, ea
 
+    def profile(self, enable):
+        """Starts (cleared) or stops per-kernel event timing of this evaluator's launches."""
+        rc = self.lib.peps_famp_profile(self.h, 1 if enable else 0)
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+
+    def profile_read(self):
+        """Per-kernel {name: (launches, ms, bytes, flops)} since profiling started."""
+        cap = 64
+        buf = (KernelStat * cap)()
+        n = ctypes.c_int()
+        rc = self.lib.peps_famp_profile_read(self.h, buf, cap, ctypes.byref(n))
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
+        return {buf[i].name.decode(): (buf[i].launches, buf[i].ms, buf[i].bytes, buf[i].flops)
+                for i in range(min(cap, n.value))}
+
+    def launches(self):
+        """Kernel launches this evaluator has made so far."""
+        return int(self.lib.peps_famp_launches(self.h))
+
     @property
     def n_moves(self):
         """Proposals in one Metropolis sweep (peps_famp_n_moves)."""
@@ -594,6 +621,18 @@ class FermionAmplitudes:
             self.close()
         except Exception:
             pass
+
+
+def famp_init_theta(L1, L2, D, noise=1e-3, seed=0):
+    """The infinite-temperature state |I> as fermionic PEPS parameters with parity-even Philox
+    noise (peps_famp_init_theta)."""
+    from .workloads import site_dims
+    n = 16 * sum(int(np.prod(d)) for d in site_dims(L1, L2, D))
+    th = np.empty(n, np.float64)
+    rc = load().peps_famp_init_theta(int(L1), int(L2), int(D), float(noise), int(seed), _ptr(th), n)
+    if rc != PEPS_OK:
+        raise PepsError(rc, "peps_famp_init_theta failed")
+    return th
 
 
 def direct_next_bd(b_d, diag_frac, N):

@@ -2501,6 +2501,53 @@ int peps_famp_sr_step(peps_famp* f, double* theta, size_t n_theta, const uint8_t
              : PEPS_OK;
 }
 
+int peps_famp_profile(peps_famp* f, int enable) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  return peps_profile(f->c, enable);
+}
+
+int peps_famp_profile_read(peps_famp* f, peps_kernel_stat* out, int cap, int* n_out) {
+  if (!f || !f->c) return PEPS_EINVAL;
+  return peps_profile_read(f->c, out, cap, n_out);
+}
+
+long long peps_famp_launches(const peps_famp* f) { return f && f->c ? f->c->kprof.launches : 0; }
+
+int peps_famp_init_theta(int L1, int L2, int D, double noise, uint64_t seed, double* theta,
+                         size_t n_theta) {
+  if (L1 < 1 || L2 < 1 || D < 1 || !(noise >= 0) || !theta) return PEPS_EINVAL;
+  size_t need = 0;
+  for (int i = 0; i < L1 * L2; ++i) {
+    const int r = i / L2, q = i % L2;
+    need += 16 * (size_t)(q == 0 ? 1 : D) * (q == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) * (r == L1 - 1 ? 1 : D);
+  }
+  if (n_theta != need) return PEPS_EINVAL;
+  size_t off = 0;
+  for (int i = 0; i < L1 * L2; ++i) {
+    const int r = i / L2, q = i % L2;
+    const int dl = q == 0 ? 1 : D, dr = q == L2 - 1 ? 1 : D, du = r == 0 ? 1 : D, dd = r == L1 - 1 ? 1 : D;
+    const size_t sz = (size_t)dl * dr * du * dd;
+    for (size_t e = 0; e < 16 * sz; ++e) {
+      const int S = (int)(e / sz);
+      size_t k = e % sz;
+      const int d = (int)(k % dd);
+      k /= dd;
+      const int u = (int)(k % du);
+      k /= du;
+      const int rr = (int)(k % dr);
+      const int l = (int)(k / dr);
+      const int par = ((S & 1) + ((S >> 1) & 1) + ((S >> 2) & 1) + ((S >> 3) & 1) + l + rr + u + d) & 1;
+      double v = 0.0;
+      if (!par && noise > 0)
+        v = noise * (2.0 * philox_uniform(seed, (uint32_t)i, (uint32_t)e, 0u, TAG_FINIT) - 1.0);
+      if (e % sz == 0 && (S & 3) == (S >> 2)) v = S == 15 ? -1.0 : 1.0;
+      theta[off + e] = v;
+    }
+    off += 16 * sz;
+  }
+  return PEPS_OK;
+}
+
 const char* peps_famp_last_error(const peps_famp* f) { return f && f->c ? f->c->err.c_str() : ""; }
 
 void peps_famp_free(peps_famp* f) {

@@ -11,6 +11,8 @@ Workloads (the paper's benchmark shapes, Sec. III.A; no dataset is involved):
   direct6 6x6 open Heisenberg (J1=1), D=2, chi=16, 30000 reweighted direct samples per SR
           step (App. A, Eqs. A2-A7; the sample count and lattice of the paper's direct-sampled
           runs, Sec. III.B, on the spin model), from the perturbed beta=0 state, b_d from 1.
+  hubbard6 6x6 open Fermi-Hubbard (Sec. III.B: t=1, U=8, mu=4), fermionic PEPS with sixteen
+          local states, D=4, chi=16, 1024 Metropolis chains, from the perturbed |I>.
 """
 from dataclasses import dataclass, field
 
@@ -43,6 +45,8 @@ WORKLOADS = {
                         n_steps=300),
     "direct6": Workload("direct6", L=6, D=2, chi=16, n_samples=30000, tau=0.02, n_steps=100,
                         extra={"exponent": 0.5, "b_d0": 1.0, "su_t": 0.0}),
+    "hubbard6": Workload("hubbard6", L=6, D=4, chi=16, n_samples=1024, tau=0.02, n_steps=100,
+                         extra={"t": 1.0, "U": 8.0, "mu": 4.0}),
 }
 
 
@@ -85,3 +89,10 @@ def random_configs(L1, L2, n, seed, diagonal_fraction=0.5):
     nd = int(round(diagonal_fraction * n))
     S[:nd] = 3 * rng.integers(0, 2, size=(nd, N), dtype=np.uint8)
     return S
+
+
+def fermion_support_configs(n, N, seed):
+    """n seeded configurations of N sixteen-valued sites with equal system and ancilla
+    occupations on every site (a | a << 2, a uniform in 0..3)."""
+    a = np.random.default_rng(seed).integers(0, 4, (n, N))
+    return (a | (a << 2)).astype(np.uint8)

@@ -121,3 +121,51 @@ def test_header_is_plain_c():
         if fn.endswith(".h"):
             subprocess.run([cc, "-fsyntax-only", "-x", "c", "-std=c99", "-Wall", "-Werror",
                             os.path.join(ROOT, "include", fn)], check=True)
+
+
+def test_fermion_calls_reject_a_null_evaluator_and_init_theta_is_the_identity():
+    # host-only: the fermionic calls refuse a null evaluator; the beta = 0 parameters equal
+    # the oracle's |I> (noise 0), and with noise the parity-even entries carry the oracle's
+    # own Philox draws, the parity-odd ones stay zero
+    import numpy as np
+    from oracle import fermion as fm
+    from oracle import philox
+    lib = binding.load()
+    assert lib.peps_famp_n_moves(None) == binding.PEPS_EINVAL
+    assert lib.peps_famp_sweep(None, None, 0, None, 0, 2, 1, 0, 0, None, None, None, None) == \
+        binding.PEPS_EINVAL
+    assert lib.peps_famp_sr_step(None, None, 0, None, 1, 1.0, 8.0, 4.0, 2, 0.01, 1e-4, 10,
+                                 1e-8, None) == binding.PEPS_EINVAL
+    assert lib.peps_famp_profile(None, 1) == binding.PEPS_EINVAL
+    assert lib.peps_famp_launches(None) == 0
+    L1, L2, D = 2, 3, 2
+    th = binding.famp_init_theta(L1, L2, D, noise=0.0, seed=3)
+    off = 0
+    for r in range(L1):
+        for c in range(L2):
+            dims = (1 if c == 0 else D, 1 if c == L2 - 1 else D, 1 if r == 0 else D, 1 if r == L1 - 1 else D)
+            A = th[off:off + 16 * int(np.prod(dims))].reshape((16,) + dims)
+            ref = np.zeros_like(A)
+            ref[(slice(None), 0, 0, 0, 0)] = fm.identity_fpeps(1, 1)[0][:, 0, 0, 0, 0]
+            assert np.array_equal(A, ref)
+            off += A.size
+    assert off == th.size
+    a = 1e-3
+    thn = binding.famp_init_theta(L1, L2, D, noise=a, seed=3)
+    off = 0
+    for i in range(L1 * L2):
+        r, c = divmod(i, L2)
+        dims = (1 if c == 0 else D, 1 if c == L2 - 1 else D, 1 if r == 0 else D, 1 if r == L1 - 1 else D)
+        A = thn[off:off + 16 * int(np.prod(dims))].reshape((16,) + dims)
+        for e, idx in enumerate(np.ndindex(*A.shape)):
+            par = (bin(idx[0]).count("1") + sum(idx[1:])) & 1
+            if par:
+                assert A[idx] == 0.0
+            elif all(x == 0 for x in idx[1:]) and (idx[0] & 3) == (idx[0] >> 2):
+                assert A[idx] == th[off + e]
+            else:
+                u = philox.uniform(3, i, e, 0, 0x46494E54)
+                assert A[idx] == pytest.approx(a * (2 * u - 1), rel=1e-15, abs=1e-300)
+        off += A.size
+    with pytest.raises(binding.PepsError):
+        binding.famp_init_theta(L1, L2, D, noise=-1.0)

@@ -325,3 +325,68 @@ def test_direct_run_prints_the_contract_line(monkeypatch, capsys):
     assert out["b_d"][0] == pytest.approx(b[1])
     assert out["e2e"]["h2d_bytes_per_step"] == 30000 * 36 * 8
     assert any(c[0] == "draw" and c[1] == (30000, 36) for c in calls)
+
+
+def test_fermion_run_prints_the_contract_line(monkeypatch, capsys):
+    # bench.py --fermion end to end on the CPU with a stand-in evaluator: a sweep and an SR
+    # step per timed step (p = 1 until beta_obs = 0.3, then 2), theta and the configurations
+    # carried between steps, the contraction's roofline on the tensor pipe
+    import numpy as np
+    bench = _bench()
+    from paper_2409_05285_gb300 import binding
+    calls = []
+
+    class FA:
+        def __init__(self, L1, L2, D, chi, n, precision=None, stream=None):
+            self.n, self.N, self.k = n, L1 * L2, 0
+            assert (L1, L2, D, chi, n) == (6, 6, 4, 16, 1024)
+
+        n_moves = 312
+
+        def sweep(self, theta, S, p=2, n_sweeps=1, seed=0, sweep0=0, u=None):
+            calls.append(("sweep", p, sweep0, n_sweeps))
+            self.k += 100
+            return S.copy(), np.ones(self.n, np.int32), np.zeros(self.n), np.ones(self.n, np.int8)
+
+        def sr_step(self, theta, S, t_hop, U, mu, p=2, **kw):
+            calls.append(("sr", p, (t_hop, U, mu)))
+            self.k += 30
+            return theta - 1e-3, {"E_site": -2.5, "E_err": 0.01, "docc": 0.2, "density": 1.0,
+                                  "cg_iters": 40, "cg_resid": 1e-8, "cg_maxit": False}
+
+        def profile(self, on):
+            pass
+
+        def profile_read(self):
+            return {"kb_gemm_tc": (500, 300.0, 500 * 2.0e7, 500 * 1.0e9), "k_fsum": (10, 5.0, 0.0, 0.0)}
+
+        def launches(self):
+            return self.k
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(binding, "FermionAmplitudes", FA)
+    monkeypatch.setattr(binding, "famp_init_theta", lambda L1, L2, D, noise, seed: np.zeros(16 * 100))
+    _stand_in_cuda(monkeypatch, bench, None, ["bench.py", "--fermion", "--steps", "2",
+                                              "--no-cpu-baseline"])
+    monkeypatch.setattr(bench, "l2_flusher", lambda stream: (lambda: calls.append(("flush",))))
+    bench.main()
+    out = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "roofline", "e2e", "gpu_launches", "clocks"):
+        assert key in out, key
+    assert "6x6 OBC Fermi-Hubbard t=1.0 U=8.0 mu=4.0" in out["config"]["workload"]
+    assert out["value"] == pytest.approx(1024 / (out["ms_per_step"] / 1e3))
+    assert out["roofline"]["kernel"] == "kb_gemm_tc" and out["roofline"]["bound"] == "tensor"
+    assert out["gpu_launches"] == 2 * 130
+    # burn-in (p = 1), three warm-up steps, two timed steps each after an L2 flush
+    sweeps = [c for c in calls if c[0] == "sweep"]
+    assert sweeps[0][1:] == (1, 0, 2)
+    assert [c[2] for c in sweeps[1:6]] == [2, 3, 4, 5, 6]
+    ps = [c[1] for c in calls if c[0] == "sr"]
+    assert ps[:4] == [1, 1, 1, 1] and ps[4] == 2
+    assert all(c[2] == (1.0, 8.0, 4.0) for c in calls if c[0] == "sr")
+    assert sum(1 for c in calls if c[0] == "flush") == 2
+    assert out["e2e"]["h2d_bytes_per_step"] == 2 * 1600 * 8 + 2 * 1024 * 36
