@@ -228,8 +228,9 @@ def tf32_peak(peaks):
 def kernel_roofline(kstats, peaks, prec, binding):
     """Roofline of the dominant kernel from the library's per-launch CUDA events (taken on an
     untimed step): achieved = algorithmic flops (tensor-core contractions) or bytes per launch /
-    mean launch time.  The tensor-core contraction is bounded by the tensor pipe (TF32 peak);
-    its HBM view (algorithmic bytes / time against the measured copy bandwidth) is given too."""
+    mean launch time.  The tensor-core contractions (register-staged and cp.async-pipelined)
+    are bounded by the tensor pipe (TF32 peak); their HBM view (algorithmic bytes / time
+    against the measured copy bandwidth) is given too."""
     total = sum(v[1] for v in kstats.values()) or 1.0
     kernels = {k: {"launches": v[0], "ms": round(v[1], 3), "share": round(v[1] / total, 4),
                    "GB_s": round(v[2] / (v[1] / 1e3) / 1e9, 1) if v[1] > 0 and v[2] > 0 else None,
@@ -240,7 +241,7 @@ def kernel_roofline(kstats, peaks, prec, binding):
     name, (n, ms, nbytes, flops) = max(kstats.items(), key=lambda kv: kv[1][1])
     hbm = peaks.get("hbm_gbs")
     hpeak, hsrc = (hbm, "measured") if hbm else (6800.0, "fallback")
-    if name == "kb_gemm_tc" and flops > 0:
+    if name in ("kb_gemm_tc", "kb_gemm_tc2") and flops > 0:
         peak, src = tf32_peak(peaks)
         achieved = flops / n / (ms / n / 1e3) / 1e12
         out = {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak,
