@@ -1975,8 +1975,9 @@ struct peps_famp {
   int* d_bad = nullptr;
   BatchImpl<double>* b64 = nullptr;
   BatchImpl<float>* b32 = nullptr;
-  // local energies: nearest-neighbour bonds, and the connected configurations of up to
-  // x_cap chains (eight hop slots per bond) with their coefficients and amplitudes
+  // local energies: nearest-neighbour bonds, and the configurations one allowed hop away
+  // (at most four per bond and chain, packed per chain at d_off) with their coefficients,
+  // slots and amplitudes
   int* d_bi = nullptr;
   int* d_bj = nullptr;
   int nbonds = 0;
@@ -1984,11 +1985,13 @@ struct peps_famp {
   uint8_t* d_Sx = nullptr;
   double *d_coef = nullptr, *d_lax = nullptr, *d_es = nullptr, *d_ea = nullptr;
   int8_t* d_sgx = nullptr;
+  int *d_cnt = nullptr, *d_off = nullptr, *d_slot = nullptr;
   void* d_O = nullptr;             // O rows of up to n_max configurations
   long long* d_ooff = nullptr;
   // sampling: the moves of one sweep, the proposed configurations and their amplitudes
   std::vector<FMove> moves;
-  uint8_t *d_Sp = nullptr, *d_skip = nullptr;
+  uint8_t *d_Sp = nullptr, *d_Sc = nullptr;
+  int *d_act = nullptr, *d_pos = nullptr;
   double *d_la2 = nullptr, *d_u = nullptr;
   int8_t* d_sg2 = nullptr;
   int* d_acc = nullptr;
@@ -2090,25 +2093,33 @@ int famp_energies(peps_famp* f, int nb, double t_hop, double U, double mu) {
     PV_CUDA(c, cudaMemcpy(f->d_bj, bj.data(), bj.size() * sizeof(int), cudaMemcpyHostToDevice));
     PV_TRY(dalloc(c, &f->d_es, (size_t)f->n_max * sizeof(double)));
     PV_TRY(dalloc(c, &f->d_ea, (size_t)f->n_max * sizeof(double)));
-  }
-  const int K = 8 * f->nbonds;
-  const long long nx = (long long)nb * K;
-  if (nx > f->x_cap) {
-    // the connected configurations of the largest batch so far (kept for later calls)
-    PV_TRY(dalloc(c, &f->d_Sx, (size_t)nx * N));
-    PV_TRY(dalloc(c, &f->d_coef, (size_t)nx * sizeof(double)));
-    PV_TRY(dalloc(c, &f->d_lax, (size_t)nx * sizeof(double)));
-    PV_TRY(dalloc(c, &f->d_sgx, (size_t)nx));
-    f->x_cap = nx;
+    PV_TRY(dalloc(c, &f->d_cnt, (size_t)f->n_max * sizeof(int)));
+    PV_TRY(dalloc(c, &f->d_off, (size_t)(f->n_max + 1) * sizeof(int)));
+    // at most one allowed hop per bond and mode: four per bond and chain
+    const long long cap = (long long)f->n_max * 4 * f->nbonds;
+    PV_TRY(dalloc(c, &f->d_Sx, (size_t)cap * N));
+    PV_TRY(dalloc(c, &f->d_coef, (size_t)cap * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_slot, (size_t)cap * sizeof(int)));
+    PV_TRY(dalloc(c, &f->d_lax, (size_t)cap * sizeof(double)));
+    PV_TRY(dalloc(c, &f->d_sgx, (size_t)cap));
+    f->x_cap = cap;
   }
   PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  const unsigned gb = (unsigned)((nb + 127) / 128);
+  PV_KLAUNCH(&c->kprof, st, "k_fhop_count", 0.0, 0.0,
+             k_fhop_count<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj, f->nbonds, f->d_cnt));
+  PV_KLAUNCH(&c->kprof, st, "k_fscan", 0.0, 0.0, k_fscan<<<1, 1024, 0, st>>>(nb, f->d_cnt, f->d_off));
   PV_KLAUNCH(&c->kprof, st, "k_fhops", 0.0, 0.0,
-             k_fhops<<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj,
-                                                                 f->nbonds, t_hop, f->d_Sx, f->d_coef));
+             k_fhops<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj, f->nbonds, t_hop, f->d_off,
+                                         f->d_Sx, f->d_coef, f->d_slot));
+  int nx = 0;
+  PV_CUDA(c, cudaMemcpyAsync(&nx, f->d_off + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
+  PV_CUDA(c, cudaStreamSynchronize(st));
+  if (nx < 0 || nx > f->x_cap) return fail(c, PEPS_ECUDA, "famp: hop count out of range");
   PV_TRY(famp_amplitudes(f, f->d_Sx, nx, f->d_lax, f->d_sgx, false));
   PV_KLAUNCH(&c->kprof, st, "k_fsum", 0.0, 0.0,
-             k_fsum<<<(nb + 127) / 128, 128, 0, st>>>(nb, N, K, f->d_S16, U, mu, f->d_coef, f->d_lax,
-                                                     f->d_sgx, f->d_la, f->d_sg, f->d_es, f->d_ea));
+             k_fsum<<<gb, 128, 0, st>>>(nb, N, f->d_S16, U, mu, f->d_off, f->d_coef, f->d_slot, f->d_lax,
+                                        f->d_sgx, f->d_la, f->d_sg, f->d_es, f->d_ea));
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
 }
@@ -2163,7 +2174,9 @@ int famp_sweep_buffers(peps_famp* f) {
   peps_ctx* c = f->c;
   const size_t n = (size_t)f->n_max;
   PV_TRY(dalloc(c, &f->d_Sp, n * c->N));
-  PV_TRY(dalloc(c, &f->d_skip, n));
+  PV_TRY(dalloc(c, &f->d_Sc, n * c->N));
+  PV_TRY(dalloc(c, &f->d_act, n * sizeof(int)));
+  PV_TRY(dalloc(c, &f->d_pos, (n + 1) * sizeof(int)));
   PV_TRY(dalloc(c, &f->d_la2, n * sizeof(double)));
   PV_TRY(dalloc(c, &f->d_sg2, n));
   PV_TRY(dalloc(c, &f->d_acc, n * sizeof(int)));
@@ -2370,13 +2383,23 @@ int peps_famp_sweep(peps_famp* f, const double* theta, size_t n_theta, uint8_t* 
   for (int k = 0; k < n_sweeps; ++k) {
     const double* uk = u ? f->d_u + (size_t)k * nb * M : nullptr;
     for (int m = 0; m < M; ++m) {
+      // the proposal per chain; only the chains where it applies are packed and contracted
       PV_KLAUNCH(&c->kprof, st, "k_fpropose", 0.0, 0.0,
-                 k_fpropose<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_Sp, f->moves[m], f->d_skip));
-      PV_TRY(famp_amplitudes(f, f->d_Sp, nb, f->d_la2, f->d_sg2, false));
+                 k_fpropose<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_Sp, f->moves[m], f->d_act));
+      PV_KLAUNCH(&c->kprof, st, "k_fscan", 0.0, 0.0, k_fscan<<<1, 1024, 0, st>>>(nb, f->d_act, f->d_pos));
+      int na = 0;
+      PV_CUDA(c, cudaMemcpyAsync(&na, f->d_pos + nb, sizeof(int), cudaMemcpyDeviceToHost, st));
+      PV_CUDA(c, cudaStreamSynchronize(st));
+      if (na < 0 || na > nb) return fail(c, PEPS_ECUDA, "famp_sweep: proposal count out of range");
+      if (na == 0) continue;
+      PV_KLAUNCH(&c->kprof, st, "k_fgather", 0.0, 0.0,
+                 k_fgather<<<(unsigned)(((long long)nb * N + 255) / 256), 256, 0, st>>>(
+                     nb, N, f->d_Sp, f->d_act, f->d_pos, f->d_Sc));
+      PV_TRY(famp_amplitudes(f, f->d_Sc, na, f->d_la2, f->d_sg2, false));
       PV_KLAUNCH(&c->kprof, st, "k_faccept", 0.0, 0.0,
                  k_faccept<<<gb, 128, 0, st>>>(nb, N, m, M, p, seed, (uint32_t)(sweep0 + k), uk,
-                                               f->d_skip, f->d_la2, f->d_sg2, f->d_S16, f->d_Sp,
-                                               f->d_la, f->d_sg, f->d_acc));
+                                               f->d_act, f->d_pos, f->d_la2, f->d_sg2, f->d_S16,
+                                               f->d_Sp, f->d_la, f->d_sg, f->d_acc));
     }
     PV_CUDA(c, cudaGetLastError());
   }

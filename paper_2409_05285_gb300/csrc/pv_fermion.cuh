@@ -160,47 +160,87 @@ __global__ void k_fapply(int n, const int8_t* __restrict__ csign, int8_t* __rest
   if (csign[s] == 0) la[s] = NAN;
 }
 
-// Local energies of the Hubbard terms of Eq. 14 on the system (layer 0) or ancilla (layer 1)
-// modes: for chain s and slot k = ((bond * 2 + spin) * 2 + direction) * 2 + layer, the
-// configuration reached by c+_a c_b (a, b the bond's sites in the slot's direction) and the
-// coefficient -t times its Jordan-Wigner sign (0 where the hop is blocked; the slot then
-// carries the configuration itself).  Modes are ordered site by site, c_up, c_dn, d_up,
-// d_dn within a site; a local index holds the site's four occupation bits.
+// Exclusive prefix sums of n counts (one block): out[i] = in[0] + ... + in[i-1], out[n] the
+// total.  Each thread sums a contiguous segment, the segment sums are scanned in shared
+// memory, then each thread writes its segment's prefixes (a fixed order).
+__global__ void k_fscan(int n, const int* __restrict__ in, int* __restrict__ out) {
+  __shared__ int part[1024];
+  const int T = blockDim.x, t = threadIdx.x;
+  const int seg = (n + T - 1) / T, i0 = min(n, t * seg), i1 = min(n, i0 + seg);
+  int sum = 0;
+  for (int i = i0; i < i1; ++i) sum += in[i];
+  part[t] = sum;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int k = 0; k < T; ++k) {
+      const int v = part[k];
+      part[k] = acc;
+      acc += v;
+    }
+    out[n] = acc;
+  }
+  __syncthreads();
+  int acc = part[t];
+  for (int i = i0; i < i1; ++i) {
+    out[i] = acc;
+    acc += in[i];
+  }
+}
+
+// Allowed hops of the Hubbard terms of Eq. 14 per chain: for every bond and mode (layer,
+// spin) exactly one direction is allowed where the two occupations differ, none otherwise.
+__global__ void k_fhop_count(int nb, int N, const uint8_t* __restrict__ S, const int* __restrict__ bi,
+                             const int* __restrict__ bj, int nbonds, int* __restrict__ cnt) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nb) return;
+  const uint8_t* x = S + (long long)s * N;
+  int c = 0;
+  for (int b = 0; b < nbonds; ++b) c += __popc((x[bi[b]] ^ x[bj[b]]) & 15);
+  cnt[s] = c;
+}
+
+// The configurations one allowed hop away (system: layer 0, ancilla: layer 1) written
+// compactly: chain s's hops at off[s], off[s] + 1, ..., in the order of the slots k = ((bond
+// * 2 + spin) * 2 + direction) * 2 + layer, each with the coefficient -t times its
+// Jordan-Wigner sign (c+_a c_b with a, b the bond's sites in the slot's direction; modes
+// ordered site by site, c_up c_dn d_up d_dn within a site) and its slot.
 __global__ void k_fhops(int nb, int N, const uint8_t* __restrict__ S, const int* __restrict__ bi,
                         const int* __restrict__ bj, int nbonds, double t_hop,
-                        uint8_t* __restrict__ Sx, double* __restrict__ coef) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int K = nbonds * 8;
-  if (q >= (long long)nb * K) return;
-  const int s = (int)(q / K), k = (int)(q % K);
-  const int layer = k & 1, dir = (k >> 1) & 1, spin = (k >> 2) & 1, bond = k >> 3;
-  const int a = dir ? bi[bond] : bj[bond], b = dir ? bj[bond] : bi[bond];   // c+_a c_b
+                        const int* __restrict__ off, uint8_t* __restrict__ Sx,
+                        double* __restrict__ coef, int* __restrict__ slot) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= nb) return;
   const uint8_t* x = S + (long long)s * N;
-  uint8_t* y = Sx + q * N;
-  for (int i = 0; i < N; ++i) y[i] = x[i];
-  const int bit = 1 << (2 * layer + spin);
-  double cf = 0.0;
-  if ((x[b] & bit) && !(x[a] & bit)) {
-    // occupied modes below mode m = 4 site + local bit position
-    auto below = [&](const uint8_t* z, int site, int pos) {
-      int cnt = 0;
-      for (int i = 0; i < site; ++i) cnt += __popc(z[i]);
-      return cnt + __popc(z[site] & ((1 << pos) - 1));
-    };
-    const int pos = 2 * layer + spin;
-    int e = below(x, b, pos);
-    y[b] = (uint8_t)(x[b] & ~bit);
-    e += below(y, a, pos);
+  // occupied modes below mode (site, pos) of configuration z
+  auto below = [&](const uint8_t* z, int site, int pos, int skip, uint8_t zskip) {
+    int cnt = 0;
+    for (int i = 0; i < site; ++i) cnt += __popc(i == skip ? zskip : z[i]);
+    return cnt + __popc((site == skip ? zskip : z[site]) & ((1 << pos) - 1));
+  };
+  long long e = off[s];
+  for (int k = 0; k < nbonds * 8; ++k) {
+    const int layer = k & 1, dir = (k >> 1) & 1, spin = (k >> 2) & 1, bond = k >> 3;
+    const int a = dir ? bi[bond] : bj[bond], b = dir ? bj[bond] : bi[bond];   // c+_a c_b
+    const int pos = 2 * layer + spin, bit = 1 << pos;
+    if (!(x[b] & bit) || (x[a] & bit)) continue;
+    const uint8_t xb = (uint8_t)(x[b] & ~bit);
+    const int js = below(x, b, pos, -1, 0) + below(x, a, pos, b, xb);
+    uint8_t* y = Sx + e * N;
+    for (int i = 0; i < N; ++i) y[i] = x[i];
+    y[b] = xb;
     y[a] = (uint8_t)(x[a] | bit);
-    cf = -t_hop * ((e & 1) ? -1.0 : 1.0);
+    coef[e] = -t_hop * ((js & 1) ? -1.0 : 1.0);
+    slot[e] = k;
+    ++e;
   }
-  coef[q] = cf;
 }
 
 // E_sys and E_anc per chain: the diagonal terms (U n_up n_dn - mu (n_up + n_dn) per site and
-// layer) plus sum_k coef_k psi(S_k) / psi(S) over the chain's slots of that layer.
-__global__ void k_fsum(int nb, int N, int K, const uint8_t* __restrict__ S, double U, double mu,
-                       const double* __restrict__ coef, const double* __restrict__ la_x,
+// layer) plus sum coef psi(S') / psi(S) over the chain's hops of that layer, in slot order.
+__global__ void k_fsum(int nb, int N, const uint8_t* __restrict__ S, double U, double mu,
+                       const int* __restrict__ off, const double* __restrict__ coef,
+                       const int* __restrict__ slot, const double* __restrict__ la_x,
                        const int8_t* __restrict__ sg_x, const double* __restrict__ la,
                        const int8_t* __restrict__ sg, double* __restrict__ es,
                        double* __restrict__ ea) {
@@ -218,11 +258,9 @@ __global__ void k_fsum(int nb, int N, int K, const uint8_t* __restrict__ S, doub
     ea[s] = NAN;
     return;
   }
-  for (int k = 0; k < K; ++k) {
-    const long long q = (long long)s * K + k;
-    const double c = coef[q];
-    if (c == 0.0 || sg_x[q] == 0) continue;
-    e[k & 1] += c * (double)(sg_x[q] * sg[s]) * exp(la_x[q] - la[s]);
+  for (int q = off[s]; q < off[s + 1]; ++q) {
+    if (sg_x[q] == 0) continue;
+    e[slot[q] & 1] += coef[q] * (double)(sg_x[q] * sg[s]) * exp(la_x[q] - la[s]);
   }
   es[s] = e[0];
   ea[s] = e[1];

@@ -36,9 +36,9 @@ struct FObs {
 
 #if defined(__CUDACC__)
 
-// Sp = S with move mv applied, per chain; skip = 1 where the move does not apply (Sp = S).
+// Sp = S with move mv applied, per chain; act = 1 where the move applies (else 0, Sp = S).
 __global__ void k_fpropose(int nb, int N, const uint8_t* __restrict__ S, uint8_t* __restrict__ Sp,
-                           FMove mv, uint8_t* __restrict__ skip) {
+                           FMove mv, int* __restrict__ act) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= nb) return;
   const uint8_t* x = S + (long long)s * N;
@@ -55,26 +55,39 @@ __global__ void k_fpropose(int nb, int N, const uint8_t* __restrict__ S, uint8_t
       y[mv.j] = (uint8_t)(x[mv.j] ^ (1 << mv.k));
     }
   }
-  skip[s] = (uint8_t)!ok;
+  act[s] = ok;
 }
 
-// The decision on move m for every chain, target |psi|^p: accept iff log u < p (log|psi'| -
-// log|psi|) in float64, psi' = 0 rejected.  u from the caller ([chain][move]) or from
-// Philox4x32-10 (seed; counter chain, sweep, m, TAG_FMC).
+// The proposed rows of the chains where the move applies, packed: row s to position pos[s].
+__global__ void k_fgather(int nb, int N, const uint8_t* __restrict__ Sp, const int* __restrict__ act,
+                          const int* __restrict__ pos, uint8_t* __restrict__ Sc) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nb * N) return;
+  const int s = (int)(e / N), q = (int)(e % N);
+  if (act[s]) Sc[(long long)pos[s] * N + q] = Sp[e];
+}
+
+// The decision on move m for every chain where it applies, target |psi|^p: accept iff log u <
+// p (log|psi'| - log|psi|) in float64, psi' = 0 rejected; psi' of chain s at the packed
+// position pos[s].  u from the caller ([chain][move]) or from Philox4x32-10 (seed; counter
+// chain, sweep, m, TAG_FMC).
 __global__ void k_faccept(int nb, int N, int m, int n_moves, int p, uint64_t seed, uint32_t sweep,
-                          const double* __restrict__ u, const uint8_t* __restrict__ skip,
-                          const double* __restrict__ la2, const int8_t* __restrict__ sg2,
-                          uint8_t* __restrict__ S, const uint8_t* __restrict__ Sp,
-                          double* __restrict__ la, int8_t* __restrict__ sg, int* __restrict__ acc) {
+                          const double* __restrict__ u, const int* __restrict__ act,
+                          const int* __restrict__ pos, const double* __restrict__ la2,
+                          const int8_t* __restrict__ sg2, uint8_t* __restrict__ S,
+                          const uint8_t* __restrict__ Sp, double* __restrict__ la,
+                          int8_t* __restrict__ sg, int* __restrict__ acc) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= nb || skip[s] || sg2[s] == 0) return;
+  if (s >= nb || !act[s]) return;
+  const int c = pos[s];
+  if (sg2[c] == 0) return;
   const double us = u ? u[(long long)s * n_moves + m]
                       : philox_uniform(seed, (uint32_t)s, sweep, (uint32_t)m, TAG_FMC);
-  const double d = log(us) - p * (la2[s] - la[s]);
+  const double d = log(us) - p * (la2[c] - la[s]);
   if (d < 0.0) {
     for (int q = 0; q < N; ++q) S[(long long)s * N + q] = Sp[(long long)s * N + q];
-    la[s] = la2[s];
-    sg[s] = sg2[s];
+    la[s] = la2[c];
+    sg[s] = sg2[c];
     acc[s] += 1;
   }
 }
