@@ -1063,6 +1063,8 @@ def run_fermion(args):
     if ws > 1:
         torch.distributed.barrier()
     wl = WORKLOADS[args.workload if args.workload != "heis8" else "hubbard6"]
+    if "U" not in wl.extra:
+        raise SystemExit("--fermion needs a Hubbard workload (hubbard6, hubbard8), not " + wl.name)
     prec = {"fp32": binding.PEPS_FP32, "tf32": binding.PEPS_TF32, "fp64": binding.PEPS_FP64}[args.precision]
     stream = torch.cuda.Stream()
     n = args.chains or wl.n_samples

@@ -200,7 +200,8 @@ int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_thet
  * amplitude is a full contraction.  S: host [nb][L1*L2], in (entries 0..15, EINVAL
  * otherwise) and out; accepted (per chain, summed over the sweeps), log_abs and sign of the
  * final configurations: host, NULL to skip.  EINVAL for p outside {1, 2}, negative
- * n_sweeps or sweep counters beyond 32 bits. */
+ * n_sweeps or sweep counters beyond 32 bits.  peps_famp_n_moves returns 2 N + 4 (bonds), or
+ * PEPS_EINVAL for a null evaluator. */
 int peps_famp_n_moves(const peps_famp* famp);
 int peps_famp_sweep(peps_famp* famp, const double* theta, size_t n_theta, uint8_t* S, int nb, int p,
                     int n_sweeps, uint64_t seed, uint64_t sweep0, const double* u, int* accepted,

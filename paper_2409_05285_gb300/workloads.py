@@ -13,6 +13,8 @@ Workloads (the paper's benchmark shapes, Sec. III.A; no dataset is involved):
           runs, Sec. III.B, on the spin model), from the perturbed beta=0 state, b_d from 1.
   hubbard6 6x6 open Fermi-Hubbard (Sec. III.B: t=1, U=8, mu=4), fermionic PEPS with sixteen
           local states, D=4, chi=16, 1024 Metropolis chains, from the perturbed |I>.
+  hubbard8 8x8 open Fermi-Hubbard at half filling (t=1, U=8, mu=4), D=6, chi=24, 8192
+          samples per SR step, tau=0.01 (bench.py --fermion --workload hubbard8).
 """
 from dataclasses import dataclass, field
 
@@ -46,6 +48,8 @@ WORKLOADS = {
     "direct6": Workload("direct6", L=6, D=2, chi=16, n_samples=30000, tau=0.02, n_steps=100,
                         extra={"exponent": 0.5, "b_d0": 1.0, "su_t": 0.0}),
     "hubbard6": Workload("hubbard6", L=6, D=4, chi=16, n_samples=1024, tau=0.02, n_steps=100,
+                         extra={"t": 1.0, "U": 8.0, "mu": 4.0}),
+    "hubbard8": Workload("hubbard8", L=8, D=6, chi=24, n_samples=8192, tau=0.01, n_steps=200,
                          extra={"t": 1.0, "U": 8.0, "mu": 4.0}),
 }
 
