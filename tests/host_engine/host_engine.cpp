@@ -9,12 +9,14 @@
 //
 // Usage: host_engine <in.bin> <out.bin>
 //   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw, 3 eval with the
-//        compression's right factors from Gram matrices), L1, L2, D, chi, n, p;
+//        compression's right factors from Gram matrices, 4 plain amplitude and O rows of a
+//        PEPS of 32 slices per site, the fermionic engine's form), L1, L2, D, chi, n, p;
 //        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
 //        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
 //        mc:   uint8 S[n][N], int32 acc[n], int32 prop[n]
 //        draw: uint8 S[n][N], float64 log_q[n]  (direct sampling, pv_direct.cuh)
+//        mode 4: float64 log_abs[n], int8 sign[n], O[n][N_o]  (pv_fermion.cuh)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -22,6 +24,7 @@
 #include <vector>
 
 #include "pv_direct.cuh"
+#include "pv_fermion.cuh"
 
 using namespace pv;
 using T = double;
@@ -160,11 +163,12 @@ int main(int argc, char** argv) {
   rd(fi, &sweep, 1);
   const int N = L1 * L2;
   std::vector<long long> toff(N + 1, 0), ooff(N + 1, 0);
+  const int slices = mode == 4 ? 32 : 4;
   for (int i = 0; i < N; ++i) {
     const int r = i / L2, c = i % L2;
     const long long sz = (long long)(c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
                          (r == L1 - 1 ? 1 : D);
-    toff[i + 1] = toff[i] + 4 * sz;
+    toff[i + 1] = toff[i] + slices * sz;
     ooff[i + 1] = ooff[i] + sz;
   }
   std::vector<T> theta((size_t)toff[N]);
@@ -234,7 +238,17 @@ int main(int argc, char** argv) {
 
   FILE* fo = std::fopen(argv[2], "wb");
   if (!fo) return 2;
-  if (mode == 0 || mode == 3) {
+  if (mode == 4) {
+    const long long No = ooff[N];
+    std::vector<double> la(n);
+    std::vector<int8_t> sg(n);
+    std::vector<T> O((size_t)n * No);
+    plain_amplitude(run, S.data(), n, la.data(), sg.data());
+    plain_log_derivative(run, S.data(), n, O.data(), No);
+    std::fwrite(la.data(), 8, n, fo);
+    std::fwrite(sg.data(), 1, n, fo);
+    std::fwrite(O.data(), 8, O.size(), fo);
+  } else if (mode == 0 || mode == 3) {
     const long long No = ooff[N];
     std::vector<double> la(n), es(n), ea(n);
     std::vector<int8_t> sg(n);

@@ -40,6 +40,11 @@ def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
         f.write(np.asarray(S, dtype=np.uint8).tobytes())
     subprocess.run([exe, fin, fout], check=True)
     raw = open(fout, "rb").read()
+    if mode == 4:
+        la = np.frombuffer(raw, np.float64, n, 0)
+        sg = np.frombuffer(raw, np.int8, n, 8 * n)
+        O = np.frombuffer(raw, np.float64, n * lat.No, 9 * n).reshape(n, lat.No)
+        return la, sg, O
     if mode in (0, 3):
         o = 0
         la = np.frombuffer(raw, np.float64, n, o); o += 8 * n
@@ -170,3 +175,39 @@ def test_host_engine_gram_path_matches_oracle(engine, tmp_path, case):
         assert abs(es[k] - r['e_sys']) <= 1e-8 * scale
         assert abs(ea[k] - r['e_anc']) <= 1e-8 * scale
         assert np.max(np.abs(O[k] - r['O'])) <= 1e-7 * max(1.0, np.max(np.abs(r['O'])))
+
+
+@pytest.mark.parametrize("case", [(2, 2, 3, 9, 4), (2, 3, 3, 9, 3), (3, 3, 2, 8, 3)])
+def test_host_engine_fermion_plain_contraction_matches_oracle(engine, tmp_path, case):
+    # the fermionic engine's form (pv_fermion.cuh, Fig. 1b): the plain boundary-MPS
+    # contraction of the 32 signed slices per site at the extended indices S_i + 16 b_i, times
+    # the configuration sign, is the fermionic amplitude; its plain O rows times each entry's
+    # slice sign are the fermionic O.  Against the oracle's sums over every virtual assignment
+    # at exact chi.
+    from oracle import fermion as fm
+    L1, L2, D, chi, n = case
+    N = L1 * L2
+    rng = np.random.default_rng(100 * L1 + 10 * L2 + D)
+    T = fm.random_even_fpeps(L1, L2, D, rng, scale=0.7)
+    th32 = np.concatenate([A.ravel() for A in fm.fpeps_signed_slices(T)])
+    signs = fm.fpeps_signed_slices([np.ones_like(A) for A in T])
+    S = rng.integers(0, 16, (n, N))
+    for k in range(n):
+        if sum(bin(int(x)).count("1") for x in S[k]) % 2:
+            S[k, 0] ^= 1
+    S32 = np.array([[int(S[k, i]) + 16 * b for i, b in enumerate(fm.fpeps_row_prefix_bits(L1, L2, S[k]))]
+                    for k in range(n)], dtype=np.uint8)
+    lat = Lattice(L1, L2, D)
+    la, sg, O = _run(engine, tmp_path, 4, lat, chi, th32, S32)
+    for k in range(n):
+        grads, psi = fm.fpeps_log_derivative(L1, L2, T, S[k])
+        assert psi == pytest.approx(fm.fpeps_amplitude_brute(L1, L2, T, S[k]), rel=1e-12)
+        assert sg[k] * fm.fpeps_config_sign(L1, L2, S[k]) == np.sign(psi), k
+        assert abs(la[k] - np.log(abs(psi))) <= 1e-10, k
+        o = 0
+        scale = max(1.0, max(np.max(np.abs(g)) for g in grads))
+        for i in range(N):
+            sz = grads[i].size
+            plain = O[k, o:o + sz] * signs[i][S32[k, i]].ravel()
+            assert np.max(np.abs(plain - grads[i].ravel())) <= 1e-9 * scale, (k, i)
+            o += sz
