@@ -34,6 +34,7 @@ Readings (the paper states neither the moves nor the observables' estimators for
 import numpy as np
 
 from . import fermion as fm
+from . import observables as obs_mod
 from . import philox
 from . import sr as sr_mod
 
@@ -184,7 +185,7 @@ def observables(N, S_batch, w, es, ea):
     """E/N, its standard error, the double occupancy and the density per site."""
     h = 0.5 * (np.asarray(es) + np.asarray(ea))
     H1 = float(w @ h)
-    err = float(np.sqrt(np.sum(w * w * (h - H1) ** 2)))
+    err = obs_mod.standard_error(w, h)
     docc = np.zeros(len(S_batch))
     dens = np.zeros(len(S_batch))
     for n, S in enumerate(S_batch):
