@@ -203,6 +203,11 @@ int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_thet
  * n_sweeps or sweep counters beyond 32 bits.  peps_famp_n_moves returns 2 N + 4 (bonds), or
  * PEPS_EINVAL for a null evaluator. */
 int peps_famp_n_moves(const peps_famp* famp);
+/* The moves of one sweep on an L1 x L2 lattice in the order above, four ints per move: kind
+ * (0 pair, 1 hop), site i, site j (= i for a pair), spin (pair) or mode (hop); the first cap
+ * moves are written to table (host).  Returns the number of moves, or PEPS_EINVAL.  Host
+ * code. */
+int peps_famp_move_table(int L1, int L2, int* table, int cap);
 int peps_famp_sweep(peps_famp* famp, const double* theta, size_t n_theta, uint8_t* S, int nb, int p,
                     int n_sweeps, uint64_t seed, uint64_t sweep0, const double* u, int* accepted,
                     double* log_abs, int8_t* sign);

@@ -45,6 +45,7 @@ EXPORTS = [
     "peps_famp_free", "peps_famp_local_energy", "peps_famp_log_derivative",
     "peps_famp_n_moves", "peps_famp_sweep", "peps_famp_sr_step", "peps_famp_profile",
     "peps_famp_profile_read", "peps_famp_launches", "peps_famp_init_theta",
+    "peps_famp_move_table",
 ]
 
 
@@ -163,6 +164,7 @@ def load(path=None):
     lib.peps_famp_launches.argtypes = [vp]
     lib.peps_famp_launches.restype = ctypes.c_longlong
     lib.peps_famp_init_theta.argtypes = [ip, ip, ip, dp, ctypes.c_uint64, vp, ctypes.c_size_t]
+    lib.peps_famp_move_table.argtypes = [ip, ip, vp, ip]
     lib.peps_famp_sweep.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, ip, ip, ctypes.c_uint64,
                                     ctypes.c_uint64, vp, vp, vp, vp]
     lib.peps_famp_sr_step.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, ip, dp, dp, ip,
@@ -633,6 +635,18 @@ def famp_init_theta(L1, L2, D, noise=1e-3, seed=0):
     if rc != PEPS_OK:
         raise PepsError(rc, "peps_famp_init_theta failed")
     return th
+
+
+def famp_move_table(L1, L2):
+    """The moves of one fermionic sweep, [n_moves][4] (kind, i, j, spin or mode)
+    (peps_famp_move_table)."""
+    lib = load()
+    n = lib.peps_famp_move_table(int(L1), int(L2), None, 0)
+    if n < 0:
+        raise PepsError(n, "peps_famp_move_table failed")
+    t = np.empty((n, 4), np.int32)
+    lib.peps_famp_move_table(int(L1), int(L2), _ptr(t), n)
+    return t
 
 
 def direct_next_bd(b_d, diag_frac, N):

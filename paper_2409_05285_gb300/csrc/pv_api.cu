@@ -2248,17 +2248,7 @@ int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, v
   }
   c->No = c->ooff[N];
   f->n16 = f->toff16[N];
-  // the moves of one sweep: pairs per site and spin, then hops per bond and mode (the
-  // horizontal bond of a site before its vertical one)
-  for (int i = 0; i < N; ++i)
-    for (int sp = 0; sp < 2; ++sp) f->moves.push_back(FMove{0, i, i, sp});
-  for (int i = 0; i < N; ++i) {
-    const int r = i / L2, q = i % L2;
-    if (q + 1 < L2)
-      for (int k = 0; k < 4; ++k) f->moves.push_back(FMove{1, i, i + 1, k});
-    if (r + 1 < L1)
-      for (int k = 0; k < 4; ++k) f->moves.push_back(FMove{1, i, i + L2, k});
-  }
+  f->moves = fermion_moves(L1, L2);
   const size_t real = precision == PEPS_FP64 ? sizeof(double) : sizeof(float);
   auto bail = [&](int rc) {
     peps_free(c);
@@ -2535,6 +2525,18 @@ int peps_famp_profile_read(peps_famp* f, peps_kernel_stat* out, int cap, int* n_
 }
 
 long long peps_famp_launches(const peps_famp* f) { return f && f->c ? f->c->kprof.launches : 0; }
+
+int peps_famp_move_table(int L1, int L2, int* table, int cap) {
+  if (L1 < 1 || L2 < 1 || L1 > MAX_L || L2 > MAX_L || cap < 0 || (cap > 0 && !table)) return PEPS_EINVAL;
+  const std::vector<FMove> mv = fermion_moves(L1, L2);
+  for (int m = 0; m < (int)mv.size() && m < cap; ++m) {
+    table[4 * m] = mv[m].kind;
+    table[4 * m + 1] = mv[m].i;
+    table[4 * m + 2] = mv[m].j;
+    table[4 * m + 3] = mv[m].k;
+  }
+  return (int)mv.size();
+}
 
 int peps_famp_init_theta(int L1, int L2, int D, double noise, uint64_t seed, double* theta,
                          size_t n_theta) {

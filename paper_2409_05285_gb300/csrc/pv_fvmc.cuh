@@ -13,6 +13,7 @@
 #ifndef PV_FVMC_CUH
 #define PV_FVMC_CUH
 #include <cstdint>
+#include <vector>
 
 #include "pv_philox.cuh"
 #include "pv_sr.cuh"
@@ -25,6 +26,23 @@ constexpr uint32_t TAG_FMC = 0x464D4331u;   // fermionic Metropolis acceptance u
 struct FMove {
   int kind, i, j, k;
 };
+
+// The moves of one sweep in order: pairs per site (row-major) and spin, then hops per bond
+// (a site's horizontal bond before its vertical one) and mode.
+inline std::vector<FMove> fermion_moves(int L1, int L2) {
+  std::vector<FMove> out;
+  const int N = L1 * L2;
+  for (int i = 0; i < N; ++i)
+    for (int sp = 0; sp < 2; ++sp) out.push_back(FMove{0, i, i, sp});
+  for (int i = 0; i < N; ++i) {
+    const int r = i / L2, q = i % L2;
+    if (q + 1 < L2)
+      for (int k = 0; k < 4; ++k) out.push_back(FMove{1, i, i + 1, k});
+    if (r + 1 < L1)
+      for (int k = 0; k < 4; ++k) out.push_back(FMove{1, i, i + L2, k});
+  }
+  return out;
+}
 
 // Observables of the samples: <H> per lattice (Eq. 11), its standard error, the double
 // occupancy and the density summed over the sites (both layers averaged), and the number

@@ -169,3 +169,15 @@ def test_fermion_calls_reject_a_null_evaluator_and_init_theta_is_the_identity():
         off += A.size
     with pytest.raises(binding.PepsError):
         binding.famp_init_theta(L1, L2, D, noise=-1.0)
+
+
+def test_fermion_move_table_is_the_oracle_sweep_order():
+    # host-only: the device sweep's proposals, in order, are the oracle's (pairs per site and
+    # spin, then hops per bond and mode)
+    from oracle import fermion_vmc as fv
+    for L1, L2 in ((2, 2), (2, 3), (3, 2), (4, 5), (6, 6)):
+        t = binding.famp_move_table(L1, L2)
+        ref = [(0, m[1], m[1], m[2]) if m[0] == "pair" else (1, m[1], m[2], m[3])
+               for m in fv.moves(L1, L2)]
+        assert [tuple(int(x) for x in row) for row in t] == ref, (L1, L2)
+    assert binding.load().peps_famp_move_table(0, 2, None, 0) == binding.PEPS_EINVAL
