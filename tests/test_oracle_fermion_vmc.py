@@ -227,3 +227,41 @@ def test_sr_dynamics_follow_exact_evolution_of_the_dimer():
     e1 = _dimer_run(0.01, 0.12)
     assert abs(e1) < 0.6 * abs(e2)
     assert abs(e2) < 0.06 and abs(e1) < 0.03
+
+
+def test_vertical_hop_flips_reduce_to_one_right_leg_parity():
+    # a vertical hop at column c flips the row-prefix bit b of every site right of c in both
+    # rows; the plain contraction of the signed slices then equals the one with the old bits
+    # and a parity operator on the right leg of the lower hop site, times the sign of the
+    # lower row's physical parities right of c (the property a cached-strip sweep relies on)
+    rng = np.random.default_rng(5)
+    L1, L2, D = 3, 4, 2
+    T = fm.random_even_fpeps(L1, L2, D, rng)
+    Ts = fm.fpeps_signed_slices(T)
+
+    def plain(S32, twist=None):
+        t = []
+        for i in range(L1 * L2):
+            A = Ts[i][S32[i]].copy()
+            if i == twist:
+                A[:, 1::2, :, :] *= -1.0          # parity of the right leg (odd indices)
+            t.append(A)
+        return fm.plain_amplitude(L1, L2, t)
+
+    n = 0
+    while n < 40:
+        S = [int(x) for x in rng.integers(0, 16, L1 * L2)]
+        if sum(bin(x).count("1") for x in S) % 2:
+            S[0] ^= 1
+        r, c, k = int(rng.integers(0, L1 - 1)), int(rng.integers(0, L2)), int(rng.integers(0, 4))
+        i, j = r * L2 + c, (r + 1) * L2 + c
+        S2 = fv.propose(S, ("hop", i, j, k))
+        if S2 is None:
+            continue
+        b_new = fm.fpeps_row_prefix_bits(L1, L2, S2)
+        b_old = fm.fpeps_row_prefix_bits(L1, L2, S)
+        true = plain([S2[q] + 16 * b_new[q] for q in range(L1 * L2)])
+        alt = plain([S2[q] + 16 * b_old[q] for q in range(L1 * L2)], twist=j if c + 1 < L2 else None)
+        sgn = (-1) ** sum(bin(S2[(r + 1) * L2 + cc]).count("1") for cc in range(c + 1, L2))
+        assert true == pytest.approx(sgn * alt, rel=1e-10, abs=1e-14)
+        n += 1
