@@ -188,12 +188,13 @@ int peps_famp_local_energy(peps_famp* famp, const double* theta, size_t n_theta,
 int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_theta,
                              const uint8_t* S, int nb, void* O);
 /* Metropolis sampling of the fermionic PEPS (Sec. II, MCMC; target |psi|^p, p = 2, or p = 1
- * with the reweighting of Eq. A1).  One sweep proposes, in order: for every site (row-major)
- * and spin s (up, then down), where c_s and d_s are equally occupied, both toggled (a
- * system-ancilla pair created or removed); then for every nearest-neighbour bond (row-major,
- * a site's horizontal bond before its vertical one) and mode k = 0..3 (c_up, c_dn, d_up,
- * d_dn), one electron of mode k hopping across the bond, where the two occupations differ.
- * A move that does not apply is skipped.  Move m (0 <= m < peps_famp_n_moves) of sweep k
+ * with the reweighting of Eq. A1).  Proposals: a pair at site i and spin s (up, then down),
+ * where c_s and d_s are equally occupied, both toggled (a system-ancilla pair created or
+ * removed); a hop across a nearest-neighbour bond for mode k = 0..3 (c_up, c_dn, d_up, d_dn),
+ * one electron of mode k moving where the two occupations differ.  One sweep visits the rows
+ * top to bottom: in row r, for every column the pairs of its site and the hops of its
+ * horizontal bond, then the hops of the vertical bonds to row r+1, column by column.  A move
+ * that does not apply is skipped.  Move m (0 <= m < peps_famp_n_moves) of sweep k
  * of chain c is accepted iff log u < p (log|psi'| - log|psi|) (float64; psi' = 0 rejected)
  * with u = u[k][c][m] (host, [n_sweeps][nb][n_moves], values in (0, 1)) or, for u = NULL,
  * Philox4x32-10 with key seed and counter (c, sweep0 + k, m, 0x464D4331).  Every proposal's

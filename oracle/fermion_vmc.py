@@ -7,13 +7,16 @@ log-derivatives come from oracle/fermion.py; the SR algebra from oracle/sr.py.
 
 Readings (the paper states neither the moves nor the observables' estimators for fermions):
   * Moves.  A configuration holds sixteen-valued local indices S_i (bits: c_up, c_dn, d_up,
-    d_dn).  One sweep proposes, in this order,
-      (i)  for every site in row-major order and each spin s (up, then down), where c_s and
-           d_s are equally occupied, toggling both (a system-ancilla pair created or removed:
+    d_dn).  Two kinds of proposal:
+      (i)  pair: at site i and spin s (up, then down), where c_s and d_s are equally
+           occupied, toggling both (a system-ancilla pair created or removed:
            S_i ^= 0b101 << s);
-      (ii) for every nearest-neighbour bond in the order of fermion.fpeps_bonds and each mode
-           k = 0..3 (c_up, c_dn, d_up, d_dn), exchanging the occupations of mode k at the two
-           sites (one electron hops).
+      (ii) hop: across a nearest-neighbour bond (i, j) and for mode k = 0..3 (c_up, c_dn,
+           d_up, d_dn), exchanging the occupations of mode k at the two sites (one electron
+           hops).
+    One sweep visits the rows top to bottom: in row r, for every column c the pairs of site
+    (r, c) and then the hops of its horizontal bond to (r, c+1); then, for every column, the
+    hops of the vertical bond from (r, c) to (r+1, c) (the order of a sweep over row strips).
     A proposal whose condition fails (c_s != d_s in (i), equal occupations in (ii)) is
     skipped, its uniform unused.  Every move keeps the total parity even (a PEPS of even
     tensors vanishes elsewhere) and is its own inverse where it applies, so proposals are
@@ -44,10 +47,19 @@ TAG_FMC = 0x464D4331   # fermionic Metropolis acceptance uniforms
 # ---------------------------------------------------------------- moves and the sweep
 
 def moves(nrow, ncol):
-    """The proposals of one sweep in order: ('pair', i, s) then ('hop', i, j, k)."""
-    out = [("pair", i, s) for i in range(nrow * ncol) for s in (0, 1)]
-    for (i, j, _) in fm.fpeps_bonds(nrow, ncol):
-        out.extend(("hop", i, j, k) for k in range(4))
+    """The proposals of one sweep in order: per row, ('pair', i, s) and the horizontal
+    ('hop', i, i + 1, k) column by column, then the vertical ('hop', i, i + ncol, k)."""
+    out = []
+    for r in range(nrow):
+        for c in range(ncol):
+            i = r * ncol + c
+            out.extend(("pair", i, s) for s in (0, 1))
+            if c + 1 < ncol:
+                out.extend(("hop", i, i + 1, k) for k in range(4))
+        if r + 1 < nrow:
+            for c in range(ncol):
+                i = r * ncol + c
+                out.extend(("hop", i, i + ncol, k) for k in range(4))
     return out
 
 

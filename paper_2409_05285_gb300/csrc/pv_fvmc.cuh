@@ -4,11 +4,11 @@
 // column sums of O rows over sixteen local states.  The CG kernels of pv_sr.cuh serve
 // unchanged: they address theta through the slice S_ij times the slice size.
 //
-// Moves of one sweep, in order: for every site (row-major) and spin s, the system-ancilla
-// pair of spin s created or removed (only where c_s and d_s are equally occupied); for every
-// nearest-neighbour bond (row-major, the horizontal bond of a site before its vertical one)
-// and mode k = 0..3, one electron of mode k hopping across the bond (only where the two
-// occupations differ).  A move that does not apply is skipped.  Both kinds keep the total
+// Moves of one sweep (fermion_moves, in row phases): per row, for every column the
+// system-ancilla pairs of its site created or removed (spin up, then down; only where c_s and
+// d_s are equally occupied) and one electron of mode k = 0..3 hopping across its horizontal
+// bond (only where the two occupations differ); then the hops across the vertical bonds to
+// the next row, column by column.  A move that does not apply is skipped.  Both kinds keep the total
 // parity even and N_s(c) - N_s(d) fixed, and each is its own inverse (symmetric proposals).
 #ifndef PV_FVMC_CUH
 #define PV_FVMC_CUH
@@ -27,19 +27,21 @@ struct FMove {
   int kind, i, j, k;
 };
 
-// The moves of one sweep in order: pairs per site (row-major) and spin, then hops per bond
-// (a site's horizontal bond before its vertical one) and mode.
+// The moves of one sweep in order: per row, for every column the pairs of its site (spin up,
+// then down) and the hops of its horizontal bond (modes 0..3); then the hops of the vertical
+// bonds to the next row, column by column.
 inline std::vector<FMove> fermion_moves(int L1, int L2) {
   std::vector<FMove> out;
-  const int N = L1 * L2;
-  for (int i = 0; i < N; ++i)
-    for (int sp = 0; sp < 2; ++sp) out.push_back(FMove{0, i, i, sp});
-  for (int i = 0; i < N; ++i) {
-    const int r = i / L2, q = i % L2;
-    if (q + 1 < L2)
-      for (int k = 0; k < 4; ++k) out.push_back(FMove{1, i, i + 1, k});
+  for (int r = 0; r < L1; ++r) {
+    for (int q = 0; q < L2; ++q) {
+      const int i = r * L2 + q;
+      for (int sp = 0; sp < 2; ++sp) out.push_back(FMove{0, i, i, sp});
+      if (q + 1 < L2)
+        for (int k = 0; k < 4; ++k) out.push_back(FMove{1, i, i + 1, k});
+    }
     if (r + 1 < L1)
-      for (int k = 0; k < 4; ++k) out.push_back(FMove{1, i, i + L2, k});
+      for (int q = 0; q < L2; ++q)
+        for (int k = 0; k < 4; ++k) out.push_back(FMove{1, r * L2 + q, (r + 1) * L2 + q, k});
   }
   return out;
 }

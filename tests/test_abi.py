@@ -172,8 +172,8 @@ def test_fermion_calls_reject_a_null_evaluator_and_init_theta_is_the_identity():
 
 
 def test_fermion_move_table_is_the_oracle_sweep_order():
-    # host-only: the device sweep's proposals, in order, are the oracle's (pairs per site and
-    # spin, then hops per bond and mode)
+    # host-only: the device sweep's proposals, in order, are the oracle's (row phases: a row's
+    # pairs and horizontal hops column by column, then its vertical hops)
     from oracle import fermion_vmc as fv
     for L1, L2 in ((2, 2), (2, 3), (3, 2), (4, 5), (6, 6)):
         t = binding.famp_move_table(L1, L2)
