@@ -62,6 +62,204 @@ void plain_log_derivative(BatchRunner<T, BE, OT>& run, const uint8_t* S, int n, 
   }
 }
 
+// ---------------------------------------------------------------- Metropolis on cached strips
+//
+// One sweep in the row phases of fermion_moves (Sec. II, MCMC; target |psi|^p) with the
+// proposals' amplitudes from one- and two-row strips between cached environments, as the
+// spin sweep does, instead of a contraction of the whole lattice per proposal.  The site
+// tensors carry 64 slices: S + 16 b (the signed slices) and S + 16 b + 32 (the same with a
+// parity (-1)^(p(r)) on the right leg).  A pair keeps its site's parity; a horizontal hop (c,
+// c+1) flips b of c+1 only; so the one-row strips of a row carry over with the actual bits.  A
+// vertical hop at column c flips b of every site right of c in both rows, which equals a
+// parity on the right leg of (r+1, c) times a sign (the right-leg parity of the lower site):
+// the two-row phase keeps the bits of its start for the columns ahead, and an accepted hop
+// carries the parity in its lower site's slice.  Only |psi'/psi| enters the decision, so the
+// signs drop out.  S32 holds every chain's current slice indices; FConf resets them to the
+// actual bits.
+
+// Applies a per-chain functor to chains 0..n-1 on a back end that runs plain host loops (a
+// device back end needs its own launch of the functor).
+template <typename BE, typename F>
+inline void fv_apply(BE& be, const F& f, int n) {
+  static_assert(BE::host_loops, "fv_apply: this back end needs its own launch");
+  (void)be;
+  for (int s = 0; s < n; ++s) f(s);
+}
+
+PV_HD int fv_parity4(int v) { return (v ^ (v >> 1) ^ (v >> 2) ^ (v >> 3)) & 1; }
+
+// S32 = S + 16 b with b the parity of the physical indices left of each site in its row.
+struct FConf {
+  const uint8_t* S16;
+  uint8_t* S32;
+  int L1, L2;
+  PV_HD void operator()(int s) const {
+    const long long N = (long long)L1 * L2;
+    for (int r = 0; r < L1; ++r) {
+      int b = 0;
+      for (int c = 0; c < L2; ++c) {
+        const int v = S16[s * N + r * L2 + c];
+        S32[s * N + r * L2 + c] = (uint8_t)(v + 16 * b);
+        b ^= fv_parity4(v);
+      }
+    }
+  }
+};
+
+// The proposal's slice indices per chain.  kind 0: pair of spin k at site i; 1: hop of mode k
+// across the horizontal bond (i, i+1) (b of i+1 flips); 2: hop of mode k across the vertical
+// bond (i, j) in the two-row phase (frame bits; the lower site's right-leg parity toggles when
+// `twist`, the site having a right neighbour).  valid = 0 where the move does not apply.
+struct FSel {
+  const uint8_t* S16;
+  const uint8_t* S32;
+  int N, kind, i, j, k, twist;
+  int8_t *si, *sj, *valid;
+  PV_HD void operator()(int s) const {
+    const uint8_t* x = S16 + (long long)s * N;
+    const uint8_t* y = S32 + (long long)s * N;
+    const int a = x[i];
+    if (kind == 0) {
+      valid[s] = (int8_t)(((a >> k) & 1) == ((a >> (2 + k)) & 1));
+      si[s] = (int8_t)((a ^ ((1 << k) | (1 << (2 + k)))) + (y[i] & 48));
+      return;
+    }
+    const int bb = x[j];
+    valid[s] = (int8_t)(((a >> k) & 1) != ((bb >> k) & 1));
+    const int a2 = a ^ (1 << k), b2 = bb ^ (1 << k);
+    si[s] = (int8_t)(a2 + (y[i] & 48));
+    if (kind == 1)
+      sj[s] = (int8_t)(b2 + ((y[j] & 48) ^ 16));
+    else
+      sj[s] = (int8_t)(b2 + ((y[j] & 48) ^ (twist ? 32 : 0)));
+  }
+};
+
+// Metropolis decision: u = Philox(seed; chain, sweep, m, TAG_FMC); accept iff log u < p log|num
+// / den| (float64).  On acceptance the chain takes the proposed slices (and physical indices)
+// and den the numerator.
+template <typename T>
+struct FAccept {
+  uint8_t* S16;
+  uint8_t* S32;
+  int N, i, j;   // j < 0: one site
+  const int8_t *si, *sj, *valid;
+  const T* num;
+  T* den;
+  int p;
+  uint64_t seed;
+  uint32_t sweep, m;
+  int* acc;
+  int8_t* accepted;
+  PV_HD void operator()(int s) const {
+    accepted[s] = 0;
+    if (!valid[s]) return;
+    const double u = philox_uniform(seed, (uint32_t)s, sweep, m, TAG_FMC);
+    const double ratio = (double)num[s] / (double)den[s];
+    const double d = log(u) - p * log(ratio < 0 ? -ratio : ratio);
+    if (d < 0.0) {
+      acc[s] += 1;
+      accepted[s] = 1;
+      S32[(long long)s * N + i] = (uint8_t)si[s];
+      S16[(long long)s * N + i] = (uint8_t)(si[s] & 15);
+      if (j >= 0) {
+        S32[(long long)s * N + j] = (uint8_t)sj[s];
+        S16[(long long)s * N + j] = (uint8_t)(sj[s] & 15);
+      }
+      den[s] = num[s];
+    }
+  }
+};
+
+// One sweep of every chain (`run` over the 64-slice tensors; S16 in and out, S32 work space
+// for the slice indices; acc counts accepted proposals).  Move m draws counter m of the sweep,
+// in the order of fermion_moves.
+template <typename T, typename BE, typename OT>
+void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, int p,
+                uint64_t seed, uint32_t sweep, int* acc) {
+  auto& b = run.b;
+  auto& be = run.be;
+  const int L1 = run.L1, L2 = run.L2, N = run.N;
+  fv_apply(be, FConf{S16, S32, L1, L2}, n);
+  run.build_down(S32, n);
+  run.trivial(run.uprow(0), b.sU, n);
+  uint32_t m = 0;
+  for (int r = 0; r < L1; ++r) {
+    // one-row phase: each column's pairs, then the hops of its horizontal bond
+    be.set(b.p1R, b.sp1R, (long long)L2 * b.P1, (T)1, n);
+    for (int c = L2 - 1; c >= 0; --c)
+      run.s1_right(r, c, run.p1R(c), b.sp1R, run.bat(run.p1R(c + 1), b.sp1R), run.site(r, c, S32), n);
+    T* Lc = b.p1L;
+    T* Ln = b.p1L + b.P1;
+    be.set(b.p1L, b.sp1L, 0, (T)1, n);
+    run.s1_left(r, 0, b.m0, b.P2, run.bat(Lc, b.sp1L), run.site(r, 0, S32), n);
+    for (int c = 0; c < L2; ++c) {
+      const int i = r * L2 + c;
+      be.dot(OpDot<T>{b.m0, b.P2, run.p1R(c + 1), b.sp1R, run.s1_len(r, c + 1), b.den}, n);
+      for (int sp = 0; sp < 2; ++sp, ++m) {
+        fv_apply(be, FSel{S16, S32, N, 0, i, i, sp, 0, b.si, b.sj, b.valid}, n);
+        run.s1_left(r, c, b.m2, b.P2, run.bat(Lc, b.sp1L), run.site_sel(r, c, b.si), n);
+        be.dot(OpDot<T>{b.m2, b.P2, run.p1R(c + 1), b.sp1R, run.s1_len(r, c + 1), b.num}, n);
+        fv_apply(be, FAccept<T>{S16, S32, N, i, -1, b.si, b.sj, b.valid, b.num, b.den, p, seed,
+                                sweep, m, acc, b.accepted}, n);
+        be.copy_masked(b.m0, b.P2, b.m2, b.P2, run.s1_len(r, c + 1), b.accepted, n);
+      }
+      if (c + 1 < L2) {
+        run.s1_left(r, c + 1, b.m1, b.P2, run.bat(b.m0, b.P2), run.site(r, c + 1, S32), n);
+        be.dot(OpDot<T>{b.m1, b.P2, run.p1R(c + 2), b.sp1R, run.s1_len(r, c + 2), b.den}, n);
+        for (int k = 0; k < 4; ++k, ++m) {
+          fv_apply(be, FSel{S16, S32, N, 1, i, i + 1, k, 0, b.si, b.sj, b.valid}, n);
+          run.s1_left(r, c, b.m2, b.P2, run.bat(Lc, b.sp1L), run.site_sel(r, c, b.si), n);
+          run.s1_left(r, c + 1, b.m3, b.P2, run.bat(b.m2, b.P2), run.site_sel(r, c + 1, b.sj), n);
+          be.dot(OpDot<T>{b.m3, b.P2, run.p1R(c + 2), b.sp1R, run.s1_len(r, c + 2), b.num}, n);
+          fv_apply(be, FAccept<T>{S16, S32, N, i, i + 1, b.si, b.sj, b.valid, b.num, b.den, p,
+                                  seed, sweep, m, acc, b.accepted}, n);
+          be.copy_masked(b.m0, b.P2, b.m2, b.P2, run.s1_len(r, c + 1), b.accepted, n);
+          be.copy_masked(b.m1, b.P2, b.m3, b.P2, run.s1_len(r, c + 2), b.accepted, n);
+        }
+      }
+      // advance: the left partial past column c is P; the next P is Q
+      be.copy_masked(Ln, b.sp1L, b.m0, b.P2, run.s1_len(r, c + 1), nullptr, n);
+      T* t = Lc;
+      Lc = Ln;
+      Ln = t;
+      if (c + 1 < L2) be.copy_masked(b.m0, b.P2, b.m1, b.P2, run.s1_len(r, c + 2), nullptr, n);
+    }
+    if (r + 1 < L1) {
+      // two-row phase: the hops of the vertical bonds to row r+1, column by column
+      be.set(b.p2R, b.sp2R, (long long)L2 * b.P2, (T)1, n);
+      for (int c = L2 - 1; c >= 0; --c)
+        run.s2_right(r, c, run.p2R(c), b.sp2R, run.bat(run.p2R(c + 1), b.sp2R), run.site(r, c, S32),
+                     run.site(r + 1, c, S32), n);
+      T* L2c = b.p2L;
+      T* L2n = b.p2L + b.P2;
+      be.set(b.p2L, b.sp2L, 0, (T)1, n);
+      for (int c = 0; c < L2; ++c) {
+        const int i = r * L2 + c, j = i + L2;
+        run.s2_left(r, c, b.m0, b.P2, run.bat(L2c, b.sp2L), run.site(r, c, S32), run.site(r + 1, c, S32), n);
+        be.dot(OpDot<T>{b.m0, b.P2, run.p2R(c + 1), b.sp2R, run.s2_len(r, c + 1), b.den}, n);
+        for (int k = 0; k < 4; ++k, ++m) {
+          fv_apply(be, FSel{S16, S32, N, 2, i, j, k, c + 1 < L2, b.si, b.sj, b.valid}, n);
+          run.s2_left(r, c, b.m1, b.P2, run.bat(L2c, b.sp2L), run.site_sel(r, c, b.si),
+                      run.site_sel(r + 1, c, b.sj), n);
+          be.dot(OpDot<T>{b.m1, b.P2, run.p2R(c + 1), b.sp2R, run.s2_len(r, c + 1), b.num}, n);
+          fv_apply(be, FAccept<T>{S16, S32, N, i, j, b.si, b.sj, b.valid, b.num, b.den, p, seed,
+                                  sweep, m, acc, b.accepted}, n);
+          be.copy_masked(b.m0, b.P2, b.m1, b.P2, run.s2_len(r, c + 1), b.accepted, n);
+        }
+        be.copy_masked(L2n, b.sp2L, b.m0, b.P2, run.s2_len(r, c + 1), nullptr, n);
+        T* t = L2c;
+        L2c = L2n;
+        L2n = t;
+      }
+      // the actual bits again (the phase's frame and parities dropped), then row r joins the
+      // up environment
+      fv_apply(be, FConf{S16, S32, L1, L2}, n);
+      run.compress(run.uprow(r), b.sU, run.shp.up[r], false, r, S32, run.uprow(r + 1), b.sU, b.lsU, 1, n);
+    }
+  }
+}
+
 #if defined(__CUDACC__)
 
 // The plain O rows into those of the fermionic tensors: entry (l, r, u, d) of site i times

@@ -20,8 +20,6 @@
 
 namespace pv {
 
-constexpr uint32_t TAG_FMC = 0x464D4331u;   // fermionic Metropolis acceptance uniforms
-
 // kind 0: pair of spin k at site i; kind 1: mode k across the bond (i, j)
 struct FMove {
   int kind, i, j, k;

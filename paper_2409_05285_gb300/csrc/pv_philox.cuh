@@ -59,5 +59,6 @@ constexpr uint32_t TAG_CFG = 0x43464731u;
 constexpr uint32_t TAG_MC = 0x4D435357u;
 constexpr uint32_t TAG_DIRECT = 0x44495231u;
 constexpr uint32_t TAG_FINIT = 0x46494E54u;   // perturbation of the fermionic beta = 0 state
+constexpr uint32_t TAG_FMC = 0x464D4331u;     // fermionic Metropolis acceptance uniforms
 
 }  // namespace pv

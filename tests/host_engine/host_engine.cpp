@@ -10,13 +10,15 @@
 // Usage: host_engine <in.bin> <out.bin>
 //   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw, 3 eval with the
 //        compression's right factors from Gram matrices, 4 plain amplitude and O rows of a
-//        PEPS of 32 slices per site, the fermionic engine's form), L1, L2, D, chi, n, p;
+//        PEPS of 32 slices per site, the fermionic engine's form, 5 one fermionic Metropolis
+//        sweep on cached strips over 64 slices per site), L1, L2, D, chi, n, p;
 //        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
 //        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
 //        mc:   uint8 S[n][N], int32 acc[n], int32 prop[n]
 //        draw: uint8 S[n][N], float64 log_q[n]  (direct sampling, pv_direct.cuh)
 //        mode 4: float64 log_abs[n], int8 sign[n], O[n][N_o]  (pv_fermion.cuh)
+//        mode 5: uint8 S[n][N], int32 acc[n]  (fermion_mc, pv_fermion.cuh)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -30,6 +32,7 @@ using namespace pv;
 using T = double;
 
 struct HostBE {
+  static constexpr bool host_loops = true;   // per-chain functors run as plain loops
   int N = 0, nb = 0;
   const int* bi = nullptr;
   const int* bj = nullptr;
@@ -163,7 +166,7 @@ int main(int argc, char** argv) {
   rd(fi, &sweep, 1);
   const int N = L1 * L2;
   std::vector<long long> toff(N + 1, 0), ooff(N + 1, 0);
-  const int slices = mode == 4 ? 32 : 4;
+  const int slices = mode == 4 ? 32 : mode == 5 ? 64 : 4;
   for (int i = 0; i < N; ++i) {
     const int r = i / L2, c = i % L2;
     const long long sz = (long long)(c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
@@ -248,6 +251,12 @@ int main(int argc, char** argv) {
     std::fwrite(la.data(), 8, n, fo);
     std::fwrite(sg.data(), 1, n, fo);
     std::fwrite(O.data(), 8, O.size(), fo);
+  } else if (mode == 5) {
+    std::vector<uint8_t> S32((size_t)n * N, 0);
+    std::vector<int> acc(n, 0);
+    fermion_mc(run, S.data(), S32.data(), n, p, seed, (uint32_t)sweep, acc.data());
+    std::fwrite(S.data(), 1, S.size(), fo);
+    std::fwrite(acc.data(), 4, n, fo);
   } else if (mode == 0 || mode == 3) {
     const long long No = ooff[N];
     std::vector<double> la(n), es(n), ea(n);

@@ -40,6 +40,10 @@ def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
         f.write(np.asarray(S, dtype=np.uint8).tobytes())
     subprocess.run([exe, fin, fout], check=True)
     raw = open(fout, "rb").read()
+    if mode == 5:
+        S2 = np.frombuffer(raw, np.uint8, n * lat.N, 0).reshape(n, lat.N)
+        acc = np.frombuffer(raw, np.int32, n, n * lat.N)
+        return S2, acc
     if mode == 4:
         la = np.frombuffer(raw, np.float64, n, 0)
         sg = np.frombuffer(raw, np.int8, n, 8 * n)
@@ -211,3 +215,43 @@ def test_host_engine_fermion_plain_contraction_matches_oracle(engine, tmp_path, 
             plain = O[k, o:o + sz] * signs[i][S32[k, i]].ravel()
             assert np.max(np.abs(plain - grads[i].ravel())) <= 1e-9 * scale, (k, i)
             o += sz
+
+
+@pytest.mark.parametrize("case,p", [((2, 2, 2, 4, 6), 2), ((3, 3, 2, 8, 6), 2), ((2, 3, 3, 9, 5), 1),
+                                    ((3, 4, 2, 8, 4), 2)])
+def test_host_engine_fermion_sweep_on_strips_matches_oracle(engine, tmp_path, case, p):
+    # the fermionic sweep on cached one- and two-row strips (fermion_mc over 64 slices per
+    # site: the signed slices and the same with a right-leg parity) against the oracle's sweep,
+    # whose every proposal is a full contraction: the same Philox uniforms, the same decisions
+    # (exact chi), so the same configurations and acceptance counts
+    import functools
+    from oracle import fermion as fm
+    from oracle import fermion_vmc as fv
+    L1, L2, D, chi, n = case
+    N = L1 * L2
+    rng = np.random.default_rng(7 * L1 + 3 * L2 + D + p)
+    T = fm.random_even_fpeps(L1, L2, D, rng, scale=0.4)
+    for i, A in enumerate(fm.identity_fpeps(L1, L2)):
+        T[i][(slice(None), 0, 0, 0, 0)] += A[:, 0, 0, 0, 0]
+    blocks = []
+    for A in fm.fpeps_signed_slices(T):
+        B = A.copy()
+        B[:, :, 1::2, :, :] *= -1.0               # parity of the right leg
+        blocks += [A.ravel(), B.ravel()]
+    th64 = np.concatenate(blocks)
+    a = rng.integers(0, 4, (n, N))
+    S0 = (a | (a << 2)).astype(np.uint8)
+    lat = Lattice(L1, L2, D)
+    seed, sweep = 77, 3
+    S, acc = _run(engine, tmp_path, 5, lat, chi, th64, S0, p=p, seed=seed, sweep=sweep)
+    amp = functools.lru_cache(maxsize=None)(fm.fpeps_amplitude_function(L1, L2, T))
+    M = len(fv.moves(L1, L2))
+    margin = np.inf
+    for c in range(n):
+        x, a_ref, mg = fv.sweep(L1, L2, T, S0[c], p, fv.uniforms(seed, c, sweep, M),
+                                amplitude=lambda X: amp(tuple(int(v) for v in X)))
+        margin = min(margin, mg)
+        assert np.array_equal(S[c], x), c
+        assert acc[c] == a_ref, c
+    assert margin > 1e-8
+    assert acc.sum() > 0
