@@ -260,6 +260,171 @@ void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, 
   }
 }
 
+// ---------------------------------------------------------------- local energies on strips
+//
+// E_sys and E_anc (Eq. 9 with the Hubbard terms of Eq. 14 on the system and ancilla modes) from
+// the same strips: the ratio psi(S')/psi(S) of a hop is cs(S')/cs(S) (the configuration signs)
+// times the plain strip ratio, times, for a vertical hop at column c, the sign
+// prod_(c' > c) (-1)^(p(S_(r+1, c'))) of its right-leg parity.
+
+// (-1)^(sum_(i<j) p_i p_j + sum_R P_(R-1) P_R) of a configuration's physical indices.
+PV_HD int fv_config_sign(const uint8_t* x, int L1, int L2) {
+  int e = 0, pre = 0, prevP = 0, accP = 0;
+  for (int r = 0; r < L1; ++r) {
+    int row = 0;
+    for (int c = 0; c < L2; ++c) {
+      const int p = fv_parity4(x[r * L2 + c]);
+      e += p * pre;
+      pre ^= p;
+      row ^= p;
+    }
+    accP ^= row;
+    e += prevP * accP;
+    prevP = accP;
+  }
+  return (e & 1) ? -1 : 1;
+}
+
+// Diagonal terms U n_up n_dn - mu (n_up + n_dn) per site, on each layer.
+struct FDiag {
+  const uint8_t* S16;
+  int N;
+  double U, mu;
+  double *es, *ea;
+  PV_HD void operator()(int s) const {
+    double e[2] = {0.0, 0.0};
+    for (int q = 0; q < N; ++q) {
+      const int x = S16[(long long)s * N + q];
+      for (int layer = 0; layer < 2; ++layer) {
+        const int nu = (x >> (2 * layer)) & 1, nd = (x >> (2 * layer + 1)) & 1;
+        e[layer] += U * nu * nd - mu * (nu + nd);
+      }
+    }
+    es[s] = e[0];
+    ea[s] = e[1];
+  }
+};
+
+// sign *= cs(S): the plain amplitude's sign into the fermionic one.
+struct FSignApply {
+  const uint8_t* S16;
+  int L1, L2;
+  int8_t* sign;
+  PV_HD void operator()(int s) const {
+    sign[s] = (int8_t)(sign[s] * fv_config_sign(S16 + (long long)s * L1 * L2, L1, L2));
+  }
+};
+
+// The hop of mode k across the bond (i, j) (one direction allowed where the occupations
+// differ): E[layer of k] += -t JW(c+_a c_b) cs(S')/cs(S) twist num/den, with a the empty and b
+// the occupied site, JW the Jordan-Wigner sign of the modes ordered site by site, and twist
+// the right-leg sign of a vertical hop (vrow: the lower row, col: the hop's column; -1: none).
+template <typename T>
+struct FRatio {
+  const uint8_t* S16;
+  int L1, L2, i, j, k, vrow, col;
+  const int8_t* valid;
+  const T* num;
+  const T* den;
+  long long dens;
+  double t_hop;
+  double *es, *ea;
+  PV_HD void operator()(int s) const {
+    if (!valid[s]) return;
+    const int N = L1 * L2;
+    const uint8_t* x = S16 + (long long)s * N;
+    const int bit = 1 << k;
+    const int a = (x[i] & bit) ? j : i, b = (x[i] & bit) ? i : j;   // c+_a c_b
+    uint8_t y[256];   // N <= 16 x 16 sites
+    for (int q = 0; q < N; ++q) y[q] = x[q];
+    // occupied modes below mode k of site b in x, then below mode k of site a after removal
+    int cnt = 0;
+    for (int q = 0; q < b; ++q) cnt += (x[q] & 1) + ((x[q] >> 1) & 1) + ((x[q] >> 2) & 1) + ((x[q] >> 3) & 1);
+    for (int q = 0; q < k; ++q) cnt += (x[b] >> q) & 1;
+    y[b] = (uint8_t)(x[b] & ~bit);
+    for (int q = 0; q < a; ++q) cnt += (y[q] & 1) + ((y[q] >> 1) & 1) + ((y[q] >> 2) & 1) + ((y[q] >> 3) & 1);
+    for (int q = 0; q < k; ++q) cnt += (y[a] >> q) & 1;
+    y[a] = (uint8_t)(x[a] | bit);
+    double f = (cnt & 1) ? t_hop : -t_hop;
+    f *= fv_config_sign(y, L1, L2) * fv_config_sign(x, L1, L2);
+    if (vrow >= 0)
+      for (int c2 = col + 1; c2 < L2; ++c2)
+        if (fv_parity4(y[vrow * L2 + c2])) f = -f;
+    const double r = (double)num[s] / (double)den[(long long)s * dens];
+    if (k < 2)
+      es[s] += f * r;
+    else
+      ea[s] += f * r;
+  }
+};
+
+// log|psi|, sign, E_sys and E_anc of every chain (`run` over the 64-slice tensors; S32 work
+// space), each hop's ratio from a one-row (horizontal) or two-row (vertical) strip.
+template <typename T, typename BE, typename OT>
+void fermion_eloc(BatchRunner<T, BE, OT>& run, const uint8_t* S16, uint8_t* S32, int n,
+                  double t_hop, double U, double mu, double* la, int8_t* sg, double* es,
+                  double* ea) {
+  auto& b = run.b;
+  auto& be = run.be;
+  const int L1 = run.L1, L2 = run.L2, N = run.N;
+  fv_apply(be, FConf{S16, S32, L1, L2}, n);
+  run.build_down(S32, n);
+  fv_apply(be, FDiag{S16, N, U, mu, es, ea}, n);
+  run.trivial(run.uprow(0), b.sU, n);
+  for (int r = 0; r < L1; ++r) {
+    be.set(b.p1R, b.sp1R, (long long)L2 * b.P1, (T)1, n);
+    for (int c = L2 - 1; c >= 0; --c)
+      run.s1_right(r, c, run.p1R(c), b.sp1R, run.bat(run.p1R(c + 1), b.sp1R), run.site(r, c, S32), n);
+    if (r == 0) {
+      be.amp(b.p1R, b.sp1R, b.lsD + 1, L1 + 1, la, sg, n);
+      fv_apply(be, FSignApply{S16, L1, L2, sg}, n);
+    }
+    T* Lc = b.p1L;
+    T* Ln = b.p1L + b.P1;
+    be.set(b.p1L, b.sp1L, 0, (T)1, n);
+    for (int c = 0; c + 1 < L2; ++c) {
+      const int i = r * L2 + c;
+      for (int k = 0; k < 4; ++k) {
+        fv_apply(be, FSel{S16, S32, N, 1, i, i + 1, k, 0, b.si, b.sj, b.valid}, n);
+        run.s1_left(r, c, b.m0, b.P2, run.bat(Lc, b.sp1L), run.site_sel(r, c, b.si), n);
+        run.s1_left(r, c + 1, b.m1, b.P2, run.bat(b.m0, b.P2), run.site_sel(r, c + 1, b.sj), n);
+        be.dot(OpDot<T>{b.m1, b.P2, run.p1R(c + 2), b.sp1R, run.s1_len(r, c + 2), b.num}, n);
+        fv_apply(be, FRatio<T>{S16, L1, L2, i, i + 1, k, -1, c, b.valid, b.num, b.p1R, b.sp1R,
+                               t_hop, es, ea}, n);
+      }
+      run.s1_left(r, c, Ln, b.sp1L, run.bat(Lc, b.sp1L), run.site(r, c, S32), n);
+      T* t = Lc;
+      Lc = Ln;
+      Ln = t;
+    }
+    if (r + 1 < L1) {
+      be.set(b.p2R, b.sp2R, (long long)L2 * b.P2, (T)1, n);
+      for (int c = L2 - 1; c >= 0; --c)
+        run.s2_right(r, c, run.p2R(c), b.sp2R, run.bat(run.p2R(c + 1), b.sp2R), run.site(r, c, S32),
+                     run.site(r + 1, c, S32), n);
+      T* L2c = b.p2L;
+      T* L2n = b.p2L + b.P2;
+      be.set(b.p2L, b.sp2L, 0, (T)1, n);
+      for (int c = 0; c < L2; ++c) {
+        const int i = r * L2 + c, j = i + L2;
+        for (int k = 0; k < 4; ++k) {
+          fv_apply(be, FSel{S16, S32, N, 2, i, j, k, c + 1 < L2, b.si, b.sj, b.valid}, n);
+          run.s2_left(r, c, b.m0, b.P2, run.bat(L2c, b.sp2L), run.site_sel(r, c, b.si),
+                      run.site_sel(r + 1, c, b.sj), n);
+          be.dot(OpDot<T>{b.m0, b.P2, run.p2R(c + 1), b.sp2R, run.s2_len(r, c + 1), b.num}, n);
+          fv_apply(be, FRatio<T>{S16, L1, L2, i, j, k, r + 1, c, b.valid, b.num, b.p2R, b.sp2R,
+                                 t_hop, es, ea}, n);
+        }
+        run.s2_left(r, c, L2n, b.sp2L, run.bat(L2c, b.sp2L), run.site(r, c, S32), run.site(r + 1, c, S32), n);
+        T* t = L2c;
+        L2c = L2n;
+        L2n = t;
+      }
+      run.compress(run.uprow(r), b.sU, run.shp.up[r], false, r, S32, run.uprow(r + 1), b.sU, b.lsU, 1, n);
+    }
+  }
+}
+
 #if defined(__CUDACC__)
 
 // The plain O rows into those of the fermionic tensors: entry (l, r, u, d) of site i times

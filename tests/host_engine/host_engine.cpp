@@ -11,7 +11,9 @@
 //   in:  int32 mode (0 eval, 1 one Metropolis sweep, 2 one direct draw, 3 eval with the
 //        compression's right factors from Gram matrices, 4 plain amplitude and O rows of a
 //        PEPS of 32 slices per site, the fermionic engine's form, 5 one fermionic Metropolis
-//        sweep on cached strips over 64 slices per site), L1, L2, D, chi, n, p;
+//        sweep on cached strips over 64 slices per site, 6 fermionic local energies on
+//        strips over 64 slices per site; t, U, mu in place of J1, J2 and seed), L1, L2, D,
+//        chi, n, p;
 //        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
 //        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
@@ -19,10 +21,12 @@
 //        draw: uint8 S[n][N], float64 log_q[n]  (direct sampling, pv_direct.cuh)
 //        mode 4: float64 log_abs[n], int8 sign[n], O[n][N_o]  (pv_fermion.cuh)
 //        mode 5: uint8 S[n][N], int32 acc[n]  (fermion_mc, pv_fermion.cuh)
+//        mode 6: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n]  (fermion_eloc)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <vector>
 
 #include "pv_direct.cuh"
@@ -166,7 +170,7 @@ int main(int argc, char** argv) {
   rd(fi, &sweep, 1);
   const int N = L1 * L2;
   std::vector<long long> toff(N + 1, 0), ooff(N + 1, 0);
-  const int slices = mode == 4 ? 32 : mode == 5 ? 64 : 4;
+  const int slices = mode == 4 ? 32 : (mode == 5 || mode == 6) ? 64 : 4;
   for (int i = 0; i < N; ++i) {
     const int r = i / L2, c = i % L2;
     const long long sz = (long long)(c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
@@ -251,6 +255,18 @@ int main(int argc, char** argv) {
     std::fwrite(la.data(), 8, n, fo);
     std::fwrite(sg.data(), 1, n, fo);
     std::fwrite(O.data(), 8, O.size(), fo);
+  } else if (mode == 6) {
+    // the couplings arrive in J1 (t), J2 (U) and the seed's bits (mu, a float64)
+    double mu;
+    std::memcpy(&mu, &seed, sizeof(mu));
+    std::vector<uint8_t> S32((size_t)n * N, 0);
+    std::vector<double> la(n), es(n), ea(n);
+    std::vector<int8_t> sg(n);
+    fermion_eloc(run, S.data(), S32.data(), n, J[0], J[1], mu, la.data(), sg.data(), es.data(), ea.data());
+    std::fwrite(la.data(), 8, n, fo);
+    std::fwrite(sg.data(), 1, n, fo);
+    std::fwrite(es.data(), 8, n, fo);
+    std::fwrite(ea.data(), 8, n, fo);
   } else if (mode == 5) {
     std::vector<uint8_t> S32((size_t)n * N, 0);
     std::vector<int> acc(n, 0);

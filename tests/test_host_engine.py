@@ -40,6 +40,12 @@ def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
         f.write(np.asarray(S, dtype=np.uint8).tobytes())
     subprocess.run([exe, fin, fout], check=True)
     raw = open(fout, "rb").read()
+    if mode == 6:
+        la = np.frombuffer(raw, np.float64, n, 0)
+        sg = np.frombuffer(raw, np.int8, n, 8 * n)
+        es = np.frombuffer(raw, np.float64, n, 9 * n)
+        ea = np.frombuffer(raw, np.float64, n, 17 * n)
+        return la, sg, es, ea
     if mode == 5:
         S2 = np.frombuffer(raw, np.uint8, n * lat.N, 0).reshape(n, lat.N)
         acc = np.frombuffer(raw, np.int32, n, n * lat.N)
@@ -255,3 +261,45 @@ def test_host_engine_fermion_sweep_on_strips_matches_oracle(engine, tmp_path, ca
         assert acc[c] == a_ref, c
     assert margin > 1e-8
     assert acc.sum() > 0
+
+
+def _fermion_th64(T):
+    # the signed slices of every site followed by the same with a parity on the right leg
+    from oracle import fermion as fm
+    blocks = []
+    for A in fm.fpeps_signed_slices(T):
+        B = A.copy()
+        B[:, :, 1::2, :, :] *= -1.0
+        blocks += [A.ravel(), B.ravel()]
+    return np.concatenate(blocks)
+
+
+@pytest.mark.parametrize("case", [(2, 2, 2, 4, 6), (3, 3, 2, 8, 5), (2, 3, 3, 9, 4), (3, 4, 2, 8, 3)])
+def test_host_engine_fermion_local_energy_on_strips_matches_oracle(engine, tmp_path, case):
+    # fermion_eloc: every hop's ratio from a one-row (horizontal) or two-row (vertical) strip,
+    # with the configuration-sign ratio, the Jordan-Wigner sign and a vertical hop's right-leg
+    # sign, against the oracle's local energies (each hop a full row contraction), exact chi;
+    # also log|psi| and the sign
+    from oracle import fermion as fm
+    L1, L2, D, chi, n = case
+    N = L1 * L2
+    t_hop, U, mu = 1.0, 8.0, 4.0
+    rng = np.random.default_rng(11 * L1 + 5 * L2 + D)
+    T = fm.random_even_fpeps(L1, L2, D, rng, scale=0.5)
+    for i, A in enumerate(fm.identity_fpeps(L1, L2)):
+        T[i][(slice(None), 0, 0, 0, 0)] += A[:, 0, 0, 0, 0]
+    S = rng.integers(0, 16, (n, N))
+    for k in range(n):
+        if sum(bin(int(x)).count("1") for x in S[k]) % 2:
+            S[k, 0] ^= 1
+    S = S.astype(np.uint8)
+    lat = Lattice(L1, L2, D, J1=t_hop, J2=U)
+    mu_bits = struct.unpack("<Q", struct.pack("<d", mu))[0]
+    la, sg, es, ea = _run(engine, tmp_path, 6, lat, chi, _fermion_th64(T), S, seed=mu_bits)
+    for k in range(n):
+        psi = fm.fpeps_amplitude_bosonic(L1, L2, T, S[k])
+        assert sg[k] == np.sign(psi) and abs(la[k] - np.log(abs(psi))) <= 1e-10, k
+        r_es, r_ea = fm.fpeps_local_energy(L1, L2, T, S[k], t_hop, U, mu)
+        scale = max(1.0, abs(r_es), abs(r_ea))
+        assert abs(es[k] - r_es) <= 1e-9 * scale, (k, es[k], r_es)
+        assert abs(ea[k] - r_ea) <= 1e-9 * scale, (k, ea[k], r_ea)
