@@ -1,5 +1,7 @@
-// Amplitudes of a fermionic PEPS of the doubled Hubbard lattice (Sec. II, Fig. 1b; Sec. III.B)
-// on the batched engine.
+// A fermionic PEPS of the doubled Hubbard lattice (Sec. II, Fig. 1b; Sec. III.B) on the batched
+// engine: amplitudes and O rows (plain_amplitude, plain_log_derivative and the sign kernels
+// below), the Metropolis sweep and the local energies on cached strips (fermion_mc,
+// fermion_eloc), and the kernels of the local energies with one full contraction per hop.
 //
 // The tensors are parity even with sixteen local states per site (system and ancilla modes
 // c_up, c_dn, d_up, d_dn; parity of a local index = popcount mod 2, of a virtual index = its
