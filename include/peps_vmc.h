@@ -204,6 +204,14 @@ int peps_famp_log_derivative(peps_famp* famp, const double* theta, size_t n_thet
  * n_sweeps or sweep counters beyond 32 bits.  peps_famp_n_moves returns 2 N + 4 (bonds), or
  * PEPS_EINVAL for a null evaluator. */
 int peps_famp_n_moves(const peps_famp* famp);
+/* Strip forms (enable = 1; 0 by default): the sweep's proposals and the local energies' hop
+ * ratios from one- and two-row strips between cached environments over 64 slices per site
+ * (the signed slices, and the same with a parity on the right leg, which carries a vertical
+ * hop's sign flips) instead of a full contraction per proposal or hop; same moves, uniforms and
+ * decision rule.  The sweep then takes Philox uniforms only (u must be NULL).  Checked in a
+ * host build of the engine against the oracle; not yet run on a GPU.  EINVAL for a null
+ * evaluator or enable outside {0, 1}. */
+int peps_famp_set_strips(peps_famp* famp, int enable);
 /* The moves of one sweep on an L1 x L2 lattice in the order above, four ints per move: kind
  * (0 pair, 1 hop), site i, site j (= i for a pair), spin (pair) or mode (hop); the first cap
  * moves are written to table (host).  Returns the number of moves, or PEPS_EINVAL.  Host

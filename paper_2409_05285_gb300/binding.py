@@ -45,7 +45,7 @@ EXPORTS = [
     "peps_famp_free", "peps_famp_local_energy", "peps_famp_log_derivative",
     "peps_famp_n_moves", "peps_famp_sweep", "peps_famp_sr_step", "peps_famp_profile",
     "peps_famp_profile_read", "peps_famp_launches", "peps_famp_init_theta",
-    "peps_famp_move_table",
+    "peps_famp_move_table", "peps_famp_set_strips",
 ]
 
 
@@ -165,6 +165,7 @@ def load(path=None):
     lib.peps_famp_launches.restype = ctypes.c_longlong
     lib.peps_famp_init_theta.argtypes = [ip, ip, ip, dp, ctypes.c_uint64, vp, ctypes.c_size_t]
     lib.peps_famp_move_table.argtypes = [ip, ip, vp, ip]
+    lib.peps_famp_set_strips.argtypes = [vp, ip]
     lib.peps_famp_sweep.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, ip, ip, ctypes.c_uint64,
                                     ctypes.c_uint64, vp, vp, vp, vp]
     lib.peps_famp_sr_step.argtypes = [vp, vp, ctypes.c_size_t, vp, ip, dp, dp, dp, ip, dp, dp, ip,
@@ -570,6 +571,12 @@ class FermionAmplitudes:
     def launches(self):
         """Kernel launches this evaluator has made so far."""
         return int(self.lib.peps_famp_launches(self.h))
+
+    def set_strips(self, enable):
+        """Sweeps and local energies on cached strips (peps_famp_set_strips)."""
+        rc = self.lib.peps_famp_set_strips(self.h, 1 if enable else 0)
+        if rc != PEPS_OK:
+            raise PepsError(rc, self.lib.peps_famp_last_error(self.h).decode())
 
     @property
     def n_moves(self):

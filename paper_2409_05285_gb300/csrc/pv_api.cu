@@ -2006,6 +2006,11 @@ struct peps_famp {
          *d_pqpart = nullptr;
   SRScalars* d_sc = nullptr;
   FObs* d_fo = nullptr;
+  // strip forms (peps_famp_set_strips): the 64 slices per site and their offsets
+  bool strips = false;
+  std::vector<long long> toff64;
+  long long* d_toff64 = nullptr;
+  void* d_th64 = nullptr;
 };
 
 namespace {
@@ -2061,8 +2066,53 @@ int famp_theta(peps_famp* f, const double* theta) {
     PV_KLAUNCH(&c->kprof, st, "k_fsigned", 0.0, 0.0,
                k_fsigned<float><<<g, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
                                                    (float*)f->d_th32, f->d_toff32));
+  if (f->strips) {
+    dim3 g64((unsigned)std::min<long long>((2 * big + 255) / 256, 1024), (unsigned)N);
+    if (f->b64)
+      PV_KLAUNCH(&c->kprof, st, "k_fsigned64", 0.0, 0.0,
+                 k_fsigned64<double><<<g64, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                          (double*)f->d_th64, f->d_toff64));
+    else
+      PV_KLAUNCH(&c->kprof, st, "k_fsigned64", 0.0, 0.0,
+                 k_fsigned64<float><<<g64, 256, 0, st>>>(c->P.L1, c->P.L2, c->P.D, f->d_th16, f->d_toff16,
+                                                         (float*)f->d_th64, f->d_toff64));
+  }
   PV_CUDA(c, cudaGetLastError());
   return PEPS_OK;
+}
+
+// The strip forms on the engine's runner, pointed at the 64 slices for the call: one sweep
+// (fermion_mc) or the local energies (fermion_eloc) of the nb chains in d_S16, chunk by chunk.
+template <typename T>
+int famp_strips_t(peps_famp* f, BatchImpl<T>* bi, int nb, bool sweep, int p, uint64_t seed,
+                  uint32_t sweep_no, double t_hop, double U, double mu) {
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  auto& run = bi->run;
+  const T* th_old = run.theta;
+  const std::vector<long long> toff_old = run.toff;
+  run.theta = (const T*)f->d_th64;
+  run.toff = f->toff64;
+  const int chunk = c->batch->chunk;
+  for (int off = 0; off < nb; off += chunk) {
+    const int n = std::min(chunk, nb - off);
+    if (sweep)
+      fermion_mc(run, f->d_S16 + (long long)off * N, f->d_S32 + (long long)off * N, n, p, seed,
+                 sweep_no, f->d_acc + off, off);
+    else
+      fermion_eloc(run, f->d_S16 + (long long)off * N, f->d_S32 + (long long)off * N, n, t_hop, U, mu,
+                   f->d_la + off, f->d_sg + off, f->d_es + off, f->d_ea + off);
+  }
+  run.theta = th_old;
+  run.toff = toff_old;
+  PV_CUDA(c, cudaGetLastError());
+  return PEPS_OK;
+}
+
+int famp_strips(peps_famp* f, int nb, bool sweep, int p, uint64_t seed, uint32_t sweep_no,
+                double t_hop, double U, double mu) {
+  return f->b64 ? famp_strips_t(f, f->b64, nb, sweep, p, seed, sweep_no, t_hop, U, mu)
+                : famp_strips_t(f, f->b32, nb, sweep, p, seed, sweep_no, t_hop, U, mu);
 }
 
 // log|psi|, sign, E_sys and E_anc of the nb configurations in d_S16 (theta's slices made):
@@ -2104,7 +2154,8 @@ int famp_energies(peps_famp* f, int nb, double t_hop, double U, double mu) {
     PV_TRY(dalloc(c, &f->d_sgx, (size_t)cap));
     f->x_cap = cap;
   }
-  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));   // also checks the entries
+  if (f->strips) return famp_strips(f, nb, false, 2, 0, 0, t_hop, U, mu);
   const unsigned gb = (unsigned)((nb + 127) / 128);
   PV_KLAUNCH(&c->kprof, st, "k_fhop_count", 0.0, 0.0,
              k_fhop_count<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj, f->nbonds, f->d_cnt));
@@ -2249,6 +2300,8 @@ int peps_famp_create(int L1, int L2, int D, int chi, int n_max, int precision, v
   c->No = c->ooff[N];
   f->n16 = f->toff16[N];
   f->moves = fermion_moves(L1, L2);
+  f->toff64.assign(N + 1, 0);
+  for (int i = 0; i < N; ++i) f->toff64[i + 1] = f->toff64[i] + 2 * (f->toff32[i + 1] - f->toff32[i]);
   const size_t real = precision == PEPS_FP64 ? sizeof(double) : sizeof(float);
   auto bail = [&](int rc) {
     peps_free(c);
@@ -2342,6 +2395,20 @@ int peps_famp_log_derivative(peps_famp* f, const double* theta, size_t n_theta, 
   return batch_status(c);
 }
 
+int peps_famp_set_strips(peps_famp* f, int enable) {
+  if (!f || !f->c || enable < 0 || enable > 1) return PEPS_EINVAL;
+  peps_ctx* c = f->c;
+  if (enable && !f->d_th64) {
+    const int N = c->N;
+    const size_t real = f->b64 ? sizeof(double) : sizeof(float);
+    PV_TRY(dalloc(c, (unsigned char**)&f->d_th64, (size_t)f->toff64[N] * real));
+    PV_TRY(dalloc(c, &f->d_toff64, (N + 1) * sizeof(long long)));
+    PV_CUDA(c, cudaMemcpy(f->d_toff64, f->toff64.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  }
+  f->strips = enable != 0;
+  return PEPS_OK;
+}
+
 int peps_famp_n_moves(const peps_famp* f) {
   if (!f || !f->c) return PEPS_EINVAL;
   return (int)f->moves.size();
@@ -2355,6 +2422,7 @@ int peps_famp_sweep(peps_famp* f, const double* theta, size_t n_theta, uint8_t* 
   if (!theta || n_theta != (size_t)f->n16 || nb < 0 || nb > f->n_max || (nb > 0 && !S) ||
       (p != 1 && p != 2) || n_sweeps < 0 || sweep0 + (uint64_t)n_sweeps > 0xFFFFFFFFull)
     return fail(c, PEPS_EINVAL, "famp_sweep: args");
+  if (u && f->strips) return fail(c, PEPS_EINVAL, "famp_sweep: given uniforms need the full-contraction sweep");
   if (nb == 0) return PEPS_OK;
   const int N = c->N, M = (int)f->moves.size();
   cudaStream_t st = c->stream;
@@ -2367,10 +2435,13 @@ int peps_famp_sweep(peps_famp* f, const double* theta, size_t n_theta, uint8_t* 
   PV_TRY(famp_theta(f, theta));
   PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
   if (u && nu) PV_CUDA(c, cudaMemcpyAsync(f->d_u, u, nu * sizeof(double), cudaMemcpyHostToDevice, st));
-  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));
+  PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));   // also checks the entries
   PV_CUDA(c, cudaMemsetAsync(f->d_acc, 0, (size_t)nb * sizeof(int), st));
   const unsigned gb = (unsigned)((nb + 127) / 128);
-  for (int k = 0; k < n_sweeps; ++k) {
+  for (int k = 0; k < n_sweeps && f->strips; ++k)
+    PV_TRY(famp_strips(f, nb, true, p, seed, (uint32_t)(sweep0 + k), 0.0, 0.0, 0.0));
+  if (f->strips && n_sweeps > 0) PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg, false));
+  for (int k = 0; k < n_sweeps && !f->strips; ++k) {
     const double* uk = u ? f->d_u + (size_t)k * nb * M : nullptr;
     for (int m = 0; m < M; ++m) {
       // the proposal per chain; only the chains where it applies are packed and contracted

@@ -137,9 +137,9 @@ struct FSel {
   }
 };
 
-// Metropolis decision: u = Philox(seed; chain, sweep, m, TAG_FMC); accept iff log u < p log|num
-// / den| (float64).  On acceptance the chain takes the proposed slices (and physical indices)
-// and den the numerator.
+// Metropolis decision: u = Philox(seed; chain0 + chain, sweep, m, TAG_FMC); accept iff log u < p
+// log|num / den| (float64).  On acceptance the chain takes the proposed slices (and physical
+// indices) and den the numerator.
 template <typename T>
 struct FAccept {
   uint8_t* S16;
@@ -150,13 +150,14 @@ struct FAccept {
   T* den;
   int p;
   uint64_t seed;
+  int chain0;
   uint32_t sweep, m;
   int* acc;
   int8_t* accepted;
   PV_HD void operator()(int s) const {
     accepted[s] = 0;
     if (!valid[s]) return;
-    const double u = philox_uniform(seed, (uint32_t)s, sweep, m, TAG_FMC);
+    const double u = philox_uniform(seed, (uint32_t)(chain0 + s), sweep, m, TAG_FMC);
     const double ratio = (double)num[s] / (double)den[s];
     const double d = log(u) - p * log(ratio < 0 ? -ratio : ratio);
     if (d < 0.0) {
@@ -174,11 +175,11 @@ struct FAccept {
 };
 
 // One sweep of every chain (`run` over the 64-slice tensors; S16 in and out, S32 work space
-// for the slice indices; acc counts accepted proposals).  Move m draws counter m of the sweep,
-// in the order of fermion_moves.
+// for the slice indices; acc counts accepted proposals; chain s draws as chain chain0 + s).
+// Move m draws counter m of the sweep, in the order of fermion_moves.
 template <typename T, typename BE, typename OT>
 void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, int p,
-                uint64_t seed, uint32_t sweep, int* acc) {
+                uint64_t seed, uint32_t sweep, int* acc, int chain0 = 0) {
   auto& b = run.b;
   auto& be = run.be;
   const int L1 = run.L1, L2 = run.L2, N = run.N;
@@ -203,7 +204,7 @@ void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, 
         run.s1_left(r, c, b.m2, b.P2, run.bat(Lc, b.sp1L), run.site_sel(r, c, b.si), n);
         be.dot(OpDot<T>{b.m2, b.P2, run.p1R(c + 1), b.sp1R, run.s1_len(r, c + 1), b.num}, n);
         fv_apply(be, FAccept<T>{S16, S32, N, i, -1, b.si, b.sj, b.valid, b.num, b.den, p, seed,
-                                sweep, m, acc, b.accepted}, n);
+                                chain0, sweep, m, acc, b.accepted}, n);
         be.copy_masked(b.m0, b.P2, b.m2, b.P2, run.s1_len(r, c + 1), b.accepted, n);
       }
       if (c + 1 < L2) {
@@ -215,7 +216,7 @@ void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, 
           run.s1_left(r, c + 1, b.m3, b.P2, run.bat(b.m2, b.P2), run.site_sel(r, c + 1, b.sj), n);
           be.dot(OpDot<T>{b.m3, b.P2, run.p1R(c + 2), b.sp1R, run.s1_len(r, c + 2), b.num}, n);
           fv_apply(be, FAccept<T>{S16, S32, N, i, i + 1, b.si, b.sj, b.valid, b.num, b.den, p,
-                                  seed, sweep, m, acc, b.accepted}, n);
+                                  seed, chain0, sweep, m, acc, b.accepted}, n);
           be.copy_masked(b.m0, b.P2, b.m2, b.P2, run.s1_len(r, c + 1), b.accepted, n);
           be.copy_masked(b.m1, b.P2, b.m3, b.P2, run.s1_len(r, c + 2), b.accepted, n);
         }
@@ -246,7 +247,7 @@ void fermion_mc(BatchRunner<T, BE, OT>& run, uint8_t* S16, uint8_t* S32, int n, 
                       run.site_sel(r + 1, c, b.sj), n);
           be.dot(OpDot<T>{b.m1, b.P2, run.p2R(c + 1), b.sp2R, run.s2_len(r, c + 1), b.num}, n);
           fv_apply(be, FAccept<T>{S16, S32, N, i, j, b.si, b.sj, b.valid, b.num, b.den, p, seed,
-                                  sweep, m, acc, b.accepted}, n);
+                                  chain0, sweep, m, acc, b.accepted}, n);
           be.copy_masked(b.m0, b.P2, b.m1, b.P2, run.s2_len(r, c + 1), b.accepted, n);
         }
         be.copy_masked(L2n, b.sp2L, b.m0, b.P2, run.s2_len(r, c + 1), nullptr, n);

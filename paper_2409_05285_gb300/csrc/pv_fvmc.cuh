@@ -15,6 +15,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "pv_fermion.cuh"
 #include "pv_philox.cuh"
 #include "pv_sr.cuh"
 
@@ -53,6 +54,43 @@ struct FObs {
 };
 
 #if defined(__CUDACC__)
+
+// The strip forms' per-chain functors (fermion_mc, fermion_eloc) on the device: one thread per
+// chain through the batched engine's element kernel.
+template <typename T, typename OT, typename F>
+inline void fv_apply(CudaBE<T, OT>& be, const F& f, int n) {
+  PV_KLAUNCH(be.prof, be.st, "kb_elem_fermion", 0.0, 0.0,
+             kb_elem<<<CudaBE<T, OT>::gx(n, 128), 128, 0, be.st>>>(f, n));
+}
+
+// The 64 slices per site of the strip forms from the sixteen of theta (float64, per site
+// [16][dl][dr][du][dd]): slice S + 16 b + 32 x is T[S] times (-1)^((p(S) + p(d)) (p(l) + p(u))
+// + p(d) b + x p(r)).  Block y = site, threads over slice x element.
+template <typename T>
+__global__ void k_fsigned64(int L1, int L2, int D, const double* __restrict__ th16,
+                            const long long* __restrict__ toff16, T* __restrict__ th64,
+                            const long long* __restrict__ toff64) {
+  const int i = blockIdx.y, r = i / L2, c = i % L2;
+  const int dl = c == 0 ? 1 : D, dr = c == L2 - 1 ? 1 : D, du = r == 0 ? 1 : D, dd = r == L1 - 1 ? 1 : D;
+  const long long sz = (long long)dl * dr * du * dd;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < 64 * sz;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int slice = (int)(e / sz), S = slice & 15, bb = (slice >> 4) & 1, x = slice >> 5;
+    const long long k = e - (long long)slice * sz;
+    long long t = k;
+    const int d = (int)(t % dd);
+    t /= dd;
+    const int u = (int)(t % du);
+    t /= du;
+    const int rr = (int)(t % dr);
+    t /= dr;
+    const int l = (int)t;
+    const int pS = __popc(S) & 1;
+    const int ex = (pS + (d & 1)) * ((l & 1) + (u & 1)) + (d & 1) * bb + x * (rr & 1);
+    const double v = th16[toff16[i] + (long long)S * sz + k];
+    th64[toff64[i] + e] = (T)((ex & 1) ? -v : v);
+  }
+}
 
 // Sp = S with move mv applied, per chain; act = 1 where the move applies (else 0, Sp = S).
 __global__ void k_fpropose(int nb, int N, const uint8_t* __restrict__ S, uint8_t* __restrict__ Sp,

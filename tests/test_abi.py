@@ -137,6 +137,7 @@ def test_fermion_calls_reject_a_null_evaluator_and_init_theta_is_the_identity():
     assert lib.peps_famp_sr_step(None, None, 0, None, 1, 1.0, 8.0, 4.0, 2, 0.01, 1e-4, 10,
                                  1e-8, None) == binding.PEPS_EINVAL
     assert lib.peps_famp_profile(None, 1) == binding.PEPS_EINVAL
+    assert lib.peps_famp_set_strips(None, 1) == binding.PEPS_EINVAL
     assert lib.peps_famp_launches(None) == 0
     L1, L2, D = 2, 3, 2
     th = binding.famp_init_theta(L1, L2, D, noise=0.0, seed=3)
