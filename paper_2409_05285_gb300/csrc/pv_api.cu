@@ -2082,9 +2082,12 @@ int famp_theta(peps_famp* f, const double* theta) {
 }
 
 // The strip forms on the engine's runner, pointed at the 64 slices for the call: one sweep
-// (fermion_mc) or the local energies (fermion_eloc) of the nb chains in d_S16, chunk by chunk.
+// (fermion_mc), the local energies (fermion_eloc) or the local energies with the O rows
+// (fermion_eval) of the nb chains in d_S16, chunk by chunk.
+enum { FAMP_SWEEP = 0, FAMP_ELOC = 1, FAMP_EVAL = 2 };
+
 template <typename T>
-int famp_strips_t(peps_famp* f, BatchImpl<T>* bi, int nb, bool sweep, int p, uint64_t seed,
+int famp_strips_t(peps_famp* f, BatchImpl<T>* bi, int nb, int what, int p, uint64_t seed,
                   uint32_t sweep_no, double t_hop, double U, double mu) {
   peps_ctx* c = f->c;
   const int N = c->N;
@@ -2096,12 +2099,16 @@ int famp_strips_t(peps_famp* f, BatchImpl<T>* bi, int nb, bool sweep, int p, uin
   const int chunk = c->batch->chunk;
   for (int off = 0; off < nb; off += chunk) {
     const int n = std::min(chunk, nb - off);
-    if (sweep)
+    if (what == FAMP_SWEEP)
       fermion_mc(run, f->d_S16 + (long long)off * N, f->d_S32 + (long long)off * N, n, p, seed,
                  sweep_no, f->d_acc + off, off);
-    else
+    else if (what == FAMP_ELOC)
       fermion_eloc(run, f->d_S16 + (long long)off * N, f->d_S32 + (long long)off * N, n, t_hop, U, mu,
                    f->d_la + off, f->d_sg + off, f->d_es + off, f->d_ea + off);
+    else
+      fermion_eval(run, f->d_S16 + (long long)off * N, f->d_S32 + (long long)off * N, n, t_hop, U, mu,
+                   f->d_la + off, f->d_sg + off, f->d_es + off, f->d_ea + off,
+                   (T*)f->d_O + (long long)off * c->No, c->No, f->d_ooff);
   }
   run.theta = th_old;
   run.toff = toff_old;
@@ -2109,10 +2116,10 @@ int famp_strips_t(peps_famp* f, BatchImpl<T>* bi, int nb, bool sweep, int p, uin
   return PEPS_OK;
 }
 
-int famp_strips(peps_famp* f, int nb, bool sweep, int p, uint64_t seed, uint32_t sweep_no,
+int famp_strips(peps_famp* f, int nb, int what, int p, uint64_t seed, uint32_t sweep_no,
                 double t_hop, double U, double mu) {
-  return f->b64 ? famp_strips_t(f, f->b64, nb, sweep, p, seed, sweep_no, t_hop, U, mu)
-                : famp_strips_t(f, f->b32, nb, sweep, p, seed, sweep_no, t_hop, U, mu);
+  return f->b64 ? famp_strips_t(f, f->b64, nb, what, p, seed, sweep_no, t_hop, U, mu)
+                : famp_strips_t(f, f->b32, nb, what, p, seed, sweep_no, t_hop, U, mu);
 }
 
 // log|psi|, sign, E_sys and E_anc of the nb configurations in d_S16 (theta's slices made):
@@ -2155,7 +2162,7 @@ int famp_energies(peps_famp* f, int nb, double t_hop, double U, double mu) {
     f->x_cap = cap;
   }
   PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));   // also checks the entries
-  if (f->strips) return famp_strips(f, nb, false, 2, 0, 0, t_hop, U, mu);
+  if (f->strips) return famp_strips(f, nb, FAMP_ELOC, 2, 0, 0, t_hop, U, mu);
   const unsigned gb = (unsigned)((nb + 127) / 128);
   PV_KLAUNCH(&c->kprof, st, "k_fhop_count", 0.0, 0.0,
              k_fhop_count<<<gb, 128, 0, st>>>(nb, N, f->d_S16, f->d_bi, f->d_bj, f->nbonds, f->d_cnt));
@@ -2177,17 +2184,24 @@ int famp_energies(peps_famp* f, int nb, double t_hop, double U, double mu) {
 
 // O rows of the nb configurations in d_S16 into d_O (theta's slices made): the plain rows of
 // the signed slices, then the per-entry signs.
+// The O-row buffer of n_max configurations and the site offsets of a row, made once.
+int famp_orows_alloc(peps_famp* f) {
+  if (f->d_O) return PEPS_OK;
+  peps_ctx* c = f->c;
+  const int N = c->N;
+  const size_t real = f->b64 ? sizeof(double) : sizeof(float);
+  PV_TRY(dalloc(c, (unsigned char**)&f->d_O, (size_t)f->n_max * c->No * real));
+  PV_TRY(dalloc(c, &f->d_ooff, (N + 1) * sizeof(long long)));
+  PV_CUDA(c, cudaMemcpy(f->d_ooff, c->ooff.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+  return PEPS_OK;
+}
+
 int famp_orows(peps_famp* f, int nb) {
   peps_ctx* c = f->c;
   const int N = c->N;
   const long long No = c->No;
   cudaStream_t st = c->stream;
-  const size_t real = f->b64 ? sizeof(double) : sizeof(float);
-  if (!f->d_O) {
-    PV_TRY(dalloc(c, (unsigned char**)&f->d_O, (size_t)f->n_max * No * real));
-    PV_TRY(dalloc(c, &f->d_ooff, (N + 1) * sizeof(long long)));
-    PV_CUDA(c, cudaMemcpy(f->d_ooff, c->ooff.data(), (N + 1) * sizeof(long long), cudaMemcpyHostToDevice));
-  }
+  PV_TRY(famp_orows_alloc(f));
   PV_CUDA(c, cudaMemsetAsync(f->d_bad, 0, sizeof(int), st));
   PV_KLAUNCH(&c->kprof, st, "k_fconfigs", 0.0, 0.0,
              k_fconfigs<<<(nb + 127) / 128, 128, 0, st>>>(nb, c->P.L1, c->P.L2, f->d_S16, f->d_S32,
@@ -2439,7 +2453,7 @@ int peps_famp_sweep(peps_famp* f, const double* theta, size_t n_theta, uint8_t* 
   PV_CUDA(c, cudaMemsetAsync(f->d_acc, 0, (size_t)nb * sizeof(int), st));
   const unsigned gb = (unsigned)((nb + 127) / 128);
   for (int k = 0; k < n_sweeps && f->strips; ++k)
-    PV_TRY(famp_strips(f, nb, true, p, seed, (uint32_t)(sweep0 + k), 0.0, 0.0, 0.0));
+    PV_TRY(famp_strips(f, nb, FAMP_SWEEP, p, seed, (uint32_t)(sweep0 + k), 0.0, 0.0, 0.0));
   if (f->strips && n_sweeps > 0) PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg, false));
   for (int k = 0; k < n_sweeps && !f->strips; ++k) {
     const double* uk = u ? f->d_u + (size_t)k * nb * M : nullptr;
@@ -2487,8 +2501,19 @@ int peps_famp_sr_step(peps_famp* f, double* theta, size_t n_theta, const uint8_t
   PV_TRY(famp_sr_buffers(f));
   PV_TRY(famp_theta(f, theta));
   PV_CUDA(c, cudaMemcpyAsync(f->d_S16, S, (size_t)nb * N, cudaMemcpyHostToDevice, st));
-  PV_TRY(famp_energies(f, nb, t_hop, U, mu));
-  PV_TRY(famp_orows(f, nb));
+  if (f->strips) {
+    // local energies and O rows in one pass over the rows (the hop buffers are not needed)
+    PV_TRY(famp_orows_alloc(f));
+    if (!f->d_es) {
+      PV_TRY(dalloc(c, &f->d_es, (size_t)f->n_max * sizeof(double)));
+      PV_TRY(dalloc(c, &f->d_ea, (size_t)f->n_max * sizeof(double)));
+    }
+    PV_TRY(famp_amplitudes(f, f->d_S16, nb, f->d_la, f->d_sg));   // checks the entries
+    PV_TRY(famp_strips(f, nb, FAMP_EVAL, 2, 0, 0, t_hop, U, mu));
+  } else {
+    PV_TRY(famp_energies(f, nb, t_hop, U, mu));
+    PV_TRY(famp_orows(f, nb));
+  }
   PV_KLAUNCH(&c->kprof, st, "k_fweights", 0.0, 0.0,
              k_fweights<<<1, SR_WEIGHT_THREADS, 0, st>>>(nb, N, p, f->d_la, f->d_sg, f->d_es, f->d_ea,
                                                          f->d_S16, f->d_w, f->d_E, f->d_sc, f->d_fo));

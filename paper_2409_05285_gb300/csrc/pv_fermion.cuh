@@ -428,6 +428,116 @@ void fermion_eloc(BatchRunner<T, BE, OT>& run, const uint8_t* S16, uint8_t* S32,
   }
 }
 
+// The plain O rows of one chain into those of the fermionic tensors: entry (l, r, u, d) of site
+// i times (-1)^((p(S_i) + p(d)) (p(l) + p(u)) + p(d) b_i) (as k_fosign, one chain per call).
+template <typename OT>
+struct FOSign {
+  const uint8_t* S16;
+  int L1, L2, D;
+  OT* O;
+  long long No;
+  const long long* ooff;
+  PV_HD void operator()(int s) const {
+    const uint8_t* x = S16 + (long long)s * L1 * L2;
+    for (int i = 0; i < L1 * L2; ++i) {
+      const int r = i / L2, c = i % L2;
+      const int dr = c == L2 - 1 ? 1 : D, du = r == 0 ? 1 : D, dd = r == L1 - 1 ? 1 : D;
+      int bb = 0;
+      for (int q = 0; q < c; ++q) bb ^= fv_parity4(x[r * L2 + q]);
+      const int pS = fv_parity4(x[i]);
+      const long long sz = ooff[i + 1] - ooff[i];
+      for (long long k = 0; k < sz; ++k) {
+        long long t = k;
+        const int d = (int)(t % dd);
+        t /= dd;
+        const int u = (int)(t % du);
+        t /= du;
+        t /= dr;
+        const int l = (int)t;
+        const int ex = (pS + (d & 1)) * ((l & 1) + (u & 1)) + (d & 1) * bb;
+        if (ex & 1) {
+          OT* q = O + (long long)s * No + ooff[i] + k;
+          *q = -*q;
+        }
+      }
+    }
+  }
+};
+
+// One pass per chain over the rows (`run` over the 64-slice tensors; S32 work space): log|psi|,
+// the sign, E_sys and E_anc (as fermion_eloc) and the O rows (Eq. 8: every site's environment
+// over the strip value, then the Fermi-arrow signs; `ooff_dev` the site offsets of the rows as
+// the functors read them).
+template <typename T, typename BE, typename OT>
+void fermion_eval(BatchRunner<T, BE, OT>& run, const uint8_t* S16, uint8_t* S32, int n,
+                  double t_hop, double U, double mu, double* la, int8_t* sg, double* es,
+                  double* ea, OT* O, long long No, const long long* ooff_dev) {
+  auto& b = run.b;
+  auto& be = run.be;
+  const int L1 = run.L1, L2 = run.L2, N = run.N;
+  fv_apply(be, FConf{S16, S32, L1, L2}, n);
+  run.build_down(S32, n);
+  fv_apply(be, FDiag{S16, N, U, mu, es, ea}, n);
+  run.trivial(run.uprow(0), b.sU, n);
+  for (int r = 0; r < L1; ++r) {
+    be.set(b.p1R, b.sp1R, (long long)L2 * b.P1, (T)1, n);
+    for (int c = L2 - 1; c >= 0; --c)
+      run.s1_right(r, c, run.p1R(c), b.sp1R, run.bat(run.p1R(c + 1), b.sp1R), run.site(r, c, S32), n);
+    if (r == 0) {
+      be.amp(b.p1R, b.sp1R, b.lsD + 1, L1 + 1, la, sg, n);
+      fv_apply(be, FSignApply{S16, L1, L2, sg}, n);
+    }
+    T* Lc = b.p1L;
+    T* Ln = b.p1L + b.P1;
+    be.set(b.p1L, b.sp1L, 0, (T)1, n);
+    for (int c = 0; c < L2; ++c) {
+      const int i = r * L2 + c;
+      run.s1_env(r, c, run.bat(Lc, b.sp1L), run.bat(run.p1R(c + 1), b.sp1R), n);
+      be.writeO(O, No, run.ooff[i], b.envo, b.D4, run.szs(r, c), b.p1R, b.sp1R, n);
+      if (c + 1 < L2) {
+        for (int k = 0; k < 4; ++k) {
+          fv_apply(be, FSel{S16, S32, N, 1, i, i + 1, k, 0, b.si, b.sj, b.valid}, n);
+          run.s1_left(r, c, b.m0, b.P2, run.bat(Lc, b.sp1L), run.site_sel(r, c, b.si), n);
+          run.s1_left(r, c + 1, b.m1, b.P2, run.bat(b.m0, b.P2), run.site_sel(r, c + 1, b.sj), n);
+          be.dot(OpDot<T>{b.m1, b.P2, run.p1R(c + 2), b.sp1R, run.s1_len(r, c + 2), b.num}, n);
+          fv_apply(be, FRatio<T>{S16, L1, L2, i, i + 1, k, -1, c, b.valid, b.num, b.p1R, b.sp1R,
+                                 t_hop, es, ea}, n);
+        }
+        run.s1_left(r, c, Ln, b.sp1L, run.bat(Lc, b.sp1L), run.site(r, c, S32), n);
+        T* t = Lc;
+        Lc = Ln;
+        Ln = t;
+      }
+    }
+    if (r + 1 < L1) {
+      be.set(b.p2R, b.sp2R, (long long)L2 * b.P2, (T)1, n);
+      for (int c = L2 - 1; c >= 0; --c)
+        run.s2_right(r, c, run.p2R(c), b.sp2R, run.bat(run.p2R(c + 1), b.sp2R), run.site(r, c, S32),
+                     run.site(r + 1, c, S32), n);
+      T* L2c = b.p2L;
+      T* L2n = b.p2L + b.P2;
+      be.set(b.p2L, b.sp2L, 0, (T)1, n);
+      for (int c = 0; c < L2; ++c) {
+        const int i = r * L2 + c, j = i + L2;
+        for (int k = 0; k < 4; ++k) {
+          fv_apply(be, FSel{S16, S32, N, 2, i, j, k, c + 1 < L2, b.si, b.sj, b.valid}, n);
+          run.s2_left(r, c, b.m0, b.P2, run.bat(L2c, b.sp2L), run.site_sel(r, c, b.si),
+                      run.site_sel(r + 1, c, b.sj), n);
+          be.dot(OpDot<T>{b.m0, b.P2, run.p2R(c + 1), b.sp2R, run.s2_len(r, c + 1), b.num}, n);
+          fv_apply(be, FRatio<T>{S16, L1, L2, i, j, k, r + 1, c, b.valid, b.num, b.p2R, b.sp2R,
+                                 t_hop, es, ea}, n);
+        }
+        run.s2_left(r, c, L2n, b.sp2L, run.bat(L2c, b.sp2L), run.site(r, c, S32), run.site(r + 1, c, S32), n);
+        T* t = L2c;
+        L2c = L2n;
+        L2n = t;
+      }
+      run.compress(run.uprow(r), b.sU, run.shp.up[r], false, r, S32, run.uprow(r + 1), b.sU, b.lsU, 1, n);
+    }
+  }
+  fv_apply(be, FOSign<OT>{S16, L1, L2, run.D, O, No, ooff_dev}, n);
+}
+
 #if defined(__CUDACC__)
 
 // The plain O rows into those of the fermionic tensors: entry (l, r, u, d) of site i times

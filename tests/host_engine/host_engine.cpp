@@ -12,8 +12,8 @@
 //        compression's right factors from Gram matrices, 4 plain amplitude and O rows of a
 //        PEPS of 32 slices per site, the fermionic engine's form, 5 one fermionic Metropolis
 //        sweep on cached strips over 64 slices per site, 6 fermionic local energies on
-//        strips over 64 slices per site; t, U, mu in place of J1, J2 and seed), L1, L2, D,
-//        chi, n, p;
+//        strips over 64 slices per site, 7 as 6 with the O rows in the same pass; t, U, mu in
+//        place of J1, J2 and seed), L1, L2, D, chi, n, p;
 //        float64 J1, J2; uint64 seed; int32 sweep; float64 theta[N_p]; uint8 S[n][N];
 //        mode 2 only: float64 b_d, exponent, u[n][N]
 //   out: eval: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n], O[n][N_o]
@@ -22,6 +22,7 @@
 //        mode 4: float64 log_abs[n], int8 sign[n], O[n][N_o]  (pv_fermion.cuh)
 //        mode 5: uint8 S[n][N], int32 acc[n]  (fermion_mc, pv_fermion.cuh)
 //        mode 6: float64 log_abs[n], int8 sign[n], float64 e_sys[n], e_anc[n]  (fermion_eloc)
+//        mode 7: as mode 6, then float64 O[n][N_o]  (fermion_eval)
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -170,7 +171,7 @@ int main(int argc, char** argv) {
   rd(fi, &sweep, 1);
   const int N = L1 * L2;
   std::vector<long long> toff(N + 1, 0), ooff(N + 1, 0);
-  const int slices = mode == 4 ? 32 : (mode == 5 || mode == 6) ? 64 : 4;
+  const int slices = mode == 4 ? 32 : (mode >= 5 && mode <= 7) ? 64 : 4;
   for (int i = 0; i < N; ++i) {
     const int r = i / L2, c = i % L2;
     const long long sz = (long long)(c == 0 ? 1 : D) * (c == L2 - 1 ? 1 : D) * (r == 0 ? 1 : D) *
@@ -254,6 +255,21 @@ int main(int argc, char** argv) {
     plain_log_derivative(run, S.data(), n, O.data(), No);
     std::fwrite(la.data(), 8, n, fo);
     std::fwrite(sg.data(), 1, n, fo);
+    std::fwrite(O.data(), 8, O.size(), fo);
+  } else if (mode == 7) {
+    double mu;
+    std::memcpy(&mu, &seed, sizeof(mu));
+    const long long No = ooff[N];
+    std::vector<uint8_t> S32((size_t)n * N, 0);
+    std::vector<double> la(n), es(n), ea(n);
+    std::vector<int8_t> sg(n);
+    std::vector<T> O((size_t)n * No);
+    fermion_eval(run, S.data(), S32.data(), n, J[0], J[1], mu, la.data(), sg.data(), es.data(),
+                 ea.data(), O.data(), No, ooff.data());
+    std::fwrite(la.data(), 8, n, fo);
+    std::fwrite(sg.data(), 1, n, fo);
+    std::fwrite(es.data(), 8, n, fo);
+    std::fwrite(ea.data(), 8, n, fo);
     std::fwrite(O.data(), 8, O.size(), fo);
   } else if (mode == 6) {
     // the couplings arrive in J1 (t), J2 (U) and the seed's bits (mu, a float64)

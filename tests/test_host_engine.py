@@ -40,11 +40,14 @@ def _run(exe, tmp, mode, lat, chi, th, S, p=2, seed=0, sweep=0):
         f.write(np.asarray(S, dtype=np.uint8).tobytes())
     subprocess.run([exe, fin, fout], check=True)
     raw = open(fout, "rb").read()
-    if mode == 6:
+    if mode in (6, 7):
         la = np.frombuffer(raw, np.float64, n, 0)
         sg = np.frombuffer(raw, np.int8, n, 8 * n)
         es = np.frombuffer(raw, np.float64, n, 9 * n)
         ea = np.frombuffer(raw, np.float64, n, 17 * n)
+        if mode == 7:
+            O = np.frombuffer(raw, np.float64, n * lat.No, 25 * n).reshape(n, lat.No)
+            return la, sg, es, ea, O
         return la, sg, es, ea
     if mode == 5:
         S2 = np.frombuffer(raw, np.uint8, n * lat.N, 0).reshape(n, lat.N)
@@ -303,3 +306,34 @@ def test_host_engine_fermion_local_energy_on_strips_matches_oracle(engine, tmp_p
         scale = max(1.0, abs(r_es), abs(r_ea))
         assert abs(es[k] - r_es) <= 1e-9 * scale, (k, es[k], r_es)
         assert abs(ea[k] - r_ea) <= 1e-9 * scale, (k, ea[k], r_ea)
+
+
+@pytest.mark.parametrize("case", [(2, 2, 2, 4, 4), (3, 3, 2, 8, 3), (2, 3, 3, 9, 3)])
+def test_host_engine_fermion_eval_one_pass_matches_oracle(engine, tmp_path, case):
+    # fermion_eval: the amplitude, the local energies and the signed O rows in one pass over the
+    # rows, against the oracle's amplitude, local energies and sums over every virtual
+    # assignment (exact chi)
+    from oracle import fermion as fm
+    L1, L2, D, chi, n = case
+    N = L1 * L2
+    t_hop, U, mu = 1.0, 8.0, 4.0
+    rng = np.random.default_rng(17 * L1 + 7 * L2 + D)
+    T = fm.random_even_fpeps(L1, L2, D, rng, scale=0.5)
+    for i, A in enumerate(fm.identity_fpeps(L1, L2)):
+        T[i][(slice(None), 0, 0, 0, 0)] += A[:, 0, 0, 0, 0]
+    S = rng.integers(0, 16, (n, N))
+    for k in range(n):
+        if sum(bin(int(x)).count("1") for x in S[k]) % 2:
+            S[k, 0] ^= 1
+    S = S.astype(np.uint8)
+    lat = Lattice(L1, L2, D, J1=t_hop, J2=U)
+    mu_bits = struct.unpack("<Q", struct.pack("<d", mu))[0]
+    la, sg, es, ea, O = _run(engine, tmp_path, 7, lat, chi, _fermion_th64(T), S, seed=mu_bits)
+    for k in range(n):
+        grads, psi = fm.fpeps_log_derivative(L1, L2, T, S[k])
+        assert sg[k] == np.sign(psi) and abs(la[k] - np.log(abs(psi))) <= 1e-10, k
+        r_es, r_ea = fm.fpeps_local_energy(L1, L2, T, S[k], t_hop, U, mu)
+        scale = max(1.0, abs(r_es), abs(r_ea))
+        assert abs(es[k] - r_es) <= 1e-9 * scale and abs(ea[k] - r_ea) <= 1e-9 * scale, k
+        ref = np.concatenate([g.ravel() for g in grads])
+        assert np.max(np.abs(O[k] - ref)) <= 1e-9 * max(1.0, np.max(np.abs(ref))), k
