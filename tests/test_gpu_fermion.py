@@ -184,3 +184,31 @@ def test_log_derivatives_match_oracle(prec, tol):
         scale = max(1.0, np.max(np.abs(ref)))
         assert np.max(np.abs(O[k] - ref)) <= tol * scale, k
     f.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(binding.PEPS_FP64, 1e-10), (binding.PEPS_TF32, 5e-2)])
+def test_bench_size_amplitudes_match_oracle(prec, tol):
+    # the fermion bench's configuration (6x6, D = 4, chi = 16, 1024 chains, its perturbed |I>
+    # from peps_famp_init_theta): six sampled configurations, on and one hop off the |I>
+    # support, against the oracle's exact row-vector contraction.  chi = 16 truncates here;
+    # on this state the truncated contraction differs from the exact one by under 1e-14 in
+    # log|psi| (measured with the host build of the engine), so FP64 is held to 1e-10.
+    from oracle import fermion_vmc as fv
+    from paper_2409_05285_gb300 import workloads as wl
+    L, D, chi, n = 6, 4, 16, 1024
+    th = binding.famp_init_theta(L, L, D, 1e-3, 0)
+    T = fv.unflatten(th, [np.zeros((16,) + d) for d in wl.site_dims(L, L, D)])
+    S = wl.fermion_support_configs(n, L * L, 1)
+    for k in range(3, 6):
+        x = fv.propose(list(S[k]), ("hop", 0, 1, 0)) or fv.propose(list(S[k]), ("hop", 0, 1, 1))
+        if x:
+            S[k] = x
+    f = binding.FermionAmplitudes(L, L, D, chi, n, precision=prec)
+    la, sg = f.eval(th, S)
+    amp = fm.fpeps_amplitude_function(L, L, T)
+    for k in range(6):
+        ref = amp(S[k])
+        assert sg[k] == np.sign(ref), k
+        assert abs(la[k] - np.log(abs(ref))) <= tol, k
+    assert np.all(sg != 0)
+    f.close()
