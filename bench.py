@@ -977,6 +977,34 @@ def run_serve(args):
     print(json.dumps(out))
 
 
+def compare_fp64_fermion(f, wl, binding, theta, S, m, stream):
+    """The fermionic mixed-precision path against the FP64 path on the same parameters and the
+    same m configurations: amplitude and local-energy differences, and the evaluation
+    throughput (amplitudes and local energies) of both paths."""
+    import numpy as np
+    t_hop, U, mu = wl.extra["t"], wl.extra["U"], wl.extra["mu"]
+    S = np.ascontiguousarray(S[:m])
+    ref = binding.FermionAmplitudes(wl.L, wl.L, wl.D, wl.chi, m, precision=binding.PEPS_FP64,
+                                    stream=ctypes_stream(stream))
+    out = {}
+    for name, g in (("mixed", f), ("fp64", ref)):
+        g.local_energy(theta, S[: min(m, 8)], t_hop, U, mu)    # warm-up
+        t0 = time.perf_counter()
+        la, sg, es, ea = g.local_energy(theta, S, t_hop, U, mu)
+        out[name] = (la, sg, es + ea, m / (time.perf_counter() - t0))
+    ref.close()
+    la32, sg32, e32, r32 = out["mixed"]
+    la64, sg64, e64, r64 = out["fp64"]
+    N = wl.L * wl.L
+    return {"chains": m, "max_abs_dlog_amp": float(np.max(np.abs(la32 - la64))),
+            "sign_mismatch": int(np.sum(sg32 != sg64)),
+            "E_site_mixed": float(np.mean(e32) / (2 * N)), "E_site_fp64": float(np.mean(e64) / (2 * N)),
+            "dE_site": float(abs(np.mean(e32) - np.mean(e64)) / (2 * N)),
+            "max_dEloc_site": float(np.max(np.abs(e32 - e64)) / (2 * N)),
+            "eval_samples_per_s_mixed": r32, "eval_samples_per_s_fp64": r64,
+            "speedup_mixed_over_fp64": r32 / r64}
+
+
 def l2_flusher(stream):
     """A function that writes a 256 MB device buffer (twice the 129 MB L2) on `stream`."""
     import torch
@@ -1163,6 +1191,9 @@ def run_fermion(args):
         state["sweep"] += 1
         state["t"] += tau
     e2e_step = statistics.median(e2e_ms)
+    fp64_check = None
+    if prec != binding.PEPS_FP64 and not args.no_fp64_check:
+        fp64_check = compare_fp64_fermion(f, wl, binding, theta, S, min(n, args.fp64_chains), stream)
     np_ = theta.size
     h2d = 2 * np_ * 8 + 2 * n * N
     d2h = n * N + n * (4 + 8 + 1) + np_ * 8
@@ -1198,6 +1229,7 @@ def run_fermion(args):
         "cg_iters": statistics.mean(s_["cg_iters"] for s_ in stats),
         "E_site": stats[-1]["E_site"], "E_err": stats[-1]["E_err"], "docc": stats[-1]["docc"],
         "density": stats[-1]["density"], "beta_obs": 4 * (state["t"] - tau * len(e2e_ms)),
+        "fp64_check": fp64_check,
         "roofline": roofline,
         "kernels": kernels,
         "kernels_by_phase": {ph: kernel_shares(prof[ph]) for ph in ("sweep", "sr_step")},

@@ -339,7 +339,9 @@ def test_fermion_run_prints_the_contract_line(monkeypatch, capsys):
     class FA:
         def __init__(self, L1, L2, D, chi, n, precision=None, stream=None):
             self.n, self.N, self.k = n, L1 * L2, 0
-            assert (L1, L2, D, chi, n) == (6, 6, 4, 16, 1024)
+            self.prec = precision
+            assert (L1, L2, D, chi) == (6, 6, 4, 16) and n in (1024, 608)
+            calls.append(("create", n, precision))
 
         n_moves = 312
 
@@ -353,6 +355,12 @@ def test_fermion_run_prints_the_contract_line(monkeypatch, capsys):
             self.k += 30
             return theta - 1e-3, {"E_site": -2.5, "E_err": 0.01, "docc": 0.2, "density": 1.0,
                                   "cg_iters": 40, "cg_resid": 1e-8, "cg_maxit": False}
+
+        def local_energy(self, theta, S, t_hop, U, mu):
+            m = len(S)
+            shift = 0.0 if self.prec == binding.PEPS_FP64 else 1e-4
+            return (np.zeros(m) + shift, np.ones(m, np.int8), np.full(m, -70.0 + shift),
+                    np.full(m, -70.0))
 
         def profile(self, on):
             pass
@@ -390,3 +398,9 @@ def test_fermion_run_prints_the_contract_line(monkeypatch, capsys):
     assert all(c[2] == (1.0, 8.0, 4.0) for c in calls if c[0] == "sr")
     assert sum(1 for c in calls if c[0] == "flush") == 2
     assert out["e2e"]["h2d_bytes_per_step"] == 2 * 1600 * 8 + 2 * 1024 * 36
+    # the FP64 comparison on 608 of the chains: a second evaluator in FP64
+    assert ("create", 608, binding.PEPS_FP64) in calls
+    chk = out["fp64_check"]
+    assert chk["chains"] == 608 and chk["sign_mismatch"] == 0
+    assert chk["max_abs_dlog_amp"] == pytest.approx(1e-4)
+    assert chk["dE_site"] == pytest.approx(1e-4 / 72)
